@@ -1,0 +1,192 @@
+/*
+ * oefe.h -- C ABI of the GB300 library for the Chebyshev-filtered subspace
+ * iteration of the orthogonalized enriched finite element (OEFE) method
+ * (Rufus, Kanungo, Gavini, arXiv 2010.09701).
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * - Every function returns an int status: OEFE_OK (0) or a negative
+ *   OEFE_ERR_* code. No exception crosses the ABI. oefe_last_error() copies a
+ *   one-line description of the last failure of a context.
+ * - A context is not thread-safe. All GPU work is ordered on the CUDA stream
+ *   given to oefe_create() (or oefe_set_stream()). Calls that return values
+ *   in host memory synchronize that stream before returning.
+ * - "device" pointers are CUDA global-memory pointers on the context's
+ *   device; "host" pointers are ordinary CPU memory. The caller owns every
+ *   pointer it passes; the library owns everything reachable from the
+ *   context and frees it in oefe_destroy().
+ * - Vector blocks X are row-major (ndof x ld) with the nv <= ld columns
+ *   innermost. Rows 0 .. n_h-1 are the classical (CFE) coefficients of the
+ *   global nodes, rows n_h .. n_h+n_O-1 the orthogonalized enrichment
+ *   coefficients (Eq. UOEFE). Complex data are interleaved (re, im).
+ * - Required call order: create -> mesh -> enrichment -> quadrature ->
+ *   kpoints -> build_hamiltonian -> {apply, filter, orthonormalize,
+ *   rayleigh_ritz, density, ...}. Out-of-order calls return OEFE_ERR_STATE.
+ */
+#ifndef OEFE_H
+#define OEFE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct oefe_ctx* oefe_ctx_t;
+
+enum {
+  OEFE_OK = 0,
+  OEFE_ERR_ARG = -1,        /* invalid argument (size, pointer, range)        */
+  OEFE_ERR_STATE = -2,      /* call made before the calls it depends on        */
+  OEFE_ERR_OOM = -3,        /* device or host allocation failed                */
+  OEFE_ERR_CUDA = -4,       /* a CUDA runtime call failed                      */
+  OEFE_ERR_CHOLESKY = -5,   /* Gram / projected overlap not positive definite  */
+  OEFE_ERR_NOTPD_MOO = -6,  /* enrichment overlap block M^oo not pos. definite */
+  OEFE_ERR_TIMEOUT = -7,    /* a bounded device wait gave up                   */
+  OEFE_ERR_NUMERIC = -8     /* NaN or Inf detected                             */
+};
+
+/* Element type of vector blocks. */
+enum { OEFE_F64 = 0, OEFE_F32 = 1, OEFE_C128 = 2, OEFE_C64 = 3 };
+
+/* Storage of the cell Hamiltonians (bit mask for oefe_build_hamiltonian). */
+enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2 };
+
+/* ---------------------------------------------------------------- context */
+int oefe_create(oefe_ctx_t* out, int device, void* cuda_stream);
+int oefe_destroy(oefe_ctx_t ctx);
+int oefe_set_stream(oefe_ctx_t ctx, void* cuda_stream);
+int oefe_last_error(oefe_ctx_t ctx, char* buf, size_t len);
+
+/* ---------------------------------------------------------------- geometry
+ * oefe_mesh -- periodic cubic cell [0,a)^3 split into ncell[0]*ncell[1]*
+ * ncell[2] hexahedral spectral elements of order p (Sec. III A: Lagrange
+ * polynomials on GLL nodes so that the CFE overlap is diagonal).
+ *   xb   host, ncell[0]+ncell[1]+ncell[2]+3 doubles: the per-axis cell
+ *        boundaries, x then y then z, each increasing from 0 to a.
+ *   p    1 .. 7.
+ * Cell (ix,iy,iz) has index ix + ncell0 (iy + ncell1 iz); global node
+ * (gx,gy,gz) has index gx + N0 (gy + N1 gz), N_d = ncell_d p.
+ */
+int oefe_mesh(oefe_ctx_t ctx, double a, const int ncell[3], const double* xb, int p);
+
+/* oefe_mesh_graded -- the same with breakpoints refined toward the nuclei:
+ * the distinct nuclear coordinates of an axis become breakpoints; when there
+ * are at most ncell/2 of them, cells are shared out among the intervals in
+ * proportion to length (at least 2 each) and graded geometrically with
+ * `ratio` from both interval ends; otherwise the axis is uniform.
+ *   pos  host, 3*natoms doubles.   xb_out  host, 3*(ncell+1) doubles or NULL. */
+int oefe_mesh_graded(oefe_ctx_t ctx, double a, int ncell, int p, int natoms,
+                     const double* pos, double ratio, double* xb_out);
+
+/* oefe_enrichment -- atomic enrichment functions (Eqs. UOEFEAtomic,
+ * KSAtomicTrunc, CutoffProperties):
+ *   N^A_{I,j}(x) = exp(-i k.(x - R_I^x)) R_{I,j}(r) S_j(x - R_I^x) h(r),
+ * r = |x - R_I^x|, R_I^x the nearest periodic image of nucleus I.
+ *   pos   host, 3*natoms doubles (bohr).
+ *   lm    host, nfun ints: angular code per function, 0 = s, 1/2/3 = p_x/p_y/p_z.
+ *   R, dR host, natoms*nfun*ngrid doubles: radial function and its
+ *         derivative on the uniform grid r_i = i rc/(ngrid-1) (cubic Hermite
+ *         interpolation between grid points, zero for r >= rc).
+ *   r0 < rc: smooth cutoff h = phi(s)/(phi(s)+phi(1-s)), s = (rc-r)/(rc-r0),
+ *         phi(t) = exp(-1/t) (t > 0), which is 1 below r0 and 0 above rc;
+ *         rc < a/2 is required. Function index nu = I*nfun + j. natoms may be 0. */
+int oefe_enrichment(oefe_ctx_t ctx, int natoms, const double* pos, int nfun, const int* lm,
+                    int ngrid, const double* R, const double* dR, double r0, double rc);
+
+/* oefe_quadrature -- per-cell point sets (Sec. III B adaptive quadrature,
+ * deterministic reading): a cell meeting no enrichment support gets
+ * nq_cell^3 Gauss points; a cell meeting one gets nq_enr^3; a cell whose
+ * closed box holds a nucleus is split into 8 children, recursively while a
+ * child holds a nucleus, up to `depth` levels, with nq_enr^3 points per leaf.
+ * Point order: cells ascending, leaves depth-first (children x fastest),
+ * points x fastest. 1 <= nq_cell, nq_enr <= 12, 0 <= depth <= 12. */
+int oefe_quadrature(oefe_ctx_t ctx, int nq_cell, int nq_enr, int depth);
+int oefe_quadrature_count(oefe_ctx_t ctx, int64_t* nq_total);
+/* host outputs: xyz 3*nq doubles, w nq doubles (either may be NULL). */
+int oefe_quadrature_points(oefe_ctx_t ctx, double* xyz, double* w);
+
+/* oefe_kpoints -- Bloch vectors (Cartesian bohr^-1, host 3*nk) and weights
+ * (host nk, sum 1). For each k the library tabulates the enrichment at the
+ * points, forms the orthogonalizing coefficients c_{nu,l} = int N^A N^C / m_l
+ * (Eq. orthCGLL), the block M^oo = M^AA - C diag(m) C^+ (Eq. Moo) and its
+ * inverse (Eq. MOEFEInv). Returns OEFE_ERR_NOTPD_MOO if M^oo is not positive
+ * definite. k = 0 exactly gives real arithmetic for that k. */
+int oefe_kpoints(oefe_ctx_t ctx, int nk, const double* k, const double* w);
+
+int oefe_ndof(oefe_ctx_t ctx, int64_t* n_h, int* n_O);
+
+/* ---------------------------------------------------------------- operators
+ * oefe_build_hamiltonian -- cell matrices H^O_e(k) = T_e^+ H_e T_e for every
+ * cell and k (Eq. HOEFEelelements; T maps OEFE to EFE coefficients,
+ * Eq. UOEFESplit). veff_q: device, nq_total doubles, V_eff at the quadrature
+ * points. store: OEFE_STORE_F64 (FP64 / complex128 matrices, needed by every
+ * FP64 call) and/or OEFE_STORE_F32 (FP32 / complex64 copies for the mixed
+ * filter). All arithmetic is FP64. */
+int oefe_build_hamiltonian(oefe_ctx_t ctx, const double* veff_q, int store);
+
+/* Row/column map of one cell matrix: idx (host, n_aug ints) receives global
+ * rows (nodes, then n_h + enrichment index). */
+int oefe_cell_info(oefe_ctx_t ctx, int cell, int* n_aug, int* idx);
+/* H^O_e of one cell (host, n_aug*n_aug doubles or complex128, row-major). */
+int oefe_cell_matrix(oefe_ctx_t ctx, int ik, int cell, void* H);
+/* Lumped CFE mass (host, n_h doubles) and M^oo (host, n_O^2, complex for k != 0). */
+int oefe_overlap(oefe_ctx_t ctx, int ik, double* m, void* Moo);
+
+/* Y = H^O X, and Y = (M^O)^{-1} H^O X (Eq. KSEignStandDiscrete).
+ * X, Y device, (n x ld); dtype OEFE_F64 or OEFE_C128 (C128 for k != 0). */
+int oefe_apply_h(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld, int dtype);
+int oefe_apply_a(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld, int dtype);
+
+/* ---------------------------------------------------------------- filter
+ * oefe_chebyshev_filter -- X <- p_m(A) X in place, A = (M^O)^{-1} H^O
+ * (Sec. IV), with the scaled three-term recurrence: e = (b-a)/2,
+ * c = (b+a)/2, sigma_1 = e/(a0-c); Y_1 = (sigma_1/e)(A - c) X;
+ * Y_{j+1} = (2 sigma_{j+1}/e)(A - c)Y_j - sigma_j sigma_{j+1} Y_{j-1},
+ * sigma_{j+1} = 1/(2/sigma_1 - sigma_j). The M^{-1} step (diagonal CFE mass,
+ * dense FP64 (M^oo)^{-1}) and the recurrence are fused into the reduction
+ * of the cell products. dtype: F64/C128 use the FP64 cell matrices, F32/C64
+ * the FP32 copies (FP32 accumulation). flags: OEFE_FILTER_LAST_FP64 runs the
+ * last degree through the FP64 path (X must then be F64/C128 storage). */
+enum { OEFE_FILTER_LAST_FP64 = 1 };
+int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, int degree,
+                          double a, double b, double a0, int flags);
+
+/* ---------------------------------------------------------------- subspace
+ * oefe_orthonormalize -- Cholesky-QR in the M inner product, twice
+ * (Sec. IV orthonormalization): S = X^+ M X = L L^+, X <- X L^{-+}.
+ * FP64; X must be F64/C128. cond_est (host, may be NULL) receives
+ * (max L_ii / min L_ii)^2 of the first pass. OEFE_ERR_CHOLESKY if S is not
+ * positive definite. */
+int oefe_orthonormalize(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, double* cond_est);
+
+/* oefe_rayleigh_ritz -- H^Q = X^+ H^O X, M^Q = X^+ M X, H^Q u = eps M^Q u
+ * (Eq. ProjKS), X <- X U. FP64. eig (host, nv) ascending; resid (host, nv or
+ * NULL) receives ||H u - eps M u||_{M^-1} / ||u||_M per rotated vector. */
+int oefe_rayleigh_ritz(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype,
+                       double* eig, double* resid);
+
+/* oefe_density -- rho(x_q) = sum_k sum_a occ_{k,a} |u_{a,k}(x_q)|^2 at every
+ * quadrature point (Eq. rho), u = N^C (X^c - C^T X^o) + N^A X^o.
+ * X[k] device (F64/C128), occ host (sum_k nv[k] doubles, already holding
+ * 2 w_k f), rho device (nq_total doubles, overwritten). */
+int oefe_density(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, const int* ld,
+                 int dtype, const double* occ, double* rho);
+
+/* oefe_band_trace_grad -- gV (device, nq_total, overwritten) = d tr(X^+ H^O X)/d V_q
+ * = w_q sum_v |u_v(x_q)|^2: the adjoint of the cell-level H.X application
+ * with respect to the quadrature-point potential (H^O is affine in V through
+ * the (|k|^2/2 + V) N_m^* N_n term of Eq. HOEFEelelements). The gradient with
+ * respect to conj(X) is H^O X (oefe_apply_h). */
+int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* gV);
+
+/* oefe_upper_bound -- b >= max eig of (M^O)^{-1} H^O: largest Ritz value of
+ * a `steps`-step Lanczos run in the M inner product from v0 (device, n
+ * F64/C128) plus the last residual norm. FP64. */
+int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, double* b);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OEFE_H */

@@ -1,0 +1,13 @@
+"""GB300 library for the Chebyshev-filtered subspace iteration of the
+orthogonalized enriched finite element (OEFE) method, arXiv 2010.09701.
+
+The computation lives in liboefe.so (C ABI, include/oefe.h, CUDA for sm_103a);
+this package is its binding. There is no CPU fallback: importing works
+without a GPU, but creating a Context needs the built library and a device.
+"""
+from .binding import (C64, C128, F32, F64, FILTER_LAST_FP64, STORE_F32, STORE_F64, Context, OefeError,
+                      SIGNATURES, load)
+from .problem import setup_workload
+
+__all__ = ["Context", "OefeError", "load", "setup_workload", "SIGNATURES", "F64", "F32", "C128", "C64",
+           "STORE_F64", "STORE_F32", "FILTER_LAST_FP64"]

@@ -1,0 +1,702 @@
+// GPU construction of the OEFE operators (Sec. III A):
+//  * enrichment tabulation at the quadrature points (Eqs. UOEFEAtomic, KSAtomicTrunc),
+//  * orthogonalizing coefficients c_{nu,l} (Eq. orthCGLL) and M^oo (Eq. Moo),
+//  * EFE cell matrices (Eq. HOEFEelelements) by sum factorization over each
+//    tensor-product leaf of the cell's point set,
+//  * H^O_e = T_e^+ H_e T_e (Eq. UOEFESplit), stored in FP64 and/or FP32.
+// All arithmetic is FP64 (complex for k != 0).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+#include "oefe_internal.h"
+#include "enrich_dev.cuh"
+
+namespace {
+
+constexpr int MAXP = 8;     // P = p + 1 <= 8
+constexpr int MAXN1 = 12;   // Gauss points per axis per leaf
+constexpr int BT = 256;     // threads per CTA of the cell kernels
+constexpr size_t SMEM_BUILD = 200 * 1024;
+
+// Tabulate N^A and grad N^A for (point, active function) pairs of a batch of cells.
+// tab entry layout: 4 complex values (value, d/dx, d/dy, d/dz) per (q, j), j fastest.
+__global__ void k_tabulate(EnrParams E, const double* qxyz, const int64_t* q_off, const int* act_off,
+                           const int* act_idx, int e0, int ncell_b, const int64_t* tab_off,
+                           double kx, double ky, double kz, cd* tab) {
+  const int64_t total = tab_off[ncell_b];
+  const double k[3] = {kx, ky, kz};
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = ncell_b - 1;
+    while (lo < hi) {  // last b with tab_off[b] <= t
+      int mid = (lo + hi + 1) / 2;
+      if (tab_off[mid] <= t) lo = mid; else hi = mid - 1;
+    }
+    const int e = e0 + lo;
+    const int ne = act_off[e + 1] - act_off[e];
+    const int64_t r = t - tab_off[lo];
+    const int64_t q = q_off[e] + r / ne;
+    const int j = (int)(r % ne);
+    const int nu = act_idx[act_off[e] + j];
+    const double x[3] = {qxyz[3 * q], qxyz[3 * q + 1], qxyz[3 * q + 2]};
+    cd v, g[3];
+    enrichment_value(E, nu, x, k, &v, g);
+    cd* o = tab + 4 * t;
+    o[0] = v;
+    o[1] = g[0];
+    o[2] = g[1];
+    o[3] = g[2];
+  }
+}
+
+struct BuildArgs {
+  const Leaf* leaves;
+  const int* leaf_off;
+  const double* qxyz;
+  const double* qw;
+  const double* veff;       // null in orthogonalization mode
+  const double* cellbox;
+  const double* gll;
+  const double* gauss_w;    // [n][i] table, 13 x 12
+  const int* act_off;
+  const int64_t* tab_off;
+  const int64_t* q_off;
+  const cd* tab;
+  int e0, P, nloc, npad, ne_max;
+  double k[3];
+  int mode;                 // 0: H blocks, 1: d and M^AA blocks
+  cd* HE;                   // mode 0: (batch, npad, npad)
+  cd* dblk;                 // mode 1: (ncells, nloc, ne_max)
+  cd* MAAblk;               // mode 1: (ncells, ne_max, ne_max)
+};
+
+// One CTA per cell: accumulate the cell's blocks over its tensor-product leaves.
+__global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
+  extern __shared__ double smem[];
+  const int b = blockIdx.x;
+  const int e = A.e0 + b;
+  const int P = A.P, nloc = A.nloc, npad = A.npad;
+  const int ne = A.act_off[e + 1] - A.act_off[e];
+  const double* box = A.cellbox + 6 * e;
+  const double kk = A.k[0] * A.k[0] + A.k[1] * A.k[1] + A.k[2] * A.k[2];
+  const bool kz = kk == 0.0;
+
+  // small tables
+  __shared__ double Lt[3][MAXN1][MAXP], Dt[3][MAXN1][MAXP], w1[3][MAXN1];
+  __shared__ double Mm[3][MAXP][MAXP], Km[3][MAXP][MAXP], Am[3][MAXP][MAXP];
+  __shared__ double xn[MAXP];
+  if (threadIdx.x < P) xn[threadIdx.x] = A.gll[threadIdx.x];
+
+  cd* HE = A.HE ? A.HE + (size_t)b * npad * npad : nullptr;
+  cd* dB = A.dblk ? A.dblk + (size_t)e * nloc * A.ne_max : nullptr;
+  cd* MB = A.MAAblk ? A.MAAblk + (size_t)e * A.ne_max * A.ne_max : nullptr;
+  if (A.mode == 0) {
+    for (int i = threadIdx.x; i < npad * npad; i += BT) HE[i] = mkc(0, 0);
+  } else {
+    for (int i = threadIdx.x; i < nloc * A.ne_max; i += BT) dB[i] = mkc(0, 0);
+    for (int i = threadIdx.x; i < A.ne_max * A.ne_max; i += BT) MB[i] = mkc(0, 0);
+  }
+  __syncthreads();
+
+  const cd* tabc = A.tab + 4 * A.tab_off[b];  // this cell's tabulation, (q, j) j fastest
+  for (int li = A.leaf_off[e]; li < A.leaf_off[e + 1]; ++li) {
+    const Leaf L = A.leaves[li];
+    const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
+    const int64_t q0 = L.q0;
+    const int64_t ql0 = q0 - A.q_off[e];  // leaf offset within the cell
+    // 1D tables: reference coordinate of the leaf's points on each axis
+    if (threadIdx.x < 3 * n1) {
+      const int d = threadIdx.x / n1, i = threadIdx.x % n1;
+      const int64_t qi = q0 + (d == 0 ? i : d == 1 ? i * n1 : i * n2);
+      const double x = A.qxyz[3 * qi + d];
+      const double xi = 2.0 * (x - box[d]) / box[3 + d] - 1.0;
+      double Lv[MAXP], Dv[MAXP];
+      lagrange_eval(xn, P, xi, Lv, Dv);
+      for (int a = 0; a < P; ++a) {
+        Lt[d][i][a] = Lv[a];
+        Dt[d][i][a] = Dv[a] * (2.0 / box[3 + d]);
+      }
+      w1[d][i] = A.gauss_w[n1 * 12 + i] * (L.hi[d] - L.lo[d]) / 2.0;
+    }
+    __syncthreads();
+
+    if (A.mode == 0) {
+      // 1D mass, stiffness and antisymmetric gradient matrices of the leaf
+      for (int t = threadIdx.x; t < 3 * P * P; t += BT) {
+        const int d = t / (P * P), a = (t / P) % P, a2 = t % P;
+        double m = 0, kq = 0, g1 = 0, g2 = 0;
+        for (int i = 0; i < n1; ++i) {
+          m += w1[d][i] * Lt[d][i][a] * Lt[d][i][a2];
+          kq += w1[d][i] * Dt[d][i][a] * Dt[d][i][a2];
+          g1 += w1[d][i] * Lt[d][i][a] * Dt[d][i][a2];
+          g2 += w1[d][i] * Dt[d][i][a] * Lt[d][i][a2];
+        }
+        Mm[d][a][a2] = m;
+        Km[d][a][a2] = kq;
+        Am[d][a][a2] = g1 - g2;
+      }
+      // potential weight field W_q (V_q + |k|^2 / 2)
+      double* Wv = smem;                       // n3
+      double* S1 = Wv + n3;                    // n2 * P * P  [(qx,qy)][c][c']
+      double* S2 = S1 + n2 * P * P;            // cx * P^4    [qx][b][b'][c][c']
+      for (int q = threadIdx.x; q < n3; q += BT) Wv[q] = A.qw[q0 + q] * (A.veff[q0 + q] + 0.5 * kk);
+      __syncthreads();
+      for (int t = threadIdx.x; t < n2 * P * P; t += BT) {
+        const int qxy = t / (P * P), c = (t / P) % P, c2 = t % P;
+        double s = 0;
+        for (int qz = 0; qz < n1; ++qz) s += Wv[qxy + n2 * qz] * Lt[2][qz][c] * Lt[2][qz][c2];
+        S1[t] = s;
+      }
+      __syncthreads();
+      const int P2 = P * P, P4 = P2 * P2;
+      const int budget = (int)((SMEM_BUILD / sizeof(double) - n3 - (size_t)n2 * P2) / P4);
+      const int cx = min(n1, max(1, budget));
+      for (int qx0 = 0; qx0 < n1; qx0 += cx) {
+        const int nx = min(cx, n1 - qx0);
+        for (int t = threadIdx.x; t < nx * P4; t += BT) {
+          const int ix = t / P4, r = t % P4;
+          const int bb = r / (P * P2), b2 = (r / P2) % P, cc = r % P2;  // (b, b', (c,c'))
+          double s = 0;
+          for (int qy = 0; qy < n1; ++qy)
+            s += Lt[1][qy][bb] * Lt[1][qy][b2] * S1[((qx0 + ix) + n1 * qy) * P2 + cc];
+          S2[t] = s;
+        }
+        __syncthreads();
+        const bool first = qx0 == 0;
+        for (int t = threadIdx.x; t < nloc * nloc; t += BT) {
+          const int m = t / nloc, n = t % nloc;
+          const int a = m % P, bb = (m / P) % P, c = m / P2;
+          const int a2 = n % P, b2 = (n / P) % P, c2 = n / P2;
+          const int ridx = (bb * P + b2) * P2 + c * P + c2;
+          double v = 0;
+          for (int ix = 0; ix < nx; ++ix) v += Lt[0][qx0 + ix][a] * Lt[0][qx0 + ix][a2] * S2[ix * P4 + ridx];
+          double im = 0;
+          if (first) {
+            v += 0.5 * (Km[0][a][a2] * Mm[1][bb][b2] * Mm[2][c][c2] + Mm[0][a][a2] * Km[1][bb][b2] * Mm[2][c][c2] +
+                        Mm[0][a][a2] * Mm[1][bb][b2] * Km[2][c][c2]);
+            if (!kz)
+              im = -0.5 * (A.k[0] * Am[0][a][a2] * Mm[1][bb][b2] * Mm[2][c][c2] +
+                           A.k[1] * Mm[0][a][a2] * Am[1][bb][b2] * Mm[2][c][c2] +
+                           A.k[2] * Mm[0][a][a2] * Mm[1][bb][b2] * Am[2][c][c2]);
+          }
+          cd* h = HE + (size_t)m * npad + n;
+          h->x += v;
+          h->y += im;
+        }
+        __syncthreads();
+      }
+    }
+
+    // enrichment columns: staged contraction of the CFE factors against the
+    // enrichment fields of the leaf (mode 0: H_CA; mode 1: d = int N^C N^A)
+    {
+      cd* F = reinterpret_cast<cd*>(smem);     // 4 fields * n3
+      cd* G = F + 4 * n3;                      // 4 * n2 * P
+      cd* Hs = G + 4 * n2 * P;                 // 3 * n1 * P * P
+      const int nf = A.mode == 0 ? 4 : 1;
+      for (int j = 0; j < ne; ++j) {
+        for (int q = threadIdx.x; q < n3; q += BT) {
+          const cd* tq = tabc + 4 * ((ql0 + q) * ne + j);
+          const double w = A.qw[q0 + q];
+          if (A.mode == 0) {
+            const double vk = A.veff[q0 + q] + 0.5 * kk;
+            const cd N = tq[0];
+            const cd kg = A.k[0] * tq[1] + A.k[1] * tq[2] + A.k[2] * tq[3];
+            // F0 = w (Vk N - (i/2) k.grad N), F_d = w (grad_d N / 2 + (i/2) k_d N)
+            F[q] = w * (vk * N - mkc(0, 0.5) * kg);
+            for (int d = 0; d < 3; ++d) F[(1 + d) * n3 + q] = w * (0.5 * tq[1 + d] + mkc(0, 0.5 * A.k[d]) * N);
+          } else {
+            F[q] = w * tq[0];
+          }
+        }
+        __syncthreads();
+        // stage z: (qx,qy,c)
+        for (int t = threadIdx.x; t < n2 * P; t += BT) {
+          const int qxy = t / P, c = t % P;
+          cd g0 = mkc(0, 0), gx = mkc(0, 0), gy = mkc(0, 0), gz = mkc(0, 0);
+          for (int qz = 0; qz < n1; ++qz) {
+            const int q = qxy + n2 * qz;
+            const double l = Lt[2][qz][c];
+            g0 += l * F[q];
+            if (nf == 4) {
+              gx += l * F[n3 + q];
+              gy += l * F[2 * n3 + q];
+              gz += Dt[2][qz][c] * F[3 * n3 + q];
+            }
+          }
+          G[t] = g0 + gz;
+          if (nf == 4) {
+            G[n2 * P + t] = gx;
+            G[2 * n2 * P + t] = gy;
+          }
+        }
+        __syncthreads();
+        // stage y: (qx,b,c)
+        for (int t = threadIdx.x; t < n1 * P * P; t += BT) {
+          const int qx = t / (P * P), bb = (t / P) % P, c = t % P;
+          cd h0 = mkc(0, 0), hx = mkc(0, 0), hy = mkc(0, 0);
+          for (int qy = 0; qy < n1; ++qy) {
+            const int g = (qx + n1 * qy) * P + c;
+            h0 += Lt[1][qy][bb] * G[g];
+            if (nf == 4) {
+              hx += Lt[1][qy][bb] * G[n2 * P + g];
+              hy += Dt[1][qy][bb] * G[2 * n2 * P + g];
+            }
+          }
+          Hs[t] = h0 + hy;
+          if (nf == 4) Hs[n1 * P * P + t] = hx;
+        }
+        __syncthreads();
+        // stage x: (a,b,c) -> local node a + P (b + P c)
+        for (int m = threadIdx.x; m < nloc; m += BT) {
+          const int a = m % P, bc = m / P;  // bc = b + P c
+          const int bb = bc % P, c = bc / P;
+          cd s = mkc(0, 0);
+          for (int qx = 0; qx < n1; ++qx) {
+            const int hidx = (qx * P + bb) * P + c;
+            s += Lt[0][qx][a] * Hs[hidx];
+            if (nf == 4) s += Dt[0][qx][a] * Hs[n1 * P * P + hidx];
+          }
+          if (A.mode == 0) HE[(size_t)m * npad + nloc + j] += s;
+          else dB[(size_t)m * A.ne_max + j] += s;
+        }
+        __syncthreads();
+      }
+    }
+
+    // enrichment-enrichment block: pairs (i <= j), points of the leaf
+    for (int t = threadIdx.x; t < ne * ne; t += BT) {
+      const int i = t / ne, j = t % ne;
+      if (i > j) continue;
+      cd s = mkc(0, 0);
+      for (int q = 0; q < n3; ++q) {
+        const cd* ti = tabc + 4 * ((ql0 + q) * ne + i);
+        const cd* tj = tabc + 4 * ((ql0 + q) * ne + j);
+        const double w = A.qw[q0 + q];
+        if (A.mode == 0) {
+          const double vk = A.veff[q0 + q] + 0.5 * kk;
+          cd v = 0.5 * (cmulc(ti[1], tj[1]) + cmulc(ti[2], tj[2]) + cmulc(ti[3], tj[3])) + vk * cmulc(ti[0], tj[0]);
+          if (!kz) {
+            const cd kgj = A.k[0] * tj[1] + A.k[1] * tj[2] + A.k[2] * tj[3];
+            const cd kgi = A.k[0] * ti[1] + A.k[1] * ti[2] + A.k[2] * ti[3];
+            const cd asym = cmulc(ti[0], kgj) - cmulc(kgi, tj[0]);
+            v += mkc(0, -0.5) * asym;
+          }
+          s += w * v;
+        } else {
+          s += w * cmulc(ti[0], tj[0]);
+        }
+      }
+      if (A.mode == 0) {
+        HE[(size_t)(nloc + i) * npad + nloc + j] += s;
+        if (i != j) HE[(size_t)(nloc + j) * npad + nloc + i] += cconj(s);
+      } else {
+        MB[i * A.ne_max + j] += s;
+        if (i != j) MB[j * A.ne_max + i] += cconj(s);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Gamma_e[a][j] = c_{act(e)_j, node(e,a)} = (sum over cells sharing the node of d) / m_node
+template <typename S>
+__global__ void k_gamma(const int* cell_nodes, const int64_t* node_off, const int64_t* node_slot,
+                        const int* act_off, const int* act_idx, const double* m, const cd* dblk,
+                        int ncells, int nloc, int npad, int ne_max, S* gamma) {
+  const int64_t total = (int64_t)ncells * nloc * ne_max;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int j = (int)(t % ne_max);
+    const int64_t ea = t / ne_max;
+    const int a = (int)(ea % nloc), e = (int)(ea / nloc);
+    const int ne = act_off[e + 1] - act_off[e];
+    cd s = mkc(0, 0);
+    if (j < ne) {
+      const int nu = act_idx[act_off[e] + j];
+      const int g = cell_nodes[(size_t)e * nloc + a];
+      for (int64_t sl = node_off[g]; sl < node_off[g + 1]; ++sl) {
+        const int64_t slot = node_slot[sl];
+        const int e2 = (int)(slot / npad), a2 = (int)(slot % npad);
+        int lo = act_off[e2], hi = act_off[e2 + 1] - 1;  // binary search nu in act(e2)
+        while (lo <= hi) {
+          const int mid = (lo + hi) / 2;
+          const int v = act_idx[mid];
+          if (v == nu) {
+            s += dblk[((size_t)e2 * nloc + a2) * ne_max + (mid - act_off[e2])];
+            break;
+          }
+          if (v < nu) lo = mid + 1; else hi = mid - 1;
+        }
+      }
+      s = (1.0 / m[g]) * s;
+    }
+    if constexpr (sizeof(S) == sizeof(cd)) gamma[t] = *reinterpret_cast<S*>(&s);
+    else gamma[t] = s.x;
+  }
+}
+
+template <typename S>
+__device__ inline cd ld_s(const S* p, size_t i) {
+  if constexpr (sizeof(S) == sizeof(cd)) { const cd* q = reinterpret_cast<const cd*>(p); return q[i]; }
+  else return mkc(reinterpret_cast<const double*>(p)[i], 0.0);
+}
+
+// subtract sum over owned nodes m_l conj(c_i) c_j from the cell's M^AA block (Eq. Moo)
+template <typename S>
+__global__ void k_moo_cell(const int* act_off, const double* m, const int* cell_nodes, const S* gamma,
+                           int P, int nloc, int ne_max, cd* MAAblk) {
+  const int e = blockIdx.x;
+  const int ne = act_off[e + 1] - act_off[e];
+  const int p = P - 1;
+  for (int t = threadIdx.x; t < ne * ne; t += blockDim.x) {
+    const int i = t / ne, j = t % ne;
+    cd s = mkc(0, 0);
+    for (int a = 0; a < nloc; ++a) {
+      const int ax = a % P, ay = (a / P) % P, az = a / (P * P);
+      if (ax == p || ay == p || az == p) continue;  // each node owned by one cell
+      const double mm = m[cell_nodes[(size_t)e * nloc + a]];
+      const size_t base = ((size_t)e * nloc + a) * ne_max;
+      s += mm * cmulc(ld_s(gamma, base + i), ld_s(gamma, base + j));
+    }
+    MAAblk[((size_t)e * ne_max + i) * ne_max + j] -= s;
+  }
+}
+
+// M^oo[nu][mu] = sum over cells holding both of the per-cell blocks
+template <typename S>
+__global__ void k_moo_reduce(const int64_t* enr_off, const int64_t* enr_slot, const int* act_off,
+                             const int* act_idx, int nO, int npad, int nloc, int ne_max,
+                             const cd* MAAblk, S* Moo) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nO * nO) return;
+  const int nu = t / nO, mu = t % nO;
+  cd s = mkc(0, 0);
+  for (int64_t sl = enr_off[nu]; sl < enr_off[nu + 1]; ++sl) {
+    const int64_t slot = enr_slot[sl];
+    const int e = (int)(slot / npad), i = (int)(slot % npad) - nloc;
+    int lo = act_off[e], hi = act_off[e + 1] - 1;
+    while (lo <= hi) {
+      const int mid = (lo + hi) / 2;
+      const int v = act_idx[mid];
+      if (v == mu) {
+        s += MAAblk[((size_t)e * ne_max + i) * ne_max + (mid - act_off[e])];
+        break;
+      }
+      if (v < mu) lo = mid + 1; else hi = mid - 1;
+    }
+  }
+  if constexpr (sizeof(S) == sizeof(cd)) reinterpret_cast<cd*>(Moo)[t] = s;
+  else reinterpret_cast<double*>(Moo)[t] = s.x;
+}
+
+template <typename S>
+__global__ void k_hermitize(S* A, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  if (i > j) return;
+  if constexpr (sizeof(S) == sizeof(cd)) {
+    cd* B = reinterpret_cast<cd*>(A);
+    cd u = B[i * n + j], l = B[j * n + i];
+    cd v = 0.5 * (u + cconj(l));
+    B[i * n + j] = v;
+    B[j * n + i] = cconj(v);
+  } else {
+    double* B = reinterpret_cast<double*>(A);
+    double v = 0.5 * (B[i * n + j] + B[j * n + i]);
+    B[i * n + j] = v;
+    B[j * n + i] = v;
+  }
+}
+
+// H^O_e = T_e^+ H_e T_e: CO = CA - H_CC Gamma, OO = AA - Gamma^+ CO - CA^+ Gamma.
+// One CTA per cell; writes the FP64 and/or FP32 stored matrices.
+template <typename S, typename S32>
+__global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma, const int* act_off,
+                                                  int e0, int nloc, int npad, int ne_max, S* H64,
+                                                  S32* H32) {
+  extern __shared__ double smem[];
+  const int b = blockIdx.x, e = e0 + b;
+  const int ne = act_off[e + 1] - act_off[e];
+  const cd* HE = HEb + (size_t)b * npad * npad;
+  const S* Gm = gamma + (size_t)e * nloc * ne_max;
+  cd* CO = reinterpret_cast<cd*>(smem);          // nloc * JB
+  constexpr int JB = 4;
+  auto put = [&](int r, int c, cd v) {
+    const size_t o = (size_t)e * npad * npad + (size_t)r * npad + c;
+    if constexpr (sizeof(S) == sizeof(cd)) {
+      if (H64) reinterpret_cast<cd*>(H64)[o] = v;
+      if (H32) reinterpret_cast<cf*>(H32)[o] = cf{(float)v.x, (float)v.y};
+    } else {
+      if (H64) reinterpret_cast<double*>(H64)[o] = v.x;
+      if (H32) reinterpret_cast<float*>(H32)[o] = (float)v.x;
+    }
+  };
+  // CC block and zero padding
+  for (int t = threadIdx.x; t < npad * npad; t += BT) {
+    const int r = t / npad, c = t % npad;
+    if (r < nloc && c < nloc) put(r, c, HE[(size_t)r * npad + c]);
+    else if (r >= nloc + ne || c >= nloc + ne) put(r, c, mkc(0, 0));
+  }
+  for (int j0 = 0; j0 < ne; j0 += JB) {
+    const int nj = min(JB, ne - j0);
+    // CO[:, j0:j0+nj] = CA - H_CC Gamma, using H_CC Hermitian: (H_CC Gamma)[m] = sum_a conj(H[a][m]) Gamma[a]
+    for (int m = threadIdx.x; m < nloc; m += BT) {
+      cd acc[JB];
+      for (int u = 0; u < JB; ++u) acc[u] = mkc(0, 0);
+      for (int a = 0; a < nloc; ++a) {
+        const cd h = cconj(HE[(size_t)a * npad + m]);
+        for (int u = 0; u < nj; ++u) acc[u] += h * ld_s(Gm, (size_t)a * ne_max + j0 + u);
+      }
+      for (int u = 0; u < nj; ++u) {
+        const cd co = HE[(size_t)m * npad + nloc + j0 + u] - acc[u];
+        CO[m * JB + u] = co;
+        put(m, nloc + j0 + u, co);
+        put(nloc + j0 + u, m, cconj(co));
+      }
+    }
+    __syncthreads();
+    // OO[i][j] = AA[i][j] - sum_m conj(Gamma[m][i]) CO[m][j] - sum_m conj(CA[m][i]) Gamma[m][j]
+    for (int t = threadIdx.x; t < ne * nj; t += BT) {
+      const int i = t / nj, u = t % nj, j = j0 + u;
+      cd s = HE[(size_t)(nloc + i) * npad + nloc + j];
+      for (int m = 0; m < nloc; ++m) {
+        s -= cmulc(ld_s(Gm, (size_t)m * ne_max + i), CO[m * JB + u]);
+        s -= cmulc(HE[(size_t)m * npad + nloc + i], ld_s(Gm, (size_t)m * ne_max + j));
+      }
+      put(nloc + i, nloc + j, s);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ host side
+static int gauss_table(oefe_ctx* c, double** d_tab) {
+  std::vector<double> tab(13 * 12, 0.0);
+  for (int n = 1; n <= 12; ++n) {
+    std::vector<double> x, w;
+    gauss_rule(n, x, w);
+    for (int i = 0; i < n; ++i) tab[n * 12 + i] = w[i];
+  }
+  OEFE_TRY(dev_alloc(c, (void**)d_tab, tab.size() * sizeof(double)));
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(*d_tab, tab.data(), tab.size() * sizeof(double),
+                                   cudaMemcpyHostToDevice, c->stream));
+  return OEFE_OK;
+}
+
+static size_t smem_build_bytes(const oefe_ctx* c) {
+  // worst case over both phases, all leaves use n1 <= max(nq_cell, nq_enr)
+  const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
+  const size_t n3 = (size_t)n1 * n1 * n1, n2 = (size_t)n1 * n1;
+  const size_t phase_cc = std::min(SMEM_BUILD, (n3 + n2 * P * P + (size_t)n1 * P * P * P * P) * 8);
+  const size_t phase_ca = (4 * n3 + 4 * n2 * P + 3 * (size_t)n1 * P * P) * 16;
+  return std::max(phase_cc, phase_ca);
+}
+
+// Process cells in batches bounded by a scratch budget; calls fn(e0, e1, tab_off_host).
+template <typename Fn>
+static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, Fn fn) {
+  const size_t budget = (size_t)6 << 30;  // bytes of tabulation + per-cell scratch per batch
+  int e0 = 0;
+  while (e0 < c->ncells) {
+    std::vector<int64_t> off(1, 0);
+    size_t bytes = 0;
+    int e1 = e0;
+    while (e1 < c->ncells) {
+      const int64_t ne = c->act_off[e1 + 1] - c->act_off[e1];
+      const int64_t ent = (c->q_off[e1 + 1] - c->q_off[e1]) * ne;
+      const size_t add = (size_t)ent * 4 * sizeof(cd) + per_cell_fixed;
+      if (e1 > e0 && bytes + add > budget) break;
+      bytes += add;
+      off.push_back(off.back() + ent);
+      ++e1;
+    }
+    OEFE_TRY(fn(e0, e1, off));
+    e0 = e1;
+  }
+  return OEFE_OK;
+}
+
+static EnrParams enr_params(const oefe_ctx* c) {
+  EnrParams E;
+  E.pos = c->d_pos;
+  E.lm = c->d_lm;
+  E.R = c->d_R;
+  E.dR = c->d_dR;
+  E.nfun = c->nfun;
+  E.ngrid = c->ngrid;
+  E.a = c->a;
+  E.r0 = c->r0;
+  E.rc = c->rc;
+  return E;
+}
+
+// Run the tabulation and the cell kernel over all cells in batches.
+static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, double* d_gw, cd* dblk,
+                           cd* MAAblk, int store) {
+  const size_t hebytes = mode == 0 ? (size_t)c->npad * c->npad * sizeof(cd) : 0;
+  const size_t smem = smem_build_bytes(c);
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_build_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  return for_cell_batches(c, hebytes, [&](int e0, int e1, const std::vector<int64_t>& off) -> int {
+    const int nb = e1 - e0;
+    const size_t tab_bytes = (size_t)off.back() * 4 * sizeof(cd);
+    const size_t off_bytes = off.size() * sizeof(int64_t);
+    const size_t he_total = hebytes * nb;
+    OEFE_TRY(ensure_ws(c, tab_bytes + he_total + off_bytes + 256));
+    char* base = (char*)c->ws;
+    cd* tab = (cd*)base;
+    cd* HE = (cd*)(base + tab_bytes);
+    int64_t* d_off = (int64_t*)(base + tab_bytes + he_total);
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_off, off.data(), off_bytes, cudaMemcpyHostToDevice, c->stream));
+    if (off.back() > 0) {
+      const int threads = 256;
+      const int64_t blocks = std::min<int64_t>((off.back() + threads - 1) / threads, 1 << 20);
+      k_tabulate<<<(unsigned)blocks, threads, 0, c->stream>>>(enr_params(c), c->d_qxyz, c->d_q_off, c->d_act_off,
+                                                             c->d_act_idx, e0, nb, d_off, K.k[0], K.k[1], K.k[2], tab);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    }
+    BuildArgs A;
+    A.leaves = c->d_leaves;
+    A.leaf_off = c->d_leaf_off;
+    A.qxyz = c->d_qxyz;
+    A.qw = c->d_qw;
+    A.veff = veff;
+    A.cellbox = c->d_cellbox;
+    A.gll = c->d_gll;
+    A.gauss_w = d_gw;
+    A.act_off = c->d_act_off;
+    A.tab_off = d_off;
+    A.q_off = c->d_q_off;
+    A.tab = tab;
+    A.e0 = e0;
+    A.P = c->P;
+    A.nloc = c->nloc;
+    A.npad = c->npad;
+    A.ne_max = c->ne_max;
+    for (int d = 0; d < 3; ++d) A.k[d] = K.k[d];
+    A.mode = mode;
+    A.HE = mode == 0 ? HE : nullptr;
+    A.dblk = dblk;
+    A.MAAblk = MAAblk;
+    k_build_cell<<<nb, BT, smem, c->stream>>>(A);
+    OEFE_CUDA_TRY(c, cudaGetLastError());
+    if (mode == 0) {
+      const size_t tsmem = (size_t)c->nloc * 4 * sizeof(cd);
+      float* H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
+      double* H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
+      if (K.cplx)
+        k_transform<cd, cf><<<nb, BT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
+                                                         c->ne_max, (cd*)H64, (cf*)H32);
+      else
+        k_transform<double, float><<<nb, BT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
+                                                                c->ne_max, H64, H32);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    }
+    OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return OEFE_OK;
+  });
+}
+
+int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
+  if (!c->has_quad) { c->err = "kpoints: call oefe_quadrature first"; return OEFE_ERR_STATE; }
+  if (nk < 1 || nk > 4096 || !k || !w) { c->err = "kpoints: need 1 <= nk <= 4096, k, w"; return OEFE_ERR_ARG; }
+  for (auto& K : c->kd) {
+    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32);
+  }
+  c->kd.assign(nk, KData());
+  double* d_gw = nullptr;
+  OEFE_TRY(gauss_table(c, &d_gw));
+  cd *dblk = nullptr, *MAAblk = nullptr;
+  const size_t dbytes = (size_t)c->ncells * c->nloc * std::max(c->ne_max, 1) * sizeof(cd);
+  const size_t mbytes = (size_t)c->ncells * std::max(c->ne_max * c->ne_max, 1) * sizeof(cd);
+  int st = dev_alloc(c, (void**)&dblk, dbytes);
+  if (st == OEFE_OK) st = dev_alloc(c, (void**)&MAAblk, mbytes);
+  for (int ik = 0; ik < nk && st == OEFE_OK; ++ik) {
+    KData& K = c->kd[ik];
+    for (int d = 0; d < 3; ++d) K.k[d] = k[3 * ik + d];
+    K.w = w[ik];
+    K.cplx = !(K.k[0] == 0.0 && K.k[1] == 0.0 && K.k[2] == 0.0);
+    const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);
+    st = dev_alloc(c, (void**)&K.gamma, (size_t)c->ncells * c->nloc * std::max(c->ne_max, 1) * sb);
+    if (st == OEFE_OK) st = dev_alloc(c, (void**)&K.Moo, (size_t)std::max(c->nO * c->nO, 1) * sb);
+    if (st == OEFE_OK) st = dev_alloc(c, (void**)&K.Mooinv, (size_t)std::max(c->nO * c->nO, 1) * sb);
+    if (st != OEFE_OK || c->nO == 0) continue;
+    st = run_cell_kernel(c, K, 1, nullptr, d_gw, dblk, MAAblk, 0);
+    if (st != OEFE_OK) break;
+    const int64_t tot = (int64_t)c->ncells * c->nloc * c->ne_max;
+    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 1 << 20);
+    if (K.cplx)
+      k_gamma<cd><<<blocks, 256, 0, c->stream>>>(c->d_cell_nodes, c->d_node_off, c->d_node_slot, c->d_act_off,
+                                                c->d_act_idx, c->d_m, dblk, c->ncells, c->nloc, c->npad, c->ne_max,
+                                                (cd*)K.gamma);
+    else
+      k_gamma<double><<<blocks, 256, 0, c->stream>>>(c->d_cell_nodes, c->d_node_off, c->d_node_slot, c->d_act_off,
+                                                    c->d_act_idx, c->d_m, dblk, c->ncells, c->nloc, c->npad,
+                                                    c->ne_max, K.gamma);
+    if (K.cplx)
+      k_moo_cell<cd><<<c->ncells, 256, 0, c->stream>>>(c->d_act_off, c->d_m, c->d_cell_nodes, (const cd*)K.gamma,
+                                                      c->P, c->nloc, c->ne_max, MAAblk);
+    else
+      k_moo_cell<double><<<c->ncells, 256, 0, c->stream>>>(c->d_act_off, c->d_m, c->d_cell_nodes, K.gamma, c->P,
+                                                          c->nloc, c->ne_max, MAAblk);
+    const int nb2 = (c->nO * c->nO + 255) / 256;
+    if (K.cplx) {
+      k_moo_reduce<cd><<<nb2, 256, 0, c->stream>>>(c->d_enr_off, c->d_enr_slot, c->d_act_off, c->d_act_idx, c->nO,
+                                                  c->npad, c->nloc, c->ne_max, MAAblk, (cd*)K.Moo);
+      k_hermitize<cd><<<nb2, 256, 0, c->stream>>>((cd*)K.Moo, c->nO);
+    } else {
+      k_moo_reduce<double><<<nb2, 256, 0, c->stream>>>(c->d_enr_off, c->d_enr_slot, c->d_act_off, c->d_act_idx,
+                                                      c->nO, c->npad, c->nloc, c->ne_max, MAAblk, K.Moo);
+      k_hermitize<double><<<nb2, 256, 0, c->stream>>>(K.Moo, c->nO);
+    }
+    OEFE_CUDA_TRY(c, cudaGetLastError());
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(K.Mooinv, K.Moo, (size_t)c->nO * c->nO * sb, cudaMemcpyDeviceToDevice,
+                                     c->stream));
+    int info = 0;
+    st = chol_inverse_inplace(c, K.Mooinv, c->nO, K.cplx, true, &info);
+    if (st == OEFE_OK && info != 0) {
+      c->err = "kpoints: M^oo is not positive definite (leading minor " + std::to_string(info) + ")";
+      st = OEFE_ERR_NOTPD_MOO;
+    }
+  }
+  cudaStreamSynchronize(c->stream);
+  dev_free(dblk);
+  dev_free(MAAblk);
+  dev_free(d_gw);
+  if (st != OEFE_OK) return st;
+  c->has_k = true;
+  c->built = false;
+  return OEFE_OK;
+}
+
+int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
+  if (!c->has_k) { c->err = "build_hamiltonian: call oefe_kpoints first"; return OEFE_ERR_STATE; }
+  if (!veff || !(store & (OEFE_STORE_F64 | OEFE_STORE_F32))) {
+    c->err = "build_hamiltonian: need veff and a storage flag";
+    return OEFE_ERR_ARG;
+  }
+  double* d_gw = nullptr;
+  OEFE_TRY(gauss_table(c, &d_gw));
+  int st = OEFE_OK;
+  for (auto& K : c->kd) {
+    const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);
+    const size_t n = (size_t)c->ncells * c->npad * c->npad;
+    dev_free(K.H64);
+    dev_free(K.H32);
+    K.H64 = nullptr;
+    K.H32 = nullptr;
+    if (store & OEFE_STORE_F64) st = dev_alloc(c, (void**)&K.H64, n * sb);
+    if (st == OEFE_OK && (store & OEFE_STORE_F32)) st = dev_alloc(c, (void**)&K.H32, n * sb / 2);
+    if (st == OEFE_OK) st = run_cell_kernel(c, K, 0, veff, d_gw, nullptr, nullptr, store);
+    if (st != OEFE_OK) break;
+    K.built = true;
+  }
+  cudaStreamSynchronize(c->stream);
+  dev_free(d_gw);
+  if (st == OEFE_OK) c->built = true;
+  return st;
+}

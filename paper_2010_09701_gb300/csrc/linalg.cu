@@ -1,0 +1,624 @@
+// Subspace linear algebra in FP64 (Sec. IV): M-inner-product Gram matrices,
+// Cholesky factorization and triangular inverse, Cholesky-QR, Rayleigh-Ritz
+// (Eq. ProjKS) and a Lanczos upper bound of the spectrum.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <vector>
+
+#include "oefe_internal.h"
+
+namespace {
+
+template <typename S> struct Ops;
+template <> struct Ops<double> {
+  __host__ __device__ static double zero() { return 0.0; }
+  __host__ __device__ static double conj(double a) { return a; }
+  __host__ __device__ static double mul(double a, double b) { return a * b; }
+  __host__ __device__ static double mulc(double a, double b) { return a * b; }  // conj(a) b
+  __host__ __device__ static double re(double a) { return a; }
+  __host__ __device__ static double scale(double a, double s) { return a * s; }
+};
+template <> struct Ops<cd> {
+  __host__ __device__ static cd zero() { return mkc(0, 0); }
+  __host__ __device__ static cd conj(cd a) { return cconj(a); }
+  __host__ __device__ static cd mul(cd a, cd b) { return a * b; }
+  __host__ __device__ static cd mulc(cd a, cd b) { return cmulc(a, b); }
+  __host__ __device__ static double re(cd a) { return a.x; }
+  __host__ __device__ static cd scale(cd a, double s) { return a * s; }
+};
+
+// In-place lower Cholesky A = L L^+ of an n x n Hermitian matrix (single CTA).
+// info = 0 on success, j+1 if the j-th pivot is not positive.
+template <typename S>
+__global__ void __launch_bounds__(1024) k_chol(S* A, int n, int* info) {
+  __shared__ double piv;
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = Ops<S>::re(A[(size_t)j * n + j]);
+      if (!(d > 0.0) || !isfinite(d)) fail = j + 1;
+      else {
+        piv = sqrt(d);
+        if constexpr (sizeof(S) == 8) A[(size_t)j * n + j] = piv;
+        else A[(size_t)j * n + j] = mkc(piv, 0.0);
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    const double inv = 1.0 / piv;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + j] = Ops<S>::scale(A[(size_t)i * n + j], inv);
+    __syncthreads();
+    const int m = n - j - 1;
+    for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+      const int ii = t / m, ll = t % m;
+      if (ll > ii) continue;
+      const int i = j + 1 + ii, l = j + 1 + ll;
+      A[(size_t)i * n + l] = A[(size_t)i * n + l] - Ops<S>::mul(A[(size_t)i * n + j], Ops<S>::conj(A[(size_t)l * n + j]));
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    const int i = t / n, l = t % n;
+    if (l > i) A[t] = Ops<S>::zero();
+  }
+  if (threadIdx.x == 0) *info = fail;
+}
+
+// Y = L^{-1} for lower-triangular L (one thread per column).
+template <typename S>
+__global__ void k_trinv(const S* L, S* Y, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = 0; i < n; ++i) {
+    if (i < c) { Y[(size_t)i * n + c] = Ops<S>::zero(); continue; }
+    S s = Ops<S>::zero();
+    if (i == c) {
+      if constexpr (sizeof(S) == 8) s = 1.0; else s = mkc(1.0, 0.0);
+    }
+    for (int k = c; k < i; ++k) s = s - Ops<S>::mul(L[(size_t)i * n + k], Y[(size_t)k * n + c]);
+    Y[(size_t)i * n + c] = Ops<S>::scale(s, 1.0 / Ops<S>::re(L[(size_t)i * n + i]));
+  }
+}
+
+// B = Y^+ Y (inverse of L L^+ when Y = L^{-1})
+template <typename S>
+__global__ void k_yhy(const S* Y, S* B, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  S s = Ops<S>::zero();
+  for (int k = max(i, j); k < n; ++k) s = s + Ops<S>::mulc(Y[(size_t)k * n + i], Y[(size_t)k * n + j]);
+  B[t] = s;
+}
+
+// Partial Gram matrices S_part[chunk] = X[rows]^+ W[rows], tiles of 32 x 32.
+constexpr int GT = 32;
+constexpr int GR = 32;
+template <typename S>
+__global__ void __launch_bounds__(256) k_gram(const S* X, int ldx, const S* W, int ldw, int64_t n, int nv,
+                                              int64_t rows_per_chunk, S* part) {
+  __shared__ S xs[GR][GT];
+  __shared__ S ws[GR][GT];
+  const int ti = blockIdx.y, tj = blockIdx.z;
+  const int64_t r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // 2 x 2 entries each: (2ty..), (2tx..)
+  S acc[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) acc[a][b] = Ops<S>::zero();
+  for (int64_t rb = r0; rb < r1; rb += GR) {
+    for (int t = threadIdx.x; t < GR * GT; t += 256) {
+      const int rr = t / GT, cc = t % GT;
+      const int64_t r = rb + rr;
+      const int ci = ti * GT + cc, cj = tj * GT + cc;
+      xs[rr][cc] = (r < r1 && ci < nv) ? X[r * ldx + ci] : Ops<S>::zero();
+      ws[rr][cc] = (r < r1 && cj < nv) ? W[r * ldw + cj] : Ops<S>::zero();
+    }
+    __syncthreads();
+    for (int rr = 0; rr < GR; ++rr) {
+      const S x0 = xs[rr][2 * ty], x1 = xs[rr][2 * ty + 1];
+      const S w0 = ws[rr][2 * tx], w1 = ws[rr][2 * tx + 1];
+      acc[0][0] = acc[0][0] + Ops<S>::mulc(x0, w0);
+      acc[0][1] = acc[0][1] + Ops<S>::mulc(x0, w1);
+      acc[1][0] = acc[1][0] + Ops<S>::mulc(x1, w0);
+      acc[1][1] = acc[1][1] + Ops<S>::mulc(x1, w1);
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = ti * GT + 2 * ty + a, j = tj * GT + 2 * tx + b;
+      if (i < nv && j < nv) part[((size_t)blockIdx.x * nv + i) * nv + j] = acc[a][b];
+    }
+}
+
+template <typename S>
+__global__ void k_sum_parts(const S* part, int nchunk, int nv, S* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv * nv) return;
+  S s = Ops<S>::zero();
+  for (int c = 0; c < nchunk; ++c) s = s + part[(size_t)c * nv * nv + t];
+  out[t] = s;
+}
+
+// W = M X: lumped diagonal rows, dense M^oo rows.
+template <typename S>
+__global__ void k_apply_M(const S* X, int ldx, const double* m, const S* Moo, int64_t nh, int nO, int nv, S* W,
+                          int ldw) {
+  const int64_t total = (nh + nO) * nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / nv;
+    const int v = (int)(t % nv);
+    if (r < nh) {
+      W[r * ldw + v] = Ops<S>::scale(X[r * ldx + v], m[r]);
+    } else {
+      const int nu = (int)(r - nh);
+      S s = Ops<S>::zero();
+      for (int mu = 0; mu < nO; ++mu) s = s + Ops<S>::mul(Moo[(size_t)nu * nO + mu], X[(nh + mu) * ldx + v]);
+      W[r * ldw + v] = s;
+    }
+  }
+}
+
+// X[rows] <- X[rows] C (C nv x nv), or X C^+ when herm.
+template <typename S>
+__global__ void k_rotate(S* X, int ldx, int64_t n, int nv, const S* C, bool herm, int rows) {
+  extern __shared__ unsigned char sm[];
+  S* xs = reinterpret_cast<S*>(sm);
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int nr = (int)min((int64_t)rows, n - r0);
+  if (nr <= 0) return;
+  for (int t = threadIdx.x; t < nr * nv; t += blockDim.x) xs[t] = X[(r0 + t / nv) * ldx + t % nv];
+  __syncthreads();
+  for (int t = threadIdx.x; t < nr * nv; t += blockDim.x) {
+    const int r = t / nv, j = t % nv;
+    S s = Ops<S>::zero();
+    for (int k = 0; k < nv; ++k) {
+      const S cv = herm ? Ops<S>::conj(C[(size_t)j * nv + k]) : C[(size_t)k * nv + j];
+      s = s + Ops<S>::mul(xs[r * nv + k], cv);
+    }
+    X[(r0 + r) * ldx + j] = s;
+  }
+}
+
+// Column norms for residuals: out[v] = sum_rows conj(R) M^{-1} R, with the
+// lumped block divided by m and the enrichment block through (M^oo)^{-1}.
+template <typename S>
+__global__ void k_resid_norms(const S* R, int ldr, const double* m, const S* Mooinv, int64_t nh, int nO, int nv,
+                              double* out) {
+  const int v = blockIdx.x;
+  double s = 0.0;
+  for (int64_t r = threadIdx.x; r < nh; r += blockDim.x) {
+    const S x = R[r * ldr + v];
+    s += Ops<S>::re(Ops<S>::mulc(x, x)) / m[r];
+  }
+  for (int t = threadIdx.x; t < nO * nO; t += blockDim.x) {
+    const int i = t / nO, j = t % nO;
+    s += Ops<S>::re(Ops<S>::mulc(R[(nh + i) * ldr + v], Ops<S>::mul(Mooinv[t], R[(nh + j) * ldr + v])));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[v] = red[0];
+}
+
+// R = HX - MX diag(eps)
+template <typename S>
+__global__ void k_resid_vec(const S* HX, const S* MX, int ld, const double* eps, int64_t n, int nv, S* R) {
+  const int64_t total = n * nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int v = (int)(t % nv);
+    const int64_t r = t / nv;
+    R[r * ld + v] = HX[r * ld + v] - Ops<S>::scale(MX[r * ld + v], eps[v]);
+  }
+}
+
+// x <- sx x + a y + b z (real views of the vectors); when out != null, out <- x
+// is not used; a plain elementwise update for the Lanczos recurrence.
+__global__ void k_lanczos_axpy(double* x, const double* y, const double* z, double* unused, int64_t n, double sx,
+                               double a, double b) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double v = sx * x[i];
+    if (y) v += a * y[i];
+    if (z) v += b * z[i];
+    x[i] = v;
+  }
+  (void)unused;
+}
+
+// ------------------------------------------------------------------ host helpers
+template <typename S>
+int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, S* part_buf,
+         int nchunk) {
+  const int tiles = (nv + GT - 1) / GT;
+  const int64_t rpc = (n + nchunk - 1) / nchunk;
+  dim3 grid(nchunk, tiles, tiles);
+  k_gram<S><<<grid, 256, 0, c->stream>>>(X, ldx, W, ldw, n, nv, rpc, part_buf);
+  k_sum_parts<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(part_buf, nchunk, nv, out);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}
+
+template <typename S>
+int rotate(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm) {
+  const int rows = std::max(1, (int)((96 * 1024) / ((size_t)nv * sizeof(S))));
+  const int64_t blocks = (n + rows - 1) / rows;
+  const size_t smem = (size_t)rows * nv * sizeof(S);
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_rotate<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_rotate<S><<<(unsigned)blocks, 256, smem, c->stream>>>(X, ldx, n, nv, C, herm, rows);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}
+
+template <typename S>
+int apply_M(oefe_ctx* c, const KData& K, const S* X, int ldx, int nv, S* W, int ldw) {
+  const int64_t tot = (c->nh + c->nO) * nv;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
+  k_apply_M<S><<<blocks, 256, 0, c->stream>>>(X, ldx, c->d_m, (const S*)K.Moo, c->nh, c->nO, nv, W, ldw);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}
+
+int nchunks_for(oefe_ctx* c, int nv) {
+  const int tiles = (nv + GT - 1) / GT;
+  return std::max(1, std::min(1024, 2 * c->num_sms / (tiles * tiles) + 1));
+}
+
+template <typename S>
+int chol_inverse_t(oefe_ctx* c, S* A, int n, bool inverse, bool want_Linv, S* Y, int* info_host) {
+  OEFE_TRY(ensure_ws2(c, 256));
+  int* d_info = c->d_status;
+  k_chol<S><<<1, 1024, 0, c->stream>>>(A, n, d_info);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(info_host, d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (*info_host != 0) return OEFE_OK;
+  if (inverse || want_Linv) {
+    k_trinv<S><<<(n + 127) / 128, 128, 0, c->stream>>>(A, Y, n);
+    if (inverse) k_yhy<S><<<(n * n + 255) / 256, 256, 0, c->stream>>>(Y, A, n);
+    OEFE_CUDA_TRY(c, cudaGetLastError());
+  }
+  return OEFE_OK;
+}
+
+// ------------------------------------------------------------------ host eigensolver
+// Cyclic Jacobi for a Hermitian matrix (row-major, n x n); eigenvalues
+// ascending in w, eigenvectors in the columns of V.
+void jacobi_eigh(int n, std::vector<std::complex<double>>& A, std::vector<double>& w,
+                 std::vector<std::complex<double>>& V) {
+  using C = std::complex<double>;
+  V.assign((size_t)n * n, C(0, 0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  auto at = [&](int i, int j) -> C& { return A[(size_t)i * n + j]; };
+  double fro = 0;
+  for (auto& x : A) fro += std::norm(x);
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j)
+        if (i != j) off += std::norm(at(i, j));
+    if (off <= 1e-30 * fro || off == 0.0) break;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const C b = at(p, q);
+        const double beta = std::abs(b);
+        if (beta < 1e-300) continue;
+        const C u = b / beta;                      // e^{i phi}
+        const double ap = at(p, p).real(), aq = at(q, q).real();
+        const double tau = (aq - ap) / (2.0 * beta);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
+        // G = diag(1, conj(u)) [[c, s], [-s, c]] acting on columns p, q
+        const C g00 = cs, g01 = sn, g10 = -std::conj(u) * sn, g11 = std::conj(u) * cs;
+        for (int k = 0; k < n; ++k) {  // A <- A G
+          const C akp = at(k, p), akq = at(k, q);
+          at(k, p) = akp * g00 + akq * g10;
+          at(k, q) = akp * g01 + akq * g11;
+        }
+        for (int k = 0; k < n; ++k) {  // A <- G^+ A
+          const C apk = at(p, k), aqk = at(q, k);
+          at(p, k) = std::conj(g00) * apk + std::conj(g10) * aqk;
+          at(q, k) = std::conj(g01) * apk + std::conj(g11) * aqk;
+        }
+        at(p, q) = 0.0;
+        at(q, p) = 0.0;
+        for (int k = 0; k < n; ++k) {  // V <- V G
+          const C vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = vkp * g00 + vkq * g10;
+          V[(size_t)k * n + q] = vkp * g01 + vkq * g11;
+        }
+      }
+  }
+  std::vector<int> idx(n);
+  for (int i = 0; i < n; ++i) idx[i] = i;
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return at(a, a).real() < at(b, b).real(); });
+  w.resize(n);
+  std::vector<C> Vs((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    w[j] = at(idx[j], idx[j]).real();
+    for (int k = 0; k < n; ++k) Vs[(size_t)k * n + j] = V[(size_t)k * n + idx[j]];
+  }
+  V = Vs;
+}
+
+// Generalized Hermitian eigenproblem H u = eps M u on the host (n small):
+// M = L L^+, C = L^{-1} H L^{-+}, C = V diag(w) V^+, U = L^{-+} V.
+int host_geneig(int n, std::vector<std::complex<double>>& H, std::vector<std::complex<double>>& M,
+                std::vector<double>& w, std::vector<std::complex<double>>& U) {
+  using C = std::complex<double>;
+  std::vector<C> L((size_t)n * n, C(0, 0));
+  for (int j = 0; j < n; ++j) {
+    double d = M[(size_t)j * n + j].real();
+    for (int k = 0; k < j; ++k) d -= std::norm(L[(size_t)j * n + k]);
+    if (!(d > 0)) return j + 1;
+    const double ljj = std::sqrt(d);
+    L[(size_t)j * n + j] = ljj;
+    for (int i = j + 1; i < n; ++i) {
+      C s = M[(size_t)i * n + j];
+      for (int k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * std::conj(L[(size_t)j * n + k]);
+      L[(size_t)i * n + j] = s / ljj;
+    }
+  }
+  // Y = L^{-1} H (forward substitution on columns), then C = Y L^{-+} = (L^{-1} Y^+)^+
+  auto fwd = [&](std::vector<C>& B) {  // B <- L^{-1} B
+    for (int col = 0; col < n; ++col)
+      for (int i = 0; i < n; ++i) {
+        C s = B[(size_t)i * n + col];
+        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * B[(size_t)k * n + col];
+        B[(size_t)i * n + col] = s / L[(size_t)i * n + i].real();
+      }
+  };
+  std::vector<C> Y = H;
+  fwd(Y);
+  std::vector<C> Yh((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Yh[(size_t)i * n + j] = std::conj(Y[(size_t)j * n + i]);
+  fwd(Yh);
+  std::vector<C> Cm((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Cm[(size_t)i * n + j] = 0.5 * (Yh[(size_t)i * n + j] + std::conj(Yh[(size_t)j * n + i]));
+  std::vector<C> V;
+  jacobi_eigh(n, Cm, w, V);
+  // U = L^{-+} V: solve L^+ U = V (backward substitution)
+  U = V;
+  for (int col = 0; col < n; ++col)
+    for (int i = n - 1; i >= 0; --i) {
+      C s = U[(size_t)i * n + col];
+      for (int k = i + 1; k < n; ++k) s -= std::conj(L[(size_t)k * n + i]) * U[(size_t)k * n + col];
+      U[(size_t)i * n + col] = s / L[(size_t)i * n + i].real();
+    }
+  return 0;
+}
+
+int check_fp64(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
+  if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
+  if (ik < 0 || ik >= (int)c->kd.size()) { c->err = "k index out of range"; return OEFE_ERR_ARG; }
+  if (!X || nv < 1 || ld < nv || nv > 4096) { c->err = "need X, 1 <= nv <= ld, nv <= 4096"; return OEFE_ERR_ARG; }
+  if (!(dtype == OEFE_F64 || dtype == OEFE_C128)) { c->err = "this call needs F64 or C128 vectors"; return OEFE_ERR_ARG; }
+  if (c->kd[ik].cplx != (dtype == OEFE_C128)) { c->err = "dtype does not match the k-point"; return OEFE_ERR_ARG; }
+  if (!c->kd[ik].H64) { c->err = "FP64 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  return OEFE_OK;
+}
+
+template <typename S>
+int orthonormalize_t(oefe_ctx* c, int ik, S* X, int nv, int ld, double* cond) {
+  const KData& K = c->kd[ik];
+  const int64_t n = c->nh + c->nO;
+  const int nchunk = nchunks_for(c, nv);
+  const size_t wbytes = (((size_t)n * nv * sizeof(S) + 255) / 256) * 256;
+  const size_t sbytes = (((size_t)nv * nv * sizeof(S) + 255) / 256) * 256;
+  const size_t pbytes = (size_t)nchunk * nv * nv * sizeof(S);
+  OEFE_TRY(ensure_ws(c, wbytes + 2 * sbytes + pbytes));
+  char* base = (char*)c->ws;
+  S* W = (S*)base;
+  S* Sm = (S*)(base + wbytes);
+  S* Y = (S*)(base + wbytes + sbytes);
+  S* part = (S*)(base + wbytes + 2 * sbytes);
+  for (int pass = 0; pass < 2; ++pass) {
+    OEFE_TRY(apply_M<S>(c, K, X, ld, nv, W, nv));
+    OEFE_TRY(gram<S>(c, X, ld, W, nv, n, nv, Sm, part, nchunk));
+    int info = 0;
+    OEFE_TRY(chol_inverse_t<S>(c, Sm, nv, false, true, Y, &info));
+    if (info != 0) {
+      c->err = "orthonormalize: Gram matrix not positive definite at column " + std::to_string(info);
+      return OEFE_ERR_CHOLESKY;
+    }
+    if (pass == 0 && cond) {
+      std::vector<S> Lh((size_t)nv * nv);
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(Lh.data(), Sm, Lh.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+      OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      double mx = 0, mn = 1e300;
+      for (int i = 0; i < nv; ++i) {
+        const double d = Ops<S>::re(Lh[(size_t)i * nv + i]);
+        mx = std::max(mx, d);
+        mn = std::min(mn, d);
+      }
+      *cond = (mx / mn) * (mx / mn);
+    }
+    OEFE_TRY(rotate<S>(c, X, ld, n, nv, Y, true));  // X <- X L^{-+}
+  }
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return OEFE_OK;
+}
+
+template <typename S>
+int rayleigh_ritz_t(oefe_ctx* c, int ik, S* X, int nv, int ld, int dtype, double* eig, double* resid) {
+  const KData& K = c->kd[ik];
+  const int64_t n = c->nh + c->nO;
+  const int nchunk = nchunks_for(c, nv);
+  const size_t vbytes = (((size_t)n * nv * sizeof(S) + 255) / 256) * 256;
+  const size_t sbytes = (((size_t)nv * nv * sizeof(S) + 255) / 256) * 256;
+  const size_t pbytes = (((size_t)nchunk * nv * nv * sizeof(S) + 255) / 256) * 256;
+  // ws is used by apply_op; keep HX, MX and small matrices in ws2
+  OEFE_TRY(ensure_ws2(c, 2 * vbytes + 3 * sbytes + pbytes + (size_t)nv * 24 + 256));
+  char* base = (char*)c->ws2;
+  S* HX = (S*)base;
+  S* MX = (S*)(base + vbytes);
+  S* Hq = (S*)(base + 2 * vbytes);
+  S* Mq = (S*)(base + 2 * vbytes + sbytes);
+  S* U = (S*)(base + 2 * vbytes + 2 * sbytes);
+  S* part = (S*)(base + 2 * vbytes + 3 * sbytes);
+  double* d_eps = (double*)(base + 2 * vbytes + 3 * sbytes + pbytes);
+  OEFE_TRY(apply_op2(c, ik, X, ld, HX, nv, nv, dtype, false));
+  OEFE_TRY(apply_M<S>(c, K, X, ld, nv, MX, nv));
+  OEFE_TRY(gram<S>(c, X, ld, HX, nv, n, nv, Hq, part, nchunk));
+  OEFE_TRY(gram<S>(c, X, ld, MX, nv, n, nv, Mq, part, nchunk));
+  std::vector<S> hH((size_t)nv * nv), hM((size_t)nv * nv);
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(hH.data(), Hq, hH.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(hM.data(), Mq, hM.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  using C = std::complex<double>;
+  std::vector<C> H2((size_t)nv * nv), M2((size_t)nv * nv), U2;
+  for (size_t i = 0; i < H2.size(); ++i) {
+    if constexpr (sizeof(S) == 8) { H2[i] = C(hH[i], 0); M2[i] = C(hM[i], 0); }
+    else { H2[i] = C(hH[i].x, hH[i].y); M2[i] = C(hM[i].x, hM[i].y); }
+  }
+  // Hermitian parts
+  for (int i = 0; i < nv; ++i)
+    for (int j = i; j < nv; ++j) {
+      C h = 0.5 * (H2[(size_t)i * nv + j] + std::conj(H2[(size_t)j * nv + i]));
+      H2[(size_t)i * nv + j] = h;
+      H2[(size_t)j * nv + i] = std::conj(h);
+      C mm = 0.5 * (M2[(size_t)i * nv + j] + std::conj(M2[(size_t)j * nv + i]));
+      M2[(size_t)i * nv + j] = mm;
+      M2[(size_t)j * nv + i] = std::conj(mm);
+    }
+  std::vector<double> w;
+  const int info = host_geneig(nv, H2, M2, w, U2);
+  if (info != 0) {
+    c->err = "rayleigh_ritz: projected overlap not positive definite";
+    return OEFE_ERR_CHOLESKY;
+  }
+  std::vector<S> hU((size_t)nv * nv);
+  for (size_t i = 0; i < hU.size(); ++i) {
+    if constexpr (sizeof(S) == 8) hU[i] = U2[i].real();
+    else hU[i] = mkc(U2[i].real(), U2[i].imag());
+  }
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(U, hU.data(), hU.size() * sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_eps, w.data(), nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  OEFE_TRY(rotate<S>(c, X, ld, n, nv, U, false));
+  if (resid) {
+    OEFE_TRY(rotate<S>(c, HX, nv, n, nv, U, false));
+    OEFE_TRY(rotate<S>(c, MX, nv, n, nv, U, false));
+    const int64_t tot = n * nv;
+    const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
+    k_resid_vec<S><<<blocks, 256, 0, c->stream>>>(HX, MX, nv, d_eps, n, nv, HX);  // HX <- residual
+    double* d_num = d_eps + nv;
+    k_resid_norms<S><<<nv, 256, 0, c->stream>>>(HX, nv, c->d_m, (const S*)K.Mooinv, c->nh, c->nO, nv, d_num);
+    // ||u||_M^2 = u^+ M u: with MX = M u, use the Gram diagonal
+    OEFE_TRY(gram<S>(c, X, ld, MX, nv, n, nv, Mq, part, nchunk));
+    std::vector<double> num(nv);
+    std::vector<S> mq((size_t)nv * nv);
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(num.data(), d_num, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(mq.data(), Mq, mq.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+    OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    for (int v = 0; v < nv; ++v) resid[v] = std::sqrt(std::max(num[v], 0.0) / Ops<S>::re(mq[(size_t)v * nv + v]));
+  }
+  for (int v = 0; v < nv; ++v) eig[v] = w[v];
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return OEFE_OK;
+}
+
+}  // namespace
+
+int chol_inverse_inplace(oefe_ctx* c, double* A, int n, bool cplx, bool inverse, int* info_host) {
+  if (n == 0) { *info_host = 0; return OEFE_OK; }
+  const size_t sb = cplx ? sizeof(cd) : sizeof(double);
+  OEFE_TRY(ensure_ws2(c, (size_t)n * n * sb + 256));
+  if (cplx) return chol_inverse_t<cd>(c, (cd*)A, n, inverse, false, (cd*)c->ws2, info_host);
+  return chol_inverse_t<double>(c, A, n, inverse, false, (double*)c->ws2, info_host);
+}
+
+int orthonormalize(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* cond) {
+  OEFE_TRY(check_fp64(c, ik, X, nv, ld, dtype));
+  if (dtype == OEFE_C128) return orthonormalize_t<cd>(c, ik, (cd*)X, nv, ld, cond);
+  return orthonormalize_t<double>(c, ik, (double*)X, nv, ld, cond);
+}
+
+int rayleigh_ritz(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* eig, double* resid) {
+  OEFE_TRY(check_fp64(c, ik, X, nv, ld, dtype));
+  if (!eig) { c->err = "rayleigh_ritz: need eig"; return OEFE_ERR_ARG; }
+  if (dtype == OEFE_C128) return rayleigh_ritz_t<cd>(c, ik, (cd*)X, nv, ld, dtype, eig, resid);
+  return rayleigh_ritz_t<double>(c, ik, (double*)X, nv, ld, dtype, eig, resid);
+}
+
+int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, double* b) {
+  const int dtype = (ik >= 0 && ik < (int)c->kd.size() && c->kd[ik].cplx) ? OEFE_C128 : OEFE_F64;
+  OEFE_TRY(check_fp64(c, ik, v0, 1, 1, dtype));
+  if (steps < 2 || steps > 1000 || !b) { c->err = "upper_bound: 2 <= steps <= 1000"; return OEFE_ERR_ARG; }
+  const int64_t n = c->nh + c->nO;
+  const size_t sb = dtype == OEFE_C128 ? sizeof(cd) : sizeof(double);
+  const size_t vb = (((size_t)n * sb + 255) / 256) * 256;
+  OEFE_TRY(ensure_ws2(c, 4 * vb + 4096));
+  char* base = (char*)c->ws2;
+  void* q = base;
+  void* qp = base + vb;
+  void* w = base + 2 * vb;
+  void* mw = base + 3 * vb;
+  double* d_dot = (double*)(base + 4 * vb);
+  const KData& K = c->kd[ik];
+  std::vector<double> al, be;
+  // q = v0 / ||v0||_M
+  auto mdot = [&](const void* x, const void* y, double* out) -> int {  // re(x^+ M y)
+    if (dtype == OEFE_C128) {
+      OEFE_TRY(apply_M<cd>(c, K, (const cd*)y, 1, 1, (cd*)mw, 1));
+      OEFE_TRY(gram<cd>(c, (const cd*)x, 1, (const cd*)mw, 1, n, 1, (cd*)d_dot, (cd*)(d_dot + 16), 32));
+      cd h;
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(&h, d_dot, sizeof(cd), cudaMemcpyDeviceToHost, c->stream));
+      OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      *out = h.x;
+    } else {
+      OEFE_TRY(apply_M<double>(c, K, (const double*)y, 1, 1, (double*)mw, 1));
+      OEFE_TRY(gram<double>(c, (const double*)x, 1, (const double*)mw, 1, n, 1, d_dot, d_dot + 16, 32));
+      double h;
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(&h, d_dot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      *out = h;
+    }
+    return OEFE_OK;
+  };
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(q, v0, n * sb, cudaMemcpyDeviceToDevice, c->stream));
+  OEFE_CUDA_TRY(c, cudaMemsetAsync(qp, 0, n * sb, c->stream));
+  double nrm;
+  OEFE_TRY(mdot(q, q, &nrm));
+  const int nr = dtype == OEFE_C128 ? 2 : 1;  // reals per entry
+  const int64_t nreal = n * nr;
+  const int lb = (int)std::min<int64_t>((nreal + 255) / 256, (int64_t)c->num_sms * 16);
+  k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, nullptr, nullptr, nullptr, nreal, 1.0 / std::sqrt(nrm), 0, 0);
+  double beta = 0.0;
+  for (int it = 0; it < steps; ++it) {
+    OEFE_TRY(apply_op2(c, ik, q, 1, w, 1, 1, dtype, true));
+    double alpha;
+    OEFE_TRY(mdot(q, w, &alpha));
+    // w <- w - alpha q - beta qp
+    k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)w, (const double*)q, (const double*)qp, nullptr, nreal, 1.0,
+                                                -alpha, -beta);
+    double bb;
+    OEFE_TRY(mdot(w, w, &bb));
+    beta = std::sqrt(std::max(bb, 0.0));
+    al.push_back(alpha);
+    be.push_back(beta);
+    // qp <- q, q <- w / beta
+    k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)qp, (const double*)q, nullptr, (double*)q, nreal, 0.0, 1.0, 0);
+    k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, (const double*)w, nullptr, nullptr, nreal, 0.0, 1.0 / beta, 0);
+    OEFE_CUDA_TRY(c, cudaGetLastError());
+  }
+  // largest eigenvalue of the Lanczos tridiagonal matrix
+  const int m = (int)al.size();
+  std::vector<std::complex<double>> T((size_t)m * m, 0.0), V;
+  for (int i = 0; i < m; ++i) {
+    T[(size_t)i * m + i] = al[i];
+    if (i + 1 < m) { T[(size_t)i * m + i + 1] = be[i]; T[(size_t)(i + 1) * m + i] = be[i]; }
+  }
+  std::vector<double> wv;
+  jacobi_eigh(m, T, wv, V);
+  *b = wv.back() + be.back();
+  return OEFE_OK;
+}

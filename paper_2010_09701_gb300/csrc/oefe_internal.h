@@ -1,0 +1,187 @@
+// Internal state and helpers of the OEFE library (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/oefe.h"
+
+// ------------------------------------------------------------------ complex
+struct cd {
+  double x, y;
+};
+struct cf {
+  float x, y;
+};
+__host__ __device__ inline cd mkc(double a, double b) { return cd{a, b}; }
+__host__ __device__ inline cd operator+(cd a, cd b) { return cd{a.x + b.x, a.y + b.y}; }
+__host__ __device__ inline cd operator-(cd a, cd b) { return cd{a.x - b.x, a.y - b.y}; }
+__host__ __device__ inline cd operator-(cd a) { return cd{-a.x, -a.y}; }
+__host__ __device__ inline cd operator*(cd a, cd b) { return cd{a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__host__ __device__ inline cd operator*(double s, cd a) { return cd{s * a.x, s * a.y}; }
+__host__ __device__ inline cd operator*(cd a, double s) { return cd{s * a.x, s * a.y}; }
+__host__ __device__ inline cd& operator+=(cd& a, cd b) { a.x += b.x; a.y += b.y; return a; }
+__host__ __device__ inline cd& operator-=(cd& a, cd b) { a.x -= b.x; a.y -= b.y; return a; }
+__host__ __device__ inline cd cconj(cd a) { return cd{a.x, -a.y}; }
+__host__ __device__ inline double cabs2(cd a) { return a.x * a.x + a.y * a.y; }
+// conj(a) * b
+__host__ __device__ inline cd cmulc(cd a, cd b) { return cd{a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x}; }
+
+// ------------------------------------------------------------------ status
+#define OEFE_CUDA_TRY(ctx, call)                                                       \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess) {                                                           \
+      (ctx)->err = std::string(#call) + ": " + cudaGetErrorString(e_);                 \
+      return OEFE_ERR_CUDA;                                                            \
+    }                                                                                  \
+  } while (0)
+
+#define OEFE_TRY(call)       \
+  do {                       \
+    int s_ = (call);         \
+    if (s_ != OEFE_OK) return s_; \
+  } while (0)
+
+// ------------------------------------------------------------------ leaves
+struct Leaf {
+  int cell;       // owning cell
+  int n1;         // Gauss points per axis
+  int64_t q0;     // first point (global index)
+  double lo[3];   // leaf box, physical coordinates
+  double hi[3];
+};
+
+// per k-point data
+struct KData {
+  double k[3] = {0, 0, 0};
+  double w = 1.0;
+  bool cplx = false;
+  double* gamma = nullptr;   // (ncells, nloc, ne_max) scalars (double or cd)
+  double* Moo = nullptr;     // nO x nO scalars
+  double* Mooinv = nullptr;  // nO x nO scalars (FP64)
+  double* H64 = nullptr;     // (ncells, npad, npad) scalars
+  float* H32 = nullptr;      // (ncells, npad, npad) float or cf
+  bool built = false;
+};
+
+struct oefe_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int num_sms = 0;
+
+  // mesh
+  bool has_mesh = false;
+  double a = 0;
+  int nc[3] = {0, 0, 0};
+  std::vector<double> xb[3];
+  int p = 0, P = 0, nloc = 0;
+  int N[3] = {0, 0, 0};
+  int64_t nh = 0;
+  int ncells = 0;
+  std::vector<double> gll_x, gll_w;
+  double* d_gll = nullptr;       // P nodes
+  double* d_m = nullptr;         // nh lumped masses
+  int* d_cell_nodes = nullptr;   // ncells * nloc
+  double* d_cellbox = nullptr;   // ncells * 6 (lo xyz, h xyz)
+  std::vector<int> cell_nodes;   // host copy
+
+  // enrichment
+  bool has_enr = false;
+  int natoms = 0, nfun = 0, nO = 0, ngrid = 0;
+  double r0 = 0, rc = 0;
+  std::vector<double> pos;
+  std::vector<int> lm;
+  double* d_pos = nullptr;
+  int* d_lm = nullptr;
+  double* d_R = nullptr;
+  double* d_dR = nullptr;
+
+  // active sets (CSR over cells)
+  std::vector<int> act_off, act_idx;
+  int* d_act_off = nullptr;
+  int* d_act_idx = nullptr;
+  int ne_max = 0;
+  int npad = 0;
+  // node -> (cell slot) lists: slot = e * npad + local
+  int64_t* d_node_off = nullptr;
+  int64_t* d_node_slot = nullptr;
+  // enrichment function -> (cell slot) lists: slot = e * npad + nloc + j
+  int64_t* d_enr_off = nullptr;
+  int64_t* d_enr_slot = nullptr;
+  std::vector<int64_t> enr_off_h;
+
+  // quadrature
+  bool has_quad = false;
+  int nq_cell = 0, nq_enr = 0, depth = 0;
+  int64_t nq = 0;
+  std::vector<int64_t> q_off;     // ncells + 1
+  std::vector<Leaf> leaves;
+  std::vector<int> leaf_off;      // ncells + 1
+  std::vector<double> qxyz, qw;   // host copies
+  double* d_qxyz = nullptr;
+  double* d_qw = nullptr;
+  Leaf* d_leaves = nullptr;
+  int* d_leaf_off = nullptr;
+  int64_t* d_q_off = nullptr;
+
+  // k-points
+  std::vector<KData> kd;
+  bool has_k = false;
+  bool built = false;
+  double* d_dblk = nullptr;       // per-k scratch: d_e blocks (ncells, nloc, ne_max) cd
+
+  // scratch (grown on demand, reused)
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  void* ws2 = nullptr;
+  size_t ws2_bytes = 0;
+  int* d_status = nullptr;        // device status word (Cholesky failures, timeouts)
+};
+
+// ------------------------------------------------------------------ internals
+int ensure_ws(oefe_ctx* c, size_t bytes);
+int ensure_ws2(oefe_ctx* c, size_t bytes);
+int dev_alloc(oefe_ctx* c, void** p, size_t bytes);
+void dev_free(void* p);
+
+// setup (setup.cpp)
+int setup_mesh(oefe_ctx* c, double a, const int ncell[3], const double* xb, int p);
+int setup_enrichment(oefe_ctx* c, int natoms, const double* pos, int nfun, const int* lm, int ngrid,
+                     const double* R, const double* dR, double r0, double rc);
+int setup_quadrature(oefe_ctx* c, int nq_cell, int nq_enr, int depth);
+void graded_breakpoints(double a, int ncell, const std::vector<double>& coords, double ratio,
+                        std::vector<double>& out);
+void gll_rule(int p, std::vector<double>& x, std::vector<double>& w);
+void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w);
+
+// build (build.cu)
+int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w);
+int build_hamiltonian(oefe_ctx* c, const double* veff, int store);
+
+// dense helpers (linalg.cu)
+int chol_inverse_inplace(oefe_ctx* c, double* A, int n, bool cplx, bool inverse, int* info_host);
+
+// operator application and filter (filter.cu)
+int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dtype, bool minv);
+int apply_op2(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv);
+int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int degree, double a,
+                double b, double a0, int flags);
+
+// subspace (linalg.cu)
+int orthonormalize(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* cond);
+int rayleigh_ritz(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* eig, double* resid);
+int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, double* b);
+
+// fields (density.cu)
+int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype,
+            const double* occ, double* rho);
+int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* gV);
+
+inline bool dtype_complex(int dt) { return dt == OEFE_C128 || dt == OEFE_C64; }
+inline bool dtype_fp64(int dt) { return dt == OEFE_F64 || dt == OEFE_C128; }
+inline size_t dtype_bytes(int dt) {
+  return dt == OEFE_F64 ? 8 : dt == OEFE_F32 ? 4 : dt == OEFE_C128 ? 16 : 8;
+}

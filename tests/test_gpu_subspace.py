@@ -1,0 +1,149 @@
+"""GPU parity of Cholesky-QR, Rayleigh-Ritz (Eq. ProjKS), the density
+(Eq. rho) and the adjoint of H.X against the oracle."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import torch
+
+import workloads as W
+from gpu_cases import c1_pair, paired, rel, to_gpu
+from oracle import solver
+
+pytestmark = pytest.mark.gpu
+
+KS = [(0.0, 0.0, 0.0), (0.25, -0.4, 0.1)]
+
+
+@pytest.mark.parametrize("k", KS)
+def test_orthonormalize(k):
+    prs, ctx, V, _ = paired(ks=[k])
+    pr = prs[0]
+    Y = W.random_vectors(pr.n, 10, complex_=pr.complex, seed=5)
+    Yd = to_gpu(Y)
+    ctx.orthonormalize(0, Yd)
+    Q = Yd.cpu().numpy()
+    assert np.allclose(Q.conj().T @ pr.apply_M(Q), np.eye(10), atol=1e-12)
+    Qo = solver.cholqr(Y, pr.apply_M)
+    # same span: Q = Qo U with U unitary -> Qo^+ M Q unitary
+    U = Qo.conj().T @ pr.apply_M(Q)
+    assert np.allclose(U.conj().T @ U, np.eye(10), atol=1e-11)
+    # CholQR is deterministic: the factors agree too
+    assert rel(Q, Qo) < 1e-10
+
+
+def test_orthonormalize_rank_deficient_reports_cholesky():
+    from paper_2010_09701_gb300 import OefeError, binding
+    prs, ctx, V, _ = paired()
+    pr = prs[0]
+    Y = W.random_vectors(pr.n, 4, seed=5)
+    Y[:, 3] = Y[:, 1]
+    with pytest.raises(OefeError) as e:
+        ctx.orthonormalize(0, to_gpu(Y))
+    assert e.value.code == binding.ERR_CHOLESKY
+
+
+@pytest.mark.parametrize("k", KS)
+def test_rayleigh_ritz(k):
+    prs, ctx, V, _ = paired(ks=[k])
+    pr = prs[0]
+    Q = solver.cholqr(W.random_vectors(pr.n, 9, complex_=pr.complex, seed=6), pr.apply_M)
+    eps_o, X_o = solver.rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
+    Qd = to_gpu(Q)
+    eps, res = ctx.rayleigh_ritz(0, Qd, resid=True)
+    assert np.max(np.abs(eps - eps_o)) < 1e-10 * max(1, np.max(np.abs(eps_o)))
+    res_o = solver.residual_norms(pr, X_o, eps_o)
+    assert np.allclose(res, res_o, rtol=1e-8, atol=1e-12)
+    # rotated vectors: unique up to a phase per (non-degenerate) column
+    X = Qd.cpu().numpy()
+    ph = np.sum(np.conj(X_o) * pr.apply_M(X), axis=0)
+    assert np.allclose(np.abs(ph), 1.0, atol=1e-9)
+
+
+@pytest.mark.parametrize("k", KS)
+def test_density_and_band_trace_grad(k):
+    prs, ctx, V, Vd = paired(ks=[k])
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 6, complex_=pr.complex, seed=8)
+    occ = np.array([2.0, 2.0, 1.5, 1.0, 0.2, 0.0])
+    rho_o = solver.density([pr], [X], [occ])
+    rho = torch.zeros(pr.quad.nq, dtype=torch.float64, device="cuda")
+    ctx.density([to_gpu(X)], [occ], rho)
+    assert rel(rho.cpu().numpy(), rho_o) < 1e-12
+    g_o = solver.band_trace_grad_V(pr, X)
+    g = torch.zeros_like(rho)
+    ctx.band_trace_grad(0, to_gpu(X), g)
+    assert rel(g.cpu().numpy(), g_o) < 1e-12
+
+
+def test_density_two_kpoints():
+    ks = [(0.3, 0.0, 0.0), (-0.3, 0.1, 0.0)]
+    prs, ctx, V, Vd = paired(ks=ks)
+    Xs = [W.random_vectors(pr.n, 5, complex_=True, seed=i) for i, pr in enumerate(prs)]
+    occs = [np.array([1.0, 1.0, 0.5, 0.25, 0.0]) * 0.5, np.array([1.0, 0.9, 0.5, 0.1, 0.0]) * 0.5]
+    rho_o = solver.density(prs, Xs, occs)
+    rho = torch.zeros(prs[0].quad.nq, dtype=torch.float64, device="cuda")
+    ctx.density([to_gpu(x) for x in Xs], occs, rho)
+    assert rel(rho.cpu().numpy(), rho_o) < 1e-12
+
+
+@pytest.mark.parametrize("k", KS)
+def test_autograd_band_trace(k):
+    from paper_2010_09701_gb300.autograd import apply_h, band_trace
+    prs, ctx, V, Vd = paired(ks=[k])
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 3, complex_=pr.complex, seed=11)
+    Vt = Vd.clone().requires_grad_(True)
+    Xt = to_gpu(X).requires_grad_(True)
+    E = band_trace(Vt, Xt, ctx, 0)
+    E.backward()
+    assert abs(E.item() - np.real(np.sum(np.conj(X) * pr.apply_H(X)))) < 1e-12 * abs(E.item())
+    assert rel(Vt.grad.cpu().numpy(), solver.band_trace_grad_V(pr, X)) < 1e-12
+    assert rel(Xt.grad.cpu().numpy(), 2 * pr.apply_H(X)) < 1e-12
+    # central differences on the GPU path itself, h = 1e-4 (E is affine in V)
+    rng = np.random.default_rng(0)
+    for q in rng.choice(pr.quad.nq, 4, replace=False):
+        Vp, Vm = Vd.clone(), Vd.clone()
+        Vp[q] += 1e-4
+        Vm[q] -= 1e-4
+        fd = (band_trace(Vp, Xt.detach(), ctx, 0).item() - band_trace(Vm, Xt.detach(), ctx, 0).item()) / 2e-4
+        assert abs(fd - Vt.grad[q].item()) < 1e-6 * max(1.0, abs(fd))
+    # vector-Jacobian product of Y = H(V) X
+    G = W.random_vectors(pr.n, 3, complex_=pr.complex, seed=12)
+    Vt2 = Vd.clone().requires_grad_(True)
+    Xt2 = to_gpu(X).requires_grad_(True)
+    Y = apply_h(Vt2, Xt2, ctx, 0)
+    Y.backward(to_gpu(G))
+    uG = [pr.values_at_points(e, G) for e in range(pr.mesh.ncells)]
+    uX = [pr.values_at_points(e, X) for e in range(pr.mesh.ncells)]
+    cross = np.concatenate([np.real(np.sum(np.conj(a) * b, axis=1)) for a, b in zip(uG, uX)]) * pr.quad.weights
+    assert rel(Vt2.grad.cpu().numpy(), cross) < 1e-11
+    assert rel(Xt2.grad.cpu().numpy(), pr.apply_H(G)) < 1e-12
+
+
+def test_c1_pass_eigenvalues_and_density():
+    # one full pass on the first configuration, GPU FP64 against the oracle:
+    # eigenvalues within 1e-8 Ha and density L2 error within 1e-8
+    w = W.config_c1()
+    prs, ctx, V, Vd = c1_pair()
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 20, seed=w.seed)
+    b = solver.lanczos_upper_bound(pr.apply_H, pr.apply_M, pr.apply_Minv, W.random_vectors(pr.n, 1, seed=9)[:, 0], 25)
+    a, a0 = 0.0, -0.5 * 14 ** 2 - 1.0
+    Y = solver.chebyshev_filter(pr.apply_A, X, w.degree, a, b, a0)
+    Q = solver.cholqr(Y, pr.apply_M)
+    eps_o, Xo = solver.rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
+    mu = solver.fermi_level([eps_o], [1.0], w.nelectrons)
+    occ = solver.occupations([eps_o], [1.0], mu)[0]
+    rho_o = solver.density([pr], [Xo], [occ])
+
+    Xd = to_gpu(X)
+    ctx.chebyshev_filter(0, Xd, w.degree, a, b, a0)
+    ctx.orthonormalize(0, Xd)
+    eps = ctx.rayleigh_ritz(0, Xd)
+    assert np.max(np.abs(eps - eps_o)) < 1e-8
+    occ_g = solver.occupations([eps], [1.0], solver.fermi_level([eps], [1.0], w.nelectrons))[0]
+    rho = torch.zeros(pr.quad.nq, dtype=torch.float64, device="cuda")
+    ctx.density([Xd], [occ_g], rho)
+    r = rho.cpu().numpy()
+    wq = pr.quad.weights
+    assert np.sqrt(np.sum(wq * (r - rho_o) ** 2)) / np.sqrt(np.sum(wq * rho_o ** 2)) < 1e-8
