@@ -1,0 +1,402 @@
+#!/usr/bin/env python
+"""Chebyshev-filter benchmark on one GB300 (or N independent replicas).
+
+Workload: the 8-atom zincblende cell a = 8.5 bohr (Z = 14 / 6), graded 16^3
+mesh, p = 6, hydrogenic 1s-2p enrichment (40 functions), Monkhorst-Pack 2x2x1
+(4 k-points, complex), 64 vectors per k, Chebyshev degree 30, frozen
+synthetic V_eff. One step is one pass of the whole hot path:
+build_hamiltonian (FP64 arithmetic, FP64 + FP32 storage), then per k the
+mixed filter (29 FP32 degrees + the last in FP64), FP64 Cholesky-QR and
+Rayleigh-Ritz, then occupations, the density and the band-trace adjoint.
+
+value = dense-count filter flops of a step / step time (TFLOP/s), with the
+flop count sum_k sum_e 2 n_aug,e^2 N_v * 4 (complex) per degree.
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import workloads as W  # noqa: E402
+
+FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
+FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12     # 2 DFMA / clk / SM on GB300
+FALLBACK_HBM_GBS = 6800.0
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            return json.load(open(p)), "measured"
+        except Exception:
+            pass
+    return {"hbm_gbs": FALLBACK_HBM_GBS}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.device), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dense_filter_flops(ctx_naug, nvs, degree):
+    """sum over k of sum_e 2 n_aug,e^2 N_v,k * 4 (complex) per degree, times the degree."""
+    s2 = float(np.sum(np.asarray(ctx_naug, float) ** 2))
+    return sum(2.0 * s2 * nv * 4.0 for nv in nvs) * degree
+
+
+def kernel_flops_per_launch(naug, nv, cplx=True):
+    return 2.0 * float(np.sum(np.asarray(naug, float) ** 2)) * nv * (4.0 if cplx else 1.0)
+
+
+# ----------------------------------------------------------------------------- GPU arm
+def run_ours(args, rank, world):
+    import torch
+    import paper_2010_09701_gb300 as P
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    w = W.CONFIGS[args.config]()
+    t0 = time.time()
+    ctx = P.setup_workload(w, device=dev)
+    nh, nO = ctx.ndof()
+    n = nh + nO
+    nk = ctx.nk
+    xyz, qw = ctx.quadrature_points()
+    V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
+    naug = np.array([len(ctx.cell_info(e)) for e in range(int(np.prod([w.ncell] * 3)))])
+    nvs = w.nv
+    deg = w.degree
+    X0 = [torch.tensor(W.random_vectors(n, nvs[ik], complex_=True, seed=w.seed + ik), dtype=torch.complex128,
+                       device="cuda") for ik in range(nk)]
+    X = [x.clone() for x in X0]
+    # filter bounds: b from a Lanczos run per k; a, a0 below/above the wanted window
+    bks = []
+    for ik in range(nk):
+        v0 = torch.tensor(W.random_vectors(n, 1, complex_=True, seed=100 + ik), dtype=torch.complex128, device="cuda")
+        bks.append(ctx.upper_bound(ik, v0, 20))
+    a_lo, a0 = 0.0, -0.5 * float(max(w.Z)) ** 2 - 1.0
+    rho = torch.zeros(len(qw), dtype=torch.float64, device="cuda")
+    gV = torch.zeros_like(rho)
+    setup_s = time.time() - t0
+    stream = torch.cuda.current_stream()
+
+    filt_events = []
+    phase_ms = {}
+    store = P.STORE_F64 | (P.STORE_BF16X3 if args.tensor else P.STORE_F32)
+    fflags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
+    ctx.build_hamiltonian(V, store)
+
+    def mark():
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record(stream)
+        return ev
+
+    def step(record=False):
+        t = [mark()]
+        ctx.build_hamiltonian(V, store)
+        t.append(mark())
+        eigs = []
+        ortho_rr = []
+        for ik in range(nk):
+            X[ik].copy_(X0[ik])
+            e0 = mark()
+            ctx.chebyshev_filter(ik, X[ik], deg, a_lo, bks[ik], a0, flags=fflags)
+            e1 = mark()
+            if record:
+                filt_events.append((e0, e1))
+            ctx.orthonormalize(ik, X[ik])
+            e2 = mark()
+            eigs.append(ctx.rayleigh_ritz(ik, X[ik]))
+            ortho_rr.append((e0, e1, e2, mark()))
+        t.append(mark())
+        mu, occ, eb = P.occupations(eigs, [1.0 / nk] * nk, w.nelectrons)
+        ctx.density(X, occ, rho)
+        t.append(mark())
+        ctx.band_trace_grad(0, X[0], gV)
+        t.append(mark())
+        if record:
+            torch.cuda.synchronize()
+            phase_ms.clear()
+            phase_ms["build_hamiltonian"] = t[0].elapsed_time(t[1])
+            phase_ms["filter"] = sum(a.elapsed_time(b) for a, b, _, _ in ortho_rr)
+            phase_ms["orthonormalize"] = sum(b.elapsed_time(c) for _, b, c, _ in ortho_rr)
+            phase_ms["rayleigh_ritz"] = sum(c.elapsed_time(d) for _, _, c, d in ortho_rr)
+            phase_ms["density"] = t[2].elapsed_time(t[3])
+            phase_ms["band_trace_grad"] = t[3].elapsed_time(t[4])
+        return eigs, eb
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    sampler = ClockSampler(dev)
+    sampler.start()
+    ctx.kernel_timing([P.C64])
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        eigs, eb_mixed = step(record=True)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    kms, klaunch = ctx.kernel_time()
+    ctx.kernel_timing([])
+    step_ms = ev0.elapsed_time(ev1) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        step_ms = t.item()
+    filt_ms = [a.elapsed_time(b) for a, b in filt_events]
+    flops_step = dense_filter_flops(naug, nvs, deg)
+    value = world * flops_step / (step_ms * 1e-3) / 1e12
+    filt_tflops = flops_step / (sum(filt_ms) / args.steps * 1e-3) / 1e12
+    s_per_pass = float(np.mean(filt_ms)) * 1e-3
+    # dominant kernel: the FP32 (complex64) cell product
+    per_launch_ms = kms / max(klaunch, 1)
+    kflops = kernel_flops_per_launch(naug, nvs[0], True)
+    kbytes = (float(np.sum(naug ** 2)) * 8 + 2 * float(np.sum(naug)) * nvs[0] * 8)
+    achieved = kflops / (per_launch_ms * 1e-3) / 1e12
+    peaks, src = measured_peaks()
+    if args.tensor:
+        hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+        ach = kbytes / (per_launch_ms * 1e-3) / 1e9
+        roofline = {"kernel": "k_cell_mma<complex> (tcgen05 BF16x3)", "bound": "hbm", "achieved": ach, "peak": hbm,
+                    "unit": "GB/s", "frac": ach / hbm, "traffic": None, "algorithmic_bytes_per_launch": kbytes,
+                    "launches": klaunch, "ms_per_launch": per_launch_ms, "peak_source": src,
+                    "dense_tflops": achieved,
+                    "tensor_frac_bf16": 3 * achieved / peaks.get("bf16_tflops", 1911.8)}
+    else:
+        roofline = {"kernel": "k_cell_apply<float,complex>", "bound": "alu", "achieved": achieved,
+                    "peak": FP32_PEAK_DERIVED, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_DERIVED,
+                    "traffic": None, "algorithmic_bytes_per_launch": kbytes, "launches": klaunch,
+                    "ms_per_launch": per_launch_ms, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
+                    "hbm_gbs_at_algorithmic_bytes": kbytes / (per_launch_ms * 1e-3) / 1e9}
+
+    # plain FP64 GPU filter pass on k = 0, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if not args.skip_fp64:
+        Xf = X0[0].clone()
+        ctx.chebyshev_filter(0, Xf, 1, a_lo, bks[0], a0)   # warm
+        Xf.copy_(X0[0])
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        ctx.chebyshev_filter(0, Xf, deg, a_lo, bks[0], a0)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        fp64_s = f0.elapsed_time(f1) * 1e-3
+        ctx.orthonormalize(0, Xf)
+        eig64 = ctx.rayleigh_ritz(0, Xf)
+        # mixed-vs-FP64 accuracy of the same pass (k = 0, same start vectors)
+        fp64 = {"s_per_pass_k0": fp64_s,
+                "tflops": dense_filter_flops(naug, [nvs[0]], deg) / fp64_s / 1e12,
+                "speedup_mixed_vs_fp64": fp64_s / (filt_ms[0] * 1e-3),
+                "max_abs_d_eig_k0_Ha": float(np.max(np.abs(eig64 - eigs[0]))),
+                "d_sum_eig_k0_per_atom_Ha": float(abs(np.sum(eig64) - np.sum(eigs[0])) / w.natoms)}
+
+    # end to end through the public API with host buffers (H2D of V and X0, D2H of rho and eigenvalues)
+    e2e = None
+    if not args.skip_e2e:
+        Vh = V.cpu().pin_memory()
+        X0h = [x.cpu().pin_memory() for x in X0]
+        rho_h = torch.empty(rho.shape, dtype=rho.dtype).pin_memory()
+        torch.cuda.synchronize()
+        t_start = time.perf_counter()
+        ee0 = torch.cuda.Event(enable_timing=True)
+        ee1 = torch.cuda.Event(enable_timing=True)
+        ee0.record(stream)
+        for _ in range(args.e2e_steps):
+            V.copy_(Vh, non_blocking=True)
+            for ik in range(nk):
+                X0[ik].copy_(X0h[ik], non_blocking=True)
+            eigs_e, _ = step()
+            rho_h.copy_(rho, non_blocking=True)
+        ee1.record(stream)
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t_start) / args.e2e_steps
+        e2e_ms = ee0.elapsed_time(ee1) / args.e2e_steps
+        bi = V.numel() * 8 + sum(x.numel() * 16 for x in X0)
+        bo = rho.numel() * 8 + sum(len(e) * 8 for e in eigs_e)
+        e2e = {"value": world * flops_step / (max(e2e_ms, wall * 1e3) * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": max(e2e_ms, wall * 1e3)}
+
+    cpu = None
+    if rank == 0 and not args.skip_cpu_baseline:
+        cpu = run_oracle_sample(w, args.sample_cells, steps=1, warmup=0)
+
+    out = {"metric": "Cheb-filter TFLOP/s (dense count) & s/filter pass, mixed vs FP64 on GB300",
+           "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "c64+c128", "data": "synthetic",
+           "config": {"workload": "zincblende a=8.5 bohr 8 atoms (Z 14/6), graded 16^3 cells p=6, 40 enrichment "
+                                  "functions, MP 2x2x1 (4 k), 64 vectors/k, Chebyshev degree 30, mixed filter "
+                                  "(29 FP32 degrees + last FP64), FP64 Cholesky-QR / Rayleigh-Ritz / density",
+                      "n_dof_per_k": int(n), "cells": int(len(naug)), "mean_n_aug": float(np.mean(naug)),
+                      "l2": "inputs larger than L2 (cell matrices %.1f GB per k)" % (np.sum(naug ** 2) * 8 / 1e9),
+                      "parallelism": "replicas" if world > 1 else "single GPU"},
+           "filter_s_per_pass": s_per_pass, "filter_tflops": filt_tflops, "fp64": fp64, "phase_ms": phase_ms,
+           "filter_precision": "BF16x3 tensor cores + last degree FP64" if args.tensor else "FP32 + last degree FP64",
+           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+           "gpu_launches": int(args.steps * (nk * (deg * 4 + 40) + 20)),
+           "peaks_source": src, "setup_s": setup_s}
+    return out
+
+
+# ----------------------------------------------------------------------------- oracle (CPU) arm
+def run_oracle_sample(w, ncells_side, steps=1, warmup=0):
+    """The oracle, as it stands, on a bounded sample of the same workload: a
+    ncells_side^3 block of cells of the mesh at k-point 0 (cell matrices of the
+    block with exact orthogonalizing coefficients), one step = build of the
+    block's cell matrices + the degree-m filter pass + Cholesky-QR +
+    Rayleigh-Ritz on the rows the block touches."""
+    from oracle import solver
+    from oracle.enrichment import Enrichment
+    from oracle.mesh import Mesh
+    from oracle.operators import Problem
+    from oracle.quadrature import Quadrature
+
+    xb = W.mesh_breakpoints(w)
+    mesh = Mesh(w.a, xb, w.p)
+    nqc, nqe, depth = w.quad_params()
+    quad = Quadrature(mesh, w.pos, w.rc, nqc, nqe, depth)
+    R, dR = W.radial_tables(w.Z, rc=w.rc, ngrid=w.ngrid)
+    enr = Enrichment(w.a, w.pos, W.orbital_lm_codes(), R, dR, w.r0, w.rc)
+    k, _ = W.monkhorst_pack(w.a, w.kgrid)
+    s = ncells_side
+    cells = [ix + w.ncell * (iy + w.ncell * iz) for iz in range(s) for iy in range(s) for ix in range(s)]
+    pr = Problem(mesh, quad, enr, k[0], cells=cells)
+    V = W.veff(quad.points, w.a, w.pos, w.Z, w.sigma)
+    nv = w.nv[0]
+    X0 = W.random_vectors(pr.n, nv, complex_=pr.complex, seed=w.seed)
+    naug = np.array([len(pr.index(e)) for e in cells])
+    flops = dense_filter_flops(naug, [nv], w.degree)
+    times = []
+    for it in range(warmup + steps):
+        t0 = time.perf_counter()
+        pr.build(V)
+        b = solver.lanczos_upper_bound(pr.apply_H, pr.apply_M, pr.apply_Minv, X0[:, 0], 10)
+        Y = solver.chebyshev_filter(pr.apply_A, X0, w.degree, 0.0, b, -0.5 * max(w.Z) ** 2 - 1.0)
+        Q = solver.cholqr(Y, pr.apply_M)
+        solver.rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
+        if it >= warmup:
+            times.append(time.perf_counter() - t0)
+    t = float(np.mean(times))
+    return {"value": flops / t / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(), "kind": "oracle",
+            "s_per_step": t,
+            "sample": "%d^3-cell block (%d of %d cells, %d rows) at k-point 0: build of the block's cell matrices, "
+                      "Lanczos bound, degree-%d filter, Cholesky-QR, Rayleigh-Ritz; dense-count flops of the "
+                      "block's filter / step time" % (s, len(cells), w.ncell ** 3, pr.n, w.degree)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    w = W.CONFIGS[args.config]()
+    res = run_oracle_sample(w, args.sample_cells, steps=args.steps, warmup=args.warmup)
+    return {"impl": "reference", "metric": "Cheb-filter TFLOP/s (dense count) & s/filter pass, mixed vs FP64 on GB300",
+            "value": res["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["s_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "c128", "data": "synthetic",
+            "config": {"workload": "zincblende a=8.5 bohr 8 atoms, graded 16^3 cells p=6, 64 vectors, degree 30 "
+                                   "(bounded sample, see cpu_baseline.sample)"},
+            "cpu_baseline": res,
+            "e2e": {"value": res["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3", choices=["c2", "c3"])
+    ap.add_argument("--sample-cells", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--fp32-simt", dest="tensor", action="store_false",
+                    help="FP32 SIMT cell products instead of the BF16x3 tensor-core path")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+        if out is not None:
+            print(json.dumps(out))
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    out = run_ours(args, rank, world)
+    if rank == 0:
+        print(json.dumps(out))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

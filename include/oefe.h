@@ -51,7 +51,7 @@ enum {
 enum { OEFE_F64 = 0, OEFE_F32 = 1, OEFE_C128 = 2, OEFE_C64 = 3 };
 
 /* Storage of the cell Hamiltonians (bit mask for oefe_build_hamiltonian). */
-enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2 };
+enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4 };
 
 /* ---------------------------------------------------------------- context */
 int oefe_create(oefe_ctx_t* out, int device, void* cuda_stream);
@@ -122,8 +122,9 @@ int oefe_ndof(oefe_ctx_t ctx, int64_t* n_h, int* n_O);
  * cell and k (Eq. HOEFEelelements; T maps OEFE to EFE coefficients,
  * Eq. UOEFESplit). veff_q: device, nq_total doubles, V_eff at the quadrature
  * points. store: OEFE_STORE_F64 (FP64 / complex128 matrices, needed by every
- * FP64 call) and/or OEFE_STORE_F32 (FP32 / complex64 copies for the mixed
- * filter). All arithmetic is FP64. */
+ * FP64 call), OEFE_STORE_F32 (FP32 / complex64 copies for the FP32 filter)
+ * and/or OEFE_STORE_BF16X3 (each real plane split into bf16 hi + lo for the
+ * tensor-core filter; same bytes as FP32). All arithmetic is FP64. */
 int oefe_build_hamiltonian(oefe_ctx_t ctx, const double* veff_q, int store);
 
 /* Row/column map of one cell matrix: idx (host, n_aug ints) receives global
@@ -148,8 +149,11 @@ int oefe_apply_a(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld,
  * dense FP64 (M^oo)^{-1}) and the recurrence are fused into the reduction
  * of the cell products. dtype: F64/C128 use the FP64 cell matrices, F32/C64
  * the FP32 copies (FP32 accumulation). flags: OEFE_FILTER_LAST_FP64 runs the
- * last degree through the FP64 path (X must then be F64/C128 storage). */
-enum { OEFE_FILTER_LAST_FP64 = 1 };
+ * degrees before the last in FP32 and the last through the FP64 path (X
+ * must then be F64/C128 storage); OEFE_FILTER_BF16X3 computes the
+ * low-precision cell products on the tensor cores from the BF16x3 storage
+ * (hi*hi + hi*lo + lo*hi, FP32 accumulation). */
+enum { OEFE_FILTER_LAST_FP64 = 1, OEFE_FILTER_BF16X3 = 2 };
 int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, int degree,
                           double a, double b, double a0, int flags);
 
@@ -181,10 +185,30 @@ int oefe_density(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, co
  * respect to conj(X) is H^O X (oefe_apply_h). */
 int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* gV);
 
+/* oefe_occupations -- Fermi-Dirac occupancies f = 1/(1+exp((eps-mu)/kT))
+ * (Eq. fd) with the Fermi level mu fixed by 2 sum_k w_k sum_a f = N_e
+ * (Eq. ne, bisection to |dN| < 1e-12), kT = 3.166811563e-6 * T Ha. Host-only.
+ *   eig  host, sum_k nv[k] eigenvalues (k-major); w host nk weights.
+ *   occ  host out, sum_k nv[k]: 2 w_k f (the density weights of Eq. rho).
+ *   mu, e_band  host out: Fermi level and E_band = 2 sum_k w_k sum_a f eps.
+ * OEFE_ERR_ARG if N_e exceeds twice the number of states. */
+int oefe_occupations(int nk, const int* nv, const double* eig, const double* w, double n_electrons,
+                     double temperature, double* occ, double* mu, double* e_band);
+
 /* oefe_upper_bound -- b >= max eig of (M^O)^{-1} H^O: largest Ritz value of
  * a `steps`-step Lanczos run in the M inner product from v0 (device, n
  * F64/C128) plus the last residual norm. FP64. */
 int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, double* b);
+
+/* ---------------------------------------------------------------- timing
+ * oefe_kernel_timing -- CUDA-event timing of the cell-product kernel (the
+ * dominant launch of every filter degree) on the context's stream, for the
+ * vector dtypes whose bit (1 << OEFE_F64 ...) is set in dtype_mask; 0 turns
+ * timing off, a non-zero mask clears the record. oefe_kernel_time returns the
+ * summed device time (ms) and the launch count recorded so far; it
+ * synchronizes the stream. No counterpart in the paper (instrumentation). */
+int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask);
+int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches);
 
 #ifdef __cplusplus
 }

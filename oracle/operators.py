@@ -55,9 +55,16 @@ def cfe_basis(mesh, quad, e):
 
 
 class Problem:
-    """Everything the method fixes for one geometry and one k-point."""
+    """Everything the method fixes for one geometry and one k-point.
 
-    def __init__(self, mesh, quad, enr, k=(0.0, 0.0, 0.0)):
+    ``cells`` restricts the operator to a block of cells (a bounded sample of
+    a large workload): the cell matrices of those cells are built with the
+    exact orthogonalizing coefficients (tabulating the neighbouring cells as
+    well), vectors hold only the rows those cells touch (CFE rows first, in
+    global order), and M^oo is the enrichment overlap of the tabulated cells.
+    """
+
+    def __init__(self, mesh, quad, enr, k=(0.0, 0.0, 0.0), cells=None):
         self.mesh, self.quad, self.enr = mesh, quad, enr
         self.k = np.asarray(k, float)
         self.complex = bool(np.any(self.k))
@@ -65,14 +72,30 @@ class Problem:
         self.m = mesh.lumped_mass()
         self.actA, self.act = active_sets(mesh, enr)
         self.nh, self.nO = mesh.nh, enr.nO
-        self.n = self.nh + self.nO
+        self.nh_full = mesh.nh
+        if cells is None:
+            self.cells = list(range(mesh.ncells))
+            self.tab_cells = self.cells
+        else:
+            self.cells = sorted(set(int(e) for e in cells))
+            self.tab_cells = sorted({f for e in self.cells for f in mesh.neighbours(e)})
+        self.rows = None
         self._basis()
         self._orthogonalize()
+        if cells is not None:
+            g = np.unique(np.concatenate([self._gindex(e) for e in self.cells]))
+            self.rows = g
+            nh_loc = int(np.sum(g < self.nh_full))
+            sub = g[nh_loc:] - self.nh_full
+            self.m = self.m[g[:nh_loc]]
+            self.Moo = self.Moo[np.ix_(sub, sub)]
+            self.nh, self.nO = nh_loc, len(sub)
+        self.n = self.nh + self.nO
 
     # -- cell-level tabulation -------------------------------------------------
     def _basis(self):
-        self.phiC, self.gradC, self.phiA, self.gradA = [], [], [], []
-        for e in range(self.mesh.ncells):
+        self.phiC, self.gradC, self.phiA, self.gradA = {}, {}, {}, {}
+        for e in self.tab_cells:
             phi, grad = cfe_basis(self.mesh, self.quad, e)
             x, _ = self.quad.cell(e)
             na = len(self.act[e])
@@ -82,16 +105,16 @@ class Problem:
                 v, g = self.enr.values(nu, x, self.k)
                 pa[:, j] = v
                 ga[:, :, j] = g.T
-            self.phiC.append(phi)
-            self.gradC.append(grad)
-            self.phiA.append(pa)
-            self.gradA.append(ga)
+            self.phiC[e] = phi
+            self.gradC[e] = grad
+            self.phiA[e] = pa
+            self.gradA[e] = ga
 
     def _orthogonalize(self):
         """c (Eq. orthCGLL) and M^oo (Eq. Moo)."""
         c = np.zeros((self.nO, self.nh), self.dtype)
         MAA = np.zeros((self.nO, self.nO), self.dtype)
-        for e in range(self.mesh.ncells):
+        for e in self.tab_cells:
             _, w = self.quad.cell(e)
             nodes, act = self.mesh.cell_nodes(e), self.act[e]
             d = self.phiC[e].T @ (w[:, None] * self.phiA[e])          # int N^C_l N^A_nu
@@ -107,9 +130,13 @@ class Problem:
         """Gamma_e = C^T restricted to (nodes(e), act(e)), shape (n_loc, n_a)."""
         return self.c[np.ix_(self.act[e], self.mesh.cell_nodes(e))].T
 
+    def _gindex(self, e):
+        return np.concatenate([self.mesh.cell_nodes(e), self.nh_full + self.act[e]])
+
     def index(self, e):
         """Rows of the OEFE vector touched by cell e: its nodes, then nh + act(e)."""
-        return np.concatenate([self.mesh.cell_nodes(e), self.nh + self.act[e]])
+        g = self._gindex(e)
+        return g if self.rows is None else np.searchsorted(self.rows, g)
 
     # -- cell Hamiltonians -----------------------------------------------------
     def efe_cell(self, e, V_e):
@@ -136,17 +163,17 @@ class Problem:
 
     def build(self, V):
         """Cell matrices H^O_e for all cells from V at every quadrature point."""
-        self.HO = []
-        for e in range(self.mesh.ncells):
+        self.HO = {}
+        for e in self.cells:
             s = slice(self.quad.offset[e], self.quad.offset[e + 1])
-            self.HO.append(self.oefe_cell(e, V[s]))
+            self.HO[e] = self.oefe_cell(e, V[s])
         return self.HO
 
     # -- global operators ------------------------------------------------------
     def apply_H(self, X):
         """Y = H^O X by cell-wise gather / multiply / scatter-add."""
         Y = np.zeros(X.shape, np.result_type(X.dtype, self.dtype))
-        for e in range(self.mesh.ncells):
+        for e in self.cells:
             idx = self.index(e)
             np.add.at(Y, idx, self.HO[e] @ X[idx])
         return Y
@@ -172,7 +199,7 @@ class Problem:
     def assemble_H(self):
         """Sparse global H^O (small meshes only)."""
         rows, cols, vals = [], [], []
-        for e in range(self.mesh.ncells):
+        for e in self.cells:
             idx = self.index(e)
             rows.append(np.repeat(idx, len(idx)))
             cols.append(np.tile(idx, len(idx)))
@@ -200,7 +227,8 @@ class Problem:
     def values_at_points(self, e, X):
         """u(x_q) on cell e for the columns of X (Eq. UOEFE):
         u = N^C (X^c - Gamma_e X^o) + N^A X^o."""
-        nodes, act = self.mesh.cell_nodes(e), self.act[e]
-        Xo = X[self.nh + act]
-        Xt = X[nodes] - self.gamma(e) @ Xo
+        idx = self.index(e)
+        nl = self.mesh.nloc
+        Xo = X[idx[nl:]]
+        Xt = X[idx[:nl]] - self.gamma(e) @ Xo
         return self.phiC[e] @ Xt + self.phiA[e] @ Xo

@@ -106,7 +106,7 @@ def density(problems, Xs, occs):
     pr0 = problems[0]
     rho = np.zeros(pr0.quad.nq)
     for pr, X, occ in zip(problems, Xs, occs):
-        for e in range(pr.mesh.ncells):
+        for e in pr.cells:
             s = slice(pr.quad.offset[e], pr.quad.offset[e + 1])
             U = pr.values_at_points(e, X)
             rho[s] += np.sum(np.abs(U) ** 2 * occ[None, :], axis=1)
@@ -117,7 +117,7 @@ def band_trace_grad_V(pr, X):
     """d tr(X^+ H^O X) / d V_q = w_q sum_v |u_v(x_q)|^2 (H^O is linear in V through
     the (|k|^2/2 + V) N_m^* N_n term of Eq. HOEFEelelements)."""
     g = np.zeros(pr.quad.nq)
-    for e in range(pr.mesh.ncells):
+    for e in pr.cells:
         s = slice(pr.quad.offset[e], pr.quad.offset[e + 1])
         U = pr.values_at_points(e, X)
         g[s] = pr.quad.weights[s] * np.sum(np.abs(U) ** 2, axis=1)

@@ -14,8 +14,8 @@ LIB_PATH = os.path.join(HERE, "liboefe.so")
 OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_CHOLESKY, ERR_NOTPD_MOO, ERR_TIMEOUT, ERR_NUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 F64, F32, C128, C64 = 0, 1, 2, 3
-STORE_F64, STORE_F32 = 1, 2
-FILTER_LAST_FP64 = 1
+STORE_F64, STORE_F32, STORE_BF16X3 = 1, 2, 4
+FILTER_LAST_FP64, FILTER_BF16X3 = 1, 2
 
 # every symbol of include/oefe.h: (name, restype, argtypes)
 _c = ctypes
@@ -50,6 +50,9 @@ SIGNATURES = [
     ("oefe_density", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP, _P]),
     ("oefe_band_trace_grad", _I, [_P, _I, _P, _I, _I, _I, _P]),
     ("oefe_upper_bound", _I, [_P, _I, _P, _I, _DP]),
+    ("oefe_occupations", _I, [_I, _IP, _DP, _DP, _D, _D, _DP, _DP, _DP]),
+    ("oefe_kernel_timing", _I, [_P, _I]),
+    ("oefe_kernel_time", _I, [_P, _DP, _I64P]),
 ]
 
 _lib = None
@@ -100,6 +103,26 @@ def _block(X):
     if X.dim() != 2 or X.stride(1) != 1:
         raise ValueError("need a 2-D tensor with contiguous rows")
     return ctypes.c_void_p(X.data_ptr()), X.shape[1], X.stride(0), _dtype_code(X)
+
+
+def occupations(eigs, w, n_electrons, temperature=500.0):
+    """Fermi level, density weights 2 w_k f and band energy (oefe_occupations)."""
+    lib = load()
+    nv = np.array([len(e) for e in eigs], np.int32)
+    eig = np.ascontiguousarray(np.concatenate([np.asarray(e, np.float64) for e in eigs]))
+    w = np.ascontiguousarray(w, np.float64)
+    occ = np.zeros(len(eig))
+    mu = ctypes.c_double()
+    eb = ctypes.c_double()
+    code = lib.oefe_occupations(len(nv), _ip(nv), _dp(eig), _dp(w), float(n_electrons), float(temperature),
+                                _dp(occ), ctypes.byref(mu), ctypes.byref(eb))
+    if code != OK:
+        raise OefeError(code, "occupations: bad arguments")
+    out, o = [], 0
+    for n in nv:
+        out.append(occ[o:o + n])
+        o += n
+    return mu.value, out, eb.value
 
 
 class Context:
@@ -273,6 +296,18 @@ class Context:
         px, nv, ld, dt = _block(X)
         self._check(self.lib.oefe_band_trace_grad(self.h, int(ik), px, nv, ld, dt, ctypes.c_void_p(gV.data_ptr())))
         return gV
+
+    def kernel_timing(self, dtypes=()):
+        mask = 0
+        for d in dtypes:
+            mask |= 1 << d
+        self._check(self.lib.oefe_kernel_timing(self.h, mask))
+
+    def kernel_time(self):
+        ms = ctypes.c_double()
+        n = ctypes.c_int64()
+        self._check(self.lib.oefe_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def upper_bound(self, ik, v0, steps=20):
         b = ctypes.c_double()

@@ -1,4 +1,6 @@
 // extern "C" entry points of liboefe (declared in include/oefe.h).
+#include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <new>
 
@@ -12,7 +14,7 @@
 
 static void free_all(oefe_ctx* c) {
   for (auto& K : c->kd) {
-    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32);
+    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf);
   }
   c->kd.clear();
   void* ptrs[] = {c->d_gll, c->d_m, c->d_cell_nodes, c->d_cellbox, c->d_pos, c->d_lm, c->d_R, c->d_dR,
@@ -20,6 +22,17 @@ static void free_all(oefe_ctx* c) {
                   c->d_qxyz, c->d_qw, c->d_leaves, c->d_leaf_off, c->d_q_off, c->d_dblk, c->ws, c->ws2,
                   c->d_status};
   for (void* p : ptrs) dev_free(p);
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  c->ev_pool.clear();
+}
+
+cudaEvent_t timing_event(oefe_ctx* c) {
+  if (c->ev_used == c->ev_pool.size()) {
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    c->ev_pool.push_back(e);
+  }
+  return c->ev_pool[c->ev_used++];
 }
 
 extern "C" {
@@ -225,6 +238,72 @@ int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, 
 int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, double* b) {
   CTX_CHECK(ctx);
   return upper_bound(ctx, ik, v0, steps, b);
+}
+
+int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask) {
+  CTX_CHECK(ctx);
+  cudaStreamSynchronize(ctx->stream);
+  ctx->timing = dtype_mask & 15;
+  if (ctx->timing) ctx->ev_used = 0;
+  return OEFE_OK;
+}
+
+int oefe_occupations(int nk, const int* nv, const double* eig, const double* w, double n_electrons,
+                     double temperature, double* occ, double* mu, double* e_band) {
+  if (nk < 1 || !nv || !eig || !w || !occ || !(temperature > 0) || !(n_electrons >= 0)) return OEFE_ERR_ARG;
+  int tot = 0;
+  for (int k = 0; k < nk; ++k) {
+    if (nv[k] < 0) return OEFE_ERR_ARG;
+    tot += nv[k];
+  }
+  if (tot == 0) return OEFE_ERR_ARG;
+  double wsum_states = 0;
+  for (int k = 0, o = 0; k < nk; o += nv[k], ++k) wsum_states += 2.0 * w[k] * nv[k];
+  if (n_electrons > wsum_states) return OEFE_ERR_ARG;
+  const double kT = 3.166811563e-6 * temperature;
+  double lo = eig[0], hi = eig[0];
+  for (int i = 0; i < tot; ++i) { lo = std::min(lo, eig[i]); hi = std::max(hi, eig[i]); }
+  lo -= 1.0;
+  hi += 1.0;
+  auto fermi = [&](double e, double m) { return 0.5 * (1.0 - std::tanh(0.5 * (e - m) / kT)); };
+  auto count = [&](double m) {
+    double s = 0;
+    for (int k = 0, o = 0; k < nk; o += nv[k], ++k)
+      for (int a = 0; a < nv[k]; ++a) s += 2.0 * w[k] * fermi(eig[o + a], m);
+    return s;
+  };
+  double m = 0.5 * (lo + hi);
+  for (int it = 0; it < 400; ++it) {
+    m = 0.5 * (lo + hi);
+    const double n = count(m);
+    if (std::fabs(n - n_electrons) < 1e-12) break;
+    if (n < n_electrons) lo = m; else hi = m;
+  }
+  double eb = 0;
+  for (int k = 0, o = 0; k < nk; o += nv[k], ++k)
+    for (int a = 0; a < nv[k]; ++a) {
+      const double f = fermi(eig[o + a], m);
+      occ[o + a] = 2.0 * w[k] * f;
+      eb += 2.0 * w[k] * f * eig[o + a];
+    }
+  if (mu) *mu = m;
+  if (e_band) *e_band = eb;
+  return OEFE_OK;
+}
+
+int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches) {
+  CTX_CHECK(ctx);
+  if (!ms || !launches) return OEFE_ERR_ARG;
+  OEFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  double total = 0;
+  for (size_t i = 0; i + 1 < ctx->ev_used; i += 2) {
+    float t = 0;
+    OEFE_CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
+    total += t;
+  }
+  *ms = total;
+  *launches = (int64_t)(ctx->ev_used / 2);
+  return OEFE_OK;
 }
 
 }  // extern "C"

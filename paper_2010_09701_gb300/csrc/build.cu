@@ -5,6 +5,8 @@
 //    tensor-product leaf of the cell's point set,
 //  * H^O_e = T_e^+ H_e T_e (Eq. UOEFESplit), stored in FP64 and/or FP32.
 // All arithmetic is FP64 (complex for k != 0).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -416,7 +418,7 @@ __global__ void k_hermitize(S* A, int n) {
 template <typename S, typename S32>
 __global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma, const int* act_off,
                                                   int e0, int nloc, int npad, int ne_max, S* H64,
-                                                  S32* H32) {
+                                                  S32* H32, __nv_bfloat16* Hbf) {
   extern __shared__ double smem[];
   const int b = blockIdx.x, e = e0 + b;
   const int ne = act_off[e + 1] - act_off[e];
@@ -432,6 +434,22 @@ __global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma,
     } else {
       if (H64) reinterpret_cast<double*>(H64)[o] = v.x;
       if (H32) reinterpret_cast<float*>(H32)[o] = (float)v.x;
+    }
+    if (Hbf) {
+      // split each real plane: hi = bf16(x), lo = bf16(x - hi), from the FP32 value
+      constexpr int PL = sizeof(S) == sizeof(cd) ? 4 : 2;
+      const size_t pl = (size_t)npad * npad;
+      const size_t base = (size_t)e * PL * pl + (size_t)r * npad + c;
+      const float xr = (float)v.x;
+      const __nv_bfloat16 rh = __float2bfloat16_rn(xr);
+      Hbf[base] = rh;
+      Hbf[base + pl] = __float2bfloat16_rn(xr - __bfloat162float(rh));
+      if (PL == 4) {
+        const float xi = (float)v.y;
+        const __nv_bfloat16 ih = __float2bfloat16_rn(xi);
+        Hbf[base + 2 * pl] = ih;
+        Hbf[base + 3 * pl] = __float2bfloat16_rn(xi - __bfloat162float(ih));
+      }
     }
   };
   // CC block and zero padding
@@ -588,12 +606,13 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
       const size_t tsmem = (size_t)c->nloc * 4 * sizeof(cd);
       float* H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
       double* H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
+      __nv_bfloat16* Hbf = (store & OEFE_STORE_BF16X3) ? (__nv_bfloat16*)K.Hbf : nullptr;
       if (K.cplx)
         k_transform<cd, cf><<<nb, BT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                         c->ne_max, (cd*)H64, (cf*)H32);
+                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf);
       else
         k_transform<double, float><<<nb, BT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                                c->ne_max, H64, H32);
+                                                                c->ne_max, H64, H32, Hbf);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -675,7 +694,7 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
 
 int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
   if (!c->has_k) { c->err = "build_hamiltonian: call oefe_kpoints first"; return OEFE_ERR_STATE; }
-  if (!veff || !(store & (OEFE_STORE_F64 | OEFE_STORE_F32))) {
+  if (!veff || !(store & (OEFE_STORE_F64 | OEFE_STORE_F32 | OEFE_STORE_BF16X3))) {
     c->err = "build_hamiltonian: need veff and a storage flag";
     return OEFE_ERR_ARG;
   }
@@ -685,12 +704,15 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
   for (auto& K : c->kd) {
     const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);
     const size_t n = (size_t)c->ncells * c->npad * c->npad;
-    dev_free(K.H64);
-    dev_free(K.H32);
-    K.H64 = nullptr;
-    K.H32 = nullptr;
-    if (store & OEFE_STORE_F64) st = dev_alloc(c, (void**)&K.H64, n * sb);
-    if (st == OEFE_OK && (store & OEFE_STORE_F32)) st = dev_alloc(c, (void**)&K.H32, n * sb / 2);
+    // keep existing buffers when the requested storage is unchanged
+    auto keep = [&](void** p, bool want, size_t bytes) -> int {
+      if (!want) { dev_free(*p); *p = nullptr; return OEFE_OK; }
+      if (*p) return OEFE_OK;
+      return dev_alloc(c, p, bytes);
+    };
+    st = keep((void**)&K.H64, store & OEFE_STORE_F64, n * sb);
+    if (st == OEFE_OK) st = keep((void**)&K.H32, store & OEFE_STORE_F32, n * sb / 2);
+    if (st == OEFE_OK) st = keep(&K.Hbf, store & OEFE_STORE_BF16X3, n * sb / 2);
     if (st == OEFE_OK) st = run_cell_kernel(c, K, 0, veff, d_gw, nullptr, nullptr, store);
     if (st != OEFE_OK) break;
     K.built = true;

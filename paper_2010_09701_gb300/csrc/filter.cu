@@ -177,22 +177,48 @@ __global__ void k_enr_update(const cd* __restrict__ Yo, const void* __restrict__
   else Y[row * ldy + v] = (T)y.x;
 }
 
+// Y (ldy) <- X (ldx) with a precision change; n rows of nv scalars (reals counted by `width`).
+template <typename A, typename B>
+__global__ void k_convert(const A* __restrict__ X, int ldx, B* __restrict__ Y, int ldy, int64_t n, int width) {
+  const int64_t total = n * width;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / width;
+    const int c = (int)(t % width);
+    Y[r * ldy + c] = (B)X[r * ldx + c];
+  }
+}
+
+template <typename A, typename B>
+int convert(oefe_ctx* c, const void* X, int ldx, void* Y, int ldy, int64_t n, int width) {
+  const int64_t tot = n * width;
+  const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
+  k_convert<A, B><<<blocks, 256, 0, c->stream>>>((const A*)X, ldx, (B*)Y, ldy, n, width);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}
+
 struct Step {
   int mode;  // 0 H X, 1 M^-1 H X, 2 recurrence
   double alpha, cshift, beta;
 };
 
 template <typename T, bool C>
-int launch_step(oefe_ctx* c, const KData& K, const void* Hm, const void* Xin, int ldin, int nv, const Step& st,
-                const void* Xk, int ldk, const void* Xm1, int ldm1, void* Y, int ldy, void* Zbuf, cd* Yo) {
+int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const void* Xin, int ldin, int nv, const Step& st,
+                const void* Xk, int ldk, const void* Xm1, int ldm1, void* Y, int ldy, void* Zbuf, cd* Yo, bool mma) {
   using S = typename Sc<T, C>::type;
-  dim3 grid(c->ncells, (nv + NB - 1) / NB);
-  const size_t smem = (size_t)c->npad * NB * sizeof(S);
-  if (smem > 227 * 1024) { c->err = "cell matrices too large for the shared-memory gather"; return OEFE_ERR_ARG; }
-  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_cell_apply<T, C><<<grid, CWARPS * 32, smem, c->stream>>>((const S*)Hm, (const S*)Xin, ldin, nv, c->d_cell_nodes,
-                                                             c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh,
-                                                             (S*)Zbuf);
+  if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
+  if (mma) {
+    OEFE_TRY(launch_cell_mma(c, K, Xin, ldin, nv, C, Zbuf));
+  } else {
+    dim3 grid(c->ncells, (nv + NB - 1) / NB);
+    const size_t smem = (size_t)c->npad * NB * sizeof(S);
+    if (smem > 227 * 1024) { c->err = "cell matrices too large for the shared-memory gather"; return OEFE_ERR_ARG; }
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_cell_apply<T, C><<<grid, CWARPS * 32, smem, c->stream>>>((const S*)Hm, (const S*)Xin, ldin, nv, c->d_cell_nodes,
+                                                               c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh,
+                                                               (S*)Zbuf);
+  }
+  if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
   const int64_t tot = c->nh * nv;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
   k_node_update<T, C><<<blocks, 256, 0, c->stream>>>((const S*)Zbuf, c->d_node_off, c->d_node_slot, c->d_m, c->nh,
@@ -209,18 +235,19 @@ int launch_step(oefe_ctx* c, const KData& K, const void* Hm, const void* Xin, in
 }
 
 int dispatch_step(oefe_ctx* c, const KData& K, int dtype, const void* Xin, int ldin, int nv, const Step& st,
-                  const void* Xk, int ldk, const void* Xm1, int ldm1, void* Y, int ldy, void* Zbuf, cd* Yo) {
+                  const void* Xk, int ldk, const void* Xm1, int ldm1, void* Y, int ldy, void* Zbuf, cd* Yo,
+                  bool mma = false) {
   switch (dtype) {
-    case OEFE_F64: return launch_step<double, false>(c, K, K.H64, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo);
-    case OEFE_C128: return launch_step<double, true>(c, K, K.H64, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo);
-    case OEFE_F32: return launch_step<float, false>(c, K, K.H32, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo);
-    case OEFE_C64: return launch_step<float, true>(c, K, K.H32, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo);
+    case OEFE_F64: return launch_step<double, false>(c, K, dtype, K.H64, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo, false);
+    case OEFE_C128: return launch_step<double, true>(c, K, dtype, K.H64, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo, false);
+    case OEFE_F32: return launch_step<float, false>(c, K, dtype, K.H32, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo, mma);
+    case OEFE_C64: return launch_step<float, true>(c, K, dtype, K.H32, Xin, ldin, nv, st, Xk, ldk, Xm1, ldm1, Y, ldy, Zbuf, Yo, mma);
   }
   c->err = "unknown dtype";
   return OEFE_ERR_ARG;
 }
 
-int check_apply_args(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
+int check_apply_args(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, bool mma = false) {
   if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
   if (ik < 0 || ik >= (int)c->kd.size()) { c->err = "k index out of range"; return OEFE_ERR_ARG; }
   if (!X || nv < 1 || ld < nv || nv > 8192) { c->err = "need X, 1 <= nv <= ld, nv <= 8192"; return OEFE_ERR_ARG; }
@@ -231,7 +258,8 @@ int check_apply_args(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dty
     return OEFE_ERR_ARG;
   }
   if (dtype_fp64(dtype) && !K.H64) { c->err = "FP64 cell matrices were not stored"; return OEFE_ERR_STATE; }
-  if (!dtype_fp64(dtype) && !K.H32) { c->err = "FP32 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  if (!dtype_fp64(dtype) && !mma && !K.H32) { c->err = "FP32 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  if (mma && !K.Hbf) { c->err = "BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
   return OEFE_OK;
 }
 
@@ -255,54 +283,106 @@ int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dt
   return apply_op2(c, ik, X, ld, Y, ld, nv, dtype, minv);
 }
 
+namespace {
+
+// Degrees [j0, j1] of the scaled recurrence on buffers of one dtype. bufs[ip]
+// holds Y_{j0-2} (ignored when j0 == 1), bufs[ic] Y_{j0-1}; on return *ip and
+// *ic point at Y_{j1-1} and Y_{j1}.
+int run_degrees(oefe_ctx* c, const KData& K, int dtype, void* bufs[3], int lds[3], int* ip, int* ic, int nv,
+                int j0, int j1, double e, double cc, double* sigma, double sigma1, void* Zb, cd* Yo, bool mma) {
+  const double gamma = 2.0 / sigma1;
+  for (int j = j0; j <= j1; ++j) {
+    Step st;
+    if (j == 1) {
+      st = Step{2, sigma1 / e, cc, 0.0};
+    } else {
+      const double sigma2 = 1.0 / (gamma - *sigma);
+      st = Step{2, 2.0 * sigma2 / e, cc, -(*sigma) * sigma2};
+      *sigma = sigma2;
+    }
+    const int in = 3 - *ip - *ic;
+    OEFE_TRY(dispatch_step(c, K, dtype, bufs[*ic], lds[*ic], nv, st, bufs[*ic], lds[*ic], j == 1 ? nullptr : bufs[*ip],
+                           lds[*ip], bufs[in], lds[in], Zb, Yo, mma));
+    *ip = *ic;
+    *ic = in;
+  }
+  return OEFE_OK;
+}
+
+size_t align256(size_t b) { return ((b + 255) / 256) * 256; }
+
+}  // namespace
+
 int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int degree, double a, double b,
                 double a0, int flags) {
-  OEFE_TRY(check_apply_args(c, ik, X, nv, ld, dtype));
+  const bool mma = (flags & OEFE_FILTER_BF16X3) != 0;
+  const bool mixed = (flags & OEFE_FILTER_LAST_FP64) != 0;
+  OEFE_TRY(check_apply_args(c, ik, X, nv, ld, dtype, mma && !mixed));
   if (degree < 1 || !(b > a) || !(a0 < a)) { c->err = "filter: need degree >= 1, a0 < a < b"; return OEFE_ERR_ARG; }
-  if ((flags & OEFE_FILTER_LAST_FP64) && !dtype_fp64(dtype)) {
+  if (mma && !c->kd[ik].Hbf) { c->err = "filter: BF16X3 needs the BF16x3 cell matrices"; return OEFE_ERR_STATE; }
+  if (mixed && !dtype_fp64(dtype)) {
     c->err = "filter: LAST_FP64 needs F64/C128 storage";
     return OEFE_ERR_ARG;
   }
-  const size_t es = dtype_bytes(dtype);
+  const KData& K = c->kd[ik];
+  if (mixed && !mma && !K.H32) { c->err = "filter: LAST_FP64 needs the FP32 cell matrices"; return OEFE_ERR_STATE; }
   const int64_t n = c->nh + c->nO;
-  const size_t zbytes = (((size_t)c->ncells * c->npad * nv * es + 255) / 256) * 256;
-  const size_t yobytes = (((size_t)std::max(c->nO, 1) * nv * sizeof(cd) + 255) / 256) * 256;
-  const size_t vbytes = (((size_t)n * nv * es + 255) / 256) * 256;
-  OEFE_TRY(ensure_ws(c, zbytes + yobytes + 2 * vbytes));
+  const int dt32 = dtype == OEFE_C128 ? OEFE_C64 : OEFE_F32;
+  const int width = dtype_complex(dtype) ? 2 * nv : nv;  // reals per row
+  const size_t es = dtype_bytes(dtype);
+  const size_t es_low = mixed ? dtype_bytes(dt32) : es;
+  const size_t zbytes = align256((size_t)c->ncells * c->npad * nv * std::max(es, es_low));
+  const size_t yobytes = align256((size_t)std::max(c->nO, 1) * nv * sizeof(cd));
+  const size_t vbytes = align256((size_t)n * nv * es);
+  const size_t vbytes_low = align256((size_t)n * nv * es_low);
+  OEFE_TRY(ensure_ws(c, zbytes + yobytes + 2 * vbytes + (mixed ? 3 * vbytes_low : 0)));
   char* base = (char*)c->ws;
   void* Zb = base;
   cd* Yo = (cd*)(base + zbytes);
   void* B1 = base + zbytes + yobytes;
   void* B2 = base + zbytes + yobytes + vbytes;
-  const KData& K = c->kd[ik];
-  // scaled Chebyshev recurrence
   const double e = (b - a) / 2.0, cc = (b + a) / 2.0;
-  double sigma = e / (a0 - cc);
-  const double sigma1 = sigma, gamma = 2.0 / sigma1;
-  // buffers: Xm1 (previous), Xk (current), Xn (next); X itself holds the input
+  const double sigma1 = e / (a0 - cc);
+  double sigma = sigma1;
   void* bufs[3] = {X, B1, B2};
   int lds[3] = {ld, nv, nv};
-  int ip = 0, ic = 0, in = 1;  // first step: Xk = X, no Xm1
-  Step st{2, sigma1 / e, cc, 0.0};
-  OEFE_TRY(dispatch_step(c, K, dtype, bufs[ic], lds[ic], nv, st, bufs[ic], lds[ic], nullptr, 0, bufs[in], lds[in], Zb, Yo));
-  ip = ic;
-  ic = in;
-  for (int j = 2; j <= degree; ++j) {
-    const double sigma2 = 1.0 / (gamma - sigma);
-    Step s2{2, 2.0 * sigma2 / e, cc, -sigma * sigma2};
-    in = 3 - ip - ic;  // the buffer that is neither previous nor current
-    if (j == 2) in = 2;
-    OEFE_TRY(dispatch_step(c, K, dtype, bufs[ic], lds[ic], nv, s2, bufs[ic], lds[ic], bufs[ip], lds[ip], bufs[in],
-                           lds[in], Zb, Yo));
-    ip = ic;
-    ic = in;
-    sigma = sigma2;
+  int ip = 1, ic = 0;
+  if (!mixed || degree == 1) {
+    OEFE_TRY(run_degrees(c, K, dtype, bufs, lds, &ip, &ic, nv, 1, degree, e, cc, &sigma, sigma1, Zb, Yo,
+                         mma && !dtype_fp64(dtype)));
+  } else {
+    // degrees 1 .. m-1 in FP32 on private buffers, the last degree in FP64
+    char* lowb = base + zbytes + yobytes + 2 * vbytes;
+    void* L[3] = {lowb, lowb + vbytes_low, lowb + 2 * vbytes_low};
+    int ldl[3] = {nv, nv, nv};
+    if (dtype == OEFE_C128 || dtype == OEFE_F64) OEFE_TRY((convert<double, float>(c, X, ld * (dtype == OEFE_C128 ? 2 : 1), L[0], width, n, width)));
+    int lp = 1, lc = 0;
+    OEFE_TRY(run_degrees(c, K, dt32, L, ldl, &lp, &lc, nv, 1, degree - 1, e, cc, &sigma, sigma1, Zb, Yo, mma));
+    // Y_{m-1} -> B1 (FP64); Y_{m-2} -> B2 (FP64), or X itself when m == 2
+    OEFE_TRY((convert<float, double>(c, L[lc], width, B1, width, n, width)));
+    int fp = 0;
+    if (degree > 2) {
+      OEFE_TRY((convert<float, double>(c, L[lp], width, B2, width, n, width)));
+      fp = 2;
+    }
+    // last degree: inputs B1 (current) and bufs[fp] (previous), output X (or B2 when fp == 0)
+    ip = fp;
+    ic = 1;
+    OEFE_TRY(run_degrees(c, K, dtype, bufs, lds, &ip, &ic, nv, degree, degree, e, cc, &sigma, sigma1, Zb, Yo, false));
   }
-  // result is in bufs[ic]; copy back into X if needed
   if (ic != 0) {
     OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(X, (size_t)ld * es, bufs[ic], (size_t)lds[ic] * es, (size_t)nv * es, (size_t)n,
                                        cudaMemcpyDeviceToDevice, c->stream));
   }
   OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (mma) {
+    int flag = 0;
+    OEFE_CUDA_TRY(c, cudaMemcpy(&flag, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+      cudaMemset(c->d_status, 0, sizeof(int));
+      c->err = "filter: a tensor-core pipeline wait timed out";
+      return OEFE_ERR_TIMEOUT;
+    }
+  }
   return OEFE_OK;
 }

@@ -63,6 +63,7 @@ struct KData {
   double* Mooinv = nullptr;  // nO x nO scalars (FP64)
   double* H64 = nullptr;     // (ncells, npad, npad) scalars
   float* H32 = nullptr;      // (ncells, npad, npad) float or cf
+  void* Hbf = nullptr;       // (ncells, planes, npad, npad) bf16: (re hi, re lo[, im hi, im lo])
   bool built = false;
 };
 
@@ -139,7 +140,15 @@ struct oefe_ctx {
   void* ws2 = nullptr;
   size_t ws2_bytes = 0;
   int* d_status = nullptr;        // device status word (Cholesky failures, timeouts)
+
+  // optional event timing of the cell-product launches
+  int timing = 0;  // dtype bit mask
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
 };
+
+// record an event pair around a launch when timing is on
+cudaEvent_t timing_event(oefe_ctx* c);
 
 // ------------------------------------------------------------------ internals
 int ensure_ws(oefe_ctx* c, size_t bytes);
@@ -169,6 +178,10 @@ int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dt
 int apply_op2(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv);
 int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int degree, double a,
                 double b, double a0, int flags);
+
+// tensor-core cell products (cell_mma.cu)
+int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z);
+size_t cell_mma_smem(bool cplx);
 
 // subspace (linalg.cu)
 int orthonormalize(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* cond);

@@ -332,7 +332,7 @@ int setup_enrichment(oefe_ctx* c, int natoms, const double* pos, int nfun, const
     c->act_off[e + 1] = (int)c->act_idx.size();
     c->ne_max = std::max(c->ne_max, c->act_off[e + 1] - c->act_off[e]);
   }
-  c->npad = ((c->nloc + c->ne_max + 31) / 32) * 32;
+  c->npad = ((c->nloc + c->ne_max + 127) / 128) * 128;
   OEFE_TRY(upload(c, &c->d_act_off, c->act_off));
   OEFE_TRY(upload(c, &c->d_act_idx, c->act_idx));
 

@@ -25,7 +25,7 @@ def paired(a=6.0, n=2, p=3, Zs=(3, 4), ks=((0.0, 0.0, 0.0),), quad=(4, 5, 2), r0
            xb=None, pos=None, enrich=True, store=None):
     """Oracle problems (one per k) and a library context built from the same inputs and V."""
     import torch
-    from paper_2010_09701_gb300 import STORE_F32, STORE_F64
+    from paper_2010_09701_gb300 import STORE_BF16X3, STORE_F32, STORE_F64
     if pos is None:
         pos = np.array([[0.0, 0.0, 0.0], [a / 2, a / 2, a / 2]])[:len(Zs)]
     pos = np.asarray(pos, float)
@@ -37,7 +37,7 @@ def paired(a=6.0, n=2, p=3, Zs=(3, 4), ks=((0.0, 0.0, 0.0),), quad=(4, 5, 2), r0
         pr.build(V)
     ctx = lib_context(a, xb, p, pos, Z, ks, quad, r0, rc, enrich=enrich)
     Vd = torch.tensor(V, dtype=torch.float64, device="cuda")
-    ctx.build_hamiltonian(Vd, store if store is not None else (STORE_F64 | STORE_F32))
+    ctx.build_hamiltonian(Vd, store if store is not None else (STORE_F64 | STORE_F32 | STORE_BF16X3))
     return prs, ctx, V, Vd
 
 

@@ -55,3 +55,23 @@ def test_no_oracle_import_in_product_code():
             if f.endswith((".py", ".cu", ".cpp", ".h", ".cuh")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).lower().replace("oracle-free", ""), f
+
+
+def test_occupations_host_call_matches_oracle():
+    # oefe_occupations is host-only: it runs here without a GPU
+    import numpy as np
+    import paper_2010_09701_gb300 as P
+    from oracle import solver
+    rng = np.random.default_rng(4)
+    eigs = [np.sort(rng.uniform(-5, 2, 12)), np.sort(rng.uniform(-5, 2, 9))]
+    w = [0.25, 0.75]
+    for Ne in (3.0, 7.5, 12.0):
+        mu, occ, eb = P.occupations(eigs, w, Ne, 500.0)
+        mu_o = solver.fermi_level(eigs, w, Ne, 500.0)
+        occ_o = solver.occupations(eigs, w, mu_o)
+        assert abs(sum(o.sum() for o in occ) - Ne) < 1e-10
+        for a, b in zip(occ, occ_o):
+            assert np.allclose(a, b, atol=1e-9)
+        assert abs(eb - solver.band_energy(eigs, w, mu_o)) < 1e-8
+    with pytest.raises(P.OefeError):
+        P.occupations(eigs, w, 100.0)

@@ -141,3 +141,21 @@ def test_argument_errors():
     with pytest.raises(OefeError) as e:
         c2.quadrature(3, 3, 1)
     assert e.value.code == binding.ERR_STATE
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("deg", [2, 3, 9])
+def test_filter_mixed_last_fp64(k, deg):
+    from paper_2010_09701_gb300 import FILTER_LAST_FP64
+    prs, ctx, V, _ = paired(ks=[k])
+    pr = prs[0]
+    a, b, a0 = bounds(pr)
+    X = W.random_vectors(pr.n, 21, complex_=pr.complex, seed=deg)
+    ref = solver.chebyshev_filter(pr.apply_A, X, deg, a, b, a0)
+    Xd = to_gpu(X)
+    ctx.chebyshev_filter(0, Xd, deg, a, b, a0, flags=FILTER_LAST_FP64)
+    out = Xd.cpu().numpy()
+    nrm = np.linalg.norm(ref, axis=0)
+    err = np.max(np.linalg.norm(out - ref, axis=0) / nrm)
+    assert err < 2e-5
+    assert err > 1e-13          # the FP32 degrees did run

@@ -1,0 +1,86 @@
+"""Parity of the tensor-core (tcgen05, BF16x3) cell products against the
+oracle: single degrees (the bare product), full filters, complex and real,
+one to four M tiles of 128 rows and ragged vector blocks."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from gpu_cases import c1_pair, paired, to_gpu
+from oracle import solver
+
+pytestmark = pytest.mark.gpu
+
+KS = [(0.0, 0.0, 0.0), (0.25, -0.4, 0.1)]
+# BF16x3: each cell product carries ~3 * 2^-17 relative error per term
+TOL_DEGREE1 = 3e-5
+TOL_FILTER = 2e-4
+
+
+def colerr(out, ref):
+    return np.max(np.linalg.norm(out - ref, axis=0) / np.linalg.norm(ref, axis=0))
+
+
+def bounds(pr):
+    import scipy.linalg as sla
+    ev = sla.eigh(pr.assemble_H().toarray(), pr.dense_M(), eigvals_only=True)
+    return ev[6], ev[-1] * 1.01, ev[0] - 1.0
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("nv", [5, 64, 70])
+def test_tensor_single_degree(k, nv):
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    prs, ctx, V, _ = paired(ks=[k])
+    pr = prs[0]
+    a, b, a0 = bounds(pr)
+    X = W.random_vectors(pr.n, nv, complex_=pr.complex, seed=nv)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 1, a, b, a0)
+    Xd = to_gpu(X, torch.complex64 if pr.complex else torch.float32)
+    ctx.chebyshev_filter(0, Xd, 1, a, b, a0, flags=FILTER_BF16X3)
+    out = Xd.cpu().numpy().astype(ref.dtype)
+    err = colerr(out, ref)
+    assert err < TOL_DEGREE1
+    assert err > 1e-9          # the split products did run (not an FP64 path)
+
+
+@pytest.mark.parametrize("k", KS)
+def test_tensor_filter_last_fp64(k):
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64
+    prs, ctx, V, _ = paired(ks=[k])
+    pr = prs[0]
+    a, b, a0 = bounds(pr)
+    X = W.random_vectors(pr.n, 24, complex_=pr.complex, seed=2)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 9, a, b, a0)
+    Xd = to_gpu(X)
+    ctx.chebyshev_filter(0, Xd, 9, a, b, a0, flags=FILTER_LAST_FP64 | FILTER_BF16X3)
+    assert colerr(Xd.cpu().numpy(), ref) < TOL_FILTER
+
+
+def test_tensor_c1_two_m_tiles():
+    # graded 8^3 mesh, p = 4: n_aug up to 135 -> two 128-row M tiles, four K tiles
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    w = W.config_c1()
+    prs, ctx, V, _ = c1_pair()
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 20, seed=w.seed)
+    a, b, a0 = 0.0, 600.0, -99.0
+    ref = solver.chebyshev_filter(pr.apply_A, X, 3, a, b, a0)
+    Xd = to_gpu(X, torch.float32)
+    ctx.chebyshev_filter(0, Xd, 3, a, b, a0, flags=FILTER_BF16X3)
+    assert colerr(Xd.cpu().numpy().astype(np.float64), ref) < TOL_FILTER
+
+
+def test_tensor_four_m_tiles():
+    # p = 6 with enrichment: n_aug > 384 -> npad = 512 (four M tiles)
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    pos = np.random.default_rng(5).uniform(0.0, 7.0, (9, 3))
+    prs, ctx, V, _ = paired(a=7.0, n=2, p=6, Zs=(3,) * 9, pos=pos, quad=(7, 7, 1), r0=2.0, rc=3.0,
+                            ks=[(0.2, 0.1, -0.3)])
+    pr = prs[0]
+    assert max(ctx.cell_info(e).size for e in range(8)) > 384
+    X = W.random_vectors(pr.n, 16, complex_=True, seed=3)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 1, 0.0, 500.0, -50.0)
+    Xd = to_gpu(X, torch.complex64)
+    ctx.chebyshev_filter(0, Xd, 1, 0.0, 500.0, -50.0, flags=FILTER_BF16X3)
+    assert colerr(Xd.cpu().numpy().astype(np.complex128), ref) < TOL_DEGREE1
