@@ -121,6 +121,8 @@ def run_ours(args, rank, world):
     nk = ctx.nk
     xyz, qw = ctx.quadrature_points()
     V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
+    store = P.STORE_F64 | (P.STORE_BF16X3 if args.tensor else P.STORE_F32)
+    ctx.build_hamiltonian(V, store)
     naug = np.array([len(ctx.cell_info(e)) for e in range(int(np.prod([w.ncell] * 3)))])
     nvs = w.nv
     deg = w.degree
@@ -140,9 +142,7 @@ def run_ours(args, rank, world):
 
     filt_events = []
     phase_ms = {}
-    store = P.STORE_F64 | (P.STORE_BF16X3 if args.tensor else P.STORE_F32)
     fflags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
-    ctx.build_hamiltonian(V, store)
 
     def mark():
         ev = torch.cuda.Event(enable_timing=True)
