@@ -143,6 +143,12 @@ def run_ours(args, rank, world):
     filt_events = []
     phase_ms = {}
     fflags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
+    if args.filter_only:
+        X32 = X0[0].to(torch.complex64)
+        for _ in range(args.steps):
+            ctx.chebyshev_filter(0, X32, deg, a_lo, bks[0], a0, flags=P.FILTER_BF16X3 if args.tensor else 0)
+        torch.cuda.synchronize()
+        return {"filter_only": True, "passes": args.steps, "config": w.name}
 
     def mark():
         ev = torch.cuda.Event(enable_timing=True)
@@ -371,7 +377,9 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3", choices=["c2", "c3"])
+    ap.add_argument("--config", default="c3", choices=["c2", "c3", "c3small"])
+    ap.add_argument("--filter-only", action="store_true",
+                    help="profiling aid: set up, then run --steps low-precision filter passes on k-point 0 only")
     ap.add_argument("--sample-cells", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--skip-fp64", action="store_true")

@@ -1,0 +1,277 @@
+// Dense FP64 generalized Hermitian eigensolver for the projected problem of
+// Rayleigh-Ritz (Eq. ProjKS), H^Q u = eps M^Q u, entirely on the GPU:
+//   M^Q = L L^+ (Cholesky), C = L^{-1} H^Q L^{-+}, C = W diag(eps) W^+ by a
+//   parallel cyclic Jacobi method (circle ordering: n/2 disjoint rotations per
+//   round, n-1 rounds per sweep), U = L^{-+} W, eigenvalues ascending.
+#include <algorithm>
+#include <cmath>
+
+#include "oefe_internal.h"
+
+namespace {
+
+constexpr int JT = 1024;
+constexpr int MAXPAIRS = 512;   // n <= 1024
+
+__device__ inline double block_sum(double v, double* red) {
+  const int tid = threadIdx.x;
+  red[tid] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (tid < w) red[tid] += red[tid + w];
+    __syncthreads();
+  }
+  const double s = red[0];
+  __syncthreads();
+  return s;
+}
+
+// C = op(A) op(B), n x n complex; op = conjugate transpose when the flag is set
+__global__ void k_small_gemm(const cd* A, bool ca, const cd* B, bool cb, cd* C, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  cd s = mkc(0, 0);
+  for (int k = 0; k < n; ++k) {
+    const cd a = ca ? cconj(A[(size_t)k * n + i]) : A[(size_t)i * n + k];
+    const cd b = cb ? cconj(B[(size_t)j * n + k]) : B[(size_t)k * n + j];
+    s += a * b;
+  }
+  C[t] = s;
+}
+
+__global__ void k_hermitian_part(cd* A, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * n) return;
+  const int i = t / n, j = t % n;
+  if (i > j) return;
+  const cd v = 0.5 * (A[(size_t)i * n + j] + cconj(A[(size_t)j * n + i]));
+  A[(size_t)i * n + j] = v;
+  A[(size_t)j * n + i] = cconj(v);
+}
+
+// Jacobi sweeps on A (n x n Hermitian, overwritten by its diagonal form), V <- eigenvectors.
+__global__ void __launch_bounds__(JT) k_jacobi(cd* A, cd* V, int n, int max_sweeps, double tol, int* sweeps_out) {
+  __shared__ double red[JT];
+  __shared__ double cs_[MAXPAIRS], sn_[MAXPAIRS];
+  __shared__ cd u_[MAXPAIRS];
+  __shared__ int p_[MAXPAIRS], q_[MAXPAIRS];
+  const int tid = threadIdx.x;
+  const int m = n + (n & 1);  // even number of players; player n is a bye when n is odd
+  const int np = m / 2;
+  for (int t = tid; t < n * n; t += JT) V[t] = (t / n == t % n) ? mkc(1, 0) : mkc(0, 0);
+  double fro = 0;
+  for (int t = tid; t < n * n; t += JT) fro += cabs2(A[t]);
+  fro = block_sum(fro, red);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double off = 0;
+    for (int t = tid; t < n * n; t += JT)
+      if (t / n != t % n) off += cabs2(A[t]);
+    off = block_sum(off, red);
+    if (off <= tol * tol * fro || off == 0.0) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = tid; k < np; k += JT) {
+        // circle method: position 0 holds player m-1, position i holds (i - 1 + r) mod (m - 1)
+        const int a = k == 0 ? m - 1 : (k - 1 + r) % (m - 1);
+        const int b = (m - 1 - k - 1 + r) % (m - 1);
+        int p = min(a, b), q = max(a, b);
+        if (q >= n) { p_[k] = -1; continue; }
+        const cd bpq = A[(size_t)p * n + q];
+        const double beta = sqrt(cabs2(bpq));
+        if (beta < 1e-300) { p_[k] = -1; continue; }
+        const cd u = (1.0 / beta) * bpq;
+        const double tau = (A[(size_t)q * n + q].x - A[(size_t)p * n + p].x) / (2.0 * beta);
+        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + tt * tt);
+        p_[k] = p;
+        q_[k] = q;
+        cs_[k] = c;
+        sn_[k] = tt * c;
+        u_[k] = u;
+      }
+      __syncthreads();
+      // rows: A <- G^+ A for every pair (disjoint rows)
+      for (int t = tid; t < np * n; t += JT) {
+        const int k = t / n, j = t % n;
+        const int p = p_[k];
+        if (p < 0) continue;
+        const int q = q_[k];
+        const double c = cs_[k], s = sn_[k];
+        const cd ub = cconj(u_[k]);
+        // G = [[c, s], [-conj(u) s, conj(u) c]]
+        const cd g10 = -s * ub, g11 = c * ub;
+        const cd apj = A[(size_t)p * n + j], aqj = A[(size_t)q * n + j];
+        A[(size_t)p * n + j] = c * apj + cmulc(g10, aqj);
+        A[(size_t)q * n + j] = s * apj + cmulc(g11, aqj);
+      }
+      __syncthreads();
+      // columns: A <- A G, V <- V G
+      for (int t = tid; t < np * n; t += JT) {
+        const int k = t / n, i = t % n;
+        const int p = p_[k];
+        if (p < 0) continue;
+        const int q = q_[k];
+        const double c = cs_[k], s = sn_[k];
+        const cd ub = cconj(u_[k]);
+        const cd g10 = -s * ub, g11 = c * ub;
+        const cd aip = A[(size_t)i * n + p], aiq = A[(size_t)i * n + q];
+        A[(size_t)i * n + p] = c * aip + aiq * g10;
+        A[(size_t)i * n + q] = s * aip + aiq * g11;
+        const cd vip = V[(size_t)i * n + p], viq = V[(size_t)i * n + q];
+        V[(size_t)i * n + p] = c * vip + viq * g10;
+        V[(size_t)i * n + q] = s * vip + viq * g11;
+      }
+      __syncthreads();
+      for (int k = tid; k < np; k += JT) {
+        const int p = p_[k];
+        if (p < 0) continue;
+        A[(size_t)p * n + q_[k]] = mkc(0, 0);
+        A[(size_t)q_[k] * n + p] = mkc(0, 0);
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) *sweeps_out = sweep;
+}
+
+// ascending order: rank of each diagonal entry (ties by index), then permute
+__global__ void k_sort_eig(const cd* A, const cd* W, int n, double* eps, cd* Wsorted) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double wi = A[(size_t)i * n + i].x;
+  int rank = 0;
+  for (int j = 0; j < n; ++j) {
+    const double wj = A[(size_t)j * n + j].x;
+    if (wj < wi || (wj == wi && j < i)) ++rank;
+  }
+  eps[rank] = wi;
+  for (int r = 0; r < n; ++r) Wsorted[(size_t)r * n + rank] = W[(size_t)r * n + i];
+}
+
+template <typename S>
+__global__ void k_to_cd(const S* A, cd* B, int n2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n2) return;
+  if constexpr (sizeof(S) == sizeof(cd)) B[t] = reinterpret_cast<const cd*>(A)[t];
+  else B[t] = mkc(reinterpret_cast<const double*>(A)[t], 0.0);
+}
+
+template <typename S>
+__global__ void k_from_cd(const cd* B, S* A, int n2) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n2) return;
+  if constexpr (sizeof(S) == sizeof(cd)) reinterpret_cast<cd*>(A)[t] = B[t];
+  else reinterpret_cast<double*>(A)[t] = B[t].x;
+}
+
+// lower Cholesky (single CTA), info = failing pivot + 1
+__global__ void __launch_bounds__(1024) k_chol_cd(cd* A, int n, int* info) {
+  __shared__ double piv;
+  __shared__ int fail;
+  if (threadIdx.x == 0) fail = 0;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = A[(size_t)j * n + j].x;
+      if (!(d > 0.0) || !isfinite(d)) fail = j + 1;
+      else {
+        piv = sqrt(d);
+        A[(size_t)j * n + j] = mkc(piv, 0.0);
+      }
+    }
+    __syncthreads();
+    if (fail) break;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * n + j] = (1.0 / piv) * A[(size_t)i * n + j];
+    __syncthreads();
+    const int mm = n - j - 1;
+    for (int t = threadIdx.x; t < mm * mm; t += blockDim.x) {
+      const int ii = t / mm, ll = t % mm;
+      if (ll > ii) continue;
+      const int i = j + 1 + ii, l = j + 1 + ll;
+      A[(size_t)i * n + l] -= A[(size_t)i * n + j] * cconj(A[(size_t)l * n + j]);
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < n * n; t += blockDim.x)
+    if (t % n > t / n) A[t] = mkc(0, 0);
+  if (threadIdx.x == 0) *info = fail;
+}
+
+__global__ void k_trinv_cd(const cd* L, cd* Y, int n) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= n) return;
+  for (int i = 0; i < n; ++i) {
+    if (i < c) { Y[(size_t)i * n + c] = mkc(0, 0); continue; }
+    cd s = i == c ? mkc(1, 0) : mkc(0, 0);
+    for (int k = c; k < i; ++k) s -= L[(size_t)i * n + k] * Y[(size_t)k * n + c];
+    Y[(size_t)i * n + c] = (1.0 / L[(size_t)i * n + i].x) * s;
+  }
+}
+
+}  // namespace
+
+// H, M: device n x n (double or cd). eps: host n. U: device n x n (same type).
+// Returns OEFE_ERR_CHOLESKY if M is not positive definite.
+template <typename S>
+int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* U) {
+  if (n > 2 * MAXPAIRS) { c->err = "eigensolver: n too large"; return OEFE_ERR_ARG; }
+  const size_t nn = (size_t)n * n;
+  // workspace: 6 complex n x n matrices + n doubles + ints, in a private allocation
+  cd* base = nullptr;
+  OEFE_TRY(dev_alloc(c, (void**)&base, 6 * nn * sizeof(cd) + (size_t)n * sizeof(double) + 64));
+  cd *Hc = base, *Mc = base + nn, *Y = base + 2 * nn, *T = base + 3 * nn, *W = base + 4 * nn, *Ws = base + 5 * nn;
+  double* d_eps = (double*)(base + 6 * nn);
+  int* d_int = (int*)(d_eps + n);
+  const int b = 256, g = (int)((nn + b - 1) / b);
+  int st = OEFE_OK;
+  k_to_cd<S><<<g, b, 0, c->stream>>>(H, Hc, (int)nn);
+  k_to_cd<S><<<g, b, 0, c->stream>>>(M, Mc, (int)nn);
+  k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
+  k_hermitian_part<<<g, b, 0, c->stream>>>(Mc, n);
+  k_chol_cd<<<1, 1024, 0, c->stream>>>(Mc, n, d_int);
+  int info = 0;
+  cudaMemcpyAsync(&info, d_int, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  if (info != 0) {
+    c->err = "rayleigh_ritz: projected overlap not positive definite";
+    st = OEFE_ERR_CHOLESKY;
+  } else {
+    k_trinv_cd<<<(n + 127) / 128, 128, 0, c->stream>>>(Mc, Y, n);   // Y = L^{-1}
+    k_small_gemm<<<g, b, 0, c->stream>>>(Y, false, Hc, false, T, n);  // T = L^{-1} H
+    k_small_gemm<<<g, b, 0, c->stream>>>(T, false, Y, true, Hc, n);   // C = T L^{-+}
+    k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
+    k_jacobi<<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+    k_sort_eig<<<(n + 127) / 128, 128, 0, c->stream>>>(Hc, W, n, d_eps, Ws);
+    k_small_gemm<<<g, b, 0, c->stream>>>(Y, true, Ws, false, T, n);   // U = L^{-+} W
+    k_from_cd<S><<<g, b, 0, c->stream>>>(T, U, (int)nn);
+    cudaMemcpyAsync(eps_host, d_eps, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (cudaGetLastError() != cudaSuccess) { c->err = "eigensolver launch failed"; st = OEFE_ERR_CUDA; }
+    cudaStreamSynchronize(c->stream);
+  }
+  dev_free(base);
+  return st;
+}
+
+template int gpu_geneig<double>(oefe_ctx*, const double*, const double*, int, double*, double*);
+template int gpu_geneig<cd>(oefe_ctx*, const cd*, const cd*, int, double*, cd*);
+
+// eigenvalues of a real symmetric tridiagonal (Lanczos) matrix, ascending
+int gpu_tridiag_eig(oefe_ctx* c, const std::vector<double>& al, const std::vector<double>& be, std::vector<double>& w) {
+  const int m = (int)al.size();
+  std::vector<double> T((size_t)m * m, 0.0), I((size_t)m * m, 0.0);
+  for (int i = 0; i < m; ++i) {
+    T[(size_t)i * m + i] = al[i];
+    I[(size_t)i * m + i] = 1.0;
+    if (i + 1 < m) T[(size_t)i * m + i + 1] = T[(size_t)(i + 1) * m + i] = be[i];
+  }
+  double *dT = nullptr;
+  OEFE_TRY(dev_alloc(c, (void**)&dT, 3 * (size_t)m * m * sizeof(double)));
+  cudaMemcpyAsync(dT, T.data(), T.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(dT + (size_t)m * m, I.data(), I.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+  w.assign(m, 0.0);
+  const int st = gpu_geneig<double>(c, dT, dT + (size_t)m * m, m, w.data(), dT + 2 * (size_t)m * m);
+  cudaStreamSynchronize(c->stream);
+  dev_free(dT);
+  return st;
+}

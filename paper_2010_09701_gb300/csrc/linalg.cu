@@ -288,115 +288,6 @@ int chol_inverse_t(oefe_ctx* c, S* A, int n, bool inverse, bool want_Linv, S* Y,
   return OEFE_OK;
 }
 
-// ------------------------------------------------------------------ host eigensolver
-// Cyclic Jacobi for a Hermitian matrix (row-major, n x n); eigenvalues
-// ascending in w, eigenvectors in the columns of V.
-void jacobi_eigh(int n, std::vector<std::complex<double>>& A, std::vector<double>& w,
-                 std::vector<std::complex<double>>& V) {
-  using C = std::complex<double>;
-  V.assign((size_t)n * n, C(0, 0));
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-  auto at = [&](int i, int j) -> C& { return A[(size_t)i * n + j]; };
-  double fro = 0;
-  for (auto& x : A) fro += std::norm(x);
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0;
-    for (int i = 0; i < n; ++i)
-      for (int j = 0; j < n; ++j)
-        if (i != j) off += std::norm(at(i, j));
-    if (off <= 1e-30 * fro || off == 0.0) break;
-    for (int p = 0; p < n - 1; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const C b = at(p, q);
-        const double beta = std::abs(b);
-        if (beta < 1e-300) continue;
-        const C u = b / beta;                      // e^{i phi}
-        const double ap = at(p, p).real(), aq = at(q, q).real();
-        const double tau = (aq - ap) / (2.0 * beta);
-        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
-        const double cs = 1.0 / std::sqrt(1.0 + t * t), sn = t * cs;
-        // G = diag(1, conj(u)) [[c, s], [-s, c]] acting on columns p, q
-        const C g00 = cs, g01 = sn, g10 = -std::conj(u) * sn, g11 = std::conj(u) * cs;
-        for (int k = 0; k < n; ++k) {  // A <- A G
-          const C akp = at(k, p), akq = at(k, q);
-          at(k, p) = akp * g00 + akq * g10;
-          at(k, q) = akp * g01 + akq * g11;
-        }
-        for (int k = 0; k < n; ++k) {  // A <- G^+ A
-          const C apk = at(p, k), aqk = at(q, k);
-          at(p, k) = std::conj(g00) * apk + std::conj(g10) * aqk;
-          at(q, k) = std::conj(g01) * apk + std::conj(g11) * aqk;
-        }
-        at(p, q) = 0.0;
-        at(q, p) = 0.0;
-        for (int k = 0; k < n; ++k) {  // V <- V G
-          const C vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = vkp * g00 + vkq * g10;
-          V[(size_t)k * n + q] = vkp * g01 + vkq * g11;
-        }
-      }
-  }
-  std::vector<int> idx(n);
-  for (int i = 0; i < n; ++i) idx[i] = i;
-  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return at(a, a).real() < at(b, b).real(); });
-  w.resize(n);
-  std::vector<C> Vs((size_t)n * n);
-  for (int j = 0; j < n; ++j) {
-    w[j] = at(idx[j], idx[j]).real();
-    for (int k = 0; k < n; ++k) Vs[(size_t)k * n + j] = V[(size_t)k * n + idx[j]];
-  }
-  V = Vs;
-}
-
-// Generalized Hermitian eigenproblem H u = eps M u on the host (n small):
-// M = L L^+, C = L^{-1} H L^{-+}, C = V diag(w) V^+, U = L^{-+} V.
-int host_geneig(int n, std::vector<std::complex<double>>& H, std::vector<std::complex<double>>& M,
-                std::vector<double>& w, std::vector<std::complex<double>>& U) {
-  using C = std::complex<double>;
-  std::vector<C> L((size_t)n * n, C(0, 0));
-  for (int j = 0; j < n; ++j) {
-    double d = M[(size_t)j * n + j].real();
-    for (int k = 0; k < j; ++k) d -= std::norm(L[(size_t)j * n + k]);
-    if (!(d > 0)) return j + 1;
-    const double ljj = std::sqrt(d);
-    L[(size_t)j * n + j] = ljj;
-    for (int i = j + 1; i < n; ++i) {
-      C s = M[(size_t)i * n + j];
-      for (int k = 0; k < j; ++k) s -= L[(size_t)i * n + k] * std::conj(L[(size_t)j * n + k]);
-      L[(size_t)i * n + j] = s / ljj;
-    }
-  }
-  // Y = L^{-1} H (forward substitution on columns), then C = Y L^{-+} = (L^{-1} Y^+)^+
-  auto fwd = [&](std::vector<C>& B) {  // B <- L^{-1} B
-    for (int col = 0; col < n; ++col)
-      for (int i = 0; i < n; ++i) {
-        C s = B[(size_t)i * n + col];
-        for (int k = 0; k < i; ++k) s -= L[(size_t)i * n + k] * B[(size_t)k * n + col];
-        B[(size_t)i * n + col] = s / L[(size_t)i * n + i].real();
-      }
-  };
-  std::vector<C> Y = H;
-  fwd(Y);
-  std::vector<C> Yh((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Yh[(size_t)i * n + j] = std::conj(Y[(size_t)j * n + i]);
-  fwd(Yh);
-  std::vector<C> Cm((size_t)n * n);
-  for (int i = 0; i < n; ++i)
-    for (int j = 0; j < n; ++j) Cm[(size_t)i * n + j] = 0.5 * (Yh[(size_t)i * n + j] + std::conj(Yh[(size_t)j * n + i]));
-  std::vector<C> V;
-  jacobi_eigh(n, Cm, w, V);
-  // U = L^{-+} V: solve L^+ U = V (backward substitution)
-  U = V;
-  for (int col = 0; col < n; ++col)
-    for (int i = n - 1; i >= 0; --i) {
-      C s = U[(size_t)i * n + col];
-      for (int k = i + 1; k < n; ++k) s -= std::conj(L[(size_t)k * n + i]) * U[(size_t)k * n + col];
-      U[(size_t)i * n + col] = s / L[(size_t)i * n + i].real();
-    }
-  return 0;
-}
-
 int check_fp64(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
   if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
   if (ik < 0 || ik >= (int)c->kd.size()) { c->err = "k index out of range"; return OEFE_ERR_ARG; }
@@ -470,38 +361,8 @@ int rayleigh_ritz_t(oefe_ctx* c, int ik, S* X, int nv, int ld, int dtype, double
   OEFE_TRY(apply_M<S>(c, K, X, ld, nv, MX, nv));
   OEFE_TRY(gram<S>(c, X, ld, HX, nv, n, nv, Hq, part, nchunk));
   OEFE_TRY(gram<S>(c, X, ld, MX, nv, n, nv, Mq, part, nchunk));
-  std::vector<S> hH((size_t)nv * nv), hM((size_t)nv * nv);
-  OEFE_CUDA_TRY(c, cudaMemcpyAsync(hH.data(), Hq, hH.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
-  OEFE_CUDA_TRY(c, cudaMemcpyAsync(hM.data(), Mq, hM.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
-  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  using C = std::complex<double>;
-  std::vector<C> H2((size_t)nv * nv), M2((size_t)nv * nv), U2;
-  for (size_t i = 0; i < H2.size(); ++i) {
-    if constexpr (sizeof(S) == 8) { H2[i] = C(hH[i], 0); M2[i] = C(hM[i], 0); }
-    else { H2[i] = C(hH[i].x, hH[i].y); M2[i] = C(hM[i].x, hM[i].y); }
-  }
-  // Hermitian parts
-  for (int i = 0; i < nv; ++i)
-    for (int j = i; j < nv; ++j) {
-      C h = 0.5 * (H2[(size_t)i * nv + j] + std::conj(H2[(size_t)j * nv + i]));
-      H2[(size_t)i * nv + j] = h;
-      H2[(size_t)j * nv + i] = std::conj(h);
-      C mm = 0.5 * (M2[(size_t)i * nv + j] + std::conj(M2[(size_t)j * nv + i]));
-      M2[(size_t)i * nv + j] = mm;
-      M2[(size_t)j * nv + i] = std::conj(mm);
-    }
-  std::vector<double> w;
-  const int info = host_geneig(nv, H2, M2, w, U2);
-  if (info != 0) {
-    c->err = "rayleigh_ritz: projected overlap not positive definite";
-    return OEFE_ERR_CHOLESKY;
-  }
-  std::vector<S> hU((size_t)nv * nv);
-  for (size_t i = 0; i < hU.size(); ++i) {
-    if constexpr (sizeof(S) == 8) hU[i] = U2[i].real();
-    else hU[i] = mkc(U2[i].real(), U2[i].imag());
-  }
-  OEFE_CUDA_TRY(c, cudaMemcpyAsync(U, hU.data(), hU.size() * sizeof(S), cudaMemcpyHostToDevice, c->stream));
+  std::vector<double> w(nv);
+  OEFE_TRY(gpu_geneig<S>(c, Hq, Mq, nv, w.data(), U));
   OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_eps, w.data(), nv * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   OEFE_TRY(rotate<S>(c, X, ld, n, nv, U, false));
   if (resid) {
@@ -611,14 +472,8 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, double* b) {
     OEFE_CUDA_TRY(c, cudaGetLastError());
   }
   // largest eigenvalue of the Lanczos tridiagonal matrix
-  const int m = (int)al.size();
-  std::vector<std::complex<double>> T((size_t)m * m, 0.0), V;
-  for (int i = 0; i < m; ++i) {
-    T[(size_t)i * m + i] = al[i];
-    if (i + 1 < m) { T[(size_t)i * m + i + 1] = be[i]; T[(size_t)(i + 1) * m + i] = be[i]; }
-  }
   std::vector<double> wv;
-  jacobi_eigh(m, T, wv, V);
+  OEFE_TRY(gpu_tridiag_eig(c, al, be, wv));
   *b = wv.back() + be.back();
   return OEFE_OK;
 }

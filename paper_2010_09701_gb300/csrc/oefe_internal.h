@@ -183,6 +183,11 @@ int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int deg
 int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z);
 size_t cell_mma_smem(bool cplx);
 
+// projected eigenproblems on the GPU (eigh.cu)
+template <typename S>
+int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* U);
+int gpu_tridiag_eig(oefe_ctx* c, const std::vector<double>& al, const std::vector<double>& be, std::vector<double>& w);
+
 // subspace (linalg.cu)
 int orthonormalize(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* cond);
 int rayleigh_ritz(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* eig, double* resid);

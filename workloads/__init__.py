@@ -128,7 +128,19 @@ def config_c5():
                     [360], 50, dtype="f32")
 
 
-CONFIGS = {"c1": config_c1, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5}
+def config_c3_small():
+    """The c3 cell with an 8^3 graded mesh and one k-point: a profiling case
+    whose cell matrices (~0.6 GB) still exceed the L2 cache."""
+    w = config_c2()
+    w.name = "c3small_8atom_8cube_p6_1k"
+    w.ncell = 8
+    w.nv = [64]
+    w.kgrid = (1, 1, 1)
+    w.dtype = "c64"
+    return w
+
+
+CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5}
 
 
 def graded_breakpoints(a, ncell, coords, ratio=1.5, tol=1e-3):
