@@ -157,6 +157,27 @@ enum { OEFE_FILTER_LAST_FP64 = 1, OEFE_FILTER_BF16X3 = 2 };
 int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, int degree,
                           double a, double b, double a0, int flags);
 
+/* oefe_filter_batched -- the Chebyshev filter of every k-point of the context
+ * at once (Sec. IV; the batched multi-k launch). Degree by degree, one
+ * persistent tensor-core launch covers all (k, cell, vector block) tiles
+ * (uneven nv per k allowed), the node and enrichment updates are batched
+ * over k, and the low-precision degrees are captured once in a CUDA graph on
+ * a private stream and replayed by later calls with the same arguments.
+ * flags must contain OEFE_FILTER_BF16X3; with OEFE_FILTER_LAST_FP64 the
+ * vectors are F64/C128 and the last degree runs per k in FP64, otherwise
+ * they are F32/C64. X: host array of nk device pointers; nv, ld, a, b, a0:
+ * host arrays of nk. The call returns after the filter has finished. */
+int oefe_filter_batched(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype,
+                        int degree, const double* a, const double* b, const double* a0, int flags);
+
+/* oefe_filter_autotune -- times the batched cell-product launch shapes
+ * (64 or 32 vectors per tile on a persistent grid of one CTA per SM, or one
+ * CTA per tile) on the given vectors and keeps the fastest for
+ * oefe_filter_batched. ms (host, 3 doubles, may be NULL) receives the time of
+ * one degree's cell products for each candidate, in that order. Vectors as
+ * for oefe_filter_batched; they are read, not changed. */
+int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
+
 /* ---------------------------------------------------------------- subspace
  * oefe_orthonormalize -- Cholesky-QR in the M inner product, twice
  * (Sec. IV orthonormalization): S = X^+ M X = L L^+, X <- X L^{-+}.

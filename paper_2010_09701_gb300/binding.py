@@ -45,6 +45,8 @@ SIGNATURES = [
     ("oefe_apply_h", _I, [_P, _I, _P, _P, _I, _I, _I]),
     ("oefe_apply_a", _I, [_P, _I, _P, _P, _I, _I, _I]),
     ("oefe_chebyshev_filter", _I, [_P, _I, _P, _I, _I, _I, _I, _D, _D, _D, _I]),
+    ("oefe_filter_batched", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _I, _DP, _DP, _DP, _I]),
+    ("oefe_filter_autotune", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP]),
     ("oefe_orthonormalize", _I, [_P, _I, _P, _I, _I, _I, _DP]),
     ("oefe_rayleigh_ritz", _I, [_P, _I, _P, _I, _I, _I, _DP, _DP]),
     ("oefe_density", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP, _P]),
@@ -260,6 +262,33 @@ class Context:
         self._check(self.lib.oefe_chebyshev_filter(self.h, int(ik), px, nv, ld, dt, int(degree), float(a),
                                                    float(b), float(a0), int(flags)))
         return X
+
+    def _blocks(self, Xs):
+        ptrs, nvs, lds, dts = [], [], [], []
+        for X in Xs:
+            p, nv, ld, dt = _block(X)
+            ptrs.append(p.value)
+            nvs.append(nv)
+            lds.append(ld)
+            dts.append(dt)
+        if len(set(dts)) != 1:
+            raise ValueError("all vector blocks must have the same dtype")
+        return (ctypes.c_void_p * len(ptrs))(*ptrs), np.array(nvs, np.int32), np.array(lds, np.int32), dts[0]
+
+    def filter_batched(self, Xs, degree, a, b, a0, flags):
+        arr, nvs, lds, dt = self._blocks(Xs)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (len(Xs),)))
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(b, np.float64), (len(Xs),)))
+        a0 = np.ascontiguousarray(np.broadcast_to(np.asarray(a0, np.float64), (len(Xs),)))
+        self._check(self.lib.oefe_filter_batched(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, int(degree), _dp(a),
+                                                 _dp(b), _dp(a0), int(flags)))
+        return Xs
+
+    def filter_autotune(self, Xs):
+        arr, nvs, lds, dt = self._blocks(Xs)
+        ms = np.zeros(3)
+        self._check(self.lib.oefe_filter_autotune(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, _dp(ms)))
+        return ms
 
     def orthonormalize(self, ik, X):
         px, nv, ld, dt = _block(X)

@@ -24,6 +24,13 @@ static void free_all(oefe_ctx* c) {
   for (void* p : ptrs) dev_free(p);
   for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
   c->ev_pool.clear();
+  for (cudaEvent_t e : c->bev_kernel) cudaEventDestroy(e);
+  c->bev_kernel.clear();
+  if (c->bgraph) cudaGraphExecDestroy(c->bgraph);
+  if (c->bev_in) cudaEventDestroy(c->bev_in);
+  if (c->bev_out) cudaEventDestroy(c->bev_out);
+  if (c->bstream) cudaStreamDestroy(c->bstream);
+  dev_free(c->bparams);
 }
 
 cudaEvent_t timing_event(oefe_ctx* c) {
@@ -214,6 +221,17 @@ int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int d
   return cheb_filter(ctx, ik, X, nv, ld, dtype, degree, a, b, a0, flags);
 }
 
+int oefe_filter_batched(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
+                        const double* a, const double* b, const double* a0, int flags) {
+  CTX_CHECK(ctx);
+  return cheb_filter_batched(ctx, nk, X, nv, ld, dtype, degree, a, b, a0, flags);
+}
+
+int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms) {
+  CTX_CHECK(ctx);
+  return filter_autotune(ctx, nk, X, nv, ld, dtype, ms);
+}
+
 int oefe_orthonormalize(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, double* cond_est) {
   CTX_CHECK(ctx);
   return orthonormalize(ctx, ik, X, nv, ld, dtype, cond_est);
@@ -244,7 +262,11 @@ int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask) {
   CTX_CHECK(ctx);
   cudaStreamSynchronize(ctx->stream);
   ctx->timing = dtype_mask & 15;
-  if (ctx->timing) ctx->ev_used = 0;
+  if (ctx->timing) {
+    ctx->ev_used = 0;
+    ctx->timing_extra_ms = 0;
+    ctx->timing_extra_n = 0;
+  }
   return OEFE_OK;
 }
 
@@ -301,8 +323,8 @@ int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches) {
     OEFE_CUDA_TRY(ctx, cudaEventElapsedTime(&t, ctx->ev_pool[i], ctx->ev_pool[i + 1]));
     total += t;
   }
-  *ms = total;
-  *launches = (int64_t)(ctx->ev_used / 2);
+  *ms = total + ctx->timing_extra_ms;
+  *launches = (int64_t)(ctx->ev_used / 2) + ctx->timing_extra_n;
   return OEFE_OK;
 }
 

@@ -26,7 +26,6 @@ namespace {
 
 constexpr int MT = 128;          // rows per M tile
 constexpr int KT = 64;           // K per tile (bf16: 128 bytes per row)
-constexpr int NBV = 64;          // vectors per CTA
 constexpr int THREADS = 256;
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
@@ -108,71 +107,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+template <int N>
+__device__ __forceinline__ void tmem_ld(uint32_t taddr, float* v) {
+  static_assert(N == 16 || N == 32, "16 or 32 columns");
+  if constexpr (N == 32) tmem_ld32(taddr, v);
+  else tmem_ld16(taddr, v);
+}
+
 // byte offset of element (row, k) of a K-major 128B-swizzled bf16 tile (128-byte rows)
 __device__ __forceinline__ uint32_t swz(int row, int k) {
   const int byte = k * 2;
   return (uint32_t)(row * 128 + ((((byte >> 4) ^ (row & 7)) & 7) << 4) + (byte & 15));
 }
 
-template <bool CPLX>
-__global__ void __launch_bounds__(THREADS, 1)
-    k_cell_mma(const __nv_bfloat16* __restrict__ Hb, const float* __restrict__ X, int ldx, int nv,
-               const int* __restrict__ cell_nodes, const int* __restrict__ act_off, const int* __restrict__ act_idx,
-               int nloc, int npad, int64_t nh, float* __restrict__ Z, int* __restrict__ err) {
+// One (cell, vector block) tile: Z_e[:, v0:v0+NB] = H_e X_e[:, v0:v0+NB].
+// g is the CTA's running pipeline iteration count (mbarrier phases continue
+// across tiles); every tile ends with all its MMAs complete and its
+// accumulators read, so the next tile starts on free stages.
+template <bool CPLX, int NB>
+__device__ __forceinline__ void mma_tile(const __nv_bfloat16* __restrict__ He, const float* __restrict__ X, int ldx,
+                                         int nv, int v0, int e, const int* __restrict__ cell_nodes,
+                                         const int* __restrict__ act_off, const int* __restrict__ act_idx, int nloc,
+                                         int npad, int64_t nh, float* __restrict__ Z, unsigned char* sA,
+                                         unsigned char* sB, uint64_t* bars, uint32_t taddr, int& g, int* s_fail) {
   constexpr int PLANES = CPLX ? 4 : 2;             // (Hr_hi, Hr_lo, Hi_hi, Hi_lo) or (H_hi, H_lo)
-  constexpr int NB_ROWS = CPLX ? 2 * NBV : NBV;    // B^T rows: [X_r | X_i] or X
+  constexpr int NB_ROWS = CPLX ? 2 * NB : NB;      // B^T rows: [X_r | X_i] or X
   constexpr int A_PLANE = MT * 128;                // bytes per A plane tile
   constexpr int A_STAGE = PLANES * A_PLANE;
   constexpr int B_PART = NB_ROWS * 128;            // bytes per B split part
   constexpr int B_STAGE = 2 * B_PART;              // hi, lo
-  constexpr int TCOLS = CPLX ? 512 : 256;
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  unsigned char* sA = smem;
-  unsigned char* sB = smem + 2 * A_STAGE;
-  __shared__ uint64_t bars[2];
-  __shared__ uint32_t tmem_slot;
-  __shared__ int s_fail;
-
+  constexpr int MCOLS = CPLX ? 2 * NB : NB;        // accumulator columns per M tile
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int e = blockIdx.x;
-  const int v0 = blockIdx.y * NBV;
   const int ne = act_off[e + 1] - act_off[e];
   const int naug = nloc + ne;
   const int mt = npad / MT, ktn = npad / KT;
   const int nit = mt * ktn;
-  const int mcols = CPLX ? 2 * NBV : NBV;          // accumulator columns per M tile
-
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
-                 "r"(TCOLS)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
-    s_fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t taddr = tmem_slot;
-  const __nv_bfloat16* He = Hb + (size_t)e * PLANES * npad * npad;
-  const int64_t* dummy = nullptr;
-  (void)dummy;
-
-  int issued = 0;  // MMA groups committed (iterations)
+  const int g0 = g;
+  int issued = 0;
   for (int it = 0; it < nit; ++it) {
-    const int kt = it / mt, m = it % mt, s = it & 1;
+    const int gi = g0 + it;
+    const int kt = it / mt, m = it % mt, s = gi & 1;
     if (it >= 2) {
-      if (!mbar_wait(&bars[s], ((it - 2) >> 1) & 1)) s_fail = 1;
+      if (!mbar_wait(&bars[s], ((gi - 2) >> 1) & 1)) *s_fail = 1;
     }
     __syncthreads();
-    if (s_fail) break;
-    // A tiles of (kt, m): PLANES x 128 rows x 8 chunks of 16 bytes, async copies into the swizzled stage
-    {
+    if (*s_fail) break;
+    {  // A tiles of (kt, m): PLANES x 128 rows x 8 chunks of 16 bytes into the swizzled stage
       const uint32_t a0 = smem_u32(sA + s * A_STAGE);
       for (int c = tid; c < PLANES * MT * 8; c += THREADS) {
         const int p = c / (MT * 8), r = (c / 8) % MT, ch = c % 8;
@@ -181,11 +173,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       asm volatile("cp.async.commit_group;" ::: "memory");
     }
-    // B tile of kt (first M tile only): gather the cell's rows, split to bf16 hi/lo
-    if (m == 0) {
+    if (m == 0) {  // B tile of kt: gather the cell's rows, split to bf16 hi / lo
       unsigned char* b0 = sB + (kt & 1) * B_STAGE;
-      for (int idx = tid; idx < KT * NBV; idx += THREADS) {
-        const int kk = idx / NBV, v = idx % NBV;
+      for (int idx = tid; idx < KT * NB; idx += THREADS) {
+        const int kk = idx / NB, v = idx % NB;
         const int r = kt * KT + kk;
         float xr = 0.f, xi = 0.f;
         if (r < naug && v0 + v < nv) {
@@ -205,8 +196,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (CPLX) {
           const __nv_bfloat16 ih = __float2bfloat16_rn(xi);
           const __nv_bfloat16 il = __float2bfloat16_rn(xi - __bfloat162float(ih));
-          *reinterpret_cast<__nv_bfloat16*>(b0 + swz(NBV + v, kk)) = ih;
-          *reinterpret_cast<__nv_bfloat16*>(b0 + B_PART + swz(NBV + v, kk)) = il;
+          *reinterpret_cast<__nv_bfloat16*>(b0 + swz(NB + v, kk)) = ih;
+          *reinterpret_cast<__nv_bfloat16*>(b0 + B_PART + swz(NB + v, kk)) = il;
         }
       }
     }
@@ -217,9 +208,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a_base = smem_u32(sA + s * A_STAGE);
       const uint32_t b_base = smem_u32(sB + (kt & 1) * B_STAGE);
-      const uint32_t dcol = taddr + m * mcols;
-      constexpr uint32_t ID = idesc_bf16(MT, NBV, false);
-      constexpr uint32_t IDN = idesc_bf16(MT, NBV, true);
+      const uint32_t dcol = taddr + m * MCOLS;
+      constexpr uint32_t ID = idesc_bf16(MT, NB, false);
+      constexpr uint32_t IDN = idesc_bf16(MT, NB, true);
 #pragma unroll
       for (int ks = 0; ks < KT / 16; ++ks) {
         const uint32_t koff = ks * 32;
@@ -227,9 +218,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (CPLX) {
           const uint64_t Arh = sdesc(a_base + 0 * A_PLANE + koff), Arl = sdesc(a_base + 1 * A_PLANE + koff);
           const uint64_t Aih = sdesc(a_base + 2 * A_PLANE + koff), Ail = sdesc(a_base + 3 * A_PLANE + koff);
-          const uint64_t Xrh = sdesc(b_base + koff), Xih = sdesc(b_base + NBV * 128 + koff);
-          const uint64_t Xrl = sdesc(b_base + B_PART + koff), Xil = sdesc(b_base + B_PART + NBV * 128 + koff);
-          const uint32_t Dr = dcol, Di = dcol + NBV;
+          const uint64_t Xrh = sdesc(b_base + koff), Xih = sdesc(b_base + NB * 128 + koff);
+          const uint64_t Xrl = sdesc(b_base + B_PART + koff), Xil = sdesc(b_base + B_PART + NB * 128 + koff);
+          const uint32_t Dr = dcol, Di = dcol + NB;
           // Z_r += H_r X_r - H_i X_i
           mma_bf16(Dr, Arh, Xrh, ID, first);
           mma_bf16(Dr, Arh, Xrl, ID, 1);
@@ -256,28 +247,29 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
     issued = it + 1;
   }
-  // drain: wait for the last committed group (it implies all earlier ones)
-  if (issued > 0) {
-    const int last = issued - 1;
-    if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) s_fail = 1;
+  if (issued > 0) {  // drain: the last committed group implies all earlier ones
+    const int last = g0 + issued - 1;
+    if (!mbar_wait(&bars[last & 1], (last >> 1) & 1)) *s_fail = 1;
   }
+  g = g0 + issued;
   asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!s_fail && issued == nit) {
+  if (!*s_fail && issued == nit) {
     // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31; the two warpgroups split the vector columns
+    constexpr int HC = NB / 2;
     const int q = warp & 3, h = warp >> 2;
     for (int m = 0; m < mt; ++m) {
       const int row = m * MT + 32 * q + lane;
-      const uint32_t tl = taddr + ((uint32_t)(32 * q) << 16) + m * mcols + 32 * h;
-      float re[32], im[32];
-      tmem_ld32(tl, re);
-      if (CPLX) tmem_ld32(tl + NBV, im);
+      const uint32_t tl = taddr + ((uint32_t)(32 * q) << 16) + m * MCOLS + HC * h;
+      float re[HC], im[HC];
+      tmem_ld<HC>(tl, re);
+      if (CPLX) tmem_ld<HC>(tl + NB, im);
       if (row < naug) {
         float* zr = Z + ((size_t)e * npad + row) * (size_t)nv * (CPLX ? 2 : 1);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int v = v0 + 32 * h + j;
+        for (int j = 0; j < HC; ++j) {
+          const int v = v0 + HC * h + j;
           if (v < nv) {
             if (CPLX) {
               zr[2 * v] = re[j];
@@ -290,41 +282,152 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
     }
   }
-  if (s_fail && tid == 0) atomicExch(err, 1);
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
+}
+
+template <bool CPLX, int NB>
+struct MmaCfg {
+  static constexpr int PLANES = CPLX ? 4 : 2;
+  static constexpr int NB_ROWS = CPLX ? 2 * NB : NB;
+  static constexpr int SMEM = 1024 + 2 * PLANES * MT * 128 + 2 * 2 * NB_ROWS * 128;
+  static constexpr int TCOLS_NEED = 4 * (CPLX ? 2 * NB : NB);   // up to 4 M tiles
+  static constexpr int TCOLS = TCOLS_NEED <= 128 ? 128 : TCOLS_NEED <= 256 ? 256 : 512;
+};
+
+__device__ __forceinline__ uint32_t cta_setup(uint64_t* bars, uint32_t* tmem_slot, int* s_fail, int tcols) {
+  const int tid = threadIdx.x, warp = tid >> 5;
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS) : "memory");
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(tcols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    *s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  return *tmem_slot;
+}
+
+__device__ __forceinline__ void cta_teardown(uint32_t taddr, int tcols, const int* s_fail, int* err) {
+  if (*s_fail && threadIdx.x == 0) atomicExch(err, 1);
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(tcols) : "memory");
+}
+
+// one CTA per (cell, vector block)
+template <bool CPLX, int NB>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_cell_mma(const __nv_bfloat16* __restrict__ Hb, const float* __restrict__ X, int ldx, int nv,
+               const int* __restrict__ cell_nodes, const int* __restrict__ act_off, const int* __restrict__ act_idx,
+               int nloc, int npad, int64_t nh, float* __restrict__ Z, int* __restrict__ err) {
+  using Cfg = MmaCfg<CPLX, NB>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const uint32_t taddr = cta_setup(bars, &tmem_slot, &s_fail, Cfg::TCOLS);
+  const int e = blockIdx.x;
+  int g = 0;
+  mma_tile<CPLX, NB>(Hb + (size_t)e * Cfg::PLANES * npad * npad, X, ldx, nv, blockIdx.y * NB, e, cell_nodes, act_off,
+                     act_idx, nloc, npad, nh, Z, smem, smem + 2 * Cfg::PLANES * MT * 128, bars, taddr, g, &s_fail);
+  cta_teardown(taddr, Cfg::TCOLS, &s_fail, err);
+}
+
+// persistent: all (k, cell, vector block) tiles of a batch of k-points
+template <bool CPLX, int NB>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_cell_mma_multi(const MmaK* __restrict__ ks, int nk, long long ntiles, const int* __restrict__ cell_nodes,
+                     const int* __restrict__ act_off, const int* __restrict__ act_idx, int nloc, int npad, int ncells,
+                     int64_t nh, int* __restrict__ err) {
+  using Cfg = MmaCfg<CPLX, NB>;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const uint32_t taddr = cta_setup(bars, &tmem_slot, &s_fail, Cfg::TCOLS);
+  int g = 0;
+  for (long long t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    int k = 0;
+    while (k + 1 < nk && ks[k + 1].tile0 <= t) ++k;
+    const MmaK P = ks[k];
+    const __nv_bfloat16* Hk = (const __nv_bfloat16*)P.H;
+    const long long r = t - P.tile0;
+    const int e = (int)(r / P.vblocks), vb = (int)(r % P.vblocks);
+    mma_tile<CPLX, NB>(Hk + (size_t)e * Cfg::PLANES * npad * npad, P.X, P.ldx, P.nv, vb * NB, e, cell_nodes, act_off,
+                       act_idx, nloc, npad, nh, P.Z, smem, smem + 2 * Cfg::PLANES * MT * 128, bars, taddr, g, &s_fail);
+    if (s_fail) break;
+  }
+  cta_teardown(taddr, Cfg::TCOLS, &s_fail, err);
 }
 
 }  // namespace
 
-size_t cell_mma_smem(bool cplx) {
-  const int planes = cplx ? 4 : 2;
-  const int nbrows = cplx ? 2 * NBV : NBV;
-  return 1024 + 2 * (size_t)planes * MT * 128 + 2 * 2 * (size_t)nbrows * 128;
+size_t cell_mma_smem(bool cplx, int nb) {
+  if (cplx) return nb == 64 ? MmaCfg<true, 64>::SMEM : MmaCfg<true, 32>::SMEM;
+  return nb == 64 ? MmaCfg<false, 64>::SMEM : MmaCfg<false, 32>::SMEM;
 }
 
-int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z) {
+static int check_npad(oefe_ctx* c) {
   if (c->npad % MT != 0 || c->npad > 4 * MT) {
     c->err = "tensor path needs npad a multiple of 128 and at most 512";
     return OEFE_ERR_ARG;
   }
-  if (!K.Hbf) { c->err = "BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
-  const size_t smem = cell_mma_smem(cplx);
-  dim3 grid(c->ncells, (nv + NBV - 1) / NBV);
-  if (cplx) {
-    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_cell_mma<true><<<grid, THREADS, smem, c->stream>>>((const __nv_bfloat16*)K.Hbf, (const float*)X, ldx, nv,
-                                                         c->d_cell_nodes, c->d_act_off, c->d_act_idx, c->nloc,
-                                                         c->npad, c->nh, (float*)Z, c->d_status);
-  } else {
-    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_cell_mma<false><<<grid, THREADS, smem, c->stream>>>((const __nv_bfloat16*)K.Hbf, (const float*)X, ldx, nv,
-                                                          c->d_cell_nodes, c->d_act_off, c->d_act_idx, c->nloc,
-                                                          c->npad, c->nh, (float*)Z, c->d_status);
-  }
+  return OEFE_OK;
+}
+
+template <bool CPLX, int NB>
+static int launch_one(oefe_ctx* c, const void* H, const void* X, int ldx, int nv, void* Z, cudaStream_t st) {
+  const size_t smem = MmaCfg<CPLX, NB>::SMEM;
+  dim3 grid(c->ncells, (nv + NB - 1) / NB);
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma<CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  k_cell_mma<CPLX, NB><<<grid, THREADS, smem, st>>>((const __nv_bfloat16*)H, (const float*)X, ldx, nv, c->d_cell_nodes,
+                                                    c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh, (float*)Z,
+                                                    c->d_status);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
+}
+
+int launch_cell_mma_ptrs(oefe_ctx* c, const void* H, const void* X, int ldx, int nv, void* Z, bool cplx, int nb,
+                         cudaStream_t st) {
+  OEFE_TRY(check_npad(c));
+  if (cplx) return nb == 64 ? launch_one<true, 64>(c, H, X, ldx, nv, Z, st) : launch_one<true, 32>(c, H, X, ldx, nv, Z, st);
+  return nb == 64 ? launch_one<false, 64>(c, H, X, ldx, nv, Z, st) : launch_one<false, 32>(c, H, X, ldx, nv, Z, st);
+}
+
+int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z) {
+  OEFE_TRY(check_npad(c));
+  if (!K.Hbf) { c->err = "BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  if (cplx) return launch_one<true, 64>(c, K.Hbf, X, ldx, nv, Z, c->stream);
+  return launch_one<false, 64>(c, K.Hbf, X, ldx, nv, Z, c->stream);
+}
+
+template <bool CPLX, int NB>
+static int launch_multi_t(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntiles, int grid, cudaStream_t st) {
+  const size_t smem = MmaCfg<CPLX, NB>::SMEM;
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_multi<CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)smem));
+  k_cell_mma_multi<CPLX, NB><<<grid, THREADS, smem, st>>>(d_ks, nk, ntiles, c->d_cell_nodes, c->d_act_off,
+                                                          c->d_act_idx, c->nloc, c->npad, c->ncells, c->nh,
+                                                          c->d_status);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}
+
+int launch_cell_mma_multi(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntiles, bool cplx, int nb, int grid,
+                          cudaStream_t st) {
+  OEFE_TRY(check_npad(c));
+  if (cplx) return nb == 64 ? launch_multi_t<true, 64>(c, d_ks, nk, ntiles, grid, st)
+                            : launch_multi_t<true, 32>(c, d_ks, nk, ntiles, grid, st);
+  return nb == 64 ? launch_multi_t<false, 64>(c, d_ks, nk, ntiles, grid, st)
+                  : launch_multi_t<false, 32>(c, d_ks, nk, ntiles, grid, st);
 }

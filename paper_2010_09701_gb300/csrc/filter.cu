@@ -177,6 +177,99 @@ __global__ void k_enr_update(const cd* __restrict__ Yo, const void* __restrict__
   else Y[row * ldy + v] = (T)y.x;
 }
 
+// Batched variants: blockIdx.y selects the k-point; per-k pointers and
+// recurrence coefficients come from a parameter table.
+struct NodeK {
+  const void* Z;
+  const void* Xk;
+  const void* Xm1;
+  void* Y;
+  cd* Yo;
+  const void* Minv;
+  int ldk, ldm1, ldy, nv, mode;
+  double alpha, cshift, beta;
+};
+
+template <typename T, bool C>
+__global__ void k_node_update_multi(const NodeK* __restrict__ P, const int64_t* __restrict__ node_off,
+                                    const int64_t* __restrict__ node_slot, const double* __restrict__ m, int64_t nh) {
+  using S = typename Sc<T, C>::type;
+  const NodeK p = P[blockIdx.y];
+  const S* Z = (const S*)p.Z;
+  const S* Xk = (const S*)p.Xk;
+  const S* Xm1 = (const S*)p.Xm1;
+  S* Y = (S*)p.Y;
+  const int nv = p.nv;
+  const int64_t total = nh * nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t g = t / nv;
+    const int v = (int)(t % nv);
+    S y = Sc<T, C>::zero();
+    for (int64_t s = node_off[g]; s < node_off[g + 1]; ++s) y = Sc<T, C>::add(y, Z[node_slot[s] * nv + v]);
+    y = Sc<T, C>::scale(y, 1.0 / m[g]);
+    const S xk = Xk[g * p.ldk + v];
+    S out;
+    if constexpr (C) {
+      out.x = (T)(p.alpha * ((double)y.x - p.cshift * (double)xk.x));
+      out.y = (T)(p.alpha * ((double)y.y - p.cshift * (double)xk.y));
+      if (p.beta != 0.0) {
+        const S xm = Xm1[g * p.ldm1 + v];
+        out.x = (T)((double)out.x + p.beta * (double)xm.x);
+        out.y = (T)((double)out.y + p.beta * (double)xm.y);
+      }
+    } else {
+      out = (T)(p.alpha * ((double)y - p.cshift * (double)xk));
+      if (p.beta != 0.0) out = (T)((double)out + p.beta * (double)Xm1[g * p.ldm1 + v]);
+    }
+    Y[g * p.ldy + v] = out;
+  }
+}
+
+template <typename T, bool C>
+__global__ void k_enr_reduce_multi(const NodeK* __restrict__ P, const int64_t* __restrict__ enr_off,
+                                   const int64_t* __restrict__ enr_slot, int nO) {
+  using S = typename Sc<T, C>::type;
+  const NodeK p = P[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nO * p.nv) return;
+  const int nu = t / p.nv, v = t % p.nv;
+  const S* Z = (const S*)p.Z;
+  double sx = 0, sy = 0;
+  for (int64_t s = enr_off[nu]; s < enr_off[nu + 1]; ++s) {
+    const auto z = Z[enr_slot[s] * p.nv + v];
+    if constexpr (C) { sx += (double)z.x; sy += (double)z.y; }
+    else sx += (double)z;
+  }
+  p.Yo[t] = mkc(sx, sy);
+}
+
+template <typename T, bool C>
+__global__ void k_enr_update_multi(const NodeK* __restrict__ P, int nO, int64_t nh) {
+  using S = typename Sc<T, C>::type;
+  const NodeK p = P[blockIdx.y];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nO * p.nv) return;
+  const int nu = t / p.nv, v = t % p.nv;
+  cd s = mkc(0, 0);
+  for (int mu = 0; mu < nO; ++mu) {
+    const cd yo = p.Yo[mu * p.nv + v];
+    if constexpr (C) s += reinterpret_cast<const cd*>(p.Minv)[nu * nO + mu] * yo;
+    else s += reinterpret_cast<const double*>(p.Minv)[nu * nO + mu] * yo;
+  }
+  const int64_t row = nh + nu;
+  const S xk = ((const S*)p.Xk)[row * p.ldk + v];
+  double xr, xi = 0;
+  if constexpr (C) { xr = (double)xk.x; xi = (double)xk.y; } else xr = (double)xk;
+  cd out = mkc(p.alpha * (s.x - p.cshift * xr), p.alpha * (s.y - p.cshift * xi));
+  if (p.beta != 0.0) {
+    const S xm = ((const S*)p.Xm1)[row * p.ldm1 + v];
+    if constexpr (C) out += mkc(p.beta * (double)xm.x, p.beta * (double)xm.y);
+    else out.x += p.beta * (double)xm;
+  }
+  if constexpr (C) ((S*)p.Y)[row * p.ldy + v] = S{(T)out.x, (T)out.y};
+  else ((S*)p.Y)[row * p.ldy + v] = (T)out.x;
+}
+
 // Y (ldy) <- X (ldx) with a precision change; n rows of nv scalars (reals counted by `width`).
 template <typename A, typename B>
 __global__ void k_convert(const A* __restrict__ X, int ldx, B* __restrict__ Y, int ldy, int64_t n, int width) {
@@ -384,5 +477,384 @@ int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int deg
       return OEFE_ERR_TIMEOUT;
     }
   }
+  return OEFE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched multi-k filter: every k-point advances degree by degree together; one
+// persistent tensor-core launch per degree covers all (k, cell, vector block)
+// tiles, followed by the batched node / enrichment updates. The low-precision
+// degrees are captured once in a CUDA graph on a private stream and replayed;
+// the last degree (LAST_FP64) runs per k through the FP64 path.
+namespace {
+
+struct BatchPlan {
+  int nk, jlow, nb, grid;
+  long long ntiles;
+  std::vector<MmaK> mk;      // jlow * nk
+  std::vector<NodeK> nd;     // jlow * nk
+  std::vector<int> lc, lp;   // per k: final buffer indices after the low degrees
+};
+
+int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const MmaK* d_mk, const NodeK* d_nd,
+                           bool timed) {
+  const int blocks = std::max(1, std::min(c->num_sms * 8, (int)((c->nh * 64 + 255) / 256)));
+  int vmax = 0;
+  for (int k = 0; k < P.nk; ++k) vmax = std::max(vmax, P.nd[k].nv);
+  const int eb = (c->nO * vmax + 127) / 128;
+  for (int j = 0; j < P.jlow; ++j) {
+    if (timed) cudaEventRecord(c->bev_kernel[2 * j], c->bstream);
+    if (P.grid > 0) {
+      OEFE_TRY(launch_cell_mma_multi(c, d_mk + (size_t)j * P.nk, P.nk, P.ntiles, cplx, P.nb, P.grid, c->bstream));
+    } else {  // one CTA per tile, one launch per k-point
+      for (int k = 0; k < P.nk; ++k) {
+        const MmaK& m = P.mk[(size_t)j * P.nk + k];
+        OEFE_TRY(launch_cell_mma_ptrs(c, m.H, m.X, m.ldx, m.nv, m.Z, cplx, P.nb, c->bstream));
+      }
+    }
+    if (timed) cudaEventRecord(c->bev_kernel[2 * j + 1], c->bstream);
+    dim3 g1(blocks, P.nk), g2(std::max(eb, 1), P.nk);
+    if (cplx) {
+      k_node_update_multi<float, true><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off, c->d_node_slot,
+                                                                   c->d_m, c->nh);
+      if (c->nO > 0) {
+        k_enr_reduce_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off, c->d_enr_slot,
+                                                                    c->nO);
+        k_enr_update_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
+      }
+    } else {
+      k_node_update_multi<float, false><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off,
+                                                                    c->d_node_slot, c->d_m, c->nh);
+      if (c->nO > 0) {
+        k_enr_reduce_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
+                                                                     c->d_enr_slot, c->nO);
+        k_enr_update_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
+      }
+    }
+    OEFE_CUDA_TRY(c, cudaGetLastError());
+  }
+  return OEFE_OK;
+}
+
+}  // namespace
+
+int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
+                        const double* a, const double* b, const double* a0, int flags) {
+  if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
+  if (nk < 1 || nk != (int)c->kd.size() || !X || !nv || !ld || !a || !b || !a0) {
+    c->err = "filter_batched: one X, nv, ld, a, b, a0 per k-point of the context";
+    return OEFE_ERR_ARG;
+  }
+  if (!(flags & OEFE_FILTER_BF16X3)) { c->err = "filter_batched runs on the tensor cores: pass OEFE_FILTER_BF16X3"; return OEFE_ERR_ARG; }
+  const bool mixed = (flags & OEFE_FILTER_LAST_FP64) != 0;
+  const bool cplx = c->kd[0].cplx;
+  for (int k = 0; k < nk; ++k) {
+    OEFE_TRY(check_apply_args(c, k, X[k], nv[k], ld[k], dtype, !mixed));
+    if (c->kd[k].cplx != cplx) { c->err = "filter_batched: all k-points must be real or all complex"; return OEFE_ERR_ARG; }
+    if (!c->kd[k].Hbf) { c->err = "filter_batched: BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
+    if (degree < 1 || !(b[k] > a[k]) || !(a0[k] < a[k])) { c->err = "filter_batched: need degree >= 1, a0 < a < b"; return OEFE_ERR_ARG; }
+  }
+  if (mixed && !dtype_fp64(dtype)) { c->err = "filter_batched: LAST_FP64 needs F64/C128 storage"; return OEFE_ERR_ARG; }
+  if (!mixed && dtype_fp64(dtype)) { c->err = "filter_batched: low-precision vectors (F32/C64) without LAST_FP64"; return OEFE_ERR_ARG; }
+  const int dt_low = cplx ? OEFE_C64 : OEFE_F32;
+  const size_t es_low = dtype_bytes(dt_low), es = dtype_bytes(dtype);
+  const int64_t n = c->nh + c->nO;
+  const int jlow = mixed ? degree - 1 : degree;
+  if (c->tune_nb == 0) { c->tune_nb = 64; c->tune_grid = c->num_sms; }
+  // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed)
+  std::vector<size_t> off(nk + 1, 0);
+  auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
+  std::vector<size_t> zb(nk), yb(nk), lb(nk), fb(nk);
+  for (int k = 0; k < nk; ++k) {
+    zb[k] = a256((size_t)c->ncells * c->npad * nv[k] * std::max(es, es_low));
+    yb[k] = a256((size_t)std::max(c->nO, 1) * nv[k] * sizeof(cd));
+    lb[k] = a256((size_t)n * nv[k] * es_low);
+    fb[k] = mixed ? a256((size_t)n * nv[k] * es) : 0;
+    off[k + 1] = off[k] + zb[k] + yb[k] + 3 * lb[k] + 2 * fb[k];
+  }
+  OEFE_TRY(ensure_ws(c, off[nk] + 256));
+  char* base = (char*)c->ws;
+  std::vector<void*> Zk(nk), L0(nk), L1(nk), L2(nk), F1(nk), F2(nk);
+  std::vector<cd*> Yo(nk);
+  for (int k = 0; k < nk; ++k) {
+    char* p = base + off[k];
+    Zk[k] = p;
+    Yo[k] = (cd*)(p + zb[k]);
+    L0[k] = p + zb[k] + yb[k];
+    L1[k] = p + zb[k] + yb[k] + lb[k];
+    L2[k] = p + zb[k] + yb[k] + 2 * lb[k];
+    F1[k] = p + zb[k] + yb[k] + 3 * lb[k];
+    F2[k] = p + zb[k] + yb[k] + 3 * lb[k] + fb[k];
+  }
+  // plan: simulate the buffer rotation of the low-precision degrees
+  BatchPlan P;
+  P.nk = nk;
+  P.jlow = jlow;
+  P.nb = c->tune_nb;
+  P.grid = c->tune_grid;
+  P.ntiles = 0;
+  std::vector<long long> tile0(nk);
+  for (int k = 0; k < nk; ++k) {
+    tile0[k] = P.ntiles;
+    P.ntiles += (long long)c->ncells * ((nv[k] + P.nb - 1) / P.nb);
+  }
+  P.lc.assign(nk, 0);
+  P.lp.assign(nk, 1);
+  std::vector<double> sig(nk);
+  for (int k = 0; k < nk; ++k) {
+    const double e = (b[k] - a[k]) / 2.0;
+    sig[k] = e / (a0[k] - (b[k] + a[k]) / 2.0);
+  }
+  const std::vector<double> sig1 = sig;
+  for (int j = 1; j <= jlow; ++j) {
+    for (int k = 0; k < nk; ++k) {
+      void* bufs[3] = {mixed ? L0[k] : X[k], L1[k], L2[k]};
+      const int lds[3] = {mixed ? nv[k] : ld[k], nv[k], nv[k]};
+      const double e = (b[k] - a[k]) / 2.0, cc = (b[k] + a[k]) / 2.0;
+      double alpha, beta;
+      if (j == 1) {
+        alpha = sig1[k] / e;
+        beta = 0.0;
+      } else {
+        const double s2 = 1.0 / (2.0 / sig1[k] - sig[k]);
+        alpha = 2.0 * s2 / e;
+        beta = -sig[k] * s2;
+        sig[k] = s2;
+      }
+      const int ic = P.lc[k], ip = P.lp[k], in = 3 - ic - ip;
+      MmaK mk;
+      mk.H = c->kd[k].Hbf;
+      mk.X = (const float*)bufs[ic];
+      mk.Z = (float*)Zk[k];
+      mk.ldx = lds[ic];
+      mk.nv = nv[k];
+      mk.vblocks = (nv[k] + P.nb - 1) / P.nb;
+      mk.tile0 = tile0[k];
+      P.mk.push_back(mk);
+      NodeK nd;
+      nd.Z = Zk[k];
+      nd.Xk = bufs[ic];
+      nd.Xm1 = j == 1 ? nullptr : bufs[ip];
+      nd.Y = bufs[in];
+      nd.Yo = Yo[k];
+      nd.Minv = c->kd[k].Mooinv;
+      nd.ldk = lds[ic];
+      nd.ldm1 = lds[ip];
+      nd.ldy = lds[in];
+      nd.nv = nv[k];
+      nd.mode = 2;
+      nd.alpha = alpha;
+      nd.cshift = cc;
+      nd.beta = beta;
+      P.nd.push_back(nd);
+      P.lp[k] = ic;
+      P.lc[k] = in;
+    }
+  }
+  // graph key: everything baked into the captured launches
+  std::vector<double> key = {(double)nk, (double)degree, (double)flags, (double)dtype, (double)(uintptr_t)base,
+                             (double)P.nb, (double)P.grid, (double)(c->timing & (1 << dt_low) ? 1 : 0)};
+  for (int k = 0; k < nk; ++k) {
+    key.push_back((double)(uintptr_t)X[k]);
+    key.push_back(nv[k]);
+    key.push_back(ld[k]);
+    key.push_back(a[k]);
+    key.push_back(b[k]);
+    key.push_back(a0[k]);
+  }
+  if (!c->bstream) {
+    OEFE_CUDA_TRY(c, cudaStreamCreateWithFlags(&c->bstream, cudaStreamNonBlocking));
+    OEFE_CUDA_TRY(c, cudaEventCreateWithFlags(&c->bev_in, cudaEventDisableTiming));
+    OEFE_CUDA_TRY(c, cudaEventCreateWithFlags(&c->bev_out, cudaEventDisableTiming));
+  }
+  const bool timed = (c->timing >> dt_low) & 1;
+  if (!c->bgraph || key != c->bkey) {
+    if (c->bgraph) {
+      cudaGraphExecDestroy(c->bgraph);
+      c->bgraph = nullptr;
+    }
+    const size_t pbytes = P.mk.size() * sizeof(MmaK) + P.nd.size() * sizeof(NodeK) + 64;
+    if (pbytes > c->bparams_bytes) {
+      cudaStreamSynchronize(c->bstream);
+      dev_free(c->bparams);
+      c->bparams = nullptr;
+      c->bparams_bytes = 0;
+      OEFE_TRY(dev_alloc(c, &c->bparams, pbytes));
+      c->bparams_bytes = pbytes;
+    }
+    MmaK* d_mk = (MmaK*)c->bparams;
+    NodeK* d_nd = (NodeK*)((char*)c->bparams + ((P.mk.size() * sizeof(MmaK) + 15) / 16) * 16);
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_mk, P.mk.data(), P.mk.size() * sizeof(MmaK), cudaMemcpyHostToDevice, c->bstream));
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_nd, P.nd.data(), P.nd.size() * sizeof(NodeK), cudaMemcpyHostToDevice, c->bstream));
+    OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
+    if (timed) {
+      while (c->bev_kernel.size() < (size_t)2 * jlow) {
+        cudaEvent_t ev;
+        OEFE_CUDA_TRY(c, cudaEventCreate(&ev));
+        c->bev_kernel.push_back(ev);
+      }
+    }
+    // set the kernels' shared-memory limits outside of the capture
+    if (P.grid > 0) OEFE_TRY(launch_cell_mma_multi(c, d_mk, nk, 0, cplx, P.nb, 1, c->bstream));
+    OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
+    cudaGraph_t graph;
+    OEFE_CUDA_TRY(c, cudaStreamBeginCapture(c->bstream, cudaStreamCaptureModeThreadLocal));
+    int st = OEFE_OK;
+    if (mixed) {
+      for (int k = 0; k < nk && st == OEFE_OK; ++k) {
+        const int width = cplx ? 2 * nv[k] : nv[k];
+        const int64_t tot = n * width;
+        const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
+        k_convert<double, float><<<blocks, 256, 0, c->bstream>>>((const double*)X[k], ld[k] * (cplx ? 2 : 1),
+                                                                 (float*)L0[k], width, n, width);
+      }
+    }
+    if (st == OEFE_OK) st = batched_launch_degrees(c, P, cplx, d_mk, d_nd, timed);
+    cudaError_t ce = cudaStreamEndCapture(c->bstream, &graph);
+    if (st != OEFE_OK) return st;
+    if (ce != cudaSuccess) { c->err = std::string("graph capture: ") + cudaGetErrorString(ce); return OEFE_ERR_CUDA; }
+    ce = cudaGraphInstantiate(&c->bgraph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) { c->err = std::string("graph instantiate: ") + cudaGetErrorString(ce); return OEFE_ERR_CUDA; }
+    c->bkey = key;
+  }
+  // run: the private stream waits for the caller's stream and vice versa
+  OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_in, c->stream));
+  OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->bstream, c->bev_in, 0));
+  OEFE_CUDA_TRY(c, cudaGraphLaunch(c->bgraph, c->bstream));
+  OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_out, c->bstream));
+  OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->bev_out, 0));
+  if (timed) {
+    OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
+    for (int j = 0; j < jlow; ++j) {
+      float t = 0;
+      OEFE_CUDA_TRY(c, cudaEventElapsedTime(&t, c->bev_kernel[2 * j], c->bev_kernel[2 * j + 1]));
+      c->timing_extra_ms += t;
+      c->timing_extra_n += 1;
+    }
+  }
+  // finish per k: the last degree in FP64, or copy the low-precision result
+  for (int k = 0; k < nk; ++k) {
+    const KData& K = c->kd[k];
+    if (mixed) {
+      const int width = cplx ? 2 * nv[k] : nv[k];
+      void* L[3] = {L0[k], L1[k], L2[k]};
+      OEFE_TRY((convert<float, double>(c, L[P.lc[k]], width, F1[k], width, n, width)));
+      void* bufs[3] = {X[k], F1[k], F2[k]};
+      int lds[3] = {ld[k], nv[k], nv[k]};
+      int fp = 0;
+      if (degree > 2) {
+        OEFE_TRY((convert<float, double>(c, L[P.lp[k]], width, F2[k], width, n, width)));
+        fp = 2;
+      }
+      const double e = (b[k] - a[k]) / 2.0, cc = (b[k] + a[k]) / 2.0;
+      double sg = e / (a0[k] - cc);
+      const double s1 = sg;
+      for (int j = 2; j < degree; ++j) sg = 1.0 / (2.0 / s1 - sg);
+      int ip = fp, ic = 1;
+      OEFE_TRY(run_degrees(c, K, dtype, bufs, lds, &ip, &ic, nv[k], degree, degree, e, cc, &sg, s1, Zk[k], Yo[k], false));
+      if (ic != 0)
+        OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(X[k], (size_t)ld[k] * es, bufs[ic], (size_t)lds[ic] * es, (size_t)nv[k] * es,
+                                           (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+    } else if (P.lc[k] != 0) {
+      void* L[3] = {X[k], L1[k], L2[k]};
+      OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(X[k], (size_t)ld[k] * es, L[P.lc[k]], (size_t)nv[k] * es, (size_t)nv[k] * es,
+                                         (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+    }
+  }
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int flag = 0;
+  OEFE_CUDA_TRY(c, cudaMemcpy(&flag, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    c->err = "filter_batched: a tensor-core pipeline wait timed out";
+    return OEFE_ERR_TIMEOUT;
+  }
+  return OEFE_OK;
+}
+
+int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms) {
+  if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
+  if (nk < 1 || nk != (int)c->kd.size() || !X || !nv || !ld) { c->err = "autotune: one X, nv, ld per k-point"; return OEFE_ERR_ARG; }
+  const bool cplx = c->kd[0].cplx;
+  for (int k = 0; k < nk; ++k) {
+    OEFE_TRY(check_apply_args(c, k, X[k], nv[k], ld[k], dtype, true));
+    if (!c->kd[k].Hbf) { c->err = "autotune: BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  }
+  // low-precision copies of the vectors and product buffers
+  const int dt_low = cplx ? OEFE_C64 : OEFE_F32;
+  const size_t es_low = dtype_bytes(dt_low);
+  const int64_t n = c->nh + c->nO;
+  std::vector<size_t> off(nk + 1, 0);
+  for (int k = 0; k < nk; ++k)
+    off[k + 1] = off[k] + (((size_t)n * nv[k] + (size_t)c->ncells * c->npad * nv[k]) * es_low + 255) / 256 * 256;
+  OEFE_TRY(ensure_ws(c, off[nk] + 256));
+  std::vector<void*> XL(nk), Z(nk);
+  for (int k = 0; k < nk; ++k) {
+    XL[k] = (char*)c->ws + off[k];
+    Z[k] = (char*)c->ws + off[k] + (size_t)n * nv[k] * es_low;
+    const int width = cplx ? 2 * nv[k] : nv[k];
+    if (dtype_fp64(dtype)) OEFE_TRY((convert<double, float>(c, X[k], ld[k] * (cplx ? 2 : 1), XL[k], width, n, width)));
+    else OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(XL[k], (size_t)nv[k] * es_low, X[k], (size_t)ld[k] * es_low,
+                                            (size_t)nv[k] * es_low, (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  struct Cand { int nb, grid; };
+  const Cand cands[3] = {{64, c->num_sms}, {32, c->num_sms}, {64, 0}};
+  double best = 1e300;
+  int bi = 0;
+  MmaK* d_mk = nullptr;
+  OEFE_TRY(dev_alloc(c, (void**)&d_mk, nk * sizeof(MmaK)));
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  int st = OEFE_OK;
+  for (int ci = 0; ci < 3 && st == OEFE_OK; ++ci) {
+    std::vector<MmaK> mk(nk);
+    long long nt = 0;
+    for (int k = 0; k < nk; ++k) {
+      mk[k].H = c->kd[k].Hbf;
+      mk[k].X = (const float*)XL[k];
+      mk[k].Z = (float*)Z[k];
+      mk[k].ldx = nv[k];
+      mk[k].nv = nv[k];
+      mk[k].vblocks = (nv[k] + cands[ci].nb - 1) / cands[ci].nb;
+      mk[k].tile0 = nt;
+      nt += (long long)c->ncells * mk[k].vblocks;
+    }
+    cudaMemcpyAsync(d_mk, mk.data(), nk * sizeof(MmaK), cudaMemcpyHostToDevice, c->stream);
+    double tbest = 1e300;
+    for (int rep = 0; rep < 3 && st == OEFE_OK; ++rep) {
+      cudaEventRecord(e0, c->stream);
+      if (cands[ci].grid > 0) {
+        st = launch_cell_mma_multi(c, d_mk, nk, nt, cplx, cands[ci].nb, cands[ci].grid, c->stream);
+      } else {
+        for (int k = 0; k < nk && st == OEFE_OK; ++k)
+          st = launch_cell_mma_ptrs(c, XL.size() ? c->kd[k].Hbf : nullptr, XL[k], nv[k], nv[k], Z[k], cplx,
+                                    cands[ci].nb, c->stream);
+      }
+      cudaEventRecord(e1, c->stream);
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) tbest = std::min(tbest, (double)t);
+    }
+    if (ms) ms[ci] = tbest;
+    c->tune_ms[ci] = tbest;
+    if (tbest < best) { best = tbest; bi = ci; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaStreamSynchronize(c->stream);
+  dev_free(d_mk);
+  if (st != OEFE_OK) return st;
+  int flag = 0;
+  OEFE_CUDA_TRY(c, cudaMemcpy(&flag, c->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) {
+    cudaMemset(c->d_status, 0, sizeof(int));
+    c->err = "autotune: a tensor-core pipeline wait timed out";
+    return OEFE_ERR_TIMEOUT;
+  }
+  c->tune_nb = cands[bi].nb;
+  c->tune_grid = cands[bi].grid;
   return OEFE_OK;
 }

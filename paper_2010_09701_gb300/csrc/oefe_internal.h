@@ -145,6 +145,19 @@ struct oefe_ctx {
   int timing = 0;  // dtype bit mask
   std::vector<cudaEvent_t> ev_pool;
   size_t ev_used = 0;
+  double timing_extra_ms = 0;     // batched launches: accumulated at each replay
+  int64_t timing_extra_n = 0;
+
+  // batched multi-k filter: private stream, captured graph, autotuned launch shape
+  cudaStream_t bstream = nullptr;
+  cudaEvent_t bev_in = nullptr, bev_out = nullptr;
+  cudaGraphExec_t bgraph = nullptr;
+  std::vector<double> bkey;
+  void* bparams = nullptr;
+  size_t bparams_bytes = 0;
+  std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
+  int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
+  double tune_ms[4] = {0, 0, 0, 0};
 };
 
 // record an event pair around a launch when timing is on
@@ -178,10 +191,24 @@ int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dt
 int apply_op2(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv);
 int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int degree, double a,
                 double b, double a0, int flags);
+int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
+                        const double* a, const double* b, const double* a0, int flags);
+int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
 
 // tensor-core cell products (cell_mma.cu)
+struct MmaK {              // one k-point of a batched launch
+  const void* H;           // BF16x3 cell matrices
+  const float* X;          // FP32 / complex64 vectors
+  float* Z;                // per-cell products
+  int ldx, nv, vblocks;
+  long long tile0;         // first tile of this k-point
+};
 int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z);
-size_t cell_mma_smem(bool cplx);
+int launch_cell_mma_multi(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntiles, bool cplx, int nb, int grid,
+                          cudaStream_t st);
+size_t cell_mma_smem(bool cplx, int nb);
+int launch_cell_mma_ptrs(oefe_ctx* c, const void* H, const void* X, int ldx, int nv, void* Z, bool cplx, int nb,
+                         cudaStream_t st);
 
 // projected eigenproblems on the GPU (eigh.cu)
 template <typename S>

@@ -84,3 +84,44 @@ def test_tensor_four_m_tiles():
     Xd = to_gpu(X, torch.complex64)
     ctx.chebyshev_filter(0, Xd, 1, 0.0, 500.0, -50.0, flags=FILTER_BF16X3)
     assert colerr(Xd.cpu().numpy().astype(np.complex128), ref) < TOL_DEGREE1
+
+
+KS2 = [(0.3, 0.0, 0.0), (-0.3, 0.1, 0.0)]
+
+
+@pytest.mark.parametrize("last_fp64", [False, True])
+def test_batched_multik_filter(last_fp64):
+    # all k-points in one persistent launch per degree, uneven vector counts, graph replay
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64
+    prs, ctx, V, _ = paired(ks=KS2)
+    nvs = [20, 37]
+    Xs = [W.random_vectors(pr.n, nv, complex_=True, seed=10 + i) for i, (pr, nv) in enumerate(zip(prs, nvs))]
+    bnds = [bounds(pr) for pr in prs]
+    deg = 7
+    refs = [solver.chebyshev_filter(pr.apply_A, X, deg, *bd) for pr, X, bd in zip(prs, Xs, bnds)]
+    dt = torch.complex128 if last_fp64 else torch.complex64
+    flags = FILTER_BF16X3 | (FILTER_LAST_FP64 if last_fp64 else 0)
+    for rep in range(2):   # the second call replays the captured graph
+        Xd = [to_gpu(X, dt) for X in Xs]
+        ctx.filter_batched(Xd, deg, [bd[0] for bd in bnds], [bd[1] for bd in bnds], [bd[2] for bd in bnds], flags)
+        for k in range(2):
+            out = Xd[k].cpu().numpy().astype(np.complex128)
+            assert colerr(out, refs[k]) < TOL_FILTER, (rep, k)
+        # the batched path computes the same products as the per-k path
+        Xs1 = to_gpu(Xs[1], dt)
+        ctx.chebyshev_filter(1, Xs1, deg, *bnds[1], flags=flags)
+        assert colerr(Xd[1].cpu().numpy().astype(np.complex128), Xs1.cpu().numpy().astype(np.complex128)) < 1e-6
+
+
+def test_autotune_then_batched_real():
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    prs, ctx, V, _ = paired()
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 70, seed=4)
+    ms = ctx.filter_autotune([to_gpu(X, torch.float32)])
+    assert np.all(ms > 0)
+    a, b, a0 = bounds(pr)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 5, a, b, a0)
+    Xd = to_gpu(X, torch.float32)
+    ctx.filter_batched([Xd], 5, a, b, a0, FILTER_BF16X3)
+    assert colerr(Xd.cpu().numpy().astype(np.float64), ref) < TOL_FILTER

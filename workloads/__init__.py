@@ -134,8 +134,8 @@ def config_c3_small():
     w = config_c2()
     w.name = "c3small_8atom_8cube_p6_1k"
     w.ncell = 8
-    w.nv = [64]
-    w.kgrid = (1, 1, 1)
+    w.nv = [64, 64]
+    w.kgrid = (2, 1, 1)
     w.dtype = "c64"
     return w
 
