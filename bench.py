@@ -133,7 +133,7 @@ def run_ours(args, rank, world):
     bks = []
     for ik in range(nk):
         v0 = torch.tensor(W.random_vectors(n, 1, complex_=True, seed=100 + ik), dtype=torch.complex128, device="cuda")
-        bks.append(ctx.upper_bound(ik, v0, 20))
+        bks.append(ctx.upper_bound(ik, v0, 20, P.FILTER_BF16X3 if args.tensor else 0))
     a_lo, a0 = 0.0, -0.5 * float(max(w.Z)) ** 2 - 1.0
     rho = torch.zeros(len(qw), dtype=torch.float64, device="cuda")
     gV = torch.zeros_like(rho)

@@ -218,8 +218,10 @@ int oefe_occupations(int nk, const int* nv, const double* eig, const double* w, 
 
 /* oefe_upper_bound -- b >= max eig of (M^O)^{-1} H^O: largest Ritz value of
  * a `steps`-step Lanczos run in the M inner product from v0 (device, n
- * F64/C128) plus the last residual norm. FP64. */
-int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, double* b);
+ * F64/C128) plus the last residual norm. The recurrence is FP64; flags = 0
+ * applies A in FP64, OEFE_FILTER_BF16X3 applies it on the tensor cores
+ * (BF16x3, relative error ~1e-5: enough for a filter bound). */
+int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, int flags, double* b);
 
 /* ---------------------------------------------------------------- timing
  * oefe_kernel_timing -- CUDA-event timing of the cell-product kernel (the

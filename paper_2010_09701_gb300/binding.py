@@ -51,7 +51,7 @@ SIGNATURES = [
     ("oefe_rayleigh_ritz", _I, [_P, _I, _P, _I, _I, _I, _DP, _DP]),
     ("oefe_density", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP, _P]),
     ("oefe_band_trace_grad", _I, [_P, _I, _P, _I, _I, _I, _P]),
-    ("oefe_upper_bound", _I, [_P, _I, _P, _I, _DP]),
+    ("oefe_upper_bound", _I, [_P, _I, _P, _I, _I, _DP]),
     ("oefe_occupations", _I, [_I, _IP, _DP, _DP, _D, _D, _DP, _DP, _DP]),
     ("oefe_kernel_timing", _I, [_P, _I]),
     ("oefe_kernel_time", _I, [_P, _DP, _I64P]),
@@ -338,8 +338,8 @@ class Context:
         self._check(self.lib.oefe_kernel_time(self.h, ctypes.byref(ms), ctypes.byref(n)))
         return ms.value, n.value
 
-    def upper_bound(self, ik, v0, steps=20):
+    def upper_bound(self, ik, v0, steps=20, flags=0):
         b = ctypes.c_double()
         self._check(self.lib.oefe_upper_bound(self.h, int(ik), ctypes.c_void_p(v0.data_ptr()), int(steps),
-                                              ctypes.byref(b)))
+                                              int(flags), ctypes.byref(b)))
         return b.value

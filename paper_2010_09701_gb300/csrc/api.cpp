@@ -15,6 +15,7 @@
 static void free_all(oefe_ctx* c) {
   for (auto& K : c->kd) {
     dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf);
+    dev_free(K.E0);
   }
   c->kd.clear();
   void* ptrs[] = {c->d_gll, c->d_m, c->d_cell_nodes, c->d_cellbox, c->d_pos, c->d_lm, c->d_R, c->d_dR,
@@ -253,9 +254,9 @@ int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, 
   return band_trace_grad(ctx, ik, X, nv, ld, dtype, gV);
 }
 
-int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, double* b) {
+int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, int flags, double* b) {
   CTX_CHECK(ctx);
-  return upper_bound(ctx, ik, v0, steps, b);
+  return upper_bound(ctx, ik, v0, steps, flags, b);
 }
 
 int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask) {

@@ -19,7 +19,7 @@ namespace {
 constexpr int MAXP = 8;     // P = p + 1 <= 8
 constexpr int MAXN1 = 12;   // Gauss points per axis per leaf
 constexpr int BT = 256;     // threads per CTA of the cell kernels
-constexpr size_t SMEM_BUILD = 200 * 1024;
+constexpr size_t SMEM_BUILD = 212 * 1024;
 
 // Tabulate N^A and grad N^A for (point, active function) pairs of a batch of cells.
 // tab entry layout: 4 complex values (value, d/dx, d/dy, d/dz) per (q, j), j fastest.
@@ -57,7 +57,7 @@ struct BuildArgs {
   const int* leaf_off;
   const double* qxyz;
   const double* qw;
-  const double* veff;       // null in orthogonalization mode
+  const double* veff;       // null in the setup mode
   const double* cellbox;
   const double* gll;
   const double* gauss_w;    // [n][i] table, 13 x 12
@@ -67,13 +67,21 @@ struct BuildArgs {
   const cd* tab;
   int e0, P, nloc, npad, ne_max;
   double k[3];
-  int mode;                 // 0: H blocks, 1: d and M^AA blocks
+  int mode;                 // 0: V-dependent blocks + cached rest -> HE; 1: setup (d, M^AA, V-independent blocks)
   cd* HE;                   // mode 0: (batch, npad, npad)
   cd* dblk;                 // mode 1: (ncells, nloc, ne_max)
   cd* MAAblk;               // mode 1: (ncells, ne_max, ne_max)
+  cd* E0;                   // per cell: V-independent CA (nloc x ne_max) then AA (ne_max x ne_max)
 };
 
-// One CTA per cell: accumulate the cell's blocks over its tensor-product leaves.
+// One CTA per cell, accumulating over the cell's tensor-product leaves.
+//
+// Setup (mode 1, once per k): d = int N^C N^A and M^AA = int conj(N^A) N^A for
+// the orthogonalization, and the V-independent parts of the enrichment
+// blocks of Eq. HOEFEelelements (kinetic and k terms) into the cache E0.
+// Build (mode 0, per V): the CC block (kinetic, k term and the potential
+// term on the leaf points, by sum factorization; Hermitian half computed),
+// the potential parts of the CA and AA blocks, plus the cached E0.
 __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   extern __shared__ double smem[];
   const int b = blockIdx.x;
@@ -83,8 +91,10 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   const double* box = A.cellbox + 6 * e;
   const double kk = A.k[0] * A.k[0] + A.k[1] * A.k[1] + A.k[2] * A.k[2];
   const bool kz = kk == 0.0;
+  const size_t e0s = (size_t)nloc * A.ne_max + (size_t)A.ne_max * A.ne_max;
+  cd* CA0 = A.E0 + (size_t)e * e0s;                 // nloc x ne_max
+  cd* AA0 = CA0 + (size_t)nloc * A.ne_max;          // ne_max x ne_max
 
-  // small tables
   __shared__ double Lt[3][MAXN1][MAXP], Dt[3][MAXN1][MAXP], w1[3][MAXN1];
   __shared__ double Mm[3][MAXP][MAXP], Km[3][MAXP][MAXP], Am[3][MAXP][MAXP];
   __shared__ double xn[MAXP];
@@ -96,8 +106,8 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   if (A.mode == 0) {
     for (int i = threadIdx.x; i < npad * npad; i += BT) HE[i] = mkc(0, 0);
   } else {
-    for (int i = threadIdx.x; i < nloc * A.ne_max; i += BT) dB[i] = mkc(0, 0);
-    for (int i = threadIdx.x; i < A.ne_max * A.ne_max; i += BT) MB[i] = mkc(0, 0);
+    for (int i = threadIdx.x; i < nloc * A.ne_max; i += BT) { dB[i] = mkc(0, 0); CA0[i] = mkc(0, 0); }
+    for (int i = threadIdx.x; i < A.ne_max * A.ne_max; i += BT) { MB[i] = mkc(0, 0); AA0[i] = mkc(0, 0); }
   }
   __syncthreads();
 
@@ -166,8 +176,10 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
         }
         __syncthreads();
         const bool first = qx0 == 0;
+        // Hermitian half: entries m <= n, mirrored
         for (int t = threadIdx.x; t < nloc * nloc; t += BT) {
           const int m = t / nloc, n = t % nloc;
+          if (m > n) continue;
           const int a = m % P, bb = (m / P) % P, c = m / P2;
           const int a2 = n % P, b2 = (n / P) % P, c2 = n / P2;
           const int ridx = (bb * P + b2) * P2 + c * P + c2;
@@ -185,120 +197,198 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
           cd* h = HE + (size_t)m * npad + n;
           h->x += v;
           h->y += im;
+          if (m != n) {
+            cd* h2 = HE + (size_t)n * npad + m;
+            h2->x += v;
+            h2->y -= im;
+          }
         }
         __syncthreads();
       }
     }
 
     // enrichment columns: staged contraction of the CFE factors against the
-    // enrichment fields of the leaf (mode 0: H_CA; mode 1: d = int N^C N^A)
+    // enrichment fields of the leaf.
+    //   mode 0: F0 = w (V + |k|^2/2) N                                 -> CA (potential part)
+    //   mode 1: F0 = -(i/2) w k.grad N, F_d = w (grad_d N / 2 + (i/2) k_d N) -> CA0;  Fd = w N -> d
     {
-      cd* F = reinterpret_cast<cd*>(smem);     // 4 fields * n3
-      cd* G = F + 4 * n3;                      // 4 * n2 * P
+      cd* F = reinterpret_cast<cd*>(smem);     // 5 fields * n3
+      cd* G = F + 5 * n3;                      // 4 * n2 * P
       cd* Hs = G + 4 * n2 * P;                 // 3 * n1 * P * P
-      const int nf = A.mode == 0 ? 4 : 1;
+      const bool full = A.mode == 1;
       for (int j = 0; j < ne; ++j) {
         for (int q = threadIdx.x; q < n3; q += BT) {
           const cd* tq = tabc + 4 * ((ql0 + q) * ne + j);
           const double w = A.qw[q0 + q];
-          if (A.mode == 0) {
-            const double vk = A.veff[q0 + q] + 0.5 * kk;
+          if (!full) {
+            F[q] = (w * (A.veff[q0 + q] + 0.5 * kk)) * tq[0];
+          } else {
             const cd N = tq[0];
             const cd kg = A.k[0] * tq[1] + A.k[1] * tq[2] + A.k[2] * tq[3];
-            // F0 = w (Vk N - (i/2) k.grad N), F_d = w (grad_d N / 2 + (i/2) k_d N)
-            F[q] = w * (vk * N - mkc(0, 0.5) * kg);
+            F[q] = w * (mkc(0, -0.5) * kg);
             for (int d = 0; d < 3; ++d) F[(1 + d) * n3 + q] = w * (0.5 * tq[1 + d] + mkc(0, 0.5 * A.k[d]) * N);
-          } else {
-            F[q] = w * tq[0];
+            F[4 * n3 + q] = w * N;
           }
         }
         __syncthreads();
         // stage z: (qx,qy,c)
         for (int t = threadIdx.x; t < n2 * P; t += BT) {
           const int qxy = t / P, c = t % P;
-          cd g0 = mkc(0, 0), gx = mkc(0, 0), gy = mkc(0, 0), gz = mkc(0, 0);
+          cd g0 = mkc(0, 0), gx = mkc(0, 0), gy = mkc(0, 0), gz = mkc(0, 0), gd = mkc(0, 0);
           for (int qz = 0; qz < n1; ++qz) {
             const int q = qxy + n2 * qz;
             const double l = Lt[2][qz][c];
             g0 += l * F[q];
-            if (nf == 4) {
+            if (full) {
               gx += l * F[n3 + q];
               gy += l * F[2 * n3 + q];
               gz += Dt[2][qz][c] * F[3 * n3 + q];
+              gd += l * F[4 * n3 + q];
             }
           }
           G[t] = g0 + gz;
-          if (nf == 4) {
+          if (full) {
             G[n2 * P + t] = gx;
             G[2 * n2 * P + t] = gy;
+            G[3 * n2 * P + t] = gd;
           }
         }
         __syncthreads();
         // stage y: (qx,b,c)
         for (int t = threadIdx.x; t < n1 * P * P; t += BT) {
           const int qx = t / (P * P), bb = (t / P) % P, c = t % P;
-          cd h0 = mkc(0, 0), hx = mkc(0, 0), hy = mkc(0, 0);
+          cd h0 = mkc(0, 0), hx = mkc(0, 0), hy = mkc(0, 0), hd = mkc(0, 0);
           for (int qy = 0; qy < n1; ++qy) {
             const int g = (qx + n1 * qy) * P + c;
             h0 += Lt[1][qy][bb] * G[g];
-            if (nf == 4) {
+            if (full) {
               hx += Lt[1][qy][bb] * G[n2 * P + g];
               hy += Dt[1][qy][bb] * G[2 * n2 * P + g];
+              hd += Lt[1][qy][bb] * G[3 * n2 * P + g];
             }
           }
           Hs[t] = h0 + hy;
-          if (nf == 4) Hs[n1 * P * P + t] = hx;
+          if (full) {
+            Hs[n1 * P * P + t] = hx;
+            Hs[2 * n1 * P * P + t] = hd;
+          }
         }
         __syncthreads();
         // stage x: (a,b,c) -> local node a + P (b + P c)
         for (int m = threadIdx.x; m < nloc; m += BT) {
-          const int a = m % P, bc = m / P;  // bc = b + P c
+          const int a = m % P, bc = m / P;
           const int bb = bc % P, c = bc / P;
-          cd s = mkc(0, 0);
+          cd s = mkc(0, 0), sd = mkc(0, 0);
           for (int qx = 0; qx < n1; ++qx) {
             const int hidx = (qx * P + bb) * P + c;
             s += Lt[0][qx][a] * Hs[hidx];
-            if (nf == 4) s += Dt[0][qx][a] * Hs[n1 * P * P + hidx];
+            if (full) {
+              s += Dt[0][qx][a] * Hs[n1 * P * P + hidx];
+              sd += Lt[0][qx][a] * Hs[2 * n1 * P * P + hidx];
+            }
           }
-          if (A.mode == 0) HE[(size_t)m * npad + nloc + j] += s;
-          else dB[(size_t)m * A.ne_max + j] += s;
+          if (!full) HE[(size_t)m * npad + nloc + j] += s;
+          else {
+            CA0[(size_t)m * A.ne_max + j] += s;
+            dB[(size_t)m * A.ne_max + j] += sd;
+          }
         }
         __syncthreads();
       }
     }
 
-    // enrichment-enrichment block: pairs (i <= j), points of the leaf
-    for (int t = threadIdx.x; t < ne * ne; t += BT) {
-      const int i = t / ne, j = t % ne;
-      if (i > j) continue;
-      cd s = mkc(0, 0);
-      for (int q = 0; q < n3; ++q) {
-        const cd* ti = tabc + 4 * ((ql0 + q) * ne + i);
-        const cd* tj = tabc + 4 * ((ql0 + q) * ne + j);
-        const double w = A.qw[q0 + q];
-        if (A.mode == 0) {
-          const double vk = A.veff[q0 + q] + 0.5 * kk;
-          cd v = 0.5 * (cmulc(ti[1], tj[1]) + cmulc(ti[2], tj[2]) + cmulc(ti[3], tj[3])) + vk * cmulc(ti[0], tj[0]);
-          if (!kz) {
-            const cd kgj = A.k[0] * tj[1] + A.k[1] * tj[2] + A.k[2] * tj[3];
-            const cd kgi = A.k[0] * ti[1] + A.k[1] * ti[2] + A.k[2] * ti[3];
-            const cd asym = cmulc(ti[0], kgj) - cmulc(kgi, tj[0]);
-            v += mkc(0, -0.5) * asym;
+    // enrichment-enrichment block: pairs (i <= j) over the leaf points, staged
+    // through shared memory in chunks of points
+    {
+      const bool full = A.mode == 1;
+      const int comps = full ? 4 : 1;
+      const int QC = max(1, min(32, (int)((SMEM_BUILD - 32 * 8) / ((size_t)max(ne, 1) * comps * sizeof(cd)))));
+      cd* Ns = reinterpret_cast<cd*>(smem);   // QC x ne x comps
+      double* Ws = reinterpret_cast<double*>(Ns + (size_t)QC * ne * comps);  // QC
+      const int npairs = ne * (ne + 1) / 2;
+      for (int pb = 0; pb < npairs; pb += 4 * BT) {
+        int pi[4], pj[4];
+        cd acc0[4], acc1[4];
+        for (int u = 0; u < 4; ++u) {
+          acc0[u] = mkc(0, 0);
+          acc1[u] = mkc(0, 0);
+          const int pp = pb + threadIdx.x + u * BT;
+          pi[u] = -1;
+          pj[u] = -1;
+          if (pp < npairs) {  // pair index -> (i, j), i <= j
+            int i = 0, rem = pp;
+            while (rem >= ne - i) { rem -= ne - i; ++i; }
+            pi[u] = i;
+            pj[u] = i + rem;
           }
-          s += w * v;
-        } else {
-          s += w * cmulc(ti[0], tj[0]);
+        }
+        for (int qc = 0; qc < n3; qc += QC) {
+          const int nq = min(QC, n3 - qc);
+          __syncthreads();
+          for (int t = threadIdx.x; t < nq * ne * comps; t += BT) {
+            const int q = t / (ne * comps), r = t % (ne * comps);
+            const int j = r / comps, cpt = r % comps;
+            Ns[t] = tabc[4 * ((ql0 + qc + q) * ne + j) + cpt];
+          }
+          for (int q = threadIdx.x; q < nq; q += BT) {
+            const double w = A.qw[q0 + qc + q];
+            Ws[q] = full ? w : w * (A.veff[q0 + qc + q] + 0.5 * kk);
+          }
+          __syncthreads();
+          for (int u = 0; u < 4; ++u) {
+            if (pi[u] < 0) continue;
+            const int i = pi[u], j = pj[u];
+            cd s0 = mkc(0, 0), s1 = mkc(0, 0);
+            for (int q = 0; q < nq; ++q) {
+              const cd* ti = Ns + ((size_t)q * ne + i) * comps;
+              const cd* tj = Ns + ((size_t)q * ne + j) * comps;
+              const double w = Ws[q];
+              if (!full) {
+                s0 += w * cmulc(ti[0], tj[0]);
+              } else {
+                cd v = 0.5 * (cmulc(ti[1], tj[1]) + cmulc(ti[2], tj[2]) + cmulc(ti[3], tj[3]));
+                if (!kz) {
+                  const cd kgj = A.k[0] * tj[1] + A.k[1] * tj[2] + A.k[2] * tj[3];
+                  const cd kgi = A.k[0] * ti[1] + A.k[1] * ti[2] + A.k[2] * ti[3];
+                  v += mkc(0, -0.5) * (cmulc(ti[0], kgj) - cmulc(kgi, tj[0]));
+                }
+                s0 += w * v;
+                s1 += w * cmulc(ti[0], tj[0]);
+              }
+            }
+            acc0[u] += s0;
+            acc1[u] += s1;
+          }
+        }
+        for (int u = 0; u < 4; ++u) {
+          if (pi[u] < 0) continue;
+          const int i = pi[u], j = pj[u];
+          if (!full) {
+            HE[(size_t)(nloc + i) * npad + nloc + j] += acc0[u];
+            if (i != j) HE[(size_t)(nloc + j) * npad + nloc + i] += cconj(acc0[u]);
+          } else {
+            AA0[i * A.ne_max + j] += acc0[u];
+            MB[i * A.ne_max + j] += acc1[u];
+            if (i != j) {
+              AA0[j * A.ne_max + i] += cconj(acc0[u]);
+              MB[j * A.ne_max + i] += cconj(acc1[u]);
+            }
+          }
         }
       }
-      if (A.mode == 0) {
-        HE[(size_t)(nloc + i) * npad + nloc + j] += s;
-        if (i != j) HE[(size_t)(nloc + j) * npad + nloc + i] += cconj(s);
-      } else {
-        MB[i * A.ne_max + j] += s;
-        if (i != j) MB[j * A.ne_max + i] += cconj(s);
-      }
+      __syncthreads();
     }
-    __syncthreads();
+  }
+  if (A.mode == 0) {
+    // cached V-independent enrichment blocks
+    for (int t = threadIdx.x; t < nloc * ne; t += BT) {
+      const int m = t / ne, j = t % ne;
+      HE[(size_t)m * npad + nloc + j] += CA0[(size_t)m * A.ne_max + j];
+    }
+    for (int t = threadIdx.x; t < ne * ne; t += BT) {
+      const int i = t / ne, j = t % ne;
+      HE[(size_t)(nloc + i) * npad + nloc + j] += AA0[i * A.ne_max + j];
+    }
   }
 }
 
@@ -511,8 +601,9 @@ static size_t smem_build_bytes(const oefe_ctx* c) {
   const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
   const size_t n3 = (size_t)n1 * n1 * n1, n2 = (size_t)n1 * n1;
   const size_t phase_cc = std::min(SMEM_BUILD, (n3 + n2 * P * P + (size_t)n1 * P * P * P * P) * 8);
-  const size_t phase_ca = (4 * n3 + 4 * n2 * P + 3 * (size_t)n1 * P * P) * 16;
-  return std::max(phase_cc, phase_ca);
+  const size_t phase_ca = (5 * n3 + 4 * n2 * P + 3 * (size_t)n1 * P * P) * 16;
+  const size_t phase_aa = 32 * (size_t)std::max(c->ne_max, 1) * 4 * 16 + 32 * 8;
+  return std::max(std::max(phase_cc, phase_ca), phase_aa);
 }
 
 // Process cells in batches bounded by a scratch budget; calls fn(e0, e1, tab_off_host).
@@ -600,6 +691,7 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     A.HE = mode == 0 ? HE : nullptr;
     A.dblk = dblk;
     A.MAAblk = MAAblk;
+    A.E0 = (cd*)K.E0;
     k_build_cell<<<nb, BT, smem, c->stream>>>(A);
     OEFE_CUDA_TRY(c, cudaGetLastError());
     if (mode == 0) {
@@ -624,7 +716,8 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
   if (!c->has_quad) { c->err = "kpoints: call oefe_quadrature first"; return OEFE_ERR_STATE; }
   if (nk < 1 || nk > 4096 || !k || !w) { c->err = "kpoints: need 1 <= nk <= 4096, k, w"; return OEFE_ERR_ARG; }
   for (auto& K : c->kd) {
-    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32);
+    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf);
+    dev_free(K.E0);
   }
   c->kd.assign(nk, KData());
   double* d_gw = nullptr;
@@ -641,6 +734,10 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
     K.cplx = !(K.k[0] == 0.0 && K.k[1] == 0.0 && K.k[2] == 0.0);
     const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);
     st = dev_alloc(c, (void**)&K.gamma, (size_t)c->ncells * c->nloc * std::max(c->ne_max, 1) * sb);
+    if (st == OEFE_OK)
+      st = dev_alloc(c, (void**)&K.E0, (size_t)c->ncells *
+                                           ((size_t)c->nloc * std::max(c->ne_max, 1) + (size_t)c->ne_max * c->ne_max) *
+                                           sizeof(cd));
     if (st == OEFE_OK) st = dev_alloc(c, (void**)&K.Moo, (size_t)std::max(c->nO * c->nO, 1) * sb);
     if (st == OEFE_OK) st = dev_alloc(c, (void**)&K.Mooinv, (size_t)std::max(c->nO * c->nO, 1) * sb);
     if (st != OEFE_OK || c->nO == 0) continue;

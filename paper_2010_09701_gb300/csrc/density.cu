@@ -26,7 +26,7 @@ struct FieldArgs {
   const int* cell_nodes;
   const int* act_off;
   const int* act_idx;
-  int ncells, P, nloc, ne_max, nbd;
+  int ncells, nleaves, P, nloc, ne_max, nbd;
   int64_t nh;
   double k[3];
   const void* X;      // F64 or C128 rows, ld
@@ -56,11 +56,13 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
   if (threadIdx.x < A.P) xn[threadIdx.x] = A.gll[threadIdx.x];
   const int P = A.P, nloc = A.nloc, NB = A.nbd;
   cd* na = A.na + (size_t)blockIdx.x * A.na_stride;
-  for (int e = blockIdx.x; e < A.ncells; e += gridDim.x) {
+  // leaves are independent (each owns its points): balance the work over leaves
+  for (int li = blockIdx.x; li < A.nleaves; li += gridDim.x) {
+    const Leaf L = A.leaves[li];
+    const int e = L.cell;
     const int ne = A.act_off[e + 1] - A.act_off[e];
     const double* box = A.cellbox + 6 * e;
-    for (int li = A.leaf_off[e]; li < A.leaf_off[e + 1]; ++li) {
-      const Leaf L = A.leaves[li];
+    {
       const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
       __syncthreads();
       if (threadIdx.x < 3 * n1) {
@@ -162,7 +164,7 @@ int run_fields(oefe_ctx* c, const KData& K, int kidx, const void* X, int nv, int
   while (nb > 1 && field_smem(c, nb) > 200 * 1024) nb /= 2;
   const size_t smem = field_smem(c, nb);
   if (smem > 220 * 1024) { c->err = "fields: quadrature too large for the interpolation tiles"; return OEFE_ERR_ARG; }
-  const int grid = std::max(1, std::min(c->ncells, 2 * c->num_sms));
+  const int grid = std::max(1, std::min((int)c->leaves.size(), 2 * c->num_sms));
   const int n1 = std::max(c->nq_cell, c->nq_enr);
   const int64_t stride = (int64_t)n1 * n1 * n1 * std::max(c->ne_max, 1);
   OEFE_TRY(ensure_ws2(c, (size_t)grid * stride * sizeof(cd) + 256));
@@ -179,6 +181,7 @@ int run_fields(oefe_ctx* c, const KData& K, int kidx, const void* X, int nv, int
   A.act_off = c->d_act_off;
   A.act_idx = c->d_act_idx;
   A.ncells = c->ncells;
+  A.nleaves = (int)c->leaves.size();
   A.P = c->P;
   A.nloc = c->nloc;
   A.ne_max = std::max(c->ne_max, 1);

@@ -376,6 +376,17 @@ int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dt
   return apply_op2(c, ik, X, ld, Y, ld, nv, dtype, minv);
 }
 
+// Y = M^{-1} H X for one low-precision column through the tensor-core products
+int apply_low(oefe_ctx* c, int ik, const void* X, void* Y, int dtype) {
+  const size_t es = dtype_bytes(dtype);
+  const size_t zbytes = (((size_t)c->ncells * c->npad * es + 255) / 256) * 256;
+  const size_t yobytes = (size_t)std::max(c->nO, 1) * sizeof(cd);
+  OEFE_TRY(ensure_ws(c, zbytes + yobytes + 256));
+  char* base = (char*)c->ws;
+  Step st{1, 1.0, 0.0, 0.0};
+  return dispatch_step(c, c->kd[ik], dtype, X, 1, 1, st, nullptr, 0, nullptr, 0, Y, 1, base, (cd*)(base + zbytes), true);
+}
+
 namespace {
 
 // Degrees [j0, j1] of the scaled recurrence on buffers of one dtype. bufs[ip]

@@ -233,6 +233,44 @@ __global__ void k_lanczos_axpy(double* x, const double* y, const double* z, doub
   (void)unused;
 }
 
+__global__ void k_to_float(const double* x, float* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (float)x[i];
+}
+
+__global__ void k_to_double(const float* x, double* y, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = (double)x[i];
+}
+
+// Re(x^+ y) over interleaved reals: partial sums per block, then one block sums them.
+__global__ void k_dot_partial(const double* x, const double* y, int64_t n, double* part) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += x[i] * y[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) part[blockIdx.x] = red[0];
+}
+
+__global__ void k_dot_final(const double* part, int nb, double* out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s += part[i];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 // ------------------------------------------------------------------ host helpers
 template <typename S>
 int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, S* part_buf,
@@ -410,52 +448,57 @@ int rayleigh_ritz(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, doubl
   return rayleigh_ritz_t<double>(c, ik, (double*)X, nv, ld, dtype, eig, resid);
 }
 
-int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, double* b) {
+int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, double* b) {
   const int dtype = (ik >= 0 && ik < (int)c->kd.size() && c->kd[ik].cplx) ? OEFE_C128 : OEFE_F64;
   OEFE_TRY(check_fp64(c, ik, v0, 1, 1, dtype));
   if (steps < 2 || steps > 1000 || !b) { c->err = "upper_bound: 2 <= steps <= 1000"; return OEFE_ERR_ARG; }
+  const bool low = (flags & OEFE_FILTER_BF16X3) != 0;
+  const KData& K = c->kd[ik];
+  if (low && !K.Hbf) { c->err = "upper_bound: BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
   const int64_t n = c->nh + c->nO;
   const size_t sb = dtype == OEFE_C128 ? sizeof(cd) : sizeof(double);
   const size_t vb = (((size_t)n * sb + 255) / 256) * 256;
-  OEFE_TRY(ensure_ws2(c, 4 * vb + 4096));
+  const int nparts = 1024;
+  OEFE_TRY(ensure_ws2(c, 6 * vb + (nparts + 64) * sizeof(double)));
   char* base = (char*)c->ws2;
   void* q = base;
   void* qp = base + vb;
   void* w = base + 2 * vb;
   void* mw = base + 3 * vb;
-  double* d_dot = (double*)(base + 4 * vb);
-  const KData& K = c->kd[ik];
+  float* q32 = (float*)(base + 4 * vb);          // low-precision copies (half of vb each)
+  float* w32 = (float*)(base + 5 * vb);
+  double* d_part = (double*)(base + 6 * vb);
+  double* d_dot = d_part + nparts;
+  const int nr = dtype == OEFE_C128 ? 2 : 1;  // reals per entry
+  const int64_t nreal = n * nr;
   std::vector<double> al, be;
-  // q = v0 / ||v0||_M
   auto mdot = [&](const void* x, const void* y, double* out) -> int {  // re(x^+ M y)
-    if (dtype == OEFE_C128) {
-      OEFE_TRY(apply_M<cd>(c, K, (const cd*)y, 1, 1, (cd*)mw, 1));
-      OEFE_TRY(gram<cd>(c, (const cd*)x, 1, (const cd*)mw, 1, n, 1, (cd*)d_dot, (cd*)(d_dot + 16), 32));
-      cd h;
-      OEFE_CUDA_TRY(c, cudaMemcpyAsync(&h, d_dot, sizeof(cd), cudaMemcpyDeviceToHost, c->stream));
-      OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-      *out = h.x;
-    } else {
-      OEFE_TRY(apply_M<double>(c, K, (const double*)y, 1, 1, (double*)mw, 1));
-      OEFE_TRY(gram<double>(c, (const double*)x, 1, (const double*)mw, 1, n, 1, d_dot, d_dot + 16, 32));
-      double h;
-      OEFE_CUDA_TRY(c, cudaMemcpyAsync(&h, d_dot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-      *out = h;
-    }
+    if (dtype == OEFE_C128) OEFE_TRY(apply_M<cd>(c, K, (const cd*)y, 1, 1, (cd*)mw, 1));
+    else OEFE_TRY(apply_M<double>(c, K, (const double*)y, 1, 1, (double*)mw, 1));
+    k_dot_partial<<<nparts, 256, 0, c->stream>>>((const double*)x, (const double*)mw, nreal, d_part);
+    k_dot_final<<<1, 256, 0, c->stream>>>(d_part, nparts, d_dot);
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(out, d_dot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    return OEFE_OK;
+  };
+  auto applyA = [&]() -> int {  // w = M^{-1} H q
+    if (!low) return apply_op2(c, ik, q, 1, w, 1, 1, dtype, true);
+    const int lb2 = (int)std::min<int64_t>((nreal + 255) / 256, (int64_t)c->num_sms * 16);
+    k_to_float<<<lb2, 256, 0, c->stream>>>((const double*)q, q32, nreal);
+    OEFE_TRY(apply_low(c, ik, q32, w32, dtype == OEFE_C128 ? OEFE_C64 : OEFE_F32));
+    k_to_double<<<lb2, 256, 0, c->stream>>>(w32, (double*)w, nreal);
+    OEFE_CUDA_TRY(c, cudaGetLastError());
     return OEFE_OK;
   };
   OEFE_CUDA_TRY(c, cudaMemcpyAsync(q, v0, n * sb, cudaMemcpyDeviceToDevice, c->stream));
   OEFE_CUDA_TRY(c, cudaMemsetAsync(qp, 0, n * sb, c->stream));
   double nrm;
   OEFE_TRY(mdot(q, q, &nrm));
-  const int nr = dtype == OEFE_C128 ? 2 : 1;  // reals per entry
-  const int64_t nreal = n * nr;
   const int lb = (int)std::min<int64_t>((nreal + 255) / 256, (int64_t)c->num_sms * 16);
   k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, nullptr, nullptr, nullptr, nreal, 1.0 / std::sqrt(nrm), 0, 0);
   double beta = 0.0;
   for (int it = 0; it < steps; ++it) {
-    OEFE_TRY(apply_op2(c, ik, q, 1, w, 1, 1, dtype, true));
+    OEFE_TRY(applyA());
     double alpha;
     OEFE_TRY(mdot(q, w, &alpha));
     // w <- w - alpha q - beta qp

@@ -64,6 +64,7 @@ struct KData {
   double* H64 = nullptr;     // (ncells, npad, npad) scalars
   float* H32 = nullptr;      // (ncells, npad, npad) float or cf
   void* Hbf = nullptr;       // (ncells, planes, npad, npad) bf16: (re hi, re lo[, im hi, im lo])
+  void* E0 = nullptr;        // per cell: V-independent enrichment blocks (cd), CA then AA
   bool built = false;
 };
 
@@ -189,6 +190,8 @@ int chol_inverse_inplace(oefe_ctx* c, double* A, int n, bool cplx, bool inverse,
 // operator application and filter (filter.cu)
 int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dtype, bool minv);
 int apply_op2(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv);
+int apply_low(oefe_ctx* c, int ik, const void* X, void* Y, int dtype);
+
 int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int degree, double a,
                 double b, double a0, int flags);
 int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
@@ -218,7 +221,7 @@ int gpu_tridiag_eig(oefe_ctx* c, const std::vector<double>& al, const std::vecto
 // subspace (linalg.cu)
 int orthonormalize(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* cond);
 int rayleigh_ritz(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, double* eig, double* resid);
-int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, double* b);
+int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, double* b);
 
 // fields (density.cu)
 int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype,

@@ -125,3 +125,17 @@ def test_autotune_then_batched_real():
     Xd = to_gpu(X, torch.float32)
     ctx.filter_batched([Xd], 5, a, b, a0, FILTER_BF16X3)
     assert colerr(Xd.cpu().numpy().astype(np.float64), ref) < TOL_FILTER
+
+
+def test_upper_bound_tensor_products():
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    import scipy.linalg as sla
+    prs, ctx, V, _ = paired(ks=[(0.25, -0.4, 0.1)])
+    pr = prs[0]
+    ev = sla.eigh(pr.assemble_H().toarray(), pr.dense_M(), eigvals_only=True)
+    v0 = to_gpu(W.random_vectors(pr.n, 1, complex_=True, seed=3))
+    b64 = ctx.upper_bound(0, v0, 30)
+    b16 = ctx.upper_bound(0, v0, 30, FILTER_BF16X3)
+    # theta_max + beta_last is a valid but loose bound; the low-precision run keeps it valid
+    assert ev[-1] * (1 - 1e-4) <= b16 < 1.5 * ev[-1]
+    assert ev[-1] * (1 - 1e-8) <= b64 < 1.5 * ev[-1]
