@@ -140,6 +140,31 @@ int oefe_overlap(oefe_ctx_t ctx, int ik, double* m, void* Moo);
 int oefe_apply_h(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld, int dtype);
 int oefe_apply_a(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld, int dtype);
 
+/* oefe_apply_a_noalloc -- the same Y = (M^O)^{-1} H^O X as oefe_apply_a, for
+ * callers that cannot allocate device memory at this point: an application
+ * whose memory pool already owns the whole device, a service that must not
+ * take the implicit device synchronization of cudaMalloc / cudaFree in its
+ * request path, or a host framework that forbids allocation once it runs.
+ * The paper has no counterpart; this is a deployment variant.
+ * It allocates nothing: the per-cell products and the enrichment-row sums
+ * that oefe_apply_a keeps in its growing workspace live in one fixed device
+ * array of OEFE_NOALLOC_SCRATCH_BYTES bytes, compiled into the library and
+ * resident on every device that loads it until the process exits. The
+ * caller passes X and Y as for oefe_apply_a (the context itself was set up
+ * earlier with allocations, as always).
+ * - The first call on a device looks up the array's device address on that
+ *   device (cudaGetSymbolAddress); make that first call outside any stream
+ *   capture.
+ * - Problems needing more than the array (ncells * npad * nv * sizeof(scalar)
+ *   rounded up to 256 bytes, plus n_O * nv * 16 bytes) are refused with
+ *   OEFE_ERR_ARG; oefe_last_error gives the sizes.
+ * - Every call uses the same array and overwrites what it reads (nothing
+ *   needs to start at zero); calls whose GPU work overlaps (other streams,
+ *   other contexts, other threads) race on it and must be serialized by the
+ *   caller. The call synchronizes the context's stream before returning. */
+#define OEFE_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+int oefe_apply_a_noalloc(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld, int dtype);
+
 /* ---------------------------------------------------------------- filter
  * oefe_chebyshev_filter -- X <- p_m(A) X in place, A = (M^O)^{-1} H^O
  * (Sec. IV), with the scaled three-term recurrence: e = (b-a)/2,

@@ -16,6 +16,7 @@ OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_CHOLESKY, ERR_NOTPD_MOO, ERR_TIME
 F64, F32, C128, C64 = 0, 1, 2, 3
 STORE_F64, STORE_F32, STORE_BF16X3 = 1, 2, 4
 FILTER_LAST_FP64, FILTER_BF16X3 = 1, 2
+NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
 # every symbol of include/oefe.h: (name, restype, argtypes)
 _c = ctypes
@@ -44,6 +45,7 @@ SIGNATURES = [
     ("oefe_overlap", _I, [_P, _I, _DP, _P]),
     ("oefe_apply_h", _I, [_P, _I, _P, _P, _I, _I, _I]),
     ("oefe_apply_a", _I, [_P, _I, _P, _P, _I, _I, _I]),
+    ("oefe_apply_a_noalloc", _I, [_P, _I, _P, _P, _I, _I, _I]),
     ("oefe_chebyshev_filter", _I, [_P, _I, _P, _I, _I, _I, _I, _D, _D, _D, _I]),
     ("oefe_filter_batched", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _I, _DP, _DP, _DP, _I]),
     ("oefe_filter_autotune", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP]),
@@ -255,6 +257,17 @@ class Context:
         if (nv2, ld2, dt2) != (nv, ld, dt):
             raise ValueError("X and Y must have the same shape, strides and dtype")
         self._check(self.lib.oefe_apply_a(self.h, int(ik), px, py, nv, ld, dt))
+        return Y
+
+    def apply_a_noalloc(self, ik, X, Y):
+        """Y = (M^O)^{-1} H^O X without any device allocation: the library's
+        scratch is a fixed device array (NOALLOC_SCRATCH_BYTES), shared by every
+        call, for callers that cannot allocate device memory."""
+        px, nv, ld, dt = _block(X)
+        py, nv2, ld2, dt2 = _block(Y)
+        if (nv2, ld2, dt2) != (nv, ld, dt):
+            raise ValueError("X and Y must have the same shape, strides and dtype")
+        self._check(self.lib.oefe_apply_a_noalloc(self.h, int(ik), px, py, nv, ld, dt))
         return Y
 
     def chebyshev_filter(self, ik, X, degree, a, b, a0, flags=0):

@@ -216,6 +216,11 @@ int oefe_apply_a(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld,
   return apply_op(ctx, ik, X, Y, nv, ld, dtype, true);
 }
 
+int oefe_apply_a_noalloc(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld, int dtype) {
+  CTX_CHECK(ctx);
+  return apply_a_noalloc(ctx, ik, X, Y, nv, ld, dtype);
+}
+
 int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, int degree, double a, double b,
                           double a0, int flags) {
   CTX_CHECK(ctx);

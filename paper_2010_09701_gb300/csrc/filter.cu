@@ -376,6 +376,27 @@ int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dt
   return apply_op2(c, ik, X, ld, Y, ld, nv, dtype, minv);
 }
 
+// Y = M^{-1} H X (or H X) with caller-provided scratch for the per-cell
+// products and the enrichment sums; allocates nothing.
+int apply_op_scratch(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv,
+                     void* scratch, size_t scratch_bytes) {
+  OEFE_TRY(check_apply_args(c, ik, X, nv, std::min(ldx, ldy), dtype));
+  if (!Y || !scratch) { c->err = "need Y and scratch"; return OEFE_ERR_ARG; }
+  const size_t es = dtype_bytes(dtype);
+  const size_t zbytes = (((size_t)c->ncells * c->npad * nv * es + 255) / 256) * 256;
+  const size_t yobytes = (size_t)std::max(c->nO, 1) * nv * sizeof(cd);
+  if (zbytes + yobytes > scratch_bytes) {
+    c->err = "problem too large for the fixed scratch: needs " + std::to_string(zbytes + yobytes) + " bytes, limit " +
+             std::to_string(scratch_bytes);
+    return OEFE_ERR_ARG;
+  }
+  char* base = (char*)scratch;
+  Step st{minv ? 1 : 0, 1.0, 0.0, 0.0};
+  OEFE_TRY(dispatch_step(c, c->kd[ik], dtype, X, ldx, nv, st, nullptr, 0, nullptr, 0, Y, ldy, base, (cd*)(base + zbytes)));
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return OEFE_OK;
+}
+
 // Y = M^{-1} H X for one low-precision column through the tensor-core products
 int apply_low(oefe_ctx* c, int ik, const void* X, void* Y, int dtype) {
   const size_t es = dtype_bytes(dtype);

@@ -191,6 +191,9 @@ int chol_inverse_inplace(oefe_ctx* c, double* A, int n, bool cplx, bool inverse,
 int apply_op(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dtype, bool minv);
 int apply_op2(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv);
 int apply_low(oefe_ctx* c, int ik, const void* X, void* Y, int dtype);
+int apply_op_scratch(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv,
+                     void* scratch, size_t scratch_bytes);
+int apply_a_noalloc(oefe_ctx* c, int ik, const void* X, void* Y, int nv, int ld, int dtype);
 
 int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int degree, double a,
                 double b, double a0, int flags);
