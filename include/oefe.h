@@ -195,11 +195,13 @@ int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int d
 int oefe_filter_batched(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype,
                         int degree, const double* a, const double* b, const double* a0, int flags);
 
-/* oefe_filter_autotune -- times the batched cell-product launch shapes
- * (64 or 32 vectors per tile on a persistent grid of one CTA per SM, or one
- * CTA per tile) on the given vectors and keeps the fastest for
- * oefe_filter_batched. ms (host, 3 doubles, may be NULL) receives the time of
- * one degree's cell products for each candidate, in that order. Vectors as
+/* oefe_filter_autotune -- times the tensor-core cell-product launch shapes
+ * on the given vectors and keeps the fastest for the BF16X3 filters:
+ * (0) 64 vectors per tile, persistent grid of one CTA per SM, cp.async loads;
+ * (1) the same with 32 vectors per tile; (2) one CTA per tile;
+ * (3) the warp-specialized kernel with TMA loads (persistent).
+ * ms (host, 4 doubles, may be NULL) receives the time of one degree's cell
+ * products for each candidate (0 when a candidate is unavailable). Vectors as
  * for oefe_filter_batched; they are read, not changed. */
 int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
 

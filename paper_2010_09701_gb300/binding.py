@@ -299,7 +299,7 @@ class Context:
 
     def filter_autotune(self, Xs):
         arr, nvs, lds, dt = self._blocks(Xs)
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         self._check(self.lib.oefe_filter_autotune(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, _dp(ms)))
         return ms
 

@@ -32,6 +32,7 @@ static void free_all(oefe_ctx* c) {
   if (c->bev_out) cudaEventDestroy(c->bev_out);
   if (c->bstream) cudaStreamDestroy(c->bstream);
   dev_free(c->bparams);
+  dev_free(c->d_tmaps);
 }
 
 cudaEvent_t timing_event(oefe_ctx* c) {

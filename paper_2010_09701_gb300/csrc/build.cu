@@ -816,6 +816,22 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
   }
   cudaStreamSynchronize(c->stream);
   dev_free(d_gw);
+  if (st == OEFE_OK && (store & OEFE_STORE_BF16X3)) {
+    // tensor maps of the split cell matrices, one per k-point
+    const size_t mb = tensor_map_bytes();
+    std::vector<unsigned char> maps(mb * c->kd.size());
+    for (size_t ik = 0; ik < c->kd.size() && st == OEFE_OK; ++ik) st = make_cell_tmap(c, c->kd[ik], maps.data() + ik * mb);
+    if (st == OEFE_OK && c->n_tmaps != (int)c->kd.size()) {
+      dev_free(c->d_tmaps);
+      c->d_tmaps = nullptr;
+      c->n_tmaps = 0;
+      st = dev_alloc(c, &c->d_tmaps, maps.size());
+      if (st == OEFE_OK) c->n_tmaps = (int)c->kd.size();
+    }
+    if (st == OEFE_OK) {
+      cudaMemcpy(c->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice);
+    }
+  }
   if (st == OEFE_OK) c->built = true;
   return st;
 }

@@ -407,6 +407,20 @@ int launch_cell_mma_ptrs(oefe_ctx* c, const void* H, const void* X, int ldx, int
 int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z) {
   OEFE_TRY(check_npad(c));
   if (!K.Hbf) { c->err = "BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  const int ik = (int)(&K - c->kd.data());
+  if (c->use_tma && c->d_tmaps && ik >= 0 && ik < c->n_tmaps) {
+    MmaK k0;
+    k0.H = K.Hbf;
+    k0.X = (const float*)X;
+    k0.Z = (float*)Z;
+    k0.ldx = ldx;
+    k0.nv = nv;
+    k0.vblocks = (nv + 63) / 64;
+    k0.tile0 = 0;
+    const long long nt = (long long)c->ncells * k0.vblocks;
+    return launch_cell_mma_tma(c, (const char*)c->d_tmaps + (size_t)ik * tensor_map_bytes(), nullptr, &k0, 1, nt, cplx,
+                               (int)std::min<long long>(nt, c->num_sms), c->stream);
+  }
   if (cplx) return launch_one<true, 64>(c, K.Hbf, X, ldx, nv, Z, c->stream);
   return launch_one<false, 64>(c, K.Hbf, X, ldx, nv, Z, c->stream);
 }

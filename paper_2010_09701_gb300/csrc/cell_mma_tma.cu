@@ -1,0 +1,475 @@
+// Warp-specialized tensor-core cell products (tcgen05 + TMA), BF16x3.
+//
+// Same arithmetic as k_cell_mma (cell_mma.cu): Z_e = H_e X_e with the cell
+// matrices stored as bf16 hi / lo planes, the vectors split on the fly,
+// Z = H_hi X_hi + H_hi X_lo + H_lo X_hi accumulated in FP32 in tensor memory,
+// complex products as real MMAs with the A-negate bit.
+//
+// Roles (one persistent CTA per SM, looping over (k, cell, vector block) tiles):
+//   warp 0      TMA producer: the cell-matrix tile of every (K tile, M tile) as
+//               one 4-plane box into a ring of shared-memory stages;
+//   warp 1      MMA issuer (one thread): waits for a full A stage (and B stage),
+//               issues the MMAs, commits to the stage's "empty" barriers;
+//   warps 2-5   gather producers: rows of X for every K tile, split to bf16;
+//   warps 6-9   epilogue: tensor memory -> registers -> per-cell products.
+// Every mbarrier wait is bounded; on a timeout the CTA raises the error flag,
+// lets the other roles drain, waits for its copies in flight, frees its
+// tensor memory and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+
+#include "oefe_internal.h"
+
+namespace {
+
+constexpr int MT = 128;     // rows per M tile
+constexpr int KT = 64;      // K per tile (bf16: 128 bytes per row)
+constexpr int NBV = 64;     // vectors per tile
+constexpr int SA = 2;       // A ring stages
+constexpr int SB = 2;       // B ring stages
+constexpr int THREADS = 320;
+constexpr long long WAIT_LIMIT = 1ll << 26;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait; gives up early when another role has failed
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((i & 1023) == 1023 && *fail) return false;
+  }
+  *fail = 1;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.shared::cta.b64 st, [%0];\n}\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("{\n .reg .b64 st;\n mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n}\n" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFF) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N, bool negA) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((negA ? 1u : 0u) << 13) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t swz(int row, int k) {
+  const int byte = k * 2;
+  return (uint32_t)(row * 128 + ((((byte >> 4) ^ (row & 7)) & 7) << 4) + (byte & 15));
+}
+
+struct TmaArgs {
+  const CUtensorMap* maps;  // one per k-point, in global memory
+  const MmaK* ks;           // per-k parameters in global memory, or null: use k0
+  MmaK k0;
+  int nk;
+  long long ntiles;
+  const int* cell_nodes;
+  const int* act_off;
+  const int* act_idx;
+  int nloc, npad;
+  int64_t nh;
+  int* err;
+};
+
+// tile t of the CTA's sequence -> (k, cell, vector block)
+__device__ __forceinline__ MmaK kparams(const TmaArgs& A, int k) { return A.ks ? A.ks[k] : A.k0; }
+
+__device__ __forceinline__ void decode_tile(const TmaArgs& A, long long t, int* k, int* e, int* vb) {
+  int kk = 0;
+  if (A.ks)
+    while (kk + 1 < A.nk && A.ks[kk + 1].tile0 <= t) ++kk;
+  const MmaK P = kparams(A, kk);
+  const long long r = t - P.tile0;
+  *k = kk;
+  *e = (int)(r / P.vblocks);
+  *vb = (int)(r % P.vblocks);
+}
+
+template <bool CPLX>
+__global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
+  constexpr int PLANES = CPLX ? 4 : 2;
+  constexpr int NB_ROWS = CPLX ? 2 * NBV : NBV;
+  constexpr int A_PLANE = MT * 128;
+  constexpr int A_STAGE = PLANES * A_PLANE;
+  constexpr int B_PART = NB_ROWS * 128;
+  constexpr int B_STAGE = 2 * B_PART;
+  constexpr int MCOLS = CPLX ? 2 * NBV : NBV;
+  constexpr int TCOLS = CPLX ? 512 : 256;
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = smem;
+  unsigned char* sB = smem + SA * A_STAGE;
+  __shared__ uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full, acc_empty;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int mt = A.npad / MT, ktn = A.npad / KT;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int s = 0; s < SA; ++s) {
+      mbar_init(&a_full[s], 1);
+      mbar_init(&a_empty[s], 1);
+    }
+    for (int s = 0; s < SB; ++s) {
+      mbar_init(&b_full[s], 128);
+      mbar_init(&b_empty[s], 1);
+    }
+    mbar_init(&acc_full, 1);
+    mbar_init(&acc_empty, 128);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = tmem_slot;
+
+  if (warp == 0) {
+    // ---------------------------------------------------------------- TMA producer
+    if (lane == 0) {
+      long long ga = 0;
+      for (int k = 0; k < A.nk; ++k)
+        asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&A.maps[k]) : "memory");
+      for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x) {
+        int k, e, vb;
+        decode_tile(A, t, &k, &e, &vb);
+        for (int it = 0; it < mt * ktn && !s_fail; ++it, ++ga) {
+          const int kt = it / mt, m = it % mt;
+          const int s = (int)(ga % SA);
+          const long long u = ga / SA;
+          if (u >= 1 && !mbar_wait(&a_empty[s], (uint32_t)((u - 1) & 1), &s_fail)) break;
+          mbar_expect_tx(&a_full[s], A_STAGE);
+          tma_load_4d(smem_u32(sA + s * A_STAGE), &A.maps[k], kt * KT, m * MT, 0, e, &a_full[s]);
+        }
+      }
+      // drain: every issued load lands before the CTA leaves
+      for (long long g = (ga > SA ? ga - SA : 0); g < ga; ++g)
+        mbar_wait(&a_full[g % SA], (uint32_t)((g / SA) & 1), &s_fail);
+    }
+  } else if (warp == 1) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      long long ga = 0, gb = 0;
+      int tl = 0;
+      for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x, ++tl) {
+        if (tl >= 1 && !mbar_wait(&acc_empty, (uint32_t)((tl - 1) & 1), &s_fail)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        bool ok = true;
+        for (int it = 0; it < mt * ktn; ++it, ++ga) {
+          const int kt = it / mt, m = it % mt;
+          const int s = (int)(ga % SA);
+          const int sb = (int)((gb + kt) % SB);
+          if (!mbar_wait(&a_full[s], (uint32_t)((ga / SA) & 1), &s_fail)) { ok = false; break; }
+          if (m == 0 && !mbar_wait(&b_full[sb], (uint32_t)(((gb + kt) / SB) & 1), &s_fail)) { ok = false; break; }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a_base = smem_u32(sA + s * A_STAGE);
+          const uint32_t b_base = smem_u32(sB + sb * B_STAGE);
+          const uint32_t dcol = taddr + m * MCOLS;
+          constexpr uint32_t ID = idesc_bf16(MT, NBV, false);
+          constexpr uint32_t IDN = idesc_bf16(MT, NBV, true);
+#pragma unroll
+          for (int ks = 0; ks < KT / 16; ++ks) {
+            const uint32_t koff = ks * 32;
+            const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
+            if (CPLX) {
+              const uint64_t Arh = sdesc(a_base + 0 * A_PLANE + koff), Arl = sdesc(a_base + 1 * A_PLANE + koff);
+              const uint64_t Aih = sdesc(a_base + 2 * A_PLANE + koff), Ail = sdesc(a_base + 3 * A_PLANE + koff);
+              const uint64_t Xrh = sdesc(b_base + koff), Xih = sdesc(b_base + NBV * 128 + koff);
+              const uint64_t Xrl = sdesc(b_base + B_PART + koff), Xil = sdesc(b_base + B_PART + NBV * 128 + koff);
+              const uint32_t Dr = dcol, Di = dcol + NBV;
+              mma_bf16(Dr, Arh, Xrh, ID, first);
+              mma_bf16(Dr, Arh, Xrl, ID, 1);
+              mma_bf16(Dr, Arl, Xrh, ID, 1);
+              mma_bf16(Dr, Aih, Xih, IDN, 1);
+              mma_bf16(Dr, Aih, Xil, IDN, 1);
+              mma_bf16(Dr, Ail, Xih, IDN, 1);
+              mma_bf16(Di, Arh, Xih, ID, first);
+              mma_bf16(Di, Arh, Xil, ID, 1);
+              mma_bf16(Di, Arl, Xih, ID, 1);
+              mma_bf16(Di, Aih, Xrh, ID, 1);
+              mma_bf16(Di, Aih, Xrl, ID, 1);
+              mma_bf16(Di, Ail, Xrh, ID, 1);
+            } else {
+              const uint64_t Ah = sdesc(a_base + koff), Al = sdesc(a_base + A_PLANE + koff);
+              const uint64_t Bh = sdesc(b_base + koff), Bl = sdesc(b_base + B_PART + koff);
+              mma_bf16(dcol, Ah, Bh, ID, first);
+              mma_bf16(dcol, Ah, Bl, ID, 1);
+              mma_bf16(dcol, Al, Bh, ID, 1);
+            }
+          }
+          mma_commit(&a_empty[s]);
+          if (m == mt - 1) mma_commit(&b_empty[sb]);
+        }
+        gb += ktn;
+        if (!ok) break;
+        mma_commit(&acc_full);
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------------------------------------------------------- gather producers
+    const int gt = tid - 64;  // 0 .. 127
+    long long gb = 0;
+    for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x) {
+      int k, e, vb;
+      decode_tile(A, t, &k, &e, &vb);
+      const MmaK P = kparams(A, k);
+      const int ne = A.act_off[e + 1] - A.act_off[e];
+      const int naug = A.nloc + ne;
+      const int v0 = vb * NBV;
+      for (int kt = 0; kt < ktn && !s_fail; ++kt, ++gb) {
+        const int sb = (int)(gb % SB);
+        const long long u = gb / SB;
+        if (u >= 1 && !mbar_wait(&b_empty[sb], (uint32_t)((u - 1) & 1), &s_fail)) break;
+        unsigned char* b0 = sB + sb * B_STAGE;
+        // each thread owns one vector column v and 16 row pairs (kk, kk+1) of the K tile;
+        // the loads of a batch are issued together so their latencies overlap, and each
+        // pair is written to shared memory as one packed bf16x2 word per plane
+        const int v = gt & (NBV - 1), r0 = gt >> 6;   // r0 in {0, 1}
+        constexpr int BATCH = 8;                        // pairs per batch: 16 loads in flight
+        const bool vok = v0 + v < P.nv;
+#pragma unroll 1
+        for (int j0 = 0; j0 < KT / 4; j0 += BATCH) {
+          float2 xv[2 * BATCH];
+#pragma unroll
+          for (int u = 0; u < 2 * BATCH; ++u) {
+            const int kk = 4 * (j0 + (u >> 1)) + 2 * r0 + (u & 1);
+            const int r = kt * KT + kk;
+            xv[u] = make_float2(0.f, 0.f);
+            if (r < naug && vok) {
+              const int64_t row = r < A.nloc ? (int64_t)A.cell_nodes[(size_t)e * A.nloc + r]
+                                             : A.nh + A.act_idx[A.act_off[e] + r - A.nloc];
+              if (CPLX) xv[u] = __ldg(reinterpret_cast<const float2*>(P.X) + row * P.ldx + v0 + v);
+              else xv[u].x = __ldg(P.X + row * P.ldx + v0 + v);
+            }
+          }
+#pragma unroll
+          for (int w = 0; w < BATCH; ++w) {
+            const int kk = 4 * (j0 + w) + 2 * r0;   // even: the pair shares one 4-byte word
+            const float2 x0 = xv[2 * w], x1 = xv[2 * w + 1];
+            const __nv_bfloat162 rh = __floats2bfloat162_rn(x0.x, x1.x);
+            const __nv_bfloat162 rl = __floats2bfloat162_rn(x0.x - __low2float(rh), x1.x - __high2float(rh));
+            *reinterpret_cast<__nv_bfloat162*>(b0 + swz(v, kk)) = rh;
+            *reinterpret_cast<__nv_bfloat162*>(b0 + B_PART + swz(v, kk)) = rl;
+            if (CPLX) {
+              const __nv_bfloat162 ih = __floats2bfloat162_rn(x0.y, x1.y);
+              const __nv_bfloat162 il = __floats2bfloat162_rn(x0.y - __low2float(ih), x1.y - __high2float(ih));
+              *reinterpret_cast<__nv_bfloat162*>(b0 + swz(NBV + v, kk)) = ih;
+              *reinterpret_cast<__nv_bfloat162*>(b0 + B_PART + swz(NBV + v, kk)) = il;
+            }
+          }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&b_full[sb]);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int q = warp & 3;
+    int tl = 0;
+    for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x, ++tl) {
+      int k, e, vb;
+      decode_tile(A, t, &k, &e, &vb);
+      const MmaK P = kparams(A, k);
+      const int ne = A.act_off[e + 1] - A.act_off[e];
+      const int naug = A.nloc + ne;
+      const int v0 = vb * NBV;
+      if (!mbar_wait(&acc_full, (uint32_t)(tl & 1), &s_fail)) break;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      for (int m = 0; m < mt; ++m) {
+        const int row = m * MT + 32 * q + lane;
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t tl0 = taddr + ((uint32_t)(32 * q) << 16) + m * MCOLS + 32 * h;
+          float re[32], im[32];
+          tmem_ld32(tl0, re);
+          if (CPLX) tmem_ld32(tl0 + NBV, im);
+          if (row < naug) {
+            float* zr = P.Z + ((size_t)e * A.npad + row) * (size_t)P.nv * (CPLX ? 2 : 1);
+            const int vb0 = v0 + 32 * h;
+            if (CPLX && (P.nv & 1) == 0 && vb0 + 32 <= P.nv) {
+              // 16-byte stores: two complex values each
+#pragma unroll
+              for (int j = 0; j < 32; j += 2)
+                *reinterpret_cast<float4*>(zr + 2 * (vb0 + j)) = make_float4(re[j], im[j], re[j + 1], im[j + 1]);
+            } else if (!CPLX && (P.nv & 3) == 0 && vb0 + 32 <= P.nv) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 4)
+                *reinterpret_cast<float4*>(zr + vb0 + j) = make_float4(re[j], re[j + 1], re[j + 2], re[j + 3]);
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) {
+                const int v = vb0 + j;
+                if (v < P.nv) {
+                  if (CPLX) {
+                    zr[2 * v] = re[j];
+                    zr[2 * v + 1] = im[j];
+                  } else {
+                    zr[v] = re[j];
+                  }
+                }
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&acc_empty);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_fail && tid == 0) atomicExch(A.err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TCOLS) : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+}  // namespace
+
+size_t cell_mma_tma_smem(bool cplx) {
+  const int planes = cplx ? 4 : 2, nbrows = cplx ? 2 * NBV : NBV;
+  return 1024 + (size_t)SA * planes * MT * 128 + (size_t)SB * 2 * nbrows * 128;
+}
+
+// Tensor map of one k-point's split cell matrices: 4D (col, row, plane, cell) box (64, 128, planes, 1).
+int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out) {
+  auto fn = encode_fn();
+  if (!fn) { c->err = "cuTensorMapEncodeTiled is not available"; return OEFE_ERR_CUDA; }
+  const int planes = K.cplx ? 4 : 2;
+  const cuuint64_t dims[4] = {(cuuint64_t)c->npad, (cuuint64_t)c->npad, (cuuint64_t)planes, (cuuint64_t)c->ncells};
+  const cuuint64_t strides[3] = {(cuuint64_t)c->npad * 2, (cuuint64_t)c->npad * c->npad * 2,
+                                 (cuuint64_t)planes * c->npad * c->npad * 2};
+  const cuuint32_t box[4] = {KT, MT, (cuuint32_t)planes, 1};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  CUtensorMap m;
+  const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, K.Hbf, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    c->err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return OEFE_ERR_CUDA;
+  }
+  std::memcpy(map_out, &m, sizeof(CUtensorMap));
+  return OEFE_OK;
+}
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
+                        bool cplx, int grid, cudaStream_t st) {
+  if (c->npad % MT != 0 || c->npad > 4 * MT) {
+    c->err = "tensor path needs npad a multiple of 128 and at most 512";
+    return OEFE_ERR_ARG;
+  }
+  TmaArgs A;
+  A.maps = (const CUtensorMap*)d_maps;
+  A.ks = d_ks;
+  if (k0) A.k0 = *k0;
+  A.nk = nk;
+  A.ntiles = ntiles;
+  A.cell_nodes = c->d_cell_nodes;
+  A.act_off = c->d_act_off;
+  A.act_idx = c->d_act_idx;
+  A.nloc = c->nloc;
+  A.npad = c->npad;
+  A.nh = c->nh;
+  A.err = c->d_status;
+  const size_t smem = cell_mma_tma_smem(cplx);
+  if (cplx) {
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_cell_mma_tma<true><<<grid, THREADS, smem, st>>>(A);
+  } else {
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_cell_mma_tma<false><<<grid, THREADS, smem, st>>>(A);
+  }
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}

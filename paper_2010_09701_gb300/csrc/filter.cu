@@ -535,8 +535,11 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
   for (int k = 0; k < P.nk; ++k) vmax = std::max(vmax, P.nd[k].nv);
   const int eb = (c->nO * vmax + 127) / 128;
   for (int j = 0; j < P.jlow; ++j) {
-    if (timed) cudaEventRecord(c->bev_kernel[2 * j], c->bstream);
-    if (P.grid > 0) {
+    if (timed) cudaEventRecordWithFlags(c->bev_kernel[2 * j], c->bstream, cudaEventRecordExternal);
+    if (c->use_tma && c->d_tmaps) {
+      OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk + (size_t)j * P.nk, nullptr, P.nk, P.ntiles, cplx,
+                                   (int)std::min<long long>(P.ntiles, c->num_sms), c->bstream));
+    } else if (P.grid > 0) {
       OEFE_TRY(launch_cell_mma_multi(c, d_mk + (size_t)j * P.nk, P.nk, P.ntiles, cplx, P.nb, P.grid, c->bstream));
     } else {  // one CTA per tile, one launch per k-point
       for (int k = 0; k < P.nk; ++k) {
@@ -544,7 +547,7 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
         OEFE_TRY(launch_cell_mma_ptrs(c, m.H, m.X, m.ldx, m.nv, m.Z, cplx, P.nb, c->bstream));
       }
     }
-    if (timed) cudaEventRecord(c->bev_kernel[2 * j + 1], c->bstream);
+    if (timed) cudaEventRecordWithFlags(c->bev_kernel[2 * j + 1], c->bstream, cudaEventRecordExternal);
     dim3 g1(blocks, P.nk), g2(std::max(eb, 1), P.nk);
     if (cplx) {
       k_node_update_multi<float, true><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off, c->d_node_slot,
@@ -593,6 +596,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   const int64_t n = c->nh + c->nO;
   const int jlow = mixed ? degree - 1 : degree;
   if (c->tune_nb == 0) { c->tune_nb = 64; c->tune_grid = c->num_sms; }
+  if (c->use_tma && c->d_tmaps) c->tune_nb = 64;
   // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed)
   std::vector<size_t> off(nk + 1, 0);
   auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
@@ -685,7 +689,8 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   }
   // graph key: everything baked into the captured launches
   std::vector<double> key = {(double)nk, (double)degree, (double)flags, (double)dtype, (double)(uintptr_t)base,
-                             (double)P.nb, (double)P.grid, (double)(c->timing & (1 << dt_low) ? 1 : 0)};
+                             (double)P.nb, (double)P.grid, (double)(c->timing & (1 << dt_low) ? 1 : 0),
+                             (double)c->use_tma};
   for (int k = 0; k < nk; ++k) {
     key.push_back((double)(uintptr_t)X[k]);
     key.push_back(nv[k]);
@@ -727,7 +732,8 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
       }
     }
     // set the kernels' shared-memory limits outside of the capture
-    if (P.grid > 0) OEFE_TRY(launch_cell_mma_multi(c, d_mk, nk, 0, cplx, P.nb, 1, c->bstream));
+    if (c->use_tma && c->d_tmaps) OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, 0, cplx, 1, c->bstream));
+    else if (P.grid > 0) OEFE_TRY(launch_cell_mma_multi(c, d_mk, nk, 0, cplx, P.nb, 1, c->bstream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
     cudaGraph_t graph;
     OEFE_CUDA_TRY(c, cudaStreamBeginCapture(c->bstream, cudaStreamCaptureModeThreadLocal));
@@ -830,8 +836,9 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
     else OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(XL[k], (size_t)nv[k] * es_low, X[k], (size_t)ld[k] * es_low,
                                             (size_t)nv[k] * es_low, (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
   }
-  struct Cand { int nb, grid; };
-  const Cand cands[3] = {{64, c->num_sms}, {32, c->num_sms}, {64, 0}};
+  struct Cand { int nb, grid, tma; };
+  const Cand cands[4] = {{64, c->num_sms, 0}, {32, c->num_sms, 0}, {64, 0, 0}, {64, c->num_sms, 1}};
+  const int ncand = c->d_tmaps ? 4 : 3;
   double best = 1e300;
   int bi = 0;
   MmaK* d_mk = nullptr;
@@ -840,7 +847,7 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int st = OEFE_OK;
-  for (int ci = 0; ci < 3 && st == OEFE_OK; ++ci) {
+  for (int ci = 0; ci < ncand && st == OEFE_OK; ++ci) {
     std::vector<MmaK> mk(nk);
     long long nt = 0;
     for (int k = 0; k < nk; ++k) {
@@ -857,7 +864,10 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
     double tbest = 1e300;
     for (int rep = 0; rep < 3 && st == OEFE_OK; ++rep) {
       cudaEventRecord(e0, c->stream);
-      if (cands[ci].grid > 0) {
+      if (cands[ci].tma) {
+        st = launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, nt, cplx, (int)std::min<long long>(nt, c->num_sms),
+                                 c->stream);
+      } else if (cands[ci].grid > 0) {
         st = launch_cell_mma_multi(c, d_mk, nk, nt, cplx, cands[ci].nb, cands[ci].grid, c->stream);
       } else {
         for (int k = 0; k < nk && st == OEFE_OK; ++k)
@@ -888,5 +898,6 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
   }
   c->tune_nb = cands[bi].nb;
   c->tune_grid = cands[bi].grid;
+  c->use_tma = cands[bi].tma;
   return OEFE_OK;
 }

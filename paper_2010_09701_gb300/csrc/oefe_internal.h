@@ -158,7 +158,10 @@ struct oefe_ctx {
   size_t bparams_bytes = 0;
   std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
   int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
+  int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
   double tune_ms[4] = {0, 0, 0, 0};
+  void* d_tmaps = nullptr;              // one tensor map per k-point (split cell matrices)
+  int n_tmaps = 0;
 };
 
 // record an event pair around a launch when timing is on
@@ -213,6 +216,12 @@ int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv,
 int launch_cell_mma_multi(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntiles, bool cplx, int nb, int grid,
                           cudaStream_t st);
 size_t cell_mma_smem(bool cplx, int nb);
+// warp-specialized TMA variant (cell_mma_tma.cu)
+int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
+                        bool cplx, int grid, cudaStream_t st);
+int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out);
+size_t tensor_map_bytes();
+size_t cell_mma_tma_smem(bool cplx);
 int launch_cell_mma_ptrs(oefe_ctx* c, const void* H, const void* X, int ldx, int nv, void* Z, bool cplx, int nb,
                          cudaStream_t st);
 

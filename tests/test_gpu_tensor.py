@@ -119,11 +119,20 @@ def test_autotune_then_batched_real():
     pr = prs[0]
     X = W.random_vectors(pr.n, 70, seed=4)
     ms = ctx.filter_autotune([to_gpu(X, torch.float32)])
-    assert np.all(ms > 0)
+    assert np.all(ms > 0)   # four candidates, the TMA kernel included
     a, b, a0 = bounds(pr)
     ref = solver.chebyshev_filter(pr.apply_A, X, 5, a, b, a0)
     Xd = to_gpu(X, torch.float32)
     ctx.filter_batched([Xd], 5, a, b, a0, FILTER_BF16X3)
+    assert colerr(Xd.cpu().numpy().astype(np.float64), ref) < TOL_FILTER
+    # with timing on, the captured graph carries one event pair per degree
+    from paper_2010_09701_gb300 import F32
+    ctx.kernel_timing([F32])
+    Xd = to_gpu(X, torch.float32)
+    ctx.filter_batched([Xd], 5, a, b, a0, FILTER_BF16X3)
+    ms, n = ctx.kernel_time()
+    ctx.kernel_timing([])
+    assert n == 5 and ms > 0
     assert colerr(Xd.cpu().numpy().astype(np.float64), ref) < TOL_FILTER
 
 
