@@ -527,9 +527,13 @@ __global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma,
     }
     if (Hbf) {
       // split each real plane: hi = bf16(x), lo = bf16(x - hi), from the FP32 value
+      // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
+      // each (K tile, M tile) of two planes is one contiguous 32 KB block for the TMA loads
       constexpr int PL = sizeof(S) == sizeof(cd) ? 4 : 2;
-      const size_t pl = (size_t)npad * npad;
-      const size_t base = (size_t)e * PL * pl + (size_t)r * npad + c;
+      const size_t pl = 128 * 64;
+      const int mtn = npad >> 7;
+      const size_t base = (size_t)e * PL * npad * npad +
+                          ((((size_t)(c >> 6) * mtn + (r >> 7)) * PL) * 128 + (r & 127)) * 64 + (c & 63);
       const float xr = (float)v.x;
       const __nv_bfloat16 rh = __float2bfloat16_rn(xr);
       Hbf[base] = rh;

@@ -168,7 +168,8 @@ __device__ __forceinline__ void mma_tile(const __nv_bfloat16* __restrict__ He, c
       const uint32_t a0 = smem_u32(sA + s * A_STAGE);
       for (int c = tid; c < PLANES * MT * 8; c += THREADS) {
         const int p = c / (MT * 8), r = (c / 8) % MT, ch = c % 8;
-        const __nv_bfloat16* src = He + ((size_t)p * npad + m * MT + r) * npad + kt * KT + ch * 8;
+        // tile-contiguous storage: [K tile][M tile][plane][128 rows][64 columns]
+        const __nv_bfloat16* src = He + ((((size_t)kt * mt + m) * PLANES + p) * MT + r) * KT + ch * 8;
         cp_async16(a0 + p * A_PLANE + r * 128 + (((ch ^ (r & 7)) & 7) << 4), src);
       }
       asm volatile("cp.async.commit_group;" ::: "memory");

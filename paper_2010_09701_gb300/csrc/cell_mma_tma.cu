@@ -7,11 +7,14 @@
 //
 // Roles (one persistent CTA per SM, looping over (k, cell, vector block) tiles):
 //   warp 0      TMA producer: the cell-matrix tile of every (K tile, M tile) as
-//               one 4-plane box into a ring of shared-memory stages;
+//               2-plane boxes (hi, lo of the real part, then of the imaginary
+//               part) into a ring of 32 KB shared-memory stages;
 //   warp 1      MMA issuer (one thread): waits for a full A stage (and B stage),
 //               issues the MMAs, commits to the stage's "empty" barriers;
 //   warps 2-5   gather producers: rows of X for every K tile, split to bf16;
-//   warps 6-9   epilogue: tensor memory -> registers -> per-cell products.
+//   warps 6-9   epilogue: tensor memory -> registers -> per-cell products, one
+//               M tile at a time, so the next tile's MMAs into an M tile start
+//               as soon as that M tile has been drained.
 // Every mbarrier wait is bounded; on a timeout the CTA raises the error flag,
 // lets the other roles drain, waits for its copies in flight, frees its
 // tensor memory and returns.
@@ -30,9 +33,11 @@ namespace {
 constexpr int MT = 128;     // rows per M tile
 constexpr int KT = 64;      // K per tile (bf16: 128 bytes per row)
 constexpr int NBV = 64;     // vectors per tile
-constexpr int SA = 2;       // A ring stages
+constexpr int SA = 3;       // A ring stages (2 planes each)
 constexpr int SB = 2;       // B ring stages
 constexpr int THREADS = 320;
+constexpr int MAXPAD = 4 * MT;  // largest npad
+constexpr int STG = 32 * 256;   // epilogue staging per warp: 32 rows x 256 bytes
 constexpr long long WAIT_LIMIT = 1ll << 26;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -51,6 +56,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// bounded wait that ignores the failure flag (used to drain work in flight)
+__device__ __forceinline__ bool mbar_wait_drain(uint64_t* bar, uint32_t parity) {
+  for (long long i = 0; i < WAIT_LIMIT; ++i)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 // bounded wait; gives up early when another role has failed
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* fail) {
   for (long long i = 0; i < WAIT_LIMIT; ++i) {
@@ -59,6 +71,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
   *fail = 1;
   return false;
+}
+
+// barrier among the 128 gather threads (named barrier 1) that also ORs a flag over them, so that
+// all of them take the same exit decision
+__device__ __forceinline__ bool gather_bar_or(bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, 1, 128, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"((uint32_t)v)
+      : "memory");
+  return r != 0;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
@@ -71,12 +95,12 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint64_t* bar) {
   asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-      "[%6];" ::"r"(dst),
-      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
       : "memory");
 }
 
@@ -158,10 +182,10 @@ __device__ __forceinline__ void decode_tile(const TmaArgs& A, long long t, int* 
 
 template <bool CPLX>
 __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
-  constexpr int PLANES = CPLX ? 4 : 2;
+  constexpr int HALVES = CPLX ? 2 : 1;   // A stages per (K tile, M tile)
   constexpr int NB_ROWS = CPLX ? 2 * NBV : NBV;
   constexpr int A_PLANE = MT * 128;
-  constexpr int A_STAGE = PLANES * A_PLANE;
+  constexpr int A_STAGE = 2 * A_PLANE;
   constexpr int B_PART = NB_ROWS * 128;
   constexpr int B_STAGE = 2 * B_PART;
   constexpr int MCOLS = CPLX ? 2 * NBV : NBV;
@@ -170,9 +194,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
   unsigned char* sB = smem + SA * A_STAGE;
-  __shared__ uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full, acc_empty;
+  unsigned char* sE = sB + SB * B_STAGE;   // epilogue staging, one STG block per epilogue warp
+  __shared__ uint64_t a_full[SA], a_empty[SA], b_full[SB], b_empty[SB], acc_full[4], acc_empty[4], mma_done;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_fail;
+  __shared__ int s_rows[2][MAXPAD];   // gathered rows of the current / next tile (gather warps)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int mt = A.npad / MT, ktn = A.npad / KT;
@@ -192,8 +218,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       mbar_init(&b_full[s], 128);
       mbar_init(&b_empty[s], 1);
     }
-    mbar_init(&acc_full, 1);
-    mbar_init(&acc_empty, 128);
+    for (int m = 0; m < 4; ++m) {
+      mbar_init(&acc_full[m], 1);
+      mbar_init(&acc_empty[m], 128);
+    }
+    mbar_init(&mma_done, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -211,89 +240,106 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x) {
         int k, e, vb;
         decode_tile(A, t, &k, &e, &vb);
-        for (int it = 0; it < mt * ktn && !s_fail; ++it, ++ga) {
-          const int kt = it / mt, m = it % mt;
+        for (int it = 0; it < mt * ktn * HALVES && !s_fail; ++it, ++ga) {
+          const int h = it % HALVES, kt = it / (HALVES * mt), m = (it / HALVES) % mt;
           const int s = (int)(ga % SA);
           const long long u = ga / SA;
           if (u >= 1 && !mbar_wait(&a_empty[s], (uint32_t)((u - 1) & 1), &s_fail)) break;
           mbar_expect_tx(&a_full[s], A_STAGE);
-          tma_load_4d(smem_u32(sA + s * A_STAGE), &A.maps[k], kt * KT, m * MT, 0, e, &a_full[s]);
+          // one contiguous 32 KB chunk: (cell, K tile, M tile, plane pair)
+          const int chunk = ((e * ktn + kt) * mt + m) * HALVES + h;
+          tma_load_3d(smem_u32(sA + s * A_STAGE), &A.maps[k], 0, 0, chunk, &a_full[s]);
         }
       }
       // drain: every issued load lands before the CTA leaves
-      for (long long g = (ga > SA ? ga - SA : 0); g < ga; ++g)
-        mbar_wait(&a_full[g % SA], (uint32_t)((g / SA) & 1), &s_fail);
+      for (long long g = (ga > SA ? ga - SA : 0); g < ga; ++g) mbar_wait_drain(&a_full[g % SA], (uint32_t)((g / SA) & 1));
     }
   } else if (warp == 1) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       long long ga = 0, gb = 0;
       int tl = 0;
-      for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x, ++tl) {
-        if (tl >= 1 && !mbar_wait(&acc_empty, (uint32_t)((tl - 1) & 1), &s_fail)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        bool ok = true;
-        for (int it = 0; it < mt * ktn; ++it, ++ga) {
+      bool ok = true;
+      for (long long t = blockIdx.x; t < A.ntiles && ok && !s_fail; t += gridDim.x, ++tl) {
+        for (int it = 0; it < mt * ktn && ok; ++it) {
           const int kt = it / mt, m = it % mt;
-          const int s = (int)(ga % SA);
           const int sb = (int)((gb + kt) % SB);
-          if (!mbar_wait(&a_full[s], (uint32_t)((ga / SA) & 1), &s_fail)) { ok = false; break; }
+          if (kt == 0 && tl >= 1 && !mbar_wait(&acc_empty[m], (uint32_t)((tl - 1) & 1), &s_fail)) { ok = false; break; }
           if (m == 0 && !mbar_wait(&b_full[sb], (uint32_t)(((gb + kt) / SB) & 1), &s_fail)) { ok = false; break; }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a_base = smem_u32(sA + s * A_STAGE);
           const uint32_t b_base = smem_u32(sB + sb * B_STAGE);
           const uint32_t dcol = taddr + m * MCOLS;
           constexpr uint32_t ID = idesc_bf16(MT, NBV, false);
           constexpr uint32_t IDN = idesc_bf16(MT, NBV, true);
+          for (int h = 0; h < HALVES; ++h, ++ga) {
+            const int s = (int)(ga % SA);
+            if (!mbar_wait(&a_full[s], (uint32_t)((ga / SA) & 1), &s_fail)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a_base = smem_u32(sA + s * A_STAGE);
 #pragma unroll
-          for (int ks = 0; ks < KT / 16; ++ks) {
-            const uint32_t koff = ks * 32;
-            const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
-            if (CPLX) {
-              const uint64_t Arh = sdesc(a_base + 0 * A_PLANE + koff), Arl = sdesc(a_base + 1 * A_PLANE + koff);
-              const uint64_t Aih = sdesc(a_base + 2 * A_PLANE + koff), Ail = sdesc(a_base + 3 * A_PLANE + koff);
-              const uint64_t Xrh = sdesc(b_base + koff), Xih = sdesc(b_base + NBV * 128 + koff);
-              const uint64_t Xrl = sdesc(b_base + B_PART + koff), Xil = sdesc(b_base + B_PART + NBV * 128 + koff);
-              const uint32_t Dr = dcol, Di = dcol + NBV;
-              mma_bf16(Dr, Arh, Xrh, ID, first);
-              mma_bf16(Dr, Arh, Xrl, ID, 1);
-              mma_bf16(Dr, Arl, Xrh, ID, 1);
-              mma_bf16(Dr, Aih, Xih, IDN, 1);
-              mma_bf16(Dr, Aih, Xil, IDN, 1);
-              mma_bf16(Dr, Ail, Xih, IDN, 1);
-              mma_bf16(Di, Arh, Xih, ID, first);
-              mma_bf16(Di, Arh, Xil, ID, 1);
-              mma_bf16(Di, Arl, Xih, ID, 1);
-              mma_bf16(Di, Aih, Xrh, ID, 1);
-              mma_bf16(Di, Aih, Xrl, ID, 1);
-              mma_bf16(Di, Ail, Xrh, ID, 1);
-            } else {
+            for (int ks = 0; ks < KT / 16; ++ks) {
+              const uint32_t koff = ks * 32;
               const uint64_t Ah = sdesc(a_base + koff), Al = sdesc(a_base + A_PLANE + koff);
-              const uint64_t Bh = sdesc(b_base + koff), Bl = sdesc(b_base + B_PART + koff);
-              mma_bf16(dcol, Ah, Bh, ID, first);
-              mma_bf16(dcol, Ah, Bl, ID, 1);
-              mma_bf16(dcol, Al, Bh, ID, 1);
+              if (CPLX) {
+                const uint64_t Xrh = sdesc(b_base + koff), Xih = sdesc(b_base + NBV * 128 + koff);
+                const uint64_t Xrl = sdesc(b_base + B_PART + koff), Xil = sdesc(b_base + B_PART + NBV * 128 + koff);
+                const uint32_t Dr = dcol, Di = dcol + NBV;
+                if (h == 0) {   // real part of the cell matrix
+                  const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
+                  mma_bf16(Dr, Ah, Xrh, ID, first);
+                  mma_bf16(Dr, Ah, Xrl, ID, 1);
+                  mma_bf16(Dr, Al, Xrh, ID, 1);
+                  mma_bf16(Di, Ah, Xih, ID, first);
+                  mma_bf16(Di, Ah, Xil, ID, 1);
+                  mma_bf16(Di, Al, Xih, ID, 1);
+                } else {        // imaginary part: Re Z -= Im H Im X, Im Z += Im H Re X
+                  mma_bf16(Dr, Ah, Xih, IDN, 1);
+                  mma_bf16(Dr, Ah, Xil, IDN, 1);
+                  mma_bf16(Dr, Al, Xih, IDN, 1);
+                  mma_bf16(Di, Ah, Xrh, ID, 1);
+                  mma_bf16(Di, Ah, Xrl, ID, 1);
+                  mma_bf16(Di, Al, Xrh, ID, 1);
+                }
+              } else {
+                const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
+                const uint64_t Bh = sdesc(b_base + koff), Bl = sdesc(b_base + B_PART + koff);
+                mma_bf16(dcol, Ah, Bh, ID, first);
+                mma_bf16(dcol, Ah, Bl, ID, 1);
+                mma_bf16(dcol, Al, Bh, ID, 1);
+              }
             }
+            mma_commit(&a_empty[s]);
           }
-          mma_commit(&a_empty[s]);
+          if (!ok) break;
           if (m == mt - 1) mma_commit(&b_empty[sb]);
+          if (kt == ktn - 1) mma_commit(&acc_full[m]);
         }
         gb += ktn;
-        if (!ok) break;
-        mma_commit(&acc_full);
+      }
+      // every MMA issued has completed before the tensor memory is released
+      if (ga > 0) {
+        mma_commit(&mma_done);
+        mbar_wait_drain(&mma_done, 0);
       }
     }
   } else if (warp < 6) {
     // ---------------------------------------------------------------- gather producers
     const int gt = tid - 64;  // 0 .. 127
     long long gb = 0;
-    for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x) {
+    int tg = 0;
+    for (long long t = blockIdx.x; t < A.ntiles; t += gridDim.x) {
       int k, e, vb;
       decode_tile(A, t, &k, &e, &vb);
       const MmaK P = kparams(A, k);
       const int ne = A.act_off[e + 1] - A.act_off[e];
       const int naug = A.nloc + ne;
       const int v0 = vb * NBV;
+      // the tile's row map, once per tile, double-buffered; the barrier publishes it and takes
+      // the exit decision on a failure uniformly over the gather threads
+      int* rows = s_rows[tg & 1];
+      for (int r = gt; r < naug; r += 128)
+        rows[r] = r < A.nloc ? A.cell_nodes[(size_t)e * A.nloc + r] : (int)(A.nh + A.act_idx[A.act_off[e] + r - A.nloc]);
+      ++tg;
+      if (gather_bar_or(s_fail != 0)) break;
       for (int kt = 0; kt < ktn && !s_fail; ++kt, ++gb) {
         const int sb = (int)(gb % SB);
         const long long u = gb / SB;
@@ -303,7 +349,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
         // the loads of a batch are issued together so their latencies overlap, and each
         // pair is written to shared memory as one packed bf16x2 word per plane
         const int v = gt & (NBV - 1), r0 = gt >> 6;   // r0 in {0, 1}
-        constexpr int BATCH = 8;                        // pairs per batch: 16 loads in flight
+        constexpr int BATCH = KT / 4;                   // pairs per batch: all 32 loads in flight
         const bool vok = v0 + v < P.nv;
 #pragma unroll 1
         for (int j0 = 0; j0 < KT / 4; j0 += BATCH) {
@@ -314,8 +360,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
             const int r = kt * KT + kk;
             xv[u] = make_float2(0.f, 0.f);
             if (r < naug && vok) {
-              const int64_t row = r < A.nloc ? (int64_t)A.cell_nodes[(size_t)e * A.nloc + r]
-                                             : A.nh + A.act_idx[A.act_off[e] + r - A.nloc];
+              const int64_t row = rows[r];
               if (CPLX) xv[u] = __ldg(reinterpret_cast<const float2*>(P.X) + row * P.ldx + v0 + v);
               else xv[u].x = __ldg(P.X + row * P.ldx + v0 + v);
             }
@@ -351,46 +396,63 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       const int ne = A.act_off[e + 1] - A.act_off[e];
       const int naug = A.nloc + ne;
       const int v0 = vb * NBV;
-      if (!mbar_wait(&acc_full, (uint32_t)(tl & 1), &s_fail)) break;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      bool ok = true;
       for (int m = 0; m < mt; ++m) {
+        if (!mbar_wait(&acc_full[m], (uint32_t)(tl & 1), &s_fail)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = m * MT + 32 * q + lane;
         for (int h = 0; h < 2; ++h) {
           const uint32_t tl0 = taddr + ((uint32_t)(32 * q) << 16) + m * MCOLS + 32 * h;
           float re[32], im[32];
           tmem_ld32(tl0, re);
           if (CPLX) tmem_ld32(tl0 + NBV, im);
-          if (row < naug) {
+          const int vb0 = v0 + 32 * h;
+          const bool full = CPLX ? ((P.nv & 1) == 0 && vb0 + 32 <= P.nv) : ((P.nv & 3) == 0 && vb0 + 32 <= P.nv);
+          if (full) {
+            // stage the warp's 32 rows x 32 values in shared memory (16-byte chunks, XOR-swizzled by
+            // row), then write whole row segments: 256 contiguous bytes per row (complex), 128 (real)
+            constexpr int CPR = CPLX ? 16 : 8;      // 16-byte chunks per row segment
+            constexpr int RPI = 32 / CPR;           // rows per store instruction
+            unsigned char* st = sE + q * STG;
+#pragma unroll
+            for (int j = 0; j < CPR; ++j) {
+              const float4 v = CPLX ? make_float4(re[2 * j], im[2 * j], re[2 * j + 1], im[2 * j + 1])
+                                    : make_float4(re[4 * j], re[4 * j + 1], re[4 * j + 2], re[4 * j + 3]);
+              *reinterpret_cast<float4*>(st + lane * (CPR * 16) + ((j ^ (lane & (CPR - 1))) << 4)) = v;
+            }
+            __syncwarp();
+            const int ch = lane % CPR, rsub = lane / CPR;
+#pragma unroll
+            for (int i = 0; i < 32; i += RPI) {
+              const int rl = i + rsub;                       // row within the warp's 32
+              const int grow = m * MT + 32 * q + rl;
+              if (grow < naug) {
+                const float4 v = *reinterpret_cast<const float4*>(st + rl * (CPR * 16) + ((ch ^ (rl & (CPR - 1))) << 4));
+                float* zr = P.Z + ((size_t)e * A.npad + grow) * (size_t)P.nv * (CPLX ? 2 : 1);
+                *reinterpret_cast<float4*>(zr + (CPLX ? 2 : 1) * vb0 + 4 * ch) = v;
+              }
+            }
+            __syncwarp();
+          } else if (row < naug) {
             float* zr = P.Z + ((size_t)e * A.npad + row) * (size_t)P.nv * (CPLX ? 2 : 1);
-            const int vb0 = v0 + 32 * h;
-            if (CPLX && (P.nv & 1) == 0 && vb0 + 32 <= P.nv) {
-              // 16-byte stores: two complex values each
 #pragma unroll
-              for (int j = 0; j < 32; j += 2)
-                *reinterpret_cast<float4*>(zr + 2 * (vb0 + j)) = make_float4(re[j], im[j], re[j + 1], im[j + 1]);
-            } else if (!CPLX && (P.nv & 3) == 0 && vb0 + 32 <= P.nv) {
-#pragma unroll
-              for (int j = 0; j < 32; j += 4)
-                *reinterpret_cast<float4*>(zr + vb0 + j) = make_float4(re[j], re[j + 1], re[j + 2], re[j + 3]);
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) {
-                const int v = vb0 + j;
-                if (v < P.nv) {
-                  if (CPLX) {
-                    zr[2 * v] = re[j];
-                    zr[2 * v + 1] = im[j];
-                  } else {
-                    zr[v] = re[j];
-                  }
+            for (int j = 0; j < 32; ++j) {
+              const int v = vb0 + j;
+              if (v < P.nv) {
+                if (CPLX) {
+                  zr[2 * v] = re[j];
+                  zr[2 * v + 1] = im[j];
+                } else {
+                  zr[v] = re[j];
                 }
               }
             }
           }
         }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        mbar_arrive(&acc_empty[m]);
       }
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      mbar_arrive(&acc_empty);
+      if (!ok) break;
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -415,22 +477,24 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 }  // namespace
 
 size_t cell_mma_tma_smem(bool cplx) {
-  const int planes = cplx ? 4 : 2, nbrows = cplx ? 2 * NBV : NBV;
-  return 1024 + (size_t)SA * planes * MT * 128 + (size_t)SB * 2 * nbrows * 128;
+  const int nbrows = cplx ? 2 * NBV : NBV;
+  return 1024 + (size_t)SA * 2 * MT * 128 + (size_t)SB * 2 * nbrows * 128 + 4 * (size_t)STG;
 }
 
-// Tensor map of one k-point's split cell matrices: 4D (col, row, plane, cell) box (64, 128, planes, 1).
+// Tensor map of one k-point's split cell matrices, stored tile-contiguous ([cell][K tile][M tile]
+// [plane][128][64]): 3D (column, row of a plane pair, chunk), box (64, 256, 1) = the hi and lo planes
+// of the real part, or of the imaginary part, of one (K tile, M tile).
 int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out) {
   auto fn = encode_fn();
   if (!fn) { c->err = "cuTensorMapEncodeTiled is not available"; return OEFE_ERR_CUDA; }
   const int planes = K.cplx ? 4 : 2;
-  const cuuint64_t dims[4] = {(cuuint64_t)c->npad, (cuuint64_t)c->npad, (cuuint64_t)planes, (cuuint64_t)c->ncells};
-  const cuuint64_t strides[3] = {(cuuint64_t)c->npad * 2, (cuuint64_t)c->npad * c->npad * 2,
-                                 (cuuint64_t)planes * c->npad * c->npad * 2};
-  const cuuint32_t box[4] = {KT, MT, (cuuint32_t)planes, 1};
-  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const cuuint64_t nchunk = (cuuint64_t)c->ncells * (c->npad / KT) * (c->npad / MT) * (planes / 2);
+  const cuuint64_t dims[3] = {(cuuint64_t)KT, (cuuint64_t)2 * MT, nchunk};
+  const cuuint64_t strides[2] = {(cuuint64_t)KT * 2, (cuuint64_t)2 * MT * KT * 2};
+  const cuuint32_t box[3] = {KT, 2 * MT, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
   CUtensorMap m;
-  const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, K.Hbf, dims, strides, box, estr,
+  const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, K.Hbf, dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {

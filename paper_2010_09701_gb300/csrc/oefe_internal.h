@@ -63,7 +63,7 @@ struct KData {
   double* Mooinv = nullptr;  // nO x nO scalars (FP64)
   double* H64 = nullptr;     // (ncells, npad, npad) scalars
   float* H32 = nullptr;      // (ncells, npad, npad) float or cf
-  void* Hbf = nullptr;       // (ncells, planes, npad, npad) bf16: (re hi, re lo[, im hi, im lo])
+  void* Hbf = nullptr;       // bf16 planes (re hi, re lo[, im hi, im lo]), per cell [K tile][M tile][plane][128][64]
   void* E0 = nullptr;        // per cell: V-independent enrichment blocks (cd), CA then AA
   bool built = false;
 };

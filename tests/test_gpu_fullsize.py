@@ -1,0 +1,144 @@
+"""Parity at the full size of the benchmark workload: the 8-atom zincblende cell
+(a = 8.5 bohr, Z = 14/6), graded 16^3 mesh, p = 6, 40 enrichment functions,
+Monkhorst-Pack 2x2x1 (4 complex k-points), 64 vectors per k.
+
+The library builds the whole operator and runs one degree of the batched
+tensor-core filter over all four k-points in one launch per degree (the launch
+configuration the benchmark times) and one FP64 operator apply. The oracle
+computes, one by one, sampled outputs it can afford: cell matrices H^O_e of
+sampled cells, and the rows of sampled CFE nodes, each from the cells that
+share the node (every cell containing a node contributes to its row; the
+orthogonalizing coefficients of those cells come from their exact
+neighbourhood). Samples: a vertex where a nucleus sits (eight octree-refined
+cells) and a vertex away from every nucleus.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import solver
+from oracle.enrichment import Enrichment
+from oracle.mesh import Mesh
+from oracle.operators import Problem
+from oracle.quadrature import Quadrature
+
+pytestmark = pytest.mark.gpu
+
+# BF16x3 products: ~3 * 2^-17 relative per term, FP32 accumulation
+TOL_BF16X3 = 1e-4
+TOL_FP64 = 1e-12
+
+
+def cid(w, ix, iy, iz):
+    n = w.ncell
+    return (ix % n) + n * ((iy % n) + n * (iz % n))
+
+
+def vertex_node(w, ix, iy, iz):
+    N = w.ncell * w.p
+    return ((iz * w.p) % N * N + (iy * w.p) % N) * N + (ix * w.p) % N
+
+
+def cells_around(w, ix, iy, iz):
+    return [cid(w, ix + dx, iy + dy, iz + dz) for dz in (-1, 0) for dy in (-1, 0) for dx in (-1, 0)]
+
+
+@pytest.fixture(scope="module")
+def full():
+    import paper_2010_09701_gb300 as P
+    w = W.config_c3()
+    xb = W.mesh_breakpoints(w)
+    mesh = Mesh(w.a, xb, w.p)
+    quad = Quadrature(mesh, w.pos, w.rc, *w.quad_params())
+    R, dR = W.radial_tables(w.Z, rc=w.rc, ngrid=w.ngrid)
+    enr = Enrichment(w.a, w.pos, W.orbital_lm_codes(), R, dR, w.r0, w.rc)
+    ks, _ = W.monkhorst_pack(w.a, w.kgrid)
+    V = W.veff(quad.points, w.a, w.pos, w.Z, w.sigma)
+
+    ctx = P.setup_workload(w)
+    xyz, qw = ctx.quadrature_points()
+    assert xyz.shape == quad.points.shape
+    assert np.max(np.abs(xyz - quad.points)) <= 1e-14 * w.a
+    ctx.build_hamiltonian(torch.tensor(V, dtype=torch.float64, device="cuda"), P.STORE_F64 | P.STORE_BF16X3)
+    nh, nO = ctx.ndof()
+    n = nh + nO
+    assert nh == mesh.nh and nO == enr.nO
+    X = [W.random_vectors(n, w.nv[ik], complex_=True, seed=w.seed + ik) for ik in range(len(ks))]
+    return dict(w=w, mesh=mesh, quad=quad, enr=enr, ks=ks, V=V, ctx=ctx, X=X, n=n)
+
+
+# (vertex in cell units, k-point index): a nucleus at the origin; a vertex away from every nucleus
+SAMPLES = [((0, 0, 0), 3), ((2, 6, 10), 0)]
+
+
+@pytest.fixture(scope="module")
+def oracle_samples(full):
+    w = full["w"]
+    out = []
+    for vtx, ik in SAMPLES:
+        cells = cells_around(w, *vtx)
+        pr = Problem(full["mesh"], full["quad"], full["enr"], full["ks"][ik], cells=cells)
+        pr.build(full["V"])
+        node = vertex_node(w, *vtx)
+        pos = int(np.searchsorted(pr.rows, node))
+        assert pr.rows[pos] == node
+        out.append(dict(vtx=vtx, ik=ik, cells=cells, pr=pr, node=node, pos=pos))
+    return out
+
+
+def abs_product_row(pr, Xr, pos):
+    """(|H^O| |X|) at one row: the scale of the rounding error of any summation order."""
+    acc = np.zeros(Xr.shape[1])
+    for e in pr.cells:
+        idx = pr.index(e)
+        hit = np.nonzero(idx == pos)[0]
+        if len(hit):
+            acc += np.abs(pr.HO[e][hit[0]]) @ np.abs(Xr[idx])
+    return acc
+
+
+def test_fullsize_cell_matrices(full, oracle_samples):
+    ctx = full["ctx"]
+    for s in oracle_samples:
+        pr = s["pr"]
+        for e in (s["cells"][0], s["cells"][-1]):
+            assert np.array_equal(ctx.cell_info(e), pr._gindex(e)), e
+            H = ctx.cell_matrix(s["ik"], e, complex_=True)
+            ref = pr.HO[e]
+            assert np.max(np.abs(H - ref)) / np.max(np.abs(ref)) < TOL_FP64, (s["vtx"], e)
+
+
+def test_fullsize_fp64_apply_rows(full, oracle_samples):
+    ctx = full["ctx"]
+    for s in oracle_samples:
+        pr, ik, pos = s["pr"], s["ik"], s["pos"]
+        Xg = torch.tensor(full["X"][ik], device="cuda")
+        Yg = torch.empty_like(Xg)
+        ctx.apply_h(ik, Xg, Yg)
+        got = Yg[s["node"]].cpu().numpy()
+        del Xg, Yg
+        Xr = full["X"][ik][pr.rows]
+        ref = pr.apply_H(Xr)[pos]
+        scale = abs_product_row(pr, Xr, pos)
+        assert np.max(np.abs(got - ref) / scale) < TOL_FP64, s["vtx"]
+
+
+def test_fullsize_batched_tensor_degree_rows(full, oracle_samples):
+    # one degree of the batched filter over all four k-points: the bench's launch configuration
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    w, ctx = full["w"], full["ctx"]
+    a, b, a0 = 0.0, 3000.0, -0.5 * float(max(w.Z)) ** 2 - 1.0
+    Xd = [torch.tensor(X, dtype=torch.complex64, device="cuda") for X in full["X"]]
+    ctx.filter_batched(Xd, 1, a, b, a0, FILTER_BF16X3)
+    for s in oracle_samples:
+        pr, ik, pos = s["pr"], s["ik"], s["pos"]
+        got = Xd[ik][s["node"]].cpu().numpy().astype(np.complex128)
+        Xr = full["X"][ik][pr.rows]
+        ref = solver.chebyshev_filter(pr.apply_A, Xr, 1, a, b, a0)[pos]
+        c = 0.5 * (a + b)
+        scale = (abs_product_row(pr, Xr, pos) / pr.m[pos] + abs(c) * np.abs(Xr[pos])) / abs(a0 - c)
+        assert np.max(np.abs(got - ref) / scale) < TOL_BF16X3, s["vtx"]
+    # every row finite, and untouched vector blocks keep their shape
+    for X in Xd:
+        assert torch.isfinite(torch.view_as_real(X)).all()
