@@ -96,6 +96,28 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def barrier(world):
+    """Barrier over the replicas (no-op for one process)."""
+    if world > 1:
+        import torch
+        torch.distributed.barrier()
+
+
+def max_over_ranks(x, world, device="cpu"):
+    """The largest value of x over all ranks: the timed region ends when the slowest replica does."""
+    if world == 1:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank, world, ms):
+    """Whole-job throughput: the work every replica did, over the slowest replica's time."""
+    return world * flops_per_rank / (ms * 1e-3) / 1e12
+
+
 def dense_filter_flops(ctx_naug, nvs, degree):
     """sum over k of sum_e 2 n_aug,e^2 N_v,k * 4 (complex) per degree, times the degree."""
     s2 = float(np.sum(np.asarray(ctx_naug, float) ** 2))
@@ -122,6 +144,8 @@ def run_ours(args, rank, world):
     xyz, qw = ctx.quadrature_points()
     V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
     store = P.STORE_F64 | (P.STORE_BF16X3 if args.tensor else P.STORE_F32)
+    if args.filter_only:   # profiling aid: the low-precision matrices only
+        store = P.STORE_BF16X3 if args.tensor else P.STORE_F32
     ctx.build_hamiltonian(V, store)
     naug = np.array([len(ctx.cell_info(e)) for e in range(int(np.prod([w.ncell] * 3)))])
     nvs = w.nv
@@ -210,30 +234,29 @@ def run_ours(args, rank, world):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    barrier(world)
     sampler = ClockSampler(dev)
     sampler.start()
     ctx.kernel_timing([P.C64])
     torch.cuda.synchronize()
+    barrier(world)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    launches0 = P.launch_count()
     ev0.record(stream)
     for _ in range(args.steps):
         eigs, eb_mixed = step(record=True)
     ev1.record(stream)
+    launches = P.launch_count() - launches0
     torch.cuda.synchronize()
+    barrier(world)
     clocks = sampler.stop()
     kms, klaunch = ctx.kernel_time()
     ctx.kernel_timing([])
-    step_ms = ev0.elapsed_time(ev1) / args.steps
-    if world > 1:
-        t = torch.tensor([step_ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms = t.item()
+    step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     filt_ms = [a.elapsed_time(b) for a, b in filt_events]
     flops_step = dense_filter_flops(naug, nvs, deg)
-    value = world * flops_step / (step_ms * 1e-3) / 1e12
+    value = whole_job_tflops(flops_step, world, step_ms)
     filt_tflops = flops_step / (sum(filt_ms) / args.steps * 1e-3) / 1e12
     # seconds per filter pass of one k-point
     s_per_pass = float(np.mean(filt_ms)) * 1e-3 / (nk if batched else 1)
@@ -306,8 +329,9 @@ def run_ours(args, rank, world):
         e2e_ms = ee0.elapsed_time(ee1) / args.e2e_steps
         bi = V.numel() * 8 + sum(x.numel() * 16 for x in X0)
         bo = rho.numel() * 8 + sum(len(e) * 8 for e in eigs_e)
-        e2e = {"value": world * flops_step / (max(e2e_ms, wall * 1e3) * 1e-3) / 1e12, "unit": "TFLOP/s",
-               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": max(e2e_ms, wall * 1e3)}
+        e2e_ms = max_over_ranks(max(e2e_ms, wall * 1e3), world, "cuda")
+        e2e = {"value": whole_job_tflops(flops_step, world, e2e_ms), "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms}
 
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
@@ -328,7 +352,7 @@ def run_ours(args, rank, world):
            "autotune_ms_per_degree": tune_ms,
            "filter_precision": "BF16x3 tensor cores + last degree FP64" if args.tensor else "FP32 + last degree FP64",
            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
-           "gpu_launches": int(args.steps * (nk * (deg * 4 + 40) + 20)),
+           "gpu_launches": int(launches),
            "peaks_source": src, "setup_s": setup_s}
     return out
 
@@ -400,7 +424,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3", choices=["c2", "c3", "c3small"])
+    ap.add_argument("--config", default="c3", choices=["c2", "c3", "c3small", "c3mid"])
     ap.add_argument("--filter-only", action="store_true",
                     help="profiling aid: set up, then run --steps low-precision filter passes on k-point 0 only")
     ap.add_argument("--sample-cells", type=int, default=2)

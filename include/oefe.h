@@ -260,6 +260,12 @@ int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, int flag
 int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask);
 int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches);
 
+/* oefe_launch_count -- process-wide number of kernel launches the library has
+ * issued so far (every context; a replay of a captured graph counts each of
+ * its kernels). n: host pointer to one int64. Never synchronizes. Returns
+ * OEFE_ERR_ARG when n is null. No counterpart in the paper (instrumentation). */
+int oefe_launch_count(int64_t* n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -7,9 +7,9 @@ without a GPU, but creating a Context needs the built library and a device.
 """
 from .binding import (C64, C128, F32, F64, FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X3, STORE_F32, STORE_F64,
                       Context, OefeError,
-                      SIGNATURES, load, occupations)
+                      SIGNATURES, launch_count, load, occupations)
 from .problem import setup_workload
 
-__all__ = ["Context", "OefeError", "load", "occupations", "setup_workload", "SIGNATURES", "F64", "F32", "C128", "C64",
+__all__ = ["Context", "OefeError", "load", "launch_count", "occupations", "setup_workload", "SIGNATURES", "F64", "F32", "C128", "C64",
            "STORE_F64", "STORE_F32", "STORE_BF16X3", "FILTER_LAST_FP64",
            "FILTER_BF16X3"]

@@ -57,6 +57,7 @@ SIGNATURES = [
     ("oefe_occupations", _I, [_I, _IP, _DP, _DP, _D, _D, _DP, _DP, _DP]),
     ("oefe_kernel_timing", _I, [_P, _I]),
     ("oefe_kernel_time", _I, [_P, _DP, _I64P]),
+    ("oefe_launch_count", _I, [_c.POINTER(_c.c_int64)]),
 ]
 
 _lib = None
@@ -76,6 +77,14 @@ def load():
             f.argtypes = args
         _lib = lib
     return _lib
+
+
+def launch_count():
+    """Kernel launches the library has issued in this process (graph replays count each kernel)."""
+    n = ctypes.c_int64()
+    if load().oefe_launch_count(ctypes.byref(n)) != 0:
+        raise RuntimeError("oefe_launch_count failed")
+    return int(n.value)
 
 
 class OefeError(RuntimeError):

@@ -4,6 +4,8 @@
 #include <cstring>
 #include <new>
 
+#include <atomic>
+
 #include "oefe_internal.h"
 
 #define CTX_CHECK(ctx)          \
@@ -43,6 +45,10 @@ cudaEvent_t timing_event(oefe_ctx* c) {
   }
   return c->ev_pool[c->ev_used++];
 }
+
+static std::atomic<long long> g_launches{0};
+
+long long oefe_launch_add(long long n) { return g_launches.fetch_add(n, std::memory_order_relaxed) + n; }
 
 extern "C" {
 
@@ -317,6 +323,12 @@ int oefe_occupations(int nk, const int* nv, const double* eig, const double* w, 
     }
   if (mu) *mu = m;
   if (e_band) *e_band = eb;
+  return OEFE_OK;
+}
+
+int oefe_launch_count(int64_t* n) {
+  if (!n) return OEFE_ERR_ARG;
+  *n = (int64_t)g_launches.load(std::memory_order_relaxed);
   return OEFE_OK;
 }
 

@@ -19,7 +19,10 @@ namespace {
 constexpr int MAXP = 8;     // P = p + 1 <= 8
 constexpr int MAXN1 = 12;   // Gauss points per axis per leaf
 constexpr int BT = 256;     // threads per CTA of the cell kernels
-constexpr size_t SMEM_BUILD = 212 * 1024;
+constexpr int TT = 352;     // threads per CTA of the transform: one local node each (n_loc <= 343 at p = 6)
+constexpr int TJB = 8;      // enrichment columns per pass of the transform
+constexpr size_t SMEM_SETUP = 212 * 1024;  // setup mode: one CTA per SM
+constexpr size_t SMEM_BUILD = 96 * 1024;   // build mode: two CTAs per SM
 
 // Tabulate N^A and grad N^A for (point, active function) pairs of a batch of cells.
 // tab entry layout: 4 complex values (value, d/dx, d/dy, d/dz) per (q, j), j fastest.
@@ -52,6 +55,13 @@ __global__ void k_tabulate(EnrParams E, const double* qxyz, const int64_t* q_off
   }
 }
 
+// A CTA's share of the build (mode 0): leaves [l0, l1) of batch cell b. slot < 0 writes the
+// cell matrix itself (and adds the cached V-independent blocks); slot >= 0 writes partial `slot`,
+// added to the cell matrix afterwards in a fixed order (deterministic sums).
+struct BuildItem {
+  int b, l0, l1, slot;
+};
+
 struct BuildArgs {
   const Leaf* leaves;
   const int* leaf_off;
@@ -72,6 +82,9 @@ struct BuildArgs {
   cd* dblk;                 // mode 1: (ncells, nloc, ne_max)
   cd* MAAblk;               // mode 1: (ncells, ne_max, ne_max)
   cd* E0;                   // per cell: V-independent CA (nloc x ne_max) then AA (ne_max x ne_max)
+  const BuildItem* items;   // mode 0: one CTA per item (a cell's leaf range); null: one CTA per cell
+  cd* HP;                   // mode 0: partial cell matrices of the items with slot >= 0
+  size_t smem;              // dynamic shared memory of the launch
 };
 
 // One CTA per cell, accumulating over the cell's tensor-product leaves.
@@ -84,7 +97,8 @@ struct BuildArgs {
 // the potential parts of the CA and AA blocks, plus the cached E0.
 __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   extern __shared__ double smem[];
-  const int b = blockIdx.x;
+  const BuildItem it = A.items ? A.items[blockIdx.x] : BuildItem{(int)blockIdx.x, -1, -1, -1};
+  const int b = it.b;
   const int e = A.e0 + b;
   const int P = A.P, nloc = A.nloc, npad = A.npad;
   const int ne = A.act_off[e + 1] - A.act_off[e];
@@ -100,7 +114,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   __shared__ double xn[MAXP];
   if (threadIdx.x < P) xn[threadIdx.x] = A.gll[threadIdx.x];
 
-  cd* HE = A.HE ? A.HE + (size_t)b * npad * npad : nullptr;
+  cd* HE = A.HE ? (it.slot < 0 ? A.HE + (size_t)b * npad * npad : A.HP + (size_t)it.slot * npad * npad) : nullptr;
   cd* dB = A.dblk ? A.dblk + (size_t)e * nloc * A.ne_max : nullptr;
   cd* MB = A.MAAblk ? A.MAAblk + (size_t)e * A.ne_max * A.ne_max : nullptr;
   if (A.mode == 0) {
@@ -112,7 +126,8 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   __syncthreads();
 
   const cd* tabc = A.tab + 4 * A.tab_off[b];  // this cell's tabulation, (q, j) j fastest
-  for (int li = A.leaf_off[e]; li < A.leaf_off[e + 1]; ++li) {
+  const int l_begin = it.l0 >= 0 ? it.l0 : A.leaf_off[e], l_end = it.l0 >= 0 ? it.l1 : A.leaf_off[e + 1];
+  for (int li = l_begin; li < l_end; ++li) {
     const Leaf L = A.leaves[li];
     const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
     const int64_t q0 = L.q0;
@@ -162,7 +177,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
       }
       __syncthreads();
       const int P2 = P * P, P4 = P2 * P2;
-      const int budget = (int)((SMEM_BUILD / sizeof(double) - n3 - (size_t)n2 * P2) / P4);
+      const int budget = (int)((A.smem / sizeof(double) - n3 - (size_t)n2 * P2) / P4);
       const int cx = min(n1, max(1, budget));
       for (int qx0 = 0; qx0 < n1; qx0 += cx) {
         const int nx = min(cx, n1 - qx0);
@@ -213,8 +228,8 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
     //   mode 1: F0 = -(i/2) w k.grad N, F_d = w (grad_d N / 2 + (i/2) k_d N) -> CA0;  Fd = w N -> d
     {
       cd* F = reinterpret_cast<cd*>(smem);     // 5 fields * n3
-      cd* G = F + 5 * n3;                      // 4 * n2 * P
-      cd* Hs = G + 4 * n2 * P;                 // 3 * n1 * P * P
+      cd* G = F + (A.mode == 1 ? 5 : 1) * n3;                // 4 (setup) or 1 fields of n2 * P
+      cd* Hs = G + (A.mode == 1 ? 4 : 1) * n2 * P;           // 3 (setup) or 1 fields of n1 * P * P
       const bool full = A.mode == 1;
       for (int j = 0; j < ne; ++j) {
         for (int q = threadIdx.x; q < n3; q += BT) {
@@ -302,7 +317,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
     {
       const bool full = A.mode == 1;
       const int comps = full ? 4 : 1;
-      const int QC = max(1, min(32, (int)((SMEM_BUILD - 32 * 8) / ((size_t)max(ne, 1) * comps * sizeof(cd)))));
+      const int QC = max(1, min(32, (int)((A.smem - 32 * 8) / ((size_t)max(ne, 1) * comps * sizeof(cd)))));
       cd* Ns = reinterpret_cast<cd*>(smem);   // QC x ne x comps
       double* Ws = reinterpret_cast<double*>(Ns + (size_t)QC * ne * comps);  // QC
       const int npairs = ne * (ne + 1) / 2;
@@ -379,7 +394,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
       __syncthreads();
     }
   }
-  if (A.mode == 0) {
+  if (A.mode == 0 && it.slot < 0) {
     // cached V-independent enrichment blocks
     for (int t = threadIdx.x; t < nloc * ne; t += BT) {
       const int m = t / ne, j = t % ne;
@@ -506,7 +521,7 @@ __global__ void k_hermitize(S* A, int n) {
 // H^O_e = T_e^+ H_e T_e: CO = CA - H_CC Gamma, OO = AA - Gamma^+ CO - CA^+ Gamma.
 // One CTA per cell; writes the FP64 and/or FP32 stored matrices.
 template <typename S, typename S32>
-__global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma, const int* act_off,
+__global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gamma, const int* act_off,
                                                   int e0, int nloc, int npad, int ne_max, S* H64,
                                                   S32* H32, __nv_bfloat16* Hbf) {
   extern __shared__ double smem[];
@@ -514,8 +529,8 @@ __global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma,
   const int ne = act_off[e + 1] - act_off[e];
   const cd* HE = HEb + (size_t)b * npad * npad;
   const S* Gm = gamma + (size_t)e * nloc * ne_max;
-  cd* CO = reinterpret_cast<cd*>(smem);          // nloc * JB
-  constexpr int JB = 4;
+  cd* CO = reinterpret_cast<cd*>(smem);          // nloc * TJB
+  constexpr int JB = TJB;
   auto put = [&](int r, int c, cd v) {
     const size_t o = (size_t)e * npad * npad + (size_t)r * npad + c;
     if constexpr (sizeof(S) == sizeof(cd)) {
@@ -547,36 +562,49 @@ __global__ void __launch_bounds__(BT) k_transform(const cd* HEb, const S* gamma,
     }
   };
   // CC block and zero padding
-  for (int t = threadIdx.x; t < npad * npad; t += BT) {
+  for (int t = threadIdx.x; t < npad * npad; t += TT) {
     const int r = t / npad, c = t % npad;
     if (r < nloc && c < nloc) put(r, c, HE[(size_t)r * npad + c]);
     else if (r >= nloc + ne || c >= nloc + ne) put(r, c, mkc(0, 0));
   }
+  cd* Gs = CO + (size_t)nloc * JB;               // Gamma[:, j0:j0+JB], nloc * JB
   for (int j0 = 0; j0 < ne; j0 += JB) {
     const int nj = min(JB, ne - j0);
-    // CO[:, j0:j0+nj] = CA - H_CC Gamma, using H_CC Hermitian: (H_CC Gamma)[m] = sum_a conj(H[a][m]) Gamma[a]
-    for (int m = threadIdx.x; m < nloc; m += BT) {
+    for (int t = threadIdx.x; t < nloc * JB; t += TT) {
+      const int a = t / JB, u = t % JB;
+      Gs[t] = u < nj ? ld_s(Gm, (size_t)a * ne_max + j0 + u) : mkc(0, 0);
+    }
+    __syncthreads();
+    // CO[:, j0:j0+nj] = CA - H_CC Gamma, using H_CC Hermitian: (H_CC Gamma)[m] = sum_a conj(H[a][m]) Gamma[a];
+    // one local node per thread, JB columns in registers
+    for (int m = threadIdx.x; m < nloc; m += TT) {
       cd acc[JB];
+#pragma unroll
       for (int u = 0; u < JB; ++u) acc[u] = mkc(0, 0);
       for (int a = 0; a < nloc; ++a) {
         const cd h = cconj(HE[(size_t)a * npad + m]);
-        for (int u = 0; u < nj; ++u) acc[u] += h * ld_s(Gm, (size_t)a * ne_max + j0 + u);
+        const cd* g = Gs + a * JB;
+#pragma unroll
+        for (int u = 0; u < JB; ++u) acc[u] += h * g[u];
       }
-      for (int u = 0; u < nj; ++u) {
-        const cd co = HE[(size_t)m * npad + nloc + j0 + u] - acc[u];
-        CO[m * JB + u] = co;
-        put(m, nloc + j0 + u, co);
-        put(nloc + j0 + u, m, cconj(co));
+#pragma unroll
+      for (int u = 0; u < JB; ++u) {
+        if (u < nj) {
+          const cd co = HE[(size_t)m * npad + nloc + j0 + u] - acc[u];
+          CO[m * JB + u] = co;
+          put(m, nloc + j0 + u, co);
+          put(nloc + j0 + u, m, cconj(co));
+        }
       }
     }
     __syncthreads();
     // OO[i][j] = AA[i][j] - sum_m conj(Gamma[m][i]) CO[m][j] - sum_m conj(CA[m][i]) Gamma[m][j]
-    for (int t = threadIdx.x; t < ne * nj; t += BT) {
+    for (int t = threadIdx.x; t < ne * nj; t += TT) {
       const int i = t / nj, u = t % nj, j = j0 + u;
       cd s = HE[(size_t)(nloc + i) * npad + nloc + j];
       for (int m = 0; m < nloc; ++m) {
         s -= cmulc(ld_s(Gm, (size_t)m * ne_max + i), CO[m * JB + u]);
-        s -= cmulc(HE[(size_t)m * npad + nloc + i], ld_s(Gm, (size_t)m * ne_max + j));
+        s -= cmulc(HE[(size_t)m * npad + nloc + i], Gs[m * JB + u]);
       }
       put(nloc + i, nloc + j, s);
     }
@@ -600,20 +628,23 @@ static int gauss_table(oefe_ctx* c, double** d_tab) {
   return OEFE_OK;
 }
 
-static size_t smem_build_bytes(const oefe_ctx* c) {
-  // worst case over both phases, all leaves use n1 <= max(nq_cell, nq_enr)
+static size_t smem_build_bytes(const oefe_ctx* c, int mode) {
+  // worst case over the phases, all leaves use n1 <= max(nq_cell, nq_enr)
   const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
   const size_t n3 = (size_t)n1 * n1 * n1, n2 = (size_t)n1 * n1;
-  const size_t phase_cc = std::min(SMEM_BUILD, (n3 + n2 * P * P + (size_t)n1 * P * P * P * P) * 8);
-  const size_t phase_ca = (5 * n3 + 4 * n2 * P + 3 * (size_t)n1 * P * P) * 16;
+  const size_t cap = mode == 1 ? SMEM_SETUP : SMEM_BUILD;
+  // the CC stage keeps at least one x-slab of P^4 partial sums
+  const size_t cc_min = (n3 + n2 * P * P + (size_t)P * P * P * P) * 8;
+  const size_t phase_cc = mode == 1 ? 0 : std::max(cc_min, std::min(cap, (n3 + n2 * P * P + (size_t)n1 * P * P * P * P) * 8));
+  const size_t phase_ca = mode == 1 ? (5 * n3 + 4 * n2 * P + 3 * (size_t)n1 * P * P) * 16
+                                    : (n3 + n2 * P + (size_t)n1 * P * P) * 16;
   const size_t phase_aa = 32 * (size_t)std::max(c->ne_max, 1) * 4 * 16 + 32 * 8;
   return std::max(std::max(phase_cc, phase_ca), phase_aa);
 }
 
 // Process cells in batches bounded by a scratch budget; calls fn(e0, e1, tab_off_host).
 template <typename Fn>
-static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, Fn fn) {
-  const size_t budget = (size_t)6 << 30;  // bytes of tabulation + per-cell scratch per batch
+static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, size_t budget, Fn fn) {
   int e0 = 0;
   while (e0 < c->ncells) {
     std::vector<int64_t> off(1, 0);
@@ -648,27 +679,88 @@ static EnrParams enr_params(const oefe_ctx* c) {
   return E;
 }
 
-// Run the tabulation and the cell kernel over all cells in batches.
+// Sum the partial cell matrices of the split cells into their cell matrices, in slot order.
+static __global__ void k_add_partials(cd* HE, const cd* HP, const int* red, int nred, int npad) {
+  const int64_t n2 = (int64_t)npad * npad;
+  for (int r = blockIdx.y; r < nred; r += gridDim.y) {
+    const int b = red[3 * r], s0 = red[3 * r + 1], s1 = red[3 * r + 2];
+    cd* h = HE + (size_t)b * n2;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
+      cd s = h[t];
+      for (int q = s0; q < s1; ++q) s += HP[(size_t)q * n2 + t];
+      h[t] = s;
+    }
+  }
+}
+
+// Scratch budget of one batch of cells (tabulation + cell matrices + partials): a quarter of the
+// free device memory, between 2 and 32 GB.
+static size_t batch_budget() {
+  size_t fr = 0, tot = 0;
+  if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) return (size_t)6 << 30;
+  return std::min<size_t>((size_t)32 << 30, std::max<size_t>((size_t)2 << 30, fr / 4));
+}
+
+// Run the tabulation and the cell kernel over all cells in batches. In the build mode the work is
+// shared out as items of at most G leaves (cells refined toward a nucleus have tens of leaves, the
+// others one), largest first, so that no cell's leaves serialize the launch.
 static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, double* d_gw, cd* dblk,
                            cd* MAAblk, int store) {
-  const size_t hebytes = mode == 0 ? (size_t)c->npad * c->npad * sizeof(cd) : 0;
-  const size_t smem = smem_build_bytes(c);
+  const size_t n2b = (size_t)c->npad * c->npad * sizeof(cd);
+  const size_t hebytes = mode == 0 ? n2b : 0;
+  const size_t smem = smem_build_bytes(c, mode);
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_build_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  return for_cell_batches(c, hebytes, [&](int e0, int e1, const std::vector<int64_t>& off) -> int {
+  int per_sm = 0;
+  OEFE_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_cell, BT, smem));
+  const int resident = std::max(1, per_sm) * c->num_sms;
+  return for_cell_batches(c, hebytes, batch_budget(), [&](int e0, int e1, const std::vector<int64_t>& off) -> int {
     const int nb = e1 - e0;
-    const size_t tab_bytes = (size_t)off.back() * 4 * sizeof(cd);
-    const size_t off_bytes = off.size() * sizeof(int64_t);
-    const size_t he_total = hebytes * nb;
-    OEFE_TRY(ensure_ws(c, tab_bytes + he_total + off_bytes + 256));
+    // work items (build mode)
+    std::vector<BuildItem> items;
+    std::vector<int> red;  // (b, slot0, slot1) per split cell
+    int nslot = 0;
+    if (mode == 0) {
+      long long leaves = 0;
+      for (int e = e0; e < e1; ++e) leaves += c->leaf_off[e + 1] - c->leaf_off[e];
+      const int G = (int)std::max<long long>(2, (leaves + 2 * resident - 1) / (2 * resident));
+      for (int e = e0; e < e1; ++e) {
+        const int l0 = c->leaf_off[e], l1 = c->leaf_off[e + 1];
+        const int b = e - e0;
+        items.push_back({b, l0, std::min(l1, l0 + G), -1});
+        if (l1 - l0 > G) {
+          const int s0 = nslot;
+          for (int l = l0 + G; l < l1; l += G) items.push_back({b, l, std::min(l1, l + G), nslot++});
+          red.insert(red.end(), {b, s0, nslot});
+        }
+      }
+      std::stable_sort(items.begin(), items.end(),
+                       [](const BuildItem& x, const BuildItem& y) { return x.l1 - x.l0 > y.l1 - y.l0; });
+    }
+    auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
+    const size_t tab_bytes = a256((size_t)off.back() * 4 * sizeof(cd));
+    const size_t off_bytes = a256(off.size() * sizeof(int64_t));
+    const size_t he_total = a256(hebytes * nb);
+    const size_t hp_total = a256((size_t)nslot * n2b);
+    const size_t it_bytes = a256(items.size() * sizeof(BuildItem));
+    const size_t red_bytes = a256(red.size() * sizeof(int));
+    OEFE_TRY(ensure_ws(c, tab_bytes + he_total + hp_total + off_bytes + it_bytes + red_bytes));
     char* base = (char*)c->ws;
     cd* tab = (cd*)base;
     cd* HE = (cd*)(base + tab_bytes);
-    int64_t* d_off = (int64_t*)(base + tab_bytes + he_total);
-    OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_off, off.data(), off_bytes, cudaMemcpyHostToDevice, c->stream));
+    cd* HP = (cd*)(base + tab_bytes + he_total);
+    int64_t* d_off = (int64_t*)(base + tab_bytes + he_total + hp_total);
+    BuildItem* d_items = (BuildItem*)((char*)d_off + off_bytes);
+    int* d_red = (int*)((char*)d_items + it_bytes);
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_off, off.data(), off.size() * sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+    if (!items.empty())
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_items, items.data(), items.size() * sizeof(BuildItem), cudaMemcpyHostToDevice,
+                                       c->stream));
+    if (!red.empty())
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_red, red.data(), red.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     if (off.back() > 0) {
       const int threads = 256;
       const int64_t blocks = std::min<int64_t>((off.back() + threads - 1) / threads, 1 << 20);
-      k_tabulate<<<(unsigned)blocks, threads, 0, c->stream>>>(enr_params(c), c->d_qxyz, c->d_q_off, c->d_act_off,
+      OEFE_COUNTED k_tabulate<<<(unsigned)blocks, threads, 0, c->stream>>>(enr_params(c), c->d_qxyz, c->d_q_off, c->d_act_off,
                                                              c->d_act_idx, e0, nb, d_off, K.k[0], K.k[1], K.k[2], tab);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
@@ -696,18 +788,32 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     A.dblk = dblk;
     A.MAAblk = MAAblk;
     A.E0 = (cd*)K.E0;
-    k_build_cell<<<nb, BT, smem, c->stream>>>(A);
+    A.items = mode == 0 ? d_items : nullptr;
+    A.HP = HP;
+    A.smem = smem;
+    const int grid = mode == 0 ? (int)items.size() : nb;
+    OEFE_COUNTED k_build_cell<<<grid, BT, smem, c->stream>>>(A);
     OEFE_CUDA_TRY(c, cudaGetLastError());
     if (mode == 0) {
-      const size_t tsmem = (size_t)c->nloc * 4 * sizeof(cd);
+      if (!red.empty()) {
+        const int nred = (int)red.size() / 3;
+        dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)c->npad * c->npad + 255) / 256)),
+               (unsigned)std::min(nred, 65535));
+        OEFE_COUNTED k_add_partials<<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
+        OEFE_CUDA_TRY(c, cudaGetLastError());
+      }
+      const size_t tsmem = (size_t)c->nloc * TJB * 2 * sizeof(cd);
+      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<cd, cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            (int)tsmem));
       float* H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
       double* H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
       __nv_bfloat16* Hbf = (store & OEFE_STORE_BF16X3) ? (__nv_bfloat16*)K.Hbf : nullptr;
       if (K.cplx)
-        k_transform<cd, cf><<<nb, BT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
+        OEFE_COUNTED k_transform<cd, cf><<<nb, TT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
                                                          c->ne_max, (cd*)H64, (cf*)H32, Hbf);
       else
-        k_transform<double, float><<<nb, BT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
+        OEFE_COUNTED k_transform<double, float><<<nb, TT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
                                                                 c->ne_max, H64, H32, Hbf);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
@@ -750,28 +856,28 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
     const int64_t tot = (int64_t)c->ncells * c->nloc * c->ne_max;
     const int blocks = (int)std::min<int64_t>((tot + 255) / 256, 1 << 20);
     if (K.cplx)
-      k_gamma<cd><<<blocks, 256, 0, c->stream>>>(c->d_cell_nodes, c->d_node_off, c->d_node_slot, c->d_act_off,
+      OEFE_COUNTED k_gamma<cd><<<blocks, 256, 0, c->stream>>>(c->d_cell_nodes, c->d_node_off, c->d_node_slot, c->d_act_off,
                                                 c->d_act_idx, c->d_m, dblk, c->ncells, c->nloc, c->npad, c->ne_max,
                                                 (cd*)K.gamma);
     else
-      k_gamma<double><<<blocks, 256, 0, c->stream>>>(c->d_cell_nodes, c->d_node_off, c->d_node_slot, c->d_act_off,
+      OEFE_COUNTED k_gamma<double><<<blocks, 256, 0, c->stream>>>(c->d_cell_nodes, c->d_node_off, c->d_node_slot, c->d_act_off,
                                                     c->d_act_idx, c->d_m, dblk, c->ncells, c->nloc, c->npad,
                                                     c->ne_max, K.gamma);
     if (K.cplx)
-      k_moo_cell<cd><<<c->ncells, 256, 0, c->stream>>>(c->d_act_off, c->d_m, c->d_cell_nodes, (const cd*)K.gamma,
+      OEFE_COUNTED k_moo_cell<cd><<<c->ncells, 256, 0, c->stream>>>(c->d_act_off, c->d_m, c->d_cell_nodes, (const cd*)K.gamma,
                                                       c->P, c->nloc, c->ne_max, MAAblk);
     else
-      k_moo_cell<double><<<c->ncells, 256, 0, c->stream>>>(c->d_act_off, c->d_m, c->d_cell_nodes, K.gamma, c->P,
+      OEFE_COUNTED k_moo_cell<double><<<c->ncells, 256, 0, c->stream>>>(c->d_act_off, c->d_m, c->d_cell_nodes, K.gamma, c->P,
                                                           c->nloc, c->ne_max, MAAblk);
     const int nb2 = (c->nO * c->nO + 255) / 256;
     if (K.cplx) {
-      k_moo_reduce<cd><<<nb2, 256, 0, c->stream>>>(c->d_enr_off, c->d_enr_slot, c->d_act_off, c->d_act_idx, c->nO,
+      OEFE_COUNTED k_moo_reduce<cd><<<nb2, 256, 0, c->stream>>>(c->d_enr_off, c->d_enr_slot, c->d_act_off, c->d_act_idx, c->nO,
                                                   c->npad, c->nloc, c->ne_max, MAAblk, (cd*)K.Moo);
-      k_hermitize<cd><<<nb2, 256, 0, c->stream>>>((cd*)K.Moo, c->nO);
+      OEFE_COUNTED k_hermitize<cd><<<nb2, 256, 0, c->stream>>>((cd*)K.Moo, c->nO);
     } else {
-      k_moo_reduce<double><<<nb2, 256, 0, c->stream>>>(c->d_enr_off, c->d_enr_slot, c->d_act_off, c->d_act_idx,
+      OEFE_COUNTED k_moo_reduce<double><<<nb2, 256, 0, c->stream>>>(c->d_enr_off, c->d_enr_slot, c->d_act_off, c->d_act_idx,
                                                       c->nO, c->npad, c->nloc, c->ne_max, MAAblk, K.Moo);
-      k_hermitize<double><<<nb2, 256, 0, c->stream>>>(K.Moo, c->nO);
+      OEFE_COUNTED k_hermitize<double><<<nb2, 256, 0, c->stream>>>(K.Moo, c->nO);
     }
     OEFE_CUDA_TRY(c, cudaGetLastError());
     OEFE_CUDA_TRY(c, cudaMemcpyAsync(K.Mooinv, K.Moo, (size_t)c->nO * c->nO * sb, cudaMemcpyDeviceToDevice,

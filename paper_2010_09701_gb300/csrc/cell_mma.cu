@@ -391,7 +391,7 @@ static int launch_one(oefe_ctx* c, const void* H, const void* X, int ldx, int nv
   const size_t smem = MmaCfg<CPLX, NB>::SMEM;
   dim3 grid(c->ncells, (nv + NB - 1) / NB);
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma<CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_cell_mma<CPLX, NB><<<grid, THREADS, smem, st>>>((const __nv_bfloat16*)H, (const float*)X, ldx, nv, c->d_cell_nodes,
+  OEFE_COUNTED k_cell_mma<CPLX, NB><<<grid, THREADS, smem, st>>>((const __nv_bfloat16*)H, (const float*)X, ldx, nv, c->d_cell_nodes,
                                                     c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh, (float*)Z,
                                                     c->d_status);
   OEFE_CUDA_TRY(c, cudaGetLastError());
@@ -431,7 +431,7 @@ static int launch_multi_t(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntile
   const size_t smem = MmaCfg<CPLX, NB>::SMEM;
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_multi<CPLX, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         (int)smem));
-  k_cell_mma_multi<CPLX, NB><<<grid, THREADS, smem, st>>>(d_ks, nk, ntiles, c->d_cell_nodes, c->d_act_off,
+  OEFE_COUNTED k_cell_mma_multi<CPLX, NB><<<grid, THREADS, smem, st>>>(d_ks, nk, ntiles, c->d_cell_nodes, c->d_act_off,
                                                           c->d_act_idx, c->nloc, c->npad, c->ncells, c->nh,
                                                           c->d_status);
   OEFE_CUDA_TRY(c, cudaGetLastError());

@@ -529,10 +529,10 @@ int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const
   const size_t smem = cell_mma_tma_smem(cplx);
   if (cplx) {
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_cell_mma_tma<true><<<grid, THREADS, smem, st>>>(A);
+    OEFE_COUNTED k_cell_mma_tma<true><<<grid, THREADS, smem, st>>>(A);
   } else {
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_cell_mma_tma<false><<<grid, THREADS, smem, st>>>(A);
+    OEFE_COUNTED k_cell_mma_tma<false><<<grid, THREADS, smem, st>>>(A);
   }
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;

@@ -199,7 +199,7 @@ int run_fields(oefe_ctx* c, const KData& K, int kidx, const void* X, int nv, int
   A.out = out;
   A.accumulate = accumulate;
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_fields, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_fields<<<grid, DT, smem, c->stream>>>(A);
+  OEFE_COUNTED k_fields<<<grid, DT, smem, c->stream>>>(A);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   (void)kidx;
   return OEFE_OK;

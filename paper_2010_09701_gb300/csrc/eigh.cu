@@ -225,11 +225,11 @@ int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* 
   int* d_int = (int*)(d_eps + n);
   const int b = 256, g = (int)((nn + b - 1) / b);
   int st = OEFE_OK;
-  k_to_cd<S><<<g, b, 0, c->stream>>>(H, Hc, (int)nn);
-  k_to_cd<S><<<g, b, 0, c->stream>>>(M, Mc, (int)nn);
-  k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
-  k_hermitian_part<<<g, b, 0, c->stream>>>(Mc, n);
-  k_chol_cd<<<1, 1024, 0, c->stream>>>(Mc, n, d_int);
+  OEFE_COUNTED k_to_cd<S><<<g, b, 0, c->stream>>>(H, Hc, (int)nn);
+  OEFE_COUNTED k_to_cd<S><<<g, b, 0, c->stream>>>(M, Mc, (int)nn);
+  OEFE_COUNTED k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
+  OEFE_COUNTED k_hermitian_part<<<g, b, 0, c->stream>>>(Mc, n);
+  OEFE_COUNTED k_chol_cd<<<1, 1024, 0, c->stream>>>(Mc, n, d_int);
   int info = 0;
   cudaMemcpyAsync(&info, d_int, sizeof(int), cudaMemcpyDeviceToHost, c->stream);
   cudaStreamSynchronize(c->stream);
@@ -237,14 +237,14 @@ int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* 
     c->err = "rayleigh_ritz: projected overlap not positive definite";
     st = OEFE_ERR_CHOLESKY;
   } else {
-    k_trinv_cd<<<(n + 127) / 128, 128, 0, c->stream>>>(Mc, Y, n);   // Y = L^{-1}
-    k_small_gemm<<<g, b, 0, c->stream>>>(Y, false, Hc, false, T, n);  // T = L^{-1} H
-    k_small_gemm<<<g, b, 0, c->stream>>>(T, false, Y, true, Hc, n);   // C = T L^{-+}
-    k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
-    k_jacobi<<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
-    k_sort_eig<<<(n + 127) / 128, 128, 0, c->stream>>>(Hc, W, n, d_eps, Ws);
-    k_small_gemm<<<g, b, 0, c->stream>>>(Y, true, Ws, false, T, n);   // U = L^{-+} W
-    k_from_cd<S><<<g, b, 0, c->stream>>>(T, U, (int)nn);
+    OEFE_COUNTED k_trinv_cd<<<(n + 127) / 128, 128, 0, c->stream>>>(Mc, Y, n);   // Y = L^{-1}
+    OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(Y, false, Hc, false, T, n);  // T = L^{-1} H
+    OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(T, false, Y, true, Hc, n);   // C = T L^{-+}
+    OEFE_COUNTED k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
+    OEFE_COUNTED k_jacobi<<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+    OEFE_COUNTED k_sort_eig<<<(n + 127) / 128, 128, 0, c->stream>>>(Hc, W, n, d_eps, Ws);
+    OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(Y, true, Ws, false, T, n);   // U = L^{-+} W
+    OEFE_COUNTED k_from_cd<S><<<g, b, 0, c->stream>>>(T, U, (int)nn);
     cudaMemcpyAsync(eps_host, d_eps, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     if (cudaGetLastError() != cudaSuccess) { c->err = "eigensolver launch failed"; st = OEFE_ERR_CUDA; }
     cudaStreamSynchronize(c->stream);

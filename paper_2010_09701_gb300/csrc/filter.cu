@@ -85,6 +85,63 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply(const typename Sc<T,
   }
 }
 
+// Complex FP64 cell products with three real multiplications per complex product (Gauss): with
+// P1 = Re H Re X, P2 = Im H Im X, P3 = (Re H + Im H)(Re X + Im X), Re Z = P1 - P2 and
+// Im Z = P3 - P1 - P2. The sum Re H + Im H is formed once per matrix entry by the lane that loads
+// it, Re X + Im X once per gathered element, so a product costs 3 FMAs instead of 4 on the FP64
+// pipe. Each warp takes two rows at once (one per half-warp), each lane one of 16 vectors.
+constexpr int NB3 = 16;
+__global__ void __launch_bounds__(CWARPS * 32) k_cell_apply_z3(const cd* __restrict__ H, const cd* __restrict__ X,
+                                                              int ldx, int nv, const int* __restrict__ cell_nodes,
+                                                              const int* __restrict__ act_off,
+                                                              const int* __restrict__ act_idx, int nloc, int npad,
+                                                              int64_t nh, cd* __restrict__ Z) {
+  extern __shared__ unsigned char smem_raw[];
+  double* Xr = reinterpret_cast<double*>(smem_raw);  // npad x NB3 each
+  double* Xi = Xr + (size_t)npad * NB3;
+  double* Xs = Xi + (size_t)npad * NB3;
+  const int e = blockIdx.x;
+  const int v0 = blockIdx.y * NB3;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int half = lane >> 4, hl = lane & 15;
+  const int ne = act_off[e + 1] - act_off[e];
+  const int naug = nloc + ne;
+  for (int t = threadIdx.x; t < npad * NB3; t += CWARPS * 32) {
+    const int r = t / NB3, v = t % NB3;
+    cd x = mkc(0, 0);
+    if (r < naug && v0 + v < nv) {
+      const int64_t row = r < nloc ? (int64_t)cell_nodes[(size_t)e * nloc + r] : nh + act_idx[act_off[e] + r - nloc];
+      x = X[row * ldx + v0 + v];
+    }
+    Xr[t] = x.x;
+    Xi[t] = x.y;
+    Xs[t] = x.x + x.y;
+  }
+  __syncthreads();
+  const cd* He = H + (size_t)e * npad * npad;
+  for (int r0 = 2 * warp; r0 < naug; r0 += 2 * CWARPS) {
+    const int r = r0 + half;
+    const bool rv = r < naug;
+    const cd* hr = He + (size_t)(rv ? r : r0) * npad;
+    double p1 = 0.0, p2 = 0.0, p3 = 0.0;
+    for (int k0 = 0; k0 < naug; k0 += 16) {
+      const cd hk = (rv && k0 + hl < npad) ? hr[k0 + hl] : mkc(0, 0);
+      const double hs = hk.x + hk.y;
+      const int kmax = min(16, naug - k0);
+      for (int kk = 0; kk < kmax; ++kk) {
+        const double a = __shfl_sync(0xffffffffu, hk.x, kk, 16);
+        const double b = __shfl_sync(0xffffffffu, hk.y, kk, 16);
+        const double s = __shfl_sync(0xffffffffu, hs, kk, 16);
+        const int k = (k0 + kk) * NB3 + hl;
+        p1 = fma(a, Xr[k], p1);
+        p2 = fma(b, Xi[k], p2);
+        p3 = fma(s, Xs[k], p3);
+      }
+    }
+    if (rv && v0 + hl < nv) Z[((size_t)e * npad + r) * nv + v0 + hl] = mkc(p1 - p2, p3 - p1 - p2);
+  }
+}
+
 // Node rows: y = sum of cell products; then
 //   mode 0: Y = y; mode 1: Y = y / m; mode 2: Y = alpha (y/m - c X) + beta Xm1.
 template <typename T, bool C>
@@ -105,17 +162,19 @@ __global__ void k_node_update(const typename Sc<T, C>::type* __restrict__ Z, con
     if (mode == 2) {
       const S xk = Xk[g * ldk + v];
       S out;
+      // the recurrence in the precision of the vectors (as the batched node update)
+      const T al = (T)alpha, cs = (T)cshift, be = (T)beta;
       if constexpr (C) {
-        out.x = (T)(alpha * ((double)y.x - cshift * (double)xk.x));
-        out.y = (T)(alpha * ((double)y.y - cshift * (double)xk.y));
+        out.x = al * (y.x - cs * xk.x);
+        out.y = al * (y.y - cs * xk.y);
         if (beta != 0.0) {
           const S xm = Xm1[g * ldm1 + v];
-          out.x = (T)((double)out.x + beta * (double)xm.x);
-          out.y = (T)((double)out.y + beta * (double)xm.y);
+          out.x += be * xm.x;
+          out.y += be * xm.y;
         }
       } else {
-        out = (T)(alpha * ((double)y - cshift * (double)xk));
-        if (beta != 0.0) out = (T)((double)out + beta * (double)Xm1[g * ldm1 + v]);
+        out = al * (y - cs * xk);
+        if (beta != 0.0) out += be * Xm1[g * ldm1 + v];
       }
       y = out;
     }
@@ -190,38 +249,81 @@ struct NodeK {
   double alpha, cshift, beta;
 };
 
+// Node rows of every k-point in one launch (blockIdx.y = k): one warp per node row with all of its
+// vectors. The product rows of up to 8 slots are loaded before any is summed, so their latencies
+// overlap (the slot indices are warp-uniform broadcast loads); rows whose width and leading
+// dimensions allow it move as float4. Complex rows are handled as interleaved reals (every
+// operation here is componentwise). The recurrence runs in the filter's precision.
 template <typename T, bool C>
-__global__ void k_node_update_multi(const NodeK* __restrict__ P, const int64_t* __restrict__ node_off,
-                                    const int64_t* __restrict__ node_slot, const double* __restrict__ m, int64_t nh) {
-  using S = typename Sc<T, C>::type;
+__global__ void __launch_bounds__(256) k_node_update_multi(const NodeK* __restrict__ P,
+                                                           const int64_t* __restrict__ node_off,
+                                                           const int64_t* __restrict__ node_slot,
+                                                           const double* __restrict__ m, int64_t nh) {
   const NodeK p = P[blockIdx.y];
-  const S* Z = (const S*)p.Z;
-  const S* Xk = (const S*)p.Xk;
-  const S* Xm1 = (const S*)p.Xm1;
-  S* Y = (S*)p.Y;
-  const int nv = p.nv;
-  const int64_t total = nh * nv;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t g = t / nv;
-    const int v = (int)(t % nv);
-    S y = Sc<T, C>::zero();
-    for (int64_t s = node_off[g]; s < node_off[g + 1]; ++s) y = Sc<T, C>::add(y, Z[node_slot[s] * nv + v]);
-    y = Sc<T, C>::scale(y, 1.0 / m[g]);
-    const S xk = Xk[g * p.ldk + v];
-    S out;
-    if constexpr (C) {
-      out.x = (T)(p.alpha * ((double)y.x - p.cshift * (double)xk.x));
-      out.y = (T)(p.alpha * ((double)y.y - p.cshift * (double)xk.y));
-      if (p.beta != 0.0) {
-        const S xm = Xm1[g * p.ldm1 + v];
-        out.x = (T)((double)out.x + p.beta * (double)xm.x);
-        out.y = (T)((double)out.y + p.beta * (double)xm.y);
+  constexpr int R = C ? 2 : 1;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int W = p.nv * R;
+  const int ldk = p.ldk * R, ldm1 = p.ldm1 * R, ldy = p.ldy * R;
+  const T* Z = (const T*)p.Z;
+  const T* Xk = (const T*)p.Xk;
+  const T* Xm1 = (const T*)p.Xm1;
+  T* Y = (T*)p.Y;
+  const T alpha = (T)p.alpha, cs = (T)p.cshift, beta = (T)p.beta;
+  const bool has_m1 = p.beta != 0.0;
+  const bool vec = sizeof(T) == 4 && W % 4 == 0 && ldk % 4 == 0 && ldy % 4 == 0 && (!has_m1 || ldm1 % 4 == 0) &&
+                   ((uintptr_t)Z & 15) == 0 && ((uintptr_t)Xk & 15) == 0 && ((uintptr_t)Y & 15) == 0 &&
+                   (!has_m1 || ((uintptr_t)Xm1 & 15) == 0);
+  for (int64_t g = warp0; g < nh; g += nwarps) {
+    const int64_t s0 = node_off[g];
+    const int ns = (int)(node_off[g + 1] - s0);
+    const T minv = (T)(1.0 / m[g]);
+    if (vec) {
+      for (int f = 4 * lane; f < W; f += 128) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int s8 = 0; s8 < ns; s8 += 8) {
+          // slot indices: the same address in every lane (one broadcast load each), then the rows
+          int64_t sl[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) sl[u] = s8 + u < ns ? node_slot[s0 + s8 + u] : 0;
+          float4 z[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            z[u] = s8 + u < ns ? *reinterpret_cast<const float4*>((const float*)Z + sl[u] * W + f)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            acc.x += z[u].x;
+            acc.y += z[u].y;
+            acc.z += z[u].z;
+            acc.w += z[u].w;
+          }
+        }
+        const float4 xk = *reinterpret_cast<const float4*>((const float*)Xk + g * ldk + f);
+        float4 o;
+        o.x = (float)alpha * (acc.x * (float)minv - (float)cs * xk.x);
+        o.y = (float)alpha * (acc.y * (float)minv - (float)cs * xk.y);
+        o.z = (float)alpha * (acc.z * (float)minv - (float)cs * xk.z);
+        o.w = (float)alpha * (acc.w * (float)minv - (float)cs * xk.w);
+        if (has_m1) {
+          const float4 xm = *reinterpret_cast<const float4*>((const float*)Xm1 + g * ldm1 + f);
+          o.x += (float)beta * xm.x;
+          o.y += (float)beta * xm.y;
+          o.z += (float)beta * xm.z;
+          o.w += (float)beta * xm.w;
+        }
+        *reinterpret_cast<float4*>((float*)Y + g * ldy + f) = o;
       }
     } else {
-      out = (T)(p.alpha * ((double)y - p.cshift * (double)xk));
-      if (p.beta != 0.0) out = (T)((double)out + p.beta * (double)Xm1[g * p.ldm1 + v]);
+      for (int f = lane; f < W; f += 32) {
+        T acc = T(0);
+        for (int s = 0; s < ns; ++s) acc += Z[node_slot[s0 + s] * W + f];
+        T o = alpha * (acc * minv - cs * Xk[g * ldk + f]);
+        if (has_m1) o += beta * Xm1[g * ldm1 + f];
+        Y[g * ldy + f] = o;
+      }
     }
-    Y[g * p.ldy + v] = out;
   }
 }
 
@@ -285,7 +387,7 @@ template <typename A, typename B>
 int convert(oefe_ctx* c, const void* X, int ldx, void* Y, int ldy, int64_t n, int width) {
   const int64_t tot = n * width;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
-  k_convert<A, B><<<blocks, 256, 0, c->stream>>>((const A*)X, ldx, (B*)Y, ldy, n, width);
+  OEFE_COUNTED k_convert<A, B><<<blocks, 256, 0, c->stream>>>((const A*)X, ldx, (B*)Y, ldy, n, width);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
 }
@@ -302,25 +404,33 @@ int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const vo
   if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
   if (mma) {
     OEFE_TRY(launch_cell_mma(c, K, Xin, ldin, nv, C, Zbuf));
+  } else if (sizeof(T) == 8 && C) {
+    dim3 grid(c->ncells, (nv + NB3 - 1) / NB3);
+    const size_t smem = (size_t)c->npad * NB3 * 3 * sizeof(double);
+    if (smem > 227 * 1024) { c->err = "cell matrices too large for the shared-memory gather"; return OEFE_ERR_ARG; }
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply_z3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    OEFE_COUNTED k_cell_apply_z3<<<grid, CWARPS * 32, smem, c->stream>>>((const cd*)Hm, (const cd*)Xin, ldin, nv,
+                                                                        c->d_cell_nodes, c->d_act_off, c->d_act_idx,
+                                                                        c->nloc, c->npad, c->nh, (cd*)Zbuf);
   } else {
     dim3 grid(c->ncells, (nv + NB - 1) / NB);
     const size_t smem = (size_t)c->npad * NB * sizeof(S);
     if (smem > 227 * 1024) { c->err = "cell matrices too large for the shared-memory gather"; return OEFE_ERR_ARG; }
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    k_cell_apply<T, C><<<grid, CWARPS * 32, smem, c->stream>>>((const S*)Hm, (const S*)Xin, ldin, nv, c->d_cell_nodes,
+    OEFE_COUNTED k_cell_apply<T, C><<<grid, CWARPS * 32, smem, c->stream>>>((const S*)Hm, (const S*)Xin, ldin, nv, c->d_cell_nodes,
                                                                c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh,
                                                                (S*)Zbuf);
   }
   if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
   const int64_t tot = c->nh * nv;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
-  k_node_update<T, C><<<blocks, 256, 0, c->stream>>>((const S*)Zbuf, c->d_node_off, c->d_node_slot, c->d_m, c->nh,
+  OEFE_COUNTED k_node_update<T, C><<<blocks, 256, 0, c->stream>>>((const S*)Zbuf, c->d_node_off, c->d_node_slot, c->d_m, c->nh,
                                                      nv, st.mode, st.alpha, st.cshift, st.beta, (const S*)Xk, ldk,
                                                      (const S*)Xm1, ldm1, (S*)Y, ldy);
   if (c->nO > 0) {
     const int eb = (c->nO * nv + 127) / 128;
-    k_enr_reduce<T, C><<<eb, 128, 0, c->stream>>>((const S*)Zbuf, c->d_enr_off, c->d_enr_slot, c->nO, nv, Yo);
-    k_enr_update<T, C><<<eb, 128, 0, c->stream>>>(Yo, K.Mooinv, c->nO, nv, c->nh, st.mode, st.alpha, st.cshift,
+    OEFE_COUNTED k_enr_reduce<T, C><<<eb, 128, 0, c->stream>>>((const S*)Zbuf, c->d_enr_off, c->d_enr_slot, c->nO, nv, Yo);
+    OEFE_COUNTED k_enr_update<T, C><<<eb, 128, 0, c->stream>>>(Yo, K.Mooinv, c->nO, nv, c->nh, st.mode, st.alpha, st.cshift,
                                                   st.beta, (const S*)Xk, ldk, (const S*)Xm1, ldm1, (S*)Y, ldy);
   }
   OEFE_CUDA_TRY(c, cudaGetLastError());
@@ -530,7 +640,8 @@ struct BatchPlan {
 
 int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const MmaK* d_mk, const NodeK* d_nd,
                            bool timed) {
-  const int blocks = std::max(1, std::min(c->num_sms * 8, (int)((c->nh * 64 + 255) / 256)));
+  // node update: one warp per node, 8 warps per CTA, enough CTAs to fill every SM several times over
+  const int nblocks = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)c->num_sms * 16, (c->nh + 7) / 8));
   int vmax = 0;
   for (int k = 0; k < P.nk; ++k) vmax = std::max(vmax, P.nd[k].nv);
   const int eb = (c->nO * vmax + 127) / 128;
@@ -548,22 +659,22 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
       }
     }
     if (timed) cudaEventRecordWithFlags(c->bev_kernel[2 * j + 1], c->bstream, cudaEventRecordExternal);
-    dim3 g1(blocks, P.nk), g2(std::max(eb, 1), P.nk);
+    dim3 g1(nblocks, P.nk), g2(std::max(eb, 1), P.nk);
     if (cplx) {
-      k_node_update_multi<float, true><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off, c->d_node_slot,
+      OEFE_COUNTED k_node_update_multi<float, true><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off, c->d_node_slot,
                                                                    c->d_m, c->nh);
       if (c->nO > 0) {
-        k_enr_reduce_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off, c->d_enr_slot,
+        OEFE_COUNTED k_enr_reduce_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off, c->d_enr_slot,
                                                                     c->nO);
-        k_enr_update_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
+        OEFE_COUNTED k_enr_update_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
       }
     } else {
-      k_node_update_multi<float, false><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off,
+      OEFE_COUNTED k_node_update_multi<float, false><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off,
                                                                     c->d_node_slot, c->d_m, c->nh);
       if (c->nO > 0) {
-        k_enr_reduce_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
+        OEFE_COUNTED k_enr_reduce_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
                                                                      c->d_enr_slot, c->nO);
-        k_enr_update_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
+        OEFE_COUNTED k_enr_update_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
       }
     }
     OEFE_CUDA_TRY(c, cudaGetLastError());
@@ -595,6 +706,11 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   const size_t es_low = dtype_bytes(dt_low), es = dtype_bytes(dtype);
   const int64_t n = c->nh + c->nO;
   const int jlow = mixed ? degree - 1 : degree;
+  if (jlow == 0) {  // a single FP64 degree: no low-precision work to batch
+    for (int k = 0; k < nk; ++k)
+      OEFE_TRY(cheb_filter(c, k, X[k], nv[k], ld[k], dtype, degree, a[k], b[k], a0[k], 0));
+    return OEFE_OK;
+  }
   if (c->tune_nb == 0) { c->tune_nb = 64; c->tune_grid = c->num_sms; }
   if (c->use_tma && c->d_tmaps) c->tune_nb = 64;
   // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed)
@@ -737,18 +853,22 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
     cudaGraph_t graph;
     OEFE_CUDA_TRY(c, cudaStreamBeginCapture(c->bstream, cudaStreamCaptureModeThreadLocal));
+    const long long launches0 = oefe_launch_add(0);
     int st = OEFE_OK;
     if (mixed) {
       for (int k = 0; k < nk && st == OEFE_OK; ++k) {
         const int width = cplx ? 2 * nv[k] : nv[k];
         const int64_t tot = n * width;
         const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
-        k_convert<double, float><<<blocks, 256, 0, c->bstream>>>((const double*)X[k], ld[k] * (cplx ? 2 : 1),
+        OEFE_COUNTED k_convert<double, float><<<blocks, 256, 0, c->bstream>>>((const double*)X[k], ld[k] * (cplx ? 2 : 1),
                                                                  (float*)L0[k], width, n, width);
       }
     }
     if (st == OEFE_OK) st = batched_launch_degrees(c, P, cplx, d_mk, d_nd, timed);
     cudaError_t ce = cudaStreamEndCapture(c->bstream, &graph);
+    // captured launches run at each replay, not here
+    c->bgraph_kernels = oefe_launch_add(0) - launches0;
+    oefe_launch_add(-c->bgraph_kernels);
     if (st != OEFE_OK) return st;
     if (ce != cudaSuccess) { c->err = std::string("graph capture: ") + cudaGetErrorString(ce); return OEFE_ERR_CUDA; }
     ce = cudaGraphInstantiate(&c->bgraph, graph, 0);
@@ -760,6 +880,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_in, c->stream));
   OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->bstream, c->bev_in, 0));
   OEFE_CUDA_TRY(c, cudaGraphLaunch(c->bgraph, c->bstream));
+  oefe_launch_add(c->bgraph_kernels);
   OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_out, c->bstream));
   OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->bev_out, 0));
   if (timed) {

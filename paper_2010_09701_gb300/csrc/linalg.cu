@@ -28,6 +28,17 @@ template <> struct Ops<cd> {
   __host__ __device__ static cd scale(cd a, double s) { return a * s; }
 };
 
+// acc += conj(a) b and acc += a b as explicit FMA chains (4 FP64 FMAs per complex product; the
+// expression forms would compile to a multiply, an FMA and an add per real part)
+__device__ __forceinline__ double fma_c(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ cd fma_c(cd a, cd b, cd acc) {
+  return mkc(fma(a.x, b.x, fma(a.y, b.y, acc.x)), fma(a.x, b.y, fma(-a.y, b.x, acc.y)));
+}
+__device__ __forceinline__ double fma_n(double a, double b, double acc) { return fma(a, b, acc); }
+__device__ __forceinline__ cd fma_n(cd a, cd b, cd acc) {
+  return mkc(fma(a.x, b.x, fma(-a.y, b.y, acc.x)), fma(a.x, b.y, fma(a.y, b.x, acc.y)));
+}
+
 // In-place lower Cholesky A = L L^+ of an n x n Hermitian matrix (single CTA).
 // info = 0 on success, j+1 if the j-th pivot is not positive.
 template <typename S>
@@ -95,15 +106,23 @@ __global__ void k_yhy(const S* Y, S* B, int n) {
   B[t] = s;
 }
 
-// Partial Gram matrices S_part[chunk] = X[rows]^+ W[rows], tiles of 32 x 32.
+// Partial Gram matrices S_part[chunk] = X[rows]^+ W[rows], tiles of 32 x 32. With herm, only the
+// tiles on and above the diagonal (the result is Hermitian: X^+ M X, X^+ H X); blockIdx.y then
+// enumerates those tile pairs.
 constexpr int GT = 32;
 constexpr int GR = 32;
 template <typename S>
 __global__ void __launch_bounds__(256) k_gram(const S* X, int ldx, const S* W, int ldw, int64_t n, int nv,
-                                              int64_t rows_per_chunk, S* part) {
+                                              int64_t rows_per_chunk, S* part, bool herm, int tiles) {
   __shared__ S xs[GR][GT];
   __shared__ S ws[GR][GT];
-  const int ti = blockIdx.y, tj = blockIdx.z;
+  int ti = blockIdx.y, tj = blockIdx.z;
+  if (herm) {  // y -> (ti, tj), ti <= tj, row-major over the upper triangle of tiles
+    int y = blockIdx.y;
+    ti = 0;
+    while (y >= tiles - ti) { y -= tiles - ti; ++ti; }
+    tj = ti + y;
+  }
   const int64_t r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;  // 2 x 2 entries each: (2ty..), (2tx..)
   S acc[2][2];
@@ -121,10 +140,10 @@ __global__ void __launch_bounds__(256) k_gram(const S* X, int ldx, const S* W, i
     for (int rr = 0; rr < GR; ++rr) {
       const S x0 = xs[rr][2 * ty], x1 = xs[rr][2 * ty + 1];
       const S w0 = ws[rr][2 * tx], w1 = ws[rr][2 * tx + 1];
-      acc[0][0] = acc[0][0] + Ops<S>::mulc(x0, w0);
-      acc[0][1] = acc[0][1] + Ops<S>::mulc(x0, w1);
-      acc[1][0] = acc[1][0] + Ops<S>::mulc(x1, w0);
-      acc[1][1] = acc[1][1] + Ops<S>::mulc(x1, w1);
+      acc[0][0] = fma_c(x0, w0, acc[0][0]);
+      acc[0][1] = fma_c(x0, w1, acc[0][1]);
+      acc[1][0] = fma_c(x1, w0, acc[1][0]);
+      acc[1][1] = fma_c(x1, w1, acc[1][1]);
     }
     __syncthreads();
   }
@@ -136,12 +155,16 @@ __global__ void __launch_bounds__(256) k_gram(const S* X, int ldx, const S* W, i
 }
 
 template <typename S>
-__global__ void k_sum_parts(const S* part, int nchunk, int nv, S* out) {
+__global__ void k_sum_parts(const S* part, int nchunk, int nv, S* out, bool herm) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nv * nv) return;
+  const int i = t / nv, j = t % nv;
+  // below the diagonal tiles of a Hermitian result: the conjugate of the mirrored entry
+  const bool mirror = herm && j / GT < i / GT;
+  const int src = mirror ? j * nv + i : t;
   S s = Ops<S>::zero();
-  for (int c = 0; c < nchunk; ++c) s = s + part[(size_t)c * nv * nv + t];
-  out[t] = s;
+  for (int c = 0; c < nchunk; ++c) s = s + part[(size_t)c * nv * nv + src];
+  out[t] = mirror ? Ops<S>::conj(s) : s;
 }
 
 // W = M X: lumped diagonal rows, dense M^oo rows.
@@ -163,7 +186,8 @@ __global__ void k_apply_M(const S* X, int ldx, const double* m, const S* Moo, in
   }
 }
 
-// X[rows] <- X[rows] C (C nv x nv), or X C^+ when herm.
+// X[rows] <- X[rows] C (C nv x nv), or X C^+ when herm; with herm, C is lower triangular (the
+// inverse Cholesky factor), so only k <= j contributes.
 template <typename S>
 __global__ void k_rotate(S* X, int ldx, int64_t n, int nv, const S* C, bool herm, int rows) {
   extern __shared__ unsigned char sm[];
@@ -176,9 +200,10 @@ __global__ void k_rotate(S* X, int ldx, int64_t n, int nv, const S* C, bool herm
   for (int t = threadIdx.x; t < nr * nv; t += blockDim.x) {
     const int r = t / nv, j = t % nv;
     S s = Ops<S>::zero();
-    for (int k = 0; k < nv; ++k) {
-      const S cv = herm ? Ops<S>::conj(C[(size_t)j * nv + k]) : C[(size_t)k * nv + j];
-      s = s + Ops<S>::mul(xs[r * nv + k], cv);
+    if (herm) {
+      for (int k = 0; k <= j; ++k) s = fma_n(xs[r * nv + k], Ops<S>::conj(C[(size_t)j * nv + k]), s);
+    } else {
+      for (int k = 0; k < nv; ++k) s = fma_n(xs[r * nv + k], C[(size_t)k * nv + j], s);
     }
     X[(r0 + r) * ldx + j] = s;
   }
@@ -198,6 +223,26 @@ __global__ void k_resid_norms(const S* R, int ldr, const double* m, const S* Moo
   for (int t = threadIdx.x; t < nO * nO; t += blockDim.x) {
     const int i = t / nO, j = t % nO;
     s += Ops<S>::re(Ops<S>::mulc(R[(nh + i) * ldr + v], Ops<S>::mul(Mooinv[t], R[(nh + j) * ldr + v])));
+  }
+  __shared__ double red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[v] = red[0];
+}
+
+// out[v] = Re (U^+ Mq U)[v][v]: the M-norms^2 of the rotated vectors X U from the Gram matrix of X
+template <typename S>
+__global__ void k_quad_diag(const S* Mq, const S* U, int nv, double* out) {
+  const int v = blockIdx.x;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+    S row = Ops<S>::zero();
+    for (int j = 0; j < nv; ++j) row = fma_n(Mq[(size_t)i * nv + j], U[(size_t)j * nv + v], row);
+    s += Ops<S>::re(Ops<S>::mulc(U[(size_t)i * nv + v], row));
   }
   __shared__ double red[256];
   red[threadIdx.x] = s;
@@ -272,14 +317,15 @@ __global__ void k_dot_final(const double* part, int nb, double* out) {
 }
 
 // ------------------------------------------------------------------ host helpers
+// out = X^+ W (nv x nv); herm: the result is known to be Hermitian, only its upper tiles are summed
 template <typename S>
 int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, S* part_buf,
-         int nchunk) {
+         int nchunk, bool herm = true) {
   const int tiles = (nv + GT - 1) / GT;
   const int64_t rpc = (n + nchunk - 1) / nchunk;
-  dim3 grid(nchunk, tiles, tiles);
-  k_gram<S><<<grid, 256, 0, c->stream>>>(X, ldx, W, ldw, n, nv, rpc, part_buf);
-  k_sum_parts<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(part_buf, nchunk, nv, out);
+  dim3 grid(nchunk, herm ? tiles * (tiles + 1) / 2 : tiles, herm ? 1 : tiles);
+  OEFE_COUNTED k_gram<S><<<grid, 256, 0, c->stream>>>(X, ldx, W, ldw, n, nv, rpc, part_buf, herm, tiles);
+  OEFE_COUNTED k_sum_parts<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(part_buf, nchunk, nv, out, herm);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
 }
@@ -290,7 +336,7 @@ int rotate(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm)
   const int64_t blocks = (n + rows - 1) / rows;
   const size_t smem = (size_t)rows * nv * sizeof(S);
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_rotate<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  k_rotate<S><<<(unsigned)blocks, 256, smem, c->stream>>>(X, ldx, n, nv, C, herm, rows);
+  OEFE_COUNTED k_rotate<S><<<(unsigned)blocks, 256, smem, c->stream>>>(X, ldx, n, nv, C, herm, rows);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
 }
@@ -299,28 +345,30 @@ template <typename S>
 int apply_M(oefe_ctx* c, const KData& K, const S* X, int ldx, int nv, S* W, int ldw) {
   const int64_t tot = (c->nh + c->nO) * nv;
   const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
-  k_apply_M<S><<<blocks, 256, 0, c->stream>>>(X, ldx, c->d_m, (const S*)K.Moo, c->nh, c->nO, nv, W, ldw);
+  OEFE_COUNTED k_apply_M<S><<<blocks, 256, 0, c->stream>>>(X, ldx, c->d_m, (const S*)K.Moo, c->nh, c->nO, nv, W, ldw);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
 }
 
+// row chunks of the Gram kernel: about four CTAs per SM over the upper tile pairs
 int nchunks_for(oefe_ctx* c, int nv) {
   const int tiles = (nv + GT - 1) / GT;
-  return std::max(1, std::min(1024, 2 * c->num_sms / (tiles * tiles) + 1));
+  const int pairs = tiles * (tiles + 1) / 2;
+  return std::max(1, std::min(1024, (4 * c->num_sms + pairs - 1) / pairs));
 }
 
 template <typename S>
 int chol_inverse_t(oefe_ctx* c, S* A, int n, bool inverse, bool want_Linv, S* Y, int* info_host) {
   OEFE_TRY(ensure_ws2(c, 256));
   int* d_info = c->d_status;
-  k_chol<S><<<1, 1024, 0, c->stream>>>(A, n, d_info);
+  OEFE_COUNTED k_chol<S><<<1, 1024, 0, c->stream>>>(A, n, d_info);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   OEFE_CUDA_TRY(c, cudaMemcpyAsync(info_host, d_info, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   if (*info_host != 0) return OEFE_OK;
   if (inverse || want_Linv) {
-    k_trinv<S><<<(n + 127) / 128, 128, 0, c->stream>>>(A, Y, n);
-    if (inverse) k_yhy<S><<<(n * n + 255) / 256, 256, 0, c->stream>>>(Y, A, n);
+    OEFE_COUNTED k_trinv<S><<<(n + 127) / 128, 128, 0, c->stream>>>(A, Y, n);
+    if (inverse) OEFE_COUNTED k_yhy<S><<<(n * n + 255) / 256, 256, 0, c->stream>>>(Y, A, n);
     OEFE_CUDA_TRY(c, cudaGetLastError());
   }
   return OEFE_OK;
@@ -386,7 +434,7 @@ int rayleigh_ritz_t(oefe_ctx* c, int ik, S* X, int nv, int ld, int dtype, double
   const size_t sbytes = (((size_t)nv * nv * sizeof(S) + 255) / 256) * 256;
   const size_t pbytes = (((size_t)nchunk * nv * nv * sizeof(S) + 255) / 256) * 256;
   // ws is used by apply_op; keep HX, MX and small matrices in ws2
-  OEFE_TRY(ensure_ws2(c, 2 * vbytes + 3 * sbytes + pbytes + (size_t)nv * 24 + 256));
+  OEFE_TRY(ensure_ws2(c, 2 * vbytes + 3 * sbytes + pbytes + (size_t)nv * 32 + 256));
   char* base = (char*)c->ws2;
   S* HX = (S*)base;
   S* MX = (S*)(base + vbytes);
@@ -408,17 +456,17 @@ int rayleigh_ritz_t(oefe_ctx* c, int ik, S* X, int nv, int ld, int dtype, double
     OEFE_TRY(rotate<S>(c, MX, nv, n, nv, U, false));
     const int64_t tot = n * nv;
     const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
-    k_resid_vec<S><<<blocks, 256, 0, c->stream>>>(HX, MX, nv, d_eps, n, nv, HX);  // HX <- residual
+    OEFE_COUNTED k_resid_vec<S><<<blocks, 256, 0, c->stream>>>(HX, MX, nv, d_eps, n, nv, HX);  // HX <- residual
     double* d_num = d_eps + nv;
-    k_resid_norms<S><<<nv, 256, 0, c->stream>>>(HX, nv, c->d_m, (const S*)K.Mooinv, c->nh, c->nO, nv, d_num);
-    // ||u||_M^2 = u^+ M u: with MX = M u, use the Gram diagonal
-    OEFE_TRY(gram<S>(c, X, ld, MX, nv, n, nv, Mq, part, nchunk));
-    std::vector<double> num(nv);
-    std::vector<S> mq((size_t)nv * nv);
+    OEFE_COUNTED k_resid_norms<S><<<nv, 256, 0, c->stream>>>(HX, nv, c->d_m, (const S*)K.Mooinv, c->nh, c->nO, nv, d_num);
+    // ||u_v||_M^2 = (U^+ (X^+ M X) U)[v][v] from the Gram matrix taken before the rotation
+    double* d_den = d_num + nv;
+    OEFE_COUNTED k_quad_diag<S><<<nv, 256, 0, c->stream>>>(Mq, U, nv, d_den);
+    std::vector<double> num(nv), den(nv);
     OEFE_CUDA_TRY(c, cudaMemcpyAsync(num.data(), d_num, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    OEFE_CUDA_TRY(c, cudaMemcpyAsync(mq.data(), Mq, mq.size() * sizeof(S), cudaMemcpyDeviceToHost, c->stream));
+    OEFE_CUDA_TRY(c, cudaMemcpyAsync(den.data(), d_den, nv * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    for (int v = 0; v < nv; ++v) resid[v] = std::sqrt(std::max(num[v], 0.0) / Ops<S>::re(mq[(size_t)v * nv + v]));
+    for (int v = 0; v < nv; ++v) resid[v] = std::sqrt(std::max(num[v], 0.0) / den[v]);
   }
   for (int v = 0; v < nv; ++v) eig[v] = w[v];
   OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -475,8 +523,8 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
   auto mdot = [&](const void* x, const void* y, double* out) -> int {  // re(x^+ M y)
     if (dtype == OEFE_C128) OEFE_TRY(apply_M<cd>(c, K, (const cd*)y, 1, 1, (cd*)mw, 1));
     else OEFE_TRY(apply_M<double>(c, K, (const double*)y, 1, 1, (double*)mw, 1));
-    k_dot_partial<<<nparts, 256, 0, c->stream>>>((const double*)x, (const double*)mw, nreal, d_part);
-    k_dot_final<<<1, 256, 0, c->stream>>>(d_part, nparts, d_dot);
+    OEFE_COUNTED k_dot_partial<<<nparts, 256, 0, c->stream>>>((const double*)x, (const double*)mw, nreal, d_part);
+    OEFE_COUNTED k_dot_final<<<1, 256, 0, c->stream>>>(d_part, nparts, d_dot);
     OEFE_CUDA_TRY(c, cudaMemcpyAsync(out, d_dot, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
     return OEFE_OK;
@@ -484,9 +532,9 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
   auto applyA = [&]() -> int {  // w = M^{-1} H q
     if (!low) return apply_op2(c, ik, q, 1, w, 1, 1, dtype, true);
     const int lb2 = (int)std::min<int64_t>((nreal + 255) / 256, (int64_t)c->num_sms * 16);
-    k_to_float<<<lb2, 256, 0, c->stream>>>((const double*)q, q32, nreal);
+    OEFE_COUNTED k_to_float<<<lb2, 256, 0, c->stream>>>((const double*)q, q32, nreal);
     OEFE_TRY(apply_low(c, ik, q32, w32, dtype == OEFE_C128 ? OEFE_C64 : OEFE_F32));
-    k_to_double<<<lb2, 256, 0, c->stream>>>(w32, (double*)w, nreal);
+    OEFE_COUNTED k_to_double<<<lb2, 256, 0, c->stream>>>(w32, (double*)w, nreal);
     OEFE_CUDA_TRY(c, cudaGetLastError());
     return OEFE_OK;
   };
@@ -495,14 +543,14 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
   double nrm;
   OEFE_TRY(mdot(q, q, &nrm));
   const int lb = (int)std::min<int64_t>((nreal + 255) / 256, (int64_t)c->num_sms * 16);
-  k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, nullptr, nullptr, nullptr, nreal, 1.0 / std::sqrt(nrm), 0, 0);
+  OEFE_COUNTED k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, nullptr, nullptr, nullptr, nreal, 1.0 / std::sqrt(nrm), 0, 0);
   double beta = 0.0;
   for (int it = 0; it < steps; ++it) {
     OEFE_TRY(applyA());
     double alpha;
     OEFE_TRY(mdot(q, w, &alpha));
     // w <- w - alpha q - beta qp
-    k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)w, (const double*)q, (const double*)qp, nullptr, nreal, 1.0,
+    OEFE_COUNTED k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)w, (const double*)q, (const double*)qp, nullptr, nreal, 1.0,
                                                 -alpha, -beta);
     double bb;
     OEFE_TRY(mdot(w, w, &bb));
@@ -510,8 +558,8 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
     al.push_back(alpha);
     be.push_back(beta);
     // qp <- q, q <- w / beta
-    k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)qp, (const double*)q, nullptr, (double*)q, nreal, 0.0, 1.0, 0);
-    k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, (const double*)w, nullptr, nullptr, nreal, 0.0, 1.0 / beta, 0);
+    OEFE_COUNTED k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)qp, (const double*)q, nullptr, (double*)q, nreal, 0.0, 1.0, 0);
+    OEFE_COUNTED k_lanczos_axpy<<<lb, 256, 0, c->stream>>>((double*)q, (const double*)w, nullptr, nullptr, nreal, 0.0, 1.0 / beta, 0);
     OEFE_CUDA_TRY(c, cudaGetLastError());
   }
   // largest eigenvalue of the Lanczos tridiagonal matrix

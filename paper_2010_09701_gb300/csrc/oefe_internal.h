@@ -159,10 +159,16 @@ struct oefe_ctx {
   std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
   int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
   int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
+  long long bgraph_kernels = 0;         // kernel launches captured in the batched graph (counted per replay)
   double tune_ms[4] = {0, 0, 0, 0};
   void* d_tmaps = nullptr;              // one tensor map per k-point (split cell matrices)
   int n_tmaps = 0;
 };
+
+// process-wide count of kernel launches issued by the library; every launch site is prefixed with
+// OEFE_COUNTED (a comma expression, so it also works as the body of an unbraced if)
+long long oefe_launch_add(long long n);
+#define OEFE_COUNTED oefe_launch_add(1),
 
 // record an event pair around a launch when timing is on
 cudaEvent_t timing_event(oefe_ctx* c);

@@ -140,7 +140,20 @@ def config_c3_small():
     return w
 
 
-CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5}
+def config_c3_mid():
+    """The c3 cell on a 12^3 graded mesh with two k-points: a profiling case
+    whose vectors (0.19 GB) and cell products (0.34 GB per k) exceed the L2
+    cache like the full workload's, at 2 GB of split cell matrices per k."""
+    w = config_c2()
+    w.name = "c3mid_8atom_12cube_p6_2k"
+    w.ncell = 12
+    w.nv = [64, 64]
+    w.kgrid = (2, 1, 1)
+    w.dtype = "c64"
+    return w
+
+
+CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c3mid": config_c3_mid, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5}
 
 
 def graded_breakpoints(a, ncell, coords, ratio=1.5, tol=1e-3):
