@@ -26,13 +26,16 @@ constexpr size_t SMEM_BUILD = 96 * 1024;   // build mode: two CTAs per SM
 
 // Tabulate N^A and grad N^A for (point, active function) pairs of a batch of cells.
 // tab entry layout: 4 complex values (value, d/dx, d/dy, d/dz) per (q, j), j fastest.
+// Active sets hold whole atoms (nfun consecutive functions), so one thread takes one (point, atom)
+// and evaluates what the atom's functions share (offset, cutoff, phase) once.
 __global__ void k_tabulate(EnrParams E, const double* qxyz, const int64_t* q_off, const int* act_off,
                            const int* act_idx, int e0, int ncell_b, const int64_t* tab_off,
                            double kx, double ky, double kz, cd* tab) {
-  const int64_t total = tab_off[ncell_b];
+  const int64_t total = E.nfun > 0 ? tab_off[ncell_b] / E.nfun : 0;
   const double k[3] = {kx, ky, kz};
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
+  for (int64_t tb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; tb < total;
+       tb += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t t = tb * E.nfun;
     int lo = 0, hi = ncell_b - 1;
     while (lo < hi) {  // last b with tab_off[b] <= t
       int mid = (lo + hi + 1) / 2;
@@ -42,16 +45,20 @@ __global__ void k_tabulate(EnrParams E, const double* qxyz, const int64_t* q_off
     const int ne = act_off[e + 1] - act_off[e];
     const int64_t r = t - tab_off[lo];
     const int64_t q = q_off[e] + r / ne;
-    const int j = (int)(r % ne);
-    const int nu = act_idx[act_off[e] + j];
+    const int j0 = (int)(r % ne);
+    const int I = act_idx[act_off[e] + j0] / E.nfun;
     const double x[3] = {qxyz[3 * q], qxyz[3 * q + 1], qxyz[3 * q + 2]};
-    cd v, g[3];
-    enrichment_value(E, nu, x, k, &v, g);
-    cd* o = tab + 4 * t;
-    o[0] = v;
-    o[1] = g[0];
-    o[2] = g[1];
-    o[3] = g[2];
+    AtomGeom G;
+    atom_geom(E, I, x, k, true, G);
+    for (int f = 0; f < E.nfun; ++f) {
+      cd v, g[3];
+      atom_function(E, I, f, G, k, &v, g);
+      cd* o = tab + 4 * (t + f);
+      o[0] = v;
+      o[1] = g[0];
+      o[2] = g[1];
+      o[3] = g[2];
+    }
   }
 }
 
@@ -253,12 +260,12 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
           for (int qz = 0; qz < n1; ++qz) {
             const int q = qxy + n2 * qz;
             const double l = Lt[2][qz][c];
-            g0 += l * F[q];
+            g0 = rfma(l, F[q], g0);
             if (full) {
-              gx += l * F[n3 + q];
-              gy += l * F[2 * n3 + q];
-              gz += Dt[2][qz][c] * F[3 * n3 + q];
-              gd += l * F[4 * n3 + q];
+              gx = rfma(l, F[n3 + q], gx);
+              gy = rfma(l, F[2 * n3 + q], gy);
+              gz = rfma(Dt[2][qz][c], F[3 * n3 + q], gz);
+              gd = rfma(l, F[4 * n3 + q], gd);
             }
           }
           G[t] = g0 + gz;
@@ -275,11 +282,11 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
           cd h0 = mkc(0, 0), hx = mkc(0, 0), hy = mkc(0, 0), hd = mkc(0, 0);
           for (int qy = 0; qy < n1; ++qy) {
             const int g = (qx + n1 * qy) * P + c;
-            h0 += Lt[1][qy][bb] * G[g];
+            h0 = rfma(Lt[1][qy][bb], G[g], h0);
             if (full) {
-              hx += Lt[1][qy][bb] * G[n2 * P + g];
-              hy += Dt[1][qy][bb] * G[2 * n2 * P + g];
-              hd += Lt[1][qy][bb] * G[3 * n2 * P + g];
+              hx = rfma(Lt[1][qy][bb], G[n2 * P + g], hx);
+              hy = rfma(Dt[1][qy][bb], G[2 * n2 * P + g], hy);
+              hd = rfma(Lt[1][qy][bb], G[3 * n2 * P + g], hd);
             }
           }
           Hs[t] = h0 + hy;
@@ -296,10 +303,10 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
           cd s = mkc(0, 0), sd = mkc(0, 0);
           for (int qx = 0; qx < n1; ++qx) {
             const int hidx = (qx * P + bb) * P + c;
-            s += Lt[0][qx][a] * Hs[hidx];
+            s = rfma(Lt[0][qx][a], Hs[hidx], s);
             if (full) {
-              s += Dt[0][qx][a] * Hs[n1 * P * P + hidx];
-              sd += Lt[0][qx][a] * Hs[2 * n1 * P * P + hidx];
+              s = rfma(Dt[0][qx][a], Hs[n1 * P * P + hidx], s);
+              sd = rfma(Lt[0][qx][a], Hs[2 * n1 * P * P + hidx], sd);
             }
           }
           if (!full) HE[(size_t)m * npad + nloc + j] += s;
@@ -359,7 +366,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
               const cd* tj = Ns + ((size_t)q * ne + j) * comps;
               const double w = Ws[q];
               if (!full) {
-                s0 += w * cmulc(ti[0], tj[0]);
+                s0 = cfmac(w * ti[0], tj[0], s0);
               } else {
                 cd v = 0.5 * (cmulc(ti[1], tj[1]) + cmulc(ti[2], tj[2]) + cmulc(ti[3], tj[3]));
                 if (!kz) {
@@ -585,7 +592,7 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
         const cd h = cconj(HE[(size_t)a * npad + m]);
         const cd* g = Gs + a * JB;
 #pragma unroll
-        for (int u = 0; u < JB; ++u) acc[u] += h * g[u];
+        for (int u = 0; u < JB; ++u) acc[u] = cfma(h, g[u], acc[u]);
       }
 #pragma unroll
       for (int u = 0; u < JB; ++u) {
@@ -603,8 +610,8 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
       const int i = t / nj, u = t % nj, j = j0 + u;
       cd s = HE[(size_t)(nloc + i) * npad + nloc + j];
       for (int m = 0; m < nloc; ++m) {
-        s -= cmulc(ld_s(Gm, (size_t)m * ne_max + i), CO[m * JB + u]);
-        s -= cmulc(HE[(size_t)m * npad + nloc + i], Gs[m * JB + u]);
+        s = cfmac(-ld_s(Gm, (size_t)m * ne_max + i), CO[m * JB + u], s);
+        s = cfmac(-HE[(size_t)m * npad + nloc + i], Gs[m * JB + u], s);
       }
       put(nloc + i, nloc + j, s);
     }
@@ -759,7 +766,7 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
       OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_red, red.data(), red.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
     if (off.back() > 0) {
       const int threads = 256;
-      const int64_t blocks = std::min<int64_t>((off.back() + threads - 1) / threads, 1 << 20);
+      const int64_t blocks = std::min<int64_t>((off.back() / std::max(c->nfun, 1) + threads - 1) / threads, 1 << 20);
       OEFE_COUNTED k_tabulate<<<(unsigned)blocks, threads, 0, c->stream>>>(enr_params(c), c->d_qxyz, c->d_q_off, c->d_act_off,
                                                              c->d_act_idx, e0, nb, d_off, K.k[0], K.k[1], K.k[2], tab);
       OEFE_CUDA_TRY(c, cudaGetLastError());

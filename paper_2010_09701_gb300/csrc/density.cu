@@ -73,14 +73,17 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
         lagrange_eval(xn, P, xi, Lv, Dv);
         for (int a = 0; a < P; ++a) Lt[d][i][a] = Lv[a];
       }
-      // enrichment values of the leaf points
-      for (int t = threadIdx.x; t < n3 * ne; t += DT) {
-        const int q = t / ne, j = t % ne;
+      // enrichment values of the leaf points, one (point, atom) per thread: the active set holds
+      // whole atoms, whose functions share the offset, cutoff and phase
+      const int nat = A.E.nfun > 0 ? ne / A.E.nfun : 0;
+      for (int t = threadIdx.x; t < n3 * nat; t += DT) {
+        const int q = t / nat, j0 = (t % nat) * A.E.nfun;
         const int64_t qg = L.q0 + q;
         const double x[3] = {A.qxyz[3 * qg], A.qxyz[3 * qg + 1], A.qxyz[3 * qg + 2]};
-        cd v, g[3];
-        enrichment_value(A.E, A.act_idx[A.act_off[e] + j], x, A.k, &v, g);
-        na[t] = v;
+        const int I = A.act_idx[A.act_off[e] + j0] / A.E.nfun;
+        AtomGeom G;
+        atom_geom(A.E, I, x, A.k, false, G);
+        for (int f = 0; f < A.E.nfun; ++f) atom_function(A.E, I, f, G, A.k, &na[q * ne + j0 + f], nullptr);
       }
       cd* Xt = reinterpret_cast<cd*>(smem);   // nloc * NB
       cd* Xo = Xt + nloc * NB;                // ne_max * NB
@@ -102,7 +105,7 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
           cd s = mkc(0, 0);
           if (u < nb) {
             s = ldX(A, A.cell_nodes[(size_t)e * nloc + a], v0 + u);
-            for (int j = 0; j < ne; ++j) s -= ldG(A, ((size_t)e * nloc + a) * A.ne_max + j) * Xo[j * NB + u];
+            for (int j = 0; j < ne; ++j) s = cfma(-ldG(A, ((size_t)e * nloc + a) * A.ne_max + j), Xo[j * NB + u], s);
           }
           Xt[t] = s;
         }
@@ -112,7 +115,7 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
           const int u = t % NB, r = t / NB;
           const int c = r % P, bb = (r / P) % P, qx = r / (P * P);
           cd s = mkc(0, 0);
-          for (int a = 0; a < P; ++a) s += Lt[0][qx][a] * Xt[(a + P * (bb + P * c)) * NB + u];
+          for (int a = 0; a < P; ++a) s = rfma(Lt[0][qx][a], Xt[(a + P * (bb + P * c)) * NB + u], s);
           T1[t] = s;
         }
         __syncthreads();
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
           const int u = t % NB, r = t / NB;
           const int c = r % P, qy = (r / P) % n1, qx = r / (P * n1);
           cd s = mkc(0, 0);
-          for (int bb = 0; bb < P; ++bb) s += Lt[1][qy][bb] * T1[((qx * P + bb) * P + c) * NB + u];
+          for (int bb = 0; bb < P; ++bb) s = rfma(Lt[1][qy][bb], T1[((qx * P + bb) * P + c) * NB + u], s);
           T2[t] = s;
         }
         __syncthreads();
@@ -130,8 +133,8 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
           const int u = t % NB, q = t / NB;
           const int qx = q % n1, qy = (q / n1) % n1, qz = q / n2;
           cd s = mkc(0, 0);
-          for (int c = 0; c < P; ++c) s += Lt[2][qz][c] * T2[((qx * n1 + qy) * P + c) * NB + u];
-          for (int j = 0; j < ne; ++j) s += na[q * ne + j] * Xo[j * NB + u];
+          for (int c = 0; c < P; ++c) s = rfma(Lt[2][qz][c], T2[((qx * n1 + qy) * P + c) * NB + u], s);
+          for (int j = 0; j < ne; ++j) s = cfma(na[q * ne + j], Xo[j * NB + u], s);
           U[t] = s;
         }
         __syncthreads();

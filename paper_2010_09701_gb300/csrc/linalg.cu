@@ -374,13 +374,13 @@ int chol_inverse_t(oefe_ctx* c, S* A, int n, bool inverse, bool want_Linv, S* Y,
   return OEFE_OK;
 }
 
-int check_fp64(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
+int check_fp64(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, bool need_h64 = true) {
   if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
   if (ik < 0 || ik >= (int)c->kd.size()) { c->err = "k index out of range"; return OEFE_ERR_ARG; }
   if (!X || nv < 1 || ld < nv || nv > 4096) { c->err = "need X, 1 <= nv <= ld, nv <= 4096"; return OEFE_ERR_ARG; }
   if (!(dtype == OEFE_F64 || dtype == OEFE_C128)) { c->err = "this call needs F64 or C128 vectors"; return OEFE_ERR_ARG; }
   if (c->kd[ik].cplx != (dtype == OEFE_C128)) { c->err = "dtype does not match the k-point"; return OEFE_ERR_ARG; }
-  if (!c->kd[ik].H64) { c->err = "FP64 cell matrices were not stored"; return OEFE_ERR_STATE; }
+  if (need_h64 && !c->kd[ik].H64) { c->err = "FP64 cell matrices were not stored"; return OEFE_ERR_STATE; }
   return OEFE_OK;
 }
 
@@ -498,9 +498,9 @@ int rayleigh_ritz(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, doubl
 
 int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, double* b) {
   const int dtype = (ik >= 0 && ik < (int)c->kd.size() && c->kd[ik].cplx) ? OEFE_C128 : OEFE_F64;
-  OEFE_TRY(check_fp64(c, ik, v0, 1, 1, dtype));
-  if (steps < 2 || steps > 1000 || !b) { c->err = "upper_bound: 2 <= steps <= 1000"; return OEFE_ERR_ARG; }
   const bool low = (flags & OEFE_FILTER_BF16X3) != 0;
+  OEFE_TRY(check_fp64(c, ik, v0, 1, 1, dtype, !low));
+  if (steps < 2 || steps > 1000 || !b) { c->err = "upper_bound: 2 <= steps <= 1000"; return OEFE_ERR_ARG; }
   const KData& K = c->kd[ik];
   if (low && !K.Hbf) { c->err = "upper_bound: BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
   const int64_t n = c->nh + c->nO;
