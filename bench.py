@@ -32,6 +32,10 @@ import workloads as W  # noqa: E402
 FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12     # 2 DFMA / clk / SM on GB300
 FALLBACK_HBM_GBS = 6800.0
+# DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, scaled to the
+# bench's launch by the units processed (valid while the kernels are unchanged since the capture)
+TRAFFIC_TENSOR = {"bytes_per_tile": 2.052740e9 / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"}
+TRAFFIC_FP64 = {"bytes_per_cell": (4.954736e9 + 0.205448e9) / 512, "source": "profiles/k_cell_apply_z3_c3small_8cube_p6.md"}
 
 
 def measured_peaks():
@@ -137,16 +141,23 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     w = W.CONFIGS[args.config]()
     t0 = time.time()
-    ctx = P.setup_workload(w, device=dev)
+    kpts = None
+    if args.filter_only:   # profiling aid: the first k-point only
+        k_all, _ = W.monkhorst_pack(w.a, w.kgrid)
+        kpts = (k_all[:1], np.array([1.0]))
+        w.nv = w.nv[:1]
+    ctx = P.setup_workload(w, device=dev, kpoints=kpts)
     nh, nO = ctx.ndof()
     n = nh + nO
     nk = ctx.nk
     xyz, qw = ctx.quadrature_points()
     V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
     store = P.STORE_F64 | (P.STORE_BF16X3 if args.tensor else P.STORE_F32)
-    if args.filter_only:   # profiling aid: the low-precision matrices only
-        store = P.STORE_BF16X3 if args.tensor else P.STORE_F32
+    if args.filter_only:   # profiling aid: the low-precision matrices (and FP64 ones on request) only
+        store = (P.STORE_BF16X3 if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
     ctx.build_hamiltonian(V, store)
+    if args.filter_only:
+        ctx.release_workspace()   # the build's scratch is several times the filter's
     naug = np.array([len(ctx.cell_info(e)) for e in range(int(np.prod([w.ncell] * 3)))])
     nvs = w.nv
     deg = w.degree
@@ -157,7 +168,7 @@ def run_ours(args, rank, world):
     bks = []
     for ik in range(nk):
         v0 = torch.tensor(W.random_vectors(n, 1, complex_=True, seed=100 + ik), dtype=torch.complex128, device="cuda")
-        bks.append(ctx.upper_bound(ik, v0, 20, P.FILTER_BF16X3 if args.tensor else 0))
+        bks.append(ctx.upper_bound(ik, v0, 20, P.FILTER_BF16X3 if (args.tensor or args.filter_only) else 0))
     a_lo, a0 = 0.0, -0.5 * float(max(w.Z)) ** 2 - 1.0
     rho = torch.zeros(len(qw), dtype=torch.float64, device="cuda")
     gV = torch.zeros_like(rho)
@@ -171,6 +182,9 @@ def run_ours(args, rank, world):
         X32 = X0[0].to(torch.complex64)
         for _ in range(args.steps):
             ctx.chebyshev_filter(0, X32, deg, a_lo, bks[0], a0, flags=P.FILTER_BF16X3 if args.tensor else 0)
+        if args.with_fp64:   # one FP64 operator application (the FP64 cell product)
+            Y64 = torch.empty_like(X0[0])
+            ctx.apply_h(0, X0[0], Y64)
         torch.cuda.synchronize()
         return {"filter_only": True, "passes": args.steps, "config": w.name}
 
@@ -270,14 +284,17 @@ def run_ours(args, rank, world):
     if args.tensor:
         hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
         ach = kbytes / (per_launch_ms * 1e-3) / 1e9
-        roofline = {"kernel": "k_cell_mma_tma<complex> (tcgen05 + TMA, BF16x3)" + (" over all k" if batched else ""),
+        roof_low = {"kernel": "k_cell_mma_tma<complex> (tcgen05 + TMA, BF16x3)" + (" over all k" if batched else ""),
                     "bound": "hbm", "achieved": ach, "peak": hbm,
-                    "unit": "GB/s", "frac": ach / hbm, "traffic": None, "algorithmic_bytes_per_launch": kbytes,
+                    "unit": "GB/s", "frac": ach / hbm,
+                    "traffic": TRAFFIC_TENSOR["bytes_per_tile"] * len(naug) * kmul * ((nvs[0] + 63) // 64),
+                    "traffic_source": TRAFFIC_TENSOR["source"] + " (scaled by tiles)",
+                    "algorithmic_bytes_per_launch": kbytes,
                     "launches": klaunch, "ms_per_launch": per_launch_ms, "peak_source": src,
                     "dense_tflops": achieved,
                     "tensor_frac_bf16": 3 * achieved / peaks.get("bf16_tflops", 1911.8)}
     else:
-        roofline = {"kernel": "k_cell_apply<float,complex>", "bound": "alu", "achieved": achieved,
+        roof_low = {"kernel": "k_cell_apply<float,complex>", "bound": "alu", "achieved": achieved,
                     "peak": FP32_PEAK_DERIVED, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_DERIVED,
                     "traffic": None, "algorithmic_bytes_per_launch": kbytes, "launches": klaunch,
                     "ms_per_launch": per_launch_ms, "peak_source": "derived: 152 SM x 128 FP32 lanes x 2 x 2070 MHz",
@@ -285,26 +302,75 @@ def run_ours(args, rank, world):
 
     # plain FP64 GPU filter pass on k = 0, for the mixed-vs-FP64 comparison
     fp64 = None
+    accuracy = None
+    fp64_ms_launch = None
     if not args.skip_fp64:
+        # one FP64 filter pass (k = 0) from the same start vectors, the FP64 cell product timed live
         Xf = X0[0].clone()
         ctx.chebyshev_filter(0, Xf, 1, a_lo, bks[0], a0)   # warm
         Xf.copy_(X0[0])
         torch.cuda.synchronize()
+        ctx.kernel_timing([P.C128])
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
         ctx.chebyshev_filter(0, Xf, deg, a_lo, bks[0], a0)
         f1.record(stream)
         torch.cuda.synchronize()
+        k64_ms, k64_n = ctx.kernel_time()
+        ctx.kernel_timing([])
+        fp64_ms_launch = k64_ms / max(k64_n, 1)
         fp64_s = f0.elapsed_time(f1) * 1e-3
-        ctx.orthonormalize(0, Xf)
-        eig64 = ctx.rayleigh_ritz(0, Xf)
-        # mixed-vs-FP64 accuracy of the same pass (k = 0, same start vectors)
         fp64 = {"s_per_pass_k0": fp64_s,
                 "tflops": dense_filter_flops(naug, [nvs[0]], deg) / fp64_s / 1e12,
-                "speedup_mixed_vs_fp64": fp64_s / s_per_pass,
-                "max_abs_d_eig_k0_Ha": float(np.max(np.abs(eig64 - eigs[0]))),
-                "d_sum_eig_k0_per_atom_Ha": float(abs(np.sum(eig64) - np.sum(eigs[0])) / w.natoms)}
+                "speedup_mixed_vs_fp64": fp64_s / s_per_pass}
+
+        # accuracy: the same subspace iteration (k = 0, same start, Zhou's bounds from the previous
+        # Ritz values) with the mixed filter and with the FP64 filter, FP64 Cholesky-QR and
+        # Rayleigh-Ritz in both; band energy and occupied Ritz values compared after the last pass
+        def iterate(flags):
+            Xp = X0[0].clone()
+            lo, hi, low = a_lo, bks[0], a0
+            for _ in range(args.acc_passes):
+                ctx.chebyshev_filter(0, Xp, deg, lo, hi, low, flags=flags)
+                ctx.orthonormalize(0, Xp)
+                ev, res = ctx.rayleigh_ritz(0, Xp, resid=True)
+                lo, low = float(ev[-1]), float(ev[0]) - 1.0
+            return ev, res
+
+        mixed_flags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
+        ev_m, res_m = iterate(mixed_flags)
+        ev_d, res_d = iterate(0)
+        _, occ_m, e_m = P.occupations([ev_m], [1.0], w.nelectrons)
+        _, occ_d, e_d = P.occupations([ev_d], [1.0], w.nelectrons)
+        occd = np.asarray(occ_d[0]) > 1e-8
+        accuracy = {"passes": args.acc_passes, "k_point": 0, "reference": "the FP64 GPU path",
+                    "d_band_energy_per_atom_Ha": float(abs(e_m - e_d) / w.natoms),
+                    "max_abs_d_eig_occupied_Ha": float(np.max(np.abs(ev_m[occd] - ev_d[occd]))),
+                    "max_residual_occupied_mixed": float(np.max(np.asarray(res_m)[occd])),
+                    "max_residual_occupied_fp64": float(np.max(np.asarray(res_d)[occd])),
+                    "occupied_states": int(np.sum(occd))}
+
+    # the dominant kernel of the step (most device time per step) carries "roofline", the other
+    # cell product "roofline_secondary"
+    roofline, roof2 = roof_low, None
+    if fp64_ms_launch is not None:
+        f64_flops = 6.0 * float(np.sum(naug.astype(float) ** 2)) * nvs[0]   # 3 FMAs per complex product
+        f64_ach = f64_flops / (fp64_ms_launch * 1e-3) / 1e12
+        roof_fp64 = {"kernel": "k_cell_apply_z3 (FP64 complex cell product, 3 real multiplications)",
+                     "bound": "alu", "achieved": f64_ach, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
+                     "frac": f64_ach / FP64_PEAK_DERIVED,
+                     "traffic": TRAFFIC_FP64["bytes_per_cell"] * len(naug),
+                     "traffic_source": TRAFFIC_FP64["source"] + " (scaled by cells)",
+                     "algorithmic_flops_per_launch": f64_flops, "ms_per_launch": fp64_ms_launch,
+                     "launches_per_step": 2 * nk,
+                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flops x 2070 MHz",
+                     "dense_equivalent_tflops": f64_ach * 8.0 / 6.0}
+        low_ms_step = per_launch_ms * klaunch / max(args.steps, 1)
+        if 2 * nk * fp64_ms_launch > low_ms_step:
+            roofline, roof2 = roof_fp64, roof_low
+        else:
+            roof2 = roof_fp64
 
     # end to end through the public API with host buffers (H2D of V and X0, D2H of rho and eigenvalues)
     e2e = None
@@ -351,7 +417,8 @@ def run_ours(args, rank, world):
            "filter_launch": "batched multi-k, CUDA graph" if batched else "per k-point",
            "autotune_ms_per_degree": tune_ms,
            "filter_precision": "BF16x3 tensor cores + last degree FP64" if args.tensor else "FP32 + last degree FP64",
-           "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+           "roofline": roofline, "roofline_secondary": roof2, "accuracy": accuracy,
+           "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
            "gpu_launches": int(launches),
            "peaks_source": src, "setup_s": setup_s}
     return out
@@ -431,6 +498,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--per-k-filter", action="store_true", help="filter each k-point separately")
+    ap.add_argument("--with-fp64", action="store_true",
+                    help="with --filter-only: store the FP64 matrices too and apply H once in FP64")
+    ap.add_argument("--acc-passes", type=int, default=4,
+                    help="subspace-iteration passes of the mixed-vs-FP64 accuracy comparison (k = 0)")
     ap.add_argument("--fp32-simt", dest="tensor", action="store_false",
                     help="FP32 SIMT cell products instead of the BF16x3 tensor-core path")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -260,6 +260,14 @@ int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, int flag
 int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask);
 int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches);
 
+/* oefe_release_workspace -- frees the context's cached scratch (the growable
+ * work arrays of the operator build, the filter and the subspace calls) and
+ * the captured graph of the batched filter, which points into it; later calls
+ * allocate what they need again. Synchronizes the context's streams. Returns
+ * OEFE_ERR_ARG for a null context. No counterpart in the paper (memory
+ * management: the build's scratch is several times the filter's). */
+int oefe_release_workspace(oefe_ctx_t ctx);
+
 /* oefe_launch_count -- process-wide number of kernel launches the library has
  * issued so far (every context; a replay of a captured graph counts each of
  * its kernels). n: host pointer to one int64. Never synchronizes. Returns

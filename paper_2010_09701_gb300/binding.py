@@ -57,6 +57,7 @@ SIGNATURES = [
     ("oefe_occupations", _I, [_I, _IP, _DP, _DP, _D, _D, _DP, _DP, _DP]),
     ("oefe_kernel_timing", _I, [_P, _I]),
     ("oefe_kernel_time", _I, [_P, _DP, _I64P]),
+    ("oefe_release_workspace", _I, [_P]),
     ("oefe_launch_count", _I, [_c.POINTER(_c.c_int64)]),
 ]
 
@@ -347,6 +348,10 @@ class Context:
         px, nv, ld, dt = _block(X)
         self._check(self.lib.oefe_band_trace_grad(self.h, int(ik), px, nv, ld, dt, ctypes.c_void_p(gV.data_ptr())))
         return gV
+
+    def release_workspace(self):
+        """Free the cached scratch arrays (the build's are several times the filter's)."""
+        self._check(self.lib.oefe_release_workspace(self.h))
 
     def kernel_timing(self, dtypes=()):
         mask = 0

@@ -326,6 +326,22 @@ int oefe_occupations(int nk, const int* nv, const double* eig, const double* w, 
   return OEFE_OK;
 }
 
+int oefe_release_workspace(oefe_ctx_t ctx) {
+  CTX_CHECK(ctx);
+  OEFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  if (ctx->bstream) OEFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->bstream));
+  if (ctx->bgraph) {
+    cudaGraphExecDestroy(ctx->bgraph);
+    ctx->bgraph = nullptr;
+  }
+  ctx->bkey.clear();
+  dev_free(ctx->ws);
+  dev_free(ctx->ws2);
+  ctx->ws = ctx->ws2 = nullptr;
+  ctx->ws_bytes = ctx->ws2_bytes = 0;
+  return OEFE_OK;
+}
+
 int oefe_launch_count(int64_t* n) {
   if (!n) return OEFE_ERR_ARG;
   *n = (int64_t)g_launches.load(std::memory_order_relaxed);

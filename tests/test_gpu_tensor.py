@@ -177,3 +177,22 @@ def test_batched_small_vector_blocks(nv, deg):
     X32 = to_gpu(X, torch.complex64)
     ctx.filter_batched([X32], deg, a, b, a0, FILTER_BF16X3)
     assert colerr(X32.cpu().numpy().astype(np.complex128), ref) < TOL_FILTER
+
+
+def test_release_workspace_then_filter_again():
+    # freeing the cached scratch drops the captured graph too; the next calls rebuild both
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64
+    prs, ctx, V, _ = paired(ks=[KS[1]])
+    pr = prs[0]
+    a, b, a0 = bounds(pr)
+    X = W.random_vectors(pr.n, 12, complex_=True, seed=44)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 5, a, b, a0)
+    for rep in range(2):
+        Xd = to_gpu(X)
+        ctx.filter_batched([Xd], 5, a, b, a0, FILTER_BF16X3 | FILTER_LAST_FP64)
+        assert colerr(Xd.cpu().numpy(), ref) < TOL_FILTER, rep
+        ctx.release_workspace()
+    Xd = to_gpu(X)
+    Y = torch.empty_like(Xd)
+    ctx.apply_h(0, Xd, Y)
+    assert np.max(np.abs(Y.cpu().numpy() - pr.apply_H(X))) < 1e-12 * np.max(np.abs(pr.apply_H(X)))
