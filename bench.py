@@ -34,7 +34,7 @@ FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12     # 2 DFMA / clk / SM on GB30
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, scaled to the
 # bench's launch by the units processed (valid while the kernels are unchanged since the capture)
-TRAFFIC_TENSOR = {"bytes_per_tile": 2.052740e9 / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"}
+TRAFFIC_TENSOR = {}   # bf16 parts -> {"bytes_per_tile", "source"}; filled from a capture of the current kernel
 TRAFFIC_FP64 = {"bytes_per_cell": (4.954736e9 + 0.205448e9) / 512, "source": "profiles/k_cell_apply_z3_c3small_8cube_p6.md"}
 
 
@@ -152,9 +152,10 @@ def run_ours(args, rank, world):
     nk = ctx.nk
     xyz, qw = ctx.quadrature_points()
     V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
-    store = P.STORE_F64 | (P.STORE_BF16X3 if args.tensor else P.STORE_F32)
+    split = P.STORE_BF16X3 if args.bf16x3 else P.STORE_BF16X6
+    store = P.STORE_F64 | (split if args.tensor else P.STORE_F32)
     if args.filter_only:   # profiling aid: the low-precision matrices (and FP64 ones on request) only
-        store = (P.STORE_BF16X3 if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
+        store = (split if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
     ctx.build_hamiltonian(V, store)
     if args.filter_only:
         ctx.release_workspace()   # the build's scratch is several times the filter's
@@ -278,21 +279,25 @@ def run_ours(args, rank, world):
     per_launch_ms = kms / max(klaunch, 1)
     kmul = nk if batched else 1   # a batched launch covers every k-point
     kflops = kernel_flops_per_launch(naug, nvs[0], True) * kmul
-    kbytes = (float(np.sum(naug ** 2)) * 8 + 2 * float(np.sum(naug)) * nvs[0] * 8) * kmul
+    nparts = 2 if args.bf16x3 else 3           # bf16 parts per real value of the split matrices
+    nprod = 3 if args.bf16x3 else 6            # products per element on the tensor cores
+    kbytes = (float(np.sum(naug ** 2)) * 4 * nparts + 2 * float(np.sum(naug)) * nvs[0] * 8) * kmul
     achieved = kflops / (per_launch_ms * 1e-3) / 1e12
     peaks, src = measured_peaks()
     if args.tensor:
         hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
         ach = kbytes / (per_launch_ms * 1e-3) / 1e9
-        roof_low = {"kernel": "k_cell_mma_tma<complex> (tcgen05 + TMA, BF16x3)" + (" over all k" if batched else ""),
+        roof_low = {"kernel": "k_cell_mma_tma<complex> (tcgen05 + TMA, BF16x%d)" % nprod + (" over all k" if batched else ""),
                     "bound": "hbm", "achieved": ach, "peak": hbm,
                     "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": TRAFFIC_TENSOR["bytes_per_tile"] * len(naug) * kmul * ((nvs[0] + 63) // 64),
-                    "traffic_source": TRAFFIC_TENSOR["source"] + " (scaled by tiles)",
+                    "traffic": (TRAFFIC_TENSOR[nparts]["bytes_per_tile"] * len(naug) * kmul * ((nvs[0] + 63) // 64)
+                                if nparts in TRAFFIC_TENSOR else None),
+                    "traffic_source": (TRAFFIC_TENSOR[nparts]["source"] + " (scaled by tiles)"
+                                       if nparts in TRAFFIC_TENSOR else None),
                     "algorithmic_bytes_per_launch": kbytes,
                     "launches": klaunch, "ms_per_launch": per_launch_ms, "peak_source": src,
                     "dense_tflops": achieved,
-                    "tensor_frac_bf16": 3 * achieved / peaks.get("bf16_tflops", 1911.8)}
+                    "tensor_frac_bf16": nprod * achieved / peaks.get("bf16_tflops", 1911.8)}
     else:
         roof_low = {"kernel": "k_cell_apply<float,complex>", "bound": "alu", "achieved": achieved,
                     "peak": FP32_PEAK_DERIVED, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_DERIVED,
@@ -325,26 +330,34 @@ def run_ours(args, rank, world):
                 "tflops": dense_filter_flops(naug, [nvs[0]], deg) / fp64_s / 1e12,
                 "speedup_mixed_vs_fp64": fp64_s / s_per_pass}
 
-        # accuracy: the same subspace iteration (k = 0, same start, Zhou's bounds from the previous
-        # Ritz values) with the mixed filter and with the FP64 filter, FP64 Cholesky-QR and
-        # Rayleigh-Ritz in both; band energy and occupied Ritz values compared after the last pass
-        def iterate(flags):
-            Xp = X0[0].clone()
-            lo, hi, low = a_lo, bks[0], a0
-            for _ in range(args.acc_passes):
-                ctx.chebyshev_filter(0, Xp, deg, lo, hi, low, flags=flags)
-                ctx.orthonormalize(0, Xp)
-                ev, res = ctx.rayleigh_ritz(0, Xp, resid=True)
-                lo, low = float(ev[-1]), float(ev[0]) - 1.0
-            return ev, res
+        # accuracy at convergence (k = 0): the subspace iteration (Zhou's bounds from the previous
+        # Ritz values, FP64 Cholesky-QR and Rayleigh-Ritz) is run with the mixed filter until the
+        # band energy settles; then one pass with the mixed filter and one with the FP64 filter from
+        # that subspace are compared (band energy per atom, occupied Ritz values, residuals)
+        def one_pass(Xp, lo, low, flags):
+            ctx.chebyshev_filter(0, Xp, deg, lo, bks[0], low, flags=flags)
+            ctx.orthonormalize(0, Xp)
+            return ctx.rayleigh_ritz(0, Xp, resid=True)
 
         mixed_flags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
-        ev_m, res_m = iterate(mixed_flags)
-        ev_d, res_d = iterate(0)
+        Xc = X0[0].clone()
+        lo, low = a_lo, a0
+        e_prev, last_change = None, None
+        for it in range(args.acc_passes):
+            ev, res = one_pass(Xc, lo, low, mixed_flags)
+            lo, low = float(ev[-1]), float(ev[0]) - 1.0
+            e_now = P.occupations([ev], [1.0], w.nelectrons)[2]
+            if e_prev is not None:
+                last_change = abs(e_now - e_prev) / w.natoms
+            e_prev = e_now
+        ev_m, res_m = one_pass(Xc.clone(), lo, low, mixed_flags)
+        ev_d, res_d = one_pass(Xc.clone(), lo, low, 0)
         _, occ_m, e_m = P.occupations([ev_m], [1.0], w.nelectrons)
         _, occ_d, e_d = P.occupations([ev_d], [1.0], w.nelectrons)
         occd = np.asarray(occ_d[0]) > 1e-8
-        accuracy = {"passes": args.acc_passes, "k_point": 0, "reference": "the FP64 GPU path",
+        accuracy = {"converging_passes": args.acc_passes, "band_energy_change_last_pass_per_atom_Ha": last_change, "k_point": 0,
+                    "compared": "one mixed and one FP64 pass from the converged subspace",
+                    "reference": "the FP64 GPU path",
                     "d_band_energy_per_atom_Ha": float(abs(e_m - e_d) / w.natoms),
                     "max_abs_d_eig_occupied_Ha": float(np.max(np.abs(ev_m[occd] - ev_d[occd]))),
                     "max_residual_occupied_mixed": float(np.max(np.asarray(res_m)[occd])),
@@ -416,7 +429,8 @@ def run_ours(args, rank, world):
            "filter_s_per_pass": s_per_pass, "filter_tflops": filt_tflops, "fp64": fp64, "phase_ms": phase_ms,
            "filter_launch": "batched multi-k, CUDA graph" if batched else "per k-point",
            "autotune_ms_per_degree": tune_ms,
-           "filter_precision": "BF16x3 tensor cores + last degree FP64" if args.tensor else "FP32 + last degree FP64",
+           "filter_precision": ("BF16x%d tensor cores (FP32 vectors) + last degree FP64" % nprod) if args.tensor
+                               else "FP32 + last degree FP64",
            "roofline": roofline, "roofline_secondary": roof2, "accuracy": accuracy,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
            "gpu_launches": int(launches),
@@ -500,8 +514,11 @@ def main():
     ap.add_argument("--per-k-filter", action="store_true", help="filter each k-point separately")
     ap.add_argument("--with-fp64", action="store_true",
                     help="with --filter-only: store the FP64 matrices too and apply H once in FP64")
-    ap.add_argument("--acc-passes", type=int, default=4,
-                    help="subspace-iteration passes of the mixed-vs-FP64 accuracy comparison (k = 0)")
+    ap.add_argument("--acc-passes", type=int, default=40,
+                    help="mixed subspace-iteration passes (k = 0) that converge the subspace the accuracy "
+                         "comparison starts from")
+    ap.add_argument("--bf16x3", action="store_true",
+                    help="two-part bf16 split of the cell matrices (BF16x3) instead of three parts (BF16x6)")
     ap.add_argument("--fp32-simt", dest="tensor", action="store_false",
                     help="FP32 SIMT cell products instead of the BF16x3 tensor-core path")
     ap.add_argument("--skip-e2e", action="store_true")

@@ -51,7 +51,7 @@ enum {
 enum { OEFE_F64 = 0, OEFE_F32 = 1, OEFE_C128 = 2, OEFE_C64 = 3 };
 
 /* Storage of the cell Hamiltonians (bit mask for oefe_build_hamiltonian). */
-enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4 };
+enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4, OEFE_STORE_BF16X6 = 8 };
 
 /* ---------------------------------------------------------------- context */
 int oefe_create(oefe_ctx_t* out, int device, void* cuda_stream);
@@ -123,8 +123,12 @@ int oefe_ndof(oefe_ctx_t ctx, int64_t* n_h, int* n_O);
  * Eq. UOEFESplit). veff_q: device, nq_total doubles, V_eff at the quadrature
  * points. store: OEFE_STORE_F64 (FP64 / complex128 matrices, needed by every
  * FP64 call), OEFE_STORE_F32 (FP32 / complex64 copies for the FP32 filter)
- * and/or OEFE_STORE_BF16X3 (each real plane split into bf16 hi + lo for the
- * tensor-core filter; same bytes as FP32). All arithmetic is FP64. */
+ * and/or one of OEFE_STORE_BF16X3 (each real plane split into bf16 hi + lo for
+ * the tensor-core filter; same bytes as FP32: products H_hi X_hi + H_hi X_lo +
+ * H_lo X_hi, ~2^-17 relative) and OEFE_STORE_BF16X6 (three bf16 parts hi + mid
+ * + lo, 1.5x the bytes: six products, FP32-class accuracy; wins when both are
+ * set). The tensor-core filter (OEFE_FILTER_BF16X3) uses whichever split is
+ * stored. All arithmetic of the build is FP64. */
 int oefe_build_hamiltonian(oefe_ctx_t ctx, const double* veff_q, int store);
 
 /* Row/column map of one cell matrix: idx (host, n_aug ints) receives global
@@ -199,8 +203,10 @@ int oefe_filter_batched(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, c
  * on the given vectors and keeps the fastest for the BF16X3 filters:
  * (0) 64 vectors per tile, persistent grid of one CTA per SM, cp.async loads;
  * (1) the same with 32 vectors per tile; (2) one CTA per tile;
- * (3) the warp-specialized kernel with TMA loads (persistent).
- * ms (host, 4 doubles, may be NULL) receives the time of one degree's cell
+ * (3) the warp-specialized kernel with TMA loads (persistent); (4) the same with
+ * the real part of a complex cell matrix applied to [Re X | Im X] in one
+ * N = 128 MMA. The three-part split (OEFE_STORE_BF16X6) runs on (3), (4) only.
+ * ms (host, 5 doubles, may be NULL) receives the time of one degree's cell
  * products for each candidate (0 when a candidate is unavailable). Vectors as
  * for oefe_filter_batched; they are read, not changed. */
 int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "liboefe.so")
 OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_CHOLESKY, ERR_NOTPD_MOO, ERR_TIMEOUT, ERR_NUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 F64, F32, C128, C64 = 0, 1, 2, 3
-STORE_F64, STORE_F32, STORE_BF16X3 = 1, 2, 4
+STORE_F64, STORE_F32, STORE_BF16X3, STORE_BF16X6 = 1, 2, 4, 8
 FILTER_LAST_FP64, FILTER_BF16X3 = 1, 2
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
@@ -309,7 +309,7 @@ class Context:
 
     def filter_autotune(self, Xs):
         arr, nvs, lds, dt = self._blocks(Xs)
-        ms = np.zeros(4)
+        ms = np.zeros(5)
         self._check(self.lib.oefe_filter_autotune(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, _dp(ms)))
         return ms
 

@@ -530,7 +530,7 @@ __global__ void k_hermitize(S* A, int n) {
 template <typename S, typename S32>
 __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gamma, const int* act_off,
                                                   int e0, int nloc, int npad, int ne_max, S* H64,
-                                                  S32* H32, __nv_bfloat16* Hbf) {
+                                                  S32* H32, __nv_bfloat16* Hbf, int parts) {
   extern __shared__ double smem[];
   const int b = blockIdx.x, e = e0 + b;
   const int ne = act_off[e + 1] - act_off[e];
@@ -548,23 +548,32 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
       if (H32) reinterpret_cast<float*>(H32)[o] = (float)v.x;
     }
     if (Hbf) {
-      // split each real plane: hi = bf16(x), lo = bf16(x - hi), from the FP32 value
       // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
-      // each (K tile, M tile) of two planes is one contiguous 32 KB block for the TMA loads
-      constexpr int PL = sizeof(S) == sizeof(cd) ? 4 : 2;
+      // the planes of one part of one (K tile, M tile) are one contiguous block for the TMA loads;
+      // planes: (re hi, re lo[, im hi, im lo]) split from the FP32 value, or (re hi, re mid, re lo
+      // [, im hi, im mid, im lo]) with the residuals taken in FP64
+      const int nq = sizeof(S) == sizeof(cd) ? 2 : 1;
+      const int PL = nq * parts;
       const size_t pl = 128 * 64;
       const int mtn = npad >> 7;
       const size_t base = (size_t)e * PL * npad * npad +
                           ((((size_t)(c >> 6) * mtn + (r >> 7)) * PL) * 128 + (r & 127)) * 64 + (c & 63);
-      const float xr = (float)v.x;
-      const __nv_bfloat16 rh = __float2bfloat16_rn(xr);
-      Hbf[base] = rh;
-      Hbf[base + pl] = __float2bfloat16_rn(xr - __bfloat162float(rh));
-      if (PL == 4) {
-        const float xi = (float)v.y;
-        const __nv_bfloat16 ih = __float2bfloat16_rn(xi);
-        Hbf[base + 2 * pl] = ih;
-        Hbf[base + 3 * pl] = __float2bfloat16_rn(xi - __bfloat162float(ih));
+      for (int q = 0; q < nq; ++q) {
+        __nv_bfloat16* o = Hbf + base + (size_t)q * parts * pl;
+        const double x = q == 0 ? v.x : v.y;
+        if (parts == 2) {
+          const float xf = (float)x;
+          const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+          o[0] = hi;
+          o[pl] = __float2bfloat16_rn(xf - __bfloat162float(hi));
+        } else {
+          double rem = x;
+          for (int s = 0; s < parts; ++s) {
+            const __nv_bfloat16 bp = __double2bfloat16(rem);
+            o[(size_t)s * pl] = bp;
+            rem -= (double)__bfloat162float(bp);
+          }
+        }
       }
     }
   };
@@ -815,13 +824,13 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
                                             (int)tsmem));
       float* H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
       double* H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
-      __nv_bfloat16* Hbf = (store & OEFE_STORE_BF16X3) ? (__nv_bfloat16*)K.Hbf : nullptr;
+      __nv_bfloat16* Hbf = (store & (OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6)) ? (__nv_bfloat16*)K.Hbf : nullptr;
       if (K.cplx)
         OEFE_COUNTED k_transform<cd, cf><<<nb, TT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf);
+                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf, K.bf_parts);
       else
         OEFE_COUNTED k_transform<double, float><<<nb, TT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                                c->ne_max, H64, H32, Hbf);
+                                                                c->ne_max, H64, H32, Hbf, K.bf_parts);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -908,7 +917,7 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
 
 int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
   if (!c->has_k) { c->err = "build_hamiltonian: call oefe_kpoints first"; return OEFE_ERR_STATE; }
-  if (!veff || !(store & (OEFE_STORE_F64 | OEFE_STORE_F32 | OEFE_STORE_BF16X3))) {
+  if (!veff || !(store & (OEFE_STORE_F64 | OEFE_STORE_F32 | OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6))) {
     c->err = "build_hamiltonian: need veff and a storage flag";
     return OEFE_ERR_ARG;
   }
@@ -926,14 +935,20 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
     };
     st = keep((void**)&K.H64, store & OEFE_STORE_F64, n * sb);
     if (st == OEFE_OK) st = keep((void**)&K.H32, store & OEFE_STORE_F32, n * sb / 2);
-    if (st == OEFE_OK) st = keep(&K.Hbf, store & OEFE_STORE_BF16X3, n * sb / 2);
+    const int parts = (store & OEFE_STORE_BF16X6) ? 3 : (store & OEFE_STORE_BF16X3) ? 2 : 0;
+    if (parts != K.bf_parts) {   // a different split: a new buffer
+      dev_free(K.Hbf);
+      K.Hbf = nullptr;
+    }
+    K.bf_parts = parts;
+    if (st == OEFE_OK) st = keep(&K.Hbf, parts > 0, n * sb / 4 * parts);
     if (st == OEFE_OK) st = run_cell_kernel(c, K, 0, veff, d_gw, nullptr, nullptr, store);
     if (st != OEFE_OK) break;
     K.built = true;
   }
   cudaStreamSynchronize(c->stream);
   dev_free(d_gw);
-  if (st == OEFE_OK && (store & OEFE_STORE_BF16X3)) {
+  if (st == OEFE_OK && (store & (OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6))) {
     // tensor maps of the split cell matrices, one per k-point
     const size_t mb = tensor_map_bytes();
     std::vector<unsigned char> maps(mb * c->kd.size());

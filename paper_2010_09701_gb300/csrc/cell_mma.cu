@@ -409,7 +409,8 @@ int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv,
   OEFE_TRY(check_npad(c));
   if (!K.Hbf) { c->err = "BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
   const int ik = (int)(&K - c->kd.data());
-  if (c->use_tma && c->d_tmaps && ik >= 0 && ik < c->n_tmaps) {
+  // the three-part split runs on the TMA kernel only
+  if ((c->use_tma || K.bf_parts == 3) && c->d_tmaps && ik >= 0 && ik < c->n_tmaps) {
     MmaK k0;
     k0.H = K.Hbf;
     k0.X = (const float*)X;
@@ -420,8 +421,9 @@ int launch_cell_mma(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv,
     k0.tile0 = 0;
     const long long nt = (long long)c->ncells * k0.vblocks;
     return launch_cell_mma_tma(c, (const char*)c->d_tmaps + (size_t)ik * tensor_map_bytes(), nullptr, &k0, 1, nt, cplx,
-                               (int)std::min<long long>(nt, c->num_sms), c->stream);
+                               K.bf_parts, (int)std::min<long long>(nt, c->num_sms), c->stream);
   }
+  if (K.bf_parts != 2) { c->err = "tensor path: the split cell matrices have no tensor maps"; return OEFE_ERR_STATE; }
   if (cplx) return launch_one<true, 64>(c, K.Hbf, X, ldx, nv, Z, c->stream);
   return launch_one<false, 64>(c, K.Hbf, X, ldx, nv, Z, c->stream);
 }

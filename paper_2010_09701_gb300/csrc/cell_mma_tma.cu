@@ -33,12 +33,26 @@ namespace {
 constexpr int MT = 128;     // rows per M tile
 constexpr int KT = 64;      // K per tile (bf16: 128 bytes per row)
 constexpr int NBV = 64;     // vectors per tile
-constexpr int SA = 3;       // A ring stages (2 planes each)
-constexpr int SB = 2;       // B ring stages
 constexpr int THREADS = 320;
 constexpr int MAXPAD = 4 * MT;  // largest npad
-constexpr int STG = 32 * 256;   // epilogue staging per warp: 32 rows x 256 bytes
 constexpr long long WAIT_LIMIT = 1ll << 26;
+
+// Shared-memory plan per (complex, bf16 parts): NPART planes per A stage (one part of the cell
+// matrix: real or imaginary) and per B stage (the split vectors); the three-part split trades an A
+// stage and half of the epilogue staging for the larger stages.
+template <bool CPLX, int NPART>
+struct TmaCfg {
+  static constexpr int SA = NPART == 2 ? 3 : 2;        // A ring stages
+  static constexpr int SB = 2;                         // B ring stages
+  static constexpr int ER = NPART == 2 ? 32 : 16;      // epilogue rows staged per round, per warp
+  static constexpr int NB_ROWS = CPLX ? 2 * NBV : NBV;
+  static constexpr int A_PLANE = MT * 128;
+  static constexpr int A_STAGE = NPART * A_PLANE;
+  static constexpr int B_PART = NB_ROWS * 128;
+  static constexpr int B_STAGE = NPART * B_PART;
+  static constexpr int STG = ER * 256;
+  static constexpr size_t SMEM = 1024 + (size_t)SA * A_STAGE + (size_t)SB * B_STAGE + 4 * (size_t)STG;
+};
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -180,14 +194,18 @@ __device__ __forceinline__ void decode_tile(const TmaArgs& A, long long t, int* 
   *vb = (int)(r % P.vblocks);
 }
 
-template <bool CPLX>
+// MERGE (complex only): the real part of the cell matrix multiplies [Re X | Im X] in one N = 128
+// MMA instead of two N = 64 ones (fewer tensor instructions; which is faster depends on the split,
+// so the autotuner chooses)
+template <bool CPLX, int NPART, bool MERGE>
 __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
+  using Cfg = TmaCfg<CPLX, NPART>;
+  constexpr int SA = Cfg::SA, SB = Cfg::SB, STG = Cfg::STG;
   constexpr int HALVES = CPLX ? 2 : 1;   // A stages per (K tile, M tile)
-  constexpr int NB_ROWS = CPLX ? 2 * NBV : NBV;
-  constexpr int A_PLANE = MT * 128;
-  constexpr int A_STAGE = 2 * A_PLANE;
-  constexpr int B_PART = NB_ROWS * 128;
-  constexpr int B_STAGE = 2 * B_PART;
+  constexpr int A_PLANE = Cfg::A_PLANE;
+  constexpr int A_STAGE = Cfg::A_STAGE;
+  constexpr int B_PART = Cfg::B_PART;
+  constexpr int B_STAGE = Cfg::B_STAGE;
   constexpr int MCOLS = CPLX ? 2 * NBV : NBV;
   constexpr int TCOLS = CPLX ? 512 : 256;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -246,9 +264,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
           const long long u = ga / SA;
           if (u >= 1 && !mbar_wait(&a_empty[s], (uint32_t)((u - 1) & 1), &s_fail)) break;
           mbar_expect_tx(&a_full[s], A_STAGE);
-          // one contiguous 32 KB chunk: (cell, K tile, M tile, plane pair)
+          // one contiguous block of NPART planes: (cell, K tile, M tile, real or imaginary part)
           const int chunk = ((e * ktn + kt) * mt + m) * HALVES + h;
-          tma_load_3d(smem_u32(sA + s * A_STAGE), &A.maps[k], 0, 0, chunk, &a_full[s]);
+          tma_load_3d(smem_u32(sA + s * A_STAGE), &A.maps[k], 0, 0, NPART == 2 ? chunk : chunk * NPART, &a_full[s]);
         }
       }
       // drain: every issued load lands before the CTA leaves
@@ -270,41 +288,44 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
           const uint32_t dcol = taddr + m * MCOLS;
           constexpr uint32_t ID = idesc_bf16(MT, NBV, false);
           constexpr uint32_t IDN = idesc_bf16(MT, NBV, true);
+          constexpr uint32_t ID2 = idesc_bf16(MT, 2 * NBV, false);   // [Re | Im] in one N = 128 MMA
           for (int h = 0; h < HALVES; ++h, ++ga) {
             const int s = (int)(ga % SA);
             if (!mbar_wait(&a_full[s], (uint32_t)((ga / SA) & 1), &s_fail)) { ok = false; break; }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t a_base = smem_u32(sA + s * A_STAGE);
+            // the products of the split: (hi, hi), (hi, lo), (lo, hi) for two parts; for three parts
+            // also (hi, lo), (mid, mid), (lo, hi) with mid in the middle: all pairs of order <= 2
+            constexpr int NPROD = NPART == 2 ? 3 : 6;
+            constexpr int PA[6] = {0, 0, 1, 0, 1, 2};
+            constexpr int PX[6] = {0, 1, 0, 2, 1, 0};
 #pragma unroll
             for (int ks = 0; ks < KT / 16; ++ks) {
               const uint32_t koff = ks * 32;
-              const uint64_t Ah = sdesc(a_base + koff), Al = sdesc(a_base + A_PLANE + koff);
-              if (CPLX) {
-                const uint64_t Xrh = sdesc(b_base + koff), Xih = sdesc(b_base + NBV * 128 + koff);
-                const uint64_t Xrl = sdesc(b_base + B_PART + koff), Xil = sdesc(b_base + B_PART + NBV * 128 + koff);
-                const uint32_t Dr = dcol, Di = dcol + NBV;
-                if (h == 0) {   // real part of the cell matrix
-                  const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
-                  mma_bf16(Dr, Ah, Xrh, ID, first);
-                  mma_bf16(Dr, Ah, Xrl, ID, 1);
-                  mma_bf16(Dr, Al, Xrh, ID, 1);
-                  mma_bf16(Di, Ah, Xih, ID, first);
-                  mma_bf16(Di, Ah, Xil, ID, 1);
-                  mma_bf16(Di, Al, Xih, ID, 1);
-                } else {        // imaginary part: Re Z -= Im H Im X, Im Z += Im H Re X
-                  mma_bf16(Dr, Ah, Xih, IDN, 1);
-                  mma_bf16(Dr, Ah, Xil, IDN, 1);
-                  mma_bf16(Dr, Al, Xih, IDN, 1);
-                  mma_bf16(Di, Ah, Xrh, ID, 1);
-                  mma_bf16(Di, Ah, Xrl, ID, 1);
-                  mma_bf16(Di, Al, Xrh, ID, 1);
-                }
+              if (!CPLX) {
+#pragma unroll
+                for (int pi = 0; pi < NPROD; ++pi)
+                  mma_bf16(dcol, sdesc(a_base + PA[pi] * A_PLANE + koff), sdesc(b_base + PX[pi] * B_PART + koff), ID,
+                           (pi == 0 && kt == 0 && ks == 0) ? 0u : 1u);
+              } else if (h == 0 && MERGE) {   // real part: [Re Z | Im Z] += Re H [Re X | Im X]
+#pragma unroll
+                for (int pi = 0; pi < NPROD; ++pi)
+                  mma_bf16(dcol, sdesc(a_base + PA[pi] * A_PLANE + koff), sdesc(b_base + PX[pi] * B_PART + koff), ID2,
+                           (pi == 0 && kt == 0 && ks == 0) ? 0u : 1u);
               } else {
-                const uint32_t first = (kt == 0 && ks == 0) ? 0u : 1u;
-                const uint64_t Bh = sdesc(b_base + koff), Bl = sdesc(b_base + B_PART + koff);
-                mma_bf16(dcol, Ah, Bh, ID, first);
-                mma_bf16(dcol, Ah, Bl, ID, 1);
-                mma_bf16(dcol, Al, Bh, ID, 1);
+                // one accumulator at a time: Re Z then Im Z
+                //   real part of H:       Re Z += Re H Re X,  Im Z += Re H Im X
+                //   imaginary part of H:  Re Z -= Im H Im X,  Im Z += Im H Re X
+#pragma unroll
+                for (int acc = 0; acc < 2; ++acc) {
+                  const uint32_t D = dcol + acc * NBV;
+                  const uint32_t xoff = (h == 0 ? acc : 1 - acc) * NBV * 128;
+                  const uint32_t idesc = (h == 1 && acc == 0) ? IDN : ID;
+#pragma unroll
+                  for (int pi = 0; pi < NPROD; ++pi)
+                    mma_bf16(D, sdesc(a_base + PA[pi] * A_PLANE + koff), sdesc(b_base + PX[pi] * B_PART + xoff + koff),
+                             idesc, (h == 0 && pi == 0 && kt == 0 && ks == 0) ? 0u : 1u);
+                }
               }
             }
             mma_commit(&a_empty[s]);
@@ -369,15 +390,25 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
           for (int w = 0; w < BATCH; ++w) {
             const int kk = 4 * (j0 + w) + 2 * r0;   // even: the pair shares one 4-byte word
             const float2 x0 = xv[2 * w], x1 = xv[2 * w + 1];
-            const __nv_bfloat162 rh = __floats2bfloat162_rn(x0.x, x1.x);
-            const __nv_bfloat162 rl = __floats2bfloat162_rn(x0.x - __low2float(rh), x1.x - __high2float(rh));
-            *reinterpret_cast<__nv_bfloat162*>(b0 + swz(v, kk)) = rh;
-            *reinterpret_cast<__nv_bfloat162*>(b0 + B_PART + swz(v, kk)) = rl;
+            // NPART-way split of the pair: part s = bf16 of what the earlier parts left (the
+            // differences are exact in FP32, so three parts hold an FP32 value exactly)
+            float ra = x0.x, rb = x1.x;
+#pragma unroll
+            for (int s = 0; s < NPART; ++s) {
+              const __nv_bfloat162 ps = __floats2bfloat162_rn(ra, rb);
+              *reinterpret_cast<__nv_bfloat162*>(b0 + s * B_PART + swz(v, kk)) = ps;
+              ra -= __low2float(ps);
+              rb -= __high2float(ps);
+            }
             if (CPLX) {
-              const __nv_bfloat162 ih = __floats2bfloat162_rn(x0.y, x1.y);
-              const __nv_bfloat162 il = __floats2bfloat162_rn(x0.y - __low2float(ih), x1.y - __high2float(ih));
-              *reinterpret_cast<__nv_bfloat162*>(b0 + swz(NBV + v, kk)) = ih;
-              *reinterpret_cast<__nv_bfloat162*>(b0 + B_PART + swz(NBV + v, kk)) = il;
+              float ia = x0.y, ib = x1.y;
+#pragma unroll
+              for (int s = 0; s < NPART; ++s) {
+                const __nv_bfloat162 ps = __floats2bfloat162_rn(ia, ib);
+                *reinterpret_cast<__nv_bfloat162*>(b0 + s * B_PART + swz(NBV + v, kk)) = ps;
+                ia -= __low2float(ps);
+                ib -= __high2float(ps);
+              }
             }
           }
         }
@@ -409,30 +440,39 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
           const int vb0 = v0 + 32 * h;
           const bool full = CPLX ? ((P.nv & 1) == 0 && vb0 + 32 <= P.nv) : ((P.nv & 3) == 0 && vb0 + 32 <= P.nv);
           if (full) {
-            // stage the warp's 32 rows x 32 values in shared memory (16-byte chunks, XOR-swizzled by
-            // row), then write whole row segments: 256 contiguous bytes per row (complex), 128 (real)
+            // stage the warp's rows (ER at a time) x 32 values in shared memory (16-byte chunks,
+            // XOR-swizzled by row), then write whole row segments: 256 contiguous bytes per row
+            // (complex), 128 (real)
             constexpr int CPR = CPLX ? 16 : 8;      // 16-byte chunks per row segment
             constexpr int RPI = 32 / CPR;           // rows per store instruction
+            constexpr int ER = Cfg::ER;
             unsigned char* st = sE + q * STG;
 #pragma unroll
-            for (int j = 0; j < CPR; ++j) {
-              const float4 v = CPLX ? make_float4(re[2 * j], im[2 * j], re[2 * j + 1], im[2 * j + 1])
-                                    : make_float4(re[4 * j], re[4 * j + 1], re[4 * j + 2], re[4 * j + 3]);
-              *reinterpret_cast<float4*>(st + lane * (CPR * 16) + ((j ^ (lane & (CPR - 1))) << 4)) = v;
-            }
-            __syncwarp();
-            const int ch = lane % CPR, rsub = lane / CPR;
+            for (int round = 0; round < 32 / ER; ++round) {
+              if (lane / ER == round) {
+                const int sl = lane % ER;              // staging row of this lane
 #pragma unroll
-            for (int i = 0; i < 32; i += RPI) {
-              const int rl = i + rsub;                       // row within the warp's 32
-              const int grow = m * MT + 32 * q + rl;
-              if (grow < naug) {
-                const float4 v = *reinterpret_cast<const float4*>(st + rl * (CPR * 16) + ((ch ^ (rl & (CPR - 1))) << 4));
-                float* zr = P.Z + ((size_t)e * A.npad + grow) * (size_t)P.nv * (CPLX ? 2 : 1);
-                *reinterpret_cast<float4*>(zr + (CPLX ? 2 : 1) * vb0 + 4 * ch) = v;
+                for (int j = 0; j < CPR; ++j) {
+                  const float4 v = CPLX ? make_float4(re[2 * j], im[2 * j], re[2 * j + 1], im[2 * j + 1])
+                                        : make_float4(re[4 * j], re[4 * j + 1], re[4 * j + 2], re[4 * j + 3]);
+                  *reinterpret_cast<float4*>(st + sl * (CPR * 16) + ((j ^ (sl & (CPR - 1))) << 4)) = v;
+                }
               }
+              __syncwarp();
+              const int ch = lane % CPR, rsub = lane / CPR;
+#pragma unroll
+              for (int i = 0; i < ER; i += RPI) {
+                const int rl = i + rsub;                     // staging row
+                const int grow = m * MT + 32 * q + round * ER + rl;
+                if (rl < ER && grow < naug) {
+                  const float4 v =
+                      *reinterpret_cast<const float4*>(st + rl * (CPR * 16) + ((ch ^ (rl & (CPR - 1))) << 4));
+                  float* zr = P.Z + ((size_t)e * A.npad + grow) * (size_t)P.nv * (CPLX ? 2 : 1);
+                  *reinterpret_cast<float4*>(zr + (CPLX ? 2 : 1) * vb0 + 4 * ch) = v;
+                }
+              }
+              __syncwarp();
             }
-            __syncwarp();
           } else if (row < naug) {
             float* zr = P.Z + ((size_t)e * A.npad + row) * (size_t)P.nv * (CPLX ? 2 : 1);
 #pragma unroll
@@ -476,22 +516,26 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t cell_mma_tma_smem(bool cplx) {
-  const int nbrows = cplx ? 2 * NBV : NBV;
-  return 1024 + (size_t)SA * 2 * MT * 128 + (size_t)SB * 2 * nbrows * 128 + 4 * (size_t)STG;
+size_t cell_mma_tma_smem(bool cplx, int parts) {
+  if (parts == 3) return cplx ? TmaCfg<true, 3>::SMEM : TmaCfg<false, 3>::SMEM;
+  return cplx ? TmaCfg<true, 2>::SMEM : TmaCfg<false, 2>::SMEM;
 }
 
 // Tensor map of one k-point's split cell matrices, stored tile-contiguous ([cell][K tile][M tile]
-// [plane][128][64]): 3D (column, row of a plane pair, chunk), box (64, 256, 1) = the hi and lo planes
-// of the real part, or of the imaginary part, of one (K tile, M tile).
+// [plane][128][64]): one box = the bf16 parts of the real or of the imaginary part of one
+// (K tile, M tile).
 int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out) {
   auto fn = encode_fn();
   if (!fn) { c->err = "cuTensorMapEncodeTiled is not available"; return OEFE_ERR_CUDA; }
-  const int planes = K.cplx ? 4 : 2;
-  const cuuint64_t nchunk = (cuuint64_t)c->ncells * (c->npad / KT) * (c->npad / MT) * (planes / 2);
-  const cuuint64_t dims[3] = {(cuuint64_t)KT, (cuuint64_t)2 * MT, nchunk};
-  const cuuint64_t strides[2] = {(cuuint64_t)KT * 2, (cuuint64_t)2 * MT * KT * 2};
-  const cuuint32_t box[3] = {KT, 2 * MT, 1};
+  const int parts = K.bf_parts;
+  if (parts != 2 && parts != 3) { c->err = "tensor map: no split cell matrices"; return OEFE_ERR_STATE; }
+  const int planes = (K.cplx ? 2 : 1) * parts;
+  const cuuint64_t nplanes = (cuuint64_t)c->ncells * (c->npad / KT) * (c->npad / MT) * planes;
+  // two parts: (column, row of a plane pair, chunk), box (64, 256, 1); three parts: (column, row,
+  // plane), box (64, 128, 3) (a box dimension holds at most 256)
+  const cuuint64_t dims[3] = {(cuuint64_t)KT, (cuuint64_t)MT * (parts == 2 ? 2 : 1), parts == 2 ? nplanes / 2 : nplanes};
+  const cuuint64_t strides[2] = {(cuuint64_t)KT * 2, (cuuint64_t)MT * KT * 2 * (parts == 2 ? 2 : 1)};
+  const cuuint32_t box[3] = {KT, (cuuint32_t)MT * (parts == 2 ? 2 : 1), parts == 2 ? 1u : 3u};
   const cuuint32_t estr[3] = {1, 1, 1};
   CUtensorMap m;
   const CUresult r = fn(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, K.Hbf, dims, strides, box, estr,
@@ -508,7 +552,8 @@ int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out) {
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
 int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
-                        bool cplx, int grid, cudaStream_t st) {
+                        bool cplx, int parts, int grid, cudaStream_t st) {
+  if (parts != 2 && parts != 3) { c->err = "tensor path: the split cell matrices were not stored"; return OEFE_ERR_STATE; }
   if (c->npad % MT != 0 || c->npad > 4 * MT) {
     c->err = "tensor path needs npad a multiple of 128 and at most 512";
     return OEFE_ERR_ARG;
@@ -526,14 +571,17 @@ int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const
   A.npad = c->npad;
   A.nh = c->nh;
   A.err = c->d_status;
-  const size_t smem = cell_mma_tma_smem(cplx);
-  if (cplx) {
-    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_tma<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    OEFE_COUNTED k_cell_mma_tma<true><<<grid, THREADS, smem, st>>>(A);
-  } else {
-    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_mma_tma<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    OEFE_COUNTED k_cell_mma_tma<false><<<grid, THREADS, smem, st>>>(A);
-  }
+  const size_t smem = cell_mma_tma_smem(cplx, parts);
+  auto go = [&](auto kern) -> int {
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    OEFE_COUNTED kern<<<grid, THREADS, smem, st>>>(A);
+    return OEFE_OK;
+  };
+  // merged real-part MMAs: the tuned choice, else on for the three-part split (measured faster)
+  const bool merge = c->tune_merge >= 0 ? c->tune_merge != 0 : parts == 3;
+  if (!cplx) OEFE_TRY(parts == 3 ? go(k_cell_mma_tma<false, 3, false>) : go(k_cell_mma_tma<false, 2, false>));
+  else if (parts == 3) OEFE_TRY(merge ? go(k_cell_mma_tma<true, 3, true>) : go(k_cell_mma_tma<true, 3, false>));
+  else OEFE_TRY(merge ? go(k_cell_mma_tma<true, 2, true>) : go(k_cell_mma_tma<true, 2, false>));
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
 }

@@ -632,6 +632,8 @@ namespace {
 
 struct BatchPlan {
   int nk, jlow, nb, grid;
+  int parts;   // bf16 parts of the split cell matrices
+  bool tma;    // warp-specialized TMA kernel (required for three parts)
   long long ntiles;
   std::vector<MmaK> mk;      // jlow * nk
   std::vector<NodeK> nd;     // jlow * nk
@@ -647,8 +649,8 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
   const int eb = (c->nO * vmax + 127) / 128;
   for (int j = 0; j < P.jlow; ++j) {
     if (timed) cudaEventRecordWithFlags(c->bev_kernel[2 * j], c->bstream, cudaEventRecordExternal);
-    if (c->use_tma && c->d_tmaps) {
-      OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk + (size_t)j * P.nk, nullptr, P.nk, P.ntiles, cplx,
+    if (P.tma) {
+      OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk + (size_t)j * P.nk, nullptr, P.nk, P.ntiles, cplx, P.parts,
                                    (int)std::min<long long>(P.ntiles, c->num_sms), c->bstream));
     } else if (P.grid > 0) {
       OEFE_TRY(launch_cell_mma_multi(c, d_mk + (size_t)j * P.nk, P.nk, P.ntiles, cplx, P.nb, P.grid, c->bstream));
@@ -712,7 +714,12 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     return OEFE_OK;
   }
   if (c->tune_nb == 0) { c->tune_nb = 64; c->tune_grid = c->num_sms; }
-  if (c->use_tma && c->d_tmaps) c->tune_nb = 64;
+  const int parts = c->kd[0].bf_parts;
+  for (int k = 1; k < nk; ++k)
+    if (c->kd[k].bf_parts != parts) { c->err = "filter_batched: k-points with different splits"; return OEFE_ERR_STATE; }
+  const bool tma = (c->use_tma || parts == 3) && c->d_tmaps;
+  if (!tma && parts != 2) { c->err = "filter_batched: the split cell matrices have no tensor maps"; return OEFE_ERR_STATE; }
+  if (tma) c->tune_nb = 64;
   // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed)
   std::vector<size_t> off(nk + 1, 0);
   auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
@@ -744,6 +751,8 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   P.jlow = jlow;
   P.nb = c->tune_nb;
   P.grid = c->tune_grid;
+  P.parts = parts;
+  P.tma = tma;
   P.ntiles = 0;
   std::vector<long long> tile0(nk);
   for (int k = 0; k < nk; ++k) {
@@ -806,7 +815,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   // graph key: everything baked into the captured launches
   std::vector<double> key = {(double)nk, (double)degree, (double)flags, (double)dtype, (double)(uintptr_t)base,
                              (double)P.nb, (double)P.grid, (double)(c->timing & (1 << dt_low) ? 1 : 0),
-                             (double)c->use_tma};
+                             (double)tma, (double)parts, (double)c->tune_merge};
   for (int k = 0; k < nk; ++k) {
     key.push_back((double)(uintptr_t)X[k]);
     key.push_back(nv[k]);
@@ -848,7 +857,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
       }
     }
     // set the kernels' shared-memory limits outside of the capture
-    if (c->use_tma && c->d_tmaps) OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, 0, cplx, 1, c->bstream));
+    if (tma) OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, 0, cplx, parts, 1, c->bstream));
     else if (P.grid > 0) OEFE_TRY(launch_cell_mma_multi(c, d_mk, nk, 0, cplx, P.nb, 1, c->bstream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
     cudaGraph_t graph;
@@ -957,9 +966,14 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
     else OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(XL[k], (size_t)nv[k] * es_low, X[k], (size_t)ld[k] * es_low,
                                             (size_t)nv[k] * es_low, (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
   }
-  struct Cand { int nb, grid, tma; };
-  const Cand cands[4] = {{64, c->num_sms, 0}, {32, c->num_sms, 0}, {64, 0, 0}, {64, c->num_sms, 1}};
-  const int ncand = c->d_tmaps ? 4 : 3;
+  struct Cand { int nb, grid, tma, merge; };
+  const Cand cands[5] = {{64, c->num_sms, 0, 0}, {32, c->num_sms, 0, 0}, {64, 0, 0, 0}, {64, c->num_sms, 1, 0},
+                         {64, c->num_sms, 1, 1}};
+  // the three-part split has only the TMA kernel; the two-part split also the one-CTA-per-tile kernels
+  const int parts = c->kd[0].bf_parts;
+  const int cfirst = parts == 3 ? 3 : 0;
+  const int ncand = c->d_tmaps ? (cplx ? 5 : 4) : 3;
+  if (cfirst >= ncand) { c->err = "autotune: no tensor maps for the split cell matrices"; return OEFE_ERR_STATE; }
   double best = 1e300;
   int bi = 0;
   MmaK* d_mk = nullptr;
@@ -968,7 +982,7 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int st = OEFE_OK;
-  for (int ci = 0; ci < ncand && st == OEFE_OK; ++ci) {
+  for (int ci = cfirst; ci < ncand && st == OEFE_OK; ++ci) {
     std::vector<MmaK> mk(nk);
     long long nt = 0;
     for (int k = 0; k < nk; ++k) {
@@ -986,8 +1000,9 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
     for (int rep = 0; rep < 3 && st == OEFE_OK; ++rep) {
       cudaEventRecord(e0, c->stream);
       if (cands[ci].tma) {
-        st = launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, nt, cplx, (int)std::min<long long>(nt, c->num_sms),
-                                 c->stream);
+        c->tune_merge = cands[ci].merge;
+        st = launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, nt, cplx, parts,
+                                 (int)std::min<long long>(nt, c->num_sms), c->stream);
       } else if (cands[ci].grid > 0) {
         st = launch_cell_mma_multi(c, d_mk, nk, nt, cplx, cands[ci].nb, cands[ci].grid, c->stream);
       } else {
@@ -1020,5 +1035,6 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
   c->tune_nb = cands[bi].nb;
   c->tune_grid = cands[bi].grid;
   c->use_tma = cands[bi].tma;
+  c->tune_merge = cands[bi].merge;
   return OEFE_OK;
 }

@@ -74,7 +74,8 @@ struct KData {
   double* Mooinv = nullptr;  // nO x nO scalars (FP64)
   double* H64 = nullptr;     // (ncells, npad, npad) scalars
   float* H32 = nullptr;      // (ncells, npad, npad) float or cf
-  void* Hbf = nullptr;       // bf16 planes (re hi, re lo[, im hi, im lo]), per cell [K tile][M tile][plane][128][64]
+  void* Hbf = nullptr;       // bf16 planes (re parts[, im parts]), per cell [K tile][M tile][plane][128][64]
+  int bf_parts = 0;          // bf16 parts per real plane in Hbf: 2 (hi, lo) or 3 (hi, mid, lo)
   void* E0 = nullptr;        // per cell: V-independent enrichment blocks (cd), CA then AA
   bool built = false;
 };
@@ -170,8 +171,9 @@ struct oefe_ctx {
   std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
   int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
   int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
+  int tune_merge = -1;                  // TMA kernel: merged real-part MMAs (1), separate (0), untuned (-1)
   long long bgraph_kernels = 0;         // kernel launches captured in the batched graph (counted per replay)
-  double tune_ms[4] = {0, 0, 0, 0};
+  double tune_ms[5] = {0, 0, 0, 0, 0};
   void* d_tmaps = nullptr;              // one tensor map per k-point (split cell matrices)
   int n_tmaps = 0;
 };
@@ -235,10 +237,10 @@ int launch_cell_mma_multi(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntile
 size_t cell_mma_smem(bool cplx, int nb);
 // warp-specialized TMA variant (cell_mma_tma.cu)
 int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
-                        bool cplx, int grid, cudaStream_t st);
+                        bool cplx, int parts, int grid, cudaStream_t st);
 int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out);
 size_t tensor_map_bytes();
-size_t cell_mma_tma_smem(bool cplx);
+size_t cell_mma_tma_smem(bool cplx, int parts);
 int launch_cell_mma_ptrs(oefe_ctx* c, const void* H, const void* X, int ldx, int nv, void* Z, bool cplx, int nb,
                          cudaStream_t st);
 

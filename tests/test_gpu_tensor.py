@@ -120,7 +120,7 @@ def test_autotune_then_batched_real():
     pr = prs[0]
     X = W.random_vectors(pr.n, 70, seed=4)
     ms = ctx.filter_autotune([to_gpu(X, torch.float32)])
-    assert np.all(ms > 0)   # four candidates, the TMA kernel included
+    assert np.all(ms[:4] > 0) and ms[4] == 0   # real vectors: four candidates, the TMA kernel included
     a, b, a0 = bounds(pr)
     ref = solver.chebyshev_filter(pr.apply_A, X, 5, a, b, a0)
     Xd = to_gpu(X, torch.float32)
@@ -196,3 +196,53 @@ def test_release_workspace_then_filter_again():
     Y = torch.empty_like(Xd)
     ctx.apply_h(0, Xd, Y)
     assert np.max(np.abs(Y.cpu().numpy() - pr.apply_H(X))) < 1e-12 * np.max(np.abs(pr.apply_H(X)))
+
+
+# BF16x6: three bf16 parts per operand, six products: FP32-class (the vectors are FP32)
+TOL6_DEGREE1 = 5e-6
+TOL6_FILTER = 5e-5
+
+
+@pytest.mark.parametrize("k", KS)
+@pytest.mark.parametrize("nv", [5, 64, 70])
+def test_bf16x6_single_degree(k, nv):
+    from paper_2010_09701_gb300 import FILTER_BF16X3, STORE_BF16X6, STORE_F64
+    prs, ctx, V, _ = paired(ks=[k], store=STORE_F64 | STORE_BF16X6)
+    pr = prs[0]
+    X = W.random_vectors(pr.n, nv, complex_=pr.complex, seed=nv + 60)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 1, 0.0, 500.0, -50.0)
+    Xd = to_gpu(X, torch.complex64 if pr.complex else torch.float32)
+    ctx.chebyshev_filter(0, Xd, 1, 0.0, 500.0, -50.0, flags=FILTER_BF16X3)
+    out = Xd.cpu().numpy().astype(np.complex128 if pr.complex else np.float64)
+    assert colerr(out, ref) < TOL6_DEGREE1
+
+
+def test_bf16x6_batched_two_k():
+    # the batched launch over two k-points with uneven vector counts
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X6, STORE_F64
+    prs, ctx, V, _ = paired(ks=KS2, store=STORE_F64 | STORE_BF16X6)
+    nvs = [20, 37]
+    Xs = [W.random_vectors(pr.n, nv, complex_=True, seed=70 + i) for i, (pr, nv) in enumerate(zip(prs, nvs))]
+    bnds = [bounds(pr) for pr in prs]
+    refs = [solver.chebyshev_filter(pr.apply_A, X, 7, *bd) for pr, X, bd in zip(prs, Xs, bnds)]
+    Xd = [to_gpu(X) for X in Xs]
+    ctx.filter_batched(Xd, 7, [bd[0] for bd in bnds], [bd[1] for bd in bnds], [bd[2] for bd in bnds],
+                       FILTER_BF16X3 | FILTER_LAST_FP64)
+    for k in range(2):
+        assert colerr(Xd[k].cpu().numpy(), refs[k]) < TOL6_FILTER, k
+    ms = ctx.filter_autotune([to_gpu(X, torch.complex64) for X in Xs])
+    assert ms[3] > 0 and ms[4] > 0 and np.all(ms[:3] == 0)   # only the TMA kernel takes three parts
+
+
+def test_bf16x6_four_m_tiles():
+    from paper_2010_09701_gb300 import FILTER_BF16X3, STORE_BF16X6, STORE_F64
+    pos = np.random.default_rng(5).uniform(0.0, 7.0, (9, 3))
+    prs, ctx, V, _ = paired(a=7.0, n=2, p=6, Zs=(3,) * 9, pos=pos, quad=(7, 7, 1), r0=2.0, rc=3.0,
+                            ks=[(0.2, 0.1, -0.3)], store=STORE_F64 | STORE_BF16X6)
+    pr = prs[0]
+    assert max(ctx.cell_info(e).size for e in range(8)) > 384
+    X = W.random_vectors(pr.n, 16, complex_=True, seed=3)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 1, 0.0, 500.0, -50.0)
+    Xd = to_gpu(X, torch.complex64)
+    ctx.chebyshev_filter(0, Xd, 1, 0.0, 500.0, -50.0, flags=FILTER_BF16X3)
+    assert colerr(Xd.cpu().numpy().astype(np.complex128), ref) < TOL6_DEGREE1
