@@ -34,7 +34,10 @@ FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12     # 2 DFMA / clk / SM on GB30
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, scaled to the
 # bench's launch by the units processed (valid while the kernels are unchanged since the capture)
-TRAFFIC_TENSOR = {}   # bf16 parts -> {"bytes_per_tile", "source"}; filled from a capture of the current kernel
+TRAFFIC_TENSOR = {   # bf16 parts of the split -> DRAM bytes per (k, cell, 64-vector) tile
+    2: {"bytes_per_tile": (2.044714e9 + 0.008223e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
+    3: {"bytes_per_tile": (3.064588e9 + 0.008374e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
+}
 TRAFFIC_FP64 = {"bytes_per_cell": (4.954736e9 + 0.205448e9) / 512, "source": "profiles/k_cell_apply_z3_c3small_8cube_p6.md"}
 
 

@@ -577,8 +577,8 @@ int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const
     OEFE_COUNTED kern<<<grid, THREADS, smem, st>>>(A);
     return OEFE_OK;
   };
-  // merged real-part MMAs: the tuned choice, else on for the three-part split (measured faster)
-  const bool merge = c->tune_merge >= 0 ? c->tune_merge != 0 : parts == 3;
+  // merged real-part MMAs: the tuned choice, else on (measured faster for both splits)
+  const bool merge = c->tune_merge >= 0 ? c->tune_merge != 0 : true;
   if (!cplx) OEFE_TRY(parts == 3 ? go(k_cell_mma_tma<false, 3, false>) : go(k_cell_mma_tma<false, 2, false>));
   else if (parts == 3) OEFE_TRY(merge ? go(k_cell_mma_tma<true, 3, true>) : go(k_cell_mma_tma<true, 3, false>));
   else OEFE_TRY(merge ? go(k_cell_mma_tma<true, 2, true>) : go(k_cell_mma_tma<true, 2, false>));
