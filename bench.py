@@ -38,7 +38,7 @@ TRAFFIC_TENSOR = {   # bf16 parts of the split -> DRAM bytes per (k, cell, 64-ve
     2: {"bytes_per_tile": (2.044714e9 + 0.008223e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
     3: {"bytes_per_tile": (3.064588e9 + 0.008374e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
 }
-TRAFFIC_FP64 = {"bytes_per_cell": (4.954736e9 + 0.205448e9) / 512, "source": "profiles/k_cell_apply_z3_c3small_8cube_p6.md"}
+TRAFFIC_FP64 = None   # {"bytes_per_cell", "source"} from a capture of the current FP64 product kernels
 
 
 def measured_peaks():
@@ -371,17 +371,18 @@ def run_ours(args, rank, world):
     # cell product "roofline_secondary"
     roofline, roof2 = roof_low, None
     if fp64_ms_launch is not None:
-        f64_flops = 6.0 * float(np.sum(naug.astype(float) ** 2)) * nvs[0]   # 3 FMAs per complex product
+        f64_flops = ctx.product_flops(0, nvs[0])   # FP64 operations the cell products execute
         f64_ach = f64_flops / (fp64_ms_launch * 1e-3) / 1e12
-        roof_fp64 = {"kernel": "k_cell_apply_z3 (FP64 complex cell product, 3 real multiplications)",
+        roof_fp64 = {"kernel": "k_cell_apply_sf + k_cell_apply_z3 (FP64 cell products: sum factorization on "
+                               "single-leaf cells, dense with 3 real multiplications on the refined cells)",
                      "bound": "alu", "achieved": f64_ach, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
                      "frac": f64_ach / FP64_PEAK_DERIVED,
-                     "traffic": TRAFFIC_FP64["bytes_per_cell"] * len(naug),
-                     "traffic_source": TRAFFIC_FP64["source"] + " (scaled by cells)",
+                     "traffic": TRAFFIC_FP64["bytes_per_cell"] * len(naug) if TRAFFIC_FP64 else None,
+                     "traffic_source": TRAFFIC_FP64["source"] + " (scaled by cells)" if TRAFFIC_FP64 else None,
                      "algorithmic_flops_per_launch": f64_flops, "ms_per_launch": fp64_ms_launch,
                      "launches_per_step": 2 * nk,
                      "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flops x 2070 MHz",
-                     "dense_equivalent_tflops": f64_ach * 8.0 / 6.0}
+                     "dense_equivalent_tflops": kernel_flops_per_launch(naug, nvs[0], True) / (fp64_ms_launch * 1e-3) / 1e12}
         low_ms_step = per_launch_ms * klaunch / max(args.steps, 1)
         if 2 * nk * fp64_ms_launch > low_ms_step:
             roofline, roof2 = roof_fp64, roof_low

@@ -274,6 +274,15 @@ int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches);
  * management: the build's scratch is several times the filter's). */
 int oefe_release_workspace(oefe_ctx_t ctx);
 
+/* oefe_product_flops -- FP64 operations (an FMA counts two) that one FP64
+ * operator application executes in its cell products for nv vectors at
+ * k-point ik: cells with one quadrature leaf are applied by sum
+ * factorization (the CFE block through 1D contractions, the enrichment blocks
+ * dense), the others densely with three real multiplications per complex
+ * product. flops: host pointer to one double. No counterpart in the paper
+ * (instrumentation for the roofline). */
+int oefe_product_flops(oefe_ctx_t ctx, int ik, int nv, double* flops);
+
 /* oefe_launch_count -- process-wide number of kernel launches the library has
  * issued so far (every context; a replay of a captured graph counts each of
  * its kernels). n: host pointer to one int64. Never synchronizes. Returns

@@ -58,6 +58,7 @@ SIGNATURES = [
     ("oefe_kernel_timing", _I, [_P, _I]),
     ("oefe_kernel_time", _I, [_P, _DP, _I64P]),
     ("oefe_release_workspace", _I, [_P]),
+    ("oefe_product_flops", _I, [_P, _I, _I, _DP]),
     ("oefe_launch_count", _I, [_c.POINTER(_c.c_int64)]),
 ]
 
@@ -348,6 +349,12 @@ class Context:
         px, nv, ld, dt = _block(X)
         self._check(self.lib.oefe_band_trace_grad(self.h, int(ik), px, nv, ld, dt, ctypes.c_void_p(gV.data_ptr())))
         return gV
+
+    def product_flops(self, ik, nv):
+        """FP64 operations of one FP64 operator application's cell products for nv vectors."""
+        f = ctypes.c_double()
+        self._check(self.lib.oefe_product_flops(self.h, int(ik), int(nv), ctypes.byref(f)))
+        return f.value
 
     def release_workspace(self):
         """Free the cached scratch arrays (the build's are several times the filter's)."""

@@ -35,6 +35,11 @@ static void free_all(oefe_ctx* c) {
   if (c->bstream) cudaStreamDestroy(c->bstream);
   dev_free(c->bparams);
   dev_free(c->d_tmaps);
+  dev_free(c->d_sf);
+  dev_free(c->d_sf_cells);
+  dev_free(c->d_dense_cells);
+  dev_free(c->d_sf_index);
+  dev_free(c->d_veff);
 }
 
 cudaEvent_t timing_event(oefe_ctx* c) {
@@ -339,6 +344,13 @@ int oefe_release_workspace(oefe_ctx_t ctx) {
   dev_free(ctx->ws2);
   ctx->ws = ctx->ws2 = nullptr;
   ctx->ws_bytes = ctx->ws2_bytes = 0;
+  return OEFE_OK;
+}
+
+int oefe_product_flops(oefe_ctx_t ctx, int ik, int nv, double* flops) {
+  CTX_CHECK(ctx);
+  if (!ctx->has_quad || ik < 0 || ik >= (int)ctx->kd.size() || nv < 1 || !flops) return OEFE_ERR_ARG;
+  *flops = fp64_product_flops(ctx, ctx->kd[ik].cplx, nv);
   return OEFE_OK;
 }
 

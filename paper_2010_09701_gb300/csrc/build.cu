@@ -13,6 +13,7 @@
 
 #include "oefe_internal.h"
 #include "enrich_dev.cuh"
+#include "sumfac_dev.cuh"
 
 namespace {
 
@@ -525,12 +526,22 @@ __global__ void k_hermitize(S* A, int n) {
   }
 }
 
+struct TransformSf {   // sum-factorized H_CC Gamma on single-leaf cells (null sf: dense everywhere)
+  const double* sf;
+  const int* sf_index;  // cell -> row of sf, or -1
+  const double* qw;
+  const double* veff;
+  const int64_t* q_off;
+  double k[3];
+  int P, nbuf;
+};
+
 // H^O_e = T_e^+ H_e T_e: CO = CA - H_CC Gamma, OO = AA - Gamma^+ CO - CA^+ Gamma.
 // One CTA per cell; writes the FP64 and/or FP32 stored matrices.
 template <typename S, typename S32>
 __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gamma, const int* act_off,
                                                   int e0, int nloc, int npad, int ne_max, S* H64,
-                                                  S32* H32, __nv_bfloat16* Hbf, int parts) {
+                                                  S32* H32, __nv_bfloat16* Hbf, int parts, TransformSf T) {
   extern __shared__ double smem[];
   const int b = blockIdx.x, e = e0 + b;
   const int ne = act_off[e + 1] - act_off[e];
@@ -582,6 +593,57 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
     const int r = t / npad, c = t % npad;
     if (r < nloc && c < nloc) put(r, c, HE[(size_t)r * npad + c]);
     else if (r >= nloc + ne || c >= nloc + ne) put(r, c, mkc(0, 0));
+  }
+  const int sfi = T.sf ? T.sf_index[e] : -1;
+  if (sfi >= 0) {
+    // single-leaf cell: H_CC Gamma by sum factorization, four columns at a time
+    constexpr bool CPLX = sizeof(S) == sizeof(cd);
+    constexpr int NB4 = 4, R = CPLX ? 2 : 1, J = NB4 * R;
+    const int P3 = T.P * T.P * T.P;
+    double* tab = smem;
+    double* Gr = tab + SF_STRIDE;
+    double* Gi = Gr + 3 * SF_MAXP * SF_MAXP;
+    double* Ws = Gi + 3 * SF_MAXP * SF_MAXP;
+    double* Xs = Ws + T.nbuf;                  // P3 * J
+    double* Ys = Xs + (size_t)P3 * J;          // P3 * J
+    double* Ab = Ys + (size_t)P3 * J;          // nbuf * J
+    double* Bb = Ab + (size_t)T.nbuf * J;      // nbuf * J
+    cd* C4 = reinterpret_cast<cd*>(Bb + (size_t)T.nbuf * J);   // nloc * NB4
+    sf_prepare(T.sf + (size_t)sfi * SF_STRIDE, tab, Gr, Gi, Ws, T.qw, T.veff, T.q_off[e], T.k);
+    for (int j0 = 0; j0 < ne; j0 += NB4) {
+      const int nj = min(NB4, ne - j0);
+      for (int t = threadIdx.x; t < P3 * NB4; t += TT) {
+        const int m = t / NB4, u = t % NB4;
+        const cd g = u < nj ? ld_s(Gm, (size_t)m * ne_max + j0 + u) : mkc(0, 0);
+        Xs[(size_t)m * J + u * R] = g.x;
+        if (CPLX) Xs[(size_t)m * J + u * R + 1] = g.y;
+      }
+      for (int t = threadIdx.x; t < P3 * J; t += TT) Ys[t] = 0.0;
+      __syncthreads();
+      sf_cc<CPLX, NB4>(tab, Gr, Gi, Ws, T.P, Xs, Ys, Ab, Bb);
+      for (int t = threadIdx.x; t < nloc * NB4; t += TT) {
+        const int m = t / NB4, u = t % NB4;
+        if (u < nj) {
+          const cd hg = mkc(Ys[(size_t)m * J + u * R], CPLX ? Ys[(size_t)m * J + u * R + 1] : 0.0);
+          const cd co = HE[(size_t)m * npad + nloc + j0 + u] - hg;
+          C4[t] = co;
+          put(m, nloc + j0 + u, co);
+          put(nloc + j0 + u, m, cconj(co));
+        }
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < ne * nj; t += TT) {
+        const int i = t / nj, u = t % nj, j = j0 + u;
+        cd s = HE[(size_t)(nloc + i) * npad + nloc + j];
+        for (int m = 0; m < nloc; ++m) {
+          s = cfmac(-ld_s(Gm, (size_t)m * ne_max + i), C4[m * NB4 + u], s);
+          s = cfmac(-HE[(size_t)m * npad + nloc + i], ld_s(Gm, (size_t)m * ne_max + j), s);
+        }
+        put(nloc + i, nloc + j, s);
+      }
+      __syncthreads();
+    }
+    return;
   }
   cd* Gs = CO + (size_t)nloc * JB;               // Gamma[:, j0:j0+JB], nloc * JB
   for (int j0 = 0; j0 < ne; j0 += JB) {
@@ -818,7 +880,22 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
         OEFE_COUNTED k_add_partials<<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
         OEFE_CUDA_TRY(c, cudaGetLastError());
       }
-      const size_t tsmem = (size_t)c->nloc * TJB * 2 * sizeof(cd);
+      TransformSf T;
+      T.sf = c->use_sumfac && c->n_sf > 0 ? c->d_sf : nullptr;
+      T.sf_index = c->d_sf_index;
+      T.qw = c->d_qw;
+      T.veff = veff;
+      T.q_off = c->d_q_off;
+      for (int d = 0; d < 3; ++d) T.k[d] = K.k[d];
+      T.P = c->P;
+      T.nbuf = c->sf_nbuf;
+      const size_t dense_smem = (size_t)c->nloc * TJB * 2 * sizeof(cd);
+      const size_t sf_smem = T.sf ? ((size_t)SF_STRIDE + SF_EXTRA + c->sf_nbuf +
+                                     (2 * (size_t)c->nloc + 2 * (size_t)c->sf_nbuf) * 4 * (K.cplx ? 2 : 1)) * sizeof(double) +
+                                        (size_t)c->nloc * 4 * sizeof(cd)
+                                  : 0;
+      if (sf_smem > 227 * 1024) T.sf = nullptr;   // too large for one CTA: dense products on these cells
+      const size_t tsmem = std::max(dense_smem, T.sf ? sf_smem : 0);
       OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<cd, cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
       OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)tsmem));
@@ -827,10 +904,10 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
       __nv_bfloat16* Hbf = (store & (OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6)) ? (__nv_bfloat16*)K.Hbf : nullptr;
       if (K.cplx)
         OEFE_COUNTED k_transform<cd, cf><<<nb, TT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf, K.bf_parts);
+                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf, K.bf_parts, T);
       else
         OEFE_COUNTED k_transform<double, float><<<nb, TT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                                c->ne_max, H64, H32, Hbf, K.bf_parts);
+                                                                c->ne_max, H64, H32, Hbf, K.bf_parts, T);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -923,6 +1000,9 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
   }
   double* d_gw = nullptr;
   OEFE_TRY(gauss_table(c, &d_gw));
+  // V at the points, kept for the sum-factorized FP64 products of this operator
+  if (!c->d_veff) OEFE_TRY(dev_alloc(c, (void**)&c->d_veff, (size_t)std::max<int64_t>(c->nq, 1) * sizeof(double)));
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(c->d_veff, veff, (size_t)c->nq * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   int st = OEFE_OK;
   for (auto& K : c->kd) {
     const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);

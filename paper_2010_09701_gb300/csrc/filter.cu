@@ -44,11 +44,12 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply(const typename Sc<T,
                                                             int ldx, int nv, const int* __restrict__ cell_nodes,
                                                             const int* __restrict__ act_off,
                                                             const int* __restrict__ act_idx, int nloc, int npad,
-                                                            int64_t nh, typename Sc<T, C>::type* __restrict__ Z) {
+                                                            int64_t nh, typename Sc<T, C>::type* __restrict__ Z,
+                                                            const int* __restrict__ cells) {
   using S = typename Sc<T, C>::type;
   extern __shared__ unsigned char smem_raw[];
   S* Xs = reinterpret_cast<S*>(smem_raw);  // npad x NB
-  const int e = blockIdx.x;
+  const int e = cells ? cells[blockIdx.x] : blockIdx.x;
   const int v0 = blockIdx.y * NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ne = act_off[e + 1] - act_off[e];
@@ -95,12 +96,13 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply_z3(const cd* __restr
                                                               int ldx, int nv, const int* __restrict__ cell_nodes,
                                                               const int* __restrict__ act_off,
                                                               const int* __restrict__ act_idx, int nloc, int npad,
-                                                              int64_t nh, cd* __restrict__ Z) {
+                                                              int64_t nh, cd* __restrict__ Z,
+                                                              const int* __restrict__ cells) {
   extern __shared__ unsigned char smem_raw[];
   double* Xr = reinterpret_cast<double*>(smem_raw);  // npad x NB3 each
   double* Xi = Xr + (size_t)npad * NB3;
   double* Xs = Xi + (size_t)npad * NB3;
-  const int e = blockIdx.x;
+  const int e = cells ? cells[blockIdx.x] : blockIdx.x;
   const int v0 = blockIdx.y * NB3;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = lane >> 4, hl = lane & 15;
@@ -402,24 +404,31 @@ int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const vo
                 const void* Xk, int ldk, const void* Xm1, int ldm1, void* Y, int ldy, void* Zbuf, cd* Yo, bool mma) {
   using S = typename Sc<T, C>::type;
   if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
+  // FP64: single-leaf cells by sum factorization, the others dense
+  const bool sf = sizeof(T) == 8 && sumfac_ready(c);
+  const int* dense_cells = sf ? c->d_dense_cells : nullptr;
+  const int ndense = sf ? c->n_dense : c->ncells;
+  if (sf) OEFE_TRY(launch_cell_apply_sf(c, K, Xin, ldin, nv, C, Zbuf, c->stream));
   if (mma) {
     OEFE_TRY(launch_cell_mma(c, K, Xin, ldin, nv, C, Zbuf));
+  } else if (ndense == 0) {
+    // every cell was a single-leaf cell
   } else if (sizeof(T) == 8 && C) {
-    dim3 grid(c->ncells, (nv + NB3 - 1) / NB3);
+    dim3 grid(ndense, (nv + NB3 - 1) / NB3);
     const size_t smem = (size_t)c->npad * NB3 * 3 * sizeof(double);
     if (smem > 227 * 1024) { c->err = "cell matrices too large for the shared-memory gather"; return OEFE_ERR_ARG; }
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply_z3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     OEFE_COUNTED k_cell_apply_z3<<<grid, CWARPS * 32, smem, c->stream>>>((const cd*)Hm, (const cd*)Xin, ldin, nv,
                                                                         c->d_cell_nodes, c->d_act_off, c->d_act_idx,
-                                                                        c->nloc, c->npad, c->nh, (cd*)Zbuf);
+                                                                        c->nloc, c->npad, c->nh, (cd*)Zbuf, dense_cells);
   } else {
-    dim3 grid(c->ncells, (nv + NB - 1) / NB);
+    dim3 grid(ndense, (nv + NB - 1) / NB);
     const size_t smem = (size_t)c->npad * NB * sizeof(S);
     if (smem > 227 * 1024) { c->err = "cell matrices too large for the shared-memory gather"; return OEFE_ERR_ARG; }
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     OEFE_COUNTED k_cell_apply<T, C><<<grid, CWARPS * 32, smem, c->stream>>>((const S*)Hm, (const S*)Xin, ldin, nv, c->d_cell_nodes,
                                                                c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh,
-                                                               (S*)Zbuf);
+                                                               (S*)Zbuf, dense_cells);
   }
   if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
   const int64_t tot = c->nh * nv;

@@ -171,6 +171,14 @@ struct oefe_ctx {
   std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
   int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
   int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
+  // sum-factorized FP64 products on single-leaf cells (sumfac.cu)
+  int use_sumfac = 1;
+  double* d_sf = nullptr;               // per single-leaf cell: n1, 1D tables, M/K/A
+  int* d_sf_cells = nullptr;            // single-leaf cells
+  int* d_dense_cells = nullptr;         // cells with several leaves (dense products)
+  int* d_sf_index = nullptr;            // cell -> row of d_sf, or -1
+  int n_sf = 0, n_dense = 0, sf_nbuf = 0;
+  double* d_veff = nullptr;             // V_eff at the points of the last operator build
   int tune_merge = -1;                  // TMA kernel: merged real-part MMAs (1), separate (0), untuned (-1)
   long long bgraph_kernels = 0;         // kernel launches captured in the batched graph (counted per replay)
   double tune_ms[5] = {0, 0, 0, 0, 0};
@@ -236,6 +244,14 @@ int launch_cell_mma_multi(oefe_ctx* c, const MmaK* d_ks, int nk, long long ntile
                           cudaStream_t st);
 size_t cell_mma_smem(bool cplx, int nb);
 // warp-specialized TMA variant (cell_mma_tma.cu)
+// sum factorization (sumfac.cu)
+int setup_sumfac(oefe_ctx* c);
+bool sumfac_ready(const oefe_ctx* c);
+int launch_cell_apply_sf(oefe_ctx* c, const KData& K, const void* X, int ldx, int nv, bool cplx, void* Z,
+                         cudaStream_t st);
+void cell_box(const oefe_ctx* c, int e, double lo[3], double hi[3]);
+double fp64_product_flops(const oefe_ctx* c, bool cplx, int nv);
+void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w);
 int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
                         bool cplx, int parts, int grid, cudaStream_t st);
 int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out);

@@ -269,7 +269,7 @@ static bool box_holds_point(const double lo[3], const double hi[3], const double
   return true;
 }
 
-static void cell_box(const oefe_ctx* c, int e, double lo[3], double hi[3]) {
+void cell_box(const oefe_ctx* c, int e, double lo[3], double hi[3]) {
   int ix = e % c->nc[0], iy = (e / c->nc[0]) % c->nc[1], iz = e / (c->nc[0] * c->nc[1]);
   lo[0] = c->xb[0][ix]; hi[0] = c->xb[0][ix + 1];
   lo[1] = c->xb[1][iy]; hi[1] = c->xb[1][iy + 1];
@@ -403,6 +403,8 @@ int setup_quadrature(oefe_ctx* c, int nq_cell, int nq_enr, int depth) {
   }
   c->nq_cell = nq_cell;
   c->nq_enr = nq_enr;
+  dev_free(c->d_veff);   // sized by the point count
+  c->d_veff = nullptr;
   c->depth = depth;
   c->leaves.clear();
   c->leaf_off.assign(c->ncells + 1, 0);
@@ -460,6 +462,7 @@ int setup_quadrature(oefe_ctx* c, int nq_cell, int nq_enr, int depth) {
   OEFE_TRY(upload(c, &c->d_leaves, c->leaves));
   OEFE_TRY(upload(c, &c->d_leaf_off, c->leaf_off));
   OEFE_TRY(upload(c, &c->d_q_off, c->q_off));
+  OEFE_TRY(setup_sumfac(c));
   c->has_quad = true;
   c->has_k = c->built = false;
   return OEFE_OK;

@@ -159,3 +159,30 @@ def test_filter_mixed_last_fp64(k, deg):
     err = np.max(np.linalg.norm(out - ref, axis=0) / nrm)
     assert err < 2e-5
     assert err > 1e-13          # the FP32 degrees did run
+
+
+@pytest.mark.parametrize("k", KS)
+def test_apply_h_c1_sum_factorized_cells(k):
+    # the graded 8^3 mesh: 496 single-leaf cells take the sum-factorized FP64 product, the 16
+    # octree-refined cells around the nuclei the dense one
+    w = W.config_c1()
+    xb = W.mesh_breakpoints(w)
+    prs, ctx, V, _ = paired(a=w.a, p=w.p, Zs=tuple(w.Z), pos=w.pos, xb=xb, quad=w.quad_params(), r0=w.r0,
+                            rc=w.rc, sigma=w.sigma, ks=[k])
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 13, complex_=pr.complex, seed=21)
+    Y = torch.empty_like(to_gpu(X))
+    ctx.apply_h(0, to_gpu(X), Y)
+    HX = pr.apply_H(X)
+    assert rel(Y.cpu().numpy(), HX) < 1e-13
+    # rounding of any summation order: |dY| <= c eps (|H| |X|) row by row
+    scale = abs(pr.assemble_H()) @ np.abs(X)
+    assert np.max(np.abs(Y.cpu().numpy() - HX) / scale) < 1e-13
+    ctx.apply_a(0, to_gpu(X), Y)
+    Ya = Y.cpu().numpy()
+    # M^{-1}: the lumped CFE rows scale row by row; the enrichment rows go through (M^oo)^{-1},
+    # whose condition number amplifies the rounding of H X, so they are checked by the residual
+    nh = pr.nh
+    assert np.max(np.abs(Ya[:nh] - HX[:nh] / pr.m[:, None]) * pr.m[:, None] / scale[:nh]) < 1e-13
+    res = pr.Moo @ Ya[nh:] - HX[nh:]
+    assert np.linalg.norm(res) < 1e-13 * np.linalg.norm(pr.Moo, 2) * np.linalg.norm(Ya[nh:])
