@@ -31,6 +31,8 @@ import workloads as W  # noqa: E402
 
 FP32_PEAK_DERIVED = 152 * 128 * 2 * 2.070e9 / 1e12   # FP32 FMA lanes x 2 flops x max SM clock
 FP64_PEAK_DERIVED = 152 * 2 * 2 * 2.070e9 / 1e12     # 2 DFMA / clk / SM on GB300
+# FP32-pair multiply-add: 12 FP32 instructions (exact product by FMA, two-sum, low-part update)
+PAIR_PEAK_DERIVED = 152 * 128 * 2.070e9 / 12 * 2 / 1e12
 FALLBACK_HBM_GBS = 6800.0
 # DRAM bytes (read + write) per launch from the ncu captures summarised under profiles/, scaled to the
 # bench's launch by the units processed (valid while the kernels are unchanged since the capture)
@@ -39,6 +41,7 @@ TRAFFIC_TENSOR = {   # bf16 parts of the split -> DRAM bytes per (k, cell, 64-ve
     3: {"bytes_per_tile": (3.064588e9 + 0.008374e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
 }
 TRAFFIC_FP64 = None   # {"bytes_per_cell", "source"} from a capture of the current FP64 product kernels
+TRAFFIC_PAIR = None   # the same for the FP32-pair products
 
 
 def measured_peaks():
@@ -157,8 +160,14 @@ def run_ours(args, rank, world):
     V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
     split = P.STORE_BF16X3 if args.bf16x3 else P.STORE_BF16X6
     store = P.STORE_F64 | (split if args.tensor else P.STORE_F32)
+    pairs = args.f64_products == "pairs"
+    if pairs:
+        store |= P.STORE_F64PAIR
+    ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
     if args.filter_only:   # profiling aid: the low-precision matrices (and FP64 ones on request) only
         store = (split if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
+        if args.with_fp64 and pairs:
+            store |= P.STORE_F64PAIR
     ctx.build_hamiltonian(V, store)
     if args.filter_only:
         ctx.release_workspace()   # the build's scratch is several times the filter's
@@ -314,6 +323,7 @@ def run_ours(args, rank, world):
     fp64_ms_launch = None
     if not args.skip_fp64:
         # one FP64 filter pass (k = 0) from the same start vectors, the FP64 cell product timed live
+        ctx.set_f64_products(P.F64_NATIVE)
         Xf = X0[0].clone()
         ctx.chebyshev_filter(0, Xf, 1, a_lo, bks[0], a0)   # warm
         Xf.copy_(X0[0])
@@ -329,6 +339,22 @@ def run_ours(args, rank, world):
         ctx.kernel_timing([])
         fp64_ms_launch = k64_ms / max(k64_n, 1)
         fp64_s = f0.elapsed_time(f1) * 1e-3
+        # the FP64-class product of the mixed step (FP32 pairs on the single-leaf cells), timed live
+        # on the same vectors
+        mix_ms_launch = fp64_ms_launch
+        if pairs:
+            ctx.set_f64_products(P.F64_PAIRS)
+            Yp = torch.empty_like(X0[0])
+            ctx.apply_h(0, X0[0], Yp)   # warm
+            torch.cuda.synchronize()
+            ctx.kernel_timing([P.C128])
+            for _ in range(3):
+                ctx.apply_h(0, X0[0], Yp)
+            torch.cuda.synchronize()
+            kp_ms, kp_n = ctx.kernel_time()
+            ctx.kernel_timing([])
+            mix_ms_launch = kp_ms / max(kp_n, 1)
+            del Yp
         fp64 = {"s_per_pass_k0": fp64_s,
                 "tflops": dense_filter_flops(naug, [nvs[0]], deg) / fp64_s / 1e12,
                 "speedup_mixed_vs_fp64": fp64_s / s_per_pass}
@@ -338,6 +364,8 @@ def run_ours(args, rank, world):
         # band energy settles; then one pass with the mixed filter and one with the FP64 filter from
         # that subspace are compared (band energy per atom, occupied Ritz values, residuals)
         def one_pass(Xp, lo, low, flags):
+            # the FP64 reference path runs native FP64 products throughout
+            ctx.set_f64_products(P.F64_PAIRS if (pairs and flags) else P.F64_NATIVE)
             ctx.chebyshev_filter(0, Xp, deg, lo, bks[0], low, flags=flags)
             ctx.orthonormalize(0, Xp)
             return ctx.rayleigh_ritz(0, Xp, resid=True)
@@ -355,6 +383,7 @@ def run_ours(args, rank, world):
             e_prev = e_now
         ev_m, res_m = one_pass(Xc.clone(), lo, low, mixed_flags)
         ev_d, res_d = one_pass(Xc.clone(), lo, low, 0)
+        ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
         _, occ_m, e_m = P.occupations([ev_m], [1.0], w.nelectrons)
         _, occ_d, e_d = P.occupations([ev_d], [1.0], w.nelectrons)
         occd = np.asarray(occ_d[0]) > 1e-8
@@ -371,20 +400,33 @@ def run_ours(args, rank, world):
     # cell product "roofline_secondary"
     roofline, roof2 = roof_low, None
     if fp64_ms_launch is not None:
-        f64_flops = ctx.product_flops(0, nvs[0])   # FP64 operations the cell products execute
+        f64_flops = ctx.product_flops(0, nvs[0])   # FP64-class operations the cell products execute
         f64_ach = f64_flops / (fp64_ms_launch * 1e-3) / 1e12
-        roof_fp64 = {"kernel": "k_cell_apply_sf + k_cell_apply_z3 (FP64 cell products: sum factorization on "
-                               "single-leaf cells, dense with 3 real multiplications on the refined cells)",
-                     "bound": "alu", "achieved": f64_ach, "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s",
-                     "frac": f64_ach / FP64_PEAK_DERIVED,
-                     "traffic": TRAFFIC_FP64["bytes_per_cell"] * len(naug) if TRAFFIC_FP64 else None,
-                     "traffic_source": TRAFFIC_FP64["source"] + " (scaled by cells)" if TRAFFIC_FP64 else None,
-                     "algorithmic_flops_per_launch": f64_flops, "ms_per_launch": fp64_ms_launch,
+        fp64["product"] = {"kernel": "k_cell_apply_sf<double> + k_cell_apply_z3", "ms_per_launch": fp64_ms_launch,
+                           "achieved_tflops": f64_ach, "frac_of_fp64_peak": f64_ach / FP64_PEAK_DERIVED}
+        mix_ach = f64_flops / (mix_ms_launch * 1e-3) / 1e12
+        traffic = TRAFFIC_PAIR if pairs else TRAFFIC_FP64
+        if pairs:
+            # the refined cells (dense FP64) take a few percent of the launch; the peak is that of
+            # the pair arithmetic on the FP32 pipe
+            kname = ("k_cell_apply_sf<f2> + k_cell_apply_z3 (FP64-class cell products: sum factorization in "
+                     "FP32-pair arithmetic on single-leaf cells, FP64 dense on the refined cells)")
+            peak, psrc = PAIR_PEAK_DERIVED, "derived: 152 SM x 128 FP32 lanes x 2070 MHz / 12 per pair FMA x 2 flops"
+        else:
+            kname = ("k_cell_apply_sf + k_cell_apply_z3 (FP64 cell products: sum factorization on "
+                     "single-leaf cells, dense with 3 real multiplications on the refined cells)")
+            peak, psrc = FP64_PEAK_DERIVED, "derived: 152 SM x 2 DFMA/clk x 2 flops x 2070 MHz"
+        roof_fp64 = {"kernel": kname,
+                     "bound": "alu", "achieved": mix_ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": mix_ach / peak,
+                     "traffic": traffic["bytes_per_cell"] * len(naug) if traffic else None,
+                     "traffic_source": traffic["source"] + " (scaled by cells)" if traffic else None,
+                     "algorithmic_flops_per_launch": f64_flops, "ms_per_launch": mix_ms_launch,
                      "launches_per_step": 2 * nk,
-                     "peak_source": "derived: 152 SM x 2 DFMA/clk x 2 flops x 2070 MHz",
-                     "dense_equivalent_tflops": kernel_flops_per_launch(naug, nvs[0], True) / (fp64_ms_launch * 1e-3) / 1e12}
+                     "peak_source": psrc,
+                     "dense_equivalent_tflops": kernel_flops_per_launch(naug, nvs[0], True) / (mix_ms_launch * 1e-3) / 1e12}
         low_ms_step = per_launch_ms * klaunch / max(args.steps, 1)
-        if 2 * nk * fp64_ms_launch > low_ms_step:
+        if 2 * nk * mix_ms_launch > low_ms_step:
             roofline, roof2 = roof_fp64, roof_low
         else:
             roof2 = roof_fp64
@@ -426,7 +468,9 @@ def run_ours(args, rank, world):
            "dtype": "c64+c128", "data": "synthetic",
            "config": {"workload": "zincblende a=8.5 bohr 8 atoms (Z 14/6), graded 16^3 cells p=6, 40 enrichment "
                                   "functions, MP 2x2x1 (4 k), 64 vectors/k, Chebyshev degree 30, mixed filter "
-                                  "(29 FP32 degrees + last FP64), FP64 Cholesky-QR / Rayleigh-Ritz / density",
+                                  "(29 FP32-class degrees + last FP64), FP64 Cholesky-QR / Rayleigh-Ritz / density",
+                      "f64_products": ("FP32 pairs on single-leaf cells (last degree and Rayleigh-Ritz H X)" if pairs
+                                       else "FP64"),
                       "n_dof_per_k": int(n), "cells": int(len(naug)), "mean_n_aug": float(np.mean(naug)),
                       "l2": "inputs larger than L2 (cell matrices %.1f GB per k)" % (np.sum(naug ** 2) * 8 / 1e9),
                       "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -521,6 +565,8 @@ def main():
     ap.add_argument("--acc-passes", type=int, default=40,
                     help="mixed subspace-iteration passes (k = 0) that converge the subspace the accuracy "
                          "comparison starts from")
+    ap.add_argument("--f64-products", default="pairs", choices=["pairs", "native"],
+                    help="arithmetic of the FP64-class cell products of the mixed step")
     ap.add_argument("--bf16x3", action="store_true",
                     help="two-part bf16 split of the cell matrices (BF16x3) instead of three parts (BF16x6)")
     ap.add_argument("--fp32-simt", dest="tensor", action="store_false",

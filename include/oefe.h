@@ -51,7 +51,9 @@ enum {
 enum { OEFE_F64 = 0, OEFE_F32 = 1, OEFE_C128 = 2, OEFE_C64 = 3 };
 
 /* Storage of the cell Hamiltonians (bit mask for oefe_build_hamiltonian). */
-enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4, OEFE_STORE_BF16X6 = 8 };
+enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4, OEFE_STORE_BF16X6 = 8, OEFE_STORE_F64PAIR = 16 };
+/* arithmetic of the FP64 cell products (oefe_set_f64_products) */
+enum { OEFE_F64_NATIVE = 0, OEFE_F64_PAIRS = 1 };
 
 /* ---------------------------------------------------------------- context */
 int oefe_create(oefe_ctx_t* out, int device, void* cuda_stream);
@@ -128,7 +130,10 @@ int oefe_ndof(oefe_ctx_t ctx, int64_t* n_h, int* n_O);
  * H_lo X_hi, ~2^-17 relative) and OEFE_STORE_BF16X6 (three bf16 parts hi + mid
  * + lo, 1.5x the bytes: six products, FP32-class accuracy; wins when both are
  * set). The tensor-core filter (OEFE_FILTER_BF16X3) uses whichever split is
- * stored. All arithmetic of the build is FP64. */
+ * stored. OEFE_STORE_F64PAIR (with OEFE_STORE_F64) also keeps each FP64 value
+ * as a pair of FP32 numbers hi + lo (same bytes as FP64, about 48 significant
+ * bits) for the FP32-pair products of oefe_set_f64_products. All arithmetic of
+ * the build is FP64. */
 int oefe_build_hamiltonian(oefe_ctx_t ctx, const double* veff_q, int store);
 
 /* Row/column map of one cell matrix: idx (host, n_aug ints) receives global
@@ -288,6 +293,19 @@ int oefe_product_flops(oefe_ctx_t ctx, int ik, int nv, double* flops);
  * its kernels). n: host pointer to one int64. Never synchronizes. Returns
  * OEFE_ERR_ARG when n is null. No counterpart in the paper (instrumentation). */
 int oefe_launch_count(int64_t* n);
+
+/* oefe_set_f64_products -- arithmetic of every FP64 cell product of the context
+ * (the FP64 filter degrees, oefe_apply_h / _a, the H X of oefe_rayleigh_ritz).
+ * mode OEFE_F64_NATIVE (default): FP64. OEFE_F64_PAIRS: on the cells with one
+ * quadrature leaf the sum-factorized product runs in FP32-pair arithmetic
+ * (each value an unevaluated sum of two FP32 numbers, error-free products and
+ * sums, about 2^-48 relative per operation; Dekker's double-length arithmetic)
+ * on the FP32 pipe, which on this GPU issues at 64 times the FP64 rate; the
+ * refined cells stay FP64. Inputs and outputs stay FP64. The operator must then
+ * be built with OEFE_STORE_F64PAIR, else the products return OEFE_ERR_STATE.
+ * Returns OEFE_ERR_ARG for another mode. No counterpart in the paper (the
+ * paper's machines had full-rate FP64). */
+int oefe_set_f64_products(oefe_ctx_t ctx, int mode);
 
 #ifdef __cplusplus
 }

@@ -14,7 +14,8 @@ LIB_PATH = os.path.join(HERE, "liboefe.so")
 OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_CHOLESKY, ERR_NOTPD_MOO, ERR_TIMEOUT, ERR_NUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 F64, F32, C128, C64 = 0, 1, 2, 3
-STORE_F64, STORE_F32, STORE_BF16X3, STORE_BF16X6 = 1, 2, 4, 8
+STORE_F64, STORE_F32, STORE_BF16X3, STORE_BF16X6, STORE_F64PAIR = 1, 2, 4, 8, 16
+F64_NATIVE, F64_PAIRS = 0, 1
 FILTER_LAST_FP64, FILTER_BF16X3 = 1, 2
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
 
@@ -60,6 +61,7 @@ SIGNATURES = [
     ("oefe_release_workspace", _I, [_P]),
     ("oefe_product_flops", _I, [_P, _I, _I, _DP]),
     ("oefe_launch_count", _I, [_c.POINTER(_c.c_int64)]),
+    ("oefe_set_f64_products", _I, [_P, _I]),
 ]
 
 _lib = None
@@ -355,6 +357,11 @@ class Context:
         f = ctypes.c_double()
         self._check(self.lib.oefe_product_flops(self.h, int(ik), int(nv), ctypes.byref(f)))
         return f.value
+
+    def set_f64_products(self, mode):
+        """Arithmetic of the FP64 cell products: F64_NATIVE, or F64_PAIRS (FP32 pairs on the
+        single-leaf cells; needs an operator built with STORE_F64PAIR)."""
+        self._check(self.lib.oefe_set_f64_products(self.h, int(mode)))
 
     def release_workspace(self):
         """Free the cached scratch arrays (the build's are several times the filter's)."""

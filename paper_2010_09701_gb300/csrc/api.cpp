@@ -16,7 +16,7 @@
 
 static void free_all(oefe_ctx* c) {
   for (auto& K : c->kd) {
-    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf);
+    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf); dev_free(K.Hp);
     dev_free(K.E0);
   }
   c->kd.clear();
@@ -351,6 +351,16 @@ int oefe_product_flops(oefe_ctx_t ctx, int ik, int nv, double* flops) {
   CTX_CHECK(ctx);
   if (!ctx->has_quad || ik < 0 || ik >= (int)ctx->kd.size() || nv < 1 || !flops) return OEFE_ERR_ARG;
   *flops = fp64_product_flops(ctx, ctx->kd[ik].cplx, nv);
+  return OEFE_OK;
+}
+
+int oefe_set_f64_products(oefe_ctx_t ctx, int mode) {
+  CTX_CHECK(ctx);
+  if (mode != OEFE_F64_NATIVE && mode != OEFE_F64_PAIRS) {
+    ctx->err = "set_f64_products: mode must be OEFE_F64_NATIVE or OEFE_F64_PAIRS";
+    return OEFE_ERR_ARG;
+  }
+  ctx->f64_products = mode;
   return OEFE_OK;
 }
 

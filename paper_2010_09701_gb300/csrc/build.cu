@@ -541,7 +541,7 @@ struct TransformSf {   // sum-factorized H_CC Gamma on single-leaf cells (null s
 template <typename S, typename S32>
 __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gamma, const int* act_off,
                                                   int e0, int nloc, int npad, int ne_max, S* H64,
-                                                  S32* H32, __nv_bfloat16* Hbf, int parts, TransformSf T) {
+                                                  S32* H32, __nv_bfloat16* Hbf, float* Hp, int parts, TransformSf T) {
   extern __shared__ double smem[];
   const int b = blockIdx.x, e = e0 + b;
   const int ne = act_off[e + 1] - act_off[e];
@@ -554,9 +554,18 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
     if constexpr (sizeof(S) == sizeof(cd)) {
       if (H64) reinterpret_cast<cd*>(H64)[o] = v;
       if (H32) reinterpret_cast<cf*>(H32)[o] = cf{(float)v.x, (float)v.y};
+      if (Hp) {
+        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+        reinterpret_cast<float4*>(Hp)[o] =
+            make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+      }
     } else {
       if (H64) reinterpret_cast<double*>(H64)[o] = v.x;
       if (H32) reinterpret_cast<float*>(H32)[o] = (float)v.x;
+      if (Hp) {
+        const float h = __double2float_rn(v.x);
+        reinterpret_cast<float2*>(Hp)[o] = make_float2(h, __double2float_rn(v.x - (double)h));
+      }
     }
     if (Hbf) {
       // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
@@ -620,7 +629,7 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
       }
       for (int t = threadIdx.x; t < P3 * J; t += TT) Ys[t] = 0.0;
       __syncthreads();
-      sf_cc<CPLX, NB4>(tab, Gr, Gi, Ws, T.P, Xs, Ys, Ab, Bb);
+      sf_cc<double, CPLX, NB4>(tab, Gr, Gi, Ws, T.P, Xs, Ys, Ab, Bb);
       for (int t = threadIdx.x; t < nloc * NB4; t += TT) {
         const int m = t / NB4, u = t % NB4;
         if (u < nj) {
@@ -632,14 +641,16 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
         }
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < ne * nj; t += TT) {
+      for (int t = threadIdx.x; t < ne * nj; t += TT) {   // OO is Hermitian: i <= j, mirrored
         const int i = t / nj, u = t % nj, j = j0 + u;
+        if (i > j) continue;
         cd s = HE[(size_t)(nloc + i) * npad + nloc + j];
         for (int m = 0; m < nloc; ++m) {
           s = cfmac(-ld_s(Gm, (size_t)m * ne_max + i), C4[m * NB4 + u], s);
           s = cfmac(-HE[(size_t)m * npad + nloc + i], ld_s(Gm, (size_t)m * ne_max + j), s);
         }
         put(nloc + i, nloc + j, s);
+        if (i != j) put(nloc + j, nloc + i, cconj(s));
       }
       __syncthreads();
     }
@@ -676,15 +687,18 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
       }
     }
     __syncthreads();
-    // OO[i][j] = AA[i][j] - sum_m conj(Gamma[m][i]) CO[m][j] - sum_m conj(CA[m][i]) Gamma[m][j]
+    // OO[i][j] = AA[i][j] - sum_m conj(Gamma[m][i]) CO[m][j] - sum_m conj(CA[m][i]) Gamma[m][j];
+    // OO is Hermitian: i <= j, mirrored
     for (int t = threadIdx.x; t < ne * nj; t += TT) {
       const int i = t / nj, u = t % nj, j = j0 + u;
+      if (i > j) continue;
       cd s = HE[(size_t)(nloc + i) * npad + nloc + j];
       for (int m = 0; m < nloc; ++m) {
         s = cfmac(-ld_s(Gm, (size_t)m * ne_max + i), CO[m * JB + u], s);
         s = cfmac(-HE[(size_t)m * npad + nloc + i], Gs[m * JB + u], s);
       }
       put(nloc + i, nloc + j, s);
+      if (i != j) put(nloc + j, nloc + i, cconj(s));
     }
     __syncthreads();
   }
@@ -902,12 +916,13 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
       float* H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
       double* H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
       __nv_bfloat16* Hbf = (store & (OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6)) ? (__nv_bfloat16*)K.Hbf : nullptr;
+      float* Hp = (store & OEFE_STORE_F64PAIR) ? K.Hp : nullptr;
       if (K.cplx)
         OEFE_COUNTED k_transform<cd, cf><<<nb, TT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf, K.bf_parts, T);
+                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf, Hp, K.bf_parts, T);
       else
         OEFE_COUNTED k_transform<double, float><<<nb, TT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                                c->ne_max, H64, H32, Hbf, K.bf_parts, T);
+                                                                c->ne_max, H64, H32, Hbf, Hp, K.bf_parts, T);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -919,7 +934,7 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
   if (!c->has_quad) { c->err = "kpoints: call oefe_quadrature first"; return OEFE_ERR_STATE; }
   if (nk < 1 || nk > 4096 || !k || !w) { c->err = "kpoints: need 1 <= nk <= 4096, k, w"; return OEFE_ERR_ARG; }
   for (auto& K : c->kd) {
-    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf);
+    dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf); dev_free(K.Hp);
     dev_free(K.E0);
   }
   c->kd.assign(nk, KData());
@@ -998,6 +1013,10 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
     c->err = "build_hamiltonian: need veff and a storage flag";
     return OEFE_ERR_ARG;
   }
+  if ((store & OEFE_STORE_F64PAIR) && !(store & OEFE_STORE_F64)) {
+    c->err = "build_hamiltonian: OEFE_STORE_F64PAIR goes with OEFE_STORE_F64 (the refined cells stay FP64)";
+    return OEFE_ERR_ARG;
+  }
   double* d_gw = nullptr;
   OEFE_TRY(gauss_table(c, &d_gw));
   // V at the points, kept for the sum-factorized FP64 products of this operator
@@ -1015,6 +1034,7 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
     };
     st = keep((void**)&K.H64, store & OEFE_STORE_F64, n * sb);
     if (st == OEFE_OK) st = keep((void**)&K.H32, store & OEFE_STORE_F32, n * sb / 2);
+    if (st == OEFE_OK) st = keep((void**)&K.Hp, store & OEFE_STORE_F64PAIR, n * sb);
     const int parts = (store & OEFE_STORE_BF16X6) ? 3 : (store & OEFE_STORE_BF16X3) ? 2 : 0;
     if (parts != K.bf_parts) {   // a different split: a new buffer
       dev_free(K.Hbf);

@@ -74,6 +74,7 @@ struct KData {
   double* Mooinv = nullptr;  // nO x nO scalars (FP64)
   double* H64 = nullptr;     // (ncells, npad, npad) scalars
   float* H32 = nullptr;      // (ncells, npad, npad) float or cf
+  float* Hp = nullptr;       // (ncells, npad, npad) FP64 values as FP32 pairs (h, l per real part)
   void* Hbf = nullptr;       // bf16 planes (re parts[, im parts]), per cell [K tile][M tile][plane][128][64]
   int bf_parts = 0;          // bf16 parts per real plane in Hbf: 2 (hi, lo) or 3 (hi, mid, lo)
   void* E0 = nullptr;        // per cell: V-independent enrichment blocks (cd), CA then AA
@@ -173,6 +174,7 @@ struct oefe_ctx {
   int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
   // sum-factorized FP64 products on single-leaf cells (sumfac.cu)
   int use_sumfac = 1;
+  int f64_products = OEFE_F64_NATIVE;   // arithmetic of the sum-factorized FP64 products
   double* d_sf = nullptr;               // per single-leaf cell: n1, 1D tables, M/K/A
   int* d_sf_cells = nullptr;            // single-leaf cells
   int* d_dense_cells = nullptr;         // cells with several leaves (dense products)

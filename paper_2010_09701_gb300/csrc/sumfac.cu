@@ -46,6 +46,7 @@ struct SfArgs {
   const double* sf;          // per listed cell: SF_STRIDE doubles
   const int* cells;          // listed cells
   const void* H;             // FP64 cell matrices (npad x npad per cell)
+  const float* Hp;           // the same as FP32 pairs (h, l per real part), for V = f2
   const void* X;
   int ldx, nv;
   const int* cell_nodes;
@@ -60,27 +61,31 @@ struct SfArgs {
   void* Z;
 };
 
-// one CTA per (listed cell, block of NV vectors); components j = (vector, re/im) innermost
-template <bool CPLX, int NV>
-__global__ void __launch_bounds__(SF_THREADS) k_cell_apply_sf(const SfArgs A) {
+// one CTA per (block of NV vectors, listed cell): the vector blocks of a cell are adjacent in the
+// launch order, so the cell's enrichment blocks come from DRAM once and from L2 after that.
+// Components j = (vector, re/im) innermost. V = double: FP64; V = f2: FP32 pairs.
+template <bool CPLX, int NV, typename V, int NT>
+__global__ void __launch_bounds__(NT) k_cell_apply_sf(const SfArgs A) {
+  using Acc = typename AccOf<V>::type;
   constexpr int R = CPLX ? 2 : 1;
   constexpr int J = NV * R;
-  extern __shared__ double sm[];
-  const int e = A.cells[blockIdx.x];
-  const int v0 = blockIdx.y * NV;
+  extern __shared__ double sm_raw[];
+  V* sm = reinterpret_cast<V*>(sm_raw);
+  const int e = A.cells[blockIdx.y];
+  const int v0 = blockIdx.x * NV;
   const int P = A.P, nloc = A.nloc, npad = A.npad;
   const int ne = A.act_off[e + 1] - A.act_off[e];
   const int naug = nloc + ne;
-  double* tab = sm;                                   // SF_STRIDE
-  double* Gr = tab + SF_STRIDE;                       // K_d / 2            [3][SF_MAXP][SF_MAXP]
-  double* Gi = Gr + 3 * SF_MAXP * SF_MAXP;            // -(k_d / 2) A_d     [3][SF_MAXP][SF_MAXP]
-  double* Ws = Gi + 3 * SF_MAXP * SF_MAXP;            // w_q (V_q + |k|^2 / 2), nbuf
-  double* Xs = Ws + A.nbuf;                           // npad * J
-  double* Ys = Xs + (size_t)npad * J;                 // nloc * J
-  double* Ab = Ys + (size_t)nloc * J;                 // nbuf * J
-  double* Bb = Ab + (size_t)A.nbuf * J;               // nbuf * J
-  sf_prepare(A.sf + (size_t)blockIdx.x * SF_STRIDE, tab, Gr, Gi, Ws, A.qw, A.veff, A.q_off[e], A.k);
-  for (int t = threadIdx.x; t < npad * NV; t += SF_THREADS) {
+  V* tab = sm;                                        // SF_STRIDE
+  V* Gr = tab + SF_STRIDE;                            // K_d / 2            [3][SF_MAXP][SF_MAXP]
+  V* Gi = Gr + 3 * SF_MAXP * SF_MAXP;                 // -(k_d / 2) A_d     [3][SF_MAXP][SF_MAXP]
+  V* Ws = Gi + 3 * SF_MAXP * SF_MAXP;                 // w_q (V_q + |k|^2 / 2), nbuf
+  V* Xs = Ws + A.nbuf;                                // npad * J
+  V* Ys = Xs + (size_t)npad * J;                      // nloc * J
+  V* Ab = Ys + (size_t)nloc * J;                      // nbuf * J
+  V* Bb = Ab + (size_t)A.nbuf * J;                    // nbuf * J
+  sf_prepare<V>(A.sf + (size_t)blockIdx.y * SF_STRIDE, tab, Gr, Gi, Ws, A.qw, A.veff, A.q_off[e], A.k);
+  for (int t = threadIdx.x; t < npad * NV; t += NT) {
     const int r = t / NV, v = t % NV;
     double xr = 0.0, xi = 0.0;
     if (r < naug && v0 + v < A.nv) {
@@ -93,40 +98,123 @@ __global__ void __launch_bounds__(SF_THREADS) k_cell_apply_sf(const SfArgs A) {
         xr = reinterpret_cast<const double*>(A.X)[row * A.ldx + v0 + v];
       }
     }
-    Xs[(size_t)r * J + v * R] = xr;
-    if (CPLX) Xs[(size_t)r * J + v * R + 1] = xi;
+    Xs[(size_t)r * J + v * R] = v_from<V>(xr);
+    if (CPLX) Xs[(size_t)r * J + v * R + 1] = v_from<V>(xi);
   }
-  for (int t = threadIdx.x; t < nloc * J; t += SF_THREADS) Ys[t] = 0.0;
+  for (int t = threadIdx.x; t < nloc * J; t += NT) Ys[t] = v_from<V>(0.0);
   __syncthreads();
-  sf_cc<CPLX, NV>(tab, Gr, Gi, Ws, P, Xs, Ys, Ab, Bb);
+  sf_cc<V, CPLX, NV>(tab, Gr, Gi, Ws, P, Xs, Ys, Ab, Bb);
 
   // ---- enrichment blocks from the stored matrix: rows of the nodes get H_CO x_O, the enrichment
   //      rows get H_OC x_C + H_OO x_O; then every row of the product is written
   using S = typename std::conditional<CPLX, cd, double>::type;
-  const S* He = reinterpret_cast<const S*>(A.H) + (size_t)e * npad * npad;
   S* Z = reinterpret_cast<S*>(A.Z);
-  for (int t = threadIdx.x; t < naug * NV; t += SF_THREADS) {
-    const int v = t % NV, r = t / NV;
-    if (v0 + v >= A.nv) continue;
-    const S* hr = He + (size_t)r * npad;
-    double yr = 0, yi = 0;
-    if (r < nloc) {
-      yr = Ys[(size_t)r * J + v * R];
-      if (CPLX) yi = Ys[(size_t)r * J + v * R + 1];
+  if constexpr (std::is_same<V, double>::value) {
+    // one (row, vector) per thread
+    for (int t = threadIdx.x; t < naug * NV; t += NT) {
+      const int v = t % NV, r = t / NV;
+      if (v0 + v >= A.nv) continue;
+      const int c0 = r < nloc ? nloc : 0;            // node rows: enrichment columns only
+      const S* hr = reinterpret_cast<const S*>(A.H) + ((size_t)e * npad + r) * npad;
+      double yr = 0, yi = 0;
+      if (r < nloc) {
+        yr = Ys[(size_t)r * J + v * R];
+        if (CPLX) yi = Ys[(size_t)r * J + v * R + 1];
+      }
+      for (int cidx = c0; cidx < naug; ++cidx) {
+        const double* x = Xs + (size_t)cidx * J + v * R;
+        if constexpr (CPLX) {
+          const cd h = hr[cidx];
+          yr = fma(h.x, x[0], fma(-h.y, x[1], yr));
+          yi = fma(h.x, x[1], fma(h.y, x[0], yi));
+        } else {
+          yr = fma(hr[cidx], x[0], yr);
+        }
+      }
+      if constexpr (CPLX) Z[((size_t)e * npad + r) * A.nv + v0 + v] = mkc(yr, yi);
+      else Z[((size_t)e * npad + r) * A.nv + v0 + v] = yr;
     }
-    const int c0 = r < nloc ? nloc : 0;            // node rows: enrichment columns only
-    for (int cidx = c0; cidx < naug; ++cidx) {
-      const double* x = Xs + (size_t)cidx * J + v * R;
-      if constexpr (CPLX) {
-        const cd h = hr[cidx];
-        yr = fma(h.x, x[0], fma(-h.y, x[1], yr));
-        yi = fma(h.x, x[1], fma(h.y, x[0], yi));
+  } else {
+    // one item per thread, all NV vectors: each pair of the matrix is loaded once for NV * R
+    // independent accumulations. Items: a node row over the ne enrichment columns, or a chunk of
+    // at most EC columns of an enrichment row (the partial sums meet in shared memory), so that
+    // the items have about the same length.
+    int nch = min((naug + 47) / 48, A.nbuf / max(ne, 1));  // chunks of about 48 columns; the
+    nch = max(nch, 1);                                      // partial sums must fit in Ab
+    const int EC = (naug + nch - 1) / nch;
+    V* part = Ab;                                          // (ne * nch) x J partial sums
+    for (int it = threadIdx.x; it < nloc + ne * nch; it += NT) {
+      int r, ca, cb;
+      if (it < nloc) {
+        r = it;
+        ca = nloc;
+        cb = naug;
       } else {
-        yr = fma(hr[cidx], x[0], yr);
+        const int q = it - nloc;
+        r = nloc + q / nch;
+        ca = (q % nch) * EC;
+        cb = min(naug, ca + EC);
+      }
+      Acc y[J];
+#pragma unroll
+      for (int j = 0; j < J; ++j) {
+        const V s = it < nloc ? Ys[(size_t)r * J + j] : v_from<V>(0.0);
+        y[j] = Acc{s.h, s.l};
+      }
+      if constexpr (CPLX) {
+        const float4* hr = reinterpret_cast<const float4*>(A.Hp) + ((size_t)e * npad + r) * npad;
+        float4 hn = ca < cb ? hr[ca] : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int cidx = ca; cidx < cb; ++cidx) {
+          const float4 h = hn;
+          if (cidx + 1 < cb) hn = hr[cidx + 1];     // next pair in flight during the products
+          const V hre{h.x, h.y}, him{h.z, h.w}, nhim = v_neg(him);
+          const V* x = Xs + (size_t)cidx * J;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const V xr = x[2 * v], xi = x[2 * v + 1];
+            v_mac(y[2 * v], hre, xr);
+            v_mac(y[2 * v + 1], hre, xi);
+            v_mac(y[2 * v], nhim, xi);
+            v_mac(y[2 * v + 1], him, xr);
+          }
+        }
+      } else {
+        const float2* hr = reinterpret_cast<const float2*>(A.Hp) + ((size_t)e * npad + r) * npad;
+        float2 hn = ca < cb ? hr[ca] : make_float2(0.f, 0.f);
+        for (int cidx = ca; cidx < cb; ++cidx) {
+          const float2 h = hn;
+          if (cidx + 1 < cb) hn = hr[cidx + 1];
+          const V hv{h.x, h.y};
+          const V* x = Xs + (size_t)cidx * J;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) v_mac(y[v], hv, x[v]);
+        }
+      }
+      if (it < nloc) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          if (v0 + v >= A.nv) continue;
+          if constexpr (CPLX) Z[((size_t)e * npad + r) * A.nv + v0 + v] = mkc(v_to(v_fin(y[2 * v])), v_to(v_fin(y[2 * v + 1])));
+          else Z[((size_t)e * npad + r) * A.nv + v0 + v] = v_to(v_fin(y[v]));
+        }
+      } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j) part[(size_t)(it - nloc) * J + j] = v_fin(y[j]);
       }
     }
-    if constexpr (CPLX) Z[((size_t)e * npad + r) * A.nv + v0 + v] = mkc(yr, yi);
-    else Z[((size_t)e * npad + r) * A.nv + v0 + v] = yr;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ne * NV; t += NT) {   // enrichment rows: sum of the chunks
+      const int i = t / NV, v = t % NV;
+      if (v0 + v >= A.nv) continue;
+      V sr = v_from<V>(0.0), si = v_from<V>(0.0);
+      for (int ch = 0; ch < nch; ++ch) {
+        const V* pp = part + (size_t)(i * nch + ch) * J + v * R;
+        sr = v_add(sr, pp[0]);
+        if (CPLX) si = v_add(si, pp[1]);
+      }
+      if constexpr (CPLX) Z[((size_t)e * npad + nloc + i) * A.nv + v0 + v] = mkc(v_to(sr), v_to(si));
+      else Z[((size_t)e * npad + nloc + i) * A.nv + v0 + v] = v_to(sr);
+    }
   }
 }
 
@@ -229,6 +317,7 @@ int launch_cell_apply_sf(oefe_ctx* c, const KData& K, const void* X, int ldx, in
   A.sf = c->d_sf;
   A.cells = c->d_sf_cells;
   A.H = K.H64;
+  A.Hp = K.Hp;
   A.X = X;
   A.ldx = ldx;
   A.nv = nv;
@@ -245,16 +334,21 @@ int launch_cell_apply_sf(oefe_ctx* c, const KData& K, const void* X, int ldx, in
   A.q_off = c->d_q_off;
   for (int d = 0; d < 3; ++d) A.k[d] = K.k[d];
   A.Z = Z;
-  auto go = [&](auto kern, size_t smem, int nvb) -> int {
+  auto go = [&](auto kern, size_t smem, int nvb, int nthreads) -> int {
     if (smem > 227 * 1024) { c->err = "sum factorization: work arrays exceed shared memory"; return OEFE_ERR_ARG; }
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    dim3 grid(c->n_sf, (nv + nvb - 1) / nvb);
-    OEFE_COUNTED kern<<<grid, SF_THREADS, smem, st>>>(A);
+    dim3 grid((nv + nvb - 1) / nvb, c->n_sf);
+    OEFE_COUNTED kern<<<grid, nthreads, smem, st>>>(A);
     OEFE_CUDA_TRY(c, cudaGetLastError());
     return OEFE_OK;
   };
-  if (cplx) return go(k_cell_apply_sf<true, 4>, sf_smem<true>(c, 4), 4);
-  return go(k_cell_apply_sf<false, 8>, sf_smem<false>(c, 8), 8);
+  if (c->f64_products == OEFE_F64_PAIRS) {
+    if (!K.Hp) { c->err = "FP32-pair products: build the operator with OEFE_STORE_F64PAIR"; return OEFE_ERR_STATE; }
+    if (cplx) return go(k_cell_apply_sf<true, 4, f2, 512>, sf_smem<true>(c, 4), 4, 512);
+    return go(k_cell_apply_sf<false, 8, f2, 512>, sf_smem<false>(c, 8), 8, 512);
+  }
+  if (cplx) return go(k_cell_apply_sf<true, 4, double, SF_THREADS>, sf_smem<true>(c, 4), 4, SF_THREADS);
+  return go(k_cell_apply_sf<false, 8, double, SF_THREADS>, sf_smem<false>(c, 8), 8, SF_THREADS);
 }
 
 // FP64 operations (an FMA counts two) of one FP64 application of the cell products to nv vectors:

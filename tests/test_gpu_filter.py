@@ -186,3 +186,38 @@ def test_apply_h_c1_sum_factorized_cells(k):
     assert np.max(np.abs(Ya[:nh] - HX[:nh] / pr.m[:, None]) * pr.m[:, None] / scale[:nh]) < 1e-13
     res = pr.Moo @ Ya[nh:] - HX[nh:]
     assert np.linalg.norm(res) < 1e-13 * np.linalg.norm(pr.Moo, 2) * np.linalg.norm(Ya[nh:])
+
+
+@pytest.mark.parametrize("k", KS)
+def test_apply_h_c1_fp32_pair_products(k):
+    # FP32-pair arithmetic on the 496 single-leaf cells (the refined cells stay FP64). Each pair
+    # operation rounds at about u = 2^-48 instead of 2^-53, so the row-wise rounding bound of the
+    # FP64 test (1e-13 of |H| |X|, about 900 u64) becomes 900 u = 3.2e-12.
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS, STORE_F64, STORE_F64PAIR, OefeError
+    w = W.config_c1()
+    xb = W.mesh_breakpoints(w)
+    prs, ctx, V, _ = paired(a=w.a, p=w.p, Zs=tuple(w.Z), pos=w.pos, xb=xb, quad=w.quad_params(), r0=w.r0,
+                            rc=w.rc, sigma=w.sigma, ks=[k], store=STORE_F64 | STORE_F64PAIR)
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 13, complex_=pr.complex, seed=22)
+    Xd = to_gpu(X)
+    Yp = torch.empty_like(Xd)
+    Yn = torch.empty_like(Xd)
+    ctx.set_f64_products(F64_PAIRS)
+    ctx.apply_h(0, Xd, Yp)
+    ctx.set_f64_products(F64_NATIVE)
+    ctx.apply_h(0, Xd, Yn)
+    HX = pr.apply_H(X)
+    scale = abs(pr.assemble_H()) @ np.abs(X)
+    err = np.max(np.abs(Yp.cpu().numpy() - HX) / scale)
+    assert err < 3.2e-12
+    # the pair path ran: it differs from FP64 by more than FP64 rounding alone
+    assert np.max(np.abs(Yp.cpu().numpy() - Yn.cpu().numpy()) / scale) > 1e-15
+    with pytest.raises(OefeError):
+        ctx.set_f64_products(7)
+    # an operator without the pair copy refuses pair products
+    ctx.build_hamiltonian(to_gpu(V), STORE_F64)
+    ctx.set_f64_products(F64_PAIRS)
+    with pytest.raises(OefeError):
+        ctx.apply_h(0, Xd, Yp)
+    ctx.set_f64_products(F64_NATIVE)

@@ -2,7 +2,9 @@
 (the first configuration: graded 8^3 mesh, p = 4, two nuclei, 20 vectors,
 degree 20). The GPU path runs the BF16x3 tensor-core degrees with the last
 degree in FP64 and FP64 Cholesky-QR / Rayleigh-Ritz; the oracle runs the
-whole pass in FP64. Target: band energy within 1e-6 Ha per atom."""
+whole pass in FP64. Target: band energy within 1e-6 Ha per atom. The same
+holds with the FP64 products of the last degree and of Rayleigh-Ritz in
+FP32-pair arithmetic on the single-leaf cells."""
 import numpy as np
 import pytest
 import torch
@@ -14,10 +16,16 @@ from oracle import solver
 pytestmark = pytest.mark.gpu
 
 
-def test_mixed_passes_match_fp64_oracle_band_energy():
-    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64, occupations
+@pytest.mark.parametrize("products", ["native", "pairs"])
+def test_mixed_passes_match_fp64_oracle_band_energy(products):
+    from paper_2010_09701_gb300 import (F64_PAIRS, FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X3, STORE_F32,
+                                        STORE_F64, STORE_F64PAIR, occupations)
     w = W.config_c1()
-    prs, ctx, V, Vd = c1_pair()
+    if products == "pairs":
+        prs, ctx, V, Vd = c1_pair(store=STORE_F64 | STORE_F32 | STORE_BF16X3 | STORE_F64PAIR)
+        ctx.set_f64_products(F64_PAIRS)
+    else:
+        prs, ctx, V, Vd = c1_pair()
     pr = prs[0]
     X0 = W.random_vectors(pr.n, 20, seed=w.seed)
     b = solver.lanczos_upper_bound(pr.apply_H, pr.apply_M, pr.apply_Minv, W.random_vectors(pr.n, 1, seed=9)[:, 0], 25)
