@@ -17,7 +17,7 @@
 static void free_all(oefe_ctx* c) {
   for (auto& K : c->kd) {
     dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf); dev_free(K.Hp);
-    dev_free(K.E0);
+    dev_free(K.E0); dev_free(K.NO); dev_free(K.NOp);
   }
   c->kd.clear();
   void* ptrs[] = {c->d_gll, c->d_m, c->d_cell_nodes, c->d_cellbox, c->d_pos, c->d_lm, c->d_R, c->d_dR,

@@ -935,7 +935,7 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
   if (nk < 1 || nk > 4096 || !k || !w) { c->err = "kpoints: need 1 <= nk <= 4096, k, w"; return OEFE_ERR_ARG; }
   for (auto& K : c->kd) {
     dev_free(K.gamma); dev_free(K.Moo); dev_free(K.Mooinv); dev_free(K.H64); dev_free(K.H32); dev_free(K.Hbf); dev_free(K.Hp);
-    dev_free(K.E0);
+    dev_free(K.E0); dev_free(K.NO); dev_free(K.NOp);
   }
   c->kd.assign(nk, KData());
   double* d_gw = nullptr;

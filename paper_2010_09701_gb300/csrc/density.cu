@@ -1,211 +1,420 @@
 // Fields at the quadrature points (Eq. UOEFE, Eq. rho):
 //   u(x_q) = sum_a N^C_a(x_q) (X^c - Gamma_e X^o)_a + sum_j N^A_j(x_q) X^o_j
-// interpolated per tensor-product leaf by sum factorization, then
+//          = sum_a N^C_a(x_q) X^c_a + sum_j N^O_j(x_q) X^o_j,
+//   N^O_j(x_q) = N^A_j(x_q) - sum_a N^C_a(x_q) Gamma_aj   (the orthogonalized enrichment),
+// then
 //   density:          rho_q += sum_v occ_v |u_v(x_q)|^2
 //   band-trace grad:  g_q    = w_q sum_v |u_v(x_q)|^2  (adjoint of H.X w.r.t. V_q).
+// N^O depends on k only: it is tabulated once per k-point (k_orth_enrichment) and kept; the
+// fields then take the CFE part by sum factorization per tensor-product leaf and the enrichment
+// part as a dense product with the table (k_fields), in FP64 or FP32-pair arithmetic.
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "oefe_internal.h"
 #include "enrich_dev.cuh"
+#include "pair_dev.cuh"
 
 namespace {
 
 constexpr int MAXP = 8;
 constexpr int MAXN1 = 12;
 constexpr int DT = 256;
+constexpr int NBO = 4;   // columns of Gamma per pass of the tabulation
+constexpr int RNB = 4;   // vectors per pass of the fields
 
-struct FieldArgs {
+struct OrthArgs {
   EnrParams E;
   const Leaf* leaves;
-  const int* leaf_off;
   const double* qxyz;
-  const double* qw;
   const double* cellbox;
   const double* gll;
-  const int* cell_nodes;
   const int* act_off;
   const int* act_idx;
-  int ncells, nleaves, P, nloc, ne_max, nbd;
-  int64_t nh;
+  int nleaves, P, nloc, ne_max;
   double k[3];
-  const void* X;      // F64 or C128 rows, ld
-  int ld, nv;
   bool cplx;
   const void* gamma;  // (ncells, nloc, ne_max)
-  const double* occ;  // nv weights (density) or null (gradient: weight 1, times w_q)
   cd* na;             // per-CTA scratch: max leaf points * ne_max
   int64_t na_stride;
-  double* out;        // nq
-  bool accumulate;    // density: out += ; gradient: out =
+  void* NO;           // out: scalars
+  float* NOp;         // out: FP32 pairs (or null)
 };
 
-__device__ inline cd ldX(const FieldArgs& A, int64_t row, int v) {
-  if (A.cplx) return reinterpret_cast<const cd*>(A.X)[row * A.ld + v];
-  return mkc(reinterpret_cast<const double*>(A.X)[row * A.ld + v], 0.0);
-}
-__device__ inline cd ldG(const FieldArgs& A, size_t i) {
+__device__ inline cd ldG(const OrthArgs& A, size_t i) {
   if (A.cplx) return reinterpret_cast<const cd*>(A.gamma)[i];
   return mkc(reinterpret_cast<const double*>(A.gamma)[i], 0.0);
 }
 
-__global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
+// N^O at the points of every leaf: the enrichment values (one (point, atom) per thread: the active
+// set holds whole atoms, whose functions share the offset, cutoff and phase) minus the CFE
+// interpolant of Gamma's columns, NBO columns per pass by sum factorization. FP64.
+__global__ void __launch_bounds__(DT) k_orth_enrichment(OrthArgs A) {
   extern __shared__ double smem[];
   __shared__ double Lt[3][MAXN1][MAXP];
   __shared__ double xn[MAXP];
   if (threadIdx.x < A.P) xn[threadIdx.x] = A.gll[threadIdx.x];
-  const int P = A.P, nloc = A.nloc, NB = A.nbd;
+  const int P = A.P, nloc = A.nloc, NB = NBO;
   cd* na = A.na + (size_t)blockIdx.x * A.na_stride;
-  // leaves are independent (each owns its points): balance the work over leaves
   for (int li = blockIdx.x; li < A.nleaves; li += gridDim.x) {
     const Leaf L = A.leaves[li];
     const int e = L.cell;
     const int ne = A.act_off[e + 1] - A.act_off[e];
     const double* box = A.cellbox + 6 * e;
-    {
-      const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
+    const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
+    __syncthreads();
+    if (threadIdx.x < 3 * n1) {
+      const int d = threadIdx.x / n1, i = threadIdx.x % n1;
+      const int64_t qi = L.q0 + (d == 0 ? i : d == 1 ? i * n1 : i * n2);
+      const double xi = 2.0 * (A.qxyz[3 * qi + d] - box[d]) / box[3 + d] - 1.0;
+      double Lv[MAXP], Dv[MAXP];
+      lagrange_eval(xn, P, xi, Lv, Dv);
+      for (int a = 0; a < P; ++a) Lt[d][i][a] = Lv[a];
+    }
+    const int nat = A.E.nfun > 0 ? ne / A.E.nfun : 0;
+    for (int t = threadIdx.x; t < n3 * nat; t += DT) {
+      const int q = t / nat, j0 = (t % nat) * A.E.nfun;
+      const int64_t qg = L.q0 + q;
+      const double x[3] = {A.qxyz[3 * qg], A.qxyz[3 * qg + 1], A.qxyz[3 * qg + 2]};
+      const int I = A.act_idx[A.act_off[e] + j0] / A.E.nfun;
+      AtomGeom G;
+      atom_geom(A.E, I, x, A.k, false, G);
+      for (int f = 0; f < A.E.nfun; ++f) atom_function(A.E, I, f, G, A.k, &na[q * ne + j0 + f], nullptr);
+    }
+    cd* Xt = reinterpret_cast<cd*>(smem);   // nloc * NB: -Gamma[:, v0:v0+NB]
+    cd* T1 = Xt + nloc * NB;                // n1 * P * P * NB   [qx][b][c][v]
+    cd* T2 = T1 + n1 * P * P * NB;          // n2 * P * NB       [qx][qy][c][v]
+    const size_t blk = (size_t)L.q0 * A.ne_max;
+    for (int v0 = 0; v0 < A.ne_max; v0 += NB) {
       __syncthreads();
-      if (threadIdx.x < 3 * n1) {
-        const int d = threadIdx.x / n1, i = threadIdx.x % n1;
-        const int64_t qi = L.q0 + (d == 0 ? i : d == 1 ? i * n1 : i * n2);
-        const double xi = 2.0 * (A.qxyz[3 * qi + d] - box[d]) / box[3 + d] - 1.0;
-        double Lv[MAXP], Dv[MAXP];
-        lagrange_eval(xn, P, xi, Lv, Dv);
-        for (int a = 0; a < P; ++a) Lt[d][i][a] = Lv[a];
+      for (int t = threadIdx.x; t < nloc * NB; t += DT) {
+        const int a = t / NB, u = t % NB;
+        Xt[t] = v0 + u < ne ? -ldG(A, ((size_t)e * nloc + a) * A.ne_max + v0 + u) : mkc(0, 0);
       }
-      // enrichment values of the leaf points, one (point, atom) per thread: the active set holds
-      // whole atoms, whose functions share the offset, cutoff and phase
-      const int nat = A.E.nfun > 0 ? ne / A.E.nfun : 0;
-      for (int t = threadIdx.x; t < n3 * nat; t += DT) {
-        const int q = t / nat, j0 = (t % nat) * A.E.nfun;
-        const int64_t qg = L.q0 + q;
-        const double x[3] = {A.qxyz[3 * qg], A.qxyz[3 * qg + 1], A.qxyz[3 * qg + 2]};
-        const int I = A.act_idx[A.act_off[e] + j0] / A.E.nfun;
-        AtomGeom G;
-        atom_geom(A.E, I, x, A.k, false, G);
-        for (int f = 0; f < A.E.nfun; ++f) atom_function(A.E, I, f, G, A.k, &na[q * ne + j0 + f], nullptr);
+      __syncthreads();
+      for (int t = threadIdx.x; t < n1 * P * P * NB; t += DT) {
+        const int u = t % NB, r = t / NB;
+        const int c = r % P, bb = (r / P) % P, qx = r / (P * P);
+        cd s = mkc(0, 0);
+        for (int a = 0; a < P; ++a) s = rfma(Lt[0][qx][a], Xt[(a + P * (bb + P * c)) * NB + u], s);
+        T1[t] = s;
       }
-      cd* Xt = reinterpret_cast<cd*>(smem);   // nloc * NB
-      cd* Xo = Xt + nloc * NB;                // ne_max * NB
-      cd* T1 = Xo + A.ne_max * NB;            // n1 * P * P * NB   [qx][b][c][v]
-      cd* T2 = T1 + n1 * P * P * NB;          // n2 * P * NB       [qx][qy][c][v]
-      cd* U = T2 + n2 * P * NB;               // n3 * NB
-      double* rho = reinterpret_cast<double*>(U + n3 * NB);  // n3
-      for (int q = threadIdx.x; q < n3; q += DT) rho[q] = 0.0;
-      for (int v0 = 0; v0 < A.nv; v0 += NB) {
-        const int nb = min(NB, A.nv - v0);
-        __syncthreads();
-        for (int t = threadIdx.x; t < ne * NB; t += DT) {
-          const int j = t / NB, u = t % NB;
-          Xo[t] = u < nb ? ldX(A, A.nh + A.act_idx[A.act_off[e] + j], v0 + u) : mkc(0, 0);
-        }
-        __syncthreads();
-        for (int t = threadIdx.x; t < nloc * NB; t += DT) {
-          const int a = t / NB, u = t % NB;
-          cd s = mkc(0, 0);
-          if (u < nb) {
-            s = ldX(A, A.cell_nodes[(size_t)e * nloc + a], v0 + u);
-            for (int j = 0; j < ne; ++j) s = cfma(-ldG(A, ((size_t)e * nloc + a) * A.ne_max + j), Xo[j * NB + u], s);
+      __syncthreads();
+      for (int t = threadIdx.x; t < n2 * P * NB; t += DT) {
+        const int u = t % NB, r = t / NB;
+        const int c = r % P, qy = (r / P) % n1, qx = r / (P * n1);
+        cd s = mkc(0, 0);
+        for (int bb = 0; bb < P; ++bb) s = rfma(Lt[1][qy][bb], T1[((qx * P + bb) * P + c) * NB + u], s);
+        T2[t] = s;
+      }
+      __syncthreads();
+      // z stage plus the enrichment value; column-major store (point fastest)
+      for (int t = threadIdx.x; t < n3 * NB; t += DT) {
+        const int q = t % n3, u = t / n3;
+        const int qx = q % n1, qy = (q / n1) % n1, qz = q / n2;
+        if (v0 + u >= A.ne_max) continue;
+        cd s = v0 + u < ne ? na[q * ne + v0 + u] : mkc(0, 0);
+        for (int c = 0; c < P; ++c) s = rfma(Lt[2][qz][c], T2[((qx * n1 + qy) * P + c) * NB + u], s);
+        const size_t o = blk + (size_t)(v0 + u) * n3 + q;
+        if (A.cplx) {
+          reinterpret_cast<cd*>(A.NO)[o] = s;
+          if (A.NOp) {
+            const float rh = __double2float_rn(s.x), ih = __double2float_rn(s.y);
+            reinterpret_cast<float4*>(A.NOp)[o] =
+                make_float4(rh, __double2float_rn(s.x - (double)rh), ih, __double2float_rn(s.y - (double)ih));
           }
-          Xt[t] = s;
+        } else {
+          reinterpret_cast<double*>(A.NO)[o] = s.x;
+          if (A.NOp) {
+            const float h = __double2float_rn(s.x);
+            reinterpret_cast<float2*>(A.NOp)[o] = make_float2(h, __double2float_rn(s.x - (double)h));
+          }
         }
-        __syncthreads();
-        // x stage: T1[qx][b][c][v] = sum_a Lx[qx][a] Xt[a + P(b + P c)][v]
-        for (int t = threadIdx.x; t < n1 * P * P * NB; t += DT) {
-          const int u = t % NB, r = t / NB;
-          const int c = r % P, bb = (r / P) % P, qx = r / (P * P);
-          cd s = mkc(0, 0);
-          for (int a = 0; a < P; ++a) s = rfma(Lt[0][qx][a], Xt[(a + P * (bb + P * c)) * NB + u], s);
-          T1[t] = s;
-        }
-        __syncthreads();
-        // y stage: T2[qx][qy][c][v] = sum_b Ly[qy][b] T1[qx][b][c][v]
-        for (int t = threadIdx.x; t < n2 * P * NB; t += DT) {
-          const int u = t % NB, r = t / NB;
-          const int c = r % P, qy = (r / P) % n1, qx = r / (P * n1);
-          cd s = mkc(0, 0);
-          for (int bb = 0; bb < P; ++bb) s = rfma(Lt[1][qy][bb], T1[((qx * P + bb) * P + c) * NB + u], s);
-          T2[t] = s;
-        }
-        __syncthreads();
-        // z stage and the enrichment part: U[q][v], q = qx + n1 (qy + n1 qz)
-        for (int t = threadIdx.x; t < n3 * NB; t += DT) {
-          const int u = t % NB, q = t / NB;
-          const int qx = q % n1, qy = (q / n1) % n1, qz = q / n2;
-          cd s = mkc(0, 0);
-          for (int c = 0; c < P; ++c) s = rfma(Lt[2][qz][c], T2[((qx * n1 + qy) * P + c) * NB + u], s);
-          for (int j = 0; j < ne; ++j) s = cfma(na[q * ne + j], Xo[j * NB + u], s);
-          U[t] = s;
-        }
-        __syncthreads();
-        for (int q = threadIdx.x; q < n3; q += DT) {
-          double s = 0;
-          for (int u = 0; u < nb; ++u) s += (A.occ ? A.occ[v0 + u] : 1.0) * cabs2(U[q * NB + u]);
-          rho[q] += s;
-        }
-      }
-      __syncthreads();
-      for (int q = threadIdx.x; q < n3; q += DT) {
-        const int64_t qg = L.q0 + q;
-        if (A.accumulate) A.out[qg] += rho[q];
-        else A.out[qg] = A.qw[qg] * rho[q];
       }
     }
   }
 }
 
-size_t field_smem(const oefe_ctx* c, int nb) {
+size_t orth_smem(const oefe_ctx* c) {
   const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
-  const size_t n3 = (size_t)n1 * n1 * n1;
-  return ((size_t)c->nloc * nb + (size_t)std::max(c->ne_max, 1) * nb + (size_t)n1 * P * P * nb +
-          (size_t)n1 * n1 * P * nb + n3 * nb) * sizeof(cd) + n3 * sizeof(double);
+  return ((size_t)c->nloc * NBO + (size_t)n1 * P * P * NBO + (size_t)n1 * n1 * P * NBO) * sizeof(cd);
 }
 
-int run_fields(oefe_ctx* c, const KData& K, int kidx, const void* X, int nv, int ld, int dtype, const double* occ,
-               double* out, bool accumulate) {
-  int nb = 8;
-  while (nb > 1 && field_smem(c, nb) > 200 * 1024) nb /= 2;
-  const size_t smem = field_smem(c, nb);
+struct FieldArgs {
+  const Leaf* leaves;
+  const double* qxyz;
+  const double* cellbox;
+  const double* gll;
+  const int* cell_nodes;
+  const int* act_off;
+  const int* act_idx;
+  int nleaves, P, nloc, ne_max, n1max;
+  int64_t nh;
+  const void* X;      // F64 or C128 rows, ld
+  int ld, nv;
+  const void* NO;     // N^O: scalars (V = double) or FP32 pairs (V = f2)
+  const double* occ;  // nv weights (density) or null (gradient: weight 1, times w_q)
+  const double* qw;
+  double* out;        // nq
+  bool accumulate;    // density: out += ; gradient: out =
+};
+
+// u_v(x_q) for RNB vectors per pass: CFE part by sum factorization (x, y, z stages over the leaf's
+// Gauss points), enrichment part sum_j N^O_j(x_q) X^o_j with one point per thread over all RNB
+// vectors; |u|^2 weighted by occ accumulated per point. V = double: FP64; V = f2: FP32 pairs.
+template <typename V, bool CPLX>
+__global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
+  constexpr int R = CPLX ? 2 : 1;
+  constexpr int J = RNB * R;
+  using Acc = typename AccOf<V>::type;
+  extern __shared__ double smem_raw[];
+  __shared__ V Lt[3][MAXN1][MAXP];
+  __shared__ double xn[MAXP];
+  if (threadIdx.x < A.P) xn[threadIdx.x] = A.gll[threadIdx.x];
+  const int P = A.P, nloc = A.nloc, n1m = A.n1max;
+  V* Xt = reinterpret_cast<V*>(smem_raw);          // nloc * J
+  V* Xo = Xt + (size_t)nloc * J;                   // ne_max * J
+  V* T1 = Xo + (size_t)A.ne_max * J;               // n1 * P * P * J   [qx][b][c][j]
+  V* T2 = T1 + (size_t)n1m * P * P * J;            // n2 * P * J       [qx][qy][c][j]
+  V* U = T2 + (size_t)n1m * n1m * P * J;           // n3 * J
+  V* rho = U + (size_t)n1m * n1m * n1m * J;        // n3
+  for (int li = blockIdx.x; li < A.nleaves; li += gridDim.x) {
+    const Leaf L = A.leaves[li];
+    const int e = L.cell;
+    const int ne = A.act_off[e + 1] - A.act_off[e];
+    const double* box = A.cellbox + 6 * e;
+    const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
+    __syncthreads();
+    if (threadIdx.x < 3 * n1) {
+      const int d = threadIdx.x / n1, i = threadIdx.x % n1;
+      const int64_t qi = L.q0 + (d == 0 ? i : d == 1 ? i * n1 : i * n2);
+      const double xi = 2.0 * (A.qxyz[3 * qi + d] - box[d]) / box[3 + d] - 1.0;
+      double Lv[MAXP], Dv[MAXP];
+      lagrange_eval(xn, P, xi, Lv, Dv);
+      for (int a = 0; a < P; ++a) Lt[d][i][a] = v_from<V>(Lv[a]);
+    }
+    for (int q = threadIdx.x; q < n3; q += DT) rho[q] = v_from<V>(0.0);
+    const size_t blk = (size_t)L.q0 * A.ne_max;
+    for (int v0 = 0; v0 < A.nv; v0 += RNB) {
+      __syncthreads();
+      for (int t = threadIdx.x; t < ne * RNB; t += DT) {
+        const int j = t / RNB, u = t % RNB;
+        double xr = 0.0, xi = 0.0;
+        if (v0 + u < A.nv) {
+          const int64_t row = A.nh + A.act_idx[A.act_off[e] + j];
+          if (CPLX) {
+            const cd x = reinterpret_cast<const cd*>(A.X)[row * A.ld + v0 + u];
+            xr = x.x;
+            xi = x.y;
+          } else {
+            xr = reinterpret_cast<const double*>(A.X)[row * A.ld + v0 + u];
+          }
+        }
+        Xo[(size_t)j * J + u * R] = v_from<V>(xr);
+        if (CPLX) Xo[(size_t)j * J + u * R + 1] = v_from<V>(xi);
+      }
+      for (int t = threadIdx.x; t < nloc * RNB; t += DT) {
+        const int a = t / RNB, u = t % RNB;
+        double xr = 0.0, xi = 0.0;
+        if (v0 + u < A.nv) {
+          const int64_t row = A.cell_nodes[(size_t)e * nloc + a];
+          if (CPLX) {
+            const cd x = reinterpret_cast<const cd*>(A.X)[row * A.ld + v0 + u];
+            xr = x.x;
+            xi = x.y;
+          } else {
+            xr = reinterpret_cast<const double*>(A.X)[row * A.ld + v0 + u];
+          }
+        }
+        Xt[(size_t)a * J + u * R] = v_from<V>(xr);
+        if (CPLX) Xt[(size_t)a * J + u * R + 1] = v_from<V>(xi);
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < n1 * P * P * J; t += DT) {   // x stage
+        const int j = t % J, r = t / J;
+        const int c = r % P, bb = (r / P) % P, qx = r / (P * P);
+        T1[t] = v_dot<V>(P, [&](int a) { return Lt[0][qx][a]; },
+                         [&](int a) { return Xt[(size_t)(a + P * (bb + P * c)) * J + j]; });
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < n2 * P * J; t += DT) {       // y stage
+        const int j = t % J, r = t / J;
+        const int c = r % P, qy = (r / P) % n1, qx = r / (P * n1);
+        T2[t] = v_dot<V>(P, [&](int bb) { return Lt[1][qy][bb]; },
+                         [&](int bb) { return T1[(size_t)((qx * P + bb) * P + c) * J + j]; });
+      }
+      __syncthreads();
+      for (int t = threadIdx.x; t < n3 * J; t += DT) {           // z stage
+        const int j = t % J, q = t / J;
+        const int qx = q % n1, qy = (q / n1) % n1, qz = q / n2;
+        U[t] = v_dot<V>(P, [&](int c) { return Lt[2][qz][c]; },
+                        [&](int c) { return T2[(size_t)((qx * n1 + qy) * P + c) * J + j]; });
+      }
+      __syncthreads();
+      // enrichment part and |u|^2: one point per thread, all RNB vectors
+      for (int q = threadIdx.x; q < n3; q += DT) {
+        Acc y[J];
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+          if constexpr (std::is_same<V, double>::value) y[j] = U[(size_t)q * J + j];
+          else y[j] = Acc{U[(size_t)q * J + j].h, U[(size_t)q * J + j].l};
+        }
+        for (int jj = 0; jj < ne; ++jj) {
+          const size_t o = blk + (size_t)jj * n3 + q;
+          const V* x = Xo + (size_t)jj * J;
+          if constexpr (CPLX) {
+            V nr, ni;
+            if constexpr (std::is_same<V, double>::value) {
+              const cd w = reinterpret_cast<const cd*>(A.NO)[o];
+              nr = w.x;
+              ni = w.y;
+            } else {
+              const float4 w = reinterpret_cast<const float4*>(A.NO)[o];
+              nr = V{w.x, w.y};
+              ni = V{w.z, w.w};
+            }
+            const V nni = v_neg(ni);
+#pragma unroll
+            for (int u = 0; u < RNB; ++u) {
+              v_mac(y[2 * u], nr, x[2 * u]);
+              v_mac(y[2 * u + 1], nr, x[2 * u + 1]);
+              v_mac(y[2 * u], nni, x[2 * u + 1]);
+              v_mac(y[2 * u + 1], ni, x[2 * u]);
+            }
+          } else {
+            V nr;
+            if constexpr (std::is_same<V, double>::value) {
+              nr = reinterpret_cast<const double*>(A.NO)[o];
+            } else {
+              const float2 w = reinterpret_cast<const float2*>(A.NO)[o];
+              nr = V{w.x, w.y};
+            }
+#pragma unroll
+            for (int u = 0; u < RNB; ++u) v_mac(y[u], nr, x[u]);
+          }
+        }
+        V s = rho[q];
+#pragma unroll
+        for (int u = 0; u < RNB; ++u) {
+          if (v0 + u >= A.nv) continue;
+          Acc m = v_zero<V>();
+          const V yr = v_fin(y[u * R]);
+          v_mac(m, yr, yr);
+          if constexpr (CPLX) {
+            const V yi = v_fin(y[u * R + 1]);
+            v_mac(m, yi, yi);
+          }
+          const V w = v_from<V>(A.occ ? A.occ[v0 + u] : 1.0);
+          s = v_add(s, v_mul(w, v_fin(m)));
+        }
+        rho[q] = s;
+      }
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < n3; q += DT) {
+      const int64_t qg = L.q0 + q;
+      if (A.accumulate) A.out[qg] += v_to(rho[q]);
+      else A.out[qg] = A.qw[qg] * v_to(rho[q]);
+    }
+  }
+}
+
+template <typename V>
+size_t field_smem(const oefe_ctx* c, bool cplx) {
+  const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
+  const size_t J = (size_t)RNB * (cplx ? 2 : 1);
+  const size_t n3 = (size_t)n1 * n1 * n1;
+  return ((size_t)c->nloc * J + (size_t)std::max(c->ne_max, 1) * J + (size_t)n1 * P * P * J +
+          (size_t)n1 * n1 * P * J + n3 * J + n3) * sizeof(V);
+}
+
+}  // namespace
+
+// N^O of k-point K (and its FP32-pair copy when the context runs pair products), once per k
+int ensure_orth_enrichment(oefe_ctx* c, KData& K) {
+  const bool pairs = c->f64_products == OEFE_F64_PAIRS;
+  if (K.NO && (K.NOp || !pairs)) return OEFE_OK;
+  const int nem = std::max(c->ne_max, 1);
+  const size_t n = (size_t)c->nq * nem;
+  const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);
+  if (!K.NO) OEFE_TRY(dev_alloc(c, &K.NO, n * sb));
+  if (pairs && !K.NOp) OEFE_TRY(dev_alloc(c, (void**)&K.NOp, n * sb));
+  const size_t smem = orth_smem(c);
   if (smem > 220 * 1024) { c->err = "fields: quadrature too large for the interpolation tiles"; return OEFE_ERR_ARG; }
   const int grid = std::max(1, std::min((int)c->leaves.size(), 2 * c->num_sms));
   const int n1 = std::max(c->nq_cell, c->nq_enr);
-  const int64_t stride = (int64_t)n1 * n1 * n1 * std::max(c->ne_max, 1);
+  const int64_t stride = (int64_t)n1 * n1 * n1 * nem;
   OEFE_TRY(ensure_ws2(c, (size_t)grid * stride * sizeof(cd) + 256));
-  FieldArgs A;
+  OrthArgs A;
   A.E.pos = c->d_pos; A.E.lm = c->d_lm; A.E.R = c->d_R; A.E.dR = c->d_dR;
   A.E.nfun = c->nfun; A.E.ngrid = c->ngrid; A.E.a = c->a; A.E.r0 = c->r0; A.E.rc = c->rc;
   A.leaves = c->d_leaves;
-  A.leaf_off = c->d_leaf_off;
   A.qxyz = c->d_qxyz;
-  A.qw = c->d_qw;
+  A.cellbox = c->d_cellbox;
+  A.gll = c->d_gll;
+  A.act_off = c->d_act_off;
+  A.act_idx = c->d_act_idx;
+  A.nleaves = (int)c->leaves.size();
+  A.P = c->P;
+  A.nloc = c->nloc;
+  A.ne_max = nem;
+  for (int d = 0; d < 3; ++d) A.k[d] = K.k[d];
+  A.cplx = K.cplx;
+  A.gamma = K.gamma;
+  A.na = (cd*)c->ws2;
+  A.na_stride = stride;
+  A.NO = K.NO;
+  A.NOp = pairs ? K.NOp : nullptr;
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_orth_enrichment, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  OEFE_COUNTED k_orth_enrichment<<<grid, DT, smem, c->stream>>>(A);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  return OEFE_OK;
+}
+
+namespace {
+
+int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, const double* occ, double* out,
+               bool accumulate) {
+  OEFE_TRY(ensure_orth_enrichment(c, K));
+  const bool pairs = c->f64_products == OEFE_F64_PAIRS;
+  const bool cplx = dtype == OEFE_C128;
+  FieldArgs A;
+  A.leaves = c->d_leaves;
+  A.qxyz = c->d_qxyz;
   A.cellbox = c->d_cellbox;
   A.gll = c->d_gll;
   A.cell_nodes = c->d_cell_nodes;
   A.act_off = c->d_act_off;
   A.act_idx = c->d_act_idx;
-  A.ncells = c->ncells;
   A.nleaves = (int)c->leaves.size();
   A.P = c->P;
   A.nloc = c->nloc;
   A.ne_max = std::max(c->ne_max, 1);
-  A.nbd = nb;
+  A.n1max = std::max(c->nq_cell, c->nq_enr);
   A.nh = c->nh;
-  for (int d = 0; d < 3; ++d) A.k[d] = K.k[d];
   A.X = X;
   A.ld = ld;
   A.nv = nv;
-  A.cplx = dtype == OEFE_C128;
-  A.gamma = K.gamma;
+  A.NO = pairs ? (const void*)K.NOp : (const void*)K.NO;
   A.occ = occ;
-  A.na = (cd*)c->ws2;
-  A.na_stride = stride;
+  A.qw = c->d_qw;
   A.out = out;
   A.accumulate = accumulate;
-  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_fields, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  OEFE_COUNTED k_fields<<<grid, DT, smem, c->stream>>>(A);
-  OEFE_CUDA_TRY(c, cudaGetLastError());
-  (void)kidx;
-  return OEFE_OK;
+  const int grid = std::max(1, std::min((int)c->leaves.size(), c->num_sms));
+  auto go = [&](auto kern, size_t smem) -> int {
+    if (smem > 227 * 1024) { c->err = "fields: quadrature too large for the interpolation tiles"; return OEFE_ERR_ARG; }
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    OEFE_COUNTED kern<<<grid, DT, smem, c->stream>>>(A);
+    OEFE_CUDA_TRY(c, cudaGetLastError());
+    return OEFE_OK;
+  };
+  if (pairs) {
+    if (cplx) return go(k_fields<f2, true>, field_smem<f2>(c, true));
+    return go(k_fields<f2, false>, field_smem<f2>(c, false));
+  }
+  if (cplx) return go(k_fields<double, true>, field_smem<double>(c, true));
+  return go(k_fields<double, false>, field_smem<double>(c, false));
 }
 
 int check_fields(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
@@ -239,7 +448,7 @@ int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int*
   int off = 0, st = OEFE_OK;
   for (int ik = 0; ik < nk && st == OEFE_OK; ++ik) {
     const int dt = c->kd[ik].cplx ? OEFE_C128 : OEFE_F64;
-    st = run_fields(c, c->kd[ik], ik, X[ik], nv[ik], ld[ik], dt, d_occ + off, rho, true);
+    st = run_fields(c, c->kd[ik], X[ik], nv[ik], ld[ik], dt, d_occ + off, rho, true);
     off += nv[ik];
   }
   cudaStreamSynchronize(c->stream);
@@ -250,7 +459,7 @@ int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int*
 int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* gV) {
   OEFE_TRY(check_fields(c, ik, X, nv, ld, dtype));
   if (!gV) { c->err = "need gV"; return OEFE_ERR_ARG; }
-  OEFE_TRY(run_fields(c, c->kd[ik], ik, X, nv, ld, dtype, nullptr, gV, false));
+  OEFE_TRY(run_fields(c, c->kd[ik], X, nv, ld, dtype, nullptr, gV, false));
   OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return OEFE_OK;
 }

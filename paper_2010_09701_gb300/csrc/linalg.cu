@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "oefe_internal.h"
+#include "pair_dev.cuh"
 
 namespace {
 
@@ -209,6 +210,116 @@ __global__ void k_rotate(S* X, int ldx, int64_t n, int nv, const S* C, bool herm
   }
 }
 
+// ---- the same two kernels in FP32-pair arithmetic (pair_dev.cuh); storage stays FP64
+struct c2 {
+  f2 r, i;
+};
+__device__ __forceinline__ c2 to_c2(double a) { return c2{f2_from(a), f2{0.0f, 0.0f}}; }
+__device__ __forceinline__ c2 to_c2(cd a) { return c2{f2_from(a.x), f2_from(a.y)}; }
+template <typename S>
+__device__ __forceinline__ S from_acc(f2acc r, f2acc i);
+template <>
+__device__ __forceinline__ double from_acc<double>(f2acc r, f2acc) { return f2_to(f2_fin(r)); }
+template <>
+__device__ __forceinline__ cd from_acc<cd>(f2acc r, f2acc i) { return mkc(f2_to(f2_fin(r)), f2_to(f2_fin(i))); }
+
+// Partial Gram matrices as k_gram, in pairs: acc += conj(x) w
+template <typename S>
+__global__ void __launch_bounds__(256) k_gram_pair(const S* X, int ldx, const S* W, int ldw, int64_t n, int nv,
+                                                   int64_t rows_per_chunk, S* part, bool herm, int tiles) {
+  constexpr bool CPLX = sizeof(S) == sizeof(cd);
+  __shared__ c2 xs[GR][GT];
+  __shared__ c2 ws[GR][GT];
+  int ti = blockIdx.y, tj = blockIdx.z;
+  if (herm) {
+    int y = blockIdx.y;
+    ti = 0;
+    while (y >= tiles - ti) { y -= tiles - ti; ++ti; }
+    tj = ti + y;
+  }
+  const int64_t r0 = blockIdx.x * rows_per_chunk, r1 = min(n, r0 + rows_per_chunk);
+  const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;
+  f2acc ar[2][2], ai[2][2];
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) ar[a][b] = ai[a][b] = f2acc{0.0f, 0.0f};
+  for (int64_t rb = r0; rb < r1; rb += GR) {
+    for (int t = threadIdx.x; t < GR * GT; t += 256) {
+      const int rr = t / GT, cc = t % GT;
+      const int64_t r = rb + rr;
+      const int ci = ti * GT + cc, cj = tj * GT + cc;
+      xs[rr][cc] = (r < r1 && ci < nv) ? to_c2(X[r * ldx + ci]) : to_c2(Ops<S>::zero());
+      ws[rr][cc] = (r < r1 && cj < nv) ? to_c2(W[r * ldw + cj]) : to_c2(Ops<S>::zero());
+    }
+    __syncthreads();
+    for (int rr = 0; rr < GR; ++rr) {
+      const c2 x[2] = {xs[rr][2 * ty], xs[rr][2 * ty + 1]};
+      const c2 w[2] = {ws[rr][2 * tx], ws[rr][2 * tx + 1]};
+#pragma unroll
+      for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          f2_mac(ar[a][b], x[a].r, w[b].r);
+          if (CPLX) {
+            f2_mac(ar[a][b], x[a].i, w[b].i);
+            f2_mac(ai[a][b], x[a].r, w[b].i);
+            f2_mac(ai[a][b], f2_neg(x[a].i), w[b].r);
+          }
+        }
+    }
+    __syncthreads();
+  }
+  for (int a = 0; a < 2; ++a)
+    for (int b = 0; b < 2; ++b) {
+      const int i = ti * GT + 2 * ty + a, j = tj * GT + 2 * tx + b;
+      if (i < nv && j < nv) part[((size_t)blockIdx.x * nv + i) * nv + j] = from_acc<S>(ar[a][b], ai[a][b]);
+    }
+}
+
+// X[rows] <- X[rows] C (or X C^+ with herm, C lower triangular) in pairs: C transposed into shared
+// memory once per CTA (Ct[k][j], consecutive j contiguous), rows staged, each thread one column j
+// of two rows.
+constexpr int RPT = 512;
+template <typename S>
+__global__ void __launch_bounds__(RPT) k_rotate_pair(S* X, int ldx, int64_t n, int nv, const S* C, bool herm,
+                                                     int rows) {
+  constexpr bool CPLX = sizeof(S) == sizeof(cd);
+  extern __shared__ unsigned char sm[];
+  c2* Ct = reinterpret_cast<c2*>(sm);            // nv * nv
+  c2* xs = Ct + (size_t)nv * nv;                 // rows * nv
+  for (int t = threadIdx.x; t < nv * nv; t += RPT) {
+    const int k = t / nv, j = t % nv;
+    Ct[t] = herm ? (k <= j ? to_c2(Ops<S>::conj(C[(size_t)j * nv + k])) : to_c2(Ops<S>::zero()))
+                 : to_c2(C[(size_t)k * nv + j]);
+  }
+  const int64_t r0 = (int64_t)blockIdx.x * rows;
+  const int nr = (int)min((int64_t)rows, n - r0);
+  if (nr <= 0) return;
+  for (int t = threadIdx.x; t < nr * nv; t += RPT) xs[t] = to_c2(X[(r0 + t / nv) * ldx + t % nv]);
+  __syncthreads();
+  const int npair = (nr + 1) / 2;
+  for (int t = threadIdx.x; t < npair * nv; t += RPT) {
+    const int rp = t / nv, j = t % nv;
+    const int ra = 2 * rp, rb = min(2 * rp + 1, nr - 1);
+    f2acc sr[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}}, si[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    const int kend = herm ? j + 1 : nv;
+    for (int k = 0; k < kend; ++k) {
+      const c2 cc = Ct[(size_t)k * nv + j];
+      const c2 x[2] = {xs[(size_t)ra * nv + k], xs[(size_t)rb * nv + k]};
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        f2_mac(sr[u], x[u].r, cc.r);
+        if (CPLX) {
+          f2_mac(sr[u], f2_neg(x[u].i), cc.i);
+          f2_mac(si[u], x[u].r, cc.i);
+          f2_mac(si[u], x[u].i, cc.r);
+        }
+      }
+    }
+    X[(r0 + ra) * ldx + j] = from_acc<S>(sr[0], si[0]);
+    if (rb != ra) X[(r0 + rb) * ldx + j] = from_acc<S>(sr[1], si[1]);
+  }
+}
+
 // Column norms for residuals: out[v] = sum_rows conj(R) M^{-1} R, with the
 // lumped block divided by m and the enrichment block through (M^oo)^{-1}.
 template <typename S>
@@ -324,7 +435,10 @@ int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int n
   const int tiles = (nv + GT - 1) / GT;
   const int64_t rpc = (n + nchunk - 1) / nchunk;
   dim3 grid(nchunk, herm ? tiles * (tiles + 1) / 2 : tiles, herm ? 1 : tiles);
-  OEFE_COUNTED k_gram<S><<<grid, 256, 0, c->stream>>>(X, ldx, W, ldw, n, nv, rpc, part_buf, herm, tiles);
+  if (c->f64_products == OEFE_F64_PAIRS)
+    OEFE_COUNTED k_gram_pair<S><<<grid, 256, 0, c->stream>>>(X, ldx, W, ldw, n, nv, rpc, part_buf, herm, tiles);
+  else
+    OEFE_COUNTED k_gram<S><<<grid, 256, 0, c->stream>>>(X, ldx, W, ldw, n, nv, rpc, part_buf, herm, tiles);
   OEFE_COUNTED k_sum_parts<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(part_buf, nchunk, nv, out, herm);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
@@ -332,6 +446,19 @@ int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int n
 
 template <typename S>
 int rotate(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm) {
+  if (c->f64_products == OEFE_F64_PAIRS) {
+    // pairs: C (transposed) and the staged rows in shared memory, when C leaves room for 32 rows
+    const size_t cb = (size_t)nv * nv * sizeof(c2);
+    const int prow = (int)std::min<int64_t>(256, ((size_t)200 * 1024 - std::min<size_t>(cb, 200 * 1024)) / ((size_t)nv * sizeof(c2)));
+    if (cb < 200 * 1024 && prow >= 32) {
+      const int64_t blocks = (n + prow - 1) / prow;
+      const size_t smem = cb + (size_t)prow * nv * sizeof(c2);
+      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_rotate_pair<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      OEFE_COUNTED k_rotate_pair<S><<<(unsigned)blocks, RPT, smem, c->stream>>>(X, ldx, n, nv, C, herm, prow);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+      return OEFE_OK;
+    }
+  }
   const int rows = std::max(1, (int)((96 * 1024) / ((size_t)nv * sizeof(S))));
   const int64_t blocks = (n + rows - 1) / rows;
   const size_t smem = (size_t)rows * nv * sizeof(S);

@@ -78,6 +78,11 @@ struct KData {
   void* Hbf = nullptr;       // bf16 planes (re parts[, im parts]), per cell [K tile][M tile][plane][128][64]
   int bf_parts = 0;          // bf16 parts per real plane in Hbf: 2 (hi, lo) or 3 (hi, mid, lo)
   void* E0 = nullptr;        // per cell: V-independent enrichment blocks (cd), CA then AA
+  // orthogonalized enrichment functions at the quadrature points, N^O_j(x_q) = N^A_j(x_q) -
+  // sum_a N_a(x_q) Gamma_aj: per leaf a column-major block (ne_max columns of its points) at
+  // offset q0 * ne_max; scalars (double or cd), and the same as FP32 pairs (float2 / float4)
+  void* NO = nullptr;
+  float* NOp = nullptr;
   bool built = false;
 };
 
@@ -214,6 +219,7 @@ void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w);
 
 // build (build.cu)
 int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w);
+int ensure_orth_enrichment(oefe_ctx* c, KData& K);
 int build_hamiltonian(oefe_ctx* c, const double* veff, int store);
 
 // dense helpers (linalg.cu)

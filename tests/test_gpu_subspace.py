@@ -14,21 +14,36 @@ pytestmark = pytest.mark.gpu
 KS = [(0.0, 0.0, 0.0), (0.25, -0.4, 0.1)]
 
 
+def _products(ctx, products):
+    # FP32-pair arithmetic rounds at u = 2^-48, 2^5 times the FP64 unit: the FP64 tolerances scale
+    # by 32
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS
+    ctx.set_f64_products(F64_PAIRS if products == "pairs" else F64_NATIVE)
+    return 32.0 if products == "pairs" else 1.0
+
+
+def _store(products):
+    from paper_2010_09701_gb300 import STORE_BF16X3, STORE_F32, STORE_F64, STORE_F64PAIR
+    return STORE_F64 | STORE_F32 | STORE_BF16X3 | (STORE_F64PAIR if products == "pairs" else 0)
+
+
+@pytest.mark.parametrize("products", ["native", "pairs"])
 @pytest.mark.parametrize("k", KS)
-def test_orthonormalize(k):
-    prs, ctx, V, _ = paired(ks=[k])
+def test_orthonormalize(k, products):
+    prs, ctx, V, _ = paired(ks=[k], store=_store(products))
+    f = _products(ctx, products)
     pr = prs[0]
     Y = W.random_vectors(pr.n, 10, complex_=pr.complex, seed=5)
     Yd = to_gpu(Y)
     ctx.orthonormalize(0, Yd)
     Q = Yd.cpu().numpy()
-    assert np.allclose(Q.conj().T @ pr.apply_M(Q), np.eye(10), atol=1e-12)
+    assert np.allclose(Q.conj().T @ pr.apply_M(Q), np.eye(10), atol=1e-12 * f)
     Qo = solver.cholqr(Y, pr.apply_M)
     # same span: Q = Qo U with U unitary -> Qo^+ M Q unitary
     U = Qo.conj().T @ pr.apply_M(Q)
-    assert np.allclose(U.conj().T @ U, np.eye(10), atol=1e-11)
+    assert np.allclose(U.conj().T @ U, np.eye(10), atol=1e-11 * f)
     # CholQR is deterministic: the factors agree too
-    assert rel(Q, Qo) < 1e-10
+    assert rel(Q, Qo) < 1e-10 * f
 
 
 def test_orthonormalize_rank_deficient_reports_cholesky():
@@ -42,21 +57,23 @@ def test_orthonormalize_rank_deficient_reports_cholesky():
     assert e.value.code == binding.ERR_CHOLESKY
 
 
+@pytest.mark.parametrize("products", ["native", "pairs"])
 @pytest.mark.parametrize("k", KS)
-def test_rayleigh_ritz(k):
-    prs, ctx, V, _ = paired(ks=[k])
+def test_rayleigh_ritz(k, products):
+    prs, ctx, V, _ = paired(ks=[k], store=_store(products))
+    f = _products(ctx, products)
     pr = prs[0]
     Q = solver.cholqr(W.random_vectors(pr.n, 9, complex_=pr.complex, seed=6), pr.apply_M)
     eps_o, X_o = solver.rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
     Qd = to_gpu(Q)
     eps, res = ctx.rayleigh_ritz(0, Qd, resid=True)
-    assert np.max(np.abs(eps - eps_o)) < 1e-10 * max(1, np.max(np.abs(eps_o)))
+    assert np.max(np.abs(eps - eps_o)) < 1e-10 * f * max(1, np.max(np.abs(eps_o)))
     res_o = solver.residual_norms(pr, X_o, eps_o)
-    assert np.allclose(res, res_o, rtol=1e-8, atol=1e-12)
+    assert np.allclose(res, res_o, rtol=1e-8 * f, atol=1e-12 * f)
     # rotated vectors: unique up to a phase per (non-degenerate) column
     X = Qd.cpu().numpy()
     ph = np.sum(np.conj(X_o) * pr.apply_M(X), axis=0)
-    assert np.allclose(np.abs(ph), 1.0, atol=1e-9)
+    assert np.allclose(np.abs(ph), 1.0, atol=1e-9 * f)
 
 
 @pytest.mark.parametrize("k", KS)
@@ -73,6 +90,30 @@ def test_density_and_band_trace_grad(k):
     g = torch.zeros_like(rho)
     ctx.band_trace_grad(0, to_gpu(X), g)
     assert rel(g.cpu().numpy(), g_o) < 1e-12
+
+
+@pytest.mark.parametrize("k", KS)
+def test_density_and_band_trace_grad_fp32_pairs(k):
+    # the fields in FP32-pair arithmetic: each operation rounds at about u = 2^-48, so the FP64
+    # bound of 1e-12 (about 9000 u64) becomes 3.2e-12 (900 u)
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS
+    prs, ctx, V, Vd = paired(ks=[k])
+    pr = prs[0]
+    X = W.random_vectors(pr.n, 6, complex_=pr.complex, seed=18)
+    occ = np.array([2.0, 2.0, 1.5, 1.0, 0.2, 0.0])
+    rho_o = solver.density([pr], [X], [occ])
+    ctx.set_f64_products(F64_PAIRS)
+    rho = torch.zeros(pr.quad.nq, dtype=torch.float64, device="cuda")
+    ctx.density([to_gpu(X)], [occ], rho)
+    assert rel(rho.cpu().numpy(), rho_o) < 3.2e-12
+    g_o = solver.band_trace_grad_V(pr, X)
+    g = torch.zeros_like(rho)
+    ctx.band_trace_grad(0, to_gpu(X), g)
+    assert rel(g.cpu().numpy(), g_o) < 3.2e-12
+    ctx.set_f64_products(F64_NATIVE)
+    g2 = torch.zeros_like(rho)
+    ctx.band_trace_grad(0, to_gpu(X), g2)
+    assert rel(g2.cpu().numpy(), g_o) < 1e-12
 
 
 def test_density_two_kpoints():
