@@ -83,9 +83,16 @@ struct BuildArgs {
   const int64_t* tab_off;
   const int64_t* q_off;
   const cd* tab;
+  const void* NO;           // mode 2: N^O at the points (per leaf, column-major), double or cd
+  bool no_cplx;
   int e0, P, nloc, npad, ne_max;
   double k[3];
-  int mode;                 // 0: V-dependent blocks + cached rest -> HE; 1: setup (d, M^AA, V-independent blocks)
+  // 0: EFE blocks with weights w (V + |k|^2/2) plus the cached V-independent CA0, AA0 -> HE (the
+  //    setup pass that forms the transformed V-independent blocks);
+  // 1: setup (d, M^AA, V-independent EFE enrichment blocks CA0, AA0);
+  // 2: per V: the CC block, and the CO, OO blocks of the V term directly in the OEFE basis
+  //    (weights w V against N^O), plus the cached transformed V-independent CO0, OO0 -> HE
+  int mode;
   cd* HE;                   // mode 0: (batch, npad, npad)
   cd* dblk;                 // mode 1: (ncells, nloc, ne_max)
   cd* MAAblk;               // mode 1: (ncells, ne_max, ne_max)
@@ -95,14 +102,20 @@ struct BuildArgs {
   size_t smem;              // dynamic shared memory of the launch
 };
 
-// One CTA per cell, accumulating over the cell's tensor-product leaves.
+// One CTA per cell (or per leaf range of a cell), accumulating over the cell's tensor-product leaves.
 //
 // Setup (mode 1, once per k): d = int N^C N^A and M^AA = int conj(N^A) N^A for
 // the orthogonalization, and the V-independent parts of the enrichment
 // blocks of Eq. HOEFEelelements (kinetic and k terms) into the cache E0.
-// Build (mode 0, per V): the CC block (kinetic, k term and the potential
+// Mode 0 (setup, V = 0): the CC block (kinetic, k term and the potential
 // term on the leaf points, by sum factorization; Hermitian half computed),
-// the potential parts of the CA and AA blocks, plus the cached E0.
+// the potential parts of the CA and AA blocks, plus the cached E0; the
+// transform then turns these into the V-independent OEFE blocks.
+// Mode 2 (per V): the CC block as in mode 0; CO and OO take only the V term,
+// directly against the orthogonalized enrichment N^O_j = N^A_j - sum_a N_a
+// Gamma_aj at the points (Eq. UOEFESplit: the OEFE basis is {N_a, N^O_j}, so
+// T^+ H T restricted to the V term is the weighted Gram matrix of that basis),
+// plus the cached V-independent OEFE blocks.
 __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   extern __shared__ double smem[];
   const BuildItem it = A.items ? A.items[blockIdx.x] : BuildItem{(int)blockIdx.x, -1, -1, -1};
@@ -123,9 +136,16 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   if (threadIdx.x < P) xn[threadIdx.x] = A.gll[threadIdx.x];
 
   cd* HE = A.HE ? (it.slot < 0 ? A.HE + (size_t)b * npad * npad : A.HP + (size_t)it.slot * npad * npad) : nullptr;
+  const bool vmode = A.mode != 1;   // a cell matrix is formed (modes 0, 2)
+  // N^O_j at point q of the current leaf (mode 2)
+  auto nov = [&](int64_t q0l, int n3l, int q, int j) -> cd {
+    const size_t o = (size_t)q0l * A.ne_max + (size_t)j * n3l + q;
+    if (A.no_cplx) return reinterpret_cast<const cd*>(A.NO)[o];
+    return mkc(reinterpret_cast<const double*>(A.NO)[o], 0.0);
+  };
   cd* dB = A.dblk ? A.dblk + (size_t)e * nloc * A.ne_max : nullptr;
   cd* MB = A.MAAblk ? A.MAAblk + (size_t)e * A.ne_max * A.ne_max : nullptr;
-  if (A.mode == 0) {
+  if (vmode) {
     for (int i = threadIdx.x; i < npad * npad; i += BT) HE[i] = mkc(0, 0);
   } else {
     for (int i = threadIdx.x; i < nloc * A.ne_max; i += BT) { dB[i] = mkc(0, 0); CA0[i] = mkc(0, 0); }
@@ -133,7 +153,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   }
   __syncthreads();
 
-  const cd* tabc = A.tab + 4 * A.tab_off[b];  // this cell's tabulation, (q, j) j fastest
+  const cd* tabc = A.tab ? A.tab + 4 * A.tab_off[b] : nullptr;  // this cell's tabulation, (q, j) j fastest
   const int l_begin = it.l0 >= 0 ? it.l0 : A.leaf_off[e], l_end = it.l0 >= 0 ? it.l1 : A.leaf_off[e + 1];
   for (int li = l_begin; li < l_end; ++li) {
     const Leaf L = A.leaves[li];
@@ -156,7 +176,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
     }
     __syncthreads();
 
-    if (A.mode == 0) {
+    if (vmode) {
       // 1D mass, stiffness and antisymmetric gradient matrices of the leaf
       for (int t = threadIdx.x; t < 3 * P * P; t += BT) {
         const int d = t / (P * P), a = (t / P) % P, a2 = t % P;
@@ -241,8 +261,12 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
       const bool full = A.mode == 1;
       for (int j = 0; j < ne; ++j) {
         for (int q = threadIdx.x; q < n3; q += BT) {
-          const cd* tq = tabc + 4 * ((ql0 + q) * ne + j);
           const double w = A.qw[q0 + q];
+          if (A.mode == 2) {
+            F[q] = (w * A.veff[q0 + q]) * nov(q0, n3, q, j);
+            continue;
+          }
+          const cd* tq = tabc + 4 * ((ql0 + q) * ne + j);
           if (!full) {
             F[q] = (w * (A.veff[q0 + q] + 0.5 * kk)) * tq[0];
           } else {
@@ -351,11 +375,11 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
           for (int t = threadIdx.x; t < nq * ne * comps; t += BT) {
             const int q = t / (ne * comps), r = t % (ne * comps);
             const int j = r / comps, cpt = r % comps;
-            Ns[t] = tabc[4 * ((ql0 + qc + q) * ne + j) + cpt];
+            Ns[t] = A.mode == 2 ? nov(q0, n3, qc + q, j) : tabc[4 * ((ql0 + qc + q) * ne + j) + cpt];
           }
           for (int q = threadIdx.x; q < nq; q += BT) {
             const double w = A.qw[q0 + qc + q];
-            Ws[q] = full ? w : w * (A.veff[q0 + qc + q] + 0.5 * kk);
+            Ws[q] = full ? w : A.mode == 2 ? w * A.veff[q0 + qc + q] : w * (A.veff[q0 + qc + q] + 0.5 * kk);
           }
           __syncthreads();
           for (int u = 0; u < 4; ++u) {
@@ -402,8 +426,8 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
       __syncthreads();
     }
   }
-  if (A.mode == 0 && it.slot < 0) {
-    // cached V-independent enrichment blocks
+  if (vmode && it.slot < 0) {
+    // cached V-independent enrichment blocks (mode 0: EFE CA0, AA0; mode 2: OEFE CO0, OO0)
     for (int t = threadIdx.x; t < nloc * ne; t += BT) {
       const int m = t / ne, j = t % ne;
       HE[(size_t)m * npad + nloc + j] += CA0[(size_t)m * A.ne_max + j];
@@ -526,6 +550,93 @@ __global__ void k_hermitize(S* A, int n) {
   }
 }
 
+// Where a finished OEFE cell matrix goes: the FP64 / FP32 / FP32-pair / bf16-split copies, or (the
+// setup pass of the V-independent part) only its CO and OO blocks into the per-cell cache E0
+// (CO: nloc x ne_max, then OO: ne_max x ne_max).
+struct StoreOut {
+  void* H64;
+  void* H32;
+  __nv_bfloat16* Hbf;
+  float* Hp;
+  int parts, nloc, npad, ne_max;
+  cd* E0;
+};
+
+template <typename S>
+__device__ inline void store_entry(const StoreOut& O, int e, int ne, int r, int c, cd v) {
+  const int nloc = O.nloc, npad = O.npad;
+  if (O.E0) {
+    if (c < nloc || c >= nloc + ne || r >= nloc + ne) return;
+    cd* co = O.E0 + (size_t)e * ((size_t)nloc * O.ne_max + (size_t)O.ne_max * O.ne_max);
+    if (r < nloc) co[(size_t)r * O.ne_max + (c - nloc)] = v;
+    else co[(size_t)nloc * O.ne_max + (size_t)(r - nloc) * O.ne_max + (c - nloc)] = v;
+    return;
+  }
+  const size_t o = (size_t)e * npad * npad + (size_t)r * npad + c;
+  if constexpr (sizeof(S) == sizeof(cd)) {
+    if (O.H64) reinterpret_cast<cd*>(O.H64)[o] = v;
+    if (O.H32) reinterpret_cast<cf*>(O.H32)[o] = cf{(float)v.x, (float)v.y};
+    if (O.Hp) {
+      const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+      reinterpret_cast<float4*>(O.Hp)[o] =
+          make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
+    }
+  } else {
+    if (O.H64) reinterpret_cast<double*>(O.H64)[o] = v.x;
+    if (O.H32) reinterpret_cast<float*>(O.H32)[o] = (float)v.x;
+    if (O.Hp) {
+      const float h = __double2float_rn(v.x);
+      reinterpret_cast<float2*>(O.Hp)[o] = make_float2(h, __double2float_rn(v.x - (double)h));
+    }
+  }
+  if (O.Hbf) {
+    // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
+    // the planes of one part of one (K tile, M tile) are one contiguous block for the TMA loads;
+    // planes: (re hi, re lo[, im hi, im lo]) split from the FP32 value, or (re hi, re mid, re lo
+    // [, im hi, im mid, im lo]) with the residuals taken in FP64
+    const int parts = O.parts;
+    const int nq = sizeof(S) == sizeof(cd) ? 2 : 1;
+    const int PL = nq * parts;
+    const size_t pl = 128 * 64;
+    const int mtn = npad >> 7;
+    const size_t base = (size_t)e * PL * npad * npad +
+                        ((((size_t)(c >> 6) * mtn + (r >> 7)) * PL) * 128 + (r & 127)) * 64 + (c & 63);
+    for (int q = 0; q < nq; ++q) {
+      __nv_bfloat16* ob = O.Hbf + base + (size_t)q * parts * pl;
+      const double x = q == 0 ? v.x : v.y;
+      if (parts == 2) {
+        const float xf = (float)x;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
+        ob[0] = hi;
+        ob[pl] = __float2bfloat16_rn(xf - __bfloat162float(hi));
+      } else {
+        double rem = x;
+        for (int s = 0; s < parts; ++s) {
+          const __nv_bfloat16 bp = __double2bfloat16(rem);
+          ob[(size_t)s * pl] = bp;
+          rem -= (double)__bfloat162float(bp);
+        }
+      }
+    }
+  }
+}
+
+// The finished cell matrices of a batch (mode 2 of k_build_cell: CC, CO and OO in HE, OC = CO^+)
+// into the stored copies; one CTA per cell.
+template <typename S>
+__global__ void k_finish(const cd* HEb, const int* act_off, int e0, StoreOut O) {
+  const int b = blockIdx.x, e = e0 + b;
+  const int ne = act_off[e + 1] - act_off[e];
+  const int nloc = O.nloc, npad = O.npad, naug = nloc + ne;
+  const cd* HE = HEb + (size_t)b * npad * npad;
+  for (int t = threadIdx.x; t < npad * npad; t += blockDim.x) {
+    const int r = t / npad, c = t % npad;
+    cd v = mkc(0, 0);
+    if (r < naug && c < naug) v = (r >= nloc && c < nloc) ? cconj(HE[(size_t)c * npad + r]) : HE[t];
+    store_entry<S>(O, e, ne, r, c, v);
+  }
+}
+
 struct TransformSf {   // sum-factorized H_CC Gamma on single-leaf cells (null sf: dense everywhere)
   const double* sf;
   const int* sf_index;  // cell -> row of sf, or -1
@@ -538,10 +649,10 @@ struct TransformSf {   // sum-factorized H_CC Gamma on single-leaf cells (null s
 
 // H^O_e = T_e^+ H_e T_e: CO = CA - H_CC Gamma, OO = AA - Gamma^+ CO - CA^+ Gamma.
 // One CTA per cell; writes the FP64 and/or FP32 stored matrices.
-template <typename S, typename S32>
+template <typename S>
 __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gamma, const int* act_off,
-                                                  int e0, int nloc, int npad, int ne_max, S* H64,
-                                                  S32* H32, __nv_bfloat16* Hbf, float* Hp, int parts, TransformSf T) {
+                                                  int e0, int nloc, int npad, int ne_max, StoreOut O,
+                                                  TransformSf T) {
   extern __shared__ double smem[];
   const int b = blockIdx.x, e = e0 + b;
   const int ne = act_off[e + 1] - act_off[e];
@@ -549,54 +660,7 @@ __global__ void __launch_bounds__(TT, 1) k_transform(const cd* HEb, const S* gam
   const S* Gm = gamma + (size_t)e * nloc * ne_max;
   cd* CO = reinterpret_cast<cd*>(smem);          // nloc * TJB
   constexpr int JB = TJB;
-  auto put = [&](int r, int c, cd v) {
-    const size_t o = (size_t)e * npad * npad + (size_t)r * npad + c;
-    if constexpr (sizeof(S) == sizeof(cd)) {
-      if (H64) reinterpret_cast<cd*>(H64)[o] = v;
-      if (H32) reinterpret_cast<cf*>(H32)[o] = cf{(float)v.x, (float)v.y};
-      if (Hp) {
-        const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-        reinterpret_cast<float4*>(Hp)[o] =
-            make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
-      }
-    } else {
-      if (H64) reinterpret_cast<double*>(H64)[o] = v.x;
-      if (H32) reinterpret_cast<float*>(H32)[o] = (float)v.x;
-      if (Hp) {
-        const float h = __double2float_rn(v.x);
-        reinterpret_cast<float2*>(Hp)[o] = make_float2(h, __double2float_rn(v.x - (double)h));
-      }
-    }
-    if (Hbf) {
-      // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
-      // the planes of one part of one (K tile, M tile) are one contiguous block for the TMA loads;
-      // planes: (re hi, re lo[, im hi, im lo]) split from the FP32 value, or (re hi, re mid, re lo
-      // [, im hi, im mid, im lo]) with the residuals taken in FP64
-      const int nq = sizeof(S) == sizeof(cd) ? 2 : 1;
-      const int PL = nq * parts;
-      const size_t pl = 128 * 64;
-      const int mtn = npad >> 7;
-      const size_t base = (size_t)e * PL * npad * npad +
-                          ((((size_t)(c >> 6) * mtn + (r >> 7)) * PL) * 128 + (r & 127)) * 64 + (c & 63);
-      for (int q = 0; q < nq; ++q) {
-        __nv_bfloat16* o = Hbf + base + (size_t)q * parts * pl;
-        const double x = q == 0 ? v.x : v.y;
-        if (parts == 2) {
-          const float xf = (float)x;
-          const __nv_bfloat16 hi = __float2bfloat16_rn(xf);
-          o[0] = hi;
-          o[pl] = __float2bfloat16_rn(xf - __bfloat162float(hi));
-        } else {
-          double rem = x;
-          for (int s = 0; s < parts; ++s) {
-            const __nv_bfloat16 bp = __double2bfloat16(rem);
-            o[(size_t)s * pl] = bp;
-            rem -= (double)__bfloat162float(bp);
-          }
-        }
-      }
-    }
-  };
+  auto put = [&](int r, int c, cd v) { store_entry<S>(O, e, ne, r, c, v); };
   // CC block and zero padding
   for (int t = threadIdx.x; t < npad * npad; t += TT) {
     const int r = t / npad, c = t % npad;
@@ -736,7 +800,7 @@ static size_t smem_build_bytes(const oefe_ctx* c, int mode) {
 
 // Process cells in batches bounded by a scratch budget; calls fn(e0, e1, tab_off_host).
 template <typename Fn>
-static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, size_t budget, Fn fn) {
+static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, size_t budget, bool with_tab, Fn fn) {
   int e0 = 0;
   while (e0 < c->ncells) {
     std::vector<int64_t> off(1, 0);
@@ -745,7 +809,7 @@ static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, size_t budget, F
     while (e1 < c->ncells) {
       const int64_t ne = c->act_off[e1 + 1] - c->act_off[e1];
       const int64_t ent = (c->q_off[e1 + 1] - c->q_off[e1]) * ne;
-      const size_t add = (size_t)ent * 4 * sizeof(cd) + per_cell_fixed;
+      const size_t add = (with_tab ? (size_t)ent * 4 * sizeof(cd) : 0) + per_cell_fixed;
       if (e1 > e0 && bytes + add > budget) break;
       bytes += add;
       off.push_back(off.back() + ent);
@@ -793,25 +857,28 @@ static size_t batch_budget() {
   return std::min<size_t>((size_t)32 << 30, std::max<size_t>((size_t)2 << 30, fr / 4));
 }
 
-// Run the tabulation and the cell kernel over all cells in batches. In the build mode the work is
-// shared out as items of at most G leaves (cells refined toward a nucleus have tens of leaves, the
-// others one), largest first, so that no cell's leaves serialize the launch.
+// Run the cell kernel over all cells in batches (modes of k_build_cell): mode 1 and mode 0 tabulate
+// the enrichment first, mode 2 reads N^O; mode 0 ends with the transform into the cache E0, mode 2
+// with the store of the cell matrices. Where a cell matrix is formed the work is shared out as
+// items of at most G leaves (cells refined toward a nucleus have tens of leaves, the others one),
+// largest first, so that no cell's leaves serialize the launch.
 static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, double* d_gw, cd* dblk,
                            cd* MAAblk, int store) {
   const size_t n2b = (size_t)c->npad * c->npad * sizeof(cd);
-  const size_t hebytes = mode == 0 ? n2b : 0;
+  const bool vmode = mode != 1;
+  const size_t hebytes = vmode ? n2b : 0;
   const size_t smem = smem_build_bytes(c, mode);
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_build_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   OEFE_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_cell, BT, smem));
   const int resident = std::max(1, per_sm) * c->num_sms;
-  return for_cell_batches(c, hebytes, batch_budget(), [&](int e0, int e1, const std::vector<int64_t>& off) -> int {
+  return for_cell_batches(c, hebytes, batch_budget(), mode != 2, [&](int e0, int e1, const std::vector<int64_t>& off) -> int {
     const int nb = e1 - e0;
     // work items (build mode)
     std::vector<BuildItem> items;
     std::vector<int> red;  // (b, slot0, slot1) per split cell
     int nslot = 0;
-    if (mode == 0) {
+    if (vmode) {
       long long leaves = 0;
       for (int e = e0; e < e1; ++e) leaves += c->leaf_off[e + 1] - c->leaf_off[e];
       const int G = (int)std::max<long long>(2, (leaves + 2 * resident - 1) / (2 * resident));
@@ -829,7 +896,7 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
                        [](const BuildItem& x, const BuildItem& y) { return x.l1 - x.l0 > y.l1 - y.l0; });
     }
     auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
-    const size_t tab_bytes = a256((size_t)off.back() * 4 * sizeof(cd));
+    const size_t tab_bytes = mode == 2 ? 0 : a256((size_t)off.back() * 4 * sizeof(cd));
     const size_t off_bytes = a256(off.size() * sizeof(int64_t));
     const size_t he_total = a256(hebytes * nb);
     const size_t hp_total = a256((size_t)nslot * n2b);
@@ -849,7 +916,7 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
                                        c->stream));
     if (!red.empty())
       OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_red, red.data(), red.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
-    if (off.back() > 0) {
+    if (mode != 2 && off.back() > 0) {
       const int threads = 256;
       const int64_t blocks = std::min<int64_t>((off.back() / std::max(c->nfun, 1) + threads - 1) / threads, 1 << 20);
       OEFE_COUNTED k_tabulate<<<(unsigned)blocks, threads, 0, c->stream>>>(enr_params(c), c->d_qxyz, c->d_q_off, c->d_act_off,
@@ -866,9 +933,11 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     A.gll = c->d_gll;
     A.gauss_w = d_gw;
     A.act_off = c->d_act_off;
-    A.tab_off = d_off;
+    A.tab_off = mode == 2 ? nullptr : d_off;
     A.q_off = c->d_q_off;
-    A.tab = tab;
+    A.tab = mode == 2 ? nullptr : tab;
+    A.NO = K.NO;
+    A.no_cplx = K.cplx;
     A.e0 = e0;
     A.P = c->P;
     A.nloc = c->nloc;
@@ -876,24 +945,41 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     A.ne_max = c->ne_max;
     for (int d = 0; d < 3; ++d) A.k[d] = K.k[d];
     A.mode = mode;
-    A.HE = mode == 0 ? HE : nullptr;
+    A.HE = vmode ? HE : nullptr;
     A.dblk = dblk;
     A.MAAblk = MAAblk;
     A.E0 = (cd*)K.E0;
-    A.items = mode == 0 ? d_items : nullptr;
+    A.items = vmode ? d_items : nullptr;
     A.HP = HP;
     A.smem = smem;
-    const int grid = mode == 0 ? (int)items.size() : nb;
+    const int grid = vmode ? (int)items.size() : nb;
     OEFE_COUNTED k_build_cell<<<grid, BT, smem, c->stream>>>(A);
     OEFE_CUDA_TRY(c, cudaGetLastError());
-    if (mode == 0) {
-      if (!red.empty()) {
+    if (vmode && !red.empty()) {
         const int nred = (int)red.size() / 3;
         dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)c->npad * c->npad + 255) / 256)),
                (unsigned)std::min(nred, 65535));
-        OEFE_COUNTED k_add_partials<<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
-        OEFE_CUDA_TRY(c, cudaGetLastError());
-      }
+      OEFE_COUNTED k_add_partials<<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    }
+    StoreOut O;
+    O.H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
+    O.H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
+    O.Hbf = (store & (OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6)) ? (__nv_bfloat16*)K.Hbf : nullptr;
+    O.Hp = (store & OEFE_STORE_F64PAIR) ? K.Hp : nullptr;
+    O.parts = K.bf_parts;
+    O.nloc = c->nloc;
+    O.npad = c->npad;
+    O.ne_max = c->ne_max;
+    O.E0 = nullptr;
+    if (mode == 2) {
+      if (K.cplx) OEFE_COUNTED k_finish<cd><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
+      else OEFE_COUNTED k_finish<double><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    }
+    if (mode == 0) {
+      // the V-independent OEFE blocks CO0, OO0 of each cell into the cache
+      O = StoreOut{nullptr, nullptr, nullptr, nullptr, 0, c->nloc, c->npad, c->ne_max, (cd*)K.E0};
       TransformSf T;
       T.sf = c->use_sumfac && c->n_sf > 0 ? c->d_sf : nullptr;
       T.sf_index = c->d_sf_index;
@@ -910,19 +996,15 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
                                   : 0;
       if (sf_smem > 227 * 1024) T.sf = nullptr;   // too large for one CTA: dense products on these cells
       const size_t tsmem = std::max(dense_smem, T.sf ? sf_smem : 0);
-      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<cd, cf>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
-      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<double, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<cd>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tsmem));
+      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_transform<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             (int)tsmem));
-      float* H32 = (store & OEFE_STORE_F32) ? K.H32 : nullptr;
-      double* H64 = (store & OEFE_STORE_F64) ? K.H64 : nullptr;
-      __nv_bfloat16* Hbf = (store & (OEFE_STORE_BF16X3 | OEFE_STORE_BF16X6)) ? (__nv_bfloat16*)K.Hbf : nullptr;
-      float* Hp = (store & OEFE_STORE_F64PAIR) ? K.Hp : nullptr;
       if (K.cplx)
-        OEFE_COUNTED k_transform<cd, cf><<<nb, TT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                         c->ne_max, (cd*)H64, (cf*)H32, Hbf, Hp, K.bf_parts, T);
+        OEFE_COUNTED k_transform<cd><<<nb, TT, tsmem, c->stream>>>(HE, (const cd*)K.gamma, c->d_act_off, e0, c->nloc, c->npad,
+                                                     c->ne_max, O, T);
       else
-        OEFE_COUNTED k_transform<double, float><<<nb, TT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
-                                                                c->ne_max, H64, H32, Hbf, Hp, K.bf_parts, T);
+        OEFE_COUNTED k_transform<double><<<nb, TT, tsmem, c->stream>>>(HE, K.gamma, c->d_act_off, e0, c->nloc, c->npad,
+                                                         c->ne_max, O, T);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -945,6 +1027,12 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
   const size_t mbytes = (size_t)c->ncells * std::max(c->ne_max * c->ne_max, 1) * sizeof(cd);
   int st = dev_alloc(c, (void**)&dblk, dbytes);
   if (st == OEFE_OK) st = dev_alloc(c, (void**)&MAAblk, mbytes);
+  double* vzero = nullptr;   // V = 0 for the pass that forms the V-independent OEFE blocks
+  if (st == OEFE_OK && c->nO > 0) st = dev_alloc(c, (void**)&vzero, (size_t)std::max<int64_t>(c->nq, 1) * sizeof(double));
+  if (st == OEFE_OK && vzero) {
+    const cudaError_t ce = cudaMemsetAsync(vzero, 0, (size_t)std::max<int64_t>(c->nq, 1) * sizeof(double), c->stream);
+    if (ce != cudaSuccess) { c->err = cudaGetErrorString(ce); st = OEFE_ERR_CUDA; }
+  }
   for (int ik = 0; ik < nk && st == OEFE_OK; ++ik) {
     KData& K = c->kd[ik];
     for (int d = 0; d < 3; ++d) K.k[d] = k[3 * ik + d];
@@ -996,10 +1084,15 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w) {
       c->err = "kpoints: M^oo is not positive definite (leading minor " + std::to_string(info) + ")";
       st = OEFE_ERR_NOTPD_MOO;
     }
+    // the orthogonalized enrichment at the points, and the V-independent OEFE blocks (kinetic,
+    // k and |k|^2/2 terms) T^+ H_0 T of every cell into E0
+    if (st == OEFE_OK) st = ensure_orth_enrichment(c, K);
+    if (st == OEFE_OK) st = run_cell_kernel(c, K, 0, vzero, d_gw, nullptr, nullptr, 0);
   }
   cudaStreamSynchronize(c->stream);
   dev_free(dblk);
   dev_free(MAAblk);
+  dev_free(vzero);
   dev_free(d_gw);
   if (st != OEFE_OK) return st;
   c->has_k = true;
@@ -1042,7 +1135,7 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
     }
     K.bf_parts = parts;
     if (st == OEFE_OK) st = keep(&K.Hbf, parts > 0, n * sb / 4 * parts);
-    if (st == OEFE_OK) st = run_cell_kernel(c, K, 0, veff, d_gw, nullptr, nullptr, store);
+    if (st == OEFE_OK) st = run_cell_kernel(c, K, 2, veff, d_gw, nullptr, nullptr, store);
     if (st != OEFE_OK) break;
     K.built = true;
   }
