@@ -198,6 +198,9 @@ def run_ours(args, rank, world):
         if args.with_fp64:   # one FP64 operator application (the FP64 cell product)
             Y64 = torch.empty_like(X0[0])
             ctx.apply_h(0, X0[0], Y64)
+        if args.with_density:   # the fields of the filtered vectors (density at the points)
+            occ = np.full(nvs[0], 2.0 / nvs[0])
+            ctx.density([X0[0]], [occ], rho)
         torch.cuda.synchronize()
         return {"filter_only": True, "passes": args.steps, "config": w.name}
 
@@ -571,6 +574,8 @@ def main():
                     help="two-part bf16 split of the cell matrices (BF16x3) instead of three parts (BF16x6)")
     ap.add_argument("--fp32-simt", dest="tensor", action="store_false",
                     help="FP32 SIMT cell products instead of the BF16x3 tensor-core path")
+    ap.add_argument("--with-density", action="store_true",
+                    help="with --filter-only: one density evaluation (profiling aid)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     args = ap.parse_args()

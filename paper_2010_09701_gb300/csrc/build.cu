@@ -12,6 +12,7 @@
 #include <cstring>
 
 #include "oefe_internal.h"
+#include "pair_dev.cuh"
 #include "enrich_dev.cuh"
 #include "sumfac_dev.cuh"
 
@@ -24,6 +25,14 @@ constexpr int TT = 352;     // threads per CTA of the transform: one local node 
 constexpr int TJB = 8;      // enrichment columns per pass of the transform
 constexpr size_t SMEM_SETUP = 212 * 1024;  // setup mode: one CTA per SM
 constexpr size_t SMEM_BUILD = 96 * 1024;   // build mode: two CTAs per SM
+
+// A complex value in arithmetic V (FP64 or an FP32 pair): the cell-matrix accumulator of the
+// per-step build, 16 bytes either way.
+template <typename V>
+struct VC {
+  V re, im;
+};
+
 
 // Tabulate N^A and grad N^A for (point, active function) pairs of a batch of cells.
 // tab entry layout: 4 complex values (value, d/dx, d/dy, d/dz) per (q, j), j fastest.
@@ -83,15 +92,11 @@ struct BuildArgs {
   const int64_t* tab_off;
   const int64_t* q_off;
   const cd* tab;
-  const void* NO;           // mode 2: N^O at the points (per leaf, column-major), double or cd
-  bool no_cplx;
   int e0, P, nloc, npad, ne_max;
   double k[3];
   // 0: EFE blocks with weights w (V + |k|^2/2) plus the cached V-independent CA0, AA0 -> HE (the
-  //    setup pass that forms the transformed V-independent blocks);
-  // 1: setup (d, M^AA, V-independent EFE enrichment blocks CA0, AA0);
-  // 2: per V: the CC block, and the CO, OO blocks of the V term directly in the OEFE basis
-  //    (weights w V against N^O), plus the cached transformed V-independent CO0, OO0 -> HE
+  //    setup pass that forms the transformed V-independent blocks, with V = 0);
+  // 1: setup (d, M^AA, V-independent EFE enrichment blocks CA0, AA0)
   int mode;
   cd* HE;                   // mode 0: (batch, npad, npad)
   cd* dblk;                 // mode 1: (ncells, nloc, ne_max)
@@ -111,11 +116,6 @@ struct BuildArgs {
 // term on the leaf points, by sum factorization; Hermitian half computed),
 // the potential parts of the CA and AA blocks, plus the cached E0; the
 // transform then turns these into the V-independent OEFE blocks.
-// Mode 2 (per V): the CC block as in mode 0; CO and OO take only the V term,
-// directly against the orthogonalized enrichment N^O_j = N^A_j - sum_a N_a
-// Gamma_aj at the points (Eq. UOEFESplit: the OEFE basis is {N_a, N^O_j}, so
-// T^+ H T restricted to the V term is the weighted Gram matrix of that basis),
-// plus the cached V-independent OEFE blocks.
 __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   extern __shared__ double smem[];
   const BuildItem it = A.items ? A.items[blockIdx.x] : BuildItem{(int)blockIdx.x, -1, -1, -1};
@@ -136,13 +136,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
   if (threadIdx.x < P) xn[threadIdx.x] = A.gll[threadIdx.x];
 
   cd* HE = A.HE ? (it.slot < 0 ? A.HE + (size_t)b * npad * npad : A.HP + (size_t)it.slot * npad * npad) : nullptr;
-  const bool vmode = A.mode != 1;   // a cell matrix is formed (modes 0, 2)
-  // N^O_j at point q of the current leaf (mode 2)
-  auto nov = [&](int64_t q0l, int n3l, int q, int j) -> cd {
-    const size_t o = (size_t)q0l * A.ne_max + (size_t)j * n3l + q;
-    if (A.no_cplx) return reinterpret_cast<const cd*>(A.NO)[o];
-    return mkc(reinterpret_cast<const double*>(A.NO)[o], 0.0);
-  };
+  const bool vmode = A.mode == 0;   // a cell matrix is formed
   cd* dB = A.dblk ? A.dblk + (size_t)e * nloc * A.ne_max : nullptr;
   cd* MB = A.MAAblk ? A.MAAblk + (size_t)e * A.ne_max * A.ne_max : nullptr;
   if (vmode) {
@@ -262,10 +256,6 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
       for (int j = 0; j < ne; ++j) {
         for (int q = threadIdx.x; q < n3; q += BT) {
           const double w = A.qw[q0 + q];
-          if (A.mode == 2) {
-            F[q] = (w * A.veff[q0 + q]) * nov(q0, n3, q, j);
-            continue;
-          }
           const cd* tq = tabc + 4 * ((ql0 + q) * ne + j);
           if (!full) {
             F[q] = (w * (A.veff[q0 + q] + 0.5 * kk)) * tq[0];
@@ -375,11 +365,11 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
           for (int t = threadIdx.x; t < nq * ne * comps; t += BT) {
             const int q = t / (ne * comps), r = t % (ne * comps);
             const int j = r / comps, cpt = r % comps;
-            Ns[t] = A.mode == 2 ? nov(q0, n3, qc + q, j) : tabc[4 * ((ql0 + qc + q) * ne + j) + cpt];
+            Ns[t] = tabc[4 * ((ql0 + qc + q) * ne + j) + cpt];
           }
           for (int q = threadIdx.x; q < nq; q += BT) {
             const double w = A.qw[q0 + qc + q];
-            Ws[q] = full ? w : A.mode == 2 ? w * A.veff[q0 + qc + q] : w * (A.veff[q0 + qc + q] + 0.5 * kk);
+            Ws[q] = full ? w : w * (A.veff[q0 + qc + q] + 0.5 * kk);
           }
           __syncthreads();
           for (int u = 0; u < 4; ++u) {
@@ -427,7 +417,7 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
     }
   }
   if (vmode && it.slot < 0) {
-    // cached V-independent enrichment blocks (mode 0: EFE CA0, AA0; mode 2: OEFE CO0, OO0)
+    // cached V-independent EFE enrichment blocks CA0, AA0
     for (int t = threadIdx.x; t < nloc * ne; t += BT) {
       const int m = t / ne, j = t % ne;
       HE[(size_t)m * npad + nloc + j] += CA0[(size_t)m * A.ne_max + j];
@@ -435,6 +425,318 @@ __global__ void __launch_bounds__(BT) k_build_cell(BuildArgs A) {
     for (int t = threadIdx.x; t < ne * ne; t += BT) {
       const int i = t / ne, j = t % ne;
       HE[(size_t)(nloc + i) * npad + nloc + j] += AA0[i * A.ne_max + j];
+    }
+  }
+}
+
+
+// ------------------------------------------------------------------ per-step build (OEFE basis)
+
+struct OefeArgs {
+  const Leaf* leaves;
+  const int* leaf_off;
+  const double* qxyz;
+  const double* qw;
+  const double* veff;
+  const double* cellbox;
+  const double* gll;
+  const double* gauss_w;    // [n][i] table, 13 x 12
+  const int* act_off;
+  const void* NO;           // N^O per leaf, column-major: double / cd (V = double), float2 / float4 (f2)
+  bool no_cplx;
+  int e0, P, nloc, npad, ne_max;
+  double k[3];
+  void* HE;                 // VC<V> (batch, npad, npad)
+  void* HP;                 // VC<V> partials of the split cells
+  const cd* E0;             // per cell: V-independent OEFE blocks CO0 (nloc x ne_max), OO0 (ne_max^2)
+  const BuildItem* items;
+  size_t smem;
+};
+
+template <typename V>
+__device__ inline VC<V> load_no(const OefeArgs& A, size_t o) {
+  if constexpr (std::is_same<V, double>::value) {
+    if (A.no_cplx) {
+      const cd w = reinterpret_cast<const cd*>(A.NO)[o];
+      return VC<V>{w.x, w.y};
+    }
+    return VC<V>{reinterpret_cast<const double*>(A.NO)[o], 0.0};
+  } else {
+    if (A.no_cplx) {
+      const float4 w = reinterpret_cast<const float4*>(A.NO)[o];
+      return VC<V>{f2{w.x, w.y}, f2{w.z, w.w}};
+    }
+    const float2 w = reinterpret_cast<const float2*>(A.NO)[o];
+    return VC<V>{f2{w.x, w.y}, f2{0.0f, 0.0f}};
+  }
+}
+
+// symmetric pair index of (i, j): max(i,j) (max(i,j) + 1) / 2 + min(i,j), and its inverse's larger
+// member
+__device__ __forceinline__ int sym_idx(int i, int j) {
+  const int h = max(i, j), l = min(i, j);
+  return h * (h + 1) / 2 + l;
+}
+__device__ __forceinline__ int sym_hi(int s) {
+  int h = 0;
+  while ((h + 1) * (h + 2) / 2 <= s) ++h;
+  return h;
+}
+
+template <typename V>
+__device__ inline void vc_add(VC<V>* h, V re, V im) {
+  VC<V> x = *h;
+  x.re = v_add(x.re, re);
+  x.im = v_add(x.im, im);
+  *h = x;
+}
+
+// The cell matrix of the V term in the OEFE basis plus the cached V-independent blocks (Eq.
+// HOEFEelelements with Eq. UOEFESplit): per tensor-product leaf of the item,
+//   CC += sum_q w_q (V_q + |k|^2/2) N_a N_b + the kinetic and k terms (sum factorization over the
+//         leaf's Gauss points; Hermitian half, mirrored),
+//   CO += sum_q w_q V_q N_a N^O_j                 (one column j at a time, staged z, y, x),
+//   OO += sum_q w_q V_q conj(N^O_i) N^O_j          (pairs i <= j, mirrored),
+// all in arithmetic V; then CO0, OO0 are added once per cell. One CTA per item (a cell's leaf
+// range); slot >= 0 writes a partial summed afterwards in a fixed order.
+template <typename V>
+__global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
+  using Acc = typename AccOf<V>::type;
+  extern __shared__ double smem_raw[];
+  V* smem = reinterpret_cast<V*>(smem_raw);
+  const BuildItem it = A.items[blockIdx.x];
+  const int b = it.b, e = A.e0 + b;
+  const int P = A.P, nloc = A.nloc, npad = A.npad;
+  const int ne = A.act_off[e + 1] - A.act_off[e];
+  const double* box = A.cellbox + 6 * e;
+  const double kk = A.k[0] * A.k[0] + A.k[1] * A.k[1] + A.k[2] * A.k[2];
+  const bool kz = kk == 0.0;
+
+  __shared__ double xn[MAXP];
+  __shared__ double Ld[3][MAXN1][MAXP], Dd[3][MAXN1][MAXP], w1[3][MAXN1];
+  __shared__ V Lt[3][MAXN1][MAXP];                 // 1D Lagrange values at the leaf's points
+  __shared__ V LL[3][MAXN1][MAXP * MAXP];          // products L[i][a] L[i][a2]
+  __shared__ V Mm[3][MAXP][MAXP], Gr[3][MAXP][MAXP], Gi[3][MAXP][MAXP];   // M, K/2, -(k/2) A
+  if (threadIdx.x < P) xn[threadIdx.x] = A.gll[threadIdx.x];
+
+  VC<V>* HE = reinterpret_cast<VC<V>*>(it.slot < 0 ? A.HE : A.HP) +
+              (size_t)(it.slot < 0 ? b : it.slot) * npad * npad;
+  for (int i = threadIdx.x; i < npad * npad; i += BT) HE[i] = VC<V>{v_from<V>(0.0), v_from<V>(0.0)};
+  __syncthreads();
+
+  for (int li = it.l0; li < it.l1; ++li) {
+    const Leaf L = A.leaves[li];
+    const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
+    const int64_t q0 = L.q0;
+    if (threadIdx.x < 3 * n1) {
+      const int d = threadIdx.x / n1, i = threadIdx.x % n1;
+      const int64_t qi = q0 + (d == 0 ? i : d == 1 ? i * n1 : i * n2);
+      const double xi = 2.0 * (A.qxyz[3 * qi + d] - box[d]) / box[3 + d] - 1.0;
+      double Lv[MAXP], Dv[MAXP];
+      lagrange_eval(xn, P, xi, Lv, Dv);
+      for (int a = 0; a < P; ++a) {
+        Ld[d][i][a] = Lv[a];
+        Dd[d][i][a] = Dv[a] * (2.0 / box[3 + d]);
+        Lt[d][i][a] = v_from<V>(Lv[a]);
+      }
+      for (int a = 0; a < P; ++a)
+        for (int a2 = 0; a2 < P; ++a2) LL[d][i][a * P + a2] = v_from<V>(Lv[a] * Lv[a2]);
+      w1[d][i] = A.gauss_w[n1 * 12 + i] * (L.hi[d] - L.lo[d]) / 2.0;
+    }
+    __syncthreads();
+    // 1D mass, stiffness and antisymmetric gradient matrices of the leaf (FP64, then V)
+    for (int t = threadIdx.x; t < 3 * P * P; t += BT) {
+      const int d = t / (P * P), a = (t / P) % P, a2 = t % P;
+      double m = 0, kq = 0, g1 = 0, g2 = 0;
+      for (int i = 0; i < n1; ++i) {
+        m = fma(w1[d][i] * Ld[d][i][a], Ld[d][i][a2], m);
+        kq = fma(w1[d][i] * Dd[d][i][a], Dd[d][i][a2], kq);
+        g1 = fma(w1[d][i] * Ld[d][i][a], Dd[d][i][a2], g1);
+        g2 = fma(w1[d][i] * Dd[d][i][a], Ld[d][i][a2], g2);
+      }
+      Mm[d][a][a2] = v_from<V>(m);
+      Gr[d][a][a2] = v_from<V>(0.5 * kq);
+      Gi[d][a][a2] = v_from<V>(-0.5 * A.k[d] * (g1 - g2));
+    }
+    // ---- CC: potential weights W_q = w_q (V_q + |k|^2 / 2). The V term is symmetric in each of
+    //      (a,a'), (b,b'), (c,c') separately, so the partial sums keep the symmetric pairs only
+    //      (PS = P (P + 1) / 2 of them): T1[(qx,qy)][c<=c'], T2[qx][b<=b'][c<=c']
+    const int P2 = P * P, PS = P * (P + 1) / 2;
+    V* Wv = smem;                            // n3
+    V* T1 = Wv + n3;                         // n2 * PS
+    V* T2 = T1 + n2 * PS;                    // cx * PS * PS
+    for (int q = threadIdx.x; q < n3; q += BT) Wv[q] = v_from<V>(A.qw[q0 + q] * (A.veff[q0 + q] + 0.5 * kk));
+    __syncthreads();
+    for (int t = threadIdx.x; t < n2 * PS; t += BT) {
+      const int qxy = t / PS, cs = t % PS;
+      const int c = sym_hi(cs), c2 = cs - c * (c + 1) / 2;   // c2 <= c
+      T1[t] = v_dot<V>(n1, [&](int qz) { return Wv[qxy + n2 * qz]; }, [&](int qz) { return LL[2][qz][c * P + c2]; });
+    }
+    __syncthreads();
+    const int budget = (int)((A.smem / sizeof(V) - n3 - (size_t)n2 * PS) / (PS * PS));
+    const int cx = min(n1, max(1, budget));
+    for (int qx0 = 0; qx0 < n1; qx0 += cx) {
+      const int nx = min(cx, n1 - qx0);
+      for (int t = threadIdx.x; t < nx * PS * PS; t += BT) {
+        const int ix = t / (PS * PS), r = t % (PS * PS);
+        const int bs = r / PS, cs = r % PS;
+        const int bb = sym_hi(bs), b2 = bs - bb * (bb + 1) / 2;
+        T2[t] = v_dot<V>(n1, [&](int qy) { return LL[1][qy][bb * P + b2]; },
+                         [&](int qy) { return T1[((qx0 + ix) + n1 * qy) * PS + cs]; });
+      }
+      __syncthreads();
+      const bool first = qx0 == 0;
+      for (int t = threadIdx.x; t < nloc * nloc; t += BT) {
+        const int m = t / nloc, n = t % nloc;
+        if (m > n) continue;
+        const int a = m % P, bb = (m / P) % P, c = m / P2;
+        const int a2 = n % P, b2 = (n / P) % P, c2 = n / P2;
+        const int ridx = sym_idx(bb, b2) * PS + sym_idx(c, c2);
+        Acc vr = v_zero<V>();
+        for (int ix = 0; ix < nx; ++ix) v_mac(vr, LL[0][qx0 + ix][a * P + a2], T2[ix * PS * PS + ridx]);
+        V re = v_fin(vr), im = v_from<V>(0.0);
+        if (first) {
+          // kinetic: sum_d G_d in position d, M elsewhere (real part K/2, imaginary -(k/2) A)
+          const V m0 = Mm[0][a][a2], m1 = Mm[1][bb][b2], m2 = Mm[2][c][c2];
+          const V m12 = v_mul(m1, m2), m02 = v_mul(m0, m2), m01 = v_mul(m0, m1);
+          Acc kr = v_zero<V>();
+          v_mac(kr, Gr[0][a][a2], m12);
+          v_mac(kr, Gr[1][bb][b2], m02);
+          v_mac(kr, Gr[2][c][c2], m01);
+          re = v_add(re, v_fin(kr));
+          if (!kz) {
+            Acc ki = v_zero<V>();
+            v_mac(ki, Gi[0][a][a2], m12);
+            v_mac(ki, Gi[1][bb][b2], m02);
+            v_mac(ki, Gi[2][c][c2], m01);
+            im = v_fin(ki);
+          }
+        }
+        vc_add(HE + (size_t)m * npad + n, re, im);
+        if (m != n) vc_add(HE + (size_t)n * npad + m, re, v_neg(im));
+      }
+      __syncthreads();
+    }
+
+    // ---- CO: column j of the V term, F_q = w_q V_q N^O_j(x_q), staged z, y, x
+    const size_t blk = (size_t)q0 * A.ne_max;
+    {
+      VC<V>* F = reinterpret_cast<VC<V>*>(smem);    // n3
+      VC<V>* G = F + n3;                            // n2 * P
+      VC<V>* H = G + n2 * P;                        // n1 * P * P
+      for (int j = 0; j < ne; ++j) {
+        for (int q = threadIdx.x; q < n3; q += BT) {
+          const V w = v_from<V>(A.qw[q0 + q] * A.veff[q0 + q]);
+          const VC<V> nv = load_no<V>(A, blk + (size_t)j * n3 + q);
+          F[q] = VC<V>{v_mul(w, nv.re), v_mul(w, nv.im)};
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < n2 * P; t += BT) {     // z: (qx,qy,c)
+          const int qxy = t / P, c = t % P;
+          Acc gr = v_zero<V>(), gi = v_zero<V>();
+          for (int qz = 0; qz < n1; ++qz) {
+            const VC<V> f = F[qxy + n2 * qz];
+            v_mac(gr, Lt[2][qz][c], f.re);
+            v_mac(gi, Lt[2][qz][c], f.im);
+          }
+          G[t] = VC<V>{v_fin(gr), v_fin(gi)};
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < n1 * P * P; t += BT) {  // y: (qx,b,c)
+          const int qx = t / (P * P), bb = (t / P) % P, c = t % P;
+          Acc hr = v_zero<V>(), hi = v_zero<V>();
+          for (int qy = 0; qy < n1; ++qy) {
+            const VC<V> g = G[(qx + n1 * qy) * P + c];
+            v_mac(hr, Lt[1][qy][bb], g.re);
+            v_mac(hi, Lt[1][qy][bb], g.im);
+          }
+          H[t] = VC<V>{v_fin(hr), v_fin(hi)};
+        }
+        __syncthreads();
+        for (int m = threadIdx.x; m < nloc; m += BT) {       // x: node a + P (b + P c)
+          const int a = m % P, bc = m / P;
+          const int bb = bc % P, c = bc / P;
+          Acc sr = v_zero<V>(), si = v_zero<V>();
+          for (int qx = 0; qx < n1; ++qx) {
+            const VC<V> h = H[(qx * P + bb) * P + c];
+            v_mac(sr, Lt[0][qx][a], h.re);
+            v_mac(si, Lt[0][qx][a], h.im);
+          }
+          vc_add(HE + (size_t)m * npad + nloc + j, v_fin(sr), v_fin(si));
+        }
+        __syncthreads();
+      }
+    }
+
+    // ---- OO: pairs (i <= j) over the leaf points in chunks, with w V N^O_i staged beside N^O_i
+    {
+      const int QC = max(1, min(32, (int)((A.smem - 64) / ((size_t)max(ne, 1) * 2 * sizeof(VC<V>)))));
+      VC<V>* Ns = reinterpret_cast<VC<V>*>(smem);   // QC x ne
+      VC<V>* Nw = Ns + (size_t)QC * ne;             // QC x ne: w V N
+      const int npairs = ne * (ne + 1) / 2;
+      for (int pb = 0; pb < npairs; pb += 2 * BT) {
+        int pi[2], pj[2];
+        Acc ar[2], ai[2];
+        for (int u = 0; u < 2; ++u) {
+          ar[u] = ai[u] = v_zero<V>();
+          const int pp = pb + threadIdx.x + u * BT;
+          pi[u] = -1;
+          pj[u] = -1;
+          if (pp < npairs) {  // pair index -> (i, j), i <= j
+            int i = 0, rem = pp;
+            while (rem >= ne - i) { rem -= ne - i; ++i; }
+            pi[u] = i;
+            pj[u] = i + rem;
+          }
+        }
+        for (int qc = 0; qc < n3; qc += QC) {
+          const int nq = min(QC, n3 - qc);
+          __syncthreads();
+          for (int t = threadIdx.x; t < nq * ne; t += BT) {
+            const int q = t / ne, j = t % ne;
+            const VC<V> nv = load_no<V>(A, blk + (size_t)j * n3 + qc + q);
+            const V w = v_from<V>(A.qw[q0 + qc + q] * A.veff[q0 + qc + q]);
+            Ns[t] = nv;
+            Nw[t] = VC<V>{v_mul(w, nv.re), v_mul(w, nv.im)};
+          }
+          __syncthreads();
+          for (int u = 0; u < 2; ++u) {
+            if (pi[u] < 0) continue;
+            const int i = pi[u], j = pj[u];
+            for (int q = 0; q < nq; ++q) {   // conj(w N_i) N_j
+              const VC<V> x = Nw[q * ne + i], y = Ns[q * ne + j];
+              v_mac(ar[u], x.re, y.re);
+              v_mac(ar[u], x.im, y.im);
+              v_mac(ai[u], x.re, y.im);
+              v_mac(ai[u], v_neg(x.im), y.re);
+            }
+          }
+        }
+        for (int u = 0; u < 2; ++u) {
+          if (pi[u] < 0) continue;
+          const int i = pi[u], j = pj[u];
+          const V re = v_fin(ar[u]), im = v_fin(ai[u]);
+          vc_add(HE + (size_t)(nloc + i) * npad + nloc + j, re, im);
+          if (i != j) vc_add(HE + (size_t)(nloc + j) * npad + nloc + i, re, v_neg(im));
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (it.slot < 0) {
+    // the cached V-independent OEFE blocks CO0, OO0
+    const size_t e0s = (size_t)nloc * A.ne_max + (size_t)A.ne_max * A.ne_max;
+    const cd* CO0 = A.E0 + (size_t)e * e0s;
+    const cd* OO0 = CO0 + (size_t)nloc * A.ne_max;
+    for (int t = threadIdx.x; t < nloc * ne; t += BT) {
+      const int m = t / ne, j = t % ne;
+      const cd v = CO0[(size_t)m * A.ne_max + j];
+      vc_add(HE + (size_t)m * npad + nloc + j, v_from<V>(v.x), v_from<V>(v.y));
+    }
+    for (int t = threadIdx.x; t < ne * ne; t += BT) {
+      const int i = t / ne, j = t % ne;
+      const cd v = OO0[i * A.ne_max + j];
+      vc_add(HE + (size_t)(nloc + i) * npad + nloc + j, v_from<V>(v.x), v_from<V>(v.y));
     }
   }
 }
@@ -562,8 +864,9 @@ struct StoreOut {
   cd* E0;
 };
 
+// v in FP64 and as FP32 pairs (pr, pi): the pair copy and the bf16 splits are taken from the pairs
 template <typename S>
-__device__ inline void store_entry(const StoreOut& O, int e, int ne, int r, int c, cd v) {
+__device__ inline void store_entry2(const StoreOut& O, int e, int ne, int r, int c, cd v, f2 pr, f2 pi) {
   const int nloc = O.nloc, npad = O.npad;
   if (O.E0) {
     if (c < nloc || c >= nloc + ne || r >= nloc + ne) return;
@@ -576,24 +879,18 @@ __device__ inline void store_entry(const StoreOut& O, int e, int ne, int r, int 
   if constexpr (sizeof(S) == sizeof(cd)) {
     if (O.H64) reinterpret_cast<cd*>(O.H64)[o] = v;
     if (O.H32) reinterpret_cast<cf*>(O.H32)[o] = cf{(float)v.x, (float)v.y};
-    if (O.Hp) {
-      const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-      reinterpret_cast<float4*>(O.Hp)[o] =
-          make_float4(rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih));
-    }
+    if (O.Hp) reinterpret_cast<float4*>(O.Hp)[o] = make_float4(pr.h, pr.l, pi.h, pi.l);
   } else {
     if (O.H64) reinterpret_cast<double*>(O.H64)[o] = v.x;
     if (O.H32) reinterpret_cast<float*>(O.H32)[o] = (float)v.x;
-    if (O.Hp) {
-      const float h = __double2float_rn(v.x);
-      reinterpret_cast<float2*>(O.Hp)[o] = make_float2(h, __double2float_rn(v.x - (double)h));
-    }
+    if (O.Hp) reinterpret_cast<float2*>(O.Hp)[o] = make_float2(pr.h, pr.l);
   }
   if (O.Hbf) {
     // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
     // the planes of one part of one (K tile, M tile) are one contiguous block for the TMA loads;
     // planes: (re hi, re lo[, im hi, im lo]) split from the FP32 value, or (re hi, re mid, re lo
-    // [, im hi, im mid, im lo]) with the residuals taken in FP64
+    // [, im hi, im mid, im lo]) from the FP32 pair x = h + l: each residual h - bf16(h) is exact in
+    // FP32 and the low part joins the second residual (rounding 2^-24 of it, far below the split)
     const int parts = O.parts;
     const int nq = sizeof(S) == sizeof(cd) ? 2 : 1;
     const int PL = nq * parts;
@@ -610,30 +907,46 @@ __device__ inline void store_entry(const StoreOut& O, int e, int ne, int r, int 
         ob[0] = hi;
         ob[pl] = __float2bfloat16_rn(xf - __bfloat162float(hi));
       } else {
-        double rem = x;
-        for (int s = 0; s < parts; ++s) {
-          const __nv_bfloat16 bp = __double2bfloat16(rem);
-          ob[(size_t)s * pl] = bp;
-          rem -= (double)__bfloat162float(bp);
-        }
+        const float h = q == 0 ? pr.h : pi.h, l = q == 0 ? pr.l : pi.l;
+        const __nv_bfloat16 b1 = __float2bfloat16_rn(h);
+        const float r1 = __fadd_rn(__fsub_rn(h, __bfloat162float(b1)), l);
+        const __nv_bfloat16 b2 = __float2bfloat16_rn(r1);
+        const __nv_bfloat16 b3 = __float2bfloat16_rn(__fsub_rn(r1, __bfloat162float(b2)));
+        ob[0] = b1;
+        ob[pl] = b2;
+        ob[2 * pl] = b3;
       }
     }
   }
 }
 
-// The finished cell matrices of a batch (mode 2 of k_build_cell: CC, CO and OO in HE, OC = CO^+)
-// into the stored copies; one CTA per cell.
 template <typename S>
-__global__ void k_finish(const cd* HEb, const int* act_off, int e0, StoreOut O) {
+__device__ inline void store_entry(const StoreOut& O, int e, int ne, int r, int c, cd v) {
+  const bool need = O.Hp || (O.Hbf && O.parts == 3);
+  store_entry2<S>(O, e, ne, r, c, v, need ? f2_from(v.x) : f2{0.0f, 0.0f}, need ? f2_from(v.y) : f2{0.0f, 0.0f});
+}
+
+// The finished cell matrices of a batch (k_build_oefe: CC, CO and OO in HE, OC = CO^+) into the
+// stored copies; one CTA per cell. HE in arithmetic V: FP64 (cd) or FP32 pairs.
+template <typename S, typename V>
+__global__ void k_finish(const void* HEb, const int* act_off, int e0, StoreOut O) {
   const int b = blockIdx.x, e = e0 + b;
   const int ne = act_off[e + 1] - act_off[e];
   const int nloc = O.nloc, npad = O.npad, naug = nloc + ne;
-  const cd* HE = HEb + (size_t)b * npad * npad;
+  const VC<V>* HE = reinterpret_cast<const VC<V>*>(HEb) + (size_t)b * npad * npad;
   for (int t = threadIdx.x; t < npad * npad; t += blockDim.x) {
     const int r = t / npad, c = t % npad;
-    cd v = mkc(0, 0);
-    if (r < naug && c < naug) v = (r >= nloc && c < nloc) ? cconj(HE[(size_t)c * npad + r]) : HE[t];
-    store_entry<S>(O, e, ne, r, c, v);
+    VC<V> v{v_from<V>(0.0), v_from<V>(0.0)};
+    if (r < naug && c < naug) {
+      if (r >= nloc && c < nloc) {
+        v = HE[(size_t)c * npad + r];
+        v.im = v_neg(v.im);
+      } else {
+        v = HE[t];
+      }
+    }
+    if constexpr (std::is_same<V, double>::value) store_entry<S>(O, e, ne, r, c, mkc(v.re, v.im));
+    else store_entry2<S>(O, e, ne, r, c, mkc(f2_to(v.re), f2_to(v.im)), v.re, v.im);
   }
 }
 
@@ -798,6 +1111,19 @@ static size_t smem_build_bytes(const oefe_ctx* c, int mode) {
   return std::max(std::max(phase_cc, phase_ca), phase_aa);
 }
 
+// Dynamic shared memory of k_build_oefe: the largest phase, capped so that two CTAs share an SM
+// (the CC stage then takes its partial sums in chunks of qx)
+static size_t smem_oefe_bytes(const oefe_ctx* c) {
+  const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P, PS = P * (P + 1) / 2;
+  const size_t n3 = (size_t)n1 * n1 * n1, n2 = (size_t)n1 * n1;
+  const size_t cc_min = (n3 + n2 * PS + (size_t)PS * PS) * 8;
+  const size_t cc = (n3 + n2 * PS + (size_t)n1 * PS * PS) * 8;
+  const size_t co = (n3 + n2 * P + (size_t)n1 * P * P) * 16;
+  const size_t oo = 32 * (size_t)std::max(c->ne_max, 1) * 2 * 16 + 64;
+  const size_t cap = 82 * 1024;
+  return std::max({cc_min, std::min(cap, cc), co, oo});
+}
+
 // Process cells in batches bounded by a scratch budget; calls fn(e0, e1, tab_off_host).
 template <typename Fn>
 static int for_cell_batches(oefe_ctx* c, size_t per_cell_fixed, size_t budget, bool with_tab, Fn fn) {
@@ -836,14 +1162,21 @@ static EnrParams enr_params(const oefe_ctx* c) {
 }
 
 // Sum the partial cell matrices of the split cells into their cell matrices, in slot order.
-static __global__ void k_add_partials(cd* HE, const cd* HP, const int* red, int nred, int npad) {
+template <typename V>
+__global__ void k_add_partials(void* HEv, const void* HPv, const int* red, int nred, int npad) {
+  VC<V>* HE = reinterpret_cast<VC<V>*>(HEv);
+  const VC<V>* HP = reinterpret_cast<const VC<V>*>(HPv);
   const int64_t n2 = (int64_t)npad * npad;
   for (int r = blockIdx.y; r < nred; r += gridDim.y) {
     const int b = red[3 * r], s0 = red[3 * r + 1], s1 = red[3 * r + 2];
-    cd* h = HE + (size_t)b * n2;
+    VC<V>* h = HE + (size_t)b * n2;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n2; t += (int64_t)gridDim.x * blockDim.x) {
-      cd s = h[t];
-      for (int q = s0; q < s1; ++q) s += HP[(size_t)q * n2 + t];
+      VC<V> s = h[t];
+      for (int q = s0; q < s1; ++q) {
+        const VC<V> x = HP[(size_t)q * n2 + t];
+        s.re = v_add(s.re, x.re);
+        s.im = v_add(s.im, x.im);
+      }
       h[t] = s;
     }
   }
@@ -867,10 +1200,20 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
   const size_t n2b = (size_t)c->npad * c->npad * sizeof(cd);
   const bool vmode = mode != 1;
   const size_t hebytes = vmode ? n2b : 0;
-  const size_t smem = smem_build_bytes(c, mode);
-  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_build_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const bool pairs = mode == 2 && c->f64_products == OEFE_F64_PAIRS;
+  const size_t smem = mode == 2 ? smem_oefe_bytes(c) : smem_build_bytes(c, mode);
   int per_sm = 0;
-  OEFE_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_cell, BT, smem));
+  if (mode == 2) {
+    auto occ = [&](auto kern) -> int {
+      OEFE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      OEFE_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, BT, smem));
+      return OEFE_OK;
+    };
+    OEFE_TRY(pairs ? occ(k_build_oefe<f2>) : occ(k_build_oefe<double>));
+  } else {
+    OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_build_cell, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    OEFE_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_build_cell, BT, smem));
+  }
   const int resident = std::max(1, per_sm) * c->num_sms;
   return for_cell_batches(c, hebytes, batch_budget(), mode != 2, [&](int e0, int e1, const std::vector<int64_t>& off) -> int {
     const int nb = e1 - e0;
@@ -933,11 +1276,9 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     A.gll = c->d_gll;
     A.gauss_w = d_gw;
     A.act_off = c->d_act_off;
-    A.tab_off = mode == 2 ? nullptr : d_off;
+    A.tab_off = d_off;
     A.q_off = c->d_q_off;
-    A.tab = mode == 2 ? nullptr : tab;
-    A.NO = K.NO;
-    A.no_cplx = K.cplx;
+    A.tab = tab;
     A.e0 = e0;
     A.P = c->P;
     A.nloc = c->nloc;
@@ -953,13 +1294,42 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     A.HP = HP;
     A.smem = smem;
     const int grid = vmode ? (int)items.size() : nb;
-    OEFE_COUNTED k_build_cell<<<grid, BT, smem, c->stream>>>(A);
+    if (mode == 2) {
+      OefeArgs B;
+      B.leaves = c->d_leaves;
+      B.leaf_off = c->d_leaf_off;
+      B.qxyz = c->d_qxyz;
+      B.qw = c->d_qw;
+      B.veff = veff;
+      B.cellbox = c->d_cellbox;
+      B.gll = c->d_gll;
+      B.gauss_w = d_gw;
+      B.act_off = c->d_act_off;
+      B.NO = pairs ? (const void*)K.NOp : (const void*)K.NO;
+      B.no_cplx = K.cplx;
+      B.e0 = e0;
+      B.P = c->P;
+      B.nloc = c->nloc;
+      B.npad = c->npad;
+      B.ne_max = c->ne_max;
+      for (int d = 0; d < 3; ++d) B.k[d] = K.k[d];
+      B.HE = HE;
+      B.HP = HP;
+      B.E0 = (const cd*)K.E0;
+      B.items = d_items;
+      B.smem = smem;
+      if (pairs) OEFE_COUNTED k_build_oefe<f2><<<grid, BT, smem, c->stream>>>(B);
+      else OEFE_COUNTED k_build_oefe<double><<<grid, BT, smem, c->stream>>>(B);
+    } else {
+      OEFE_COUNTED k_build_cell<<<grid, BT, smem, c->stream>>>(A);
+    }
     OEFE_CUDA_TRY(c, cudaGetLastError());
     if (vmode && !red.empty()) {
-        const int nred = (int)red.size() / 3;
-        dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)c->npad * c->npad + 255) / 256)),
-               (unsigned)std::min(nred, 65535));
-      OEFE_COUNTED k_add_partials<<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
+      const int nred = (int)red.size() / 3;
+      dim3 g((unsigned)std::max<int64_t>(1, std::min<int64_t>(64, ((int64_t)c->npad * c->npad + 255) / 256)),
+             (unsigned)std::min(nred, 65535));
+      if (pairs) OEFE_COUNTED k_add_partials<f2><<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
+      else OEFE_COUNTED k_add_partials<double><<<g, 256, 0, c->stream>>>(HE, HP, d_red, nred, c->npad);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     StoreOut O;
@@ -973,8 +1343,10 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     O.ne_max = c->ne_max;
     O.E0 = nullptr;
     if (mode == 2) {
-      if (K.cplx) OEFE_COUNTED k_finish<cd><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
-      else OEFE_COUNTED k_finish<double><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
+      if (K.cplx && pairs) OEFE_COUNTED k_finish<cd, f2><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
+      else if (K.cplx) OEFE_COUNTED k_finish<cd, double><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
+      else if (pairs) OEFE_COUNTED k_finish<double, f2><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
+      else OEFE_COUNTED k_finish<double, double><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
       OEFE_CUDA_TRY(c, cudaGetLastError());
     }
     if (mode == 0) {
@@ -1135,6 +1507,7 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
     }
     K.bf_parts = parts;
     if (st == OEFE_OK) st = keep(&K.Hbf, parts > 0, n * sb / 4 * parts);
+    if (st == OEFE_OK && c->nO > 0) st = ensure_orth_enrichment(c, K);
     if (st == OEFE_OK) st = run_cell_kernel(c, K, 2, veff, d_gw, nullptr, nullptr, store);
     if (st != OEFE_OK) break;
     K.built = true;

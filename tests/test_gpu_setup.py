@@ -45,6 +45,33 @@ def test_cell_matrices(k):
         assert rel(H, pr.HO[e]) < 1e-12, e
 
 
+@pytest.mark.parametrize("k", KS)
+def test_cell_matrices_fp32_pair_build(k):
+    # the per-step build in FP32-pair arithmetic (u = 2^-48, 2^5 times the FP64 unit): the FP64
+    # tolerance scales by 32
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS, STORE_F64, STORE_F64PAIR
+    prs, ctx, V, Vd = paired(ks=[k])
+    pr = prs[0]
+    ctx.set_f64_products(F64_PAIRS)
+    ctx.build_hamiltonian(Vd, STORE_F64 | STORE_F64PAIR)
+    for e in range(pr.mesh.ncells):
+        assert rel(ctx.cell_matrix(0, e, complex_=pr.complex), pr.HO[e]) < 32e-12, e
+    ctx.set_f64_products(F64_NATIVE)
+
+
+def test_c1_pair_build_nucleus_cells():
+    # the refined cells (many leaves, partial sums) of the first configuration, pair arithmetic
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS, STORE_F64, STORE_F64PAIR
+    prs, ctx, V, Vd = c1_pair()
+    pr = prs[0]
+    ctx.set_f64_products(F64_PAIRS)
+    ctx.build_hamiltonian(Vd, STORE_F64 | STORE_F64PAIR)
+    cells = [e for e in range(pr.mesh.ncells) if pr.quad.cls[e] == 2][:4] + [5, 100, 511]
+    for e in cells:
+        assert rel(ctx.cell_matrix(0, e), pr.HO[e]) < 32e-12, e
+    ctx.set_f64_products(F64_NATIVE)
+
+
 def test_c1_cell_matrices_nucleus_cells():
     prs, ctx, V, _ = c1_pair()
     pr = prs[0]
