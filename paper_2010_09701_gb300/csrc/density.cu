@@ -23,6 +23,7 @@ constexpr int MAXN1 = 12;
 constexpr int DT = 256;
 constexpr int NBO = 4;   // columns of Gamma per pass of the tabulation
 constexpr int RNB = 4;   // vectors per pass of the fields
+constexpr int FT = 512;  // threads per CTA of the fields
 
 struct OrthArgs {
   EnrParams E;
@@ -164,7 +165,7 @@ struct FieldArgs {
 // Gauss points), enrichment part sum_j N^O_j(x_q) X^o_j with one point per thread over all RNB
 // vectors; |u|^2 weighted by occ accumulated per point. V = double: FP64; V = f2: FP32 pairs.
 template <typename V, bool CPLX>
-__global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
+__global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
   constexpr int R = CPLX ? 2 : 1;
   constexpr int J = RNB * R;
   using Acc = typename AccOf<V>::type;
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
   V* T1 = Xo + (size_t)A.ne_max * J;               // n1 * P * P * J   [qx][b][c][j]
   V* T2 = T1 + (size_t)n1m * P * P * J;            // n2 * P * J       [qx][qy][c][j]
   V* U = T2 + (size_t)n1m * n1m * P * J;           // n3 * J
-  V* rho = U + (size_t)n1m * n1m * n1m * J;        // n3
+  V* rho = U + (size_t)n1m * n1m * n1m * J;        // 2 x n3: one per half of the vectors
   for (int li = blockIdx.x; li < A.nleaves; li += gridDim.x) {
     const Leaf L = A.leaves[li];
     const int e = L.cell;
@@ -194,11 +195,11 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
       lagrange_eval(xn, P, xi, Lv, Dv);
       for (int a = 0; a < P; ++a) Lt[d][i][a] = v_from<V>(Lv[a]);
     }
-    for (int q = threadIdx.x; q < n3; q += DT) rho[q] = v_from<V>(0.0);
+    for (int q = threadIdx.x; q < 2 * n3; q += FT) rho[q] = v_from<V>(0.0);
     const size_t blk = (size_t)L.q0 * A.ne_max;
     for (int v0 = 0; v0 < A.nv; v0 += RNB) {
       __syncthreads();
-      for (int t = threadIdx.x; t < ne * RNB; t += DT) {
+      for (int t = threadIdx.x; t < ne * RNB; t += FT) {
         const int j = t / RNB, u = t % RNB;
         double xr = 0.0, xi = 0.0;
         if (v0 + u < A.nv) {
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
         Xo[(size_t)j * J + u * R] = v_from<V>(xr);
         if (CPLX) Xo[(size_t)j * J + u * R + 1] = v_from<V>(xi);
       }
-      for (int t = threadIdx.x; t < nloc * RNB; t += DT) {
+      for (int t = threadIdx.x; t < nloc * RNB; t += FT) {
         const int a = t / RNB, u = t % RNB;
         double xr = 0.0, xi = 0.0;
         if (v0 + u < A.nv) {
@@ -231,38 +232,41 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
         if (CPLX) Xt[(size_t)a * J + u * R + 1] = v_from<V>(xi);
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < n1 * P * P * J; t += DT) {   // x stage
+      for (int t = threadIdx.x; t < n1 * P * P * J; t += FT) {   // x stage
         const int j = t % J, r = t / J;
         const int c = r % P, bb = (r / P) % P, qx = r / (P * P);
         T1[t] = v_dot<V>(P, [&](int a) { return Lt[0][qx][a]; },
                          [&](int a) { return Xt[(size_t)(a + P * (bb + P * c)) * J + j]; });
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < n2 * P * J; t += DT) {       // y stage
+      for (int t = threadIdx.x; t < n2 * P * J; t += FT) {       // y stage
         const int j = t % J, r = t / J;
         const int c = r % P, qy = (r / P) % n1, qx = r / (P * n1);
         T2[t] = v_dot<V>(P, [&](int bb) { return Lt[1][qy][bb]; },
                          [&](int bb) { return T1[(size_t)((qx * P + bb) * P + c) * J + j]; });
       }
       __syncthreads();
-      for (int t = threadIdx.x; t < n3 * J; t += DT) {           // z stage
+      for (int t = threadIdx.x; t < n3 * J; t += FT) {           // z stage
         const int j = t % J, q = t / J;
         const int qx = q % n1, qy = (q / n1) % n1, qz = q / n2;
         U[t] = v_dot<V>(P, [&](int c) { return Lt[2][qz][c]; },
                         [&](int c) { return T2[(size_t)((qx * n1 + qy) * P + c) * J + j]; });
       }
       __syncthreads();
-      // enrichment part and |u|^2: one point per thread, all RNB vectors
-      for (int q = threadIdx.x; q < n3; q += DT) {
-        Acc y[J];
+      // enrichment part and |u|^2: items (point, half of the RNB vectors)
+      constexpr int HV = RNB / 2, HJ = HV * R;
+      for (int tq = threadIdx.x; tq < 2 * n3; tq += FT) {
+        const int q = tq >> 1, h = tq & 1;
+        Acc y[HJ];
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-          if constexpr (std::is_same<V, double>::value) y[j] = U[(size_t)q * J + j];
-          else y[j] = Acc{U[(size_t)q * J + j].h, U[(size_t)q * J + j].l};
+        for (int j = 0; j < HJ; ++j) {
+          const V u0 = U[(size_t)q * J + h * HJ + j];
+          if constexpr (std::is_same<V, double>::value) y[j] = u0;
+          else y[j] = Acc{u0.h, u0.l};
         }
         for (int jj = 0; jj < ne; ++jj) {
           const size_t o = blk + (size_t)jj * n3 + q;
-          const V* x = Xo + (size_t)jj * J;
+          const V* x = Xo + (size_t)jj * J + h * HJ;
           if constexpr (CPLX) {
             V nr, ni;
             if constexpr (std::is_same<V, double>::value) {
@@ -276,7 +280,7 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
             }
             const V nni = v_neg(ni);
 #pragma unroll
-            for (int u = 0; u < RNB; ++u) {
+            for (int u = 0; u < HV; ++u) {
               v_mac(y[2 * u], nr, x[2 * u]);
               v_mac(y[2 * u + 1], nr, x[2 * u + 1]);
               v_mac(y[2 * u], nni, x[2 * u + 1]);
@@ -291,13 +295,14 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
               nr = V{w.x, w.y};
             }
 #pragma unroll
-            for (int u = 0; u < RNB; ++u) v_mac(y[u], nr, x[u]);
+            for (int u = 0; u < HV; ++u) v_mac(y[u], nr, x[u]);
           }
         }
-        V s = rho[q];
+        V s = rho[h * n3 + q];
 #pragma unroll
-        for (int u = 0; u < RNB; ++u) {
-          if (v0 + u >= A.nv) continue;
+        for (int u = 0; u < HV; ++u) {
+          const int v = v0 + h * HV + u;
+          if (v >= A.nv) continue;
           Acc m = v_zero<V>();
           const V yr = v_fin(y[u * R]);
           v_mac(m, yr, yr);
@@ -305,17 +310,18 @@ __global__ void __launch_bounds__(DT) k_fields(FieldArgs A) {
             const V yi = v_fin(y[u * R + 1]);
             v_mac(m, yi, yi);
           }
-          const V w = v_from<V>(A.occ ? A.occ[v0 + u] : 1.0);
+          const V w = v_from<V>(A.occ ? A.occ[v] : 1.0);
           s = v_add(s, v_mul(w, v_fin(m)));
         }
-        rho[q] = s;
+        rho[h * n3 + q] = s;
       }
     }
     __syncthreads();
-    for (int q = threadIdx.x; q < n3; q += DT) {
+    for (int q = threadIdx.x; q < n3; q += FT) {
       const int64_t qg = L.q0 + q;
-      if (A.accumulate) A.out[qg] += v_to(rho[q]);
-      else A.out[qg] = A.qw[qg] * v_to(rho[q]);
+      const double r = v_to(v_add(rho[q], rho[n3 + q]));
+      if (A.accumulate) A.out[qg] += r;
+      else A.out[qg] = A.qw[qg] * r;
     }
   }
 }
@@ -326,7 +332,7 @@ size_t field_smem(const oefe_ctx* c, bool cplx) {
   const size_t J = (size_t)RNB * (cplx ? 2 : 1);
   const size_t n3 = (size_t)n1 * n1 * n1;
   return ((size_t)c->nloc * J + (size_t)std::max(c->ne_max, 1) * J + (size_t)n1 * P * P * J +
-          (size_t)n1 * n1 * P * J + n3 * J + n3) * sizeof(V);
+          (size_t)n1 * n1 * P * J + n3 * J + 2 * n3) * sizeof(V);
 }
 
 }  // namespace
@@ -405,7 +411,7 @@ int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, 
   auto go = [&](auto kern, size_t smem) -> int {
     if (smem > 227 * 1024) { c->err = "fields: quadrature too large for the interpolation tiles"; return OEFE_ERR_ARG; }
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    OEFE_COUNTED kern<<<grid, DT, smem, c->stream>>>(A);
+    OEFE_COUNTED kern<<<grid, FT, smem, c->stream>>>(A);
     OEFE_CUDA_TRY(c, cudaGetLastError());
     return OEFE_OK;
   };
