@@ -41,7 +41,27 @@ TRAFFIC_TENSOR = {   # bf16 parts of the split -> DRAM bytes per (k, cell, 64-ve
     3: {"bytes_per_tile": (3.064588e9 + 0.008374e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
 }
 TRAFFIC_FP64 = None   # {"bytes_per_cell", "source"} from a capture of the current FP64 product kernels
-TRAFFIC_PAIR = None   # the same for the FP32-pair products
+# the FP64-class products in pair mode: DRAM bytes per launch and cell of each kind, from the 8^3 capture
+TRAFFIC_PAIR = {"sf_bytes_per_cell": (343.697e6 + 150.831e6) / 448, "dense_bytes_per_cell": (319.123e6 + 23.752e6) / 64,
+                "source": "profiles/fp64_class_products_c3small_8cube_p6.md"}
+
+
+def nucleus_cells(w):
+    """Cells whose closed box holds a nucleus (periodic images included): the refined cells."""
+    xb = W.mesh_breakpoints(w)
+    tol = 1e-12 * w.a
+    hold = set()
+    for R in w.pos:
+        per_axis = []
+        for d in range(3):
+            x = R[d] % w.a
+            idx = [i for i in range(w.ncell) for y in (x - w.a, x, x + w.a) if xb[d][i] - tol <= y <= xb[d][i + 1] + tol]
+            per_axis.append(sorted(set(idx)))
+        for iz in per_axis[2]:
+            for iy in per_axis[1]:
+                for ix in per_axis[0]:
+                    hold.add((iz * w.ncell + iy) * w.ncell + ix)
+    return len(hold)
 
 
 def measured_peaks():
@@ -408,7 +428,15 @@ def run_ours(args, rank, world):
         fp64["product"] = {"kernel": "k_cell_apply_sf<double> + k_cell_apply_z3", "ms_per_launch": fp64_ms_launch,
                            "achieved_tflops": f64_ach, "frac_of_fp64_peak": f64_ach / FP64_PEAK_DERIVED}
         mix_ach = f64_flops / (mix_ms_launch * 1e-3) / 1e12
-        traffic = TRAFFIC_PAIR if pairs else TRAFFIC_FP64
+        n_dense = nucleus_cells(w)
+        n_sf = len(naug) - n_dense
+        traffic = None
+        if pairs and TRAFFIC_PAIR:
+            traffic = {"bytes": TRAFFIC_PAIR["sf_bytes_per_cell"] * n_sf + TRAFFIC_PAIR["dense_bytes_per_cell"] * n_dense,
+                       "source": TRAFFIC_PAIR["source"] + " (scaled by cells of each kind)"}
+        elif not pairs and TRAFFIC_FP64:
+            traffic = {"bytes": TRAFFIC_FP64["bytes_per_cell"] * len(naug),
+                       "source": TRAFFIC_FP64["source"] + " (scaled by cells)"}
         if pairs:
             # the refined cells (dense FP64) take a few percent of the launch; the peak is that of
             # the pair arithmetic on the FP32 pipe
@@ -422,8 +450,8 @@ def run_ours(args, rank, world):
         roof_fp64 = {"kernel": kname,
                      "bound": "alu", "achieved": mix_ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": mix_ach / peak,
-                     "traffic": traffic["bytes_per_cell"] * len(naug) if traffic else None,
-                     "traffic_source": traffic["source"] + " (scaled by cells)" if traffic else None,
+                     "traffic": traffic["bytes"] if traffic else None,
+                     "traffic_source": traffic["source"] if traffic else None,
                      "algorithmic_flops_per_launch": f64_flops, "ms_per_launch": mix_ms_launch,
                      "launches_per_step": 2 * nk,
                      "peak_source": psrc,
