@@ -39,6 +39,9 @@ static void free_all(oefe_ctx* c) {
   dev_free(c->d_sf_cells);
   dev_free(c->d_dense_cells);
   dev_free(c->d_sf_index);
+  dev_free(c->d_rotp);
+  c->d_rotp = nullptr;
+  c->rotp_bytes = 0;
   dev_free(c->d_veff);
 }
 

@@ -51,7 +51,16 @@ __global__ void k_hermitian_part(cd* A, int n) {
 }
 
 // Jacobi sweeps on A (n x n Hermitian, overwritten by its diagonal form), V <- eigenvectors.
-__global__ void __launch_bounds__(JT) k_jacobi(cd* A, cd* V, int n, int max_sweeps, double tol, int* sweeps_out) {
+// SM: A and V are staged in shared memory for the sweeps (when 2 n^2 complex values fit).
+template <bool SM>
+__global__ void __launch_bounds__(JT) k_jacobi(cd* Ag, cd* Vg, int n, int max_sweeps, double tol, int* sweeps_out) {
+  extern __shared__ cd jsm[];
+  cd* A = SM ? jsm : Ag;
+  cd* V = SM ? jsm + (size_t)n * n : Vg;
+  if (SM) {
+    for (int t = threadIdx.x; t < n * n; t += JT) A[t] = Ag[t];
+    __syncthreads();
+  }
   __shared__ double red[JT];
   __shared__ double cs_[MAXPAIRS], sn_[MAXPAIRS];
   __shared__ cd u_[MAXPAIRS];
@@ -133,6 +142,13 @@ __global__ void __launch_bounds__(JT) k_jacobi(cd* A, cd* V, int n, int max_swee
     }
   }
   if (tid == 0) *sweeps_out = sweep;
+  if (SM) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += JT) {
+      Ag[t] = A[t];
+      Vg[t] = V[t];
+    }
+  }
 }
 
 // ascending order: rank of each diagonal entry (ties by index), then permute
@@ -241,7 +257,13 @@ int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* 
     OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(Y, false, Hc, false, T, n);  // T = L^{-1} H
     OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(T, false, Y, true, Hc, n);   // C = T L^{-+}
     OEFE_COUNTED k_hermitian_part<<<g, b, 0, c->stream>>>(Hc, n);
-    OEFE_COUNTED k_jacobi<<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+    const size_t jsm = 2 * nn * sizeof(cd);
+    if (jsm <= 200 * 1024) {
+      cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+      OEFE_COUNTED k_jacobi<true><<<1, JT, jsm, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+    } else {
+      OEFE_COUNTED k_jacobi<false><<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+    }
     OEFE_COUNTED k_sort_eig<<<(n + 127) / 128, 128, 0, c->stream>>>(Hc, W, n, d_eps, Ws);
     OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(Y, true, Ws, false, T, n);   // U = L^{-+} W
     OEFE_COUNTED k_from_cd<S><<<g, b, 0, c->stream>>>(T, U, (int)nn);

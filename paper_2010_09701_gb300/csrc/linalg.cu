@@ -275,22 +275,28 @@ __global__ void __launch_bounds__(256) k_gram_pair(const S* X, int ldx, const S*
     }
 }
 
-// X[rows] <- X[rows] C (or X C^+ with herm, C lower triangular) in pairs: C transposed into shared
-// memory once per CTA (Ct[k][j], consecutive j contiguous), rows staged, each thread one column j
-// of two rows.
+// The small matrix of a rotation as pairs, transposed so that consecutive j are contiguous:
+// Ct[k][j] = C[k][j], or conj(C[j][k]) for k <= j (herm, C lower triangular).
+template <typename S>
+__global__ void k_rot_pairs(const S* C, int nv, bool herm, c2* Ct) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv * nv) return;
+  const int k = t / nv, j = t % nv;
+  Ct[t] = herm ? (k <= j ? to_c2(Ops<S>::conj(C[(size_t)j * nv + k])) : to_c2(Ops<S>::zero()))
+               : to_c2(C[(size_t)k * nv + j]);
+}
+
+// X[rows] <- X[rows] C (or X C^+ with herm) in pairs: Ct (k_rot_pairs) copied into shared memory
+// once per CTA, rows staged, each thread one column j of two rows.
 constexpr int RPT = 512;
 template <typename S>
-__global__ void __launch_bounds__(RPT) k_rotate_pair(S* X, int ldx, int64_t n, int nv, const S* C, bool herm,
+__global__ void __launch_bounds__(RPT) k_rotate_pair(S* X, int ldx, int64_t n, int nv, const c2* Cp, bool herm,
                                                      int rows) {
   constexpr bool CPLX = sizeof(S) == sizeof(cd);
   extern __shared__ unsigned char sm[];
   c2* Ct = reinterpret_cast<c2*>(sm);            // nv * nv
   c2* xs = Ct + (size_t)nv * nv;                 // rows * nv
-  for (int t = threadIdx.x; t < nv * nv; t += RPT) {
-    const int k = t / nv, j = t % nv;
-    Ct[t] = herm ? (k <= j ? to_c2(Ops<S>::conj(C[(size_t)j * nv + k])) : to_c2(Ops<S>::zero()))
-                 : to_c2(C[(size_t)k * nv + j]);
-  }
+  for (int t = threadIdx.x; t < nv * nv; t += RPT) Ct[t] = Cp[t];
   const int64_t r0 = (int64_t)blockIdx.x * rows;
   const int nr = (int)min((int64_t)rows, n - r0);
   if (nr <= 0) return;
@@ -447,14 +453,28 @@ int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int n
 template <typename S>
 int rotate(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm) {
   if (c->f64_products == OEFE_F64_PAIRS) {
-    // pairs: C (transposed) and the staged rows in shared memory, when C leaves room for 32 rows
+    // pairs: C (transposed, as pairs) and the staged rows in shared memory; rows per CTA such that
+    // two CTAs share an SM (one stages while the other computes), else as many as fit
     const size_t cb = (size_t)nv * nv * sizeof(c2);
-    const int prow = (int)std::min<int64_t>(256, ((size_t)200 * 1024 - std::min<size_t>(cb, 200 * 1024)) / ((size_t)nv * sizeof(c2)));
-    if (cb < 200 * 1024 && prow >= 32) {
+    const size_t rb = (size_t)nv * sizeof(c2);
+    int prow = cb < 110 * 1024 ? (int)((110 * 1024 - cb) / rb) : 0;
+    if (prow < 16) prow = cb < 200 * 1024 ? (int)((200 * 1024 - cb) / rb) : 0;
+    prow = std::min(prow, 256);
+    if (prow >= 16) {
+      if (c->rotp_bytes < cb) {
+        cudaStreamSynchronize(c->stream);
+        dev_free(c->d_rotp);
+        c->d_rotp = nullptr;
+        c->rotp_bytes = 0;
+        OEFE_TRY(dev_alloc(c, &c->d_rotp, cb));
+        c->rotp_bytes = cb;
+      }
+      c2* Cp = (c2*)c->d_rotp;
+      OEFE_COUNTED k_rot_pairs<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(C, nv, herm, Cp);
       const int64_t blocks = (n + prow - 1) / prow;
-      const size_t smem = cb + (size_t)prow * nv * sizeof(c2);
+      const size_t smem = cb + (size_t)prow * rb;
       OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_rotate_pair<S>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      OEFE_COUNTED k_rotate_pair<S><<<(unsigned)blocks, RPT, smem, c->stream>>>(X, ldx, n, nv, C, herm, prow);
+      OEFE_COUNTED k_rotate_pair<S><<<(unsigned)blocks, RPT, smem, c->stream>>>(X, ldx, n, nv, Cp, herm, prow);
       OEFE_CUDA_TRY(c, cudaGetLastError());
       return OEFE_OK;
     }

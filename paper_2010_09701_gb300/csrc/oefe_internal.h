@@ -158,6 +158,8 @@ struct oefe_ctx {
   size_t ws_bytes = 0;
   void* ws2 = nullptr;
   size_t ws2_bytes = 0;
+  void* d_rotp = nullptr;               // the small matrix of a pair rotation, as pairs
+  size_t rotp_bytes = 0;
   int* d_status = nullptr;        // device status word (Cholesky failures, timeouts)
 
   // optional event timing of the cell-product launches
@@ -180,6 +182,7 @@ struct oefe_ctx {
   // sum-factorized FP64 products on single-leaf cells (sumfac.cu)
   int use_sumfac = 1;
   int f64_products = OEFE_F64_NATIVE;   // arithmetic of the sum-factorized FP64 products
+  int sf_variant = -1;                  // launch shape of the pair product: chosen by timing at first use
   double* d_sf = nullptr;               // per single-leaf cell: n1, 1D tables, M/K/A
   int* d_sf_cells = nullptr;            // single-leaf cells
   int* d_dense_cells = nullptr;         // cells with several leaves (dense products)
