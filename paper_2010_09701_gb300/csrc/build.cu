@@ -519,15 +519,20 @@ __global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
   __shared__ V Mm[3][MAXP][MAXP], Gr[3][MAXP][MAXP], Gi[3][MAXP][MAXP];   // M, K/2, -(k/2) A
   if (threadIdx.x < P) xn[threadIdx.x] = A.gll[threadIdx.x];
 
+  // The item's first leaf writes every entry the store reads (CC, CO, OO; OC is CO^+), later leaves
+  // add to them; the padding is never read.
   VC<V>* HE = reinterpret_cast<VC<V>*>(it.slot < 0 ? A.HE : A.HP) +
               (size_t)(it.slot < 0 ? b : it.slot) * npad * npad;
-  for (int i = threadIdx.x; i < npad * npad; i += BT) HE[i] = VC<V>{v_from<V>(0.0), v_from<V>(0.0)};
-  __syncthreads();
 
   for (int li = it.l0; li < it.l1; ++li) {
     const Leaf L = A.leaves[li];
     const int n1 = L.n1, n2 = n1 * n1, n3 = n2 * n1;
     const int64_t q0 = L.q0;
+    const bool fst = li == it.l0;
+    auto put = [&](VC<V>* h, V re, V im) {
+      if (fst) *h = VC<V>{re, im};
+      else vc_add(h, re, im);
+    };
     if (threadIdx.x < 3 * n1) {
       const int d = threadIdx.x / n1, i = threadIdx.x % n1;
       const int64_t qi = q0 + (d == 0 ? i : d == 1 ? i * n1 : i * n2);
@@ -612,21 +617,30 @@ __global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
             im = v_fin(ki);
           }
         }
-        vc_add(HE + (size_t)m * npad + n, re, im);
-        if (m != n) vc_add(HE + (size_t)n * npad + m, re, v_neg(im));
+        if (fst && first) {
+          HE[(size_t)m * npad + n] = VC<V>{re, im};
+          if (m != n) HE[(size_t)n * npad + m] = VC<V>{re, v_neg(im)};
+        } else {
+          vc_add(HE + (size_t)m * npad + n, re, im);
+          if (m != n) vc_add(HE + (size_t)n * npad + m, re, v_neg(im));
+        }
       }
       __syncthreads();
     }
 
-    // ---- CO: column j of the V term, F_q = w_q V_q N^O_j(x_q), staged z, y, x
+    // ---- CO: column j of the V term, F_q = w_q V_q N^O_j(x_q), staged z, y, x. The weights w_q V_q
+    //      of the leaf sit at the end of the shared memory (the CC stage is done with it) for CO and OO
     const size_t blk = (size_t)q0 * A.ne_max;
+    V* WVs = smem + A.smem / sizeof(V) - n3;
+    for (int q = threadIdx.x; q < n3; q += BT) WVs[q] = v_from<V>(A.qw[q0 + q] * A.veff[q0 + q]);
+    __syncthreads();
     {
       VC<V>* F = reinterpret_cast<VC<V>*>(smem);    // n3
       VC<V>* G = F + n3;                            // n2 * P
       VC<V>* H = G + n2 * P;                        // n1 * P * P
       for (int j = 0; j < ne; ++j) {
         for (int q = threadIdx.x; q < n3; q += BT) {
-          const V w = v_from<V>(A.qw[q0 + q] * A.veff[q0 + q]);
+          const V w = WVs[q];
           const VC<V> nv = load_no<V>(A, blk + (size_t)j * n3 + q);
           F[q] = VC<V>{v_mul(w, nv.re), v_mul(w, nv.im)};
         }
@@ -662,7 +676,7 @@ __global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
             v_mac(sr, Lt[0][qx][a], h.re);
             v_mac(si, Lt[0][qx][a], h.im);
           }
-          vc_add(HE + (size_t)m * npad + nloc + j, v_fin(sr), v_fin(si));
+          put(HE + (size_t)m * npad + nloc + j, v_fin(sr), v_fin(si));
         }
         __syncthreads();
       }
@@ -670,7 +684,7 @@ __global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
 
     // ---- OO: pairs (i <= j) over the leaf points in chunks, with w V N^O_i staged beside N^O_i
     {
-      const int QC = max(1, min(32, (int)((A.smem - 64) / ((size_t)max(ne, 1) * 2 * sizeof(VC<V>)))));
+      const int QC = max(1, min(32, (int)((A.smem - (size_t)n3 * sizeof(V) - 64) / ((size_t)max(ne, 1) * 2 * sizeof(VC<V>)))));
       VC<V>* Ns = reinterpret_cast<VC<V>*>(smem);   // QC x ne
       VC<V>* Nw = Ns + (size_t)QC * ne;             // QC x ne: w V N
       const int npairs = ne * (ne + 1) / 2;
@@ -695,7 +709,7 @@ __global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
           for (int t = threadIdx.x; t < nq * ne; t += BT) {
             const int q = t / ne, j = t % ne;
             const VC<V> nv = load_no<V>(A, blk + (size_t)j * n3 + qc + q);
-            const V w = v_from<V>(A.qw[q0 + qc + q] * A.veff[q0 + qc + q]);
+            const V w = WVs[qc + q];
             Ns[t] = nv;
             Nw[t] = VC<V>{v_mul(w, nv.re), v_mul(w, nv.im)};
           }
@@ -716,8 +730,8 @@ __global__ void __launch_bounds__(BT) k_build_oefe(OefeArgs A) {
           if (pi[u] < 0) continue;
           const int i = pi[u], j = pj[u];
           const V re = v_fin(ar[u]), im = v_fin(ai[u]);
-          vc_add(HE + (size_t)(nloc + i) * npad + nloc + j, re, im);
-          if (i != j) vc_add(HE + (size_t)(nloc + j) * npad + nloc + i, re, v_neg(im));
+          put(HE + (size_t)(nloc + i) * npad + nloc + j, re, im);
+          if (i != j) put(HE + (size_t)(nloc + j) * npad + nloc + i, re, v_neg(im));
         }
       }
       __syncthreads();
