@@ -7,6 +7,7 @@
 #include <cmath>
 
 #include "oefe_internal.h"
+#include "pair_dev.cuh"
 
 namespace {
 
@@ -52,13 +53,18 @@ __global__ void k_hermitian_part(cd* A, int n) {
 
 // Jacobi sweeps on A (n x n Hermitian, overwritten by its diagonal form), V <- eigenvectors.
 // SM: A and V are staged in shared memory for the sweeps (when 2 n^2 complex values fit).
+// init_v: start from V = I; otherwise from the V given (the sweeps continue an earlier phase).
 template <bool SM>
-__global__ void __launch_bounds__(JT) k_jacobi(cd* Ag, cd* Vg, int n, int max_sweeps, double tol, int* sweeps_out) {
+__global__ void __launch_bounds__(JT) k_jacobi(cd* Ag, cd* Vg, int n, int max_sweeps, double tol, int* sweeps_out,
+                                               bool init_v) {
   extern __shared__ cd jsm[];
   cd* A = SM ? jsm : Ag;
   cd* V = SM ? jsm + (size_t)n * n : Vg;
   if (SM) {
-    for (int t = threadIdx.x; t < n * n; t += JT) A[t] = Ag[t];
+    for (int t = threadIdx.x; t < n * n; t += JT) {
+      A[t] = Ag[t];
+      if (!init_v) V[t] = Vg[t];
+    }
     __syncthreads();
   }
   __shared__ double red[JT];
@@ -68,7 +74,8 @@ __global__ void __launch_bounds__(JT) k_jacobi(cd* Ag, cd* Vg, int n, int max_sw
   const int tid = threadIdx.x;
   const int m = n + (n & 1);  // even number of players; player n is a bye when n is odd
   const int np = m / 2;
-  for (int t = tid; t < n * n; t += JT) V[t] = (t / n == t % n) ? mkc(1, 0) : mkc(0, 0);
+  if (init_v)
+    for (int t = tid; t < n * n; t += JT) V[t] = (t / n == t % n) ? mkc(1, 0) : mkc(0, 0);
   double fro = 0;
   for (int t = tid; t < n * n; t += JT) fro += cabs2(A[t]);
   fro = block_sum(fro, red);
@@ -148,6 +155,125 @@ __global__ void __launch_bounds__(JT) k_jacobi(cd* Ag, cd* Vg, int n, int max_sw
       Ag[t] = A[t];
       Vg[t] = V[t];
     }
+  }
+}
+
+
+// ---- the first sweeps in FP32-pair arithmetic (pair_dev.cuh), on the FP32 pipe: the same rotations
+// (parameters taken in FP64 from the current entries), the row and column updates in pairs, until
+// the off-diagonal part is below tol (about the pair precision); the FP64 sweeps of k_jacobi then
+// continue from A and V to FP64 accuracy.
+struct c2j {
+  f2 r, i;
+};
+__device__ __forceinline__ c2j c2j_from(cd a) { return c2j{f2_from(a.x), f2_from(a.y)}; }
+__device__ __forceinline__ cd c2j_to(c2j a) { return mkc(f2_to(a.r), f2_to(a.i)); }
+// x a + conj(g) b
+__device__ __forceinline__ c2j rot_c(f2 x, c2j a, c2j g, c2j b) {
+  f2acc r{0.0f, 0.0f}, i{0.0f, 0.0f};
+  f2_mac(r, x, a.r);
+  f2_mac(r, g.r, b.r);
+  f2_mac(r, g.i, b.i);
+  f2_mac(i, x, a.i);
+  f2_mac(i, g.r, b.i);
+  f2_mac(i, f2_neg(g.i), b.r);
+  return c2j{f2_fin(r), f2_fin(i)};
+}
+// x a + b g
+__device__ __forceinline__ c2j rot_n(f2 x, c2j a, c2j b, c2j g) {
+  f2acc r{0.0f, 0.0f}, i{0.0f, 0.0f};
+  f2_mac(r, x, a.r);
+  f2_mac(r, b.r, g.r);
+  f2_mac(r, f2_neg(b.i), g.i);
+  f2_mac(i, x, a.i);
+  f2_mac(i, b.r, g.i);
+  f2_mac(i, b.i, g.r);
+  return c2j{f2_fin(r), f2_fin(i)};
+}
+
+__global__ void __launch_bounds__(JT) k_jacobi_pair(cd* Ag, cd* Vg, int n, int max_sweeps, double tol) {
+  extern __shared__ cd jsm[];
+  c2j* A = reinterpret_cast<c2j*>(jsm);
+  c2j* V = A + (size_t)n * n;
+  __shared__ double red[JT];
+  __shared__ f2 cs_[MAXPAIRS], sn_[MAXPAIRS];
+  __shared__ c2j g10_[MAXPAIRS], g11_[MAXPAIRS];
+  __shared__ int p_[MAXPAIRS], q_[MAXPAIRS];
+  const int tid = threadIdx.x;
+  const int m = n + (n & 1);
+  const int np = m / 2;
+  double fro = 0;
+  for (int t = tid; t < n * n; t += JT) {
+    const cd a = Ag[t];
+    A[t] = c2j_from(a);
+    V[t] = c2j_from((t / n == t % n) ? mkc(1, 0) : mkc(0, 0));
+    fro += cabs2(a);
+  }
+  fro = block_sum(fro, red);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0;
+    for (int t = tid; t < n * n; t += JT)
+      if (t / n != t % n) off += cabs2(c2j_to(A[t]));
+    off = block_sum(off, red);
+    if (off <= tol * tol * fro || off == 0.0) break;
+    for (int r = 0; r < m - 1; ++r) {
+      for (int k = tid; k < np; k += JT) {
+        const int a = k == 0 ? m - 1 : (k - 1 + r) % (m - 1);
+        const int b = (m - 1 - k - 1 + r) % (m - 1);
+        int p = min(a, b), q = max(a, b);
+        if (q >= n) { p_[k] = -1; continue; }
+        const cd bpq = c2j_to(A[(size_t)p * n + q]);
+        const double beta = sqrt(cabs2(bpq));
+        if (beta < 1e-300) { p_[k] = -1; continue; }
+        const cd u = (1.0 / beta) * bpq;
+        const double tau = (f2_to(A[(size_t)q * n + q].r) - f2_to(A[(size_t)p * n + p].r)) / (2.0 * beta);
+        const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+        const double c = 1.0 / sqrt(1.0 + tt * tt), s = tt * c;
+        const cd ub = cconj(u);
+        p_[k] = p;
+        q_[k] = q;
+        cs_[k] = f2_from(c);
+        sn_[k] = f2_from(s);
+        g10_[k] = c2j_from(-s * ub);
+        g11_[k] = c2j_from(c * ub);
+      }
+      __syncthreads();
+      for (int t = tid; t < np * n; t += JT) {   // rows: A <- G^+ A
+        const int k = t / n, j = t % n;
+        const int p = p_[k];
+        if (p < 0) continue;
+        const int q = q_[k];
+        const c2j apj = A[(size_t)p * n + j], aqj = A[(size_t)q * n + j];
+        A[(size_t)p * n + j] = rot_c(cs_[k], apj, g10_[k], aqj);
+        A[(size_t)q * n + j] = rot_c(sn_[k], apj, g11_[k], aqj);
+      }
+      __syncthreads();
+      for (int t = tid; t < np * n; t += JT) {   // columns: A <- A G, V <- V G
+        const int k = t / n, i = t % n;
+        const int p = p_[k];
+        if (p < 0) continue;
+        const int q = q_[k];
+        const c2j aip = A[(size_t)i * n + p], aiq = A[(size_t)i * n + q];
+        A[(size_t)i * n + p] = rot_n(cs_[k], aip, aiq, g10_[k]);
+        A[(size_t)i * n + q] = rot_n(sn_[k], aip, aiq, g11_[k]);
+        const c2j vip = V[(size_t)i * n + p], viq = V[(size_t)i * n + q];
+        V[(size_t)i * n + p] = rot_n(cs_[k], vip, viq, g10_[k]);
+        V[(size_t)i * n + q] = rot_n(sn_[k], vip, viq, g11_[k]);
+      }
+      __syncthreads();
+      for (int k = tid; k < np; k += JT) {
+        const int p = p_[k];
+        if (p < 0) continue;
+        A[(size_t)p * n + q_[k]] = c2j{f2{0.0f, 0.0f}, f2{0.0f, 0.0f}};
+        A[(size_t)q_[k] * n + p] = c2j{f2{0.0f, 0.0f}, f2{0.0f, 0.0f}};
+      }
+      __syncthreads();
+    }
+  }
+  __syncthreads();
+  for (int t = tid; t < n * n; t += JT) {
+    Ag[t] = c2j_to(A[t]);
+    Vg[t] = c2j_to(V[t]);
   }
 }
 
@@ -260,9 +386,16 @@ int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* 
     const size_t jsm = 2 * nn * sizeof(cd);
     if (jsm <= 200 * 1024) {
       cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
-      OEFE_COUNTED k_jacobi<true><<<1, JT, jsm, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+      bool init_v = true;
+      if (c->f64_products == OEFE_F64_PAIRS) {
+        // the sweeps down to about the pair precision on the FP32 pipe, the rest in FP64
+        cudaFuncSetAttribute(k_jacobi_pair, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)jsm);
+        OEFE_COUNTED k_jacobi_pair<<<1, JT, jsm, c->stream>>>(Hc, W, n, 40, 1e-12);
+        init_v = false;
+      }
+      OEFE_COUNTED k_jacobi<true><<<1, JT, jsm, c->stream>>>(Hc, W, n, 40, 1e-15, d_int, init_v);
     } else {
-      OEFE_COUNTED k_jacobi<false><<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int);
+      OEFE_COUNTED k_jacobi<false><<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int, true);
     }
     OEFE_COUNTED k_sort_eig<<<(n + 127) / 128, 128, 0, c->stream>>>(Hc, W, n, d_eps, Ws);
     OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(Y, true, Ws, false, T, n);   // U = L^{-+} W
