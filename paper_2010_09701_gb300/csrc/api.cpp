@@ -42,6 +42,9 @@ static void free_all(oefe_ctx* c) {
   dev_free(c->d_rotp);
   c->d_rotp = nullptr;
   c->rotp_bytes = 0;
+  dev_free(c->d_ozpart);
+  c->d_ozpart = nullptr;
+  c->ozpart_bytes = 0;
   dev_free(c->d_veff);
 }
 

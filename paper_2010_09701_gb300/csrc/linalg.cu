@@ -438,6 +438,11 @@ __global__ void k_dot_final(const double* part, int nb, double* out) {
 template <typename S>
 int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, S* part_buf,
          int nchunk, bool herm = true) {
+  if (c->f64_products == OEFE_F64_PAIRS) {   // FP64-class on the tensor cores (exact bf16 digits)
+    bool done = false;
+    OEFE_TRY(gram_ozaki<S>(c, X, ldx, W, ldw, n, nv, out, &done));
+    if (done) return OEFE_OK;
+  }
   const int tiles = (nv + GT - 1) / GT;
   const int64_t rpc = (n + nchunk - 1) / nchunk;
   dim3 grid(nchunk, herm ? tiles * (tiles + 1) / 2 : tiles, herm ? 1 : tiles);

@@ -160,6 +160,8 @@ struct oefe_ctx {
   size_t ws2_bytes = 0;
   void* d_rotp = nullptr;               // the small matrix of a pair rotation, as pairs
   size_t rotp_bytes = 0;
+  void* d_ozpart = nullptr;             // partial sums of the tensor-core Gram matrices
+  size_t ozpart_bytes = 0;
   int* d_status = nullptr;        // device status word (Cholesky failures, timeouts)
 
   // optional event timing of the cell-product launches
@@ -223,6 +225,8 @@ void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w);
 // build (build.cu)
 int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w);
 int ensure_orth_enrichment(oefe_ctx* c, KData& K);
+template <typename S>
+int gram_ozaki(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, bool* done);
 int build_hamiltonian(oefe_ctx* c, const double* veff, int store);
 
 // dense helpers (linalg.cu)

@@ -1,0 +1,345 @@
+// FP64-class Gram matrices S = X^+ W of the subspace linear algebra (Sec. IV: Cholesky-QR and the
+// projected matrices of Rayleigh-Ritz) on the tensor cores, by exact slicing of the operands
+// (the Ozaki scheme).
+//
+// Real form: with A = [Re X | Im X]^T (2 nv rows) and B = [Re W | Im W] (2 nv columns),
+// D = A B over the n rows gives Re S = D[i][j] + D[nv+i][nv+j] and Im S = D[i][nv+j] - D[nv+i][j].
+// Per pass of 64 rows, each row of A (each column of B) is written as 7 digits of 7 bits with a
+// common exponent E_i (F_j):  x = 2^(E-49) (c0 2^42 + c1 2^35 + ... + c6), c0 in [-128, 127], the
+// others in [0, 127], exact to 2^(E-49) (truncation of x 2^(49-E) to an integer, taken from the
+// bits of x by integer operations). A digit is exact
+// in bf16; a product of two digits is below 2^14; the sum that one accumulator of level d = s + t
+// (at most 7 digit pairs) takes over 64 rows stays below 2^24, so the FP32 accumulation of the
+// tensor cores is exact. The levels d = 0..6 (28 digit products) are kept, the rest (below
+// 2^-49 of the row and column maxima) dropped; the levels are combined in FP32-pair arithmetic
+// and summed over the passes in pairs. Error: about 2^-46 of |x|max |w|max per term.
+//
+// Two kernels. k_oz_digits (one CTA per pass of 64 rows) writes the digit planes of an operand to
+// global memory, already in the 128-byte-swizzled K-major layout the MMA reads, with the
+// exponent of each operand row; it touches FP64 values only through their bits (integer
+// operations). k_gram_oz (one CTA of 128 threads per (block of passes, half): half 0 takes the
+// real parts of W's columns, half 1 the imaginary parts) streams the planes of each pass into
+// shared memory with bulk copies; thread 0 issues the 112 MMAs (M 128, N 64, K 16) into 7
+// tensor-memory accumulators (448 columns); while every thread reads its accumulator row and adds
+// the combined pass to its running sums in pairs, the next pass's planes are already on their
+// way. Every wait is bounded; on a timeout the CTA raises the error flag, waits for its copies and
+// MMAs in flight and frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "oefe_internal.h"
+#include "pair_dev.cuh"
+#include "tcgen05_dev.cuh"
+
+namespace {
+
+constexpr int OZ_T = 128;           // threads per CTA of the MMA kernel
+constexpr int OZ_K = 64;            // rows per pass (one 128-byte swizzle row of bf16)
+constexpr int OZ_S = 7;             // digits per value
+constexpr int OZ_N = 64;            // columns of B per CTA
+constexpr int PL = 128 * 128;       // one digit plane: 128 operand rows x 64 bf16
+constexpr int PASS_BYTES = OZ_S * PL;
+constexpr int BH = OZ_N * 128;      // the half of a plane one CTA takes from B
+constexpr size_t OZ_SMEM = 1024 + (size_t)PASS_BYTES + (size_t)OZ_S * BH;
+constexpr int OZ_TCOLS = 512;       // tensor-memory columns (7 x 64 used)
+constexpr int DG_T = 256;           // threads per CTA of the digits kernel
+
+__device__ __forceinline__ double ld_part(const void* M, int ld, long long r, int c, int part, bool cplx) {
+  if (cplx) {
+    const cd v = reinterpret_cast<const cd*>(M)[r * ld + c];
+    return part ? v.y : v.x;
+  }
+  return reinterpret_cast<const double*>(M)[r * ld + c];
+}
+
+// Y = trunc(x 2^(49-E)) from the bits of x by integer operations only (|x| < 2^E; subnormals
+// count as zero), then the digits: c0 signed, the rest non-negative (two's complement split)
+__device__ __forceinline__ void digits7(unsigned long long b, int E, float c[OZ_S]) {
+  const int ex = (int)((b >> 52) & 0x7FF);
+  const int sh = 1026 - ex + E;                         // >= 4 since |x| < 2^E
+  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const unsigned long long ya = (ex == 0 || sh >= 64) ? 0ull : (mant >> sh);
+  const long long Y = (b >> 63) ? -(long long)ya : (long long)ya;
+  c[0] = (float)(Y >> 42);
+#pragma unroll
+  for (int s = 1; s < OZ_S; ++s) c[s] = (float)((Y >> (42 - 7 * s)) & 127);
+}
+
+struct DigArgs {
+  const void* M;
+  int ld;
+  long long n;
+  int nv;
+  bool cplx;
+  bool right;                // operand rows: left (X): [Re cols | Im cols]; right (W): half h = row / 64
+  unsigned char* planes;     // per pass PASS_BYTES
+  int* exps;                 // per pass 128
+};
+
+// operand row r -> (column, part) of M, or -1 when the row is zero
+__device__ __forceinline__ int op_col(const DigArgs& D, int r, int* part) {
+  if (D.right) {
+    *part = r / OZ_N;
+    const int c = r % OZ_N;
+    return (c < D.nv && (D.cplx || *part == 0)) ? c : -1;
+  }
+  if (D.cplx) {
+    *part = r / max(D.nv, 1);
+    return r < 2 * D.nv ? r % D.nv : -1;
+  }
+  *part = 0;
+  return r < D.nv ? r : -1;
+}
+
+__global__ void __launch_bounds__(DG_T) k_oz_digits(const DigArgs D) {
+  extern __shared__ unsigned long long dbits[];    // [64 k][129]: bits of the pass, padded
+  __shared__ int sE[128];
+  const long long p = blockIdx.x, r0 = p * OZ_K;
+  const int nk = (int)min((long long)OZ_K, D.n - r0);
+  for (int t = threadIdx.x; t < OZ_K * 128; t += DG_T) {
+    const int k = t / 128, r = t % 128;
+    int part;
+    const int c = op_col(D, r, &part);
+    dbits[k * 129 + r] = (c >= 0 && k < nk) ? (unsigned long long)__double_as_longlong(ld_part(D.M, D.ld, r0 + k, c, part, D.cplx))
+                                            : 0ull;
+  }
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    int mex = 0;
+    for (int k = 0; k < OZ_K; ++k) mex = max(mex, (int)((dbits[k * 129 + threadIdx.x] >> 52) & 0x7FF));
+    const int E = mex ? mex - 1022 : 0;
+    sE[threadIdx.x] = E;
+    D.exps[p * 128 + threadIdx.x] = E;
+  }
+  __syncthreads();
+  unsigned char* base = D.planes + (size_t)p * PASS_BYTES;
+  for (int t = threadIdx.x; t < 128 * (OZ_K / 2); t += DG_T) {   // a warp: one row, 32 pairs of k
+    const int r = t / (OZ_K / 2), kp = t % (OZ_K / 2);
+    float c0[OZ_S], c1[OZ_S];
+    digits7(dbits[(2 * kp) * 129 + r], sE[r], c0);
+    digits7(dbits[(2 * kp + 1) * 129 + r], sE[r], c1);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s)
+      *reinterpret_cast<__nv_bfloat162*>(base + (size_t)s * PL + swz(r, 2 * kp)) = __floats2bfloat162_rn(c0[s], c1[s]);
+  }
+}
+
+__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
+struct OzArgs {
+  const unsigned char* pa;   // digit planes of X (left operand), per pass PASS_BYTES
+  const int* ea;             // exponents of X's operand rows, per pass 128
+  const unsigned char* pb;   // digit planes of W (right operand)
+  const int* eb;
+  long long passes;
+  long long passes_per_cta;
+  bool cplx;
+  int nv;
+  double* part;              // (halves, blocks, 128, 64)
+  int* err;
+};
+
+__global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
+  extern __shared__ __align__(1024) unsigned char oz_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + PASS_BYTES;
+  __shared__ int Fexp[OZ_N];
+  __shared__ uint64_t ld_bar, mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int half = blockIdx.y;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(OZ_TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&ld_bar, 1);
+    mbar_init(&mma_bar, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = tmem_slot;
+
+  const long long pb = (long long)blockIdx.x * A.passes_per_cta, pe = min(A.passes, pb + A.passes_per_cta);
+  const int nrowA = A.cplx ? 2 * A.nv : A.nv;
+  auto load_pass = [&](long long p) {   // thread 0: the planes of pass p into shared memory
+    mbar_expect_tx(&ld_bar, (uint32_t)(PASS_BYTES + OZ_S * BH));
+    bulk_copy(smem_u32(sA), A.pa + (size_t)p * PASS_BYTES, PASS_BYTES, &ld_bar);
+    for (int s = 0; s < OZ_S; ++s)
+      bulk_copy(smem_u32(sB + s * BH), A.pb + (size_t)p * PASS_BYTES + (size_t)s * PL + (size_t)half * BH, BH, &ld_bar);
+  };
+  if (tid == 0 && pb < pe) load_pass(pb);
+  f2 R[OZ_N];
+#pragma unroll
+  for (int j = 0; j < OZ_N; ++j) R[j] = f2{0.0f, 0.0f};
+  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  constexpr uint32_t ID = idesc_bf16(128, OZ_N, false);
+  int it = 0;
+  bool loads_out = pb < pe, mma_out = false;
+  for (long long p = pb; p < pe; ++p, ++it) {
+    bool ok = mbar_wait(&ld_bar, (uint32_t)(it & 1), &s_fail);
+    if (__syncthreads_or(!ok)) { s_fail = 1; break; }
+    loads_out = false;
+    // ---- the digit products of levels d = s + t <= 6 into accumulator d
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int d = 0; d < OZ_S; ++d)
+#pragma unroll 1
+        for (int s = 0; s <= d; ++s) {
+          const int t = d - s;
+#pragma unroll
+          for (int ks = 0; ks < OZ_K / 16; ++ks)
+            mma_bf16(taddr + d * OZ_N, sdesc(smem_u32(sA + s * PL) + ks * 32), sdesc(smem_u32(sB + t * BH) + ks * 32),
+                     ID, (s == 0 && ks == 0) ? 0u : 1u);
+        }
+      mma_commit(&mma_bar);
+    }
+    mma_out = true;
+    ok = mbar_wait(&mma_bar, (uint32_t)(it & 1), &s_fail);
+    if (__syncthreads_or(!ok)) { s_fail = 1; break; }
+    mma_out = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the planes are free: the next pass's copies run during this pass's epilogue
+    if (tid == 0 && p + 1 < pe) load_pass(p + 1);
+    loads_out = p + 1 < pe;
+    const int E = A.ea[p * 128 + tid];
+    if (tid < OZ_N) Fexp[tid] = A.eb[p * 128 + half * OZ_N + tid];
+    __syncthreads();
+    // ---- combine the levels of row tid and add them to the running sums
+#pragma unroll
+    for (int g = 0; g < OZ_N / 16; ++g) {
+      f2 S[16];
+#pragma unroll
+      for (int c = 0; c < 16; ++c) S[c] = f2{0.0f, 0.0f};
+#pragma unroll 1
+      for (int d = OZ_S - 1; d >= 0; --d) {
+        float v[16];
+        tmem_ld16(taddr + lane_base + d * OZ_N + 16 * g, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S[c] = f2_add(S[c], f2{ldexpf(v[c], -7 * d), 0.0f});
+      }
+#pragma unroll
+      for (int c = 0; c < 16; ++c) {
+        const int sc = E + Fexp[16 * g + c] - 14;
+        R[16 * g + c] = f2_add(R[16 * g + c], f2{ldexpf(S[c].h, sc), ldexpf(S[c].l, sc)});
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+  }
+  // copies and MMAs in flight have landed before the shared and tensor memory are released
+  if (tid == 0 && s_fail) {
+    if (mma_out) mbar_wait_drain(&mma_bar, (uint32_t)(it & 1));
+    if (loads_out) mbar_wait_drain(&ld_bar, (uint32_t)(it & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (tid < nrowA && !s_fail) {
+    double* out = A.part + (((size_t)half * gridDim.x + blockIdx.x) * 128 + tid) * OZ_N;
+#pragma unroll
+    for (int j = 0; j < OZ_N; ++j) out[j] = f2_to(R[j]);
+  }
+  if (s_fail && tid == 0) atomicExch(A.err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(OZ_TCOLS) : "memory");
+}
+
+// S from the partial sums of all blocks: Re S = D[i][j] + D[nv+i][nv+j], Im S = D[i][nv+j] - D[nv+i][j]
+template <typename S>
+__global__ void k_gram_oz_reduce(const double* part, int nbx, int nv, S* out) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv * nv) return;
+  const int i = t / nv, j = t % nv;
+  auto P = [&](int h, int b, int row, int col) { return part[(((size_t)h * nbx + b) * 128 + row) * OZ_N + col]; };
+  double re = 0.0, im = 0.0;
+  for (int b = 0; b < nbx; ++b) {
+    if constexpr (sizeof(S) == sizeof(cd)) {
+      re += P(0, b, i, j) + P(1, b, nv + i, j);
+      im += P(1, b, i, j) - P(0, b, nv + i, j);
+    } else {
+      re += P(0, b, i, j);
+    }
+  }
+  if constexpr (sizeof(S) == sizeof(cd)) out[t] = mkc(re, im);
+  else out[t] = re;
+}
+
+}  // namespace
+
+// out = X^+ W (nv x nv) on the tensor cores; *done = false when the shape is not covered (nv > 64)
+template <typename S>
+int gram_ozaki(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, bool* done) {
+  *done = false;
+  constexpr bool CPLX = sizeof(S) == sizeof(cd);
+  if (nv > OZ_N || n <= 0) return OEFE_OK;
+  const int halves = CPLX ? 2 : 1;
+  const int nbx = std::max(1, c->num_sms / halves);
+  const long long passes = (n + OZ_K - 1) / OZ_K;
+  auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
+  const size_t pl_bytes = a256((size_t)passes * PASS_BYTES), ex_bytes = a256((size_t)passes * 128 * sizeof(int));
+  const size_t pt_bytes = a256((size_t)halves * nbx * 128 * OZ_N * sizeof(double));
+  const size_t need = 2 * pl_bytes + 2 * ex_bytes + pt_bytes;
+  if (c->ozpart_bytes < need) {
+    cudaStreamSynchronize(c->stream);
+    dev_free(c->d_ozpart);
+    c->d_ozpart = nullptr;
+    c->ozpart_bytes = 0;
+    OEFE_TRY(dev_alloc(c, &c->d_ozpart, need));
+    c->ozpart_bytes = need;
+  }
+  unsigned char* base = (unsigned char*)c->d_ozpart;
+  unsigned char* pa = base;
+  unsigned char* pbp = base + pl_bytes;
+  int* ea = (int*)(base + 2 * pl_bytes);
+  int* eb = (int*)(base + 2 * pl_bytes + ex_bytes);
+  double* part = (double*)(base + 2 * pl_bytes + 2 * ex_bytes);
+  const size_t dsm = (size_t)OZ_K * 129 * sizeof(unsigned long long);
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_oz_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  DigArgs D{X, ldx, n, nv, CPLX, false, pa, ea};
+  OEFE_COUNTED k_oz_digits<<<(unsigned)passes, DG_T, dsm, c->stream>>>(D);
+  D = DigArgs{W, ldw, n, nv, CPLX, true, pbp, eb};
+  OEFE_COUNTED k_oz_digits<<<(unsigned)passes, DG_T, dsm, c->stream>>>(D);
+  OzArgs A;
+  A.pa = pa;
+  A.ea = ea;
+  A.pb = pbp;
+  A.eb = eb;
+  A.passes = passes;
+  A.passes_per_cta = (passes + nbx - 1) / nbx;
+  A.cplx = CPLX;
+  A.nv = nv;
+  A.part = part;
+  A.err = c->d_status + 2;   // its own word: the Cholesky kernels report through word 0
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_gram_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM));
+  dim3 grid(nbx, halves);
+  OEFE_COUNTED k_gram_oz<<<grid, OZ_T, OZ_SMEM, c->stream>>>(A);
+  OEFE_COUNTED k_gram_oz_reduce<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(part, nbx, nv, out);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  int flag = 0;
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (flag) {
+    cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), c->stream);
+    c->err = "gram: a tensor-core wait timed out";
+    return OEFE_ERR_TIMEOUT;
+  }
+  *done = true;
+  return OEFE_OK;
+}
+
+template int gram_ozaki<double>(oefe_ctx*, const double*, int, const double*, int, int64_t, int, double*, bool*);
+template int gram_ozaki<cd>(oefe_ctx*, const cd*, int, const cd*, int, int64_t, int, cd*, bool*);

@@ -46,6 +46,31 @@ def test_orthonormalize(k, products):
     assert rel(Q, Qo) < 1e-10 * f
 
 
+@pytest.mark.parametrize("case", ["c1_real_64", "complex_24"])
+def test_orthonormalize_tensor_core_gram(case):
+    # pair mode takes the Gram matrices on the tensor cores (exact bf16 digits, about 2^-46 of the
+    # row and column maxima per term): Q^+ M Q = I and Q against the native FP64 path within the
+    # pair tolerances (32x the FP64 ones); 64 vectors fill the 128-row MMA tile
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS
+    if case == "c1_real_64":
+        prs, ctx, V, _ = c1_pair()
+        nv = 64
+    else:
+        prs, ctx, V, _ = paired(ks=[(0.25, -0.4, 0.1)])
+        nv = 24
+    pr = prs[0]
+    Y = W.random_vectors(pr.n, nv, complex_=pr.complex, seed=31)
+    ctx.set_f64_products(F64_PAIRS)
+    Yp = to_gpu(Y)
+    ctx.orthonormalize(0, Yp)
+    ctx.set_f64_products(F64_NATIVE)
+    Yn = to_gpu(Y)
+    ctx.orthonormalize(0, Yn)
+    Q = Yp.cpu().numpy()
+    assert np.allclose(Q.conj().T @ pr.apply_M(Q), np.eye(nv), atol=32e-12)
+    assert rel(Q, Yn.cpu().numpy()) < 32e-10
+
+
 def test_orthonormalize_rank_deficient_reports_cholesky():
     from paper_2010_09701_gb300 import OefeError, binding
     prs, ctx, V, _ = paired()
