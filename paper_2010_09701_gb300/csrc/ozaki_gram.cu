@@ -11,18 +11,19 @@
 // in bf16; a product of two digits is below 2^14; the sum that one accumulator of level d = s + t
 // (at most 7 digit pairs) takes over 64 rows stays below 2^24, so the FP32 accumulation of the
 // tensor cores is exact. The levels d = 0..6 (28 digit products) are kept, the rest (below
-// 2^-49 of the row and column maxima) dropped; the levels are combined in FP32-pair arithmetic
-// and summed over the passes in pairs. Error: about 2^-46 of |x|max |w|max per term.
+// 2^-49 of the row and column maxima) dropped; levels 6..4 are combined in FP32 (2^-28 below
+// level 0, so their rounding is about 2^-51 of it), levels 3..0 in FP32-pair arithmetic, and the
+// passes are summed in pairs. Error: about 2^-46 of |x|max |w|max per term.
 //
 // Two kernels. k_oz_digits (one CTA per pass of 64 rows) writes the digit planes of an operand to
 // global memory, already in the 128-byte-swizzled K-major layout the MMA reads, with the
 // exponent of each operand row; it touches FP64 values only through their bits (integer
-// operations). k_gram_oz (one CTA of 128 threads per (block of passes, half): half 0 takes the
+// operations). k_gram_oz (one CTA of 256 threads per (block of passes, half): half 0 takes the
 // real parts of W's columns, half 1 the imaginary parts) streams the planes of each pass into
 // shared memory with bulk copies; thread 0 issues the 112 MMAs (M 128, N 64, K 16) into 7
-// tensor-memory accumulators (448 columns); while every thread reads its accumulator row and adds
-// the combined pass to its running sums in pairs, the next pass's planes are already on their
-// way. Every wait is bounded; on a timeout the CTA raises the error flag, waits for its copies and
+// tensor-memory accumulators (448 columns); while every thread reads its part of an accumulator
+// row (two warps per lane quadrant, 32 columns each) and adds the combined pass to its running
+// sums in pairs, the next pass's planes are already on their way. Every wait is bounded; on a timeout the CTA raises the error flag, waits for its copies and
 // MMAs in flight and frees its tensor memory.
 #include <cuda_bf16.h>
 
@@ -35,7 +36,8 @@
 
 namespace {
 
-constexpr int OZ_T = 128;           // threads per CTA of the MMA kernel
+constexpr int OZ_T = 256;           // threads per CTA of the MMA kernel: two warps per lane quadrant
+constexpr int OZ_C = 32;            // accumulator columns of one thread's running sums
 constexpr int OZ_K = 64;            // rows per pass (one 128-byte swizzle row of bf16)
 constexpr int OZ_S = 7;             // digits per value
 constexpr int OZ_N = 64;            // columns of B per CTA
@@ -62,9 +64,12 @@ __device__ __forceinline__ void digits7(unsigned long long b, int E, float c[OZ_
   const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
   const unsigned long long ya = (ex == 0 || sh >= 64) ? 0ull : (mant >> sh);
   const long long Y = (b >> 63) ? -(long long)ya : (long long)ya;
-  c[0] = (float)(Y >> 42);
+  // small integers to float without a conversion instruction: 2^23 + m as bits, minus 2^23
+  const int top = (int)(Y >> 42) + 128;                 // c0 + 128 in [0, 255]
+  c[0] = __fsub_rn(__int_as_float(0x4B000000 | top), 8388736.0f);   // 2^23 + 128
 #pragma unroll
-  for (int s = 1; s < OZ_S; ++s) c[s] = (float)((Y >> (42 - 7 * s)) & 127);
+  for (int s = 1; s < OZ_S; ++s)
+    c[s] = __fsub_rn(__int_as_float(0x4B000000 | (int)((Y >> (42 - 7 * s)) & 127)), 8388608.0f);
 }
 
 struct DigArgs {
@@ -94,21 +99,34 @@ __device__ __forceinline__ int op_col(const DigArgs& D, int r, int* part) {
 }
 
 __global__ void __launch_bounds__(DG_T) k_oz_digits(const DigArgs D) {
-  extern __shared__ unsigned long long dbits[];    // [64 k][129]: bits of the pass, padded
+  extern __shared__ unsigned long long dbits[];    // [128 operand rows][65]: bits of the pass, padded
   __shared__ int sE[128];
   const long long p = blockIdx.x, r0 = p * OZ_K;
   const int nk = (int)min((long long)OZ_K, D.n - r0);
-  for (int t = threadIdx.x; t < OZ_K * 128; t += DG_T) {
-    const int k = t / 128, r = t % 128;
-    int part;
-    const int c = op_col(D, r, &part);
-    dbits[k * 129 + r] = (c >= 0 && k < nk) ? (unsigned long long)__double_as_longlong(ld_part(D.M, D.ld, r0 + k, c, part, D.cplx))
-                                            : 0ull;
+  // loads: a warp takes 32 consecutive operand rows (consecutive columns of M) of one row of M;
+  // eight loads in flight per thread
+  for (int t0 = threadIdx.x; t0 < OZ_K * 128; t0 += 8 * DG_T) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * DG_T;
+      const int k = t / 128, r = t % 128;
+      int part;
+      const int c = op_col(D, r, &part);
+      v[u] = (t < OZ_K * 128 && c >= 0 && k < nk)
+                 ? (unsigned long long)__double_as_longlong(ld_part(D.M, D.ld, r0 + k, c, part, D.cplx))
+                 : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * DG_T;
+      if (t < OZ_K * 128) dbits[(t % 128) * 65 + t / 128] = v[u];
+    }
   }
   __syncthreads();
   if (threadIdx.x < 128) {
     int mex = 0;
-    for (int k = 0; k < OZ_K; ++k) mex = max(mex, (int)((dbits[k * 129 + threadIdx.x] >> 52) & 0x7FF));
+    for (int k = 0; k < OZ_K; ++k) mex = max(mex, (int)((dbits[threadIdx.x * 65 + k] >> 52) & 0x7FF));
     const int E = mex ? mex - 1022 : 0;
     sE[threadIdx.x] = E;
     D.exps[p * 128 + threadIdx.x] = E;
@@ -118,8 +136,8 @@ __global__ void __launch_bounds__(DG_T) k_oz_digits(const DigArgs D) {
   for (int t = threadIdx.x; t < 128 * (OZ_K / 2); t += DG_T) {   // a warp: one row, 32 pairs of k
     const int r = t / (OZ_K / 2), kp = t % (OZ_K / 2);
     float c0[OZ_S], c1[OZ_S];
-    digits7(dbits[(2 * kp) * 129 + r], sE[r], c0);
-    digits7(dbits[(2 * kp + 1) * 129 + r], sE[r], c1);
+    digits7(dbits[r * 65 + 2 * kp], sE[r], c0);
+    digits7(dbits[r * 65 + 2 * kp + 1], sE[r], c1);
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s)
       *reinterpret_cast<__nv_bfloat162*>(base + (size_t)s * PL + swz(r, 2 * kp)) = __floats2bfloat162_rn(c0[s], c1[s]);
@@ -175,6 +193,7 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
 
   const long long pb = (long long)blockIdx.x * A.passes_per_cta, pe = min(A.passes, pb + A.passes_per_cta);
   const int nrowA = A.cplx ? 2 * A.nv : A.nv;
+  const int row = tid & 127, ch = tid >> 7;   // accumulator row (tensor-memory lane) and column half
   auto load_pass = [&](long long p) {   // thread 0: the planes of pass p into shared memory
     mbar_expect_tx(&ld_bar, (uint32_t)(PASS_BYTES + OZ_S * BH));
     bulk_copy(smem_u32(sA), A.pa + (size_t)p * PASS_BYTES, PASS_BYTES, &ld_bar);
@@ -182,10 +201,10 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
       bulk_copy(smem_u32(sB + s * BH), A.pb + (size_t)p * PASS_BYTES + (size_t)s * PL + (size_t)half * BH, BH, &ld_bar);
   };
   if (tid == 0 && pb < pe) load_pass(pb);
-  f2 R[OZ_N];
+  f2 R[OZ_C];
 #pragma unroll
-  for (int j = 0; j < OZ_N; ++j) R[j] = f2{0.0f, 0.0f};
-  const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+  for (int j = 0; j < OZ_C; ++j) R[j] = f2{0.0f, 0.0f};
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
   constexpr uint32_t ID = idesc_bf16(128, OZ_N, false);
   int it = 0;
   bool loads_out = pb < pe, mma_out = false;
@@ -193,6 +212,9 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
     bool ok = mbar_wait(&ld_bar, (uint32_t)(it & 1), &s_fail);
     if (__syncthreads_or(!ok)) { s_fail = 1; break; }
     loads_out = false;
+    // the exponents of this pass, loaded while the MMAs run
+    const int E = A.ea[p * 128 + row];
+    if (tid < OZ_N) Fexp[tid] = A.eb[p * 128 + half * OZ_N + tid];
     // ---- the digit products of levels d = s + t <= 6 into accumulator d
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -216,26 +238,48 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
     // the planes are free: the next pass's copies run during this pass's epilogue
     if (tid == 0 && p + 1 < pe) load_pass(p + 1);
     loads_out = p + 1 < pe;
-    const int E = A.ea[p * 128 + tid];
-    if (tid < OZ_N) Fexp[tid] = A.eb[p * 128 + half * OZ_N + tid];
-    __syncthreads();
-    // ---- combine the levels of row tid and add them to the running sums
+    // ---- combine the levels of (row, this half of the columns) and add them to the running sums;
+    //      the scalings are exact multiplications by powers of two
 #pragma unroll
-    for (int g = 0; g < OZ_N / 16; ++g) {
+    for (int g = 0; g < OZ_C / 16; ++g) {
+      const int c0 = ch * OZ_C + 16 * g;
+      // levels 6, 5, 4 by FP32 Horner steps in units of level 4 (their rounding, 2^-24 of a
+      // quantity 2^-28 below level 0, is far below the pair precision); levels 3..0 in pairs
+      float lo[16];
+      {
+        float v[16];
+        tmem_ld16(taddr + lane_base + 6 * OZ_N + c0, v);
+#pragma unroll
+        for (int c = 0; c < 16; ++c) lo[c] = v[c];
+#pragma unroll
+        for (int d = 5; d >= 4; --d) {
+          tmem_ld16(taddr + lane_base + d * OZ_N + c0, v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) lo[c] = __fmaf_rn(lo[c], 0.0078125f, v[c]);
+        }
+      }
       f2 S[16];
 #pragma unroll
-      for (int c = 0; c < 16; ++c) S[c] = f2{0.0f, 0.0f};
+      for (int c = 0; c < 16; ++c) S[c] = f2{__fmul_rn(lo[c], 3.7252902984619141e-09f), 0.0f};   // 2^-28
 #pragma unroll 1
-      for (int d = OZ_S - 1; d >= 0; --d) {
+      for (int d = 3; d >= 0; --d) {
         float v[16];
-        tmem_ld16(taddr + lane_base + d * OZ_N + 16 * g, v);
+        tmem_ld16(taddr + lane_base + d * OZ_N + c0, v);
+        const float w = __int_as_float((127 - 7 * d) << 23);   // 2^(-7 d)
 #pragma unroll
-        for (int c = 0; c < 16; ++c) S[c] = f2_add(S[c], f2{ldexpf(v[c], -7 * d), 0.0f});
+        for (int c = 0; c < 16; ++c) S[c] = f2_add(S[c], f2{__fmul_rn(v[c], w), 0.0f});
       }
 #pragma unroll
       for (int c = 0; c < 16; ++c) {
-        const int sc = E + Fexp[16 * g + c] - 14;
-        R[16 * g + c] = f2_add(R[16 * g + c], f2{ldexpf(S[c].h, sc), ldexpf(S[c].l, sc)});
+        const int sc = E + Fexp[c0 + c] - 14;
+        f2 x;
+        if (sc > -127 && sc < 128) {
+          const float w = __int_as_float((sc + 127) << 23);
+          x = f2{__fmul_rn(S[c].h, w), __fmul_rn(S[c].l, w)};
+        } else {
+          x = f2{ldexpf(S[c].h, sc), ldexpf(S[c].l, sc)};
+        }
+        R[16 * g + c] = f2_add(R[16 * g + c], x);
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -248,10 +292,10 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (tid < nrowA && !s_fail) {
-    double* out = A.part + (((size_t)half * gridDim.x + blockIdx.x) * 128 + tid) * OZ_N;
+  if (row < nrowA && !s_fail) {
+    double* out = A.part + (((size_t)half * gridDim.x + blockIdx.x) * 128 + row) * OZ_N + ch * OZ_C;
 #pragma unroll
-    for (int j = 0; j < OZ_N; ++j) out[j] = f2_to(R[j]);
+    for (int j = 0; j < OZ_C; ++j) out[j] = f2_to(R[j]);
   }
   if (s_fail && tid == 0) atomicExch(A.err, 1);
   if (warp == 0)
@@ -307,7 +351,7 @@ int gram_ozaki(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n,
   int* ea = (int*)(base + 2 * pl_bytes);
   int* eb = (int*)(base + 2 * pl_bytes + ex_bytes);
   double* part = (double*)(base + 2 * pl_bytes + 2 * ex_bytes);
-  const size_t dsm = (size_t)OZ_K * 129 * sizeof(unsigned long long);
+  const size_t dsm = (size_t)128 * 65 * sizeof(unsigned long long);
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_oz_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
   DigArgs D{X, ldx, n, nv, CPLX, false, pa, ea};
   OEFE_COUNTED k_oz_digits<<<(unsigned)passes, DG_T, dsm, c->stream>>>(D);
