@@ -457,6 +457,11 @@ int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int n
 
 template <typename S>
 int rotate(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm) {
+  if (c->f64_products == OEFE_F64_PAIRS) {   // FP64-class on the tensor cores (exact bf16 digits)
+    bool done = false;
+    OEFE_TRY(rotate_ozaki<S>(c, X, ldx, n, nv, C, herm, &done));
+    if (done) return OEFE_OK;
+  }
   if (c->f64_products == OEFE_F64_PAIRS) {
     // pairs: C (transposed, as pairs) and the staged rows in shared memory; rows per CTA such that
     // two CTAs share an SM (one stages while the other computes), else as many as fit

@@ -227,6 +227,8 @@ int setup_kpoints(oefe_ctx* c, int nk, const double* k, const double* w);
 int ensure_orth_enrichment(oefe_ctx* c, KData& K);
 template <typename S>
 int gram_ozaki(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, bool* done);
+template <typename S>
+int rotate_ozaki(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm, bool* done);
 int build_hamiltonian(oefe_ctx* c, const double* veff, int store);
 
 // dense helpers (linalg.cu)

@@ -302,6 +302,266 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(OZ_TCOLS) : "memory");
 }
 
+// ------------------------------------------------------------------ rotations X <- X G
+// Real form: A = the rows of X with K = [Re X | Im X] (K half 0: real parts of the 64 columns, half 1:
+// imaginary parts), B = the real form of G, N half 0 the real parts of the products, half 1 the
+// imaginary parts: B[(0, j)][(0, n)] = Re G_jn, B[(0, j)][(1, n)] = Im G_jn, B[(1, j)][(0, n)] =
+// -Im G_jn, B[(1, j)][(1, n)] = Re G_jn. The exponent of an A row covers both K halves, so the two
+// halves accumulate into the same (exact) accumulators: 7 pairs x 128 x 2^14 < 2^24.
+
+struct RotDigArgs {
+  const void* X;
+  int ldx;
+  long long n;
+  int nv;
+  bool cplx;
+  unsigned char* planes;   // per tile of 128 rows: 2 K halves x PASS_BYTES
+  int* exps;               // per tile 128
+};
+
+// digits of 128 rows of X (one CTA per tile)
+__global__ void __launch_bounds__(DG_T) k_oz_rot_digits(const RotDigArgs D) {
+  extern __shared__ unsigned long long rbits[];   // [128 rows][129]: both K halves, padded
+  __shared__ int sE[128];
+  const long long tile = blockIdx.x, r0 = tile * 128;
+  const int nr = (int)min(128ll, D.n - r0);
+  const int kh_n = D.cplx ? 2 : 1;
+  for (int t0 = threadIdx.x; t0 < 128 * 128; t0 += 8 * DG_T) {
+    unsigned long long v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * DG_T;
+      const int r = t / 128, k = t % 128, part = k / 64, c = k % 64;   // consecutive threads: one row
+      v[u] = (t < 128 * 128 && r < nr && c < D.nv && part < kh_n)
+                 ? (unsigned long long)__double_as_longlong(ld_part(D.X, D.ldx, r0 + r, c, part, D.cplx))
+                 : 0ull;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int t = t0 + u * DG_T;
+      if (t < 128 * 128) rbits[(t / 128) * 129 + t % 128] = v[u];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    int mex = 0;
+    for (int k = 0; k < 128; ++k) mex = max(mex, (int)((rbits[threadIdx.x * 129 + k] >> 52) & 0x7FF));
+    const int E = mex ? mex - 1022 : 0;
+    sE[threadIdx.x] = E;
+    D.exps[tile * 128 + threadIdx.x] = E;
+  }
+  __syncthreads();
+  unsigned char* base = D.planes + (size_t)tile * 2 * PASS_BYTES;
+  for (int t = threadIdx.x; t < 2 * 128 * (OZ_K / 2); t += DG_T) {   // a warp: one row, 32 pairs of k
+    const int kh = t / (128 * (OZ_K / 2)), rem = t % (128 * (OZ_K / 2));
+    const int r = rem / (OZ_K / 2), kp = rem % (OZ_K / 2);
+    float c0[OZ_S], c1[OZ_S];
+    digits7(rbits[r * 129 + kh * 64 + 2 * kp], sE[r], c0);
+    digits7(rbits[r * 129 + kh * 64 + 2 * kp + 1], sE[r], c1);
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s)
+      *reinterpret_cast<__nv_bfloat162*>(base + (size_t)kh * PASS_BYTES + (size_t)s * PL + swz(r, 2 * kp)) =
+          __floats2bfloat162_rn(c0[s], c1[s]);
+  }
+}
+
+// digits of the real form of G (one thread per B column = N index n of half nh): planes
+// [nh][kh][digit][64 rows][64 k], exponents [nh][64]; G[k][j] = herm ? (k <= j ? conj(C[j][k]) : 0) : C[k][j]
+template <typename S>
+__global__ void k_oz_rot_bdigits(const S* C, int nv, bool herm, unsigned char* planes, int* exps) {
+  constexpr bool CPLX = sizeof(S) == sizeof(cd);
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;   // 0..127: (nh, n)
+  if (t >= 128) return;
+  const int nh = t / 64, n = t % 64;
+  auto G = [&](int k, int j) -> cd {   // entry of the rotation applied as X G
+    if (k >= nv || j >= nv) return mkc(0, 0);
+    cd v;
+    if (herm) {
+      if (k > j) return mkc(0, 0);
+      if constexpr (CPLX) v = cconj(C[(size_t)j * nv + k]);
+      else v = mkc(C[(size_t)j * nv + k], 0.0);
+    } else {
+      if constexpr (CPLX) v = C[(size_t)k * nv + j];
+      else v = mkc(C[(size_t)k * nv + j], 0.0);
+    }
+    return v;
+  };
+  auto Bv = [&](int k) -> double {   // B[k][(nh, n)], k = (kh, j)
+    const int kh = k / 64, j = k % 64;
+    const cd g = G(j, n);
+    if (kh == 0) return nh == 0 ? g.x : g.y;
+    return nh == 0 ? -g.y : g.x;
+  };
+  int mex = 0;
+  for (int k = 0; k < 128; ++k) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(Bv(k));
+    mex = max(mex, (int)((b >> 52) & 0x7FF));
+  }
+  const int E = mex ? mex - 1022 : 0;
+  exps[nh * 64 + n] = E;
+  for (int kh = 0; kh < 2; ++kh)
+    for (int kp = 0; kp < OZ_K / 2; ++kp) {
+      float c0[OZ_S], c1[OZ_S];
+      digits7((unsigned long long)__double_as_longlong(Bv(kh * 64 + 2 * kp)), E, c0);
+      digits7((unsigned long long)__double_as_longlong(Bv(kh * 64 + 2 * kp + 1)), E, c1);
+      unsigned char* base = planes + (size_t)(nh * 2 + kh) * OZ_S * BH;
+#pragma unroll
+      for (int s = 0; s < OZ_S; ++s)
+        *reinterpret_cast<__nv_bfloat162*>(base + (size_t)s * BH + swz(n, 2 * kp)) = __floats2bfloat162_rn(c0[s], c1[s]);
+    }
+}
+
+struct RotArgs {
+  const unsigned char* pa;   // tile digit planes (2 K halves per tile)
+  const int* ea;             // tile row exponents
+  const unsigned char* pb;   // G digit planes [nh][kh]
+  const int* eb;             // [nh][64]
+  long long tiles;
+  long long n;
+  int nv;
+  bool cplx;
+  void* X;                   // output rows (double or cd), ld
+  int ldx;
+  int* err;
+};
+
+__global__ void __launch_bounds__(OZ_T, 1) k_rot_oz(const RotArgs A) {
+  extern __shared__ __align__(1024) unsigned char oz_raw[];
+  unsigned char* sm = (unsigned char*)(((uintptr_t)oz_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* sA = sm;
+  unsigned char* sB = sm + PASS_BYTES;
+  __shared__ int Fexp[OZ_N];
+  __shared__ uint64_t ld_bar, mma_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(OZ_TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(&ld_bar, 1);
+    mbar_init(&mma_bar, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t taddr = tmem_slot;
+  const int row = tid & 127, ch = tid >> 7;
+  const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
+  constexpr uint32_t ID = idesc_bf16(128, OZ_N, false);
+  const int nkh = A.cplx ? 2 : 1, nnh = A.cplx ? 2 : 1;
+  const int rounds = nkh * nnh;   // (nh, kh), kh fastest
+  // the rounds of this CTA: tiles blockIdx.x, blockIdx.x + gridDim.x, ...
+  auto load_round = [&](long long tile, int nh, int kh) {
+    mbar_expect_tx(&ld_bar, (uint32_t)(PASS_BYTES + OZ_S * BH));
+    bulk_copy(smem_u32(sA), A.pa + ((size_t)tile * 2 + kh) * PASS_BYTES, PASS_BYTES, &ld_bar);
+    bulk_copy(smem_u32(sB), A.pb + (size_t)(nh * 2 + kh) * OZ_S * BH, OZ_S * BH, &ld_bar);
+  };
+  long long tile = blockIdx.x;
+  int q = 0;   // round within the tile
+  if (tid == 0 && tile < A.tiles) load_round(tile, 0, 0);
+  int it = 0;
+  bool loads_out = tile < A.tiles, mma_out = false;
+  while (tile < A.tiles) {
+    const int nh = q / nkh, kh = q % nkh;
+    bool ok = mbar_wait(&ld_bar, (uint32_t)(it & 1), &s_fail);
+    if (__syncthreads_or(!ok)) { s_fail = 1; break; }
+    loads_out = false;
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll 1
+      for (int d = 0; d < OZ_S; ++d)
+#pragma unroll 1
+        for (int s = 0; s <= d; ++s) {
+          const int t = d - s;
+#pragma unroll
+          for (int ks = 0; ks < OZ_K / 16; ++ks)
+            mma_bf16(taddr + d * OZ_N, sdesc(smem_u32(sA + s * PL) + ks * 32), sdesc(smem_u32(sB + t * BH) + ks * 32),
+                     ID, (kh == 0 && s == 0 && ks == 0) ? 0u : 1u);
+        }
+      mma_commit(&mma_bar);
+    }
+    mma_out = true;
+    ok = mbar_wait(&mma_bar, (uint32_t)(it & 1), &s_fail);
+    if (__syncthreads_or(!ok)) { s_fail = 1; break; }
+    mma_out = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    ++it;
+    // next round (this tile's next (nh, kh), or the CTA's next tile): its copies run during the epilogue
+    const long long cur_tile = tile;
+    ++q;
+    if (q == rounds) { q = 0; tile += gridDim.x; }
+    if (tid == 0 && tile < A.tiles) load_round(tile, q / nkh, q % nkh);
+    loads_out = tile < A.tiles;
+    if (kh == nkh - 1) {
+      // ---- epilogue of (cur_tile, nh): 32 columns of one row per thread
+      const long long grow = cur_tile * 128 + row;
+      const int E = A.ea[cur_tile * 128 + row];
+      if (tid < OZ_N) Fexp[tid] = A.eb[nh * 64 + tid];
+      __syncthreads();
+#pragma unroll
+      for (int g = 0; g < OZ_C / 16; ++g) {
+        const int c0 = ch * OZ_C + 16 * g;
+        float lo[16];
+        {
+          float v[16];
+          tmem_ld16(taddr + lane_base + 6 * OZ_N + c0, v);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) lo[c] = v[c];
+#pragma unroll
+          for (int d = 5; d >= 4; --d) {
+            tmem_ld16(taddr + lane_base + d * OZ_N + c0, v);
+#pragma unroll
+            for (int c = 0; c < 16; ++c) lo[c] = __fmaf_rn(lo[c], 0.0078125f, v[c]);
+          }
+        }
+        f2 S[16];
+#pragma unroll
+        for (int c = 0; c < 16; ++c) S[c] = f2{__fmul_rn(lo[c], 3.7252902984619141e-09f), 0.0f};   // 2^-28
+#pragma unroll 1
+        for (int d = 3; d >= 0; --d) {
+          float v[16];
+          tmem_ld16(taddr + lane_base + d * OZ_N + c0, v);
+          const float w = __int_as_float((127 - 7 * d) << 23);
+#pragma unroll
+          for (int c = 0; c < 16; ++c) S[c] = f2_add(S[c], f2{__fmul_rn(v[c], w), 0.0f});
+        }
+        if (grow < A.n) {
+#pragma unroll
+          for (int c = 0; c < 16; ++c) {
+            const int col = c0 + c;
+            if (col >= A.nv) continue;
+            const int sc = E + Fexp[col] - 14;
+            const double val = ldexp(f2_to(S[c]), sc);
+            if (A.cplx) {
+              double* xr = reinterpret_cast<double*>(A.X) + 2 * ((size_t)grow * A.ldx + col);
+              xr[nh] = val;
+            } else {
+              reinterpret_cast<double*>(A.X)[(size_t)grow * A.ldx + col] = val;
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  if (tid == 0 && s_fail) {
+    if (mma_out) mbar_wait_drain(&mma_bar, (uint32_t)(it & 1));
+    if (loads_out) mbar_wait_drain(&ld_bar, (uint32_t)(it & 1));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (s_fail && tid == 0) atomicExch(A.err, 1);
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(OZ_TCOLS) : "memory");
+}
+
 // S from the partial sums of all blocks: Re S = D[i][j] + D[nv+i][nv+j], Im S = D[i][nv+j] - D[nv+i][j]
 template <typename S>
 __global__ void k_gram_oz_reduce(const double* part, int nbx, int nv, S* out) {
@@ -387,3 +647,64 @@ int gram_ozaki(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n,
 
 template int gram_ozaki<double>(oefe_ctx*, const double*, int, const double*, int, int64_t, int, double*, bool*);
 template int gram_ozaki<cd>(oefe_ctx*, const cd*, int, const cd*, int, int64_t, int, cd*, bool*);
+
+// X[0:n] <- X G (G = C, or C^+ of a lower triangular C when herm) on the tensor cores; *done =
+// false when the shape is not covered (nv > 64)
+template <typename S>
+int rotate_ozaki(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm, bool* done) {
+  *done = false;
+  constexpr bool CPLX = sizeof(S) == sizeof(cd);
+  if (nv > OZ_N || n <= 0) return OEFE_OK;
+  const long long tiles = (n + 127) / 128;
+  auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
+  const size_t pa_bytes = a256((size_t)tiles * 2 * PASS_BYTES), ea_bytes = a256((size_t)tiles * 128 * sizeof(int));
+  const size_t pb_bytes = a256((size_t)4 * OZ_S * BH), eb_bytes = 256 + 128 * sizeof(int);
+  const size_t need = pa_bytes + ea_bytes + pb_bytes + eb_bytes;
+  if (c->ozpart_bytes < need) {
+    cudaStreamSynchronize(c->stream);
+    dev_free(c->d_ozpart);
+    c->d_ozpart = nullptr;
+    c->ozpart_bytes = 0;
+    OEFE_TRY(dev_alloc(c, &c->d_ozpart, need));
+    c->ozpart_bytes = need;
+  }
+  unsigned char* base = (unsigned char*)c->d_ozpart;
+  unsigned char* pa = base;
+  int* ea = (int*)(base + pa_bytes);
+  unsigned char* pb = base + pa_bytes + ea_bytes;
+  int* eb = (int*)(pb + pb_bytes);
+  const size_t dsm = (size_t)128 * 129 * sizeof(unsigned long long);
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_oz_rot_digits, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm));
+  RotDigArgs D{X, ldx, n, nv, CPLX, pa, ea};
+  OEFE_COUNTED k_oz_rot_digits<<<(unsigned)tiles, DG_T, dsm, c->stream>>>(D);
+  OEFE_COUNTED k_oz_rot_bdigits<S><<<1, 128, 0, c->stream>>>(C, nv, herm, pb, eb);
+  RotArgs A;
+  A.pa = pa;
+  A.ea = ea;
+  A.pb = pb;
+  A.eb = eb;
+  A.tiles = tiles;
+  A.n = n;
+  A.nv = nv;
+  A.cplx = CPLX;
+  A.X = X;
+  A.ldx = ldx;
+  A.err = c->d_status + 2;
+  OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_rot_oz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)OZ_SMEM));
+  const int grid = (int)std::min<long long>(tiles, c->num_sms);
+  OEFE_COUNTED k_rot_oz<<<grid, OZ_T, OZ_SMEM, c->stream>>>(A);
+  OEFE_CUDA_TRY(c, cudaGetLastError());
+  int flag = 0;
+  OEFE_CUDA_TRY(c, cudaMemcpyAsync(&flag, c->d_status + 2, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (flag) {
+    cudaMemsetAsync(c->d_status + 2, 0, sizeof(int), c->stream);
+    c->err = "rotate: a tensor-core wait timed out";
+    return OEFE_ERR_TIMEOUT;
+  }
+  *done = true;
+  return OEFE_OK;
+}
+
+template int rotate_ozaki<double>(oefe_ctx*, double*, int, int64_t, int, const double*, bool, bool*);
+template int rotate_ozaki<cd>(oefe_ctx*, cd*, int, int64_t, int, const cd*, bool, bool*);

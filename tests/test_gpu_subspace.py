@@ -47,7 +47,7 @@ def test_orthonormalize(k, products):
 
 
 @pytest.mark.parametrize("case", ["c1_real_64", "complex_24"])
-def test_orthonormalize_tensor_core_gram(case):
+def test_orthonormalize_tensor_core_gram(case):  # Gram and rotations on the tensor cores
     # pair mode takes the Gram matrices on the tensor cores (exact bf16 digits, about 2^-46 of the
     # row and column maxima per term): Q^+ M Q = I and Q against the native FP64 path within the
     # pair tolerances (32x the FP64 ones); 64 vectors fill the 128-row MMA tile
