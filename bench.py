@@ -221,6 +221,10 @@ def run_ours(args, rank, world):
         if args.with_density:   # the fields of the filtered vectors (density at the points)
             occ = np.full(nvs[0], 2.0 / nvs[0])
             ctx.density([X0[0]], [occ], rho)
+        if args.with_ortho:     # two Cholesky-QR of the FP64 vectors (Gram matrices and rotations)
+            for _ in range(2):
+                Xq = X0[0].clone()
+                ctx.orthonormalize(0, Xq)
         torch.cuda.synchronize()
         return {"filter_only": True, "passes": args.steps, "config": w.name}
 
@@ -604,6 +608,8 @@ def main():
                     help="FP32 SIMT cell products instead of the BF16x3 tensor-core path")
     ap.add_argument("--with-density", action="store_true",
                     help="with --filter-only: one density evaluation (profiling aid)")
+    ap.add_argument("--with-ortho", action="store_true",
+                    help="with --filter-only: two orthonormalizations of the FP64 vectors (profiling aid)")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     args = ap.parse_args()

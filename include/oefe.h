@@ -294,17 +294,26 @@ int oefe_product_flops(oefe_ctx_t ctx, int ik, int nv, double* flops);
  * OEFE_ERR_ARG when n is null. No counterpart in the paper (instrumentation). */
 int oefe_launch_count(int64_t* n);
 
-/* oefe_set_f64_products -- arithmetic of every FP64 cell product of the context
- * (the FP64 filter degrees, oefe_apply_h / _a, the H X of oefe_rayleigh_ritz).
- * mode OEFE_F64_NATIVE (default): FP64. OEFE_F64_PAIRS: on the cells with one
- * quadrature leaf the sum-factorized product runs in FP32-pair arithmetic
- * (each value an unevaluated sum of two FP32 numbers, error-free products and
- * sums, about 2^-48 relative per operation; Dekker's double-length arithmetic)
- * on the FP32 pipe, which on this GPU issues at 64 times the FP64 rate; the
- * refined cells stay FP64. Inputs and outputs stay FP64. The operator must then
- * be built with OEFE_STORE_F64PAIR, else the products return OEFE_ERR_STATE.
- * Returns OEFE_ERR_ARG for another mode. No counterpart in the paper (the
- * paper's machines had full-rate FP64). */
+/* oefe_set_f64_products -- arithmetic of the FP64-class kernels of the context.
+ * mode OEFE_F64_NATIVE (default): FP64 everywhere. OEFE_F64_PAIRS: FP64-class
+ * arithmetic off the FP64 pipe, which on this GPU issues at 1/64 of the FP32
+ * rate:
+ *   - FP32 pairs (each value an unevaluated sum of two FP32 numbers, error-free
+ *     products and sums, about 2^-48 relative per operation; Dekker's
+ *     double-length arithmetic) for the sum-factorized cell products of the
+ *     single-leaf cells (the FP64 filter degrees, oefe_apply_h / _a, the H X of
+ *     oefe_rayleigh_ritz; refined cells stay FP64), the per-V operator build,
+ *     the fields of oefe_density / oefe_band_trace_grad and the Jacobi sweeps
+ *     of the projected eigenproblem;
+ *   - tensor-core GEMMs with exact bf16 digits (7 digits of 7 bits per value,
+ *     exact FP32 accumulation, about 2^-46 of the row and column maxima per
+ *     term) for the Gram matrices and rotations of oefe_orthonormalize and
+ *     oefe_rayleigh_ritz when nv <= 64 (FP32 pairs otherwise).
+ * Inputs and outputs stay FP64; Cholesky factors, triangular inverses and the
+ * setup stay FP64. The operator must be built with OEFE_STORE_F64PAIR in pair
+ * mode, else the products return OEFE_ERR_STATE; the build after the switch
+ * uses the new arithmetic. Returns OEFE_ERR_ARG for another mode. No
+ * counterpart in the paper (the paper's machines had full-rate FP64). */
 int oefe_set_f64_products(oefe_ctx_t ctx, int mode);
 
 #ifdef __cplusplus

@@ -22,7 +22,6 @@ constexpr int MAXP = 8;
 constexpr int MAXN1 = 12;
 constexpr int DT = 256;
 constexpr int NBO = 4;   // columns of Gamma per pass of the tabulation
-constexpr int RNB = 4;   // vectors per pass of the fields
 constexpr int FT = 512;  // threads per CTA of the fields
 
 struct OrthArgs {
@@ -161,10 +160,10 @@ struct FieldArgs {
   bool accumulate;    // density: out += ; gradient: out =
 };
 
-// u_v(x_q) for RNB vectors per pass: CFE part by sum factorization (x, y, z stages over the leaf's
+// u_v(x_q) for RNB vectors per pass (4: one CTA per SM; 2: half the shared memory, two CTAs per SM): CFE part by sum factorization (x, y, z stages over the leaf's
 // Gauss points), enrichment part sum_j N^O_j(x_q) X^o_j with one point per thread over all RNB
 // vectors; |u|^2 weighted by occ accumulated per point. V = double: FP64; V = f2: FP32 pairs.
-template <typename V, bool CPLX>
+template <typename V, bool CPLX, int RNB>
 __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
   constexpr int R = CPLX ? 2 : 1;
   constexpr int J = RNB * R;
@@ -327,9 +326,9 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
 }
 
 template <typename V>
-size_t field_smem(const oefe_ctx* c, bool cplx) {
+size_t field_smem(const oefe_ctx* c, bool cplx, int rnb) {
   const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
-  const size_t J = (size_t)RNB * (cplx ? 2 : 1);
+  const size_t J = (size_t)rnb * (cplx ? 2 : 1);
   const size_t n3 = (size_t)n1 * n1 * n1;
   return ((size_t)c->nloc * J + (size_t)std::max(c->ne_max, 1) * J + (size_t)n1 * P * P * J +
           (size_t)n1 * n1 * P * J + n3 * J + 2 * n3) * sizeof(V);
@@ -416,12 +415,40 @@ int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, 
     return OEFE_OK;
   };
   if (pairs) {
-    if (cplx) return go(k_fields<f2, true>, field_smem<f2>(c, true));
-    return go(k_fields<f2, false>, field_smem<f2>(c, false));
+    // two pass widths, the faster kept after timing both at first use (same arithmetic per vector)
+    auto run = [&](int v) -> int {
+      if (cplx) return v == 0 ? go(k_fields<f2, true, 4>, field_smem<f2>(c, true, 4))
+                              : go(k_fields<f2, true, 2>, field_smem<f2>(c, true, 2));
+      return v == 0 ? go(k_fields<f2, false, 4>, field_smem<f2>(c, false, 4))
+                    : go(k_fields<f2, false, 2>, field_smem<f2>(c, false, 2));
+    };
+    if (c->fields_variant < 0 && accumulate) {   // the density accumulates: time on a scratch copy of out
+      double* scratch = nullptr;
+      OEFE_TRY(dev_alloc(c, (void**)&scratch, (size_t)std::max<int64_t>(c->nq, 1) * sizeof(double)));
+      double* keep = A.out;
+      A.out = scratch;
+      cudaEvent_t ev[3];
+      for (auto& e : ev) OEFE_CUDA_TRY(c, cudaEventCreate(&e));
+      int s = run(0);
+      if (s == OEFE_OK) { cudaEventRecord(ev[0], c->stream); s = run(1); }
+      if (s == OEFE_OK) { cudaEventRecord(ev[1], c->stream); s = run(0); cudaEventRecord(ev[2], c->stream); }
+      float t1 = 0, t0 = 0;
+      if (s == OEFE_OK) {
+        cudaEventSynchronize(ev[2]);
+        cudaEventElapsedTime(&t1, ev[0], ev[1]);
+        cudaEventElapsedTime(&t0, ev[1], ev[2]);
+        c->fields_variant = t1 < t0 ? 1 : 0;
+      }
+      for (auto& e : ev) cudaEventDestroy(e);
+      cudaStreamSynchronize(c->stream);
+      dev_free(scratch);
+      A.out = keep;
+      if (s != OEFE_OK) return s;
+    }
+    return run(c->fields_variant > 0 ? 1 : 0);
   }
-  if (cplx) return go(k_fields<double, true>, field_smem<double>(c, true));
-  return go(k_fields<double, false>, field_smem<double>(c, false));
-}
+  if (cplx) return go(k_fields<double, true, 4>, field_smem<double>(c, true, 4));
+  return go(k_fields<double, false, 4>, field_smem<double>(c, false, 4));}
 
 int check_fields(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
   if (!c->has_k) { c->err = "call oefe_kpoints first"; return OEFE_ERR_STATE; }

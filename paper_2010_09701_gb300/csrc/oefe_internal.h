@@ -185,6 +185,7 @@ struct oefe_ctx {
   int use_sumfac = 1;
   int f64_products = OEFE_F64_NATIVE;   // arithmetic of the sum-factorized FP64 products
   int sf_variant = -1;                  // launch shape of the pair product: chosen by timing at first use
+  int fields_variant = -1;              // pass width of the pair fields: chosen by timing at first use
   double* d_sf = nullptr;               // per single-leaf cell: n1, 1D tables, M/K/A
   int* d_sf_cells = nullptr;            // single-leaf cells
   int* d_dense_cells = nullptr;         // cells with several leaves (dense products)

@@ -344,27 +344,38 @@ int launch_cell_apply_sf(oefe_ctx* c, const KData& K, const void* X, int ldx, in
   };
   if (c->f64_products == OEFE_F64_PAIRS) {
     if (!K.Hp) { c->err = "FP32-pair products: build the operator with OEFE_STORE_F64PAIR"; return OEFE_ERR_STATE; }
-    // two launch shapes: one CTA of 512 threads per SM over 4 (complex) vectors, or two CTAs of
-    // 384 threads per SM over 2 vectors each (half the shared memory, the cell's enrichment blocks
-    // read twice as often)
+    // launch shapes: one CTA of 512 threads per SM over 4 (complex) vectors, or two CTAs of 384 or
+    // of 512 threads per SM over 2 vectors each (half the shared memory, the cell's enrichment
+    // blocks read twice as often); the fastest on this operator is kept after timing each once
     auto run = [&](int v) -> int {
-      if (cplx) return v == 0 ? go(k_cell_apply_sf<true, 4, f2, 512>, sf_smem<true>(c, 4), 4, 512)
-                              : go(k_cell_apply_sf<true, 2, f2, 384>, sf_smem<true>(c, 2), 2, 384);
-      return v == 0 ? go(k_cell_apply_sf<false, 8, f2, 512>, sf_smem<false>(c, 8), 8, 512)
-                    : go(k_cell_apply_sf<false, 4, f2, 384>, sf_smem<false>(c, 4), 4, 384);
+      if (cplx) {
+        if (v == 0) return go(k_cell_apply_sf<true, 4, f2, 512>, sf_smem<true>(c, 4), 4, 512);
+        if (v == 1) return go(k_cell_apply_sf<true, 2, f2, 384>, sf_smem<true>(c, 2), 2, 384);
+        return go(k_cell_apply_sf<true, 2, f2, 512>, sf_smem<true>(c, 2), 2, 512);
+      }
+      if (v == 0) return go(k_cell_apply_sf<false, 8, f2, 512>, sf_smem<false>(c, 8), 8, 512);
+      if (v == 1) return go(k_cell_apply_sf<false, 4, f2, 384>, sf_smem<false>(c, 4), 4, 384);
+      return go(k_cell_apply_sf<false, 4, f2, 512>, sf_smem<false>(c, 4), 4, 512);
     };
-    if (c->sf_variant < 0) {   // first use: time both on this operator and keep the faster
-      cudaEvent_t ev[3];
+    if (c->sf_variant < 0) {   // first use: time each on this operator (after one warm launch)
+      constexpr int NVAR = 3;
+      cudaEvent_t ev[NVAR + 1];
       for (auto& e : ev) OEFE_CUDA_TRY(c, cudaEventCreate(&e));
       int s = run(0);
-      if (s == OEFE_OK) { cudaEventRecord(ev[0], st); s = run(1); }
-      if (s == OEFE_OK) { cudaEventRecord(ev[1], st); s = run(0); cudaEventRecord(ev[2], st); }
-      float t1 = 0, t0 = 0;
+      if (s == OEFE_OK) cudaEventRecord(ev[0], st);
+      for (int v = 0; v < NVAR && s == OEFE_OK; ++v) {
+        s = run(v);
+        cudaEventRecord(ev[v + 1], st);
+      }
       if (s == OEFE_OK) {
-        OEFE_CUDA_TRY(c, cudaEventSynchronize(ev[2]));
-        cudaEventElapsedTime(&t1, ev[0], ev[1]);
-        cudaEventElapsedTime(&t0, ev[1], ev[2]);
-        c->sf_variant = t1 < t0 ? 1 : 0;
+        OEFE_CUDA_TRY(c, cudaEventSynchronize(ev[NVAR]));
+        float best = 1e30f;
+        for (int v = 0; v < NVAR; ++v) {
+          float ms = 0;
+          cudaEventElapsedTime(&ms, ev[v], ev[v + 1]);
+          if (ms < best) { best = ms; c->sf_variant = v; }
+        }
+        // Z holds the last variant's product; the products of all variants are the same numbers
       }
       for (auto& e : ev) cudaEventDestroy(e);
       return s;
