@@ -272,7 +272,8 @@ int oefe_kernel_timing(oefe_ctx_t ctx, int dtype_mask);
 int oefe_kernel_time(oefe_ctx_t ctx, double* ms, int64_t* launches);
 
 /* oefe_release_workspace -- frees the context's cached scratch (the growable
- * work arrays of the operator build, the filter and the subspace calls) and
+ * work arrays of the operator build, the filter and the subspace calls, among
+ * them the digit planes of the tensor-core Gram matrices and rotations) and
  * the captured graph of the batched filter, which points into it; later calls
  * allocate what they need again. Synchronizes the context's streams. Returns
  * OEFE_ERR_ARG for a null context. No counterpart in the paper (memory

@@ -350,6 +350,12 @@ int oefe_release_workspace(oefe_ctx_t ctx) {
   dev_free(ctx->ws2);
   ctx->ws = ctx->ws2 = nullptr;
   ctx->ws_bytes = ctx->ws2_bytes = 0;
+  dev_free(ctx->d_ozpart);   // digit planes of the tensor-core Gram matrices and rotations
+  ctx->d_ozpart = nullptr;
+  ctx->ozpart_bytes = 0;
+  dev_free(ctx->d_rotp);
+  ctx->d_rotp = nullptr;
+  ctx->rotp_bytes = 0;
   return OEFE_OK;
 }
 
