@@ -238,13 +238,10 @@ def run_ours(args, rank, world):
     if batched:
         tune_ms = [float(x) for x in ctx.filter_autotune(X0)]
 
-    def step(record=False, x_ready=None):
+    def step(record=False):
         t = [mark()]
         ctx.build_hamiltonian(V, store)
         t.append(mark())
-        if x_ready is not None:
-            # the starting vectors arrive on another stream while the operator is built
-            stream.wait_event(x_ready)
         eigs = []
         ortho_rr = []
         if batched:
@@ -469,34 +466,23 @@ def run_ours(args, rank, world):
         else:
             roof2 = roof_fp64
 
-    # end to end through the public API with host buffers (H2D of V and X0, D2H of rho and eigenvalues).
-    # The potential goes first on the compute stream (the build reads it); the starting vectors
-    # go on a copy stream, overlapped with the build, and the filter waits for them.
+    # end to end through the public API with host buffers (H2D of V and X0, D2H of rho and eigenvalues)
     e2e = None
     if not args.skip_e2e:
         Vh = V.cpu().pin_memory()
         X0h = [x.cpu().pin_memory() for x in X0]
         rho_h = torch.empty(rho.shape, dtype=rho.dtype).pin_memory()
-        copy_stream = torch.cuda.Stream()
-        h2d_ms = []
         torch.cuda.synchronize()
         t_start = time.perf_counter()
         ee0 = torch.cuda.Event(enable_timing=True)
         ee1 = torch.cuda.Event(enable_timing=True)
         ee0.record(stream)
         for _ in range(args.e2e_steps):
-            copy_stream.wait_stream(stream)   # the previous step has read X0
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(copy_stream):
-                c0.record(copy_stream)
-                for ik in range(nk):
-                    X0[ik].copy_(X0h[ik], non_blocking=True)
-                c1.record(copy_stream)
             V.copy_(Vh, non_blocking=True)
-            eigs_e, _ = step(x_ready=c1)
+            for ik in range(nk):
+                X0[ik].copy_(X0h[ik], non_blocking=True)
+            eigs_e, _ = step()
             rho_h.copy_(rho, non_blocking=True)
-            h2d_ms.append((c0, c1))
         ee1.record(stream)
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t_start) / args.e2e_steps
@@ -505,9 +491,7 @@ def run_ours(args, rank, world):
         bo = rho.numel() * 8 + sum(len(e) * 8 for e in eigs_e)
         e2e_ms = max_over_ranks(max(e2e_ms, wall * 1e3), world, "cuda")
         e2e = {"value": whole_job_tflops(flops_step, world, e2e_ms), "unit": "TFLOP/s",
-               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms,
-               "h2d_vectors_ms": sum(a.elapsed_time(b) for a, b in h2d_ms) / len(h2d_ms),
-               "h2d_vectors_overlapped": "with the operator build, on a copy stream"}
+               "h2d_bytes_per_step": int(bi), "d2h_bytes_per_step": int(bo), "ms_per_step": e2e_ms}
 
     cpu = None
     if rank == 0 and not args.skip_cpu_baseline:
