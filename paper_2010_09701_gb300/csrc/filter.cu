@@ -184,20 +184,61 @@ __global__ void k_node_update(const typename Sc<T, C>::type* __restrict__ Z, con
   }
 }
 
-// Enrichment rows: raw sums over cells (FP64 accumulation).
-template <typename T, bool C>
-__global__ void k_enr_reduce(const typename Sc<T, C>::type* __restrict__ Z, const int64_t* __restrict__ enr_off,
-                             const int64_t* __restrict__ enr_slot, int nO, int nv, cd* __restrict__ Yo) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nO * nv) return;
-  const int nu = t / nv, v = t % nv;
-  double sx = 0, sy = 0;
-  for (int64_t s = enr_off[nu]; s < enr_off[nu + 1]; ++s) {
-    const auto z = Z[enr_slot[s] * nv + v];
-    if constexpr (C) { sx += (double)z.x; sy += (double)z.y; }
-    else sx += (double)z;
+// Enrichment rows: raw sums over the cells' product rows of one enrichment function (FP64
+// accumulation), by one CTA: each warp takes 32 vectors and one group of the slots (every G-th
+// slot, four loads in flight), and the groups' partial sums are added in a fixed order.
+constexpr int ER_T = 1024;
+
+template <typename S, bool C>
+__device__ __forceinline__ void enr_reduce_cta(const S* __restrict__ Z, int nv, int64_t s0, int64_t s1,
+                                               const int64_t* __restrict__ enr_slot, cd* __restrict__ yo) {
+  __shared__ double2 red[ER_T];
+  constexpr int NW = ER_T / 32;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nvc = (nv + 31) / 32;
+  for (int vc0 = 0; vc0 < nvc; vc0 += NW) {
+    const int nc = min(NW, nvc - vc0);   // vector chunks of this pass
+    const int G = NW / nc;               // slot groups
+    const int g = w / nc, v = (vc0 + w % nc) * 32 + lane;
+    double sx = 0, sy = 0;
+    auto add = [&](const S z) {
+      if constexpr (C) { sx += (double)z.x; sy += (double)z.y; }
+      else sx += (double)z;
+    };
+    if (g < G && v < nv) {
+      int64_t s = s0 + g;
+      for (; s + 3 * G < s1; s += 4 * G) {
+        const int64_t a0 = enr_slot[s], a1 = enr_slot[s + G], a2 = enr_slot[s + 2 * G], a3 = enr_slot[s + 3 * G];
+        const S z0 = Z[a0 * nv + v], z1 = Z[a1 * nv + v], z2 = Z[a2 * nv + v], z3 = Z[a3 * nv + v];
+        add(z0);
+        add(z1);
+        add(z2);
+        add(z3);
+      }
+      for (; s < s1; s += G) add(Z[enr_slot[s] * nv + v]);
+    }
+    red[threadIdx.x] = make_double2(sx, sy);
+    __syncthreads();
+    if (w < nc) {
+      double ax = 0, ay = 0;
+      for (int gg = 0; gg < G; ++gg) {
+        const double2 r = red[(gg * nc + w) * 32 + lane];
+        ax += r.x;
+        ay += r.y;
+      }
+      if (v < nv) yo[v] = mkc(ax, ay);
+    }
+    __syncthreads();
   }
-  Yo[t] = mkc(sx, sy);
+}
+
+// one CTA per enrichment function
+template <typename T, bool C>
+__global__ void __launch_bounds__(ER_T) k_enr_reduce(const typename Sc<T, C>::type* __restrict__ Z,
+                                                     const int64_t* __restrict__ enr_off,
+                                                     const int64_t* __restrict__ enr_slot, int nv, cd* __restrict__ Yo) {
+  const int nu = blockIdx.x;
+  enr_reduce_cta<typename Sc<T, C>::type, C>(Z, nv, enr_off[nu], enr_off[nu + 1], enr_slot, Yo + (size_t)nu * nv);
 }
 
 // Enrichment rows: Y = Yo (mode 0), (M^oo)^{-1} Yo (mode 1), or the recurrence (mode 2).
@@ -329,22 +370,14 @@ __global__ void __launch_bounds__(256) k_node_update_multi(const NodeK* __restri
   }
 }
 
+// one CTA per (enrichment function, k-point)
 template <typename T, bool C>
-__global__ void k_enr_reduce_multi(const NodeK* __restrict__ P, const int64_t* __restrict__ enr_off,
-                                   const int64_t* __restrict__ enr_slot, int nO) {
+__global__ void __launch_bounds__(ER_T) k_enr_reduce_multi(const NodeK* __restrict__ P, const int64_t* __restrict__ enr_off,
+                                                           const int64_t* __restrict__ enr_slot) {
   using S = typename Sc<T, C>::type;
-  const NodeK p = P[blockIdx.y];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= nO * p.nv) return;
-  const int nu = t / p.nv, v = t % p.nv;
-  const S* Z = (const S*)p.Z;
-  double sx = 0, sy = 0;
-  for (int64_t s = enr_off[nu]; s < enr_off[nu + 1]; ++s) {
-    const auto z = Z[enr_slot[s] * p.nv + v];
-    if constexpr (C) { sx += (double)z.x; sy += (double)z.y; }
-    else sx += (double)z;
-  }
-  p.Yo[t] = mkc(sx, sy);
+  const NodeK& p = P[blockIdx.y];
+  const int nu = blockIdx.x;
+  enr_reduce_cta<S, C>((const S*)p.Z, p.nv, enr_off[nu], enr_off[nu + 1], enr_slot, p.Yo + (size_t)nu * p.nv);
 }
 
 template <typename T, bool C>
@@ -438,7 +471,7 @@ int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const vo
                                                      (const S*)Xm1, ldm1, (S*)Y, ldy);
   if (c->nO > 0) {
     const int eb = (c->nO * nv + 127) / 128;
-    OEFE_COUNTED k_enr_reduce<T, C><<<eb, 128, 0, c->stream>>>((const S*)Zbuf, c->d_enr_off, c->d_enr_slot, c->nO, nv, Yo);
+    OEFE_COUNTED k_enr_reduce<T, C><<<c->nO, ER_T, 0, c->stream>>>((const S*)Zbuf, c->d_enr_off, c->d_enr_slot, nv, Yo);
     OEFE_COUNTED k_enr_update<T, C><<<eb, 128, 0, c->stream>>>(Yo, K.Mooinv, c->nO, nv, c->nh, st.mode, st.alpha, st.cshift,
                                                   st.beta, (const S*)Xk, ldk, (const S*)Xm1, ldm1, (S*)Y, ldy);
   }
@@ -670,21 +703,21 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
       }
     }
     if (timed) cudaEventRecordWithFlags(c->bev_kernel[2 * j + 1], c->bstream, cudaEventRecordExternal);
-    dim3 g1(nblocks, P.nk), g2(std::max(eb, 1), P.nk);
+    dim3 g1(nblocks, P.nk), g2(std::max(eb, 1), P.nk), gr(std::max(c->nO, 1), P.nk);
     if (cplx) {
       OEFE_COUNTED k_node_update_multi<float, true><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off, c->d_node_slot,
                                                                    c->d_m, c->nh);
       if (c->nO > 0) {
-        OEFE_COUNTED k_enr_reduce_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off, c->d_enr_slot,
-                                                                    c->nO);
+        OEFE_COUNTED k_enr_reduce_multi<float, true><<<gr, ER_T, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
+                                                                     c->d_enr_slot);
         OEFE_COUNTED k_enr_update_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
       }
     } else {
       OEFE_COUNTED k_node_update_multi<float, false><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off,
                                                                     c->d_node_slot, c->d_m, c->nh);
       if (c->nO > 0) {
-        OEFE_COUNTED k_enr_reduce_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
-                                                                     c->d_enr_slot, c->nO);
+        OEFE_COUNTED k_enr_reduce_multi<float, false><<<gr, ER_T, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
+                                                                      c->d_enr_slot);
         OEFE_COUNTED k_enr_update_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
       }
     }
