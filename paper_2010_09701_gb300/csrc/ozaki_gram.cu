@@ -411,6 +411,19 @@ __global__ void k_oz_rot_bdigits(const S* C, int nv, bool herm, unsigned char* p
     }
 }
 
+// x 2^sc as a double (exact): the float's sign and fraction with the exponent rebased, by integer
+// operations (IEEE 754 binary32 and binary64 layouts); zero, subnormal, infinite or NaN x and a
+// result outside the normal range go through ldexp
+__device__ __forceinline__ double f_scaled(float x, int sc) {
+  const unsigned int b = __float_as_uint(x);
+  const int ef = (int)((b >> 23) & 0xFFu);
+  const int e = ef - 127 + 1023 + sc;
+  if (ef == 0 || ef == 255 || e < 1 || e > 2046) return ldexp((double)x, sc);
+  const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)e << 52) |
+                                  ((unsigned long long)(b & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+
 struct RotArgs {
   const unsigned char* pa;   // tile digit planes (2 K halves per tile)
   const int* ea;             // tile row exponents
@@ -537,7 +550,7 @@ __global__ void __launch_bounds__(OZ_T, 1) k_rot_oz(const RotArgs A) {
             const int col = c0 + c;
             if (col >= A.nv) continue;
             const int sc = E + Fexp[col] - 14;
-            const double val = ldexp(f2_to(S[c]), sc);
+            const double val = f_scaled(S[c].h, sc) + f_scaled(S[c].l, sc);
             if (A.cplx) {
               double* xr = reinterpret_cast<double*>(A.X) + 2 * ((size_t)grow * A.ldx + col);
               xr[nh] = val;
