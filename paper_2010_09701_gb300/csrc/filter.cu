@@ -185,14 +185,17 @@ __global__ void k_node_update(const typename Sc<T, C>::type* __restrict__ Z, con
 }
 
 // Enrichment rows: raw sums over the cells' product rows of one enrichment function (FP64
-// accumulation), by one CTA: each warp takes 32 vectors and one group of the slots (every G-th
-// slot, four loads in flight), and the groups' partial sums are added in a fixed order.
+// accumulation), by one CTA: the row offsets of the function's slots are staged in shared memory
+// (chunks of ER_SC), each warp takes 32 vectors and one group of the slots (every G-th slot, eight
+// loads in flight), and the groups' partial sums are added in a fixed order.
 constexpr int ER_T = 1024;
+constexpr int ER_SC = 2048;
 
 template <typename S, bool C>
 __device__ __forceinline__ void enr_reduce_cta(const S* __restrict__ Z, int nv, int64_t s0, int64_t s1,
                                                const int64_t* __restrict__ enr_slot, cd* __restrict__ yo) {
   __shared__ double2 red[ER_T];
+  __shared__ int64_t off[ER_SC];
   constexpr int NW = ER_T / 32;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int nvc = (nv + 31) / 32;
@@ -200,22 +203,28 @@ __device__ __forceinline__ void enr_reduce_cta(const S* __restrict__ Z, int nv, 
     const int nc = min(NW, nvc - vc0);   // vector chunks of this pass
     const int G = NW / nc;               // slot groups
     const int g = w / nc, v = (vc0 + w % nc) * 32 + lane;
+    const bool active = g < G && v < nv;
     double sx = 0, sy = 0;
     auto add = [&](const S z) {
       if constexpr (C) { sx += (double)z.x; sy += (double)z.y; }
       else sx += (double)z;
     };
-    if (g < G && v < nv) {
-      int64_t s = s0 + g;
-      for (; s + 3 * G < s1; s += 4 * G) {
-        const int64_t a0 = enr_slot[s], a1 = enr_slot[s + G], a2 = enr_slot[s + 2 * G], a3 = enr_slot[s + 3 * G];
-        const S z0 = Z[a0 * nv + v], z1 = Z[a1 * nv + v], z2 = Z[a2 * nv + v], z3 = Z[a3 * nv + v];
-        add(z0);
-        add(z1);
-        add(z2);
-        add(z3);
+    for (int64_t c0 = s0; c0 < s1; c0 += ER_SC) {   // the same trip count in every thread
+      const int m = (int)min((int64_t)ER_SC, s1 - c0);
+      __syncthreads();
+      for (int j = threadIdx.x; j < m; j += ER_T) off[j] = enr_slot[c0 + j] * nv;
+      __syncthreads();
+      if (active) {
+        int j = g;
+        for (; j + 7 * G < m; j += 8 * G) {
+          S z[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) z[u] = Z[off[j + u * G] + v];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) add(z[u]);
+        }
+        for (; j < m; j += G) add(Z[off[j] + v]);
       }
-      for (; s < s1; s += G) add(Z[enr_slot[s] * nv + v]);
     }
     red[threadIdx.x] = make_double2(sx, sy);
     __syncthreads();
