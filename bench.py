@@ -184,6 +184,7 @@ def run_ours(args, rank, world):
     if pairs:
         store |= P.STORE_F64PAIR
     ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
+    ctx.set_product_shape(args.product_shape)
     if args.filter_only:   # profiling aid: the low-precision matrices (and FP64 ones on request) only
         store = (split if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
         if args.with_fp64 and pairs:
@@ -602,6 +603,8 @@ def main():
                          "comparison starts from")
     ap.add_argument("--f64-products", default="pairs", choices=["pairs", "native"],
                     help="arithmetic of the FP64-class cell products of the mixed step")
+    ap.add_argument("--product-shape", type=int, default=-1, choices=[-1, 0, 1, 2],
+                    help="launch shape of the FP32-pair cell products (-1: timed at first use)")
     ap.add_argument("--bf16x3", action="store_true",
                     help="two-part bf16 split of the cell matrices (BF16x3) instead of three parts (BF16x6)")
     ap.add_argument("--fp32-simt", dest="tensor", action="store_false",

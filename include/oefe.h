@@ -317,6 +317,14 @@ int oefe_launch_count(int64_t* n);
  * counterpart in the paper (the paper's machines had full-rate FP64). */
 int oefe_set_f64_products(oefe_ctx_t ctx, int mode);
 
+/* oefe_set_product_shape -- launch shape of the FP32-pair cell products of the
+ * single-leaf cells. shape -1 (default): each shape is timed once at the first
+ * pair product of the context and the fastest is kept; 0: 4 complex (8 real)
+ * vectors per CTA of 512 threads; 1: 2 complex (4 real) vectors per CTA of
+ * 384 threads; 2: 2 complex (4 real) vectors per CTA of 512 threads. Every
+ * shape computes the same numbers. Returns OEFE_ERR_ARG for another value. */
+int oefe_set_product_shape(oefe_ctx_t ctx, int shape);
+
 #ifdef __cplusplus
 }
 #endif

@@ -62,6 +62,7 @@ SIGNATURES = [
     ("oefe_product_flops", _I, [_P, _I, _I, _DP]),
     ("oefe_launch_count", _I, [_c.POINTER(_c.c_int64)]),
     ("oefe_set_f64_products", _I, [_P, _I]),
+    ("oefe_set_product_shape", _I, [_P, _I]),
 ]
 
 _lib = None
@@ -362,6 +363,10 @@ class Context:
         """Arithmetic of the FP64 cell products: F64_NATIVE, or F64_PAIRS (FP32 pairs on the
         single-leaf cells; needs an operator built with STORE_F64PAIR)."""
         self._check(self.lib.oefe_set_f64_products(self.h, int(mode)))
+
+    def set_product_shape(self, shape):
+        """Launch shape of the FP32-pair cell products: -1 timed at first use (default), or 0, 1, 2."""
+        self._check(self.lib.oefe_set_product_shape(self.h, int(shape)))
 
     def release_workspace(self):
         """Free the cached scratch arrays (the build's are several times the filter's)."""

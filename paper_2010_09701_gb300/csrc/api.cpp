@@ -376,6 +376,16 @@ int oefe_set_f64_products(oefe_ctx_t ctx, int mode) {
   return OEFE_OK;
 }
 
+int oefe_set_product_shape(oefe_ctx_t ctx, int shape) {
+  CTX_CHECK(ctx);
+  if (shape < -1 || shape > 2) {
+    ctx->err = "set_product_shape: shape must be -1 (timed at first use), 0, 1 or 2";
+    return OEFE_ERR_ARG;
+  }
+  ctx->sf_variant = shape;
+  return OEFE_OK;
+}
+
 int oefe_launch_count(int64_t* n) {
   if (!n) return OEFE_ERR_ARG;
   *n = (int64_t)g_launches.load(std::memory_order_relaxed);

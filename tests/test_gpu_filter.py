@@ -213,6 +213,19 @@ def test_apply_h_c1_fp32_pair_products(k):
     assert err < 3.2e-12
     # the pair path ran: it differs from FP64 by more than FP64 rounding alone
     assert np.max(np.abs(Yp.cpu().numpy() - Yn.cpu().numpy()) / scale) > 1e-15
+    # every launch shape of the pair product gives the same products
+    ctx.set_f64_products(F64_PAIRS)
+    Ys = torch.empty_like(Xd)
+    for shape in (0, 1, 2):
+        ctx.set_product_shape(shape)
+        ctx.apply_h(0, Xd, Ys)
+        ys = Ys.cpu().numpy()
+        assert np.max(np.abs(ys - HX) / scale) < 3.2e-12
+        assert np.max(np.abs(ys - Yp.cpu().numpy()) / scale) < 1e-14
+    ctx.set_product_shape(-1)
+    with pytest.raises(OefeError):
+        ctx.set_product_shape(3)
+    ctx.set_f64_products(F64_NATIVE)
     with pytest.raises(OefeError):
         ctx.set_f64_products(7)
     # an operator without the pair copy refuses pair products
