@@ -42,7 +42,8 @@ TRAFFIC_TENSOR = {   # bf16 parts of the split -> DRAM bytes per (k, cell, 64-ve
 }
 TRAFFIC_FP64 = None   # {"bytes_per_cell", "source"} from a capture of the current FP64 product kernels
 # the FP64-class products in pair mode: DRAM bytes per launch and cell of each kind, from the 8^3 capture
-TRAFFIC_PAIR = {"sf_bytes_per_cell": (343.697e6 + 150.831e6) / 448, "dense_bytes_per_cell": (319.123e6 + 23.752e6) / 64,
+# of the launch shape kept at the bench size (two vectors per CTA of 512 threads)
+TRAFFIC_PAIR = {"sf_bytes_per_cell": (344.007e6 + 151.686e6) / 448, "dense_bytes_per_cell": (319.195e6 + 19.950e6) / 64,
                 "source": "profiles/fp64_class_products_c3small_8cube_p6.md"}
 
 
