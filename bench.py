@@ -47,6 +47,16 @@ TRAFFIC_PAIR = {"sf_bytes_per_cell": (344.007e6 + 151.686e6) / 448, "dense_bytes
                 "source": "profiles/fp64_class_products_c3small_8cube_p6.md"}
 
 
+def workload_text(w):
+    """The workload as the JSON line names it (both arms): cell, mesh, basis, k-points, vectors."""
+    zs = "/".join(str(int(z)) for z in sorted(set(np.asarray(w.Z).tolist()), reverse=True))
+    kg = tuple(w.kgrid)
+    return ("zincblende a=%g bohr %d atoms (Z %s), graded %d^3 cells p=%d, %d enrichment functions, "
+            "MP %dx%dx%d (%d k), %d vectors/k, Chebyshev degree %d"
+            % (w.a, w.natoms, zs, w.ncell, w.p, len(W.ORBITALS_1S_2P) * w.natoms, kg[0], kg[1], kg[2],
+               len(w.nv), w.nv[0], w.degree))
+
+
 def nucleus_cells(w):
     """Cells whose closed box holds a nucleus (periodic images included): the refined cells."""
     xb = W.mesh_breakpoints(w)
@@ -503,9 +513,9 @@ def run_ours(args, rank, world):
            "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "c64+c128", "data": "synthetic",
-           "config": {"workload": "zincblende a=8.5 bohr 8 atoms (Z 14/6), graded 16^3 cells p=6, 40 enrichment "
-                                  "functions, MP 2x2x1 (4 k), 64 vectors/k, Chebyshev degree 30, mixed filter "
-                                  "(29 FP32-class degrees + last FP64), FP64 Cholesky-QR / Rayleigh-Ritz / density",
+           "config": {"workload": workload_text(w),
+                      "arithmetic": "mixed filter (%d FP32-class degrees + last FP64-class), FP64-class Cholesky-QR / "
+                                    "Rayleigh-Ritz / density" % (w.degree - 1),
                       "f64_products": ("FP32 pairs on single-leaf cells (last degree and Rayleigh-Ritz H X)" if pairs
                                        else "FP64"),
                       "n_dof_per_k": int(n), "cells": int(len(naug)), "mean_n_aug": float(np.mean(naug)),
@@ -578,8 +588,8 @@ def run_reference(args, rank, world):
             "value": res["value"], "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": res["s_per_step"] * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "c128", "data": "synthetic",
-            "config": {"workload": "zincblende a=8.5 bohr 8 atoms, graded 16^3 cells p=6, 64 vectors, degree 30 "
-                                   "(bounded sample, see cpu_baseline.sample)"},
+            "config": {"workload": workload_text(w),
+                       "arithmetic": "FP64 (the oracle), on a bounded sample of the workload (cpu_baseline.sample)"},
             "cpu_baseline": res,
             "e2e": {"value": res["value"], "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
