@@ -42,3 +42,13 @@ def test_workload_description_follows_the_configuration():
                     "MP 2x2x1 (4 k), 64 vectors/k, Chebyshev degree 30")
     small = bench.workload_text(W.CONFIGS["c3small"]())
     assert "graded 8^3 cells" in small and "(2 k)" in small
+
+
+def test_refined_cell_count_used_for_traffic_scaling():
+    # the graded meshes put each of the 8 nuclei on a corner shared by 8 cells: 64 refined cells,
+    # the rest single-leaf (the bench scales the captured traffic by these counts)
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    for name in ("c3", "c3small"):
+        assert bench.nucleus_cells(W.CONFIGS[name]()) == 64
