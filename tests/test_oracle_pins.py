@@ -375,3 +375,36 @@ def test_lanczos_upper_bound():
     b = solver.lanczos_upper_bound(pr.apply_H, pr.apply_M, pr.apply_Minv, v0, 30)
     assert b >= ev[-1] - 1e-8
     assert b < ev[-1] * 1.2
+
+
+@pytest.mark.parametrize("k", [(0.0, 0.0, 0.0), (0.25, -0.4, 0.1)])
+def test_residual_norms_closed_form(k):
+    # residual of a mixture of two exact eigenvectors (Sec. IV, Eq. ProjKS; the norm of the survey's
+    # step 16). With M-orthonormal eigenpairs (eps_i, u_i), (eps_j, u_j) of H u = eps M u and
+    # u = s (u_i + d u_j):
+    #   H u - t M u = s M [(eps_i - t) u_i + d (eps_j - t) u_j],
+    #   ||.||_{M^-1}^2 = s^2 [(eps_i - t)^2 + d^2 (eps_j - t)^2],  ||u||_M^2 = s^2 (1 + d^2),
+    # and at the Rayleigh quotient t = (eps_i + d^2 eps_j) / (1 + d^2) the ratio is
+    # |d| |eps_i - eps_j| / (1 + d^2). The lumped-plus-enrichment mass is far from a multiple of I,
+    # so the 2-norm, or M in place of M^-1, gives other numbers; the scale s = 3.7 catches a dropped
+    # denominator.
+    pr, _ = small_case(k=k, n=1, p=3)
+    H = pr.assemble_H().toarray()
+    Md = pr.dense_M()
+    md = np.real(np.diag(Md))[: pr.nh]
+    assert md.max() / md.min() > 3.0          # the pin needs a non-uniform mass
+    ev, U = sla.eigh(H, Md)
+    pairs = [(0, 3, 0.5), (2, 7, -0.2), (5, 1, 1.3), (9, 4, 0.05)]
+    s = 3.7
+    X = np.stack([s * (U[:, i] + d * U[:, j]) for i, j, d in pairs], axis=1)
+    rq = np.array([(ev[i] + d * d * ev[j]) / (1 + d * d) for i, j, d in pairs])
+    expect = np.array([abs(d) * abs(ev[i] - ev[j]) / (1 + d * d) for i, j, d in pairs])
+    got = solver.residual_norms(pr, X, rq)
+    assert np.allclose(got, expect, rtol=1e-9, atol=1e-12)
+    # any other shift t: the general form above
+    t = rq + np.array([0.3, -1.1, 0.7, 2.0])
+    expect_t = np.array([math.sqrt(((ev[i] - tt) ** 2 + d * d * (ev[j] - tt) ** 2) / (1 + d * d))
+                         for (i, j, d), tt in zip(pairs, t)])
+    assert np.allclose(solver.residual_norms(pr, X, t), expect_t, rtol=1e-9, atol=1e-12)
+    # an exact eigenvector at its eigenvalue has no residual
+    assert np.max(solver.residual_norms(pr, s * U[:, :6], ev[:6])) < 1e-9 * np.max(np.abs(ev[:6]))
