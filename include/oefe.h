@@ -163,7 +163,9 @@ int oefe_apply_a(oefe_ctx_t ctx, int ik, const void* X, void* Y, int nv, int ld,
  * earlier with allocations, as always).
  * - The first call on a device looks up the array's device address on that
  *   device (cudaGetSymbolAddress); make that first call outside any stream
- *   capture.
+ *   capture. The address is kept for later calls while the CUDA context it
+ *   came from is still current; after a device reset (a new primary context)
+ *   the next call looks it up again, so make that call outside a capture too.
  * - Problems needing more than the array (ncells * npad * nv * sizeof(scalar)
  *   rounded up to 256 bytes, plus n_O * nv * 16 bytes) are refused with
  *   OEFE_ERR_ARG; oefe_last_error gives the sizes.

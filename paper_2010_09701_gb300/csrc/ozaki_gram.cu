@@ -8,7 +8,8 @@
 // common exponent E_i (F_j):  x = 2^(E-49) (c0 2^42 + c1 2^35 + ... + c6), c0 in [-128, 127], the
 // others in [0, 127], exact to 2^(E-49) (truncation of x 2^(49-E) to an integer, taken from the
 // bits of x by integer operations). A digit is exact
-// in bf16; a product of two digits is below 2^14; the sum that one accumulator of level d = s + t
+// in bf16; a product of two digits is at most 2^14 in magnitude (c0 c0 = (-128)^2 = 2^14 is the largest);
+// the sum that one accumulator of level d = s + t
 // (at most 7 digit pairs) takes over 64 rows stays below 2^24, so the FP32 accumulation of the
 // tensor cores is exact. The levels d = 0..6 (28 digit products) are kept, the rest (below
 // 2^-49 of the row and column maxima) dropped; levels 6..4 are combined in FP32 (2^-28 below
@@ -47,6 +48,11 @@ constexpr int BH = OZ_N * 128;      // the half of a plane one CTA takes from B
 constexpr size_t OZ_SMEM = 1024 + (size_t)PASS_BYTES + (size_t)OZ_S * BH;
 constexpr int OZ_TCOLS = 512;       // tensor-memory columns (7 x 64 used)
 constexpr int DG_T = 256;           // threads per CTA of the digits kernel
+// Exactness of one accumulator in FP32: at most OZ_S digit pairs per level, each product at most
+// 2^14 in magnitude, summed over the rows one accumulator takes (OZ_K for a Gram pass, 2 OZ_K for a
+// rotation, whose two K halves share the accumulators), must stay within 2^24.
+static_assert((long long)OZ_S * OZ_K * (1LL << 14) <= (1LL << 24), "Gram pass: level sums must be exact in FP32");
+static_assert((long long)OZ_S * 2 * OZ_K * (1LL << 14) <= (1LL << 24), "rotation: level sums must be exact in FP32");
 
 __device__ __forceinline__ double ld_part(const void* M, int ld, long long r, int c, int part, bool cplx) {
   if (cplx) {
@@ -307,7 +313,7 @@ __global__ void __launch_bounds__(OZ_T, 1) k_gram_oz(const OzArgs A) {
 // imaginary parts), B = the real form of G, N half 0 the real parts of the products, half 1 the
 // imaginary parts: B[(0, j)][(0, n)] = Re G_jn, B[(0, j)][(1, n)] = Im G_jn, B[(1, j)][(0, n)] =
 // -Im G_jn, B[(1, j)][(1, n)] = Re G_jn. The exponent of an A row covers both K halves, so the two
-// halves accumulate into the same (exact) accumulators: 7 pairs x 128 x 2^14 < 2^24.
+// halves accumulate into the same (exact) accumulators: 7 pairs x 128 x 2^14 <= 2^24.
 
 struct RotDigArgs {
   const void* X;

@@ -17,8 +17,33 @@ namespace {
 static __device__ __align__(256) unsigned char g_noalloc_scratch[OEFE_NOALLOC_SCRATCH_BYTES];
 
 constexpr int MAX_DEVICES = 64;
-void* g_scratch_addr[MAX_DEVICES] = {};
+struct ScratchAddr {
+  void* addr = nullptr;   // device address of g_noalloc_scratch
+  void* owner = nullptr;  // the CUDA context that address belongs to
+};
+ScratchAddr g_scratch_addr[MAX_DEVICES];
 std::mutex g_scratch_mutex;
+
+// The CUDA context current on this thread (driver entry point, no link-time dependency on libcuda),
+// or null when it cannot be queried. A device reset replaces the primary context, and with it the
+// module that holds the array, so an address is only reused while its context is still current.
+void* current_context() {
+  typedef int (*ctx_get_current_fn)(void**);
+  static ctx_get_current_fn fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (ctx_get_current_fn)p;
+    cudaGetLastError();
+  }
+  void* cur = nullptr;
+  if (!fn || fn(&cur) != 0) return nullptr;
+  return cur;
+}
 
 int scratch_address(oefe_ctx* c, void** out) {
   if (c->device < 0 || c->device >= MAX_DEVICES) {
@@ -26,8 +51,11 @@ int scratch_address(oefe_ctx* c, void** out) {
     return OEFE_ERR_ARG;
   }
   std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_addr[c->device]) {
-    // the context's device is current here (every entry point selects it first)
+  ScratchAddr& s = g_scratch_addr[c->device];
+  void* cur = current_context();
+  if (!s.addr || !cur || cur != s.owner) {
+    // the context's device is current here (every entry point selects it first); the lookup is
+    // repeated whenever the current context is not the one the cached address came from
     void* p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess || !p) {
@@ -35,9 +63,10 @@ int scratch_address(oefe_ctx* c, void** out) {
       cudaGetLastError();
       return OEFE_ERR_CUDA;
     }
-    g_scratch_addr[c->device] = p;
+    s.addr = p;
+    s.owner = cur;
   }
-  *out = g_scratch_addr[c->device];
+  *out = s.addr;
   return OEFE_OK;
 }
 

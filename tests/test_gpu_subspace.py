@@ -46,14 +46,18 @@ def test_orthonormalize(k, products):
     assert rel(Q, Qo) < 1e-10 * f
 
 
-@pytest.mark.parametrize("case", ["c1_real_64", "complex_24"])
+@pytest.mark.parametrize("case", ["c1_real_64", "complex_24", "complex_64"])
 def test_orthonormalize_tensor_core_gram(case):  # Gram and rotations on the tensor cores
     # pair mode takes the Gram matrices on the tensor cores (exact bf16 digits, about 2^-46 of the
     # row and column maxima per term): Q^+ M Q = I and Q against the native FP64 path within the
-    # pair tolerances (32x the FP64 ones); 64 vectors fill the 128-row MMA tile
+    # pair tolerances (32x the FP64 ones); 64 real vectors fill the 128-row MMA tile, and so do 64
+    # complex ones (128 real rows: the benchmark's shape)
     from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS
     if case == "c1_real_64":
         prs, ctx, V, _ = c1_pair()
+        nv = 64
+    elif case == "complex_64":
+        prs, ctx, V, _ = paired(ks=[(0.25, -0.4, 0.1)], n=4, a=8.0)
         nv = 64
     else:
         prs, ctx, V, _ = paired(ks=[(0.25, -0.4, 0.1)])
@@ -99,6 +103,32 @@ def test_rayleigh_ritz(k, products):
     X = Qd.cpu().numpy()
     ph = np.sum(np.conj(X_o) * pr.apply_M(X), axis=0)
     assert np.allclose(np.abs(ph), 1.0, atol=1e-9 * f)
+
+
+@pytest.mark.parametrize("k", KS)
+def test_rayleigh_ritz_tensor_core_64(k):
+    # the benchmark's shape in pair mode: 64 vectors (64 complex = 128 real rows, a full MMA tile),
+    # Gram matrices and rotations on the tensor cores, H X by FP32-pair products on the single-leaf
+    # cells of a 4^3 mesh, the projected problem by pair then FP64 Jacobi sweeps
+    from paper_2010_09701_gb300 import F64_PAIRS, STORE_F64, STORE_F64PAIR
+    prs, ctx, V, _ = paired(ks=[k], n=4, a=8.0, store=STORE_F64 | STORE_F64PAIR)
+    ctx.set_f64_products(F64_PAIRS)
+    f = 32.0
+    pr = prs[0]
+    nv = 64
+    Q = solver.cholqr(W.random_vectors(pr.n, nv, complex_=pr.complex, seed=6), pr.apply_M)
+    eps_o, X_o = solver.rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
+    Qd = to_gpu(Q)
+    eps, res = ctx.rayleigh_ritz(0, Qd, resid=True)
+    assert np.max(np.abs(eps - eps_o)) < 1e-10 * f * max(1, np.max(np.abs(eps_o)))
+    res_o = solver.residual_norms(pr, X_o, eps_o)
+    assert np.allclose(res, res_o, rtol=1e-8 * f, atol=1e-12 * f * max(1, np.max(np.abs(eps_o))))
+    # the rotated vectors span the same Ritz directions: |<x_o, M x>| = 1 per well-separated column
+    X = Qd.cpu().numpy()
+    gaps = np.minimum(np.abs(np.diff(eps_o, prepend=-np.inf)), np.abs(np.diff(eps_o, append=np.inf)))
+    sep = gaps > 1e-6 * max(1, np.max(np.abs(eps_o)))
+    ph = np.sum(np.conj(X_o) * pr.apply_M(X), axis=0)
+    assert np.allclose(np.abs(ph[sep]), 1.0, atol=1e-9 * f)
 
 
 @pytest.mark.parametrize("k", KS)
