@@ -4,10 +4,14 @@
 Workload: the 8-atom zincblende cell a = 8.5 bohr (Z = 14 / 6), graded 16^3
 mesh, p = 6, hydrogenic 1s-2p enrichment (40 functions), Monkhorst-Pack 2x2x1
 (4 k-points, complex), 64 vectors per k, Chebyshev degree 30, frozen
-synthetic V_eff. One step is one pass of the whole hot path:
-build_hamiltonian (FP64 arithmetic, FP64 + FP32 storage), then per k the
-mixed filter (29 FP32 degrees + the last in FP64), FP64 Cholesky-QR and
-Rayleigh-Ritz, then occupations, the density and the band-trace adjoint.
+synthetic V_eff. One step is one pass of the whole hot path in the steady
+state of the subspace iteration: build_hamiltonian, then the batched filter of
+every k-point in defect form from the Ritz pairs of the previous pass
+(p_m(A) Q = Q p_m(Theta) + D_m: R = A Q - Q Theta by one FP64-class product,
+the 30 degrees of D_m on the tensor cores, the sum in FP64), FP64-class
+Cholesky-QR and Rayleigh-Ritz per k, then occupations, the density and the
+band-trace adjoint. The Ritz pairs a step starts from come from a few untimed
+passes from random vectors.
 
 value = dense-count filter flops of a step / step time (TFLOP/s), with the
 flop count sum_k sum_e 2 n_aug,e^2 N_v * 4 (complex) per degree.
@@ -246,9 +250,44 @@ def run_ours(args, rank, world):
         return ev
 
     batched = args.tensor and not args.per_k_filter
+    defect = batched and not args.plain_filter
     tune_ms = None
     if batched:
         tune_ms = [float(x) for x in ctx.filter_autotune(X0)]
+
+    def subspace_pass(Xs, bnd, theta, resid=False):
+        """One pass of the subspace iteration over all k (outside the timed region): the batched
+        filter (defect form from the previous Ritz pairs when theta is given), Cholesky-QR,
+        Rayleigh-Ritz. Returns Ritz values, residuals and the next pass's bounds."""
+        lo = [bd[0] for bd in bnd]
+        low = [bd[1] for bd in bnd]
+        if theta is None:
+            ctx.filter_batched(Xs, deg, lo, bks, low, P.FILTER_BF16X3 | P.FILTER_LAST_FP64)
+        else:
+            ctx.filter_batched_defect(Xs, deg, lo, bks, low, theta, P.FILTER_BF16X3)
+        out = []
+        for ik in range(nk):
+            ctx.orthonormalize(ik, Xs[ik])
+            out.append(ctx.rayleigh_ritz(ik, Xs[ik], resid=True))
+        ev = [o[0] for o in out]
+        res = [o[1] for o in out]
+        # Zhou's bounds for the next pass: a = the largest Ritz value, a0 below the smallest
+        return ev, res, [(float(e[-1]), float(e[0]) - 1.0) for e in ev]
+
+    # the state a step starts from: Ritz pairs after a few passes from the random start vectors (the
+    # steady state of the subspace iteration inside an SCF loop), untimed
+    theta0 = None
+    bnd0 = [(a_lo, a0)] * nk
+    if defect:
+        Xs = [x.clone() for x in X0]
+        theta0 = None
+        for _ in range(args.init_passes):
+            theta0, _res, bnd0 = subspace_pass(Xs, bnd0, theta0)
+        for ik in range(nk):
+            X0[ik].copy_(Xs[ik])
+        del Xs
+    lo_k = [bd[0] for bd in bnd0]
+    low_k = [bd[1] for bd in bnd0]
 
     def step(record=False):
         t = [mark()]
@@ -261,7 +300,10 @@ def run_ours(args, rank, world):
             for ik in range(nk):
                 X[ik].copy_(X0[ik])
             e0 = mark()
-            ctx.filter_batched(X, deg, a_lo, bks, a0, fflags)
+            if defect:   # from the Ritz pairs (X0, theta0): p_m(A) X0 = X0 p_m(theta0) + D_m
+                ctx.filter_batched_defect(X, deg, lo_k, bks, low_k, theta0, P.FILTER_BF16X3)
+            else:
+                ctx.filter_batched(X, deg, a_lo, bks, a0, fflags)
             e1 = mark()
             if record:
                 filt_events.append((e0, e1))
@@ -398,42 +440,56 @@ def run_ours(args, rank, world):
                 "tflops": dense_filter_flops(naug, [nvs[0]], deg) / fp64_s / 1e12,
                 "speedup_mixed_vs_fp64": fp64_s / s_per_pass}
 
-        # accuracy at convergence (k = 0): the subspace iteration (Zhou's bounds from the previous
-        # Ritz values, FP64 Cholesky-QR and Rayleigh-Ritz) is run with the mixed filter until the
-        # band energy settles; then one pass with the mixed filter and one with the FP64 filter from
-        # that subspace are compared (band energy per atom, occupied Ritz values, residuals)
-        def one_pass(Xp, lo, low, flags):
-            # the FP64 reference path runs native FP64 products throughout
-            ctx.set_f64_products(P.F64_PAIRS if (pairs and flags) else P.F64_NATIVE)
-            ctx.chebyshev_filter(0, Xp, deg, lo, bks[0], low, flags=flags)
-            ctx.orthonormalize(0, Xp)
-            return ctx.rayleigh_ritz(0, Xp, resid=True)
-
-        mixed_flags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
-        Xc = X0[0].clone()
-        lo, low = a_lo, a0
-        e_prev, last_change = None, None
-        for it in range(args.acc_passes):
-            ev, res = one_pass(Xc, lo, low, mixed_flags)
-            lo, low = float(ev[-1]), float(ev[0]) - 1.0
-            e_now = P.occupations([ev], [1.0], w.nelectrons)[2]
-            if e_prev is not None:
-                last_change = abs(e_now - e_prev) / w.natoms
-            e_prev = e_now
-        ev_m, res_m = one_pass(Xc.clone(), lo, low, mixed_flags)
-        ev_d, res_d = one_pass(Xc.clone(), lo, low, 0)
-        ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
-        _, occ_m, e_m = P.occupations([ev_m], [1.0], w.nelectrons)
-        _, occ_d, e_d = P.occupations([ev_d], [1.0], w.nelectrons)
-        occd = np.asarray(occ_d[0]) > 1e-8
-        accuracy = {"converging_passes": args.acc_passes, "band_energy_change_last_pass_per_atom_Ha": last_change, "k_point": 0,
-                    "compared": "one mixed and one FP64 pass from the converged subspace",
-                    "reference": "the FP64 GPU path",
-                    "d_band_energy_per_atom_Ha": float(abs(e_m - e_d) / w.natoms),
-                    "max_abs_d_eig_occupied_Ha": float(np.max(np.abs(ev_m[occd] - ev_d[occd]))),
-                    "max_residual_occupied_mixed": float(np.max(np.asarray(res_m)[occd])),
-                    "max_residual_occupied_fp64": float(np.max(np.asarray(res_d)[occd])),
-                    "occupied_states": int(np.sum(occd))}
+        # accuracy at convergence: the subspace iteration of the step (defect-form mixed filter from the
+        # previous Ritz pairs, FP64-class Cholesky-QR and Rayleigh-Ritz, every k) runs from the step's
+        # starting state until the largest residual of the occupied states is below the 1e-7 target or
+        # stops falling; then one pass with the native FP64 filter (FP64 products, Cholesky-QR and
+        # Rayleigh-Ritz) from that subspace is compared with it
+        if defect:
+            Xc = [x.clone() for x in X0]
+            theta, bnd = theta0, bnd0
+            hist = []
+            occ_idx = None
+            t_acc = time.time()
+            for it in range(args.acc_passes):
+                theta, res, bnd = subspace_pass(Xc, bnd, theta)
+                _, occ_m, e_m = P.occupations(theta, [1.0 / nk] * nk, w.nelectrons)
+                occ_idx = [np.asarray(o) > 1e-8 for o in occ_m]
+                hist.append(float(max(np.max(np.asarray(r)[o]) for r, o in zip(res, occ_idx))))
+                if hist[-1] < args.acc_target * 0.1:
+                    break
+                if len(hist) > 25 and hist[-1] > 0.5 * min(hist[:-20]):
+                    break   # no longer falling
+            acc_s = time.time() - t_acc
+            ev_m = theta
+            # one FP64 pass from the converged subspace: native FP64 filter, Cholesky-QR, Rayleigh-Ritz
+            ctx.set_f64_products(P.F64_NATIVE)
+            ev_d, res_d = [], []
+            for ik in range(nk):
+                Xd_ = Xc[ik].clone()
+                ctx.chebyshev_filter(ik, Xd_, deg, bnd[ik][0], bks[ik], bnd[ik][1])
+                ctx.orthonormalize(ik, Xd_)
+                e_, r_ = ctx.rayleigh_ritz(ik, Xd_, resid=True)
+                ev_d.append(e_)
+                res_d.append(r_)
+                del Xd_
+            ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
+            _, occ_d, e_d = P.occupations(ev_d, [1.0 / nk] * nk, w.nelectrons)
+            occ_idx_d = [np.asarray(o) > 1e-8 for o in occ_d]
+            accuracy = {"passes": len(hist), "seconds": acc_s, "k_points": nk,
+                        "residual_target": args.acc_target,
+                        "max_residual_occupied_history": hist[:5] + (["..."] if len(hist) > 10 else []) + hist[-5:],
+                        "max_residual_occupied_mixed": hist[-1],
+                        "max_residual_occupied_fp64": float(max(np.max(np.asarray(r)[o]) for r, o in zip(res_d, occ_idx_d))),
+                        "target_met_mixed": bool(hist[-1] < args.acc_target),
+                        "compared": "the converged mixed subspace iteration against one native FP64 pass from it",
+                        "reference": "the FP64 GPU path",
+                        "residual": "||H u - eps M u||_{M^-1} / ||u||_M of the occupied Ritz pairs",
+                        "d_band_energy_per_atom_Ha": float(abs(e_m - e_d) / w.natoms),
+                        "max_abs_d_eig_occupied_Ha": float(max(np.max(np.abs(np.asarray(a)[o] - np.asarray(b)[o]))
+                                                               for a, b, o in zip(ev_m, ev_d, occ_idx))),
+                        "occupied_states": int(sum(int(np.sum(o)) for o in occ_idx))}
+            del Xc
 
     # the dominant kernel of the step (most device time per step) carries "roofline", the other
     # cell product "roofline_secondary"
@@ -514,8 +570,13 @@ def run_ours(args, rank, world):
            "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
            "dtype": "c64+c128", "data": "synthetic",
            "config": {"workload": workload_text(w),
-                      "arithmetic": "mixed filter (%d FP32-class degrees + last FP64-class), FP64-class Cholesky-QR / "
-                                    "Rayleigh-Ritz / density" % (w.degree - 1),
+                      "arithmetic": (("mixed filter in defect form from the previous Ritz pairs (R = AQ - Q theta "
+                                     "FP64-class, %d degrees of the defect on the tensor cores, Q p_m(theta) + D_m in "
+                                     "FP64), FP64-class Cholesky-QR / Rayleigh-Ritz / density" % w.degree) if defect else
+                                     "mixed filter (%d FP32-class degrees + last FP64-class), FP64-class Cholesky-QR / "
+                                     "Rayleigh-Ritz / density" % (w.degree - 1)),
+                      "start": ("Ritz pairs after %d untimed passes from random vectors" % args.init_passes
+                                if defect else "random vectors"),
                       "f64_products": ("FP32 pairs on single-leaf cells (last degree and Rayleigh-Ritz H X)" if pairs
                                        else "FP64"),
                       "n_dof_per_k": int(n), "cells": int(len(naug)), "mean_n_aug": float(np.mean(naug)),
@@ -524,8 +585,9 @@ def run_ours(args, rank, world):
            "filter_s_per_pass": s_per_pass, "filter_tflops": filt_tflops, "fp64": fp64, "phase_ms": phase_ms,
            "filter_launch": "batched multi-k, CUDA graph" if batched else "per k-point",
            "autotune_ms_per_degree": tune_ms,
-           "filter_precision": ("BF16x%d tensor cores (FP32 vectors) + last degree FP64" % nprod) if args.tensor
-                               else "FP32 + last degree FP64",
+           "filter_precision": (("BF16x%d tensor cores (FP32 defect vectors), FP64-class residual and sum" % nprod)
+                                if defect else ("BF16x%d tensor cores (FP32 vectors) + last degree FP64" % nprod)
+                                if args.tensor else "FP32 + last degree FP64"),
            "roofline": roofline, "roofline_secondary": roof2, "accuracy": accuracy,
            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
            "gpu_launches": int(launches),
@@ -609,9 +671,15 @@ def main():
     ap.add_argument("--per-k-filter", action="store_true", help="filter each k-point separately")
     ap.add_argument("--with-fp64", action="store_true",
                     help="with --filter-only: store the FP64 matrices too and apply H once in FP64")
-    ap.add_argument("--acc-passes", type=int, default=40,
-                    help="mixed subspace-iteration passes (k = 0) that converge the subspace the accuracy "
-                         "comparison starts from")
+    ap.add_argument("--acc-passes", type=int, default=150,
+                    help="largest number of mixed subspace-iteration passes (all k) of the accuracy run")
+    ap.add_argument("--acc-target", type=float, default=1e-7,
+                    help="residual of the occupied states the accuracy run converges to")
+    ap.add_argument("--init-passes", type=int, default=4,
+                    help="untimed passes from the random start vectors to the Ritz pairs a step starts from")
+    ap.add_argument("--plain-filter", action="store_true",
+                    help="the plain mixed filter from the random start vectors (last degree FP64) instead of "
+                         "the defect form from Ritz pairs")
     ap.add_argument("--f64-products", default="pairs", choices=["pairs", "native"],
                     help="arithmetic of the FP64-class cell products of the mixed step")
     ap.add_argument("--product-shape", type=int, default=-1, choices=[-1, 0, 1, 2],

@@ -206,6 +206,33 @@ int oefe_chebyshev_filter(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int d
 int oefe_filter_batched(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype,
                         int degree, const double* a, const double* b, const double* a0, int flags);
 
+/* oefe_filter_batched_defect -- the batched filter in defect form, for a block
+ * that already approximates eigenvectors: on entry X[k] holds Q (F64/C128)
+ * with approximate eigenvalues theta (the Ritz pairs of the previous pass of
+ * the subspace iteration, Sec. IV, Eq. ProjKS); on return X[k] = p_m(A) Q,
+ * computed as p_m(A) Q = Q p_m(Theta) + D_m with Theta = diag(theta),
+ *   R = A Q - Q Theta                      (one FP64-class operator application),
+ *   D_0 = 0, D_1 = alpha_1 R,
+ *   D_j = alpha_j [(A - c) D_{j-1} + R p_{j-1}(Theta)] + beta_j D_{j-2},
+ * where c, alpha_j, beta_j and the scaled polynomials p_j are those of
+ * oefe_chebyshev_filter (a three-term recurrence, so the identity is exact).
+ * Every degree of D runs on the tensor cores like oefe_filter_batched (one
+ * persistent launch per degree over all k, captured once in a CUDA graph; the
+ * first degree needs no product), and Q p_m(Theta) + D_m is formed in FP64.
+ * The low-precision rounding then scales with |D| -- about the size of the
+ * residuals of Q -- instead of with |p_m(A) Q|, so directions that have
+ * converged stay converged to FP64-class accuracy (the plain mixed filter
+ * leaves them at about eps_FP32 times the spectral width). Any theta gives the
+ * same p_m(A) Q in exact arithmetic; the Ritz values make R smallest.
+ *   theta  host, sum_k nv[k] doubles (k-major), finite.
+ * flags must contain OEFE_FILTER_BF16X3 (OEFE_FILTER_LAST_FP64 is ignored);
+ * X, nv, ld, a, b, a0 as for oefe_filter_batched, the operator built with
+ * OEFE_STORE_F64 (and OEFE_STORE_F64PAIR in pair mode) besides the split.
+ * The paper filters in double precision throughout; this form is ours. */
+int oefe_filter_batched_defect(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype,
+                               int degree, const double* a, const double* b, const double* a0, const double* theta,
+                               int flags);
+
 /* oefe_filter_autotune -- times the tensor-core cell-product launch shapes
  * on the given vectors and keeps the fastest for the BF16X3 filters:
  * (0) 64 vectors per tile, persistent grid of one CTA per SM, cp.async loads;

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("oefe_apply_a_noalloc", _I, [_P, _I, _P, _P, _I, _I, _I]),
     ("oefe_chebyshev_filter", _I, [_P, _I, _P, _I, _I, _I, _I, _D, _D, _D, _I]),
     ("oefe_filter_batched", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _I, _DP, _DP, _DP, _I]),
+    ("oefe_filter_batched_defect", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _I, _DP, _DP, _DP, _DP, _I]),
     ("oefe_filter_autotune", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP]),
     ("oefe_orthonormalize", _I, [_P, _I, _P, _I, _I, _I, _DP]),
     ("oefe_rayleigh_ritz", _I, [_P, _I, _P, _I, _I, _I, _DP, _DP]),
@@ -309,6 +310,19 @@ class Context:
         a0 = np.ascontiguousarray(np.broadcast_to(np.asarray(a0, np.float64), (len(Xs),)))
         self._check(self.lib.oefe_filter_batched(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, int(degree), _dp(a),
                                                  _dp(b), _dp(a0), int(flags)))
+        return Xs
+
+    def filter_batched_defect(self, Xs, degree, a, b, a0, theta, flags):
+        """X[k] <- p_m(A) X[k] for Ritz-like blocks X[k] with values theta[k] (oefe_filter_batched_defect)."""
+        arr, nvs, lds, dt = self._blocks(Xs)
+        a = np.ascontiguousarray(np.broadcast_to(np.asarray(a, np.float64), (len(Xs),)))
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(b, np.float64), (len(Xs),)))
+        a0 = np.ascontiguousarray(np.broadcast_to(np.asarray(a0, np.float64), (len(Xs),)))
+        th = np.ascontiguousarray(np.concatenate([np.asarray(t, np.float64).ravel() for t in theta]))
+        if len(theta) != len(Xs) or th.size != int(np.sum(nvs)):
+            raise ValueError("one theta per vector of every block")
+        self._check(self.lib.oefe_filter_batched_defect(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, int(degree),
+                                                        _dp(a), _dp(b), _dp(a0), _dp(th), int(flags)))
         return Xs
 
     def filter_autotune(self, Xs):

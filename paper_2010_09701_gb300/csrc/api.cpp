@@ -251,6 +251,13 @@ int oefe_filter_batched(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, c
   return cheb_filter_batched(ctx, nk, X, nv, ld, dtype, degree, a, b, a0, flags);
 }
 
+int oefe_filter_batched_defect(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype,
+                               int degree, const double* a, const double* b, const double* a0, const double* theta,
+                               int flags) {
+  CTX_CHECK(ctx);
+  return cheb_filter_batched_defect(ctx, nk, X, nv, ld, dtype, degree, a, b, a0, theta, flags);
+}
+
 int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms) {
   CTX_CHECK(ctx);
   return filter_autotune(ctx, nk, X, nv, ld, dtype, ms);

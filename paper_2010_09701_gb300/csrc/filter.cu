@@ -291,14 +291,18 @@ __global__ void k_enr_update(const cd* __restrict__ Yo, const void* __restrict__
 // Batched variants: blockIdx.y selects the k-point; per-k pointers and
 // recurrence coefficients come from a parameter table.
 struct NodeK {
-  const void* Z;
-  const void* Xk;
+  const void* Z;       // per-cell products; null: no product this degree (the iterate is zero)
+  const void* Xk;      // current iterate; null: zero
   const void* Xm1;
   void* Y;
   cd* Yo;
   const void* Minv;
   int ldk, ldm1, ldy, nv, mode;
   double alpha, cshift, beta;
+  // defect recurrence: Y += alpha coef[v] R[:, v] (R null: no addend)
+  const void* R;
+  const float* coef;
+  int ldr;
 };
 
 // Node rows of every k-point in one launch (blockIdx.y = k): one warp per node row with all of its
@@ -317,19 +321,24 @@ __global__ void __launch_bounds__(256) k_node_update_multi(const NodeK* __restri
   const int64_t warp0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int W = p.nv * R;
-  const int ldk = p.ldk * R, ldm1 = p.ldm1 * R, ldy = p.ldy * R;
+  const int ldk = p.ldk * R, ldm1 = p.ldm1 * R, ldy = p.ldy * R, ldr = p.ldr * R;
   const T* Z = (const T*)p.Z;
   const T* Xk = (const T*)p.Xk;
   const T* Xm1 = (const T*)p.Xm1;
+  const T* Rr = (const T*)p.R;
+  const float* coef = p.coef;
   T* Y = (T*)p.Y;
   const T alpha = (T)p.alpha, cs = (T)p.cshift, beta = (T)p.beta;
-  const bool has_m1 = p.beta != 0.0;
-  const bool vec = sizeof(T) == 4 && W % 4 == 0 && ldk % 4 == 0 && ldy % 4 == 0 && (!has_m1 || ldm1 % 4 == 0) &&
-                   ((uintptr_t)Z & 15) == 0 && ((uintptr_t)Xk & 15) == 0 && ((uintptr_t)Y & 15) == 0 &&
-                   (!has_m1 || ((uintptr_t)Xm1 & 15) == 0);
+  const bool has_z = Z != nullptr, has_k = Xk != nullptr, has_r = Rr != nullptr;
+  const bool has_m1 = p.beta != 0.0 && Xm1 != nullptr;
+  const bool vec = sizeof(T) == 4 && W % 4 == 0 && ldy % 4 == 0 && ((uintptr_t)Y & 15) == 0 &&
+                   (!has_z || ((uintptr_t)Z & 15) == 0) &&
+                   (!has_k || (ldk % 4 == 0 && ((uintptr_t)Xk & 15) == 0)) &&
+                   (!has_m1 || (ldm1 % 4 == 0 && ((uintptr_t)Xm1 & 15) == 0)) &&
+                   (!has_r || (ldr % 4 == 0 && ((uintptr_t)Rr & 15) == 0));
   for (int64_t g = warp0; g < nh; g += nwarps) {
     const int64_t s0 = node_off[g];
-    const int ns = (int)(node_off[g + 1] - s0);
+    const int ns = has_z ? (int)(node_off[g + 1] - s0) : 0;
     const T minv = (T)(1.0 / m[g]);
     if (vec) {
       for (int f = 4 * lane; f < W; f += 128) {
@@ -352,7 +361,8 @@ __global__ void __launch_bounds__(256) k_node_update_multi(const NodeK* __restri
             acc.w += z[u].w;
           }
         }
-        const float4 xk = *reinterpret_cast<const float4*>((const float*)Xk + g * ldk + f);
+        const float4 xk = has_k ? *reinterpret_cast<const float4*>((const float*)Xk + g * ldk + f)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
         float4 o;
         o.x = (float)alpha * (acc.x * (float)minv - (float)cs * xk.x);
         o.y = (float)alpha * (acc.y * (float)minv - (float)cs * xk.y);
@@ -365,14 +375,22 @@ __global__ void __launch_bounds__(256) k_node_update_multi(const NodeK* __restri
           o.z += (float)beta * xm.z;
           o.w += (float)beta * xm.w;
         }
+        if (has_r) {   // component f + i belongs to vector (f + i) / R
+          const float4 r = *reinterpret_cast<const float4*>((const float*)Rr + g * ldr + f);
+          o.x += (float)alpha * coef[(f + 0) / R] * r.x;
+          o.y += (float)alpha * coef[(f + 1) / R] * r.y;
+          o.z += (float)alpha * coef[(f + 2) / R] * r.z;
+          o.w += (float)alpha * coef[(f + 3) / R] * r.w;
+        }
         *reinterpret_cast<float4*>((float*)Y + g * ldy + f) = o;
       }
     } else {
       for (int f = lane; f < W; f += 32) {
         T acc = T(0);
         for (int s = 0; s < ns; ++s) acc += Z[node_slot[s0 + s] * W + f];
-        T o = alpha * (acc * minv - cs * Xk[g * ldk + f]);
+        T o = alpha * (acc * minv - cs * (has_k ? Xk[g * ldk + f] : T(0)));
         if (has_m1) o += beta * Xm1[g * ldm1 + f];
+        if (has_r) o += alpha * (T)coef[f / R] * Rr[g * ldr + f];
         Y[g * ldy + f] = o;
       }
     }
@@ -397,20 +415,30 @@ __global__ void k_enr_update_multi(const NodeK* __restrict__ P, int nO, int64_t 
   if (t >= nO * p.nv) return;
   const int nu = t / p.nv, v = t % p.nv;
   cd s = mkc(0, 0);
-  for (int mu = 0; mu < nO; ++mu) {
-    const cd yo = p.Yo[mu * p.nv + v];
-    if constexpr (C) s += reinterpret_cast<const cd*>(p.Minv)[nu * nO + mu] * yo;
-    else s += reinterpret_cast<const double*>(p.Minv)[nu * nO + mu] * yo;
+  if (p.Z) {   // no products at the first degree of the defect recurrence
+    for (int mu = 0; mu < nO; ++mu) {
+      const cd yo = p.Yo[mu * p.nv + v];
+      if constexpr (C) s += reinterpret_cast<const cd*>(p.Minv)[nu * nO + mu] * yo;
+      else s += reinterpret_cast<const double*>(p.Minv)[nu * nO + mu] * yo;
+    }
   }
   const int64_t row = nh + nu;
-  const S xk = ((const S*)p.Xk)[row * p.ldk + v];
-  double xr, xi = 0;
-  if constexpr (C) { xr = (double)xk.x; xi = (double)xk.y; } else xr = (double)xk;
+  double xr = 0, xi = 0;
+  if (p.Xk) {
+    const S xk = ((const S*)p.Xk)[row * p.ldk + v];
+    if constexpr (C) { xr = (double)xk.x; xi = (double)xk.y; } else xr = (double)xk;
+  }
   cd out = mkc(p.alpha * (s.x - p.cshift * xr), p.alpha * (s.y - p.cshift * xi));
-  if (p.beta != 0.0) {
+  if (p.beta != 0.0 && p.Xm1) {
     const S xm = ((const S*)p.Xm1)[row * p.ldm1 + v];
     if constexpr (C) out += mkc(p.beta * (double)xm.x, p.beta * (double)xm.y);
     else out.x += p.beta * (double)xm;
+  }
+  if (p.R) {
+    const S r = ((const S*)p.R)[row * p.ldr + v];
+    const double ac = p.alpha * (double)p.coef[v];
+    if constexpr (C) out += mkc(ac * (double)r.x, ac * (double)r.y);
+    else out.x += ac * (double)r;
   }
   if constexpr (C) ((S*)p.Y)[row * p.ldy + v] = S{(T)out.x, (T)out.y};
   else ((S*)p.Y)[row * p.ldy + v] = (T)out.x;
@@ -434,6 +462,31 @@ int convert(oefe_ctx* c, const void* X, int ldx, void* Y, int ldy, int64_t n, in
   OEFE_COUNTED k_convert<A, B><<<blocks, 256, 0, c->stream>>>((const A*)X, ldx, (B*)Y, ldy, n, width);
   OEFE_CUDA_TRY(c, cudaGetLastError());
   return OEFE_OK;
+}
+
+// Defect form of the filter (p_m(A) Q = Q p_m(Theta) + D_m, see cheb_filter_batched):
+// R = A Q - Q diag(theta) in low precision, from the FP64-class product AQ and the FP64 Q; real
+// views, W reals per row, component f of a row belongs to vector f / Rs.
+__global__ void k_defect_residual(const double* __restrict__ AQ, int ldaq, const double* __restrict__ Q, int ldq,
+                                  const double* __restrict__ theta, int64_t n, int W, int Rs, float* __restrict__ Rl,
+                                  int ldr) {
+  const int64_t total = n * W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / W;
+    const int f = (int)(t % W);
+    Rl[r * ldr + f] = (float)fma(-theta[f / Rs], Q[r * ldq + f], AQ[r * ldaq + f]);
+  }
+}
+
+// X <- X p_m(theta) + D: the exactly scaled FP64 part plus the low-precision defect
+__global__ void k_defect_finish(double* __restrict__ X, int ldx, const float* __restrict__ D, int ldd,
+                                const double* __restrict__ pm, int64_t n, int W, int Rs) {
+  const int64_t total = n * W;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / W;
+    const int f = (int)(t % W);
+    X[r * ldx + f] = fma(X[r * ldx + f], pm[f / Rs], (double)D[r * ldd + f]);
+  }
 }
 
 struct Step {
@@ -685,6 +738,7 @@ struct BatchPlan {
   int nk, jlow, nb, grid;
   int parts;   // bf16 parts of the split cell matrices
   bool tma;    // warp-specialized TMA kernel (required for three parts)
+  bool defect; // defect recurrence: the first degree has no cell product (its iterate is zero)
   long long ntiles;
   std::vector<MmaK> mk;      // jlow * nk
   std::vector<NodeK> nd;     // jlow * nk
@@ -699,8 +753,11 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
   for (int k = 0; k < P.nk; ++k) vmax = std::max(vmax, P.nd[k].nv);
   const int eb = (c->nO * vmax + 127) / 128;
   for (int j = 0; j < P.jlow; ++j) {
+    const bool product = !(P.defect && j == 0);
     if (timed) cudaEventRecordWithFlags(c->bev_kernel[2 * j], c->bstream, cudaEventRecordExternal);
-    if (P.tma) {
+    if (!product) {
+      // D_1 = alpha_1 R: nothing to multiply
+    } else if (P.tma) {
       OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk + (size_t)j * P.nk, nullptr, P.nk, P.ntiles, cplx, P.parts,
                                    (int)std::min<long long>(P.ntiles, c->num_sms), c->bstream));
     } else if (P.grid > 0) {
@@ -717,16 +774,18 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
       OEFE_COUNTED k_node_update_multi<float, true><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off, c->d_node_slot,
                                                                    c->d_m, c->nh);
       if (c->nO > 0) {
-        OEFE_COUNTED k_enr_reduce_multi<float, true><<<gr, ER_T, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
-                                                                     c->d_enr_slot);
+        if (product)
+          OEFE_COUNTED k_enr_reduce_multi<float, true><<<gr, ER_T, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
+                                                                       c->d_enr_slot);
         OEFE_COUNTED k_enr_update_multi<float, true><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
       }
     } else {
       OEFE_COUNTED k_node_update_multi<float, false><<<g1, 256, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_node_off,
                                                                     c->d_node_slot, c->d_m, c->nh);
       if (c->nO > 0) {
-        OEFE_COUNTED k_enr_reduce_multi<float, false><<<gr, ER_T, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
-                                                                      c->d_enr_slot);
+        if (product)
+          OEFE_COUNTED k_enr_reduce_multi<float, false><<<gr, ER_T, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->d_enr_off,
+                                                                        c->d_enr_slot);
         OEFE_COUNTED k_enr_update_multi<float, false><<<g2, 128, 0, c->bstream>>>(d_nd + (size_t)j * P.nk, c->nO, c->nh);
       }
     }
@@ -737,29 +796,47 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
 
 }  // namespace
 
-int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
-                        const double* a, const double* b, const double* a0, int flags) {
+namespace {
+
+// theta == nullptr: the plain filter. theta != nullptr: the defect form. With Q = X (FP64, on entry)
+// and Theta = diag(theta), p_m(A) Q = Q p_m(Theta) + D_m, where D_0 = 0, D_1 = alpha_1 R and
+//   D_j = alpha_j [(A - c) D_{j-1} + R p_{j-1}(Theta)] + beta_j D_{j-2},   R = A Q - Q Theta,
+// (alpha_j, beta_j the coefficients of the scaled recurrence, p_j the scaled polynomials). R comes
+// from one FP64-class product; every degree of D runs on the tensor cores; the result is formed in
+// FP64. The low-precision rounding then scales with |D| (about the size of the residuals of Q)
+// instead of with |p_m(A) Q|, so converged directions stay converged to FP64-class accuracy.
+int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
+                        const double* a, const double* b, const double* a0, const double* theta, int flags) {
   if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
+  const bool defect = theta != nullptr;
   if (nk < 1 || nk != (int)c->kd.size() || !X || !nv || !ld || !a || !b || !a0) {
     c->err = "filter_batched: one X, nv, ld, a, b, a0 per k-point of the context";
     return OEFE_ERR_ARG;
   }
   if (!(flags & OEFE_FILTER_BF16X3)) { c->err = "filter_batched runs on the tensor cores: pass OEFE_FILTER_BF16X3"; return OEFE_ERR_ARG; }
-  const bool mixed = (flags & OEFE_FILTER_LAST_FP64) != 0;
+  // the defect form takes FP64 vectors and runs every degree on the tensor cores
+  const bool mixed = !defect && (flags & OEFE_FILTER_LAST_FP64) != 0;
   const bool cplx = c->kd[0].cplx;
   for (int k = 0; k < nk; ++k) {
-    OEFE_TRY(check_apply_args(c, k, X[k], nv[k], ld[k], dtype, !mixed));
+    OEFE_TRY(check_apply_args(c, k, X[k], nv[k], ld[k], dtype, !mixed && !defect));
     if (c->kd[k].cplx != cplx) { c->err = "filter_batched: all k-points must be real or all complex"; return OEFE_ERR_ARG; }
     if (!c->kd[k].Hbf) { c->err = "filter_batched: BF16x3 cell matrices were not stored"; return OEFE_ERR_STATE; }
     if (degree < 1 || !(b[k] > a[k]) || !(a0[k] < a[k])) { c->err = "filter_batched: need degree >= 1, a0 < a < b"; return OEFE_ERR_ARG; }
   }
+  if (defect) {
+    if (!dtype_fp64(dtype)) { c->err = "filter_batched_defect: needs F64/C128 vectors"; return OEFE_ERR_ARG; }
+    size_t tot = 0;
+    for (int k = 0; k < nk; ++k) tot += nv[k];
+    for (size_t i = 0; i < tot; ++i)
+      if (!std::isfinite(theta[i])) { c->err = "filter_batched_defect: theta must be finite"; return OEFE_ERR_ARG; }
+  }
   if (mixed && !dtype_fp64(dtype)) { c->err = "filter_batched: LAST_FP64 needs F64/C128 storage"; return OEFE_ERR_ARG; }
-  if (!mixed && dtype_fp64(dtype)) { c->err = "filter_batched: low-precision vectors (F32/C64) without LAST_FP64"; return OEFE_ERR_ARG; }
+  if (!mixed && !defect && dtype_fp64(dtype)) { c->err = "filter_batched: low-precision vectors (F32/C64) without LAST_FP64"; return OEFE_ERR_ARG; }
   const int dt_low = cplx ? OEFE_C64 : OEFE_F32;
   const size_t es_low = dtype_bytes(dt_low), es = dtype_bytes(dtype);
   const int64_t n = c->nh + c->nO;
   const int jlow = mixed ? degree - 1 : degree;
-  if (jlow == 0) {  // a single FP64 degree: no low-precision work to batch
+  if (jlow == 0) {   // (never in the defect form: jlow = degree >= 1)  // a single FP64 degree: no low-precision work to batch
     for (int k = 0; k < nk; ++k)
       OEFE_TRY(cheb_filter(c, k, X[k], nv[k], ld[k], dtype, degree, a[k], b[k], a0[k], 0));
     return OEFE_OK;
@@ -771,21 +848,25 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   const bool tma = (c->use_tma || parts == 3) && c->d_tmaps;
   if (!tma && parts != 2) { c->err = "filter_batched: the split cell matrices have no tensor maps"; return OEFE_ERR_STATE; }
   if (tma) c->tune_nb = 64;
-  // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed)
+  // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed) or R, A Q, coefficients (defect)
   std::vector<size_t> off(nk + 1, 0);
   auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
-  std::vector<size_t> zb(nk), yb(nk), lb(nk), fb(nk);
+  std::vector<size_t> zb(nk), yb(nk), lb(nk), fb(nk), cb(nk);
   for (int k = 0; k < nk; ++k) {
     zb[k] = a256((size_t)c->ncells * c->npad * nv[k] * std::max(es, es_low));
     yb[k] = a256((size_t)std::max(c->nO, 1) * nv[k] * sizeof(cd));
     lb[k] = a256((size_t)n * nv[k] * es_low);
-    fb[k] = mixed ? a256((size_t)n * nv[k] * es) : 0;
-    off[k + 1] = off[k] + zb[k] + yb[k] + 3 * lb[k] + 2 * fb[k];
+    fb[k] = (mixed || defect) ? a256((size_t)n * nv[k] * es) : 0;
+    // defect: p_0 .. p_{m-1} per vector (float), then p_m and theta (double)
+    cb[k] = defect ? a256((size_t)degree * nv[k] * sizeof(float)) + 2 * a256((size_t)nv[k] * sizeof(double)) : 0;
+    off[k + 1] = off[k] + zb[k] + yb[k] + 3 * lb[k] + 2 * fb[k] + cb[k];
   }
   OEFE_TRY(ensure_ws(c, off[nk] + 256));
   char* base = (char*)c->ws;
   std::vector<void*> Zk(nk), L0(nk), L1(nk), L2(nk), F1(nk), F2(nk);
   std::vector<cd*> Yo(nk);
+  std::vector<float*> coef(nk);
+  std::vector<double*> pmv(nk), thv(nk);
   for (int k = 0; k < nk; ++k) {
     char* p = base + off[k];
     Zk[k] = p;
@@ -793,8 +874,12 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     L0[k] = p + zb[k] + yb[k];
     L1[k] = p + zb[k] + yb[k] + lb[k];
     L2[k] = p + zb[k] + yb[k] + 2 * lb[k];
-    F1[k] = p + zb[k] + yb[k] + 3 * lb[k];
-    F2[k] = p + zb[k] + yb[k] + 3 * lb[k] + fb[k];
+    F1[k] = p + zb[k] + yb[k] + 3 * lb[k];   // defect: A Q (FP64)
+    F2[k] = p + zb[k] + yb[k] + 3 * lb[k] + fb[k];   // defect: R (low precision)
+    char* q = p + zb[k] + yb[k] + 3 * lb[k] + 2 * fb[k];
+    coef[k] = (float*)q;
+    pmv[k] = (double*)(q + a256((size_t)degree * nv[k] * sizeof(float)));
+    thv[k] = (double*)(q + a256((size_t)degree * nv[k] * sizeof(float)) + a256((size_t)nv[k] * sizeof(double)));
   }
   // plan: simulate the buffer rotation of the low-precision degrees
   BatchPlan P;
@@ -804,6 +889,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   P.grid = c->tune_grid;
   P.parts = parts;
   P.tma = tma;
+  P.defect = defect;
   P.ntiles = 0;
   std::vector<long long> tile0(nk);
   for (int k = 0; k < nk; ++k) {
@@ -820,8 +906,9 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   const std::vector<double> sig1 = sig;
   for (int j = 1; j <= jlow; ++j) {
     for (int k = 0; k < nk; ++k) {
-      void* bufs[3] = {mixed ? L0[k] : X[k], L1[k], L2[k]};
-      const int lds[3] = {mixed ? nv[k] : ld[k], nv[k], nv[k]};
+      // defect: D_0 = 0 is never read, so all three buffers are private
+      void* bufs[3] = {(mixed || defect) ? L0[k] : X[k], L1[k], L2[k]};
+      const int lds[3] = {(mixed || defect) ? nv[k] : ld[k], nv[k], nv[k]};
       const double e = (b[k] - a[k]) / 2.0, cc = (b[k] + a[k]) / 2.0;
       double alpha, beta;
       if (j == 1) {
@@ -858,6 +945,16 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
       nd.alpha = alpha;
       nd.cshift = cc;
       nd.beta = beta;
+      nd.R = nullptr;
+      nd.coef = nullptr;
+      nd.ldr = 0;
+      if (defect) {
+        if (j == 1) { nd.Z = nullptr; nd.Xk = nullptr; }   // D_0 = 0: no product, no shift term
+        if (j <= 2) nd.Xm1 = nullptr;                      // D_{j-2} = D_0 = 0 (or none)
+        nd.R = F2[k];                                      // R in low precision, rows of nv
+        nd.ldr = nv[k];
+        nd.coef = coef[k] + (size_t)(j - 1) * nv[k];       // p_{j-1}(theta) per vector
+      }
       P.nd.push_back(nd);
       P.lp[k] = ic;
       P.lc[k] = in;
@@ -866,7 +963,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   // graph key: everything baked into the captured launches
   std::vector<double> key = {(double)nk, (double)degree, (double)flags, (double)dtype, (double)(uintptr_t)base,
                              (double)P.nb, (double)P.grid, (double)(c->timing & (1 << dt_low) ? 1 : 0),
-                             (double)tma, (double)parts, (double)c->tune_merge};
+                             (double)tma, (double)parts, (double)c->tune_merge, (double)defect};
   for (int k = 0; k < nk; ++k) {
     key.push_back((double)(uintptr_t)X[k]);
     key.push_back(nv[k]);
@@ -936,6 +1033,43 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     if (ce != cudaSuccess) { c->err = std::string("graph instantiate: ") + cudaGetErrorString(ce); return OEFE_ERR_CUDA; }
     c->bkey = key;
   }
+  if (defect) {
+    // per k: the scaled polynomials at theta (host, FP64), R = A Q - Q Theta from one FP64-class
+    // product, on the caller's stream before the replay
+    size_t t0 = 0;
+    for (int k = 0; k < nk; ++k) {
+      const double e = (b[k] - a[k]) / 2.0, cc = (b[k] + a[k]) / 2.0;
+      const double s1 = e / (a0[k] - cc);
+      std::vector<float> cf((size_t)degree * nv[k]);
+      std::vector<double> pm(nv[k]), th(theta + t0, theta + t0 + nv[k]);
+      for (int v = 0; v < nv[k]; ++v) {
+        double pprev = 1.0, pcur = (s1 / e) * (th[v] - cc), sg = s1;   // p_0, p_1
+        cf[v] = 1.0f;
+        for (int j = 2; j <= degree; ++j) {
+          cf[(size_t)(j - 1) * nv[k] + v] = (float)pcur;                 // p_{j-1}
+          const double s2 = 1.0 / (2.0 / s1 - sg);
+          const double pn = (2.0 * s2 / e) * (th[v] - cc) * pcur - sg * s2 * pprev;
+          pprev = pcur;
+          pcur = pn;
+          sg = s2;
+        }
+        pm[v] = pcur;                                                    // p_m
+      }
+      t0 += nv[k];
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(coef[k], cf.data(), cf.size() * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(pmv[k], pm.data(), pm.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      OEFE_CUDA_TRY(c, cudaMemcpyAsync(thv[k], th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      // A Q into F1 (FP64-class: FP32 pairs in pair mode), then R (low precision) over it, row by row
+      const Step st{1, 1.0, 0.0, 0.0};
+      OEFE_TRY(dispatch_step(c, c->kd[k], dtype, X[k], ld[k], nv[k], st, nullptr, 0, nullptr, 0, F1[k], nv[k], Zk[k],
+                             Yo[k], false));
+      const int Rs = cplx ? 2 : 1, W = nv[k] * Rs;
+      const int blocks = (int)std::min<int64_t>((n * W + 255) / 256, (int64_t)c->num_sms * 32);
+      OEFE_COUNTED k_defect_residual<<<blocks, 256, 0, c->stream>>>((const double*)F1[k], W, (const double*)X[k],
+                                                                  ld[k] * Rs, thv[k], n, W, Rs, (float*)F2[k], W);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    }
+  }
   // run: the private stream waits for the caller's stream and vice versa
   OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_in, c->stream));
   OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->bstream, c->bev_in, 0));
@@ -946,16 +1080,24 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   if (timed) {
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
     for (int j = 0; j < jlow; ++j) {
+      if (defect && j == 0) continue;   // no product at the first degree of the defect form
       float t = 0;
       OEFE_CUDA_TRY(c, cudaEventElapsedTime(&t, c->bev_kernel[2 * j], c->bev_kernel[2 * j + 1]));
       c->timing_extra_ms += t;
       c->timing_extra_n += 1;
     }
   }
-  // finish per k: the last degree in FP64, or copy the low-precision result
+  // finish per k: X p_m(theta) + D_m (defect), the last degree in FP64, or copy the low-precision result
   for (int k = 0; k < nk; ++k) {
     const KData& K = c->kd[k];
-    if (mixed) {
+    if (defect) {
+      const int Rs = cplx ? 2 : 1, W = nv[k] * Rs;
+      void* L[3] = {L0[k], L1[k], L2[k]};
+      const int blocks = (int)std::min<int64_t>((n * W + 255) / 256, (int64_t)c->num_sms * 32);
+      OEFE_COUNTED k_defect_finish<<<blocks, 256, 0, c->stream>>>((double*)X[k], ld[k] * Rs, (const float*)L[P.lc[k]], W,
+                                                                pmv[k], n, W, Rs);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    } else if (mixed) {
       const int width = cplx ? 2 * nv[k] : nv[k];
       void* L[3] = {L0[k], L1[k], L2[k]};
       OEFE_TRY((convert<float, double>(c, L[P.lc[k]], width, F1[k], width, n, width)));
@@ -990,6 +1132,20 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     return OEFE_ERR_TIMEOUT;
   }
   return OEFE_OK;
+}
+
+}  // namespace
+
+int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
+                        const double* a, const double* b, const double* a0, int flags) {
+  return filter_batched_impl(c, nk, X, nv, ld, dtype, degree, a, b, a0, nullptr, flags);
+}
+
+int cheb_filter_batched_defect(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype,
+                               int degree, const double* a, const double* b, const double* a0, const double* theta,
+                               int flags) {
+  if (!theta) { c->err = "filter_batched_defect: need theta"; return OEFE_ERR_ARG; }
+  return filter_batched_impl(c, nk, X, nv, ld, dtype, degree, a, b, a0, theta, flags);
 }
 
 int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms) {

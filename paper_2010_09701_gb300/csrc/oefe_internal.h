@@ -247,6 +247,9 @@ int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int deg
                 double b, double a0, int flags);
 int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
                         const double* a, const double* b, const double* a0, int flags);
+int cheb_filter_batched_defect(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype,
+                               int degree, const double* a, const double* b, const double* a0, const double* theta,
+                               int flags);
 int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
 
 // tensor-core cell products (cell_mma.cu)

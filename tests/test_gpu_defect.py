@@ -1,0 +1,128 @@
+"""The batched Chebyshev filter in defect form, p_m(A) Q = Q p_m(Theta) + D_m
+(Sec. IV filter; the defect recurrence is ours), against the oracle's FP64
+filter: the identity on arbitrary blocks, the accuracy it keeps on nearly
+converged blocks, and converged subspace iteration on the first
+configuration (graded 8^3 mesh, p = 4, two nuclei, 20 vectors, degree 20) to
+the spec residual, with eigenvalues and band energy against exact
+eigenpairs of the oracle's operator."""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+import torch
+
+import workloads as W
+from gpu_cases import c1_pair, paired, to_gpu
+from oracle import solver
+
+pytestmark = pytest.mark.gpu
+
+KS2 = [(0.3, 0.0, 0.0), (-0.3, 0.1, 0.0)]
+TOL_FILTER = 2e-4     # BF16x3 degrees on an arbitrary block (as the plain tensor-core filter)
+
+
+def colerr(out, ref):
+    return np.max(np.linalg.norm(out - ref, axis=0) / np.linalg.norm(ref, axis=0))
+
+
+def bounds(pr):
+    ev = sla.eigh(pr.assemble_H().toarray(), pr.dense_M(), eigvals_only=True)
+    return ev[6], ev[-1] * 1.01, ev[0] - 1.0
+
+
+def test_defect_identity_random_blocks():
+    # any Q and any theta: the result is p_m(A) Q, two k-points with uneven vector counts, twice
+    # (the second call replays the captured graph with new theta)
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    prs, ctx, V, _ = paired(ks=KS2)
+    nvs = [20, 37]
+    bnds = [bounds(pr) for pr in prs]
+    deg = 7
+    rng = np.random.default_rng(4)
+    for rep in range(2):
+        Qs = [W.random_vectors(pr.n, nv, complex_=True, seed=30 + 2 * i + rep) for i, (pr, nv) in enumerate(zip(prs, nvs))]
+        th = [rng.uniform(bd[2], bd[0], nv) for bd, nv in zip(bnds, nvs)]
+        refs = [solver.chebyshev_filter(pr.apply_A, Q, deg, *bd) for pr, Q, bd in zip(prs, Qs, bnds)]
+        Xd = [to_gpu(Q) for Q in Qs]
+        ctx.filter_batched_defect(Xd, deg, [bd[0] for bd in bnds], [bd[1] for bd in bnds], [bd[2] for bd in bnds],
+                                  th, FILTER_BF16X3)
+        for k in range(2):
+            assert colerr(Xd[k].cpu().numpy(), refs[k]) < TOL_FILTER, (rep, k)
+
+
+@pytest.mark.parametrize("k", [(0.0, 0.0, 0.0), (0.25, -0.4, 0.1)])
+def test_defect_keeps_converged_directions(k):
+    # Q = exact eigenvectors + 1e-6 noise, theta = their eigenvalues: the plain mixed filter rounds
+    # at ~1e-5 of |p_m(A) Q| (BF16x3), the defect form at ~1e-5 of |D_m| ~ 1e-6 |p_m(A) Q|
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64
+    prs, ctx, V, _ = paired(ks=[k])
+    pr = prs[0]
+    ev, U = sla.eigh(pr.assemble_H().toarray(), pr.dense_M())
+    nv, deg = 12, 9
+    a, b, a0 = ev[nv + 2], ev[-1] * 1.01, ev[0] - 1.0
+    Q = U[:, :nv] + 1e-6 * W.random_vectors(pr.n, nv, complex_=pr.complex, seed=3)
+    ref = solver.chebyshev_filter(pr.apply_A, Q, deg, a, b, a0)
+    Xp = to_gpu(Q)
+    ctx.filter_batched([Xp], deg, a, b, a0, FILTER_BF16X3 | FILTER_LAST_FP64)
+    err_plain = colerr(Xp.cpu().numpy(), ref)
+    Xd = to_gpu(Q)
+    ctx.filter_batched_defect([Xd], deg, a, b, a0, [ev[:nv]], FILTER_BF16X3)
+    err_defect = colerr(Xd.cpu().numpy(), ref)
+    assert err_plain > 1e-8                 # the plain mixed filter really rounds in low precision
+    assert err_defect < 1e-9
+    assert err_defect < 1e-3 * err_plain
+
+
+def _exact_lowest(pr, k, sigma):
+    """The k lowest eigenpairs of H u = eps M u (oracle operators, shift-invert Lanczos)."""
+    H = pr.assemble_H().tocsc()
+    M = sp.block_diag([sp.diags(pr.m), sp.csr_matrix(pr.Moo)]).tocsc()
+    ev = spla.eigsh(H, k=k, M=M, sigma=sigma, which="LM", return_eigenvectors=False, tol=1e-13)
+    return np.sort(ev)
+
+
+@pytest.mark.parametrize("products", ["native", "bf16x6_pairs"])
+def test_c1_defect_passes_reach_residual_target(products):
+    # subspace iteration on the first configuration with the bench's pass (BF16 tensor-core filter in
+    # defect form from the previous Ritz pairs, FP64-class Cholesky-QR and Rayleigh-Ritz): the
+    # occupied states reach a residual below 1e-7 (the benchmark spec's target for the chosen forms);
+    # their eigenvalues then match the oracle operator's exact ones within 1e-8 Ha and the band
+    # energy within 1e-6 Ha/atom
+    from paper_2010_09701_gb300 import (F64_PAIRS, FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X6, STORE_F64,
+                                        STORE_F64PAIR, occupations)
+    w = W.config_c1()
+    if products == "bf16x6_pairs":
+        prs, ctx, V, Vd = c1_pair(store=STORE_F64 | STORE_BF16X6 | STORE_F64PAIR)
+        ctx.set_f64_products(F64_PAIRS)
+    else:
+        prs, ctx, V, Vd = c1_pair()
+    pr = prs[0]
+    nv, nocc = w.nv[0], w.nelectrons // 2
+    b = solver.lanczos_upper_bound(pr.apply_H, pr.apply_M, pr.apply_Minv, W.random_vectors(pr.n, 1, seed=9)[:, 0], 25)
+    a, a0 = 0.0, -0.5 * 14 ** 2 - 1.0
+    X = to_gpu(W.random_vectors(pr.n, nv, seed=w.seed))
+    ctx.filter_batched([X], w.degree, a, b, a0, FILTER_BF16X3 | FILTER_LAST_FP64)   # from random vectors
+    ctx.orthonormalize(0, X)
+    eps, res = ctx.rayleigh_ritz(0, X, resid=True)
+    history = [float(np.max(res[:nocc]))]
+    for it in range(120):
+        a, a0 = float(eps[-1]), float(eps[0]) - 1.0
+        ctx.filter_batched_defect([X], w.degree, a, b, a0, [eps], FILTER_BF16X3)
+        ctx.orthonormalize(0, X)
+        eps, res = ctx.rayleigh_ritz(0, X, resid=True)
+        history.append(float(np.max(res[:nocc])))
+        if history[-1] < 1e-8:
+            break
+    assert history[-1] < 1e-7, history[-12:]
+    # the GPU residuals are the oracle's residual norms of the GPU vectors
+    Xh = X.cpu().numpy()
+    res_o = solver.residual_norms(pr, Xh[:, :nocc], eps[:nocc])
+    assert np.max(res_o) < 1e-7
+    assert np.allclose(res[:nocc], res_o, rtol=1e-3, atol=1e-10)
+    exact = _exact_lowest(pr, nocc + 2, a0)
+    assert np.max(np.abs(eps[:nocc] - exact[:nocc])) < 1e-8
+    _, _, Eg = occupations([eps], [1.0], w.nelectrons)
+    mu = solver.fermi_level([exact], [1.0], w.nelectrons)
+    Eo = solver.band_energy([exact], [1.0], mu)
+    assert abs(Eg - Eo) / w.natoms < 1e-6
