@@ -248,9 +248,13 @@ int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, 
 /* ---------------------------------------------------------------- subspace
  * oefe_orthonormalize -- Cholesky-QR in the M inner product, twice
  * (Sec. IV orthonormalization): S = X^+ M X = L L^+, X <- X L^{-+}.
+ * The first pass equilibrates the columns by exact powers of two (X <- X D,
+ * S <- D S D, D_vv = 2^-e with sqrt(S_vv) in [2^(e-1), 2^e)), which leaves
+ * the result unchanged up to rounding and keeps columns of very different
+ * norms (a filtered block) resolved to their own scale.
  * FP64; X must be F64/C128. cond_est (host, may be NULL) receives
- * (max L_ii / min L_ii)^2 of the first pass. OEFE_ERR_CHOLESKY if S is not
- * positive definite. */
+ * (max L_ii / min L_ii)^2 of the first (equilibrated) pass. OEFE_ERR_CHOLESKY
+ * if S is not positive definite. */
 int oefe_orthonormalize(oefe_ctx_t ctx, int ik, void* X, int nv, int ld, int dtype, double* cond_est);
 
 /* oefe_rayleigh_ritz -- H^Q = X^+ H^O X, M^Q = X^+ M X, H^Q u = eps M^Q u

@@ -371,6 +371,44 @@ __global__ void k_quad_diag(const S* Mq, const S* U, int nv, double* out) {
   if (threadIdx.x == 0) out[v] = red[0];
 }
 
+// Column equilibration of the first Cholesky-QR pass by exact powers of two: d_v = 2^-e with
+// sqrt(S_vv) = f 2^e, f in [0.5, 1) (d_v = 1 when S_vv is not positive, so the factorization still
+// reports it). The filtered block's columns differ by orders of magnitude (the filter's gain at the
+// Ritz values), and a rotation whose operand digits share one exponent per row would otherwise
+// resolve the small columns only relative to the largest column of the row.
+template <typename S>
+__global__ void k_gram_scales(const S* Sm, int nv, double* d) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= nv) return;
+  const double s = Ops<S>::re(Sm[(size_t)v * nv + v]);
+  double out = 1.0;
+  if (s > 0.0 && isfinite(s)) {
+    int e = 0;
+    frexp(sqrt(s), &e);
+    out = ldexp(1.0, -e);
+  }
+  d[v] = out;
+}
+
+// S_vw <- d_v d_w S_vw
+template <typename S>
+__global__ void k_scale_gram(S* Sm, int nv, const double* d) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nv * nv) return;
+  Sm[t] = Ops<S>::scale(Sm[t], d[t / nv] * d[t % nv]);
+}
+
+// X_rv <- d_v X_rv
+template <typename S>
+__global__ void k_scale_cols(S* X, int ldx, int64_t n, int nv, const double* d) {
+  const int64_t total = n * nv;
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = t / nv;
+    const int v = (int)(t % nv);
+    X[r * ldx + v] = Ops<S>::scale(X[r * ldx + v], d[v]);
+  }
+}
+
 // R = HX - MX diag(eps)
 template <typename S>
 __global__ void k_resid_vec(const S* HX, const S* MX, int ld, const double* eps, int64_t n, int nv, S* R) {
@@ -549,15 +587,27 @@ int orthonormalize_t(oefe_ctx* c, int ik, S* X, int nv, int ld, double* cond) {
   const size_t wbytes = (((size_t)n * nv * sizeof(S) + 255) / 256) * 256;
   const size_t sbytes = (((size_t)nv * nv * sizeof(S) + 255) / 256) * 256;
   const size_t pbytes = (size_t)nchunk * nv * nv * sizeof(S);
-  OEFE_TRY(ensure_ws(c, wbytes + 2 * sbytes + pbytes));
+  const size_t pbytes_a = ((pbytes + 255) / 256) * 256;
+  OEFE_TRY(ensure_ws(c, wbytes + 2 * sbytes + pbytes_a + (size_t)nv * sizeof(double)));
   char* base = (char*)c->ws;
   S* W = (S*)base;
   S* Sm = (S*)(base + wbytes);
   S* Y = (S*)(base + wbytes + sbytes);
   S* part = (S*)(base + wbytes + 2 * sbytes);
+  double* dsc = (double*)(base + wbytes + 2 * sbytes + pbytes_a);
   for (int pass = 0; pass < 2; ++pass) {
     OEFE_TRY(apply_M<S>(c, K, X, ld, nv, W, nv));
     OEFE_TRY(gram<S>(c, X, ld, W, nv, n, nv, Sm, part, nchunk));
+    if (pass == 0) {
+      // equilibrate: X <- X D, S <- D S D (exact); Q = (X D) (D S D)^{-1/2 Cholesky} spans the same
+      // space and is the same matrix up to rounding
+      OEFE_COUNTED k_gram_scales<S><<<(nv + 127) / 128, 128, 0, c->stream>>>(Sm, nv, dsc);
+      OEFE_COUNTED k_scale_gram<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(Sm, nv, dsc);
+      const int64_t tot = n * nv;
+      const int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)c->num_sms * 32);
+      OEFE_COUNTED k_scale_cols<S><<<blocks, 256, 0, c->stream>>>(X, ld, n, nv, dsc);
+      OEFE_CUDA_TRY(c, cudaGetLastError());
+    }
     int info = 0;
     OEFE_TRY(chol_inverse_t<S>(c, Sm, nv, false, true, Y, &info));
     if (info != 0) {
