@@ -51,14 +51,21 @@ TRAFFIC_PAIR = {"sf_bytes_per_cell": (344.007e6 + 151.686e6) / 448, "dense_bytes
                 "source": "profiles/fp64_class_products_c3small_8cube_p6.md"}
 
 
+def is_complex(w):
+    """k-points other than Gamma need complex arithmetic; a 1x1x1 grid is the Gamma point alone."""
+    return tuple(w.kgrid) != (1, 1, 1)
+
+
 def workload_text(w):
     """The workload as the JSON line names it (both arms): cell, mesh, basis, k-points, vectors."""
     zs = "/".join(str(int(z)) for z in sorted(set(np.asarray(w.Z).tolist()), reverse=True))
     kg = tuple(w.kgrid)
-    return ("zincblende a=%g bohr %d atoms (Z %s), graded %d^3 cells p=%d, %d enrichment functions, "
-            "MP %dx%dx%d (%d k), %d vectors/k, Chebyshev degree %d"
-            % (w.a, w.natoms, zs, w.ncell, w.p, len(W.ORBITALS_1S_2P) * w.natoms, kg[0], kg[1], kg[2],
-               len(w.nv), w.nv[0], w.degree))
+    kt = ("MP %dx%dx%d (%d k, complex)" % (kg[0], kg[1], kg[2], len(w.nv))) if is_complex(w) else "Gamma point (real)"
+    nvt = ("%d vectors/k" % w.nv[0]) if len(set(w.nv)) == 1 else ("%d-%d vectors/k" % (min(w.nv), max(w.nv)))
+    cell = "zincblende" if w.natoms == 8 else "supercell"
+    return ("%s: %s a=%g bohr, %d atoms (Z %s), graded %d^3 cells p=%d, %d enrichment functions, %s, %s, "
+            "Chebyshev degree %d"
+            % (w.name, cell, w.a, w.natoms, zs, w.ncell, w.p, len(W.ORBITALS_1S_2P) * w.natoms, kt, nvt, w.degree))
 
 
 def nucleus_cells(w):
@@ -163,10 +170,10 @@ def whole_job_tflops(flops_per_rank, world, ms):
     return world * flops_per_rank / (ms * 1e-3) / 1e12
 
 
-def dense_filter_flops(ctx_naug, nvs, degree):
-    """sum over k of sum_e 2 n_aug,e^2 N_v,k * 4 (complex) per degree, times the degree."""
+def dense_filter_flops(ctx_naug, nvs, degree, cplx=True):
+    """sum over k of sum_e 2 n_aug,e^2 N_v,k c_k per degree (c_k = 4 complex, 1 real), times the degree."""
     s2 = float(np.sum(np.asarray(ctx_naug, float) ** 2))
-    return sum(2.0 * s2 * nv * 4.0 for nv in nvs) * degree
+    return sum(2.0 * s2 * nv * (4.0 if cplx else 1.0) for nv in nvs) * degree
 
 
 def kernel_flops_per_launch(naug, nv, cplx=True):
@@ -192,12 +199,27 @@ def run_ours(args, rank, world):
     n = nh + nO
     nk = ctx.nk
     xyz, qw = ctx.quadrature_points()
-    V = torch.tensor(W.veff(xyz, w.a, w.pos, w.Z, w.sigma), dtype=torch.float64, device="cuda")
+    V = W.veff_device(xyz, w.a, w.pos, w.Z, w.sigma, device="cuda")
+    cplx = is_complex(w)
+    vdt = torch.complex128 if cplx else torch.float64      # FP64-class vectors
+    ldt = torch.complex64 if cplx else torch.float32       # low-precision vectors
+    dt64 = P.C128 if cplx else P.F64
+    dt32 = P.C64 if cplx else P.F32
     split = P.STORE_BF16X3 if args.bf16x3 else P.STORE_BF16X6
     store = P.STORE_F64 | (split if args.tensor else P.STORE_F32)
     pairs = args.f64_products == "pairs"
     if pairs:
         store |= P.STORE_F64PAIR
+    # the compact FP64 layout (enrichment strips of single-leaf cells) when the whole FP64 copies
+    # would take more than a quarter of the device
+    ncells = w.ncell ** 3
+    naug = np.array([len(ctx.cell_info(e)) for e in range(ncells)])
+    npad = -(-int(naug.max()) // 128) * 128
+    full64 = ncells * npad * npad * (16 if cplx else 8) * (2 if pairs else 1) * nk
+    dev_bytes = torch.cuda.get_device_properties(dev).total_memory
+    compact = args.compact == "on" or (args.compact == "auto" and full64 > dev_bytes / 4)
+    if compact:
+        store |= P.STORE_COMPACT
     ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
     ctx.set_product_shape(args.product_shape)
     if args.filter_only:   # profiling aid: the low-precision matrices (and FP64 ones on request) only
@@ -207,16 +229,15 @@ def run_ours(args, rank, world):
     ctx.build_hamiltonian(V, store)
     if args.filter_only:
         ctx.release_workspace()   # the build's scratch is several times the filter's
-    naug = np.array([len(ctx.cell_info(e)) for e in range(int(np.prod([w.ncell] * 3)))])
     nvs = w.nv
     deg = w.degree
-    X0 = [torch.tensor(W.random_vectors(n, nvs[ik], complex_=True, seed=w.seed + ik), dtype=torch.complex128,
-                       device="cuda") for ik in range(nk)]
+    X0 = [torch.tensor(W.random_vectors(n, nvs[ik], complex_=cplx, seed=w.seed + ik), dtype=vdt, device="cuda")
+          for ik in range(nk)]
     X = [x.clone() for x in X0]
     # filter bounds: b from a Lanczos run per k; a, a0 below/above the wanted window
     bks = []
     for ik in range(nk):
-        v0 = torch.tensor(W.random_vectors(n, 1, complex_=True, seed=100 + ik), dtype=torch.complex128, device="cuda")
+        v0 = torch.tensor(W.random_vectors(n, 1, complex_=cplx, seed=100 + ik), dtype=vdt, device="cuda")
         bks.append(ctx.upper_bound(ik, v0, 20, P.FILTER_BF16X3 if (args.tensor or args.filter_only) else 0))
     a_lo, a0 = 0.0, -0.5 * float(max(w.Z)) ** 2 - 1.0
     rho = torch.zeros(len(qw), dtype=torch.float64, device="cuda")
@@ -228,7 +249,7 @@ def run_ours(args, rank, world):
     phase_ms = {}
     fflags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
     if args.filter_only:
-        X32 = X0[0].to(torch.complex64)
+        X32 = X0[0].to(ldt)
         for _ in range(args.steps):
             ctx.chebyshev_filter(0, X32, deg, a_lo, bks[0], a0, flags=P.FILTER_BF16X3 if args.tensor else 0)
         if args.with_fp64:   # one FP64 operator application (the FP64 cell product)
@@ -253,7 +274,8 @@ def run_ours(args, rank, world):
     defect = batched and not args.plain_filter
     tune_ms = None
     if batched:
-        tune_ms = [float(x) for x in ctx.filter_autotune(X0)]
+        # on at most one batched group of vectors per k (wider blocks run as several groups)
+        tune_ms = [float(x) for x in ctx.filter_autotune([x[:, :min(x.shape[1], 128)] for x in X0])]
 
     def subspace_pass(Xs, bnd, theta, resid=False):
         """One pass of the subspace iteration over all k (outside the timed region): the batched
@@ -345,7 +367,7 @@ def run_ours(args, rank, world):
     barrier(world)
     sampler = ClockSampler(dev)
     sampler.start()
-    ctx.kernel_timing([P.C64])
+    ctx.kernel_timing([dt32])
     torch.cuda.synchronize()
     barrier(world)
     ev0 = torch.cuda.Event(enable_timing=True)
@@ -363,30 +385,34 @@ def run_ours(args, rank, world):
     ctx.kernel_timing([])
     step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
     filt_ms = [a.elapsed_time(b) for a, b in filt_events]
-    flops_step = dense_filter_flops(naug, nvs, deg)
+    flops_step = dense_filter_flops(naug, nvs, deg, cplx)
     value = whole_job_tflops(flops_step, world, step_ms)
     filt_tflops = flops_step / (sum(filt_ms) / args.steps * 1e-3) / 1e12
     # seconds per filter pass of one k-point
     s_per_pass = float(np.mean(filt_ms)) * 1e-3 / (nk if batched else 1)
     # dominant kernel: the FP32 (complex64) cell product
     per_launch_ms = kms / max(klaunch, 1)
-    kmul = nk if batched else 1   # a batched launch covers every k-point
-    kflops = kernel_flops_per_launch(naug, nvs[0], True) * kmul
+    # a batched launch covers every k-point and one group of at most 128 vectors per k
+    ngroups = -(-max(nvs) // 128)
+    nv_launch = [-(-v // ngroups) for v in nvs] if batched else nvs[:1]
+    kflops = sum(kernel_flops_per_launch(naug, v, cplx) for v in nv_launch)
     nparts = 2 if args.bf16x3 else 3           # bf16 parts per real value of the split matrices
     nprod = 3 if args.bf16x3 else 6            # products per element on the tensor cores
-    kbytes = (float(np.sum(naug ** 2)) * 4 * nparts + 2 * float(np.sum(naug)) * nvs[0] * 8) * kmul
+    cf = 2 if cplx else 1                      # real planes per matrix entry / reals per vector entry
+    kbytes = sum(float(np.sum(naug ** 2)) * 2 * nparts * cf + 2 * float(np.sum(naug)) * v * 4 * cf for v in nv_launch)
     achieved = kflops / (per_launch_ms * 1e-3) / 1e12
     peaks, src = measured_peaks()
     if args.tensor:
         hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
         ach = kbytes / (per_launch_ms * 1e-3) / 1e9
-        roof_low = {"kernel": "k_cell_mma_tma<complex> (tcgen05 + TMA, BF16x%d)" % nprod + (" over all k" if batched else ""),
+        roof_low = {"kernel": ("k_cell_mma_tma<%s> (tcgen05 + TMA, BF16x%d)" % ("complex" if cplx else "real", nprod)
+                               + (" over all k" if batched else "")),
                     "bound": "hbm", "achieved": ach, "peak": hbm,
                     "unit": "GB/s", "frac": ach / hbm,
-                    "traffic": (TRAFFIC_TENSOR[nparts]["bytes_per_tile"] * len(naug) * kmul * ((nvs[0] + 63) // 64)
-                                if nparts in TRAFFIC_TENSOR else None),
+                    "traffic": (TRAFFIC_TENSOR[nparts]["bytes_per_tile"] * len(naug) * sum((v + 63) // 64 for v in nv_launch)
+                                if (nparts in TRAFFIC_TENSOR and cplx) else None),
                     "traffic_source": (TRAFFIC_TENSOR[nparts]["source"] + " (scaled by tiles)"
-                                       if nparts in TRAFFIC_TENSOR else None),
+                                       if (nparts in TRAFFIC_TENSOR and cplx) else None),
                     "algorithmic_bytes_per_launch": kbytes,
                     "launches": klaunch, "ms_per_launch": per_launch_ms, "peak_source": src,
                     "dense_tflops": achieved,
@@ -403,13 +429,18 @@ def run_ours(args, rank, world):
     accuracy = None
     fp64_ms_launch = None
     if not args.skip_fp64:
-        # one FP64 filter pass (k = 0) from the same start vectors, the FP64 cell product timed live
+        # one FP64 filter pass (k = 0) from the same start vectors, the FP64 cell product timed live.
+        # Blocks wider than 64 vectors go through the FP64 filter in independent chunks of 64 columns:
+        # one chunk is timed and the pass time scaled by the chunk count (the columns are independent
+        # and every chunk does the same work)
         ctx.set_f64_products(P.F64_NATIVE)
-        Xf = X0[0].clone()
+        vslice = min(nvs[0], 64)
+        fp64_scale = nvs[0] / vslice
+        Xf = X0[0][:, :vslice].clone()
         ctx.chebyshev_filter(0, Xf, 1, a_lo, bks[0], a0)   # warm
-        Xf.copy_(X0[0])
+        Xf.copy_(X0[0][:, :vslice])
         torch.cuda.synchronize()
-        ctx.kernel_timing([P.C128])
+        ctx.kernel_timing([dt64])
         f0 = torch.cuda.Event(enable_timing=True)
         f1 = torch.cuda.Event(enable_timing=True)
         f0.record(stream)
@@ -418,27 +449,32 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         k64_ms, k64_n = ctx.kernel_time()
         ctx.kernel_timing([])
+        del Xf
         fp64_ms_launch = k64_ms / max(k64_n, 1)
-        fp64_s = f0.elapsed_time(f1) * 1e-3
+        fp64_s = f0.elapsed_time(f1) * 1e-3 * fp64_scale
         # the FP64-class product of the mixed step (FP32 pairs on the single-leaf cells), timed live
         # on the same vectors
         mix_ms_launch = fp64_ms_launch
         if pairs:
             ctx.set_f64_products(P.F64_PAIRS)
-            Yp = torch.empty_like(X0[0])
-            ctx.apply_h(0, X0[0], Yp)   # warm
+            Xs_ = X0[0][:, :vslice]
+            Yp = torch.empty_like(Xs_)
+            ctx.apply_h(0, Xs_, Yp)   # warm
             torch.cuda.synchronize()
-            ctx.kernel_timing([P.C128])
+            ctx.kernel_timing([dt64])
             for _ in range(3):
-                ctx.apply_h(0, X0[0], Yp)
+                ctx.apply_h(0, Xs_, Yp)
             torch.cuda.synchronize()
             kp_ms, kp_n = ctx.kernel_time()
             ctx.kernel_timing([])
             mix_ms_launch = kp_ms / max(kp_n, 1)
             del Yp
         fp64 = {"s_per_pass_k0": fp64_s,
-                "tflops": dense_filter_flops(naug, [nvs[0]], deg) / fp64_s / 1e12,
+                "tflops": dense_filter_flops(naug, [nvs[0]], deg, cplx) / fp64_s / 1e12,
                 "speedup_mixed_vs_fp64": fp64_s / s_per_pass}
+        if fp64_scale != 1.0:
+            fp64["timed_columns"] = vslice
+            fp64["scaled_to_columns"] = nvs[0]
 
         # accuracy at convergence: the subspace iteration of the step (defect-form mixed filter from the
         # previous Ritz pairs, FP64-class Cholesky-QR and Rayleigh-Ritz, every k) runs from the step's
@@ -446,7 +482,10 @@ def run_ours(args, rank, world):
         # stops falling; then one pass with the native FP64 filter (FP64 products, Cholesky-QR and
         # Rayleigh-Ritz) from that subspace is compared with it
         if defect:
-            Xc = [x.clone() for x in X0]
+            # the step's buffers hold the iteration (every step copies its start from X0 again)
+            Xc = X
+            for ik in range(nk):
+                Xc[ik].copy_(X0[ik])
             theta, bnd = theta0, bnd0
             hist = []
             occ_idx = None
@@ -465,14 +504,12 @@ def run_ours(args, rank, world):
             # one FP64 pass from the converged subspace: native FP64 filter, Cholesky-QR, Rayleigh-Ritz
             ctx.set_f64_products(P.F64_NATIVE)
             ev_d, res_d = [], []
-            for ik in range(nk):
-                Xd_ = Xc[ik].clone()
-                ctx.chebyshev_filter(ik, Xd_, deg, bnd[ik][0], bks[ik], bnd[ik][1])
-                ctx.orthonormalize(ik, Xd_)
-                e_, r_ = ctx.rayleigh_ritz(ik, Xd_, resid=True)
+            for ik in range(nk):   # in place: the mixed state is not needed any more
+                ctx.chebyshev_filter(ik, Xc[ik], deg, bnd[ik][0], bks[ik], bnd[ik][1])
+                ctx.orthonormalize(ik, Xc[ik])
+                e_, r_ = ctx.rayleigh_ritz(ik, Xc[ik], resid=True)
                 ev_d.append(e_)
                 res_d.append(r_)
-                del Xd_
             ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
             _, occ_d, e_d = P.occupations(ev_d, [1.0 / nk] * nk, w.nelectrons)
             occ_idx_d = [np.asarray(o) > 1e-8 for o in occ_d]
@@ -489,13 +526,12 @@ def run_ours(args, rank, world):
                         "max_abs_d_eig_occupied_Ha": float(max(np.max(np.abs(np.asarray(a)[o] - np.asarray(b)[o]))
                                                                for a, b, o in zip(ev_m, ev_d, occ_idx))),
                         "occupied_states": int(sum(int(np.sum(o)) for o in occ_idx))}
-            del Xc
 
     # the dominant kernel of the step (most device time per step) carries "roofline", the other
     # cell product "roofline_secondary"
     roofline, roof2 = roof_low, None
     if fp64_ms_launch is not None:
-        f64_flops = ctx.product_flops(0, nvs[0])   # FP64-class operations the cell products execute
+        f64_flops = ctx.product_flops(0, vslice)   # FP64-class operations of one launch (<= 64 vectors)
         f64_ach = f64_flops / (fp64_ms_launch * 1e-3) / 1e12
         fp64["product"] = {"kernel": "k_cell_apply_sf<double> + k_cell_apply_z3", "ms_per_launch": fp64_ms_launch,
                            "achieved_tflops": f64_ach, "frac_of_fp64_peak": f64_ach / FP64_PEAK_DERIVED}
@@ -525,11 +561,11 @@ def run_ours(args, rank, world):
                      "traffic": traffic["bytes"] if traffic else None,
                      "traffic_source": traffic["source"] if traffic else None,
                      "algorithmic_flops_per_launch": f64_flops, "ms_per_launch": mix_ms_launch,
-                     "launches_per_step": 2 * nk,
+                     "launches_per_step": 2 * sum(-(-v // 64) for v in nvs),
                      "peak_source": psrc,
-                     "dense_equivalent_tflops": kernel_flops_per_launch(naug, nvs[0], True) / (mix_ms_launch * 1e-3) / 1e12}
+                     "dense_equivalent_tflops": kernel_flops_per_launch(naug, vslice, cplx) / (mix_ms_launch * 1e-3) / 1e12}
         low_ms_step = per_launch_ms * klaunch / max(args.steps, 1)
-        if 2 * nk * mix_ms_launch > low_ms_step:
+        if roof_fp64["launches_per_step"] * mix_ms_launch > low_ms_step:
             roofline, roof2 = roof_fp64, roof_low
         else:
             roof2 = roof_fp64
@@ -555,7 +591,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t_start) / args.e2e_steps
         e2e_ms = ee0.elapsed_time(ee1) / args.e2e_steps
-        bi = V.numel() * 8 + sum(x.numel() * 16 for x in X0)
+        bi = V.numel() * 8 + sum(x.numel() * x.element_size() for x in X0)
         bo = rho.numel() * 8 + sum(len(e) * 8 for e in eigs_e)
         e2e_ms = max_over_ranks(max(e2e_ms, wall * 1e3), world, "cuda")
         e2e = {"value": whole_job_tflops(flops_step, world, e2e_ms), "unit": "TFLOP/s",
@@ -618,7 +654,10 @@ def run_oracle_sample(w, ncells_side, steps=1, warmup=0):
     s = ncells_side
     cells = [ix + w.ncell * (iy + w.ncell * iz) for iz in range(s) for iy in range(s) for ix in range(s)]
     pr = Problem(mesh, quad, enr, k[0], cells=cells)
-    V = W.veff(quad.points, w.a, w.pos, w.Z, w.sigma)
+    V = np.zeros(quad.nq)   # the potential is needed only at the block's points
+    for e in cells:
+        sl = slice(quad.offset[e], quad.offset[e + 1])
+        V[sl] = W.veff(quad.points[sl], w.a, w.pos, w.Z, w.sigma)
     nv = w.nv[0]
     X0 = W.random_vectors(pr.n, nv, complex_=pr.complex, seed=w.seed)
     naug = np.array([len(pr.index(e)) for e in cells])
@@ -662,7 +701,10 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c3", choices=["c2", "c3", "c3small", "c3mid"])
+    ap.add_argument("--config", default="c3", choices=["c2", "c3", "c3small", "c3mid", "c5", "c5mid"])
+    ap.add_argument("--compact", default="auto", choices=["auto", "on", "off"],
+                    help="compact layout of the FP64-class cell matrices (auto: when the full copies would take "
+                         "more than a quarter of the device)")
     ap.add_argument("--filter-only", action="store_true",
                     help="profiling aid: set up, then run --steps low-precision filter passes on k-point 0 only")
     ap.add_argument("--sample-cells", type=int, default=2)

@@ -51,7 +51,8 @@ enum {
 enum { OEFE_F64 = 0, OEFE_F32 = 1, OEFE_C128 = 2, OEFE_C64 = 3 };
 
 /* Storage of the cell Hamiltonians (bit mask for oefe_build_hamiltonian). */
-enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4, OEFE_STORE_BF16X6 = 8, OEFE_STORE_F64PAIR = 16 };
+enum { OEFE_STORE_F64 = 1, OEFE_STORE_F32 = 2, OEFE_STORE_BF16X3 = 4, OEFE_STORE_BF16X6 = 8, OEFE_STORE_F64PAIR = 16,
+       OEFE_STORE_COMPACT = 32 };
 /* arithmetic of the FP64 cell products (oefe_set_f64_products) */
 enum { OEFE_F64_NATIVE = 0, OEFE_F64_PAIRS = 1 };
 
@@ -132,7 +133,14 @@ int oefe_ndof(oefe_ctx_t ctx, int64_t* n_h, int* n_O);
  * set). The tensor-core filter (OEFE_FILTER_BF16X3) uses whichever split is
  * stored. OEFE_STORE_F64PAIR (with OEFE_STORE_F64) also keeps each FP64 value
  * as a pair of FP32 numbers hi + lo (same bytes as FP64, about 48 significant
- * bits) for the FP32-pair products of oefe_set_f64_products. All arithmetic of
+ * bits) for the FP32-pair products of oefe_set_f64_products.
+ * OEFE_STORE_COMPACT (with OEFE_STORE_F64) keeps the FP64 and FP32-pair
+ * copies in a compact layout: cells with several quadrature leaves whole,
+ * single-leaf cells only as their enrichment strip (the CO block and the
+ * enrichment rows), whose CFE-CFE block the FP64-class products apply by sum
+ * factorization anyway (about 1/6 of the bytes at p = 6); oefe_cell_matrix then
+ * returns OEFE_ERR_STATE for single-leaf cells. It needs the sum-factorized
+ * products (hexahedral cells, p <= 7), else OEFE_ERR_ARG. All arithmetic of
  * the build is FP64. */
 int oefe_build_hamiltonian(oefe_ctx_t ctx, const double* veff_q, int store);
 

@@ -24,12 +24,12 @@ the lowest Ritz value; FILTER_BF16X3 selects the tensor-core degrees, whose
 split (two or three bf16 parts) follows the stored matrices.
 """
 from .binding import (C64, C128, F32, F64, F64_NATIVE, F64_PAIRS, FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X3,
-                      STORE_BF16X6, STORE_F32, STORE_F64, STORE_F64PAIR,
+                      STORE_BF16X6, STORE_COMPACT, STORE_F32, STORE_F64, STORE_F64PAIR,
                       Context, OefeError,
                       SIGNATURES, launch_count, load, occupations)
 from .problem import setup_workload
 
 __all__ = ["Context", "OefeError", "load", "launch_count", "occupations", "setup_workload", "SIGNATURES", "F64", "F32", "C128", "C64",
-           "STORE_F64", "STORE_F32", "STORE_BF16X3", "STORE_BF16X6", "STORE_F64PAIR", "F64_NATIVE", "F64_PAIRS",
+           "STORE_F64", "STORE_F32", "STORE_BF16X3", "STORE_BF16X6", "STORE_F64PAIR", "STORE_COMPACT", "F64_NATIVE", "F64_PAIRS",
            "FILTER_LAST_FP64",
            "FILTER_BF16X3"]

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "liboefe.so")
 OK, ERR_ARG, ERR_STATE, ERR_OOM, ERR_CUDA, ERR_CHOLESKY, ERR_NOTPD_MOO, ERR_TIMEOUT, ERR_NUMERIC = \
     0, -1, -2, -3, -4, -5, -6, -7, -8
 F64, F32, C128, C64 = 0, 1, 2, 3
-STORE_F64, STORE_F32, STORE_BF16X3, STORE_BF16X6, STORE_F64PAIR = 1, 2, 4, 8, 16
+STORE_F64, STORE_F32, STORE_BF16X3, STORE_BF16X6, STORE_F64PAIR, STORE_COMPACT = 1, 2, 4, 8, 16, 32
 F64_NATIVE, F64_PAIRS = 0, 1
 FILTER_LAST_FP64, FILTER_BF16X3 = 1, 2
 NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024

@@ -29,16 +29,16 @@ static void free_all(oefe_ctx* c) {
   c->ev_pool.clear();
   for (cudaEvent_t e : c->bev_kernel) cudaEventDestroy(e);
   c->bev_kernel.clear();
-  if (c->bgraph) cudaGraphExecDestroy(c->bgraph);
+  release_batch_graphs(c);
   if (c->bev_in) cudaEventDestroy(c->bev_in);
   if (c->bev_out) cudaEventDestroy(c->bev_out);
   if (c->bstream) cudaStreamDestroy(c->bstream);
-  dev_free(c->bparams);
   dev_free(c->d_tmaps);
   dev_free(c->d_sf);
   dev_free(c->d_sf_cells);
   dev_free(c->d_dense_cells);
   dev_free(c->d_sf_index);
+  dev_free(c->d_dense_index);
   dev_free(c->d_rotp);
   c->d_rotp = nullptr;
   c->rotp_bytes = 0;
@@ -204,7 +204,17 @@ int oefe_cell_matrix(oefe_ctx_t ctx, int ik, int cell, void* H) {
   const int ne = ctx->act_off[cell + 1] - ctx->act_off[cell];
   const int na = ctx->nloc + ne;
   const size_t sb = K.cplx ? 16 : 8;
-  const char* src = (const char*)K.H64 + (size_t)cell * ctx->npad * ctx->npad * sb;
+  size_t slot = (size_t)cell;
+  if (K.compact) {   // only the cells with several quadrature leaves are kept whole
+    int d = -1;
+    OEFE_CUDA_TRY(ctx, cudaMemcpy(&d, ctx->d_dense_index + cell, sizeof(int), cudaMemcpyDeviceToHost));
+    if (d < 0) {
+      ctx->err = "cell_matrix: the compact storage keeps only the enrichment strip of a single-leaf cell";
+      return OEFE_ERR_STATE;
+    }
+    slot = (size_t)d;
+  }
+  const char* src = (const char*)K.H64 + slot * ctx->npad * ctx->npad * sb;
   OEFE_CUDA_TRY(ctx, cudaMemcpy2DAsync(H, na * sb, src, ctx->npad * sb, na * sb, na, cudaMemcpyDeviceToHost,
                                        ctx->stream));
   OEFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
@@ -348,11 +358,7 @@ int oefe_release_workspace(oefe_ctx_t ctx) {
   CTX_CHECK(ctx);
   OEFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
   if (ctx->bstream) OEFE_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->bstream));
-  if (ctx->bgraph) {
-    cudaGraphExecDestroy(ctx->bgraph);
-    ctx->bgraph = nullptr;
-  }
-  ctx->bkey.clear();
+  release_batch_graphs(ctx);   // they point into the workspace
   dev_free(ctx->ws);
   dev_free(ctx->ws2);
   ctx->ws = ctx->ws2 = nullptr;

@@ -876,6 +876,12 @@ struct StoreOut {
   float* Hp;
   int parts, nloc, npad, ne_max;
   cd* E0;
+  // compact layout of H64 / Hp (KData::compact): cell -> dense-list position or sum-factorization
+  // row, and where the strips start
+  const int* dense_index;
+  const int* sf_index;
+  long long sf_base, strip;
+  int compact;
 };
 
 // v in FP64 and as FP32 pairs (pr, pi): the pair copy and the bf16 splits are taken from the pairs
@@ -890,14 +896,27 @@ __device__ inline void store_entry2(const StoreOut& O, int e, int ne, int r, int
     return;
   }
   const size_t o = (size_t)e * npad * npad + (size_t)r * npad + c;
+  // H64 / Hp offset: the full layout, or the compact one (the CFE-CFE block of single-leaf cells and
+  // rows beyond the enrichment strip are not kept)
+  long long oc = (long long)o;
+  if (O.compact) {
+    const int d = O.dense_index[e];
+    if (d >= 0) {
+      oc = ((long long)d * npad + r) * npad + c;
+    } else {
+      const long long b = O.sf_base + (long long)O.sf_index[e] * O.strip;
+      if (r < nloc) oc = (c >= nloc && c < nloc + O.ne_max) ? b + (long long)r * O.ne_max + (c - nloc) : -1;
+      else oc = r < nloc + O.ne_max ? b + (long long)nloc * O.ne_max + (long long)(r - nloc) * npad + c : -1;
+    }
+  }
   if constexpr (sizeof(S) == sizeof(cd)) {
-    if (O.H64) reinterpret_cast<cd*>(O.H64)[o] = v;
+    if (O.H64 && oc >= 0) reinterpret_cast<cd*>(O.H64)[oc] = v;
     if (O.H32) reinterpret_cast<cf*>(O.H32)[o] = cf{(float)v.x, (float)v.y};
-    if (O.Hp) reinterpret_cast<float4*>(O.Hp)[o] = make_float4(pr.h, pr.l, pi.h, pi.l);
+    if (O.Hp && oc >= 0) reinterpret_cast<float4*>(O.Hp)[oc] = make_float4(pr.h, pr.l, pi.h, pi.l);
   } else {
-    if (O.H64) reinterpret_cast<double*>(O.H64)[o] = v.x;
+    if (O.H64 && oc >= 0) reinterpret_cast<double*>(O.H64)[oc] = v.x;
     if (O.H32) reinterpret_cast<float*>(O.H32)[o] = (float)v.x;
-    if (O.Hp) reinterpret_cast<float2*>(O.Hp)[o] = make_float2(pr.h, pr.l);
+    if (O.Hp && oc >= 0) reinterpret_cast<float2*>(O.Hp)[oc] = make_float2(pr.h, pr.l);
   }
   if (O.Hbf) {
     // tile-contiguous: per cell [K tile of 64 columns][M tile of 128 rows][plane][128][64], so that
@@ -1356,6 +1375,11 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     O.npad = c->npad;
     O.ne_max = c->ne_max;
     O.E0 = nullptr;
+    O.dense_index = c->d_dense_index;
+    O.sf_index = c->d_sf_index;
+    O.sf_base = (long long)c->n_dense * c->npad * c->npad;
+    O.strip = (long long)compact_strip(c);
+    O.compact = K.compact ? 1 : 0;
     if (mode == 2) {
       if (K.cplx && pairs) OEFE_COUNTED k_finish<cd, f2><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
       else if (K.cplx) OEFE_COUNTED k_finish<cd, double><<<nb, 256, 0, c->stream>>>(HE, c->d_act_off, e0, O);
@@ -1365,7 +1389,7 @@ static int run_cell_kernel(oefe_ctx* c, KData& K, int mode, const double* veff, 
     }
     if (mode == 0) {
       // the V-independent OEFE blocks CO0, OO0 of each cell into the cache
-      O = StoreOut{nullptr, nullptr, nullptr, nullptr, 0, c->nloc, c->npad, c->ne_max, (cd*)K.E0};
+      O = StoreOut{nullptr, nullptr, nullptr, nullptr, 0, c->nloc, c->npad, c->ne_max, (cd*)K.E0, nullptr, nullptr, 0, 0, 0};
       TransformSf T;
       T.sf = c->use_sumfac && c->n_sf > 0 ? c->d_sf : nullptr;
       T.sf_index = c->d_sf_index;
@@ -1496,6 +1520,15 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
     c->err = "build_hamiltonian: OEFE_STORE_F64PAIR goes with OEFE_STORE_F64 (the refined cells stay FP64)";
     return OEFE_ERR_ARG;
   }
+  const bool compact = (store & OEFE_STORE_COMPACT) != 0;
+  if (compact && !(store & OEFE_STORE_F64)) {
+    c->err = "build_hamiltonian: OEFE_STORE_COMPACT is a layout of the OEFE_STORE_F64 (and F64PAIR) copies";
+    return OEFE_ERR_ARG;
+  }
+  if (compact && !(c->use_sumfac && c->d_dense_index && c->d_sf_index)) {
+    c->err = "build_hamiltonian: OEFE_STORE_COMPACT needs the sum-factorized products (p <= 7, hexahedral cells)";
+    return OEFE_ERR_ARG;
+  }
   double* d_gw = nullptr;
   OEFE_TRY(gauss_table(c, &d_gw));
   // V at the points, kept for the sum-factorized FP64 products of this operator
@@ -1505,15 +1538,23 @@ int build_hamiltonian(oefe_ctx* c, const double* veff, int store) {
   for (auto& K : c->kd) {
     const size_t sb = K.cplx ? sizeof(cd) : sizeof(double);
     const size_t n = (size_t)c->ncells * c->npad * c->npad;
+    const size_t n64 = h64_entries(c, compact);
     // keep existing buffers when the requested storage is unchanged
     auto keep = [&](void** p, bool want, size_t bytes) -> int {
       if (!want) { dev_free(*p); *p = nullptr; return OEFE_OK; }
       if (*p) return OEFE_OK;
       return dev_alloc(c, p, bytes);
     };
-    st = keep((void**)&K.H64, store & OEFE_STORE_F64, n * sb);
+    if (compact != K.compact) {   // another layout: new FP64 / pair buffers
+      dev_free(K.H64);
+      dev_free(K.Hp);
+      K.H64 = nullptr;
+      K.Hp = nullptr;
+    }
+    K.compact = compact;
+    st = keep((void**)&K.H64, store & OEFE_STORE_F64, n64 * sb);
     if (st == OEFE_OK) st = keep((void**)&K.H32, store & OEFE_STORE_F32, n * sb / 2);
-    if (st == OEFE_OK) st = keep((void**)&K.Hp, store & OEFE_STORE_F64PAIR, n * sb);
+    if (st == OEFE_OK) st = keep((void**)&K.Hp, store & OEFE_STORE_F64PAIR, n64 * sb);
     const int parts = (store & OEFE_STORE_BF16X6) ? 3 : (store & OEFE_STORE_BF16X3) ? 2 : 0;
     if (parts != K.bf_parts) {   // a different split: a new buffer
       dev_free(K.Hbf);

@@ -45,11 +45,13 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply(const typename Sc<T,
                                                             const int* __restrict__ act_off,
                                                             const int* __restrict__ act_idx, int nloc, int npad,
                                                             int64_t nh, typename Sc<T, C>::type* __restrict__ Z,
-                                                            const int* __restrict__ cells) {
+                                                            const int* __restrict__ cells, int compact) {
   using S = typename Sc<T, C>::type;
   extern __shared__ unsigned char smem_raw[];
   S* Xs = reinterpret_cast<S*>(smem_raw);  // npad x NB
   const int e = cells ? cells[blockIdx.x] : blockIdx.x;
+  // compact layout: the listed (dense) cells' matrices in list order
+  const size_t hslot = compact ? (size_t)blockIdx.x : (size_t)e;
   const int v0 = blockIdx.y * NB;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int ne = act_off[e + 1] - act_off[e];
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply(const typename Sc<T,
     Xs[r * NB + lane] = val;
   }
   __syncthreads();
-  const S* He = H + (size_t)e * npad * npad;
+  const S* He = H + hslot * npad * npad;
   for (int r = warp; r < naug; r += CWARPS) {
     const S* hr = He + (size_t)r * npad;
     S acc = Sc<T, C>::zero();
@@ -97,12 +99,13 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply_z3(const cd* __restr
                                                               const int* __restrict__ act_off,
                                                               const int* __restrict__ act_idx, int nloc, int npad,
                                                               int64_t nh, cd* __restrict__ Z,
-                                                              const int* __restrict__ cells) {
+                                                              const int* __restrict__ cells, int compact) {
   extern __shared__ unsigned char smem_raw[];
   double* Xr = reinterpret_cast<double*>(smem_raw);  // npad x NB3 each
   double* Xi = Xr + (size_t)npad * NB3;
   double* Xs = Xi + (size_t)npad * NB3;
   const int e = cells ? cells[blockIdx.x] : blockIdx.x;
+  const size_t hslot = compact ? (size_t)blockIdx.x : (size_t)e;   // compact layout: list order
   const int v0 = blockIdx.y * NB3;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int half = lane >> 4, hl = lane & 15;
@@ -120,7 +123,7 @@ __global__ void __launch_bounds__(CWARPS * 32) k_cell_apply_z3(const cd* __restr
     Xs[t] = x.x + x.y;
   }
   __syncthreads();
-  const cd* He = H + (size_t)e * npad * npad;
+  const cd* He = H + hslot * npad * npad;
   for (int r0 = 2 * warp; r0 < naug; r0 += 2 * CWARPS) {
     const int r = r0 + half;
     const bool rv = r < naug;
@@ -503,6 +506,8 @@ int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const vo
   const bool sf = sizeof(T) == 8 && sumfac_ready(c);
   const int* dense_cells = sf ? c->d_dense_cells : nullptr;
   const int ndense = sf ? c->n_dense : c->ncells;
+  const int compact = (sizeof(T) == 8 && K.compact) ? 1 : 0;
+  if (compact && !sf) { c->err = "compact FP64 storage needs the sum-factorized products"; return OEFE_ERR_STATE; }
   if (sf) OEFE_TRY(launch_cell_apply_sf(c, K, Xin, ldin, nv, C, Zbuf, c->stream));
   if (mma) {
     OEFE_TRY(launch_cell_mma(c, K, Xin, ldin, nv, C, Zbuf));
@@ -515,7 +520,8 @@ int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const vo
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply_z3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     OEFE_COUNTED k_cell_apply_z3<<<grid, CWARPS * 32, smem, c->stream>>>((const cd*)Hm, (const cd*)Xin, ldin, nv,
                                                                         c->d_cell_nodes, c->d_act_off, c->d_act_idx,
-                                                                        c->nloc, c->npad, c->nh, (cd*)Zbuf, dense_cells);
+                                                                        c->nloc, c->npad, c->nh, (cd*)Zbuf, dense_cells,
+                                                                        compact);
   } else {
     dim3 grid(ndense, (nv + NB - 1) / NB);
     const size_t smem = (size_t)c->npad * NB * sizeof(S);
@@ -523,7 +529,7 @@ int launch_step(oefe_ctx* c, const KData& K, int dtype, const void* Hm, const vo
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_cell_apply<T, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     OEFE_COUNTED k_cell_apply<T, C><<<grid, CWARPS * 32, smem, c->stream>>>((const S*)Hm, (const S*)Xin, ldin, nv, c->d_cell_nodes,
                                                                c->d_act_off, c->d_act_idx, c->nloc, c->npad, c->nh,
-                                                               (S*)Zbuf, dense_cells);
+                                                               (S*)Zbuf, dense_cells, compact);
   }
   if ((c->timing >> dtype) & 1) cudaEventRecord(timing_event(c), c->stream);
   const int64_t tot = c->nh * nv;
@@ -572,16 +578,25 @@ int check_apply_args(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dty
 
 }  // namespace
 
+// vectors per pass of the operator application: the per-cell products of one pass are held at once
+// (ncells x npad x chunk scalars), so wide blocks go through in column chunks
+constexpr int APPLY_CHUNK = 64;
+
 int apply_op2(oefe_ctx* c, int ik, const void* X, int ldx, void* Y, int ldy, int nv, int dtype, bool minv) {
   OEFE_TRY(check_apply_args(c, ik, X, nv, std::min(ldx, ldy), dtype));
   if (!Y) { c->err = "need Y"; return OEFE_ERR_ARG; }
   const size_t es = dtype_bytes(dtype);
-  const size_t zbytes = (((size_t)c->ncells * c->npad * nv * es + 255) / 256) * 256;
-  const size_t yobytes = (size_t)std::max(c->nO, 1) * nv * sizeof(cd);
+  const int nvc_max = std::min(nv, APPLY_CHUNK);
+  const size_t zbytes = (((size_t)c->ncells * c->npad * nvc_max * es + 255) / 256) * 256;
+  const size_t yobytes = (size_t)std::max(c->nO, 1) * nvc_max * sizeof(cd);
   OEFE_TRY(ensure_ws(c, zbytes + yobytes + 256));
   char* base = (char*)c->ws;
   Step st{minv ? 1 : 0, 1.0, 0.0, 0.0};
-  OEFE_TRY(dispatch_step(c, c->kd[ik], dtype, X, ldx, nv, st, nullptr, 0, nullptr, 0, Y, ldy, base, (cd*)(base + zbytes)));
+  for (int c0 = 0; c0 < nv; c0 += APPLY_CHUNK) {
+    const int nvc = std::min(APPLY_CHUNK, nv - c0);
+    OEFE_TRY(dispatch_step(c, c->kd[ik], dtype, (const char*)X + (size_t)c0 * es, ldx, nvc, st, nullptr, 0, nullptr, 0,
+                           (char*)Y + (size_t)c0 * es, ldy, base, (cd*)(base + zbytes)));
+  }
   OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return OEFE_OK;
 }
@@ -665,6 +680,13 @@ int cheb_filter(oefe_ctx* c, int ik, void* X, int nv, int ld, int dtype, int deg
   }
   const KData& K = c->kd[ik];
   if (mixed && !mma && !K.H32) { c->err = "filter: LAST_FP64 needs the FP32 cell matrices"; return OEFE_ERR_STATE; }
+  if (nv > APPLY_CHUNK) {   // the columns are independent: wide blocks in chunks (bounded scratch)
+    const size_t esx = dtype_bytes(dtype);
+    for (int c0 = 0; c0 < nv; c0 += APPLY_CHUNK)
+      OEFE_TRY(cheb_filter(c, ik, (char*)X + (size_t)c0 * esx, std::min(APPLY_CHUNK, nv - c0), ld, dtype, degree, a, b,
+                           a0, flags));
+    return OEFE_OK;
+  }
   const int64_t n = c->nh + c->nO;
   const int dt32 = dtype == OEFE_C128 ? OEFE_C64 : OEFE_F32;
   const int width = dtype_complex(dtype) ? 2 * nv : nv;  // reals per row
@@ -853,7 +875,9 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
   std::vector<size_t> zb(nk), yb(nk), lb(nk), fb(nk), cb(nk);
   for (int k = 0; k < nk; ++k) {
-    zb[k] = a256((size_t)c->ncells * c->npad * nv[k] * std::max(es, es_low));
+    // products of the low-precision degrees (all nv[k] vectors), or of one FP64-class pass (chunks)
+    zb[k] = a256((size_t)c->ncells * c->npad *
+                 std::max((size_t)nv[k] * es_low, (size_t)std::min(nv[k], APPLY_CHUNK) * es));
     yb[k] = a256((size_t)std::max(c->nO, 1) * nv[k] * sizeof(cd));
     lb[k] = a256((size_t)n * nv[k] * es_low);
     fb[k] = (mixed || defect) ? a256((size_t)n * nv[k] * es) : 0;
@@ -978,22 +1002,33 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     OEFE_CUDA_TRY(c, cudaEventCreateWithFlags(&c->bev_out, cudaEventDisableTiming));
   }
   const bool timed = (c->timing >> dt_low) & 1;
-  if (!c->bgraph || key != c->bkey) {
-    if (c->bgraph) {
-      cudaGraphExecDestroy(c->bgraph);
-      c->bgraph = nullptr;
+  // entries left without a graph by an earlier failed capture are dropped first
+  for (size_t i = 0; i < c->bgraphs.size();) {
+    if (c->bgraphs[i].exec) { ++i; continue; }
+    dev_free(c->bgraphs[i].params);
+    c->bgraphs.erase(c->bgraphs.begin() + i);
+  }
+  BatchGraph* G = nullptr;
+  for (auto& g : c->bgraphs)
+    if (g.key == key) G = &g;
+  if (!G) {
+    cudaStreamSynchronize(c->bstream);
+    if (c->bgraphs.size() >= 4) {   // the oldest goes
+      if (c->bgraphs.front().exec) cudaGraphExecDestroy(c->bgraphs.front().exec);
+      dev_free(c->bgraphs.front().params);
+      c->bgraphs.erase(c->bgraphs.begin());
     }
+    c->bgraphs.emplace_back();
+    G = &c->bgraphs.back();
+    G->key = key;
     const size_t pbytes = P.mk.size() * sizeof(MmaK) + P.nd.size() * sizeof(NodeK) + 64;
-    if (pbytes > c->bparams_bytes) {
-      cudaStreamSynchronize(c->bstream);
-      dev_free(c->bparams);
-      c->bparams = nullptr;
-      c->bparams_bytes = 0;
-      OEFE_TRY(dev_alloc(c, &c->bparams, pbytes));
-      c->bparams_bytes = pbytes;
+    int sa = dev_alloc(c, &G->params, pbytes);
+    if (sa != OEFE_OK) {
+      c->bgraphs.pop_back();
+      return sa;
     }
-    MmaK* d_mk = (MmaK*)c->bparams;
-    NodeK* d_nd = (NodeK*)((char*)c->bparams + ((P.mk.size() * sizeof(MmaK) + 15) / 16) * 16);
+    MmaK* d_mk = (MmaK*)G->params;
+    NodeK* d_nd = (NodeK*)((char*)G->params + ((P.mk.size() * sizeof(MmaK) + 15) / 16) * 16);
     OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_mk, P.mk.data(), P.mk.size() * sizeof(MmaK), cudaMemcpyHostToDevice, c->bstream));
     OEFE_CUDA_TRY(c, cudaMemcpyAsync(d_nd, P.nd.data(), P.nd.size() * sizeof(NodeK), cudaMemcpyHostToDevice, c->bstream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
@@ -1008,7 +1043,7 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     if (tma) OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, 0, cplx, parts, 1, c->bstream));
     else if (P.grid > 0) OEFE_TRY(launch_cell_mma_multi(c, d_mk, nk, 0, cplx, P.nb, 1, c->bstream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
-    cudaGraph_t graph;
+    cudaGraph_t graph = nullptr;
     OEFE_CUDA_TRY(c, cudaStreamBeginCapture(c->bstream, cudaStreamCaptureModeThreadLocal));
     const long long launches0 = oefe_launch_add(0);
     int st = OEFE_OK;
@@ -1024,14 +1059,25 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     if (st == OEFE_OK) st = batched_launch_degrees(c, P, cplx, d_mk, d_nd, timed);
     cudaError_t ce = cudaStreamEndCapture(c->bstream, &graph);
     // captured launches run at each replay, not here
-    c->bgraph_kernels = oefe_launch_add(0) - launches0;
-    oefe_launch_add(-c->bgraph_kernels);
-    if (st != OEFE_OK) return st;
-    if (ce != cudaSuccess) { c->err = std::string("graph capture: ") + cudaGetErrorString(ce); return OEFE_ERR_CUDA; }
-    ce = cudaGraphInstantiate(&c->bgraph, graph, 0);
-    cudaGraphDestroy(graph);
-    if (ce != cudaSuccess) { c->err = std::string("graph instantiate: ") + cudaGetErrorString(ce); return OEFE_ERR_CUDA; }
-    c->bkey = key;
+    G->kernels = oefe_launch_add(0) - launches0;
+    oefe_launch_add(-G->kernels);
+    if (st == OEFE_OK && ce != cudaSuccess) {
+      c->err = std::string("graph capture: ") + cudaGetErrorString(ce);
+      st = OEFE_ERR_CUDA;
+    }
+    if (st == OEFE_OK) {
+      ce = cudaGraphInstantiate(&G->exec, graph, 0);
+      if (ce != cudaSuccess) {
+        c->err = std::string("graph instantiate: ") + cudaGetErrorString(ce);
+        st = OEFE_ERR_CUDA;
+      }
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (st != OEFE_OK) {
+      dev_free(G->params);
+      c->bgraphs.pop_back();
+      return st;
+    }
   }
   if (defect) {
     // per k: the scaled polynomials at theta (host, FP64), R = A Q - Q Theta from one FP64-class
@@ -1061,8 +1107,10 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
       OEFE_CUDA_TRY(c, cudaMemcpyAsync(thv[k], th.data(), th.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
       // A Q into F1 (FP64-class: FP32 pairs in pair mode), then R (low precision) over it, row by row
       const Step st{1, 1.0, 0.0, 0.0};
-      OEFE_TRY(dispatch_step(c, c->kd[k], dtype, X[k], ld[k], nv[k], st, nullptr, 0, nullptr, 0, F1[k], nv[k], Zk[k],
-                             Yo[k], false));
+      for (int c0 = 0; c0 < nv[k]; c0 += APPLY_CHUNK)
+        OEFE_TRY(dispatch_step(c, c->kd[k], dtype, (const char*)X[k] + (size_t)c0 * es, ld[k],
+                               std::min(APPLY_CHUNK, nv[k] - c0), st, nullptr, 0, nullptr, 0, (char*)F1[k] + (size_t)c0 * es,
+                               nv[k], Zk[k], Yo[k], false));
       const int Rs = cplx ? 2 : 1, W = nv[k] * Rs;
       const int blocks = (int)std::min<int64_t>((n * W + 255) / 256, (int64_t)c->num_sms * 32);
       OEFE_COUNTED k_defect_residual<<<blocks, 256, 0, c->stream>>>((const double*)F1[k], W, (const double*)X[k],
@@ -1073,8 +1121,8 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
   // run: the private stream waits for the caller's stream and vice versa
   OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_in, c->stream));
   OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->bstream, c->bev_in, 0));
-  OEFE_CUDA_TRY(c, cudaGraphLaunch(c->bgraph, c->bstream));
-  oefe_launch_add(c->bgraph_kernels);
+  OEFE_CUDA_TRY(c, cudaGraphLaunch(G->exec, c->bstream));
+  oefe_launch_add(G->kernels);
   OEFE_CUDA_TRY(c, cudaEventRecord(c->bev_out, c->bstream));
   OEFE_CUDA_TRY(c, cudaStreamWaitEvent(c->stream, c->bev_out, 0));
   if (timed) {
@@ -1136,16 +1184,56 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
 
 }  // namespace
 
+namespace {
+
+// vectors per k-point of one batched pass: wider blocks run as several passes over column groups
+// (the columns of the filter are independent), which bounds the per-cell products and recurrence
+// buffers; each group keeps its own captured graph
+constexpr int FILTER_CHUNK = 128;
+
+int filter_batched_groups(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
+                          const double* a, const double* b, const double* a0, const double* theta, int flags) {
+  int vmax = 0;
+  bool ok = nk >= 1 && X && nv && ld;
+  for (int k = 0; ok && k < nk; ++k) {
+    ok = nv[k] >= 1;
+    vmax = std::max(vmax, ok ? nv[k] : 0);
+  }
+  const int Q = (vmax + FILTER_CHUNK - 1) / FILTER_CHUNK;
+  for (int k = 0; ok && k < nk; ++k) ok = nv[k] >= Q;
+  if (!ok || Q <= 1 || dtype < 0 || dtype > 3)   // one pass (the call checks its arguments itself)
+    return filter_batched_impl(c, nk, X, nv, ld, dtype, degree, a, b, a0, theta, flags);
+  const size_t es = dtype_bytes(dtype);
+  std::vector<size_t> toff(nk + 1, 0);
+  for (int k = 0; k < nk; ++k) toff[k + 1] = toff[k] + nv[k];
+  for (int q = 0; q < Q; ++q) {   // group q: columns [q nv / Q, (q + 1) nv / Q) of every k-point
+    std::vector<void*> Xq(nk);
+    std::vector<int> nvq(nk);
+    std::vector<double> thq;
+    for (int k = 0; k < nk; ++k) {
+      const int c0 = (int)((long long)q * nv[k] / Q), c1 = (int)((long long)(q + 1) * nv[k] / Q);
+      Xq[k] = (char*)X[k] + (size_t)c0 * es;
+      nvq[k] = c1 - c0;
+      if (theta) thq.insert(thq.end(), theta + toff[k] + c0, theta + toff[k] + c1);
+    }
+    OEFE_TRY(filter_batched_impl(c, nk, Xq.data(), nvq.data(), ld, dtype, degree, a, b, a0,
+                                 theta ? thq.data() : nullptr, flags));
+  }
+  return OEFE_OK;
+}
+
+}  // namespace
+
 int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, int degree,
                         const double* a, const double* b, const double* a0, int flags) {
-  return filter_batched_impl(c, nk, X, nv, ld, dtype, degree, a, b, a0, nullptr, flags);
+  return filter_batched_groups(c, nk, X, nv, ld, dtype, degree, a, b, a0, nullptr, flags);
 }
 
 int cheb_filter_batched_defect(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype,
                                int degree, const double* a, const double* b, const double* a0, const double* theta,
                                int flags) {
   if (!theta) { c->err = "filter_batched_defect: need theta"; return OEFE_ERR_ARG; }
-  return filter_batched_impl(c, nk, X, nv, ld, dtype, degree, a, b, a0, theta, flags);
+  return filter_batched_groups(c, nk, X, nv, ld, dtype, degree, a, b, a0, theta, flags);
 }
 
 int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms) {
@@ -1244,4 +1332,12 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
   c->use_tma = cands[bi].tma;
   c->tune_merge = cands[bi].merge;
   return OEFE_OK;
+}
+
+void release_batch_graphs(oefe_ctx* c) {
+  for (auto& g : c->bgraphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    dev_free(g.params);
+  }
+  c->bgraphs.clear();
 }

@@ -75,6 +75,12 @@ struct KData {
   double* H64 = nullptr;     // (ncells, npad, npad) scalars
   float* H32 = nullptr;      // (ncells, npad, npad) float or cf
   float* Hp = nullptr;       // (ncells, npad, npad) FP64 values as FP32 pairs (h, l per real part)
+  // H64 / Hp in the compact layout (OEFE_STORE_COMPACT): the cells with several quadrature leaves
+  // whole (npad x npad each, in the order of the dense-cell list), then per single-leaf cell (in the
+  // order of the sum-factorization list) its enrichment strip: the CO block (nloc x ne_max), then
+  // the enrichment rows (ne_max x npad); the CFE-CFE block of those cells is not stored (their
+  // FP64-class products apply it by sum factorization)
+  bool compact = false;
   void* Hbf = nullptr;       // bf16 planes (re parts[, im parts]), per cell [K tile][M tile][plane][128][64]
   int bf_parts = 0;          // bf16 parts per real plane in Hbf: 2 (hi, lo) or 3 (hi, mid, lo)
   void* E0 = nullptr;        // per cell: V-independent enrichment blocks (cd), CA then AA
@@ -84,6 +90,15 @@ struct KData {
   void* NO = nullptr;
   float* NOp = nullptr;
   bool built = false;
+};
+
+// one captured sequence of the batched filter's low-precision degrees: the key of everything baked
+// into it, the instantiated graph, the device parameter table its kernels read, its kernel count
+struct BatchGraph {
+  std::vector<double> key;
+  cudaGraphExec_t exec = nullptr;
+  void* params = nullptr;
+  long long kernels = 0;
 };
 
 struct oefe_ctx {
@@ -174,10 +189,7 @@ struct oefe_ctx {
   // batched multi-k filter: private stream, captured graph, autotuned launch shape
   cudaStream_t bstream = nullptr;
   cudaEvent_t bev_in = nullptr, bev_out = nullptr;
-  cudaGraphExec_t bgraph = nullptr;
-  std::vector<double> bkey;
-  void* bparams = nullptr;
-  size_t bparams_bytes = 0;
+  std::vector<BatchGraph> bgraphs;      // captured low-precision degrees, one per vector chunk (<= 4 kept)
   std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
   int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
   int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
@@ -190,10 +202,10 @@ struct oefe_ctx {
   int* d_sf_cells = nullptr;            // single-leaf cells
   int* d_dense_cells = nullptr;         // cells with several leaves (dense products)
   int* d_sf_index = nullptr;            // cell -> row of d_sf, or -1
+  int* d_dense_index = nullptr;         // cell -> position in d_dense_cells, or -1
   int n_sf = 0, n_dense = 0, sf_nbuf = 0;
   double* d_veff = nullptr;             // V_eff at the points of the last operator build
   int tune_merge = -1;                  // TMA kernel: merged real-part MMAs (1), separate (0), untuned (-1)
-  long long bgraph_kernels = 0;         // kernel launches captured in the batched graph (counted per replay)
   double tune_ms[5] = {0, 0, 0, 0, 0};
   void* d_tmaps = nullptr;              // one tensor map per k-point (split cell matrices)
   int n_tmaps = 0;
@@ -251,6 +263,7 @@ int cheb_filter_batched_defect(oefe_ctx* c, int nk, void* const* X, const int* n
                                int degree, const double* a, const double* b, const double* a0, const double* theta,
                                int flags);
 int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
+void release_batch_graphs(oefe_ctx* c);
 
 // tensor-core cell products (cell_mma.cu)
 struct MmaK {              // one k-point of a batched launch
@@ -295,6 +308,14 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
 int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype,
             const double* occ, double* rho);
 int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* gV);
+
+// compact layout of the FP64 / FP32-pair cell matrices: scalars of one enrichment strip, and of the
+// whole store (see KData::compact)
+inline size_t compact_strip(const oefe_ctx* c) { return (size_t)c->nloc * c->ne_max + (size_t)c->ne_max * c->npad; }
+inline size_t h64_entries(const oefe_ctx* c, bool compact) {
+  return compact ? (size_t)c->n_dense * c->npad * c->npad + (size_t)c->n_sf * compact_strip(c)
+                 : (size_t)c->ncells * c->npad * c->npad;
+}
 
 inline bool dtype_complex(int dt) { return dt == OEFE_C128 || dt == OEFE_C64; }
 inline bool dtype_fp64(int dt) { return dt == OEFE_F64 || dt == OEFE_C128; }

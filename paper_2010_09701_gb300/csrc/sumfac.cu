@@ -45,8 +45,10 @@ void lagrange_host(const std::vector<double>& xn, double x, double* L, double* D
 struct SfArgs {
   const double* sf;          // per listed cell: SF_STRIDE doubles
   const int* cells;          // listed cells
-  const void* H;             // FP64 cell matrices (npad x npad per cell)
+  const void* H;             // FP64 cell matrices (npad x npad per cell, or the compact layout)
   const float* Hp;           // the same as FP32 pairs (h, l per real part), for V = f2
+  int compact, ne_max;       // compact layout: the listed cell's strip starts at sf_base + slot * strip
+  long long sf_base, strip;
   const void* X;
   int ldx, nv;
   const int* cell_nodes;
@@ -60,6 +62,23 @@ struct SfArgs {
   double k[3];
   void* Z;
 };
+
+// Offset (in scalars) of entry (r, 0) of row r of a listed cell's matrix, and the first column that
+// row holds: the full layout keeps every column; a compact strip keeps the enrichment columns of
+// the node rows (column c at offset + c - nloc) and every column of the enrichment rows.
+__device__ __forceinline__ long long sf_row(const SfArgs& A, int e, int slot, int r, int* c_first) {
+  if (!A.compact) {
+    *c_first = 0;
+    return ((long long)e * A.npad + r) * A.npad;
+  }
+  const long long b = A.sf_base + (long long)slot * A.strip;
+  if (r < A.nloc) {
+    *c_first = A.nloc;
+    return b + (long long)r * A.ne_max;
+  }
+  *c_first = 0;
+  return b + (long long)A.nloc * A.ne_max + (long long)(r - A.nloc) * A.npad;
+}
 
 // one CTA per (block of NV vectors, listed cell): the vector blocks of a cell are adjacent in the
 // launch order, so the cell's enrichment blocks come from DRAM once and from L2 after that.
@@ -115,7 +134,9 @@ __global__ void __launch_bounds__(NT) k_cell_apply_sf(const SfArgs A) {
       const int v = t % NV, r = t / NV;
       if (v0 + v >= A.nv) continue;
       const int c0 = r < nloc ? nloc : 0;            // node rows: enrichment columns only
-      const S* hr = reinterpret_cast<const S*>(A.H) + ((size_t)e * npad + r) * npad;
+      int cf = 0;
+      const long long ro = sf_row(A, e, blockIdx.y, r, &cf);
+      const S* hr = reinterpret_cast<const S*>(A.H) + ro - cf;   // hr[c] for c >= cf
       double yr = 0, yi = 0;
       if (r < nloc) {
         yr = Ys[(size_t)r * J + v * R];
@@ -162,7 +183,9 @@ __global__ void __launch_bounds__(NT) k_cell_apply_sf(const SfArgs A) {
         y[j] = Acc{s.h, s.l};
       }
       if constexpr (CPLX) {
-        const float4* hr = reinterpret_cast<const float4*>(A.Hp) + ((size_t)e * npad + r) * npad;
+        int cf = 0;
+        const long long ro = sf_row(A, e, blockIdx.y, r, &cf);
+        const float4* hr = reinterpret_cast<const float4*>(A.Hp) + ro - cf;   // hr[c] for c >= cf
         float4 hn = ca < cb ? hr[ca] : make_float4(0.f, 0.f, 0.f, 0.f);
         for (int cidx = ca; cidx < cb; ++cidx) {
           const float4 h = hn;
@@ -179,7 +202,9 @@ __global__ void __launch_bounds__(NT) k_cell_apply_sf(const SfArgs A) {
           }
         }
       } else {
-        const float2* hr = reinterpret_cast<const float2*>(A.Hp) + ((size_t)e * npad + r) * npad;
+        int cf = 0;
+        const long long ro = sf_row(A, e, blockIdx.y, r, &cf);
+        const float2* hr = reinterpret_cast<const float2*>(A.Hp) + ro - cf;   // hr[c] for c >= cf
         float2 hn = ca < cb ? hr[ca] : make_float2(0.f, 0.f);
         for (int cidx = ca; cidx < cb; ++cidx) {
           const float2 h = hn;
@@ -234,8 +259,9 @@ int setup_sumfac(oefe_ctx* c) {
   dev_free(c->d_sf_cells);
   dev_free(c->d_dense_cells);
   dev_free(c->d_sf_index);
+  dev_free(c->d_dense_index);
   c->d_sf = nullptr;
-  c->d_sf_cells = c->d_dense_cells = c->d_sf_index = nullptr;
+  c->d_sf_cells = c->d_dense_cells = c->d_sf_index = c->d_dense_index = nullptr;
   c->n_sf = c->n_dense = 0;
   const int P = c->P;
   if (P > SF_MAXP || c->nloc != P * P * P) return OEFE_OK;
@@ -303,6 +329,10 @@ int setup_sumfac(oefe_ctx* c) {
     OEFE_TRY(dev_alloc(c, (void**)&c->d_dense_cells, den.size() * sizeof(int)));
     OEFE_CUDA_TRY(c, cudaMemcpy(c->d_dense_cells, den.data(), den.size() * sizeof(int), cudaMemcpyHostToDevice));
   }
+  std::vector<int> dindex(c->ncells, -1);
+  for (size_t i = 0; i < den.size(); ++i) dindex[den[i]] = (int)i;
+  OEFE_TRY(dev_alloc(c, (void**)&c->d_dense_index, dindex.size() * sizeof(int)));
+  OEFE_CUDA_TRY(c, cudaMemcpy(c->d_dense_index, dindex.data(), dindex.size() * sizeof(int), cudaMemcpyHostToDevice));
   c->n_sf = (int)sfc.size();
   c->n_dense = (int)den.size();
   return OEFE_OK;
@@ -318,6 +348,10 @@ int launch_cell_apply_sf(oefe_ctx* c, const KData& K, const void* X, int ldx, in
   A.cells = c->d_sf_cells;
   A.H = K.H64;
   A.Hp = K.Hp;
+  A.compact = K.compact ? 1 : 0;
+  A.ne_max = c->ne_max;
+  A.sf_base = (long long)c->n_dense * c->npad * c->npad;
+  A.strip = (long long)compact_strip(c);
   A.X = X;
   A.ldx = ldx;
   A.nv = nv;

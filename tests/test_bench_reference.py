@@ -38,10 +38,14 @@ def test_workload_description_follows_the_configuration():
     import bench
     import workloads as W
     full = bench.workload_text(W.CONFIGS["c3"]())
-    assert full == ("zincblende a=8.5 bohr 8 atoms (Z 14/6), graded 16^3 cells p=6, 40 enrichment functions, "
-                    "MP 2x2x1 (4 k), 64 vectors/k, Chebyshev degree 30")
+    assert full == ("c3_mixed_4k_8atom_16cube_p6: zincblende a=8.5 bohr, 8 atoms (Z 14/6), graded 16^3 cells p=6, "
+                    "40 enrichment functions, MP 2x2x1 (4 k, complex), 64 vectors/k, Chebyshev degree 30")
     small = bench.workload_text(W.CONFIGS["c3small"]())
-    assert "graded 8^3 cells" in small and "(2 k)" in small
+    assert "graded 8^3 cells" in small and "(2 k, complex)" in small
+    large = bench.workload_text(W.CONFIGS["c5"]())
+    assert large == ("c5_mixed_gamma_62atom_32cube_p6: supercell a=16.4 bohr, 62 atoms (Z 14/6), graded 32^3 cells "
+                     "p=6, 310 enrichment functions, Gamma point (real), 360 vectors/k, Chebyshev degree 50")
+    assert not bench.is_complex(W.CONFIGS["c5"]()) and bench.is_complex(W.CONFIGS["c3"]())
 
 
 def test_refined_cell_count_used_for_traffic_scaling():
@@ -52,3 +56,17 @@ def test_refined_cell_count_used_for_traffic_scaling():
     import workloads as W
     for name in ("c3", "c3small"):
         assert bench.nucleus_cells(W.CONFIGS[name]()) == 64
+
+
+def test_device_potential_matches_host_potential():
+    # the bench evaluates the synthetic V_eff with torch (large point sets); it must be the same input
+    # the oracle side computes with numpy, a nucleus position included
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import workloads as W
+    w = W.CONFIGS["c5mid"]()
+    pts = np.random.default_rng(0).uniform(0.0, w.a, (5000, 3))
+    pts[:3] = w.pos[:3]
+    a = W.veff(pts, w.a, w.pos, w.Z, w.sigma)
+    b = W.veff_device(pts, w.a, w.pos, w.Z, w.sigma, device="cpu").numpy()
+    assert np.max(np.abs(a - b)) <= 1e-14 * np.max(np.abs(a))

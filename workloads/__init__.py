@@ -153,7 +153,16 @@ def config_c3_mid():
     return w
 
 
-CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c3mid": config_c3_mid, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5}
+def config_c5_mid():
+    """The 62-atom divacancy supercell on a 16^3 graded mesh (about 0.9M nodes): a test case of the
+    Gamma-point path with 360 vectors at an eighth of the large supercell's mesh."""
+    w = config_c5()
+    w.name = "c5mid_gamma_62atom_16cube_p6"
+    w.ncell = 16
+    return w
+
+
+CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c3mid": config_c3_mid, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5, "c5mid": config_c5_mid}
 
 
 def graded_breakpoints(a, ncell, coords, ratio=1.5, tol=1e-3):
@@ -262,6 +271,25 @@ def veff(points, a, pos, Z, sigma=0.05):
         rr = np.where(small, 1.0, r)
         v = -z * erf(rr / s2) / rr
         v[small] = -z * math.sqrt(2.0 / math.pi) / sigma
+        V += v
+    return V
+
+
+def veff_device(points, a, pos, Z, sigma=0.05, device="cuda"):
+    """The same V_eff as ``veff`` evaluated with torch on a device (large point sets); returns a
+    float64 tensor on ``device``. Input generation only: the formula is that of ``veff``."""
+    import torch
+    pts = torch.as_tensor(np.asarray(points, float), dtype=torch.float64, device=device)
+    V = torch.zeros(pts.shape[0], dtype=torch.float64, device=device)
+    s2 = math.sqrt(2.0) * sigma
+    for R, z in zip(np.asarray(pos, float), Z):
+        d = pts - torch.as_tensor(R, dtype=torch.float64, device=device)
+        d = d - a * torch.round(d / a)
+        r = torch.sqrt(torch.sum(d * d, dim=1))
+        small = r < 1e-12
+        rr = torch.where(small, torch.ones_like(r), r)
+        v = -float(z) * torch.special.erf(rr / s2) / rr
+        v = torch.where(small, torch.full_like(v, -float(z) * math.sqrt(2.0 / math.pi) / sigma), v)
         V += v
     return V
 
