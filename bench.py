@@ -148,6 +148,11 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def progress(msg, t0=[time.time()]):
+    """One line of progress on stderr (the JSON result goes to stdout)."""
+    print("[bench %7.1f s] %s" % (time.time() - t0[0], msg), file=sys.stderr, flush=True)
+
+
 def barrier(world):
     """Barrier over the replicas (no-op for one process)."""
     if world > 1:
@@ -226,7 +231,9 @@ def run_ours(args, rank, world):
         store = (split if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
         if args.with_fp64 and pairs:
             store |= P.STORE_F64PAIR
+    progress("set up: %d dof, %d points; building (store %d)" % (n, len(qw), store))
     ctx.build_hamiltonian(V, store)
+    progress("operator built")
     if args.filter_only:
         ctx.release_workspace()   # the build's scratch is several times the filter's
     nvs = w.nv
@@ -361,8 +368,10 @@ def run_ours(args, rank, world):
             phase_ms["band_trace_grad"] = t[3].elapsed_time(t[4])
         return eigs, eb
 
+    progress("start state ready; %d warm-up steps" % args.warmup)
     for _ in range(args.warmup):
         step()
+    progress("timed steps")
     torch.cuda.synchronize()
     barrier(world)
     sampler = ClockSampler(dev)
@@ -381,6 +390,7 @@ def run_ours(args, rank, world):
     torch.cuda.synchronize()
     barrier(world)
     clocks = sampler.stop()
+    progress("timed: %.1f ms per step" % (ev0.elapsed_time(ev1) / args.steps))
     kms, klaunch = ctx.kernel_time()
     ctx.kernel_timing([])
     step_ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, "cuda")
@@ -457,7 +467,7 @@ def run_ours(args, rank, world):
         mix_ms_launch = fp64_ms_launch
         if pairs:
             ctx.set_f64_products(P.F64_PAIRS)
-            Xs_ = X0[0][:, :vslice]
+            Xs_ = X0[0][:, :vslice].contiguous()
             Yp = torch.empty_like(Xs_)
             ctx.apply_h(0, Xs_, Yp)   # warm
             torch.cuda.synchronize()
@@ -469,6 +479,7 @@ def run_ours(args, rank, world):
             ctx.kernel_timing([])
             mix_ms_launch = kp_ms / max(kp_n, 1)
             del Yp
+        progress("FP64 filter pass %.2f s" % fp64_s)
         fp64 = {"s_per_pass_k0": fp64_s,
                 "tflops": dense_filter_flops(naug, [nvs[0]], deg, cplx) / fp64_s / 1e12,
                 "speedup_mixed_vs_fp64": fp64_s / s_per_pass}
@@ -500,6 +511,7 @@ def run_ours(args, rank, world):
                 if len(hist) > 25 and hist[-1] > 0.5 * min(hist[:-20]):
                     break   # no longer falling
             acc_s = time.time() - t_acc
+            progress("accuracy run: %d passes, residual %.2e" % (len(hist), hist[-1]))
             ev_m = theta
             # one FP64 pass from the converged subspace: native FP64 filter, Cholesky-QR, Rayleigh-Ritz
             ctx.set_f64_products(P.F64_NATIVE)
