@@ -159,6 +159,122 @@ __global__ void __launch_bounds__(JT) k_jacobi(cd* Ag, cd* Vg, int n, int max_sw
 }
 
 
+// ---- the same cyclic Jacobi method for matrices too large for one CTA's shared memory, spread over
+// the whole GPU: per round of the circle ordering one kernel takes the rotation of every pair from the
+// current diagonal 2x2 blocks, a second applies them, each thread one 2x2 block of A (rows of one
+// pair, columns of another: the row and the column rotation of that block commute with every other
+// block's), a third rotates the columns of V. Same rotations and the same arithmetic per entry as
+// k_jacobi (rows first, then columns, the rotated pair's off-diagonal entries set to zero).
+struct JRot {
+  int a, b;     // the pair's indices (b >= n: the bye of an odd n)
+  int rot;      // 1 when the pair rotates
+  double c, s;
+  cd u;
+};
+
+__global__ void k_jg_params(const cd* __restrict__ A, int n, int r, JRot* __restrict__ R) {
+  const int m = n + (n & 1), np = m / 2;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= np) return;
+  const int a = k == 0 ? m - 1 : (k - 1 + r) % (m - 1);
+  const int b = (m - 1 - k - 1 + r) % (m - 1);
+  JRot o;
+  o.a = min(a, b);
+  o.b = max(a, b);
+  o.rot = 0;
+  o.c = 1.0;
+  o.s = 0.0;
+  o.u = mkc(1, 0);
+  if (o.b < n) {
+    const int p = o.a, q = o.b;
+    const cd bpq = A[(size_t)p * n + q];
+    const double beta = sqrt(cabs2(bpq));
+    if (beta >= 1e-300) {
+      o.u = (1.0 / beta) * bpq;
+      const double tau = (A[(size_t)q * n + q].x - A[(size_t)p * n + p].x) / (2.0 * beta);
+      const double tt = (tau >= 0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+      o.c = 1.0 / sqrt(1.0 + tt * tt);
+      o.s = tt * o.c;
+      o.rot = 1;
+    }
+  }
+  R[k] = o;
+}
+
+__global__ void k_jg_apply(cd* __restrict__ A, int n, const JRot* __restrict__ R) {
+  const int m = n + (n & 1), np = m / 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)np * np) return;
+  const int kr = (int)(t / np), kc = (int)(t % np);
+  const JRot gr = R[kr], gc = R[kc];
+  const int ri[2] = {gr.a, gr.b}, ci[2] = {gc.a, gc.b};
+  cd x[2][2];
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      x[i][j] = (ri[i] < n && ci[j] < n) ? A[(size_t)ri[i] * n + ci[j]] : mkc(0, 0);
+  if (gr.rot) {   // rows: (x_p, x_q) <- (c x_p + conj(g10) x_q, s x_p + conj(g11) x_q)
+    const cd ub = cconj(gr.u);
+    const cd g10 = -gr.s * ub, g11 = gr.c * ub;
+    for (int j = 0; j < 2; ++j) {
+      const cd xp = x[0][j], xq = x[1][j];
+      x[0][j] = gr.c * xp + cmulc(g10, xq);
+      x[1][j] = gr.s * xp + cmulc(g11, xq);
+    }
+  }
+  if (gc.rot) {   // columns: (y_p, y_q) <- (c y_p + y_q g10, s y_p + y_q g11)
+    const cd ub = cconj(gc.u);
+    const cd g10 = -gc.s * ub, g11 = gc.c * ub;
+    for (int i = 0; i < 2; ++i) {
+      const cd yp = x[i][0], yq = x[i][1];
+      x[i][0] = gc.c * yp + yq * g10;
+      x[i][1] = gc.s * yp + yq * g11;
+    }
+  }
+  if (kr == kc && gr.rot) {
+    x[0][1] = mkc(0, 0);
+    x[1][0] = mkc(0, 0);
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j)
+      if (ri[i] < n && ci[j] < n) A[(size_t)ri[i] * n + ci[j]] = x[i][j];
+}
+
+__global__ void k_jg_vrot(cd* __restrict__ V, int n, const JRot* __restrict__ R) {
+  const int m = n + (n & 1), np = m / 2;
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t >= (long long)np * n) return;
+  const int k = (int)(t / n), i = (int)(t % n);
+  const JRot g = R[k];
+  if (!g.rot) return;
+  const cd ub = cconj(g.u);
+  const cd g10 = -g.s * ub, g11 = g.c * ub;
+  const cd vp = V[(size_t)i * n + g.a], vq = V[(size_t)i * n + g.b];
+  V[(size_t)i * n + g.a] = g.c * vp + vq * g10;
+  V[(size_t)i * n + g.b] = g.s * vp + vq * g11;
+}
+
+// out[0] = sum of |A_ij|^2 off the diagonal, out[1] = over all entries (one CTA)
+__global__ void k_jg_norms(const cd* __restrict__ A, int n, double* out) {
+  __shared__ double red[1024];
+  double off = 0, all = 0;
+  for (long long t = threadIdx.x; t < (long long)n * n; t += blockDim.x) {
+    const double v = cabs2(A[t]);
+    all += v;
+    if (t / n != t % n) off += v;
+  }
+  off = block_sum(off, red);
+  all = block_sum(all, red);
+  if (threadIdx.x == 0) {
+    out[0] = off;
+    out[1] = all;
+  }
+}
+
+__global__ void k_eye(cd* V, int n) {
+  const long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (t < (long long)n * n) V[t] = (t / n == t % n) ? mkc(1, 0) : mkc(0, 0);
+}
+
 // ---- the sweeps in FP32-pair arithmetic (pair_dev.cuh), on the FP32 pipe: the same rotations
 // (parameters taken in FP64 from the current entries), the row and column updates in pairs, until
 // the off-diagonal part is below tol; k_jacobi then continues in FP64 from A and V until its own
@@ -396,7 +512,30 @@ int gpu_geneig(oefe_ctx* c, const S* H, const S* M, int n, double* eps_host, S* 
       }
       OEFE_COUNTED k_jacobi<true><<<1, JT, jsm, c->stream>>>(Hc, W, n, 40, 1e-15, d_int, init_v);
     } else {
-      OEFE_COUNTED k_jacobi<false><<<1, JT, 0, c->stream>>>(Hc, W, n, 40, 1e-15, d_int, true);
+      // the whole GPU per round: parameters, block updates, V; the stopping test of k_jacobi per sweep
+      JRot* rot = reinterpret_cast<JRot*>(Ws);   // Ws is free until the sort below (n^2 cd >= n/2 JRot)
+      double* nrm = d_eps;                      // two doubles, overwritten by the sort
+      const int m = n + (n & 1), np = m / 2;
+      const int gb = (int)(((long long)np * np + 255) / 256), gv = (int)(((long long)np * n + 255) / 256);
+      OEFE_COUNTED k_eye<<<g, b, 0, c->stream>>>(W, n);
+      double fro = -1.0;
+      for (int sweep = 0; sweep <= 40 && st == OEFE_OK; ++sweep) {
+        OEFE_COUNTED k_jg_norms<<<1, 1024, 0, c->stream>>>(Hc, n, nrm);
+        double h[2] = {0, 0};
+        if (cudaMemcpyAsync(h, nrm, sizeof(h), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+            cudaStreamSynchronize(c->stream) != cudaSuccess) {
+          c->err = "eigensolver: norm read-back failed";
+          st = OEFE_ERR_CUDA;
+          break;
+        }
+        if (fro < 0) fro = h[1];   // the Frobenius norm of the matrix the sweeps start from
+        if (sweep == 40 || h[0] <= 1e-30 * fro || h[0] == 0.0) break;
+        for (int r = 0; r < m - 1; ++r) {
+          OEFE_COUNTED k_jg_params<<<(np + 127) / 128, 128, 0, c->stream>>>(Hc, n, r, rot);
+          OEFE_COUNTED k_jg_apply<<<gb, 256, 0, c->stream>>>(Hc, n, rot);
+          OEFE_COUNTED k_jg_vrot<<<gv, 256, 0, c->stream>>>(W, n, rot);
+        }
+      }
     }
     OEFE_COUNTED k_sort_eig<<<(n + 127) / 128, 128, 0, c->stream>>>(Hc, W, n, d_eps, Ws);
     OEFE_COUNTED k_small_gemm<<<g, b, 0, c->stream>>>(Y, true, Ws, false, T, n);   // U = L^{-+} W

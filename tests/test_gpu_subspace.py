@@ -131,6 +131,29 @@ def test_rayleigh_ritz_tensor_core_64(k):
     assert np.allclose(np.abs(ph[sep]), 1.0, atol=1e-9 * f)
 
 
+@pytest.mark.parametrize("nv", [97, 150])
+@pytest.mark.parametrize("k", KS)
+def test_rayleigh_ritz_wide(k, nv):
+    # projected problems too large for one CTA's shared memory: the Jacobi rounds spread over the GPU
+    # (odd nv: one index sits out each round); FP64 and the pair products
+    prs, ctx, V, _ = paired(ks=[k], n=4, a=8.0)
+    pr = prs[0]
+    Q = solver.cholqr(W.random_vectors(pr.n, nv, complex_=pr.complex, seed=16), pr.apply_M)
+    eps_o, X_o = solver.rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
+    Qd = to_gpu(Q)
+    eps, res = ctx.rayleigh_ritz(0, Qd, resid=True)
+    assert np.max(np.abs(eps - eps_o)) < 1e-10 * max(1, np.max(np.abs(eps_o)))
+    res_o = solver.residual_norms(pr, X_o, eps_o)
+    assert np.allclose(res, res_o, rtol=1e-8, atol=1e-12 * max(1, np.max(np.abs(eps_o))))
+    X = Qd.cpu().numpy()
+    # M-orthonormal Ritz vectors spanning the oracle's: |<x_o, M x>| = 1 where the values are apart
+    assert np.allclose(X.conj().T @ pr.apply_M(X), np.eye(nv), atol=1e-11)
+    gaps = np.minimum(np.abs(np.diff(eps_o, prepend=-np.inf)), np.abs(np.diff(eps_o, append=np.inf)))
+    sep = gaps > 1e-6 * max(1, np.max(np.abs(eps_o)))
+    ph = np.sum(np.conj(X_o) * pr.apply_M(X), axis=0)
+    assert np.allclose(np.abs(ph[sep]), 1.0, atol=1e-9)
+
+
 @pytest.mark.parametrize("k", KS)
 def test_density_and_band_trace_grad(k):
     prs, ctx, V, Vd = paired(ks=[k])
