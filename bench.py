@@ -149,8 +149,16 @@ class ClockSampler:
 
 
 def progress(msg, t0=[time.time()]):
-    """One line of progress on stderr (the JSON result goes to stdout)."""
-    print("[bench %7.1f s] %s" % (time.time() - t0[0], msg), file=sys.stderr, flush=True)
+    """One line of progress on stderr (the JSON result goes to stdout), with the device memory in use."""
+    used = ""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            fr, tot = torch.cuda.mem_get_info()
+            used = " [%.1f of %.1f GB in use]" % ((tot - fr) / 1e9, tot / 1e9)
+    except Exception:
+        pass
+    print("[bench %7.1f s] %s%s" % (time.time() - t0[0], msg, used), file=sys.stderr, flush=True)
 
 
 def barrier(world):
