@@ -89,6 +89,14 @@ struct TmaArgs {
   int* err;
 };
 
+// M tiles (128 rows) and K tiles (64 columns) a cell's matrix occupies: the rest of the npad x npad
+// block is zero padding, which no role loads, multiplies or drains
+__device__ __forceinline__ void cell_tiles(const TmaArgs& A, int e, int mt, int ktn, int* mte, int* kte) {
+  const int naug = A.nloc + A.act_off[e + 1] - A.act_off[e];
+  *mte = min(mt, (naug + MT - 1) / MT);
+  *kte = min(ktn, (naug + KT - 1) / KT);
+}
+
 // tile t of the CTA's sequence -> (k, cell, vector block)
 __device__ __forceinline__ MmaK kparams(const TmaArgs& A, int k) { return A.ks ? A.ks[k] : A.k0; }
 
@@ -165,10 +173,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       for (int k = 0; k < A.nk; ++k)
         asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(&A.maps[k]) : "memory");
       for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x) {
-        int k, e, vb;
+        int k, e, vb, mte, kte;
         decode_tile(A, t, &k, &e, &vb);
-        for (int it = 0; it < mt * ktn * HALVES && !s_fail; ++it, ++ga) {
-          const int h = it % HALVES, kt = it / (HALVES * mt), m = (it / HALVES) % mt;
+        cell_tiles(A, e, mt, ktn, &mte, &kte);
+        for (int it = 0; it < mte * kte * HALVES && !s_fail; ++it, ++ga) {
+          const int h = it % HALVES, kt = it / (HALVES * mte), m = (it / HALVES) % mte;
           const int s = (int)(ga % SA);
           const long long u = ga / SA;
           if (u >= 1 && !mbar_wait(&a_empty[s], (uint32_t)((u - 1) & 1), &s_fail)) break;
@@ -185,13 +194,19 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
     // ---------------------------------------------------------------- MMA issuer
     if (lane == 0) {
       long long ga = 0, gb = 0;
-      int tl = 0;
+      int use[4] = {0, 0, 0, 0};   // tiles so far whose products went to M tile m
       bool ok = true;
-      for (long long t = blockIdx.x; t < A.ntiles && ok && !s_fail; t += gridDim.x, ++tl) {
-        for (int it = 0; it < mt * ktn && ok; ++it) {
-          const int kt = it / mt, m = it % mt;
+      for (long long t = blockIdx.x; t < A.ntiles && ok && !s_fail; t += gridDim.x) {
+        int k, e, vb, mte, kte;
+        decode_tile(A, t, &k, &e, &vb);
+        cell_tiles(A, e, mt, ktn, &mte, &kte);
+        for (int it = 0; it < mte * kte && ok; ++it) {
+          const int kt = it / mte, m = it % mte;
           const int sb = (int)((gb + kt) % SB);
-          if (kt == 0 && tl >= 1 && !mbar_wait(&acc_empty[m], (uint32_t)((tl - 1) & 1), &s_fail)) { ok = false; break; }
+          if (kt == 0 && use[m] >= 1 && !mbar_wait(&acc_empty[m], (uint32_t)((use[m] - 1) & 1), &s_fail)) {
+            ok = false;
+            break;
+          }
           if (m == 0 && !mbar_wait(&b_full[sb], (uint32_t)(((gb + kt) / SB) & 1), &s_fail)) { ok = false; break; }
           const uint32_t b_base = smem_u32(sB + sb * B_STAGE);
           const uint32_t dcol = taddr + m * MCOLS;
@@ -240,10 +255,11 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
             mma_commit(&a_empty[s]);
           }
           if (!ok) break;
-          if (m == mt - 1) mma_commit(&b_empty[sb]);
-          if (kt == ktn - 1) mma_commit(&acc_full[m]);
+          if (m == mte - 1) mma_commit(&b_empty[sb]);
+          if (kt == kte - 1) mma_commit(&acc_full[m]);
         }
-        gb += ktn;
+        for (int m = 0; m < mte; ++m) ++use[m];
+        gb += kte;
       }
       // every MMA issued has completed before the tensor memory is released
       if (ga > 0) {
@@ -263,6 +279,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       const int ne = A.act_off[e + 1] - A.act_off[e];
       const int naug = A.nloc + ne;
       const int v0 = vb * NBV;
+      int mte, kte;
+      cell_tiles(A, e, mt, ktn, &mte, &kte);
       // the tile's row map, once per tile, double-buffered; the barrier publishes it and takes
       // the exit decision on a failure uniformly over the gather threads
       int* rows = s_rows[tg & 1];
@@ -270,7 +288,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
         rows[r] = r < A.nloc ? A.cell_nodes[(size_t)e * A.nloc + r] : (int)(A.nh + A.act_idx[A.act_off[e] + r - A.nloc]);
       ++tg;
       if (gather_bar_or(s_fail != 0)) break;
-      for (int kt = 0; kt < ktn && !s_fail; ++kt, ++gb) {
+      for (int kt = 0; kt < kte && !s_fail; ++kt, ++gb) {
         const int sb = (int)(gb % SB);
         const long long u = gb / SB;
         if (u >= 1 && !mbar_wait(&b_empty[sb], (uint32_t)((u - 1) & 1), &s_fail)) break;
@@ -328,17 +346,18 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
   } else {
     // ---------------------------------------------------------------- epilogue
     const int q = warp & 3;
-    int tl = 0;
-    for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x, ++tl) {
-      int k, e, vb;
+    int use[4] = {0, 0, 0, 0};   // tiles so far whose M tile m was drained
+    for (long long t = blockIdx.x; t < A.ntiles && !s_fail; t += gridDim.x) {
+      int k, e, vb, mte, kte;
       decode_tile(A, t, &k, &e, &vb);
+      cell_tiles(A, e, mt, ktn, &mte, &kte);
       const MmaK P = kparams(A, k);
       const int ne = A.act_off[e + 1] - A.act_off[e];
       const int naug = A.nloc + ne;
       const int v0 = vb * NBV;
       bool ok = true;
-      for (int m = 0; m < mt; ++m) {
-        if (!mbar_wait(&acc_full[m], (uint32_t)(tl & 1), &s_fail)) { ok = false; break; }
+      for (int m = 0; m < mte; ++m) {
+        if (!mbar_wait(&acc_full[m], (uint32_t)(use[m] & 1), &s_fail)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = m * MT + 32 * q + lane;
         for (int h = 0; h < 2; ++h) {
@@ -400,6 +419,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         mbar_arrive(&acc_empty[m]);
+        ++use[m];
       }
       if (!ok) break;
     }
