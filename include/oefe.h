@@ -285,6 +285,31 @@ int oefe_density(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, co
  * respect to conj(X) is H^O X (oefe_apply_h). */
 int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* gV);
 
+/* oefe_band_trace -- e (host, one double) = tr(X^+ H^O X) = Re sum_v x_v^+ H^O x_v,
+ * the band-energy trace whose V-gradient oefe_band_trace_grad returns
+ * (Eq. HOEFEelelements). HX: device (n x ld, the dtype of X) receiving H^O X,
+ * or NULL (then a workspace of the context holds it). X: device F64/C128. */
+int oefe_band_trace(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* e, void* HX);
+
+/* oefe_band_trace_vjp -- the backward pass of E = tr(X^+ H^O(V) X) for an upstream
+ * gradient alpha (host double): gV (device, nq_total doubles, overwritten, may be
+ * NULL) = alpha w_q sum_v |u_v(x_q)|^2, gX (device n x ld like X, overwritten, may
+ * be NULL) = 2 alpha H^O X (the gradient with respect to X in torch's convention
+ * for real and complex tensors). At least one of gV, gX. The fields and the
+ * cell products are recomputed from X (nothing of the forward pass is kept). */
+int oefe_band_trace_vjp(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double alpha, double* gV,
+                        void* gX);
+
+/* oefe_apply_h_vjp -- the backward pass of Y = H^O(V) X for a cotangent Gy of Y
+ * (device, n x ld like X): H^O is affine in V through the (|k|^2/2 + V) N_m^* N_n
+ * term of Eq. HOEFEelelements and Hermitian, so
+ *   gV_q = w_q Re sum_v conj(u_Gy,v(x_q)) u_X,v(x_q)   (device, nq_total, overwritten, may be NULL),
+ *   gX   = H^O Gy                                      (device, n x ld, overwritten, may be NULL),
+ * u the fields of the columns at the quadrature points (Eq. UOEFE), both fields
+ * evaluated in one pass over the points. At least one of gV, gX. */
+int oefe_apply_h_vjp(oefe_ctx_t ctx, int ik, const void* X, const void* Gy, double* gV, void* gX, int nv, int ld,
+                     int dtype);
+
 /* oefe_occupations -- Fermi-Dirac occupancies f = 1/(1+exp((eps-mu)/kT))
  * (Eq. fd) with the Fermi level mu fixed by 2 sum_k w_k sum_a f = N_e
  * (Eq. ne, bisection to |dN| < 1e-12), kT = 3.166811563e-6 * T Ha. Host-only.

@@ -1,12 +1,16 @@
 """Adjoint of the cell-level H.X application as torch.autograd Functions.
 
 H^O(V) is affine in the quadrature-point potential V through the
-(|k|^2/2 + V) N_m^* N_n term of Eq. HOEFEelelements, so for the band trace
-E = tr(X^+ H^O(V) X):
+(|k|^2/2 + V) N_m^* N_n term of Eq. HOEFEelelements and Hermitian, so for the
+band trace E = tr(X^+ H^O(V) X):
     dE/dV_q = w_q sum_v |u_v(x_q)|^2   (u the field of column v, Eq. UOEFE),
-    dE/dX   = 2 H^O X                  (torch's convention for real and complex X).
-Both are evaluated by the CUDA library; the backward pass recomputes the cell
-gathers and the field interpolation instead of storing them.
+    dE/dX   = 2 H^O X                  (torch's convention for real and complex X);
+and for Y = H^O(V) X with a cotangent G:
+    d/dV_q  = w_q Re sum_v conj(u_G,v(x_q)) u_X,v(x_q),   d/dX = H^O G.
+Every value here is computed by the CUDA library (oefe_band_trace,
+oefe_band_trace_vjp, oefe_apply_h_vjp); this module only allocates the output
+tensors and passes pointers. The backward passes recompute the cell gathers
+and the field interpolation instead of storing them.
 """
 import torch
 
@@ -22,34 +26,25 @@ class BandTrace(torch.autograd.Function):
     @staticmethod
     def forward(fctx, V, X, octx, ik):
         _ensure_built(octx, V)
-        HX = torch.empty_like(X)
-        octx.apply_h(ik, X.detach(), HX)
-        E = torch.sum(X.detach().conj() * HX).real
+        E = octx.band_trace(ik, X.detach())
         fctx.save_for_backward(V, X)
         fctx.octx, fctx.ik = octx, ik
-        return E
+        return torch.tensor(E, dtype=torch.float64, device=X.device)
 
     @staticmethod
     def backward(fctx, g):
         V, X = fctx.saved_tensors
         octx, ik = fctx.octx, fctx.ik
         _ensure_built(octx, V)
-        gV = gX = None
-        if fctx.needs_input_grad[0]:
-            gV = torch.empty_like(V)
-            octx.band_trace_grad(ik, X.detach(), gV)
-            gV = gV * g
-        if fctx.needs_input_grad[1]:
-            HX = torch.empty_like(X)
-            octx.apply_h(ik, X.detach(), HX)
-            gX = 2.0 * g * HX
+        gV = torch.empty_like(V) if fctx.needs_input_grad[0] else None
+        gX = torch.empty_like(X) if fctx.needs_input_grad[1] else None
+        if gV is not None or gX is not None:
+            octx.band_trace_vjp(ik, X.detach(), float(g), gV, gX)
         return gV, gX, None, None
 
 
 class ApplyH(torch.autograd.Function):
-    """Y = H^O(V) X. Vector-Jacobian products: grad_X = H^O G (H^O Hermitian);
-    grad_V_q = w_q Re sum_v conj(u_G,v) u_X,v, obtained from the band-trace
-    gradient by polarization: (f(X + G) - f(X - G)) / 4 with f(Z) = w_q sum |u_Z|^2."""
+    """Y = H^O(V) X with its vector-Jacobian products from oefe_apply_h_vjp."""
 
     @staticmethod
     def forward(fctx, V, X, octx, ik):
@@ -66,16 +61,10 @@ class ApplyH(torch.autograd.Function):
         octx, ik = fctx.octx, fctx.ik
         _ensure_built(octx, V)
         G = G.contiguous()
-        gV = gX = None
-        if fctx.needs_input_grad[0]:
-            fp = torch.empty_like(V)
-            fm = torch.empty_like(V)
-            octx.band_trace_grad(ik, (X.detach() + G).contiguous(), fp)
-            octx.band_trace_grad(ik, (X.detach() - G).contiguous(), fm)
-            gV = 0.25 * (fp - fm)
-        if fctx.needs_input_grad[1]:
-            gX = torch.empty_like(X)
-            octx.apply_h(ik, G, gX)
+        gV = torch.empty_like(V) if fctx.needs_input_grad[0] else None
+        gX = torch.empty_like(X) if fctx.needs_input_grad[1] else None
+        if gV is not None or gX is not None:
+            octx.apply_h_vjp(ik, X.detach(), G, gV, gX)
         return gV, gX, None, None
 
 

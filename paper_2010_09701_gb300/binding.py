@@ -55,6 +55,9 @@ SIGNATURES = [
     ("oefe_rayleigh_ritz", _I, [_P, _I, _P, _I, _I, _I, _DP, _DP]),
     ("oefe_density", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP, _P]),
     ("oefe_band_trace_grad", _I, [_P, _I, _P, _I, _I, _I, _P]),
+    ("oefe_band_trace", _I, [_P, _I, _P, _I, _I, _I, _DP, _P]),
+    ("oefe_band_trace_vjp", _I, [_P, _I, _P, _I, _I, _I, _D, _P, _P]),
+    ("oefe_apply_h_vjp", _I, [_P, _I, _P, _P, _P, _P, _I, _I, _I]),
     ("oefe_upper_bound", _I, [_P, _I, _P, _I, _I, _DP]),
     ("oefe_occupations", _I, [_I, _IP, _DP, _DP, _D, _D, _DP, _DP, _DP]),
     ("oefe_kernel_timing", _I, [_P, _I]),
@@ -366,6 +369,43 @@ class Context:
         px, nv, ld, dt = _block(X)
         self._check(self.lib.oefe_band_trace_grad(self.h, int(ik), px, nv, ld, dt, ctypes.c_void_p(gV.data_ptr())))
         return gV
+
+    @staticmethod
+    def _same(X, Y, what):
+        if Y.shape != X.shape or Y.stride() != X.stride() or Y.dtype != X.dtype or not Y.is_cuda:
+            raise ValueError("%s must have the shape, strides and dtype of X" % what)
+
+    def band_trace(self, ik, X, HX=None):
+        """tr(X^+ H X) (a float); H X into HX when given."""
+        px, nv, ld, dt = _block(X)
+        if HX is not None:
+            self._same(X, HX, "HX")
+        e = ctypes.c_double()
+        self._check(self.lib.oefe_band_trace(self.h, int(ik), px, nv, ld, dt, ctypes.byref(e),
+                                             ctypes.c_void_p(HX.data_ptr()) if HX is not None else None))
+        return e.value
+
+    def band_trace_vjp(self, ik, X, alpha, gV=None, gX=None):
+        """gV = alpha w_q sum |u|^2 and gX = 2 alpha H X, into the given tensors (either may be None)."""
+        px, nv, ld, dt = _block(X)
+        if gX is not None:
+            self._same(X, gX, "gX")
+        self._check(self.lib.oefe_band_trace_vjp(self.h, int(ik), px, nv, ld, dt, float(alpha),
+                                                 ctypes.c_void_p(gV.data_ptr()) if gV is not None else None,
+                                                 ctypes.c_void_p(gX.data_ptr()) if gX is not None else None))
+        return gV, gX
+
+    def apply_h_vjp(self, ik, X, Gy, gV=None, gX=None):
+        """gV = w_q Re sum conj(u_Gy) u_X and gX = H Gy, into the given tensors (either may be None)."""
+        px, nv, ld, dt = _block(X)
+        self._same(X, Gy, "Gy")
+        if gX is not None:
+            self._same(X, gX, "gX")
+        self._check(self.lib.oefe_apply_h_vjp(self.h, int(ik), px, ctypes.c_void_p(Gy.data_ptr()),
+                                              ctypes.c_void_p(gV.data_ptr()) if gV is not None else None,
+                                              ctypes.c_void_p(gX.data_ptr()) if gX is not None else None,
+                                              nv, ld, dt))
+        return gV, gX
 
     def product_flops(self, ik, nv):
         """FP64 operations of one FP64 operator application's cell products for nv vectors."""

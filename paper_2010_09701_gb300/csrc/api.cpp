@@ -294,6 +294,23 @@ int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, 
   return band_trace_grad(ctx, ik, X, nv, ld, dtype, gV);
 }
 
+int oefe_band_trace(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* e, void* HX) {
+  CTX_CHECK(ctx);
+  return band_trace(ctx, ik, X, nv, ld, dtype, e, HX);
+}
+
+int oefe_band_trace_vjp(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double alpha, double* gV,
+                        void* gX) {
+  CTX_CHECK(ctx);
+  return band_trace_vjp(ctx, ik, X, nv, ld, dtype, alpha, gV, gX);
+}
+
+int oefe_apply_h_vjp(oefe_ctx_t ctx, int ik, const void* X, const void* Gy, double* gV, void* gX, int nv, int ld,
+                     int dtype) {
+  CTX_CHECK(ctx);
+  return apply_h_vjp(ctx, ik, X, Gy, gV, gX, nv, ld, dtype);
+}
+
 int oefe_upper_bound(oefe_ctx_t ctx, int ik, const void* v0, int steps, int flags, double* b) {
   CTX_CHECK(ctx);
   return upper_bound(ctx, ik, v0, steps, flags, b);

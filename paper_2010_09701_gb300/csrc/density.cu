@@ -4,7 +4,8 @@
 //   N^O_j(x_q) = N^A_j(x_q) - sum_a N^C_a(x_q) Gamma_aj   (the orthogonalized enrichment),
 // then
 //   density:          rho_q += sum_v occ_v |u_v(x_q)|^2
-//   band-trace grad:  g_q    = w_q sum_v |u_v(x_q)|^2  (adjoint of H.X w.r.t. V_q).
+//   band-trace grad:  g_q    = w_q sum_v |u_v(x_q)|^2  (adjoint of H.X w.r.t. V_q),
+//   VJP of Y = H X:   g_q    = w_q Re sum_v conj(u_G,v(x_q)) u_X,v(x_q) (cotangent G of Y).
 // N^O depends on k only: it is tabulated once per k-point (k_orth_enrichment) and kept; the
 // fields then take the CFE part by sum factorization per tensor-product leaf and the enrichment
 // part as a dense product with the table (k_fields), in FP64 or FP32-pair arithmetic.
@@ -158,6 +159,11 @@ struct FieldArgs {
   const double* qw;
   double* out;        // nq
   bool accumulate;    // density: out += ; gradient: out =
+  double scale;       // gradient: out = scale w_q (...)
+  // cross mode (X2 != null): a pass of RNB takes RNB/2 columns of X and the same columns of X2; the
+  // point's sum is Re sum_v conj(u_X2,v) u_X,v instead of sum_v |u_X,v|^2
+  const void* X2;
+  int ld2;
 };
 
 // u_v(x_q) for RNB vectors per pass (4: one CTA per SM; 2: half the shared memory, two CTAs per SM): CFE part by sum factorization (x, y, z stages over the leaf's
@@ -196,19 +202,37 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
     }
     for (int q = threadIdx.x; q < 2 * n3; q += FT) rho[q] = v_from<V>(0.0);
     const size_t blk = (size_t)L.q0 * A.ne_max;
-    for (int v0 = 0; v0 < A.nv; v0 += RNB) {
+    const bool cross = A.X2 != nullptr;
+    constexpr int HV = RNB / 2, HJ = HV * R;
+    // slot u of a pass: column v0 + u of X, or (cross mode) column v0 / 2 + u % HV of X (u < HV) or
+    // of X2 (u >= HV)
+    auto column = [&](int v0, int u, const void** M, int* ld) -> int {
+      if (!cross) {
+        *M = A.X;
+        *ld = A.ld;
+        return v0 + u;
+      }
+      *M = u < HV ? A.X : A.X2;
+      *ld = u < HV ? A.ld : A.ld2;
+      return v0 / 2 + u % HV;
+    };
+    const int vend = cross ? 2 * A.nv : A.nv;
+    for (int v0 = 0; v0 < vend; v0 += RNB) {
       __syncthreads();
       for (int t = threadIdx.x; t < ne * RNB; t += FT) {
         const int j = t / RNB, u = t % RNB;
         double xr = 0.0, xi = 0.0;
-        if (v0 + u < A.nv) {
+        const void* M;
+        int ldm;
+        const int v = column(v0, u, &M, &ldm);
+        if (v < A.nv) {
           const int64_t row = A.nh + A.act_idx[A.act_off[e] + j];
           if (CPLX) {
-            const cd x = reinterpret_cast<const cd*>(A.X)[row * A.ld + v0 + u];
+            const cd x = reinterpret_cast<const cd*>(M)[row * ldm + v];
             xr = x.x;
             xi = x.y;
           } else {
-            xr = reinterpret_cast<const double*>(A.X)[row * A.ld + v0 + u];
+            xr = reinterpret_cast<const double*>(M)[row * ldm + v];
           }
         }
         Xo[(size_t)j * J + u * R] = v_from<V>(xr);
@@ -217,14 +241,17 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
       for (int t = threadIdx.x; t < nloc * RNB; t += FT) {
         const int a = t / RNB, u = t % RNB;
         double xr = 0.0, xi = 0.0;
-        if (v0 + u < A.nv) {
+        const void* M;
+        int ldm;
+        const int v = column(v0, u, &M, &ldm);
+        if (v < A.nv) {
           const int64_t row = A.cell_nodes[(size_t)e * nloc + a];
           if (CPLX) {
-            const cd x = reinterpret_cast<const cd*>(A.X)[row * A.ld + v0 + u];
+            const cd x = reinterpret_cast<const cd*>(M)[row * ldm + v];
             xr = x.x;
             xi = x.y;
           } else {
-            xr = reinterpret_cast<const double*>(A.X)[row * A.ld + v0 + u];
+            xr = reinterpret_cast<const double*>(M)[row * ldm + v];
           }
         }
         Xt[(size_t)a * J + u * R] = v_from<V>(xr);
@@ -253,7 +280,6 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
       }
       __syncthreads();
       // enrichment part and |u|^2: items (point, half of the RNB vectors)
-      constexpr int HV = RNB / 2, HJ = HV * R;
       for (int tq = threadIdx.x; tq < 2 * n3; tq += FT) {
         const int q = tq >> 1, h = tq & 1;
         Acc y[HJ];
@@ -298,19 +324,44 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
           }
         }
         V s = rho[h * n3 + q];
+        if (cross) {
+          // the partner item (same point, other half: adjacent threads of one warp, both active)
+          // holds the X2 fields of the same columns; the X half takes Re conj(u_X2) u_X
+          const unsigned mask = __activemask();
 #pragma unroll
-        for (int u = 0; u < HV; ++u) {
-          const int v = v0 + h * HV + u;
-          if (v >= A.nv) continue;
-          Acc m = v_zero<V>();
-          const V yr = v_fin(y[u * R]);
-          v_mac(m, yr, yr);
-          if constexpr (CPLX) {
-            const V yi = v_fin(y[u * R + 1]);
-            v_mac(m, yi, yi);
+          for (int j = 0; j < HJ; ++j) {
+            const V mine = v_fin(y[j]);
+            V other;
+            if constexpr (std::is_same<V, double>::value) {
+              other = __shfl_xor_sync(mask, mine, 1);
+            } else {
+              other.h = __shfl_xor_sync(mask, mine.h, 1);
+              other.l = __shfl_xor_sync(mask, mine.l, 1);
+            }
+            if (h == 0) {
+              const int u = j / R;
+              if (v0 / 2 + u < A.nv) {
+                Acc m = v_zero<V>();
+                v_mac(m, mine, other);   // Re: x_r g_r + x_i g_i over the two components
+                s = v_add(s, v_fin(m));
+              }
+            }
           }
-          const V w = v_from<V>(A.occ ? A.occ[v] : 1.0);
-          s = v_add(s, v_mul(w, v_fin(m)));
+        } else {
+#pragma unroll
+          for (int u = 0; u < HV; ++u) {
+            const int v = v0 + h * HV + u;
+            if (v >= A.nv) continue;
+            Acc m = v_zero<V>();
+            const V yr = v_fin(y[u * R]);
+            v_mac(m, yr, yr);
+            if constexpr (CPLX) {
+              const V yi = v_fin(y[u * R + 1]);
+              v_mac(m, yi, yi);
+            }
+            const V w = v_from<V>(A.occ ? A.occ[v] : 1.0);
+            s = v_add(s, v_mul(w, v_fin(m)));
+          }
         }
         rho[h * n3 + q] = s;
       }
@@ -320,7 +371,7 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
       const int64_t qg = L.q0 + q;
       const double r = v_to(v_add(rho[q], rho[n3 + q]));
       if (A.accumulate) A.out[qg] += r;
-      else A.out[qg] = A.qw[qg] * r;
+      else A.out[qg] = A.scale * A.qw[qg] * r;
     }
   }
 }
@@ -380,7 +431,7 @@ int ensure_orth_enrichment(oefe_ctx* c, KData& K) {
 namespace {
 
 int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, const double* occ, double* out,
-               bool accumulate) {
+               bool accumulate, double scale = 1.0, const void* X2 = nullptr, int ld2 = 0) {
   OEFE_TRY(ensure_orth_enrichment(c, K));
   const bool pairs = c->f64_products == OEFE_F64_PAIRS;
   const bool cplx = dtype == OEFE_C128;
@@ -406,6 +457,9 @@ int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, 
   A.qw = c->d_qw;
   A.out = out;
   A.accumulate = accumulate;
+  A.scale = scale;
+  A.X2 = X2;
+  A.ld2 = ld2;
   const int grid = std::max(1, std::min((int)c->leaves.size(), c->num_sms));
   auto go = [&](auto kern, size_t smem) -> int {
     if (smem > 227 * 1024) { c->err = "fields: quadrature too large for the interpolation tiles"; return OEFE_ERR_ARG; }
@@ -493,6 +547,18 @@ int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtyp
   OEFE_TRY(check_fields(c, ik, X, nv, ld, dtype));
   if (!gV) { c->err = "need gV"; return OEFE_ERR_ARG; }
   OEFE_TRY(run_fields(c, c->kd[ik], X, nv, ld, dtype, nullptr, gV, false));
+  OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return OEFE_OK;
+}
+
+// d/dV_q of Re sum conj(G) (H X) = w_q Re sum_v conj(u_G,v(x_q)) u_X,v(x_q), one fields pass over the
+// columns of both blocks; scaled by `scale` (the band-trace gradient: G = X, any scale)
+int fields_cross(oefe_ctx* c, int ik, const void* X, const void* G, int nv, int ld, int dtype, double scale,
+                 double* gV) {
+  OEFE_TRY(check_fields(c, ik, X, nv, ld, dtype));
+  if (!gV) { c->err = "need gV"; return OEFE_ERR_ARG; }
+  if (G) OEFE_TRY(run_fields(c, c->kd[ik], X, nv, ld, dtype, nullptr, gV, false, scale, G, ld));
+  else OEFE_TRY(run_fields(c, c->kd[ik], X, nv, ld, dtype, nullptr, gV, false, scale));
   OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return OEFE_OK;
 }

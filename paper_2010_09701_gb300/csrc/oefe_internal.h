@@ -308,6 +308,10 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
 int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype,
             const double* occ, double* rho);
 int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* gV);
+// adjoint.cu
+int band_trace(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* e, void* HX);
+int band_trace_vjp(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double alpha, double* gV, void* gX);
+int apply_h_vjp(oefe_ctx* c, int ik, const void* X, const void* Gy, double* gV, void* gX, int nv, int ld, int dtype);
 
 // compact layout of the FP64 / FP32-pair cell matrices: scalars of one enrichment strip, and of the
 // whole store (see KData::compact)
