@@ -480,6 +480,7 @@ int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int n
     bool done = false;
     OEFE_TRY(gram_ozaki<S>(c, X, ldx, W, ldw, n, nv, out, &done));
     if (done) return OEFE_OK;
+    return gram_ozaki_wide<S>(c, X, ldx, W, ldw, n, nv, out);   // wider blocks: digits cut in the kernel
   }
   const int tiles = (nv + GT - 1) / GT;
   const int64_t rpc = (n + nchunk - 1) / nchunk;
@@ -499,6 +500,7 @@ int rotate(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm)
     bool done = false;
     OEFE_TRY(rotate_ozaki<S>(c, X, ldx, n, nv, C, herm, &done));
     if (done) return OEFE_OK;
+    return rotate_ozaki_wide<S>(c, X, ldx, n, nv, C, herm);   // wider blocks: digits cut in the kernel
   }
   if (c->f64_products == OEFE_F64_PAIRS) {
     // pairs: C (transposed, as pairs) and the staged rows in shared memory; rows per CTA such that

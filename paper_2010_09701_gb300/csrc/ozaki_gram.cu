@@ -34,13 +34,13 @@
 #include "oefe_internal.h"
 #include "pair_dev.cuh"
 #include "tcgen05_dev.cuh"
+#include "ozaki_dev.cuh"
 
 namespace {
 
 constexpr int OZ_T = 256;           // threads per CTA of the MMA kernel: two warps per lane quadrant
 constexpr int OZ_C = 32;            // accumulator columns of one thread's running sums
 constexpr int OZ_K = 64;            // rows per pass (one 128-byte swizzle row of bf16)
-constexpr int OZ_S = 7;             // digits per value
 constexpr int OZ_N = 64;            // columns of B per CTA
 constexpr int PL = 128 * 128;       // one digit plane: 128 operand rows x 64 bf16
 constexpr int PASS_BYTES = OZ_S * PL;
@@ -60,22 +60,6 @@ __device__ __forceinline__ double ld_part(const void* M, int ld, long long r, in
     return part ? v.y : v.x;
   }
   return reinterpret_cast<const double*>(M)[r * ld + c];
-}
-
-// Y = trunc(x 2^(49-E)) from the bits of x by integer operations only (|x| < 2^E; subnormals
-// count as zero), then the digits: c0 signed, the rest non-negative (two's complement split)
-__device__ __forceinline__ void digits7(unsigned long long b, int E, float c[OZ_S]) {
-  const int ex = (int)((b >> 52) & 0x7FF);
-  const int sh = 1026 - ex + E;                         // >= 4 since |x| < 2^E
-  const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
-  const unsigned long long ya = (ex == 0 || sh >= 64) ? 0ull : (mant >> sh);
-  const long long Y = (b >> 63) ? -(long long)ya : (long long)ya;
-  // small integers to float without a conversion instruction: 2^23 + m as bits, minus 2^23
-  const int top = (int)(Y >> 42) + 128;                 // c0 + 128 in [0, 255]
-  c[0] = __fsub_rn(__int_as_float(0x4B000000 | top), 8388736.0f);   // 2^23 + 128
-#pragma unroll
-  for (int s = 1; s < OZ_S; ++s)
-    c[s] = __fsub_rn(__int_as_float(0x4B000000 | (int)((Y >> (42 - 7 * s)) & 127)), 8388608.0f);
 }
 
 struct DigArgs {
@@ -148,12 +132,6 @@ __global__ void __launch_bounds__(DG_T) k_oz_digits(const DigArgs D) {
     for (int s = 0; s < OZ_S; ++s)
       *reinterpret_cast<__nv_bfloat162*>(base + (size_t)s * PL + swz(r, 2 * kp)) = __floats2bfloat162_rn(c0[s], c1[s]);
   }
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void* src, uint32_t bytes, uint64_t* bar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(smem_u32(bar))
-               : "memory");
 }
 
 struct OzArgs {
@@ -415,19 +393,6 @@ __global__ void k_oz_rot_bdigits(const S* C, int nv, bool herm, unsigned char* p
       for (int s = 0; s < OZ_S; ++s)
         *reinterpret_cast<__nv_bfloat162*>(base + (size_t)s * BH + swz(n, 2 * kp)) = __floats2bfloat162_rn(c0[s], c1[s]);
     }
-}
-
-// x 2^sc as a double (exact): the float's sign and fraction with the exponent rebased, by integer
-// operations (IEEE 754 binary32 and binary64 layouts); zero, subnormal, infinite or NaN x and a
-// result outside the normal range go through ldexp
-__device__ __forceinline__ double f_scaled(float x, int sc) {
-  const unsigned int b = __float_as_uint(x);
-  const int ef = (int)((b >> 23) & 0xFFu);
-  const int e = ef - 127 + 1023 + sc;
-  if (ef == 0 || ef == 255 || e < 1 || e > 2046) return ldexp((double)x, sc);
-  const unsigned long long bits = ((unsigned long long)(b >> 31) << 63) | ((unsigned long long)e << 52) |
-                                  ((unsigned long long)(b & 0x7FFFFFu) << 29);
-  return __longlong_as_double((long long)bits);
 }
 
 struct RotArgs {
