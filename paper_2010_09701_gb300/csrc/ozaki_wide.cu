@@ -194,18 +194,22 @@ __global__ void __launch_bounds__(WT, 1) k_gram_wide(const WGramArgs A) {
       const int ra = isA ? I * 128 + r : J * WN + r;
       const void* M = isA ? A.X : A.W;
       const int ld = isA ? A.ldx : A.ldw;
+      // register u holds K entry (u + 2 s) mod 64, s = (r / 8) mod 4: at the store of register pair q
+      // the 32 lanes of a warp (rows with 8 values of r mod 8, 4 of s) write 32 different banks
+      const int sh = 2 * ((r >> 3) & 3);
       double v[64];
       int mex = 0;
 #pragma unroll
-      for (int kk = 0; kk < 64; ++kk) {
-        v[kk] = kk < ng ? gram_op(M, ld, g0 + kk, ra, A.nv, A.cplx) : 0.0;
-        mex = max(mex, bexp(v[kk]));
+      for (int u = 0; u < 64; ++u) {
+        const int kk = (u + sh) & 63;
+        v[u] = kk < ng ? gram_op(M, ld, g0 + kk, ra, A.nv, A.cplx) : 0.0;
+        mex = max(mex, bexp(v[u]));
       }
       const int E = mex ? mex - 1022 : 0;
       unsigned char* base = isA ? sA : sB;
       const int pbytes = isA ? PLA : PLB;
 #pragma unroll
-      for (int kp = 0; kp < 32; ++kp) put_pair(base, pbytes, r, 2 * kp, v[2 * kp], v[2 * kp + 1], E);
+      for (int q = 0; q < 32; ++q) put_pair(base, pbytes, r, (2 * q + sh) & 63, v[2 * q], v[2 * q + 1], E);
       if (isA) sE[r] = E;
       else Fexp[r] = E;
     }
@@ -321,7 +325,7 @@ __global__ void __launch_bounds__(WT, 1) k_rot_wide(const WRotArgs A) {
   unsigned char* sm = (unsigned char*)(((uintptr_t)wz_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;
   unsigned char* sB = sm + OZ_S * PLA;
-  __shared__ int sE[128], Fexp[WN];
+  __shared__ int sE[128], Fexp[WN], sEh[2][128];
   __shared__ uint64_t b_bar, mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_fail;
@@ -361,20 +365,25 @@ __global__ void __launch_bounds__(WT, 1) k_rot_wide(const WRotArgs A) {
         }
         b_out = true;
         if (tid < WN) Fexp[tid] = A.bex[blk * WN + tid];
-        {   // A digits: two threads per row, 32 K entries each, a common exponent per row
-          const int r = tid >> 1, h = tid & 1;
+        {   // A digits: thread (row r, half h of the 64 K entries), a common exponent per row; register
+            // u holds entry h 32 + (u + 2 s) mod 32, s = (r / 8) mod 4, so that the lanes of a warp
+            // store to 32 different banks
+          const int r = tid & 127, h = tid >> 7, sh = 2 * ((r >> 3) & 3);
           double v[32];
           int mex = 0;
 #pragma unroll
           for (int u = 0; u < 32; ++u) {
-            v[u] = r < nr ? rot_op(A.X, A.ldx, r0 + r, kc, h * 32 + u, A.nv, A.cplx) : 0.0;
+            v[u] = r < nr ? rot_op(A.X, A.ldx, r0 + r, kc, h * 32 + ((u + sh) & 31), A.nv, A.cplx) : 0.0;
             mex = max(mex, bexp(v[u]));
           }
-          mex = max(mex, __shfl_xor_sync(0xffffffffu, mex, 1));
+          sEh[h][r] = mex;
+          __syncthreads();
+          mex = max(sEh[0][r], sEh[1][r]);
           const int E = mex ? mex - 1022 : 0;
           if (h == 0) sE[r] = E;
 #pragma unroll
-          for (int kp = 0; kp < 16; ++kp) put_pair(sA, PLA, r, h * 32 + 2 * kp, v[2 * kp], v[2 * kp + 1], E);
+          for (int q = 0; q < 16; ++q)
+            put_pair(sA, PLA, r, h * 32 + ((2 * q + sh) & 31), v[2 * q], v[2 * q + 1], E);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncthreads();
