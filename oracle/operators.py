@@ -111,24 +111,40 @@ class Problem:
             self.gradA[e] = ga
 
     def _orthogonalize(self):
-        """c (Eq. orthCGLL) and M^oo (Eq. Moo)."""
-        c = np.zeros((self.nO, self.nh), self.dtype)
+        """c (Eq. orthCGLL) and M^oo (Eq. Moo). On a block of cells only the columns of c of the
+        tabulated cells' nodes can be nonzero; c then holds those columns (``c_cols`` maps a global
+        node to its column), the full mesh keeps every column."""
+        if self.tab_cells is self.cells:
+            cols_nodes = None
+            m = self.m
+            ncol = self.nh
+        else:
+            cols_nodes = np.unique(np.concatenate([self.mesh.cell_nodes(e) for e in self.tab_cells]))
+            self.c_cols = np.full(self.nh, -1, dtype=np.int64)
+            self.c_cols[cols_nodes] = np.arange(len(cols_nodes))
+            m = self.m[cols_nodes]
+            ncol = len(cols_nodes)
+        c = np.zeros((self.nO, ncol), self.dtype)
         MAA = np.zeros((self.nO, self.nO), self.dtype)
         for e in self.tab_cells:
             _, w = self.quad.cell(e)
-            nodes, act = self.mesh.cell_nodes(e), self.act[e]
+            nodes, act = self._ccols(self.mesh.cell_nodes(e)), self.act[e]
             d = self.phiC[e].T @ (w[:, None] * self.phiA[e])          # int N^C_l N^A_nu
             np.add.at(c, (act[None, :], nodes[:, None]), d)
             MAA[np.ix_(act, act)] += self.phiA[e].conj().T @ (w[:, None] * self.phiA[e])
-        c /= self.m[None, :]
+        c /= m[None, :]
         self.c = c
         self.MAA = MAA
-        self.Moo = MAA - (c.conj() * self.m[None, :]) @ c.T
+        self.Moo = MAA - (c.conj() * m[None, :]) @ c.T
         self.Moo = 0.5 * (self.Moo + self.Moo.conj().T)
+
+    def _ccols(self, nodes):
+        """Columns of c of global nodes."""
+        return nodes if getattr(self, "c_cols", None) is None else self.c_cols[nodes]
 
     def gamma(self, e):
         """Gamma_e = C^T restricted to (nodes(e), act(e)), shape (n_loc, n_a)."""
-        return self.c[np.ix_(self.act[e], self.mesh.cell_nodes(e))].T
+        return self.c[np.ix_(self.act[e], self._ccols(self.mesh.cell_nodes(e)))].T
 
     def _gindex(self, e):
         return np.concatenate([self.mesh.cell_nodes(e), self.nh_full + self.act[e]])

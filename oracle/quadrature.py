@@ -83,12 +83,20 @@ def tensor_gauss_box(lo, hi, n):
 
 
 class Quadrature:
-    """Point sets of every cell; ``offset[e]:offset[e+1]`` slices cell e."""
+    """Point sets of every cell; ``offset[e]:offset[e+1]`` slices cell e.
 
-    def __init__(self, mesh, pos, rc, nq_cell, nq_enr, depth):
+    ``cells`` (optional) limits the point sets to those cells, the others get none: a bounded
+    sample of a large mesh (every listed cell has exactly the points it has in the full set)."""
+
+    def __init__(self, mesh, pos, rc, nq_cell, nq_enr, depth, cells=None):
         self.mesh = mesh
+        keep = None if cells is None else set(int(e) for e in cells)
         pts, wts, off, cls = [], [], [0], []
         for e in range(mesh.ncells):
+            if keep is not None and e not in keep:
+                cls.append(-1)
+                off.append(off[-1])
+                continue
             lo, hi = mesh.cell_box(e)
             c = cell_class(lo, hi, pos, mesh.a, rc)
             cls.append(c)

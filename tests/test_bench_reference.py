@@ -30,7 +30,7 @@ def test_reference_arm_prints_one_contract_line():
     sys.path.insert(0, ROOT)
     import bench
     import workloads as W
-    assert d["config"]["workload"] == bench.workload_text(W.CONFIGS["c3"]())
+    assert d["config"]["workload"] == bench.workload_text(W.CONFIGS["c5"]())
 
 
 def test_workload_description_follows_the_configuration():
