@@ -746,7 +746,7 @@ def main():
                     help="with --filter-only: store the FP64 matrices too and apply H once in FP64")
     ap.add_argument("--acc-passes", type=int, default=150,
                     help="largest number of mixed subspace-iteration passes (all k) of the accuracy run")
-    ap.add_argument("--acc-seconds", type=float, default=150.0,
+    ap.add_argument("--acc-seconds", type=float, default=120.0,
                     help="time budget of the accuracy run (it stops at the target, the pass limit or this)")
     ap.add_argument("--acc-target", type=float, default=1e-7,
                     help="residual of the occupied states the accuracy run converges to")
