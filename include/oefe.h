@@ -247,11 +247,22 @@ int oefe_filter_batched_defect(oefe_ctx_t ctx, int nk, void* const* X, const int
  * (1) the same with 32 vectors per tile; (2) one CTA per tile;
  * (3) the warp-specialized kernel with TMA loads (persistent); (4) the same with
  * the real part of a complex cell matrix applied to [Re X | Im X] in one
- * N = 128 MMA. The three-part split (OEFE_STORE_BF16X6) runs on (3), (4) only.
- * ms (host, 5 doubles, may be NULL) receives the time of one degree's cell
+ * N = 128 MMA (complex data only); (5) the TMA kernel with 128 vectors per
+ * tile (real data only: each cell matrix streams once per 128 vectors). The
+ * three-part split (OEFE_STORE_BF16X6) runs on (3), (4), (5) only.
+ * ms (host, 6 doubles, may be NULL) receives the time of one degree's cell
  * products for each candidate (0 when a candidate is unavailable). Vectors as
  * for oefe_filter_batched; they are read, not changed. */
 int oefe_filter_autotune(oefe_ctx_t ctx, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
+
+/* oefe_set_filter_shape -- keeps launch shape `shape` (0..5, the candidates of
+ * oefe_filter_autotune) for the BF16X3 filters without timing; -1 returns to
+ * the untuned default ((4) on complex data, (3) on real data). A shape the stored split or
+ * the data type does not have falls back at filter time: (0)-(2) run as (3)
+ * for the three-part split; (4) runs as (3) on real data, (5) as (3) on
+ * complex data. Every shape computes the same products up to FP32 summation
+ * order. Returns OEFE_ERR_ARG for another value. */
+int oefe_set_filter_shape(oefe_ctx_t ctx, int shape);
 
 /* ---------------------------------------------------------------- subspace
  * oefe_orthonormalize -- Cholesky-QR in the M inner product, twice

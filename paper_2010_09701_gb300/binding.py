@@ -67,6 +67,7 @@ SIGNATURES = [
     ("oefe_launch_count", _I, [_c.POINTER(_c.c_int64)]),
     ("oefe_set_f64_products", _I, [_P, _I]),
     ("oefe_set_product_shape", _I, [_P, _I]),
+    ("oefe_set_filter_shape", _I, [_P, _I]),
 ]
 
 _lib = None
@@ -330,7 +331,7 @@ class Context:
 
     def filter_autotune(self, Xs):
         arr, nvs, lds, dt = self._blocks(Xs)
-        ms = np.zeros(5)
+        ms = np.zeros(6)
         self._check(self.lib.oefe_filter_autotune(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dt, _dp(ms)))
         return ms
 
@@ -417,6 +418,10 @@ class Context:
         """Arithmetic of the FP64 cell products: F64_NATIVE, or F64_PAIRS (FP32 pairs on the
         single-leaf cells; needs an operator built with STORE_F64PAIR)."""
         self._check(self.lib.oefe_set_f64_products(self.h, int(mode)))
+
+    def set_filter_shape(self, shape):
+        """Keep one of the autotuner's launch shapes (0..5) for the BF16X3 filters; -1: untuned."""
+        self._check(self.lib.oefe_set_filter_shape(self.h, int(shape)))
 
     def set_product_shape(self, shape):
         """Launch shape of the FP32-pair cell products: -1 timed at first use (default), or 0, 1, 2."""

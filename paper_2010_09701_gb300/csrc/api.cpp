@@ -416,6 +416,11 @@ int oefe_set_product_shape(oefe_ctx_t ctx, int shape) {
   return OEFE_OK;
 }
 
+int oefe_set_filter_shape(oefe_ctx_t ctx, int shape) {
+  CTX_CHECK(ctx);
+  return filter_set_shape(ctx, shape);
+}
+
 int oefe_launch_count(int64_t* n) {
   if (!n) return OEFE_ERR_ARG;
   *n = (int64_t)g_launches.load(std::memory_order_relaxed);

@@ -33,19 +33,19 @@ namespace {
 
 constexpr int MT = 128;     // rows per M tile
 constexpr int KT = 64;      // K per tile (bf16: 128 bytes per row)
-constexpr int NBV = 64;     // vectors per tile
+constexpr int NBV = 64;     // vectors per tile (complex; real data also 128, the NVT parameter)
 constexpr int THREADS = 320;
 constexpr int MAXPAD = 4 * MT;  // largest npad
 
 // Shared-memory plan per (complex, bf16 parts): NPART planes per A stage (one part of the cell
 // matrix: real or imaginary) and per B stage (the split vectors); the three-part split trades an A
 // stage and half of the epilogue staging for the larger stages.
-template <bool CPLX, int NPART>
+template <bool CPLX, int NPART, int NVT = NBV>
 struct TmaCfg {
   static constexpr int SA = NPART == 2 ? 3 : 2;        // A ring stages
   static constexpr int SB = 2;                         // B ring stages
   static constexpr int ER = NPART == 2 ? 32 : 16;      // epilogue rows staged per round, per warp
-  static constexpr int NB_ROWS = CPLX ? 2 * NBV : NBV;
+  static constexpr int NB_ROWS = CPLX ? 2 * NBV : NVT;
   static constexpr int A_PLANE = MT * 128;
   static constexpr int A_STAGE = NPART * A_PLANE;
   static constexpr int B_PART = NB_ROWS * 128;
@@ -114,17 +114,20 @@ __device__ __forceinline__ void decode_tile(const TmaArgs& A, long long t, int* 
 // MERGE (complex only): the real part of the cell matrix multiplies [Re X | Im X] in one N = 128
 // MMA instead of two N = 64 ones (fewer tensor instructions; which is faster depends on the split,
 // so the autotuner chooses)
-template <bool CPLX, int NPART, bool MERGE>
+// NVT (real data only): vectors per tile, 64 or 128; with 128 a cell's matrix streams once for
+// twice the vectors (one N = 128 MMA per product, 128 tensor-memory columns per M tile)
+template <bool CPLX, int NPART, bool MERGE, int NVT = NBV>
 __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
-  using Cfg = TmaCfg<CPLX, NPART>;
+  static_assert(NVT == NBV || (!CPLX && NVT == 2 * NBV), "128-vector tiles are for real data");
+  using Cfg = TmaCfg<CPLX, NPART, NVT>;
   constexpr int SA = Cfg::SA, SB = Cfg::SB, STG = Cfg::STG;
   constexpr int HALVES = CPLX ? 2 : 1;   // A stages per (K tile, M tile)
   constexpr int A_PLANE = Cfg::A_PLANE;
   constexpr int A_STAGE = Cfg::A_STAGE;
   constexpr int B_PART = Cfg::B_PART;
   constexpr int B_STAGE = Cfg::B_STAGE;
-  constexpr int MCOLS = CPLX ? 2 * NBV : NBV;
-  constexpr int TCOLS = CPLX ? 512 : 256;
+  constexpr int MCOLS = CPLX ? 2 * NBV : NVT;
+  constexpr int TCOLS = (CPLX || NVT == 2 * NBV) ? 512 : 256;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = smem;
@@ -210,7 +213,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
           if (m == 0 && !mbar_wait(&b_full[sb], (uint32_t)(((gb + kt) / SB) & 1), &s_fail)) { ok = false; break; }
           const uint32_t b_base = smem_u32(sB + sb * B_STAGE);
           const uint32_t dcol = taddr + m * MCOLS;
-          constexpr uint32_t ID = idesc_bf16(MT, NBV, false);
+          constexpr uint32_t ID = idesc_bf16(MT, CPLX ? NBV : NVT, false);
           constexpr uint32_t IDN = idesc_bf16(MT, NBV, true);
           constexpr uint32_t ID2 = idesc_bf16(MT, 2 * NBV, false);   // [Re | Im] in one N = 128 MMA
           for (int h = 0; h < HALVES; ++h, ++ga) {
@@ -278,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       const MmaK P = kparams(A, k);
       const int ne = A.act_off[e + 1] - A.act_off[e];
       const int naug = A.nloc + ne;
-      const int v0 = vb * NBV;
+      const int v0 = vb * NVT;
       int mte, kte;
       cell_tiles(A, e, mt, ktn, &mte, &kte);
       // the tile's row map, once per tile, double-buffered; the barrier publishes it and takes
@@ -293,18 +296,20 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
         const long long u = gb / SB;
         if (u >= 1 && !mbar_wait(&b_empty[sb], (uint32_t)((u - 1) & 1), &s_fail)) break;
         unsigned char* b0 = sB + sb * B_STAGE;
-        // each thread owns one vector column v and 16 row pairs (kk, kk+1) of the K tile;
-        // the loads of a batch are issued together so their latencies overlap, and each
-        // pair is written to shared memory as one packed bf16x2 word per plane
-        const int v = gt & (NBV - 1), r0 = gt >> 6;   // r0 in {0, 1}
-        constexpr int BATCH = KT / 4;                   // pairs per batch: all 32 loads in flight
+        // each thread owns one vector column v and the row pairs (kk, kk+1) p = r0 + TPV w of the
+        // K tile (TPV threads per vector: 16 pairs each for 64-vector tiles, 32 for 128); the loads
+        // of a batch are issued together so their latencies overlap, and each pair is written to
+        // shared memory as one packed bf16x2 word per plane
+        constexpr int TPV = 128 / NVT;
+        const int v = gt % NVT, r0 = gt / NVT;          // r0 in [0, TPV)
+        constexpr int BATCH = 16;                       // pairs per batch: 32 loads in flight
         const bool vok = v0 + v < P.nv;
 #pragma unroll 1
-        for (int j0 = 0; j0 < KT / 4; j0 += BATCH) {
+        for (int j0 = 0; j0 < KT / (2 * TPV); j0 += BATCH) {
           float2 xv[2 * BATCH];
 #pragma unroll
           for (int u = 0; u < 2 * BATCH; ++u) {
-            const int kk = 4 * (j0 + (u >> 1)) + 2 * r0 + (u & 1);
+            const int kk = 2 * (r0 + TPV * (j0 + (u >> 1))) + (u & 1);
             const int r = kt * KT + kk;
             xv[u] = make_float2(0.f, 0.f);
             if (r < naug && vok) {
@@ -315,7 +320,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
           }
 #pragma unroll
           for (int w = 0; w < BATCH; ++w) {
-            const int kk = 4 * (j0 + w) + 2 * r0;   // even: the pair shares one 4-byte word
+            const int kk = 2 * (r0 + TPV * (j0 + w));   // even: the pair shares one 4-byte word
             const float2 x0 = xv[2 * w], x1 = xv[2 * w + 1];
             // NPART-way split of the pair: part s = bf16 of what the earlier parts left (the
             // differences are exact in FP32, so three parts hold an FP32 value exactly)
@@ -354,13 +359,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
       const MmaK P = kparams(A, k);
       const int ne = A.act_off[e + 1] - A.act_off[e];
       const int naug = A.nloc + ne;
-      const int v0 = vb * NBV;
+      const int v0 = vb * NVT;
       bool ok = true;
       for (int m = 0; m < mte; ++m) {
         if (!mbar_wait(&acc_full[m], (uint32_t)(use[m] & 1), &s_fail)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int row = m * MT + 32 * q + lane;
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < (CPLX ? 2 : NVT / 32); ++h) {
           const uint32_t tl0 = taddr + ((uint32_t)(32 * q) << 16) + m * MCOLS + 32 * h;
           float re[32], im[32];
           tmem_ld32(tl0, re);
@@ -445,7 +450,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 }  // namespace
 
-size_t cell_mma_tma_smem(bool cplx, int parts) {
+size_t cell_mma_tma_smem(bool cplx, int parts, int nvt) {
+  if (!cplx && nvt == 2 * NBV) return parts == 3 ? TmaCfg<false, 3, 2 * NBV>::SMEM : TmaCfg<false, 2, 2 * NBV>::SMEM;
   if (parts == 3) return cplx ? TmaCfg<true, 3>::SMEM : TmaCfg<false, 3>::SMEM;
   return cplx ? TmaCfg<true, 2>::SMEM : TmaCfg<false, 2>::SMEM;
 }
@@ -481,8 +487,9 @@ int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out) {
 size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
 
 int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
-                        bool cplx, int parts, int grid, cudaStream_t st) {
+                        bool cplx, int parts, int grid, cudaStream_t st, int nvt) {
   if (parts != 2 && parts != 3) { c->err = "tensor path: the split cell matrices were not stored"; return OEFE_ERR_STATE; }
+  if (nvt != NBV && (cplx || nvt != 2 * NBV)) { c->err = "tensor path: 64 vectors per tile, or 128 for real data"; return OEFE_ERR_ARG; }
   if (c->npad % MT != 0 || c->npad > 4 * MT) {
     c->err = "tensor path needs npad a multiple of 128 and at most 512";
     return OEFE_ERR_ARG;
@@ -500,7 +507,7 @@ int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const
   A.npad = c->npad;
   A.nh = c->nh;
   A.err = c->d_status;
-  const size_t smem = cell_mma_tma_smem(cplx, parts);
+  const size_t smem = cell_mma_tma_smem(cplx, parts, nvt);
   auto go = [&](auto kern) -> int {
     OEFE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     OEFE_COUNTED kern<<<grid, THREADS, smem, st>>>(A);
@@ -508,7 +515,9 @@ int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const
   };
   // merged real-part MMAs: the tuned choice, else on (measured faster for both splits)
   const bool merge = c->tune_merge >= 0 ? c->tune_merge != 0 : true;
-  if (!cplx) OEFE_TRY(parts == 3 ? go(k_cell_mma_tma<false, 3, false>) : go(k_cell_mma_tma<false, 2, false>));
+  if (!cplx && nvt == 2 * NBV)
+    OEFE_TRY(parts == 3 ? go(k_cell_mma_tma<false, 3, false, 2 * NBV>) : go(k_cell_mma_tma<false, 2, false, 2 * NBV>));
+  else if (!cplx) OEFE_TRY(parts == 3 ? go(k_cell_mma_tma<false, 3, false>) : go(k_cell_mma_tma<false, 2, false>));
   else if (parts == 3) OEFE_TRY(merge ? go(k_cell_mma_tma<true, 3, true>) : go(k_cell_mma_tma<true, 3, false>));
   else OEFE_TRY(merge ? go(k_cell_mma_tma<true, 2, true>) : go(k_cell_mma_tma<true, 2, false>));
   OEFE_CUDA_TRY(c, cudaGetLastError());

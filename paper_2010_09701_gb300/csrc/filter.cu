@@ -781,7 +781,7 @@ int batched_launch_degrees(oefe_ctx* c, const BatchPlan& P, bool cplx, const Mma
       // D_1 = alpha_1 R: nothing to multiply
     } else if (P.tma) {
       OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk + (size_t)j * P.nk, nullptr, P.nk, P.ntiles, cplx, P.parts,
-                                   (int)std::min<long long>(P.ntiles, c->num_sms), c->bstream));
+                                   (int)std::min<long long>(P.ntiles, c->num_sms), c->bstream, P.nb));
     } else if (P.grid > 0) {
       OEFE_TRY(launch_cell_mma_multi(c, d_mk + (size_t)j * P.nk, P.nk, P.ntiles, cplx, P.nb, P.grid, c->bstream));
     } else {  // one CTA per tile, one launch per k-point
@@ -869,7 +869,7 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
     if (c->kd[k].bf_parts != parts) { c->err = "filter_batched: k-points with different splits"; return OEFE_ERR_STATE; }
   const bool tma = (c->use_tma || parts == 3) && c->d_tmaps;
   if (!tma && parts != 2) { c->err = "filter_batched: the split cell matrices have no tensor maps"; return OEFE_ERR_STATE; }
-  if (tma) c->tune_nb = 64;
+  if (tma) c->tune_nb = (!cplx && c->tma_nvt == 128) ? 128 : 64;
   // workspace: per k  Z | Yo | L0 L1 L2 | B1 B2 (mixed) or R, A Q, coefficients (defect)
   std::vector<size_t> off(nk + 1, 0);
   auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
@@ -1040,7 +1040,7 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
       }
     }
     // set the kernels' shared-memory limits outside of the capture
-    if (tma) OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, 0, cplx, parts, 1, c->bstream));
+    if (tma) OEFE_TRY(launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, 0, cplx, parts, 1, c->bstream, P.nb));
     else if (P.grid > 0) OEFE_TRY(launch_cell_mma_multi(c, d_mk, nk, 0, cplx, P.nb, 1, c->bstream));
     OEFE_CUDA_TRY(c, cudaStreamSynchronize(c->bstream));
     cudaGraph_t graph = nullptr;
@@ -1160,11 +1160,18 @@ int filter_batched_impl(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
       double sg = e / (a0[k] - cc);
       const double s1 = sg;
       for (int j = 2; j < degree; ++j) sg = 1.0 / (2.0 / s1 - sg);
-      int ip = fp, ic = 1;
-      OEFE_TRY(run_degrees(c, K, dtype, bufs, lds, &ip, &ic, nv[k], degree, degree, e, cc, &sg, s1, Zk[k], Yo[k], false));
-      if (ic != 0)
-        OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(X[k], (size_t)ld[k] * es, bufs[ic], (size_t)lds[ic] * es, (size_t)nv[k] * es,
-                                           (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+      // the FP64 degree in column chunks: the product buffer holds APPLY_CHUNK FP64 columns
+      for (int c0 = 0; c0 < nv[k]; c0 += APPLY_CHUNK) {
+        const int w = std::min(APPLY_CHUNK, nv[k] - c0);
+        void* bq[3] = {(char*)bufs[0] + (size_t)c0 * es, (char*)bufs[1] + (size_t)c0 * es,
+                       (char*)bufs[2] + (size_t)c0 * es};
+        double sgq = sg;
+        int ip = fp, ic = 1;
+        OEFE_TRY(run_degrees(c, K, dtype, bq, lds, &ip, &ic, w, degree, degree, e, cc, &sgq, s1, Zk[k], Yo[k], false));
+        if (ic != 0)
+          OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(bq[0], (size_t)ld[k] * es, bq[ic], (size_t)lds[ic] * es, (size_t)w * es,
+                                             (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
+      }
     } else if (P.lc[k] != 0) {
       void* L[3] = {X[k], L1[k], L2[k]};
       OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(X[k], (size_t)ld[k] * es, L[P.lc[k]], (size_t)nv[k] * es, (size_t)nv[k] * es,
@@ -1236,6 +1243,37 @@ int cheb_filter_batched_defect(oefe_ctx* c, int nk, void* const* X, const int* n
   return filter_batched_groups(c, nk, X, nv, ld, dtype, degree, a, b, a0, theta, flags);
 }
 
+// the launch shapes the autotuner chooses among: vectors per tile, persistent grid (0: one CTA per
+// tile), TMA kernel, merged real-part MMAs
+struct FilterShape { int nb, grid, tma, merge; };
+static FilterShape filter_shape(const oefe_ctx* c, int i) {
+  const FilterShape s[6] = {{64, c->num_sms, 0, 0}, {32, c->num_sms, 0, 0}, {64, 0, 0, 0}, {64, c->num_sms, 1, 0},
+                            {64, c->num_sms, 1, 1}, {128, c->num_sms, 1, 0}};
+  return s[i];
+}
+
+static void keep_shape(oefe_ctx* c, const FilterShape& s) {
+  c->tune_nb = s.nb;
+  c->tune_grid = s.grid;
+  c->use_tma = s.tma;
+  c->tune_merge = s.merge;
+  c->tma_nvt = s.tma ? s.nb : 64;
+}
+
+int filter_set_shape(oefe_ctx* c, int shape) {
+  if (shape < -1 || shape > 5) { c->err = "set_filter_shape: shape must be -1 or 0..5"; return OEFE_ERR_ARG; }
+  if (shape < 0) {
+    c->tune_nb = 0;
+    c->tune_grid = 0;
+    c->use_tma = 1;
+    c->tune_merge = -1;
+    c->tma_nvt = 64;
+  } else {
+    keep_shape(c, filter_shape(c, shape));
+  }
+  return OEFE_OK;
+}
+
 int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms) {
   if (!c->built) { c->err = "call oefe_build_hamiltonian first"; return OEFE_ERR_STATE; }
   if (nk < 1 || nk != (int)c->kd.size() || !X || !nv || !ld) { c->err = "autotune: one X, nv, ld per k-point"; return OEFE_ERR_ARG; }
@@ -1261,23 +1299,31 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
     else OEFE_CUDA_TRY(c, cudaMemcpy2DAsync(XL[k], (size_t)nv[k] * es_low, X[k], (size_t)ld[k] * es_low,
                                             (size_t)nv[k] * es_low, (size_t)n, cudaMemcpyDeviceToDevice, c->stream));
   }
-  struct Cand { int nb, grid, tma, merge; };
-  const Cand cands[5] = {{64, c->num_sms, 0, 0}, {32, c->num_sms, 0, 0}, {64, 0, 0, 0}, {64, c->num_sms, 1, 0},
-                         {64, c->num_sms, 1, 1}};
-  // the three-part split has only the TMA kernel; the two-part split also the one-CTA-per-tile kernels
+  FilterShape cands[6];
+  for (int i = 0; i < 6; ++i) cands[i] = filter_shape(c, i);
+  // the three-part split has only the TMA kernel; the two-part split also the one-CTA-per-tile
+  // kernels; merged MMAs are for complex data, 128-vector TMA tiles for real data
   const int parts = c->kd[0].bf_parts;
-  const int cfirst = parts == 3 ? 3 : 0;
-  const int ncand = c->d_tmaps ? (cplx ? 5 : 4) : 3;
-  if (cfirst >= ncand) { c->err = "autotune: no tensor maps for the split cell matrices"; return OEFE_ERR_STATE; }
+  std::vector<int> order;
+  if (parts != 3)
+    for (int ci = 0; ci < 3; ++ci) order.push_back(ci);
+  if (c->d_tmaps) {
+    order.push_back(3);
+    order.push_back(cplx ? 4 : 5);
+  }
+  if (order.empty()) { c->err = "autotune: no tensor maps for the split cell matrices"; return OEFE_ERR_STATE; }
+  if (ms)
+    for (int ci = 0; ci < 6; ++ci) ms[ci] = 0.0;
   double best = 1e300;
-  int bi = 0;
+  int bi = order[0];
   MmaK* d_mk = nullptr;
   OEFE_TRY(dev_alloc(c, (void**)&d_mk, nk * sizeof(MmaK)));
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   int st = OEFE_OK;
-  for (int ci = cfirst; ci < ncand && st == OEFE_OK; ++ci) {
+  for (size_t oi = 0; oi < order.size() && st == OEFE_OK; ++oi) {
+    const int ci = order[oi];
     std::vector<MmaK> mk(nk);
     long long nt = 0;
     for (int k = 0; k < nk; ++k) {
@@ -1297,7 +1343,7 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
       if (cands[ci].tma) {
         c->tune_merge = cands[ci].merge;
         st = launch_cell_mma_tma(c, c->d_tmaps, d_mk, nullptr, nk, nt, cplx, parts,
-                                 (int)std::min<long long>(nt, c->num_sms), c->stream);
+                                 (int)std::min<long long>(nt, c->num_sms), c->stream, cands[ci].nb);
       } else if (cands[ci].grid > 0) {
         st = launch_cell_mma_multi(c, d_mk, nk, nt, cplx, cands[ci].nb, cands[ci].grid, c->stream);
       } else {
@@ -1327,10 +1373,7 @@ int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const in
     c->err = "autotune: a tensor-core pipeline wait timed out";
     return OEFE_ERR_TIMEOUT;
   }
-  c->tune_nb = cands[bi].nb;
-  c->tune_grid = cands[bi].grid;
-  c->use_tma = cands[bi].tma;
-  c->tune_merge = cands[bi].merge;
+  keep_shape(c, cands[bi]);
   return OEFE_OK;
 }
 

@@ -192,6 +192,7 @@ struct oefe_ctx {
   std::vector<BatchGraph> bgraphs;      // captured low-precision degrees, one per vector chunk (<= 4 kept)
   std::vector<cudaEvent_t> bev_kernel;  // event pairs around the batched cell products (when timed)
   int tune_nb = 0, tune_grid = 0;       // chosen vectors per tile and persistent grid size
+  int tma_nvt = 64;                     // vectors per tile of the TMA kernel on real data (64 or 128, tuned)
   int use_tma = 1;                      // warp-specialized TMA kernel for the tensor-core products
   // sum-factorized FP64 products on single-leaf cells (sumfac.cu)
   int use_sumfac = 1;
@@ -206,7 +207,7 @@ struct oefe_ctx {
   int n_sf = 0, n_dense = 0, sf_nbuf = 0;
   double* d_veff = nullptr;             // V_eff at the points of the last operator build
   int tune_merge = -1;                  // TMA kernel: merged real-part MMAs (1), separate (0), untuned (-1)
-  double tune_ms[5] = {0, 0, 0, 0, 0};
+  double tune_ms[6] = {0, 0, 0, 0, 0, 0};
   void* d_tmaps = nullptr;              // one tensor map per k-point (split cell matrices)
   int n_tmaps = 0;
 };
@@ -267,6 +268,7 @@ int cheb_filter_batched(oefe_ctx* c, int nk, void* const* X, const int* nv, cons
 int cheb_filter_batched_defect(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype,
                                int degree, const double* a, const double* b, const double* a0, const double* theta,
                                int flags);
+int filter_set_shape(oefe_ctx* c, int shape);
 int filter_autotune(oefe_ctx* c, int nk, void* const* X, const int* nv, const int* ld, int dtype, double* ms);
 void release_batch_graphs(oefe_ctx* c);
 
@@ -292,10 +294,10 @@ void cell_box(const oefe_ctx* c, int e, double lo[3], double hi[3]);
 double fp64_product_flops(const oefe_ctx* c, bool cplx, int nv);
 void gauss_rule(int n, std::vector<double>& x, std::vector<double>& w);
 int launch_cell_mma_tma(oefe_ctx* c, const void* d_maps, const MmaK* d_ks, const MmaK* k0, int nk, long long ntiles,
-                        bool cplx, int parts, int grid, cudaStream_t st);
+                        bool cplx, int parts, int grid, cudaStream_t st, int nvt = 64);
 int make_cell_tmap(oefe_ctx* c, const KData& K, void* map_out);
 size_t tensor_map_bytes();
-size_t cell_mma_tma_smem(bool cplx, int parts);
+size_t cell_mma_tma_smem(bool cplx, int parts, int nvt = 64);
 int launch_cell_mma_ptrs(oefe_ctx* c, const void* H, const void* X, int ldx, int nv, void* Z, bool cplx, int nb,
                          cudaStream_t st);
 

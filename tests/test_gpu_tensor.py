@@ -120,7 +120,8 @@ def test_autotune_then_batched_real():
     pr = prs[0]
     X = W.random_vectors(pr.n, 70, seed=4)
     ms = ctx.filter_autotune([to_gpu(X, torch.float32)])
-    assert np.all(ms[:4] > 0) and ms[4] == 0   # real vectors: four candidates, the TMA kernel included
+    # real vectors: five candidates, the TMA kernel with 64 and with 128 vectors per tile included
+    assert np.all(ms[:4] > 0) and ms[4] == 0 and ms[5] > 0
     a, b, a0 = bounds(pr)
     ref = solver.chebyshev_filter(pr.apply_A, X, 5, a, b, a0)
     Xd = to_gpu(X, torch.float32)
@@ -231,7 +232,8 @@ def test_bf16x6_batched_two_k():
     for k in range(2):
         assert colerr(Xd[k].cpu().numpy(), refs[k]) < TOL6_FILTER, k
     ms = ctx.filter_autotune([to_gpu(X, torch.complex64) for X in Xs])
-    assert ms[3] > 0 and ms[4] > 0 and np.all(ms[:3] == 0)   # only the TMA kernel takes three parts
+    # only the TMA kernel takes three parts; 128-vector tiles are for real data
+    assert ms[3] > 0 and ms[4] > 0 and np.all(ms[:3] == 0) and ms[5] == 0
 
 
 def test_bf16x6_four_m_tiles():
@@ -246,3 +248,68 @@ def test_bf16x6_four_m_tiles():
     Xd = to_gpu(X, torch.complex64)
     ctx.chebyshev_filter(0, Xd, 1, 0.0, 500.0, -50.0, flags=FILTER_BF16X3)
     assert colerr(Xd.cpu().numpy().astype(np.complex128), ref) < TOL6_DEGREE1
+
+
+@pytest.mark.parametrize("store", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("nv", [70, 128, 200])
+def test_real_128_vector_tiles(store, nv):
+    # real data with 128 vectors per TMA tile (each cell matrix streams once per 128 vectors):
+    # ragged last block, both splits; same products as 64-vector tiles up to FP32 summation order
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X3, STORE_BF16X6, STORE_F64
+    prs, ctx, V, _ = paired(ks=[(0.0, 0.0, 0.0)],
+                            store=STORE_F64 | (STORE_BF16X6 if store == "bf16x6" else STORE_BF16X3))
+    pr = prs[0]
+    a, b, a0 = bounds(pr)
+    X = W.random_vectors(pr.n, nv, seed=nv + 1)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 6, a, b, a0)
+    outs = {}
+    for shape in (3, 5):
+        ctx.set_filter_shape(shape)
+        Xd = to_gpu(X)
+        ctx.filter_batched([Xd], 6, [a], [b], [a0], FILTER_BF16X3 | FILTER_LAST_FP64)
+        outs[shape] = Xd.cpu().numpy()
+        assert colerr(outs[shape], ref) < (TOL6_FILTER if store == "bf16x6" else TOL_FILTER), shape
+    ctx.set_filter_shape(-1)
+    assert colerr(outs[5], outs[3]) < (1e-6 if store == "bf16x6" else 2e-5)
+
+
+def test_real_128_vector_tiles_four_m_tiles():
+    # n_aug > 384 (four M tiles, 512 accumulator columns of TMEM) with 128-vector tiles
+    from paper_2010_09701_gb300 import FILTER_BF16X3
+    pos = np.random.default_rng(5).uniform(0.0, 7.0, (9, 3))
+    prs, ctx, V, _ = paired(a=7.0, n=2, p=6, Zs=(3,) * 9, pos=pos, quad=(7, 7, 1), r0=2.0, rc=3.0,
+                            ks=[(0.0, 0.0, 0.0)])
+    pr = prs[0]
+    assert not pr.complex and max(ctx.cell_info(e).size for e in range(8)) > 384
+    X = W.random_vectors(pr.n, 150, seed=9)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 1, 0.0, 500.0, -50.0)
+    ctx.set_filter_shape(5)
+    Xd = to_gpu(X, torch.float32)
+    ctx.filter_batched([Xd], 1, [0.0], [500.0], [-50.0], FILTER_BF16X3)
+    ctx.set_filter_shape(-1)
+    assert colerr(Xd.cpu().numpy().astype(np.float64), ref) < TOL_DEGREE1
+
+
+def test_filter_shape_argument_checked():
+    from paper_2010_09701_gb300 import OefeError
+    prs, ctx, V, _ = paired(ks=[(0.0, 0.0, 0.0)])
+    for bad in (-2, 6):
+        with pytest.raises(OefeError):
+            ctx.set_filter_shape(bad)
+
+
+@pytest.mark.parametrize("cplx", [False, True])
+@pytest.mark.parametrize("nv", [96, 120, 128])
+def test_mixed_filter_wide_blocks(cplx, nv):
+    # more than 64 vectors in one column group: the last (FP64) degree runs in column chunks that
+    # fit the product buffer; vector counts above half the basis size included
+    from paper_2010_09701_gb300 import FILTER_BF16X3, FILTER_LAST_FP64
+    prs, ctx, V, _ = paired(ks=[KS[1] if cplx else KS[0]])
+    pr = prs[0]
+    assert 2 * nv > pr.n or nv == 96
+    a, b, a0 = bounds(pr)
+    X = W.random_vectors(pr.n, nv, complex_=cplx, seed=40 + nv)
+    ref = solver.chebyshev_filter(pr.apply_A, X, 6, a, b, a0)
+    Xd = to_gpu(X)
+    ctx.filter_batched([Xd], 6, a, b, a0, FILTER_BF16X3 | FILTER_LAST_FP64)
+    assert colerr(Xd.cpu().numpy(), ref) < TOL_FILTER
