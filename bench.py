@@ -518,6 +518,8 @@ def run_ours(args, rank, world):
                 _, occ_m, e_m = P.occupations(theta, [1.0 / nk] * nk, w.nelectrons)
                 occ_idx = [np.asarray(o) > 1e-8 for o in occ_m]
                 hist.append(float(max(np.max(np.asarray(r)[o]) for r, o in zip(res, occ_idx))))
+                if len(hist) % 5 == 0:
+                    progress("accuracy pass %d: residual %.3e" % (len(hist), hist[-1]))
                 if hist[-1] < args.acc_target * 0.1 or time.time() - t_acc > args.acc_seconds:
                     break
                 if len(hist) > 25 and hist[-1] > 0.5 * min(hist[:-20]):

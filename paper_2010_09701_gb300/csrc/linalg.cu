@@ -480,7 +480,7 @@ int gram(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int n
     bool done = false;
     OEFE_TRY(gram_ozaki<S>(c, X, ldx, W, ldw, n, nv, out, &done));
     if (done) return OEFE_OK;
-    return gram_ozaki_wide<S>(c, X, ldx, W, ldw, n, nv, out);   // wider blocks: digits cut in the kernel
+    return gram_ozaki_wide<S>(c, X, ldx, W, ldw, n, nv, out, herm);   // wider blocks: digits cut in the kernel
   }
   const int tiles = (nv + GT - 1) / GT;
   const int64_t rpc = (n + nchunk - 1) / nchunk;

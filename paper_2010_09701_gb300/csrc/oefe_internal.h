@@ -245,7 +245,7 @@ template <typename S>
 int rotate_ozaki(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm, bool* done);
 // the same for any nv, the digits cut inside the MMA kernels (ozaki_wide.cu)
 template <typename S>
-int gram_ozaki_wide(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out);
+int gram_ozaki_wide(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, bool herm);
 template <typename S>
 int rotate_ozaki_wide(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C, bool herm);
 int build_hamiltonian(oefe_ctx* c, const double* veff, int store);

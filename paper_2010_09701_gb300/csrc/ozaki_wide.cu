@@ -17,9 +17,10 @@
 //
 //   Rotation X <- X G: A = rows of X, a K chunk = 64 columns (real) or [Re | Im] of 32 complex
 //   columns; B = the matching rows of the real form of G for 64 output columns (the real parts, or
-//   the imaginary parts, of 64 complex output columns). A CTA takes whole tiles of 128 rows, all
-//   output blocks of a tile into a staging area first, so the in-place update never reads a row it
-//   has written.
+//   the imaginary parts, of 64 complex output columns). A CTA takes whole tiles of 128 rows, the K
+//   chunks outermost (the A digits of a chunk cut once for all output blocks), every output block's
+//   FP32-pair partial sums in a staging area, so the in-place update never reads a row it has
+//   written.
 //
 // Every wait is bounded; on a timeout the CTA raises the error flag, lets its copies and MMAs in
 // flight land, frees its tensor memory and returns.
@@ -149,6 +150,7 @@ struct WGramArgs {
   int nv;
   bool cplx;
   int nI, nJ;                // tiles of 128 A rows and 64 B columns of D
+  bool upper;                // symmetric result: only the tiles (I, J >= 2 I) that meet the upper triangle
   long long passes, ppc;     // passes of 64 rows, passes per CTA
   double* part;              // [block][I][J][128][64]
   int* err;
@@ -174,7 +176,16 @@ __global__ void __launch_bounds__(WT, 1) k_gram_wide(const WGramArgs A) {
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t taddr = tmem_slot;
-  const int I = blockIdx.y / A.nJ, J = blockIdx.y % A.nJ;
+  int I = blockIdx.y / A.nJ, J = blockIdx.y % A.nJ;
+  if (A.upper) {   // blockIdx.y enumerates the tiles with J >= 2 I row by row
+    int y = blockIdx.y;
+    I = 0;
+    while (y >= A.nJ - 2 * I) {
+      y -= A.nJ - 2 * I;
+      ++I;
+    }
+    J = 2 * I + y;
+  }
   const long long pb = (long long)blockIdx.x * A.ppc, pe = min(A.passes, pb + A.ppc);
   const int row = tid & 127, ch = tid >> 7;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
@@ -243,10 +254,12 @@ __global__ void __launch_bounds__(WT, 1) k_gram_wide(const WGramArgs A) {
 
 // S from the partial sums of all blocks (real form combined for complex data)
 template <typename S>
-__global__ void k_gram_wide_reduce(const double* part, int nbx, int nI, int nJ, int nv, S* out) {
+__global__ void k_gram_wide_reduce(const double* part, int nbx, int nI, int nJ, int nv, bool upper, S* out) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nv * nv) return;
-  const int i = t / nv, j = t % nv;
+  // upper (real symmetric result): entry (i, j) below the diagonal is entry (j, i), which lies in a
+  // computed tile (column tile j / 64 >= 2 (row tile i / 128) whenever i <= j)
+  const int i = upper ? min(t / nv, t % nv) : t / nv, j = upper ? max(t / nv, t % nv) : t % nv;
   auto D = [&](int ra, int rb) {
     double s = 0.0;
     for (int b = 0; b < nbx; ++b)
@@ -314,22 +327,34 @@ struct WRotArgs {
   int nv;
   bool cplx;
   int nkc, nob;
+  bool herm;                 // G upper triangular: K chunks past an output block's columns are zero
   const unsigned char* bpl;  // B digit planes per (kc, ob)
   const int* bex;            // B exponents per (kc, ob)
-  double* stage;             // per CTA: 128 rows x (nv reals, or 2 nv for complex)
+  float2* stage;             // per CTA: [ob][128 rows][64 columns] FP32-pair partial sums
   int* err;
 };
 
+// K chunk kc contributes to output block ob (an upper triangular G has no entries in the chunks past
+// the block's last column)
+__device__ __forceinline__ bool rot_active(const WRotArgs& A, int kc, int ob) {
+  return !A.herm || kc < (A.cplx ? 2 * (ob >> 1) + 2 : ob + 1);
+}
+
+// Per tile of 128 rows the K chunks run outermost: the A digits of a chunk are cut once (a warp per
+// 16 rows, a lane per pair of K entries: coalesced loads, a row's exponent by one warp reduction)
+// and serve every output block the chunk contributes to; each (chunk, block) round's combined
+// levels are added to the block's FP32-pair partial sums staged per CTA (the first chunk stores),
+// and the tile's rows of X are rewritten from the stage once every chunk is done.
 __global__ void __launch_bounds__(WT, 1) k_rot_wide(const WRotArgs A) {
   extern __shared__ __align__(1024) unsigned char wz_raw[];
   unsigned char* sm = (unsigned char*)(((uintptr_t)wz_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* sA = sm;
   unsigned char* sB = sm + OZ_S * PLA;
-  __shared__ int sE[128], Fexp[WN], sEh[2][128];
+  __shared__ int sE[128], Fexp[WN];
   __shared__ uint64_t b_bar, mma_bar;
   __shared__ uint32_t tmem_slot;
   __shared__ volatile int s_fail;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) tmem_alloc_cta(&tmem_slot);
   if (tid == 0) {
     mbar_init(&b_bar, 1);
@@ -343,92 +368,95 @@ __global__ void __launch_bounds__(WT, 1) k_rot_wide(const WRotArgs A) {
   const uint32_t taddr = tmem_slot;
   const int row = tid & 127, ch = tid >> 7;
   const uint32_t lane_base = (uint32_t)(32 * (warp & 3)) << 16;
-  const int Rw = A.cplx ? 2 * A.nv : A.nv;   // reals per row
-  double* stage = A.stage + (size_t)blockIdx.x * 128 * Rw;
+  float2* stage = A.stage + (size_t)blockIdx.x * A.nob * 128 * WN;
   double* Xd = reinterpret_cast<double*>(A.X);
   const long long ldr = (long long)A.ldx * (A.cplx ? 2 : 1);
   const long long tiles = (A.n + 127) / 128;
-  int it = 0;
+  long long it = 0;   // rounds so far: the phase of both barriers
   bool b_out = false, mma_out = false;
   for (long long tile = blockIdx.x; tile < tiles && !s_fail; tile += gridDim.x) {
     const long long r0 = tile * 128;
     const int nr = (int)min(128ll, A.n - r0);
-    for (int ob = 0; ob < A.nob && !s_fail; ++ob) {
-      f2 R[32];
+    for (int kc = 0; kc < A.nkc && !s_fail; ++kc) {
+      {   // A digits of the chunk: warp w takes rows 16 w .. 16 w + 15, lane l the K entries 2 l, 2 l + 1
+        double v[32];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) R[j] = f2{0.0f, 0.0f};
-      for (int kc = 0; kc < A.nkc; ++kc, ++it) {
+        for (int i = 0; i < 16; ++i) {
+          const int r = warp * 16 + i;
+          const bool ok = r < nr;
+          v[2 * i] = ok ? rot_op(A.X, A.ldx, r0 + r, kc, 2 * lane, A.nv, A.cplx) : 0.0;
+          v[2 * i + 1] = ok ? rot_op(A.X, A.ldx, r0 + r, kc, 2 * lane + 1, A.nv, A.cplx) : 0.0;
+        }
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int r = warp * 16 + i;
+          const int mex = (int)__reduce_max_sync(0xffffffffu, (unsigned)max(bexp(v[2 * i]), bexp(v[2 * i + 1])));
+          const int E = mex ? mex - 1022 : 0;
+          if (lane == 0) sE[r] = E;
+          put_pair(sA, PLA, r, 2 * lane, v[2 * i], v[2 * i + 1], E);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncthreads();
+      for (int ob = 0; ob < A.nob; ++ob, ++it) {
+        if (!rot_active(A, kc, ob)) { --it; continue; }
         const size_t blk = (size_t)kc * A.nob + ob;
-        if (tid == 0) {   // the B digits of (kc, ob) arrive while the A digits are cut
+        if (tid < WN) Fexp[tid] = A.bex[blk * WN + tid];
+        if (tid == 0) {   // the round's B digits, then its 112 MMAs
           mbar_expect_tx(&b_bar, (uint32_t)(OZ_S * PLB));
           bulk_copy(smem_u32(sB), A.bpl + blk * OZ_S * PLB, (uint32_t)(OZ_S * PLB), &b_bar);
-        }
-        b_out = true;
-        if (tid < WN) Fexp[tid] = A.bex[blk * WN + tid];
-        {   // A digits: thread (row r, half h of the 64 K entries), a common exponent per row; register
-            // u holds entry h 32 + (u + 2 s) mod 32, s = (r / 8) mod 4, so that the lanes of a warp
-            // store to 32 different banks
-          const int r = tid & 127, h = tid >> 7, sh = 2 * ((r >> 3) & 3);
-          double v[32];
-          int mex = 0;
-#pragma unroll
-          for (int u = 0; u < 32; ++u) {
-            v[u] = r < nr ? rot_op(A.X, A.ldx, r0 + r, kc, h * 32 + ((u + sh) & 31), A.nv, A.cplx) : 0.0;
-            mex = max(mex, bexp(v[u]));
-          }
-          sEh[h][r] = mex;
-          __syncthreads();
-          mex = max(sEh[0][r], sEh[1][r]);
-          const int E = mex ? mex - 1022 : 0;
-          if (h == 0) sE[r] = E;
-#pragma unroll
-          for (int q = 0; q < 16; ++q)
-            put_pair(sA, PLA, r, h * 32 + ((2 * q + sh) & 31), v[2 * q], v[2 * q + 1], E);
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (tid == 0) {
+          b_out = true;
           if (mbar_wait(&b_bar, (uint32_t)(it & 1), &s_fail)) {
             b_out = false;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             issue_round(taddr, smem_u32(sA), smem_u32(sB));
             mma_commit(&mma_bar);
-            mma_out = true;
+          } else {
+            s_fail = 1;
           }
         }
         __syncthreads();
         if (s_fail) break;
-        b_out = false;
         mma_out = true;
         const bool ok = mbar_wait(&mma_bar, (uint32_t)(it & 1), &s_fail);
         if (__syncthreads_or(!ok)) { s_fail = 1; break; }
         mma_out = false;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        f2 R[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) R[j] = f2{0.0f, 0.0f};
         add_levels(taddr, lane_base, ch, sE[row], Fexp, R);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncthreads();
-      }
-      if (s_fail) break;
-      // this block's 64 output columns of the tile into the stage
-      if (row < nr) {
+        // the block's partial sums of (row, 32 columns ch 32 ..): 256 contiguous bytes per thread
+        float4* st = reinterpret_cast<float4*>(stage + ((size_t)ob * 128 + row) * WN + ch * 32);
+        if (kc == 0) {
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const int col = ch * 32 + j;
-          if (!A.cplx) {
-            const int c = ob * WN + col;
-            if (c < A.nv) stage[(size_t)row * Rw + c] = f2_to(R[j]);
-          } else {
-            const int c = (ob >> 1) * WN + col;
-            if (c < A.nv) stage[(size_t)row * Rw + 2 * c + (ob & 1)] = f2_to(R[j]);
+          for (int j = 0; j < 16; ++j) st[j] = make_float4(R[2 * j].h, R[2 * j].l, R[2 * j + 1].h, R[2 * j + 1].l);
+        } else {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const float4 o = st[j];
+            const f2 a = f2_add(f2{o.x, o.y}, R[2 * j]), b = f2_add(f2{o.z, o.w}, R[2 * j + 1]);
+            st[j] = make_float4(a.h, a.l, b.h, b.l);
           }
         }
+        __syncthreads();
       }
     }
-    __syncthreads();
-    if (!s_fail)   // every output block of the tile is done: its rows of X can change now
-      for (int t = tid; t < nr * Rw; t += WT) {
-        const int r = t / Rw, f = t % Rw;
-        Xd[(r0 + r) * ldr + f] = stage[(size_t)r * Rw + f];
+    if (s_fail) break;
+    // every chunk of the tile is done: its rows of X from the stage (a thread per real of a row)
+    for (int ob = 0; ob < A.nob; ++ob)
+      for (int t = tid; t < nr * WN; t += WT) {
+        const int r = t / WN, col = t % WN;
+        const float2 v = stage[((size_t)ob * 128 + r) * WN + col];
+        const double x = f2_to(f2{v.x, v.y});
+        if (!A.cplx) {
+          const int c = ob * WN + col;
+          if (c < A.nv) Xd[(r0 + r) * ldr + c] = x;
+        } else {
+          const int c = (ob >> 1) * WN + col;
+          if (c < A.nv) Xd[(r0 + r) * ldr + 2 * c + (ob & 1)] = x;
+        }
       }
     __syncthreads();
   }
@@ -468,14 +496,21 @@ int finish_wide(oefe_ctx* c, const char* what) {
 
 }  // namespace
 
-// out = X^+ W (nv x nv) on the tensor cores, any nv
+// out = X^+ W (nv x nv) on the tensor cores, any nv; herm: the result is known to be Hermitian
+// (real data: only the tiles meeting the upper triangle run, the rest is mirrored)
 template <typename S>
-int gram_ozaki_wide(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out) {
+int gram_ozaki_wide(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64_t n, int nv, S* out, bool herm) {
   constexpr bool CPLX = sizeof(S) == sizeof(cd);
   const int NA = CPLX ? 2 * nv : nv;
   const int nI = (NA + 127) / 128, nJ = (NA + WN - 1) / WN;
+  const bool upper = herm && !CPLX;
+  int ntile = nI * nJ;
+  if (upper) {
+    ntile = 0;
+    for (int I = 0; I < nI; ++I) ntile += std::max(0, nJ - 2 * I);
+  }
   const long long passes = std::max<long long>(1, (n + 63) / 64);
-  const int nbx = (int)std::max<long long>(1, std::min<long long>(passes, c->num_sms / std::max(1, nI * nJ)));
+  const int nbx = (int)std::max<long long>(1, std::min<long long>(passes, c->num_sms / std::max(1, ntile)));
   const long long ppc = (passes + nbx - 1) / nbx;
   const size_t need = (size_t)nbx * nI * nJ * 128 * WN * sizeof(double);
   OEFE_TRY(grow_ozpart(c, need));
@@ -489,14 +524,15 @@ int gram_ozaki_wide(oefe_ctx* c, const S* X, int ldx, const S* W, int ldw, int64
   A.cplx = CPLX;
   A.nI = nI;
   A.nJ = nJ;
+  A.upper = upper;
   A.passes = passes;
   A.ppc = ppc;
   A.part = (double*)c->d_ozpart;
   A.err = c->d_status + 2;
   OEFE_CUDA_TRY(c, cudaFuncSetAttribute(k_gram_wide, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)WSMEM));
-  dim3 grid(nbx, nI * nJ);
+  dim3 grid(nbx, ntile);
   OEFE_COUNTED k_gram_wide<<<grid, WT, WSMEM, c->stream>>>(A);
-  OEFE_COUNTED k_gram_wide_reduce<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(A.part, nbx, nI, nJ, nv, out);
+  OEFE_COUNTED k_gram_wide_reduce<S><<<(nv * nv + 255) / 256, 256, 0, c->stream>>>(A.part, nbx, nI, nJ, nv, upper, out);
   return finish_wide(c, "gram");
 }
 
@@ -508,10 +544,9 @@ int rotate_ozaki_wide(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C,
   const int nob = CPLX ? 2 * ((nv + WN - 1) / WN) : (nv + WN - 1) / WN;
   const long long tiles = (n + 127) / 128;
   const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, c->num_sms));
-  const int Rw = CPLX ? 2 * nv : nv;
   auto a256 = [](size_t x) { return ((x + 255) / 256) * 256; };
   const size_t pl_bytes = a256((size_t)nkc * nob * OZ_S * PLB), ex_bytes = a256((size_t)nkc * nob * WN * sizeof(int));
-  const size_t st_bytes = a256((size_t)grid * 128 * Rw * sizeof(double));
+  const size_t st_bytes = a256((size_t)grid * nob * 128 * WN * sizeof(float2));
   OEFE_TRY(grow_ozpart(c, pl_bytes + ex_bytes + st_bytes));
   unsigned char* base = (unsigned char*)c->d_ozpart;
   WRotArgs A;
@@ -522,9 +557,10 @@ int rotate_ozaki_wide(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C,
   A.cplx = CPLX;
   A.nkc = nkc;
   A.nob = nob;
+  A.herm = herm;
   A.bpl = base;
   A.bex = (const int*)(base + pl_bytes);
-  A.stage = (double*)(base + pl_bytes + ex_bytes);
+  A.stage = (float2*)(base + pl_bytes + ex_bytes);
   A.err = c->d_status + 2;
   const long long nb = (long long)nkc * nob * WN;
   OEFE_COUNTED k_rot_wide_bdigits<S><<<(unsigned)((nb + 127) / 128), 128, 0, c->stream>>>(C, nv, herm, nkc, nob, base,
@@ -534,7 +570,7 @@ int rotate_ozaki_wide(oefe_ctx* c, S* X, int ldx, int64_t n, int nv, const S* C,
   return finish_wide(c, "rotate");
 }
 
-template int gram_ozaki_wide<double>(oefe_ctx*, const double*, int, const double*, int, int64_t, int, double*);
-template int gram_ozaki_wide<cd>(oefe_ctx*, const cd*, int, const cd*, int, int64_t, int, cd*);
+template int gram_ozaki_wide<double>(oefe_ctx*, const double*, int, const double*, int, int64_t, int, double*, bool);
+template int gram_ozaki_wide<cd>(oefe_ctx*, const cd*, int, const cd*, int, int64_t, int, cd*, bool);
 template int rotate_ozaki_wide<double>(oefe_ctx*, double*, int, int64_t, int, const double*, bool);
 template int rotate_ozaki_wide<cd>(oefe_ctx*, cd*, int, int64_t, int, const cd*, bool);

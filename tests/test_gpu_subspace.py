@@ -46,7 +46,7 @@ def test_orthonormalize(k, products):
     assert rel(Q, Qo) < 1e-10 * f
 
 
-@pytest.mark.parametrize("case", ["c1_real_64", "complex_24", "complex_64", "real_150", "complex_100"])
+@pytest.mark.parametrize("case", ["c1_real_64", "complex_24", "complex_64", "real_150", "real_300", "complex_100"])
 def test_orthonormalize_tensor_core_gram(case):  # Gram and rotations on the tensor cores
     # pair mode takes the Gram matrices on the tensor cores (exact bf16 digits, about 2^-46 of the
     # row and column maxima per term): Q^+ M Q = I and Q against the native FP64 path within the
@@ -59,9 +59,10 @@ def test_orthonormalize_tensor_core_gram(case):  # Gram and rotations on the ten
     elif case == "complex_64":
         prs, ctx, V, _ = paired(ks=[(0.25, -0.4, 0.1)], n=4, a=8.0)
         nv = 64
-    elif case == "real_150":   # wider than one digit tile: the digits cut inside the MMA kernels
+    elif case in ("real_150", "real_300"):   # wider than one digit tile: the digits cut inside the MMA
+        # kernels; a real Gram matrix runs only its tiles that meet the upper triangle (4 of 6, 9 of 15)
         prs, ctx, V, _ = paired(n=4, a=8.0)
-        nv = 150
+        nv = int(case.split("_")[1])
     elif case == "complex_100":
         prs, ctx, V, _ = paired(ks=[(0.25, -0.4, 0.1)], n=4, a=8.0)
         nv = 100
