@@ -296,6 +296,17 @@ int oefe_density(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, co
  * respect to conj(X) is H^O X (oefe_apply_h). */
 int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* gV);
 
+/* oefe_density_grad -- oefe_density and, from the same evaluation of the fields
+ * at the quadrature points, oefe_band_trace_grad of k-point ik's block X[ik]:
+ * rho as oefe_density, gV (device, nq_total doubles, overwritten) =
+ * w_q sum_v |u_v(x_q)|^2 over the columns of X[ik] (Eq. rho; the adjoint of
+ * Eq. HOEFEelelements with respect to V). Same arguments as oefe_density plus
+ * ik (0 <= ik < nk) and gV (non-NULL); the results equal those of the two
+ * separate calls (same arithmetic per point), at the cost of one pass over
+ * the fields of X[ik] instead of two. */
+int oefe_density_grad(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, const int* ld, int dtype,
+                      const double* occ, double* rho, int ik, double* gV);
+
 /* oefe_band_trace -- e (host, one double) = tr(X^+ H^O X) = Re sum_v x_v^+ H^O x_v,
  * the band-energy trace whose V-gradient oefe_band_trace_grad returns
  * (Eq. HOEFEelelements). HX: device (n x ld, the dtype of X) receiving H^O X,
@@ -386,7 +397,8 @@ int oefe_launch_count(int64_t* n);
  *   - tensor-core GEMMs with exact bf16 digits (7 digits of 7 bits per value,
  *     exact FP32 accumulation, about 2^-46 of the row and column maxima per
  *     term) for the Gram matrices and rotations of oefe_orthonormalize and
- *     oefe_rayleigh_ritz when nv <= 64 (FP32 pairs otherwise).
+ *     oefe_rayleigh_ritz (digits cut into planes for nv <= 64, inside the MMA
+ *     kernels for wider blocks).
  * Inputs and outputs stay FP64; Cholesky factors, triangular inverses and the
  * setup stay FP64. The operator must be built with OEFE_STORE_F64PAIR in pair
  * mode, else the products return OEFE_ERR_STATE; the build after the switch

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("oefe_rayleigh_ritz", _I, [_P, _I, _P, _I, _I, _I, _DP, _DP]),
     ("oefe_density", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP, _P]),
     ("oefe_band_trace_grad", _I, [_P, _I, _P, _I, _I, _I, _P]),
+    ("oefe_density_grad", _I, [_P, _I, _c.POINTER(_P), _IP, _IP, _I, _DP, _P, _I, _P]),
     ("oefe_band_trace", _I, [_P, _I, _P, _I, _I, _I, _DP, _P]),
     ("oefe_band_trace_vjp", _I, [_P, _I, _P, _I, _I, _I, _D, _P, _P]),
     ("oefe_apply_h_vjp", _I, [_P, _I, _P, _P, _P, _P, _I, _I, _I]),
@@ -349,7 +350,8 @@ class Context:
                                                 _dp(res) if resid else None))
         return (eig, res) if resid else eig
 
-    def density(self, Xs, occ, rho):
+    @staticmethod
+    def _density_args(Xs, occ):
         ptrs, nvs, lds, dts = [], [], [], []
         for X in Xs:
             p, nv, ld, dt = _block(X)
@@ -362,9 +364,21 @@ class Context:
         lds = np.array(lds, np.int32)
         occ = np.ascontiguousarray(np.concatenate([np.asarray(o, np.float64) for o in occ]))
         dtype = C128 if C128 in dts else F64
-        self._check(self.lib.oefe_density(self.h, len(ptrs), arr, _ip(nvs), _ip(lds), dtype, _dp(occ),
+        return arr, nvs, lds, dtype, occ
+
+    def density(self, Xs, occ, rho):
+        arr, nvs, lds, dtype, occ = self._density_args(Xs, occ)
+        self._check(self.lib.oefe_density(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dtype, _dp(occ),
                                           ctypes.c_void_p(rho.data_ptr())))
         return rho
+
+    def density_grad(self, Xs, occ, rho, ik, gV):
+        """rho (as density) and gV = band_trace_grad(ik, Xs[ik]) from one pass over the fields."""
+        arr, nvs, lds, dtype, occ = self._density_args(Xs, occ)
+        self._check(self.lib.oefe_density_grad(self.h, len(Xs), arr, _ip(nvs), _ip(lds), dtype, _dp(occ),
+                                               ctypes.c_void_p(rho.data_ptr()), int(ik),
+                                               ctypes.c_void_p(gV.data_ptr())))
+        return rho, gV
 
     def band_trace_grad(self, ik, X, gV):
         px, nv, ld, dt = _block(X)

@@ -289,6 +289,13 @@ int oefe_density(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, co
   return density(ctx, nk, X, nv, ld, dtype, occ, rho);
 }
 
+int oefe_density_grad(oefe_ctx_t ctx, int nk, const void* const* X, const int* nv, const int* ld, int dtype,
+                      const double* occ, double* rho, int ik, double* gV) {
+  CTX_CHECK(ctx);
+  if (!gV) { ctx->err = "density_grad: need gV"; return OEFE_ERR_ARG; }
+  return density_grad(ctx, nk, X, nv, ld, dtype, occ, rho, ik, gV);
+}
+
 int oefe_band_trace_grad(oefe_ctx_t ctx, int ik, const void* X, int nv, int ld, int dtype, double* gV) {
   CTX_CHECK(ctx);
   return band_trace_grad(ctx, ik, X, nv, ld, dtype, gV);

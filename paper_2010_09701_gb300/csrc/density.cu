@@ -160,6 +160,9 @@ struct FieldArgs {
   double* out;        // nq
   bool accumulate;    // density: out += ; gradient: out =
   double scale;       // gradient: out = scale w_q (...)
+  // with the density (occ set, accumulate): out2 (nq, overwritten, or null) = w_q sum_v |u_v|^2 of
+  // the same fields, the band-trace gradient of these columns
+  double* out2;
   // cross mode (X2 != null): a pass of RNB takes RNB/2 columns of X and the same columns of X2; the
   // point's sum is Re sum_v conj(u_X2,v) u_X,v instead of sum_v |u_X,v|^2
   const void* X2;
@@ -184,7 +187,9 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
   V* T1 = Xo + (size_t)A.ne_max * J;               // n1 * P * P * J   [qx][b][c][j]
   V* T2 = T1 + (size_t)n1m * P * P * J;            // n2 * P * J       [qx][qy][c][j]
   V* U = T2 + (size_t)n1m * n1m * P * J;           // n3 * J
-  V* rho = U + (size_t)n1m * n1m * n1m * J;        // 2 x n3: one per half of the vectors
+  V* rho = U + (size_t)n1m * n1m * n1m * J;        // 2 x n3: one per half of the vectors (4 x n3
+                                                   // with out2: the unweighted sums after them)
+  const bool dual = A.out2 != nullptr;
   for (int li = blockIdx.x; li < A.nleaves; li += gridDim.x) {
     const Leaf L = A.leaves[li];
     const int e = L.cell;
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
       lagrange_eval(xn, P, xi, Lv, Dv);
       for (int a = 0; a < P; ++a) Lt[d][i][a] = v_from<V>(Lv[a]);
     }
-    for (int q = threadIdx.x; q < 2 * n3; q += FT) rho[q] = v_from<V>(0.0);
+    for (int q = threadIdx.x; q < (dual ? 4 : 2) * n3; q += FT) rho[q] = v_from<V>(0.0);
     const size_t blk = (size_t)L.q0 * A.ne_max;
     const bool cross = A.X2 != nullptr;
     constexpr int HV = RNB / 2, HJ = HV * R;
@@ -324,6 +329,7 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
           }
         }
         V s = rho[h * n3 + q];
+        V s2 = dual ? rho[(2 + h) * n3 + q] : v_from<V>(0.0);
         if (cross) {
           // the partner item (same point, other half: adjacent threads of one warp, both active)
           // holds the X2 fields of the same columns; the X half takes Re conj(u_X2) u_X
@@ -361,9 +367,11 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
             }
             const V w = v_from<V>(A.occ ? A.occ[v] : 1.0);
             s = v_add(s, v_mul(w, v_fin(m)));
+            if (dual) s2 = v_add(s2, v_fin(m));
           }
         }
         rho[h * n3 + q] = s;
+        if (dual) rho[(2 + h) * n3 + q] = s2;
       }
     }
     __syncthreads();
@@ -372,17 +380,18 @@ __global__ void __launch_bounds__(FT) k_fields(FieldArgs A) {
       const double r = v_to(v_add(rho[q], rho[n3 + q]));
       if (A.accumulate) A.out[qg] += r;
       else A.out[qg] = A.scale * A.qw[qg] * r;
+      if (dual) A.out2[qg] = A.qw[qg] * v_to(v_add(rho[2 * n3 + q], rho[3 * n3 + q]));
     }
   }
 }
 
 template <typename V>
-size_t field_smem(const oefe_ctx* c, bool cplx, int rnb) {
+size_t field_smem(const oefe_ctx* c, bool cplx, int rnb, bool dual = false) {
   const int n1 = std::max(c->nq_cell, c->nq_enr), P = c->P;
   const size_t J = (size_t)rnb * (cplx ? 2 : 1);
   const size_t n3 = (size_t)n1 * n1 * n1;
   return ((size_t)c->nloc * J + (size_t)std::max(c->ne_max, 1) * J + (size_t)n1 * P * P * J +
-          (size_t)n1 * n1 * P * J + n3 * J + 2 * n3) * sizeof(V);
+          (size_t)n1 * n1 * P * J + n3 * J + (dual ? 4 : 2) * n3) * sizeof(V);
 }
 
 }  // namespace
@@ -431,7 +440,7 @@ int ensure_orth_enrichment(oefe_ctx* c, KData& K) {
 namespace {
 
 int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, const double* occ, double* out,
-               bool accumulate, double scale = 1.0, const void* X2 = nullptr, int ld2 = 0) {
+               bool accumulate, double scale = 1.0, const void* X2 = nullptr, int ld2 = 0, double* out2 = nullptr) {
   OEFE_TRY(ensure_orth_enrichment(c, K));
   const bool pairs = c->f64_products == OEFE_F64_PAIRS;
   const bool cplx = dtype == OEFE_C128;
@@ -460,6 +469,8 @@ int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, 
   A.scale = scale;
   A.X2 = X2;
   A.ld2 = ld2;
+  A.out2 = out2;
+  const bool dual = out2 != nullptr;
   const int grid = std::max(1, std::min((int)c->leaves.size(), c->num_sms));
   auto go = [&](auto kern, size_t smem) -> int {
     if (smem > 227 * 1024) { c->err = "fields: quadrature too large for the interpolation tiles"; return OEFE_ERR_ARG; }
@@ -471,16 +482,19 @@ int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, 
   if (pairs) {
     // two pass widths, the faster kept after timing both at first use (same arithmetic per vector)
     auto run = [&](int v) -> int {
-      if (cplx) return v == 0 ? go(k_fields<f2, true, 4>, field_smem<f2>(c, true, 4))
-                              : go(k_fields<f2, true, 2>, field_smem<f2>(c, true, 2));
-      return v == 0 ? go(k_fields<f2, false, 4>, field_smem<f2>(c, false, 4))
-                    : go(k_fields<f2, false, 2>, field_smem<f2>(c, false, 2));
+      if (v == 0 && field_smem<f2>(c, cplx, 4, dual) > 227 * 1024) v = 1;   // the wide pass does not fit
+      if (cplx) return v == 0 ? go(k_fields<f2, true, 4>, field_smem<f2>(c, true, 4, dual))
+                              : go(k_fields<f2, true, 2>, field_smem<f2>(c, true, 2, dual));
+      return v == 0 ? go(k_fields<f2, false, 4>, field_smem<f2>(c, false, 4, dual))
+                    : go(k_fields<f2, false, 2>, field_smem<f2>(c, false, 2, dual));
     };
     if (c->fields_variant < 0 && accumulate) {   // the density accumulates: time on a scratch copy of out
       double* scratch = nullptr;
       OEFE_TRY(dev_alloc(c, (void**)&scratch, (size_t)std::max<int64_t>(c->nq, 1) * sizeof(double)));
       double* keep = A.out;
+      double* keep2 = A.out2;
       A.out = scratch;
+      A.out2 = nullptr;
       cudaEvent_t ev[3];
       for (auto& e : ev) OEFE_CUDA_TRY(c, cudaEventCreate(&e));
       int s = run(0);
@@ -497,12 +511,17 @@ int run_fields(oefe_ctx* c, KData& K, const void* X, int nv, int ld, int dtype, 
       cudaStreamSynchronize(c->stream);
       dev_free(scratch);
       A.out = keep;
+      A.out2 = keep2;
       if (s != OEFE_OK) return s;
     }
     return run(c->fields_variant > 0 ? 1 : 0);
   }
-  if (cplx) return go(k_fields<double, true, 4>, field_smem<double>(c, true, 4));
-  return go(k_fields<double, false, 4>, field_smem<double>(c, false, 4));}
+  if (cplx) {
+    if (field_smem<double>(c, true, 4, dual) > 227 * 1024) return go(k_fields<double, true, 2>, field_smem<double>(c, true, 2, dual));
+    return go(k_fields<double, true, 4>, field_smem<double>(c, true, 4, dual));
+  }
+  return go(k_fields<double, false, 4>, field_smem<double>(c, false, 4, dual));
+}
 
 int check_fields(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) {
   if (!c->has_k) { c->err = "call oefe_kpoints first"; return OEFE_ERR_STATE; }
@@ -515,12 +534,13 @@ int check_fields(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype) 
 
 }  // namespace
 
-int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype, const double* occ,
-            double* rho) {
+int density_grad(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype, const double* occ,
+                 double* rho, int ik_grad, double* gV) {
   if (nk != (int)c->kd.size() || !X || !nv || !ld || !occ || !rho) {
     c->err = "density: need one X, nv, ld per k-point, occ and rho";
     return OEFE_ERR_ARG;
   }
+  if (gV && (ik_grad < 0 || ik_grad >= nk)) { c->err = "density: gradient k index out of range"; return OEFE_ERR_ARG; }
   int tot = 0;
   for (int ik = 0; ik < nk; ++ik) {
     const int dt = c->kd[ik].cplx ? OEFE_C128 : OEFE_F64;
@@ -535,12 +555,18 @@ int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int*
   int off = 0, st = OEFE_OK;
   for (int ik = 0; ik < nk && st == OEFE_OK; ++ik) {
     const int dt = c->kd[ik].cplx ? OEFE_C128 : OEFE_F64;
-    st = run_fields(c, c->kd[ik], X[ik], nv[ik], ld[ik], dt, d_occ + off, rho, true);
+    st = run_fields(c, c->kd[ik], X[ik], nv[ik], ld[ik], dt, d_occ + off, rho, true, 1.0, nullptr, 0,
+                    ik == ik_grad ? gV : nullptr);
     off += nv[ik];
   }
   cudaStreamSynchronize(c->stream);
   dev_free(d_occ);
   return st;
+}
+
+int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype, const double* occ,
+            double* rho) {
+  return density_grad(c, nk, X, nv, ld, dtype, occ, rho, -1, nullptr);
 }
 
 int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* gV) {

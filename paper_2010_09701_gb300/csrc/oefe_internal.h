@@ -314,6 +314,8 @@ int upper_bound(oefe_ctx* c, int ik, const void* v0, int steps, int flags, doubl
 // fields (density.cu)
 int density(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype,
             const double* occ, double* rho);
+int density_grad(oefe_ctx* c, int nk, const void* const* X, const int* nv, const int* ld, int dtype, const double* occ,
+                 double* rho, int ik_grad, double* gV);
 int band_trace_grad(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* gV);
 // adjoint.cu
 int band_trace(oefe_ctx* c, int ik, const void* X, int nv, int ld, int dtype, double* e, void* HX);

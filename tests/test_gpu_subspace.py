@@ -260,6 +260,34 @@ def test_density_two_kpoints():
     assert rel(rho.cpu().numpy(), rho_o) < 1e-12
 
 
+@pytest.mark.parametrize("products", ["native", "pairs"])
+def test_density_grad_one_field_pass(products):
+    # density over two k-points and the band-trace gradient of the second from the same field pass:
+    # the oracle's density and gradient, and the separate calls' results (same arithmetic per point)
+    from paper_2010_09701_gb300 import F64_NATIVE, F64_PAIRS
+    ks = [(0.3, 0.0, 0.0), (-0.3, 0.1, 0.0)]
+    prs, ctx, V, Vd = paired(ks=ks)
+    ctx.set_f64_products(F64_PAIRS if products == "pairs" else F64_NATIVE)
+    tol = 3.2e-12 if products == "pairs" else 1e-12
+    Xs = [W.random_vectors(pr.n, 5 + i, complex_=True, seed=40 + i) for i, pr in enumerate(prs)]
+    occs = [np.array([1.0, 1.0, 0.5, 0.25, 0.0]) * 0.5, np.array([1.0, 0.9, 0.5, 0.1, 0.0, 0.0]) * 0.5]
+    Xd = [to_gpu(x) for x in Xs]
+    nq = prs[0].quad.nq
+    rho = torch.zeros(nq, dtype=torch.float64, device="cuda")
+    g = torch.full((nq,), 7.0, dtype=torch.float64, device="cuda")   # overwritten
+    ctx.density_grad(Xd, occs, rho, 1, g)
+    assert rel(rho.cpu().numpy(), solver.density(prs, Xs, occs)) < tol
+    assert rel(g.cpu().numpy(), solver.band_trace_grad_V(prs[1], Xs[1])) < tol
+    rho1 = torch.zeros_like(rho)
+    g1 = torch.zeros_like(rho)
+    ctx.density(Xd, occs, rho1)
+    ctx.band_trace_grad(1, Xd[1], g1)
+    assert rel(rho.cpu().numpy(), rho1.cpu().numpy()) < 1e-14 and rel(g.cpu().numpy(), g1.cpu().numpy()) < 1e-14
+    with pytest.raises(Exception):
+        ctx.density_grad(Xd, occs, rho, 2, g)
+    ctx.set_f64_products(F64_NATIVE)
+
+
 @pytest.mark.parametrize("k", KS)
 def test_autograd_band_trace(k):
     from paper_2010_09701_gb300.autograd import apply_h, band_trace
