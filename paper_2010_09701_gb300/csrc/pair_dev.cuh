@@ -13,12 +13,14 @@
 
 namespace {
 
-struct f2 {
+// 8-byte aligned, so that a pair moves as one 64-bit load or store (two 32-bit accesses to
+// interleaved words would take twice the shared-memory wavefronts)
+struct alignas(8) f2 {
   float h, l;
 };
 
 // accumulator: h holds the running sum, l the collected rounding errors (normalized by f2_fin)
-struct f2acc {
+struct alignas(8) f2acc {
   float h, l;
 };
 

@@ -165,16 +165,20 @@ __global__ void __launch_bounds__(NT) k_cell_apply_sf(const SfArgs A) {
     const int EC = (naug + nch - 1) / nch;
     V* part = Ab;                                          // (ne * nch) x J partial sums
     for (int it = threadIdx.x; it < nloc + ne * nch; it += NT) {
-      int r, ca, cb;
+      int r, ca, cb, pidx = 0;
       if (it < nloc) {
         r = it;
         ca = nloc;
         cb = naug;
       } else {
-        const int q = it - nloc;
-        r = nloc + q / nch;
-        ca = (q % nch) * EC;
+        // consecutive items take the same chunk of consecutive enrichment rows, so that a warp reads
+        // one row of the vectors per column (a broadcast) instead of one per chunk (chunks a multiple
+        // of 128 bytes apart fall in the same banks)
+        const int q = it - nloc, ch = q / ne, i = q % ne;
+        r = nloc + i;
+        ca = ch * EC;
         cb = min(naug, ca + EC);
+        pidx = i * nch + ch;
       }
       Acc y[J];
 #pragma unroll
@@ -224,7 +228,7 @@ __global__ void __launch_bounds__(NT) k_cell_apply_sf(const SfArgs A) {
         }
       } else {
 #pragma unroll
-        for (int j = 0; j < J; ++j) part[(size_t)(it - nloc) * J + j] = v_fin(y[j]);
+        for (int j = 0; j < J; ++j) part[(size_t)pidx * J + j] = v_fin(y[j]);
       }
     }
     __syncthreads();
