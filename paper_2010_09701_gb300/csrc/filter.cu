@@ -339,6 +339,78 @@ __global__ void __launch_bounds__(256) k_node_update_multi(const NodeK* __restri
                    (!has_k || (ldk % 4 == 0 && ((uintptr_t)Xk & 15) == 0)) &&
                    (!has_m1 || (ldm1 % 4 == 0 && ((uintptr_t)Xm1 & 15) == 0)) &&
                    (!has_r || (ldr % 4 == 0 && ((uintptr_t)Rr & 15) == 0));
+  if (vec && W <= 128) {
+    // one float4 per lane covers a row: two nodes per pass of the warp, so that the dependent loads
+    // of the two (slot range, slot indices, product rows) overlap; per node the same operations in
+    // the same order as the general loop below
+    const int f = 4 * lane;
+    const bool act = f < W;
+    for (int64_t g0 = warp0; g0 < nh; g0 += 2 * nwarps) {
+      const int64_t gg[2] = {g0, g0 + nwarps};
+      const bool ok[2] = {true, g0 + nwarps < nh};
+      int64_t s0[2];
+      int ns[2];
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        s0[u] = ok[u] ? node_off[gg[u]] : 0;
+        ns[u] = (ok[u] && has_z) ? (int)(node_off[gg[u] + 1] - s0[u]) : 0;
+      }
+      float4 acc[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
+      const int nsm = max(ns[0], ns[1]);
+      for (int s8 = 0; s8 < nsm; s8 += 4) {   // four slots per node at a time (most rows have one or two)
+        int64_t sl[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) sl[u][i] = s8 + i < ns[u] ? node_slot[s0[u] + s8 + i] : -1;
+        float4 z[2][4];
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            z[u][i] = (sl[u][i] >= 0 && act) ? *reinterpret_cast<const float4*>((const float*)Z + sl[u][i] * W + f)
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            acc[u].x += z[u][i].x;
+            acc[u].y += z[u][i].y;
+            acc[u].z += z[u][i].z;
+            acc[u].w += z[u][i].w;
+          }
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!ok[u] || !act) continue;
+        const int64_t g = gg[u];
+        const T minv = (T)(1.0 / m[g]);
+        const float4 xk = has_k ? *reinterpret_cast<const float4*>((const float*)Xk + g * ldk + f)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 o;
+        o.x = (float)alpha * (acc[u].x * (float)minv - (float)cs * xk.x);
+        o.y = (float)alpha * (acc[u].y * (float)minv - (float)cs * xk.y);
+        o.z = (float)alpha * (acc[u].z * (float)minv - (float)cs * xk.z);
+        o.w = (float)alpha * (acc[u].w * (float)minv - (float)cs * xk.w);
+        if (has_m1) {
+          const float4 xm = *reinterpret_cast<const float4*>((const float*)Xm1 + g * ldm1 + f);
+          o.x += (float)beta * xm.x;
+          o.y += (float)beta * xm.y;
+          o.z += (float)beta * xm.z;
+          o.w += (float)beta * xm.w;
+        }
+        if (has_r) {
+          const float4 r = *reinterpret_cast<const float4*>((const float*)Rr + g * ldr + f);
+          o.x += (float)alpha * coef[(f + 0) / R] * r.x;
+          o.y += (float)alpha * coef[(f + 1) / R] * r.y;
+          o.z += (float)alpha * coef[(f + 2) / R] * r.z;
+          o.w += (float)alpha * coef[(f + 3) / R] * r.w;
+        }
+        *reinterpret_cast<float4*>((float*)Y + g * ldy + f) = o;
+      }
+    }
+    return;
+  }
   for (int64_t g = warp0; g < nh; g += nwarps) {
     const int64_t s0 = node_off[g];
     const int ns = has_z ? (int)(node_off[g + 1] - s0) : 0;
