@@ -240,7 +240,8 @@ def run_ours(args, rank, world):
     ctx.set_f64_products(P.F64_PAIRS if pairs else P.F64_NATIVE)
     ctx.set_product_shape(args.product_shape)
     if args.filter_only:   # profiling aid: the low-precision matrices (and FP64 ones on request) only
-        store = (split if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0)
+        store = ((split if args.tensor else P.STORE_F32) | (P.STORE_F64 if args.with_fp64 else 0) |
+                 (store & P.STORE_COMPACT))
         if args.with_fp64 and pairs:
             store |= P.STORE_F64PAIR
     progress("set up: %d dof, %d points; building (store %d)" % (n, len(qw), store))
@@ -269,8 +270,14 @@ def run_ours(args, rank, world):
     fflags = P.FILTER_LAST_FP64 | (P.FILTER_BF16X3 if args.tensor else 0)
     if args.filter_only:
         X32 = X0[0].to(ldt)
-        for _ in range(args.steps):
-            ctx.chebyshev_filter(0, X32, deg, a_lo, bks[0], a0, flags=P.FILTER_BF16X3 if args.tensor else 0)
+        if args.batched_filter:   # the batched launch on one group of at most 128 vectors, a fixed shape
+            ctx.set_filter_shape(args.filter_shape)
+            Xg = X32[:, :min(nvs[0], 128)].contiguous()
+            for _ in range(args.steps):
+                ctx.filter_batched([Xg], deg, [a_lo], [bks[0]], [a0], P.FILTER_BF16X3)
+        else:
+            for _ in range(args.steps):
+                ctx.chebyshev_filter(0, X32, deg, a_lo, bks[0], a0, flags=P.FILTER_BF16X3 if args.tensor else 0)
         if args.with_fp64:   # one FP64 operator application (the FP64 cell product)
             Y64 = torch.empty_like(X0[0])
             ctx.apply_h(0, X0[0], Y64)
@@ -733,7 +740,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c5", choices=["c2", "c3", "c3small", "c3mid", "c5", "c5mid"],
+    ap.add_argument("--config", default="c5", choices=["c2", "c3", "c3small", "c3mid", "c4mid", "c5", "c5mid"],
                     help="workload: c5 the large supercell the metric is quoted on (default), c3 the 8-atom cell "
                          "with 4 k-points")
     ap.add_argument("--compact", default="auto", choices=["auto", "on", "off"],
@@ -767,6 +774,11 @@ def main():
                          "products) or three parts (BF16x6, six products)")
     ap.add_argument("--fp32-simt", dest="tensor", action="store_false",
                     help="FP32 SIMT cell products instead of the BF16x3 tensor-core path")
+    ap.add_argument("--batched-filter", action="store_true",
+                    help="with --filter-only: the batched tensor-core filter on one group of at most 128 vectors "
+                         "of k-point 0 in the launch shape --filter-shape (profiling aid)")
+    ap.add_argument("--filter-shape", type=int, default=-1, choices=[-1, 0, 1, 2, 3, 4, 5],
+                    help="launch shape of the batched filter (oefe_set_filter_shape); -1: the default")
     ap.add_argument("--with-density", action="store_true",
                     help="with --filter-only: one density evaluation (profiling aid)")
     ap.add_argument("--with-ortho", action="store_true",

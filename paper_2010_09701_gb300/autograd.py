@@ -16,8 +16,9 @@ import torch
 
 
 def _ensure_built(ctx, V):
-    if ctx.built_from != (V.data_ptr(), V._version):
-        ctx.build_hamiltonian(V.detach())
+    # rebuilt (with the storage of the last build) unless the operator comes from these values of V
+    if not ctx.built_from(V):
+        ctx.build_hamiltonian(V.detach(), ctx.built_store)
 
 
 class BandTrace(torch.autograd.Function):

@@ -161,7 +161,7 @@ class Context:
         self.h = ctypes.c_void_p()
         self._check(self.lib.oefe_create(ctypes.byref(self.h), device, ctypes.c_void_p(stream)))
         self.nk = 0
-        self.built_from = None
+        self._built_v, self._built_version, self.built_store = None, -1, STORE_F64
 
     def _check(self, code):
         if code != OK:
@@ -241,7 +241,15 @@ class Context:
         if not (veff.is_cuda and veff.dtype == torch.float64 and veff.is_contiguous()):
             raise ValueError("veff must be a contiguous float64 CUDA tensor")
         self._check(self.lib.oefe_build_hamiltonian(self.h, ctypes.c_void_p(veff.data_ptr()), int(store)))
-        self.built_from = (veff.data_ptr(), veff._version)
+        # the potential of the build is held (so no other tensor can take its memory and pass for it)
+        # with its version counter, which changes on any in-place write
+        self._built_v, self._built_version, self.built_store = veff, veff._version, int(store)
+
+    def built_from(self, veff):
+        """True when the stored operator was built from this potential's current values."""
+        b = self._built_v
+        return (b is not None and b.data_ptr() == veff.data_ptr() and b.shape == veff.shape and
+                self._built_version == veff._version)
 
     def cell_info(self, cell):
         n = ctypes.c_int()

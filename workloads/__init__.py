@@ -153,6 +153,16 @@ def config_c3_mid():
     return w
 
 
+def config_c4_mid():
+    """The 16-atom cell of the batched-k configuration (8 complex k-points, 97-123 vectors each) on
+    a 12^3 graded mesh: the whole configuration at about a fifth of the mesh, since at 20^3 its
+    operator data, vectors and batched-filter workspaces exceed one device's memory."""
+    w = config_c4()
+    w.name = "c4mid_c64_8k_16atom_12cube_p6"
+    w.ncell = 12
+    return w
+
+
 def config_c5_mid():
     """The 62-atom divacancy supercell on a 16^3 graded mesh (about 0.9M nodes): a test case of the
     Gamma-point path with 360 vectors at an eighth of the large supercell's mesh."""
@@ -162,7 +172,8 @@ def config_c5_mid():
     return w
 
 
-CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c3mid": config_c3_mid, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5, "c5mid": config_c5_mid}
+CONFIGS = {"c1": config_c1, "c3small": config_c3_small, "c3mid": config_c3_mid, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5, "c5mid": config_c5_mid,
+           "c4mid": config_c4_mid}
 
 
 def graded_breakpoints(a, ncell, coords, ratio=1.5, tol=1e-3):
