@@ -98,7 +98,7 @@ def test_band_trace_adjoint_at_scale(c4mid):
     d[idx] = torch.tensor(rng.uniform(0.5, 1.0, 64), dtype=torch.float64, device="cuda")
     fd = (energy(V + d) - energy(V - d)) / 2.0
     ad = float(torch.dot(d, g))
-    assert abs(fd - ad) <= 1e-6 * abs(ad) + 1e-14 * abs(float(E))
+    assert abs(fd - ad) <= 1e-6 * abs(ad) + 1e-14 * abs(float(E.detach()))
 
     # the oracle's fields on a 2^3 block of cells around a nucleus: w_q sum_v |u_v(x_q)|^2 there
     from scipy.spatial import cKDTree
@@ -119,7 +119,7 @@ def test_band_trace_adjoint_at_scale(c4mid):
     go = solver.band_trace_grad_V(pr, Xb)
     pts = np.concatenate([quad.points[quad.offset[e]:quad.offset[e + 1]] for e in cells])
     gob = np.concatenate([go[quad.offset[e]:quad.offset[e + 1]] for e in cells])
-    tree = cKDTree(xyz.cpu().numpy())
+    tree = cKDTree(np.asarray(xyz))
     dist, j = tree.query(pts)
     assert np.max(dist) < 1e-9   # the same point sets on both sides
     gb = g.cpu().numpy()[j]
