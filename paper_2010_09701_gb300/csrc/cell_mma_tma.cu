@@ -297,12 +297,12 @@ __global__ void __launch_bounds__(THREADS, 1) k_cell_mma_tma(const TmaArgs A) {
         if (u >= 1 && !mbar_wait(&b_empty[sb], (uint32_t)((u - 1) & 1), &s_fail)) break;
         unsigned char* b0 = sB + sb * B_STAGE;
         // each thread owns one vector column v and the row pairs (kk, kk+1) p = r0 + TPV w of the
-        // K tile (TPV threads per vector: 16 pairs each for 64-vector tiles, 32 for 128); the loads
-        // of a batch are issued together so their latencies overlap, and each pair is written to
-        // shared memory as one packed bf16x2 word per plane
+        // K tile (TPV threads per vector: 16 pairs each for 64-vector tiles, 32 for 128); all the
+        // thread's loads of a K tile are issued together so their latencies overlap, and each pair
+        // is written to shared memory as one packed bf16x2 word per plane
         constexpr int TPV = 128 / NVT;
         const int v = gt % NVT, r0 = gt / NVT;          // r0 in [0, TPV)
-        constexpr int BATCH = 16;                       // pairs per batch: 32 loads in flight
+        constexpr int BATCH = KT / (2 * TPV);           // pairs per batch: all the thread's loads in flight
         const bool vok = v0 + v < P.nv;
 #pragma unroll 1
         for (int j0 = 0; j0 < KT / (2 * TPV); j0 += BATCH) {
