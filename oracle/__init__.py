@@ -20,4 +20,9 @@ enrichment  truncated atomic orbitals, smooth cutoff, Bloch phase, supports
 operators   cell Hamiltonians, orthogonalizing coefficients, overlap blocks
 solver      Chebyshev filter, Cholesky-QR, Rayleigh-Ritz, occupations,
             density, band energy, adjoint, residuals
+electrostatics  smeared nuclear charges, their potential, the periodic Poisson
+            solve, the nuclear correction, the electrostatic energy
+xc          LDA exchange and correlation (Ceperley-Alder data, Perdew-Zunger fit)
+mixing      linear and Anderson density mixing
+scf         the self-consistent field loop and the total energy
 """
