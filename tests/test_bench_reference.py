@@ -46,6 +46,9 @@ def test_workload_description_follows_the_configuration():
     assert large == ("c5_mixed_gamma_62atom_32cube_p6: supercell a=16.4 bohr, 62 atoms (Z 14/6), graded 32^3 cells "
                      "p=6, 310 enrichment functions, Gamma point (real), 360 vectors/k, Chebyshev degree 50")
     assert not bench.is_complex(W.CONFIGS["c5"]()) and bench.is_complex(W.CONFIGS["c3"]())
+    c4 = bench.workload_text(W.CONFIGS["c4mid"]())
+    assert c4 == ("c4mid_c64_8k_16atom_12cube_p6: supercell a=12 bohr, 16 atoms (Z 14/6), graded 12^3 cells p=6, "
+                  "80 enrichment functions, MP 2x2x2 (8 k, complex), 97-123 vectors/k, Chebyshev degree 30")
 
 
 def test_refined_cell_count_used_for_traffic_scaling():
