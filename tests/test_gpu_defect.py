@@ -3,7 +3,7 @@
 filter: the identity on arbitrary blocks, the accuracy it keeps on nearly
 converged blocks, and converged subspace iteration on the first
 configuration (graded 8^3 mesh, p = 4, two nuclei, 20 vectors, degree 20) to
-the spec residual, with eigenvalues and band energy against exact
+a residual below 1e-7, with eigenvalues and band energy against exact
 eigenpairs of the oracle's operator."""
 import numpy as np
 import pytest
@@ -88,7 +88,7 @@ def _exact_lowest(pr, k, sigma):
 def test_c1_defect_passes_reach_residual_target(products):
     # subspace iteration on the first configuration with the bench's pass (BF16 tensor-core filter in
     # defect form from the previous Ritz pairs, FP64-class Cholesky-QR and Rayleigh-Ritz): the
-    # occupied states reach a residual below 1e-7 (the benchmark spec's target for the chosen forms);
+    # occupied states reach a residual below 1e-7 (the target for the mixed-precision forms);
     # their eigenvalues then match the oracle operator's exact ones within 1e-8 Ha and the band
     # energy within 1e-6 Ha/atom
     from paper_2010_09701_gb300 import (F64_PAIRS, FILTER_BF16X3, FILTER_LAST_FP64, STORE_BF16X6, STORE_F64,

@@ -379,8 +379,8 @@ def test_lanczos_upper_bound():
 
 @pytest.mark.parametrize("k", [(0.0, 0.0, 0.0), (0.25, -0.4, 0.1)])
 def test_residual_norms_closed_form(k):
-    # residual of a mixture of two exact eigenvectors (Sec. IV, Eq. ProjKS; the norm of the survey's
-    # step 16). With M-orthonormal eigenpairs (eps_i, u_i), (eps_j, u_j) of H u = eps M u and
+    # residual of a mixture of two exact eigenvectors (Sec. IV, Eq. ProjKS; the residual norm
+    # ||H u - eps M u||_{M^-1} / ||u||_M). With M-orthonormal eigenpairs (eps_i, u_i), (eps_j, u_j) of H u = eps M u and
     # u = s (u_i + d u_j):
     #   H u - t M u = s M [(eps_i - t) u_i + d (eps_j - t) u_j],
     #   ||.||_{M^-1}^2 = s^2 [(eps_i - t)^2 + d^2 (eps_j - t)^2],  ||u||_M^2 = s^2 (1 + d^2),
