@@ -13,6 +13,11 @@ Readings:
   E_tot = E_band + E_xc[rho] + E_elec[rho] - int rho V_xc - int rho phi_tot; at self-consistency it
   is the Kohn-Sham total energy.
 * The first input density is the neutralizing smeared charge sum_I Z_I g(|x - R_I|).
+* With ``degree`` set, the eigenstates of every pass but the first come from the paper's
+  Chebyshev-filtered subspace iteration instead (Sec. IV): one filter pass of that degree on the
+  previous pass's states, with a = the largest previous Ritz value, a0 one below the smallest and b
+  a Lanczos upper bound of the new operator, then Cholesky-QR and Rayleigh-Ritz. The first pass
+  takes exact eigenstates (an initial subspace).
 """
 import numpy as np
 import scipy.sparse as sp
@@ -24,7 +29,8 @@ from .operators import Problem
 
 
 class SCF:
-    def __init__(self, mesh, quad, enr, pos, Z, nstates, ks=((0.0, 0.0, 0.0),), w_k=None, T=500.0):
+    def __init__(self, mesh, quad, enr, pos, Z, nstates, ks=((0.0, 0.0, 0.0),), w_k=None, T=500.0,
+                 degree=None):
         self.mesh, self.quad = mesh, quad
         self.pos = np.asarray(pos, float).reshape(-1, 3)
         self.Z = np.asarray(Z, float)
@@ -40,6 +46,7 @@ class SCF:
         self.A, self.tabs = es.poisson_matrices(mesh, quad)
         self.lu = es.poisson_factor(self.A)
         self.prev = {}
+        self.degree = degree
 
     def initial_density(self):
         return -self.b
@@ -51,7 +58,19 @@ class SCF:
         exc, vxc = xc.lda(rho)
         return phi_aux, phi_aux + self.corr, exc, vxc
 
+    def filtered(self, pr, V):
+        """One pass of the Chebyshev-filtered subspace iteration from the previous pass's states."""
+        pr.build(V)
+        eps0, X0 = self.prev[id(pr)][:2]
+        b = solver.lanczos_upper_bound(pr.apply_H, pr.apply_M, pr.apply_Minv, X0[:, -1], 20)
+        Y = solver.chebyshev_filter(pr.apply_A, X0, self.degree, float(eps0[-1]), b, float(eps0[0]) - 1.0)
+        vals, vecs = solver.rayleigh_ritz(solver.cholqr(Y, pr.apply_M), pr.apply_H, pr.apply_M)
+        self.prev[id(pr)] = (vals, vecs) + tuple(self.prev[id(pr)][2:])
+        return vals, vecs
+
     def eigenstates(self, pr, V):
+        if self.degree is not None and id(pr) in self.prev:
+            return self.filtered(pr, V)
         pr.build(V)
         H = pr.assemble_H().tocsc()
         M = sp.block_diag((sp.diags(pr.m), sp.csr_matrix(pr.Moo))).tocsc()

@@ -135,7 +135,7 @@ def test_mixing_on_a_linear_fixed_point():
     assert np.linalg.norm(y - xs) > 1e-3 * np.linalg.norm(xs)
 
 
-def test_scf_helium_lda_total_energy():
+def test_scf_helium_lda_total_energy_exact_and_filtered():
     # the whole loop (smeared-charge Poisson, nuclear correction, LDA, eigenstates, occupations,
     # density, Anderson mixing, E_tot) on a helium atom in a periodic box of 8 bohr, where its
     # neighbours' images are negligible (a neutral, spherical atom): the LDA total energy of the
@@ -160,3 +160,9 @@ def test_scf_helium_lda_total_energy():
     # point sets, which differ by the lumping error
     assert abs(np.sum(quad.weights * rho) - 2.0) < 1e-4
     assert abs(etot[-1] - (-2.834836)) < 4e-3
+    # the same loop with the paper's eigensolver: one Chebyshev filter pass (degree 40) per SCF pass
+    # on six vectors, Cholesky-QR and Rayleigh-Ritz (Sec. IV): the same self-consistent energy
+    run.degree, run.nstates, run.prev = 40, 6, {}
+    mix = mixing.Anderson(0.5, 20, quad.weights)
+    _, etot_f, res_f, _ = run.run(mix.step, maxit=60, tol=1e-7)
+    assert res_f[-1] < 1e-7 and abs(etot_f[-1] - etot[-1]) < 1e-7
