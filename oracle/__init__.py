@@ -16,6 +16,7 @@ Modules
 fe1d        1D GLL and Gauss rules, Lagrange basis on GLL nodes
 mesh        periodic rectilinear spectral-element mesh, lumped GLL mass
 quadrature  per-cell point sets (plain, enriched, octree toward nuclei)
+adaptive    convergence-driven adaptive point sets (trial integrals per box)
 enrichment  truncated atomic orbitals, smooth cutoff, Bloch phase, supports
 operators   cell Hamiltonians, orthogonalizing coefficients, overlap blocks
 solver      Chebyshev filter, Cholesky-QR, Rayleigh-Ritz, occupations,
