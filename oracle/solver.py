@@ -150,3 +150,35 @@ def lanczos_upper_bound(apply_H, apply_M, apply_Minv, v0, steps):
         q_prev, q = q, w / beta
     T = np.diag(alphas) + np.diag(betas[:-1], 1) + np.diag(betas[:-1], -1)
     return np.max(np.linalg.eigvalsh(T)) + betas[-1]
+
+
+def subspace_iteration(pr, X, m, passes, b, lock_tol=None):
+    """Chebyshev-filtered subspace iteration (Sec. IV) from the block X: per pass the degree-m filter
+    with a = the largest Ritz value of the previous pass (the largest eigenvalue of the first
+    Rayleigh-Ritz before the first pass), a0 one below the smallest, b the given upper bound; then
+    Cholesky-QR and Rayleigh-Ritz over the whole block.
+
+    With ``lock_tol``, the Ritz vectors whose residual (``residual_norms``) is below it stay out of
+    the next filter (locking: the leading converged columns keep their vectors; the filter runs on
+    the rest) but take part in the orthonormalization and the projection. Reading: the locked set
+    is the longest leading run of converged Ritz vectors in ascending order, so the filtered
+    columns are one contiguous block.
+
+    Returns (eps, X, residuals per pass, filtered column-degrees per pass)."""
+    Q = cholqr(X, pr.apply_M)
+    eps, X = rayleigh_ritz(Q, pr.apply_H, pr.apply_M)
+    res_hist, work = [], []
+    nlock = 0
+    for _ in range(passes):
+        a, a0 = float(eps[-1]), float(eps[0]) - 1.0
+        Y = X.copy()
+        Y[:, nlock:] = chebyshev_filter(pr.apply_A, X[:, nlock:], m, a, b, a0)
+        work.append(m * (X.shape[1] - nlock))
+        eps, X = rayleigh_ritz(cholqr(Y, pr.apply_M), pr.apply_H, pr.apply_M)
+        r = residual_norms(pr, X, eps)
+        res_hist.append(r)
+        if lock_tol is not None:
+            ok = r < lock_tol
+            nlock = int(np.argmin(ok)) if not np.all(ok) else len(ok)
+            nlock = min(nlock, X.shape[1] - 1)   # keep one column filtered: a keeps moving
+    return eps, X, res_hist, work
