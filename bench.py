@@ -48,10 +48,15 @@ TRAFFIC_TENSOR = {   # bf16 parts of the split -> DRAM bytes per (k, cell, 64-ve
     3: {"bytes_per_tile": (3.064588e9 + 0.008374e9) / 1728, "source": "profiles/k_cell_mma_tma_c3mid_12cube_p6.md"},
 }
 TRAFFIC_FP64 = None   # {"bytes_per_cell", "source"} from a capture of the current FP64 product kernels
-# the FP64-class products in pair mode: DRAM bytes per launch and cell of each kind, from the 8^3 capture
-# of the launch shape kept at the bench size (two vectors per CTA of 512 threads)
-TRAFFIC_PAIR = {"sf_bytes_per_cell": (344.007e6 + 151.686e6) / 448, "dense_bytes_per_cell": (319.195e6 + 19.950e6) / 64,
-                "source": "profiles/fp64_class_products_c3small_8cube_p6.md"}
+# the FP64-class products in pair mode, real data: DRAM bytes of the sum-factorized kernel per launch
+# of 64 columns and single-leaf cell, from the capture of the current kernel on the 16^3 supercell
+# (3600 single-leaf cells; eight vectors per CTA there); the refined cells' dense product is not in it.
+# Complex data has no capture of the current kernel (the one of the small zincblende cell predates the
+# chunk-major enrichment rows), so its traffic is reported as unknown.
+TRAFFIC_PAIR = {"sf_bytes_per_cell": (2.167341e9 + 0.736962e9) / 3600,
+                "source": ("profiles/fp64_class_product_fields_wide_c5mid_16cube_p6.md: k_cell_apply_sf DRAM bytes "
+                           "per single-leaf cell, scaled by the single-leaf cells; the refined cells' dense product "
+                           "not included")}
 
 
 def is_complex(w):
@@ -573,9 +578,8 @@ def run_ours(args, rank, world):
         n_dense = nucleus_cells(w)
         n_sf = len(naug) - n_dense
         traffic = None
-        if pairs and TRAFFIC_PAIR:
-            traffic = {"bytes": TRAFFIC_PAIR["sf_bytes_per_cell"] * n_sf + TRAFFIC_PAIR["dense_bytes_per_cell"] * n_dense,
-                       "source": TRAFFIC_PAIR["source"] + " (scaled by cells of each kind)"}
+        if pairs and TRAFFIC_PAIR and not cplx:
+            traffic = {"bytes": TRAFFIC_PAIR["sf_bytes_per_cell"] * n_sf, "source": TRAFFIC_PAIR["source"]}
         elif not pairs and TRAFFIC_FP64:
             traffic = {"bytes": TRAFFIC_FP64["bytes_per_cell"] * len(naug),
                        "source": TRAFFIC_FP64["source"] + " (scaled by cells)"}
