@@ -572,7 +572,8 @@ def run_ours(args, rank, world):
     if fp64_ms_launch is not None:
         f64_flops = ctx.product_flops(0, vslice)   # FP64-class operations of one launch (<= 64 vectors)
         f64_ach = f64_flops / (fp64_ms_launch * 1e-3) / 1e12
-        fp64["product"] = {"kernel": "k_cell_apply_sf<double> + k_cell_apply_z3", "ms_per_launch": fp64_ms_launch,
+        fp64["product"] = {"kernel": "k_cell_apply_sf<double> + %s" % ("k_cell_apply_z3" if cplx else "k_cell_apply<double>"),
+                           "ms_per_launch": fp64_ms_launch,
                            "achieved_tflops": f64_ach, "frac_of_fp64_peak": f64_ach / FP64_PEAK_DERIVED}
         mix_ach = f64_flops / (mix_ms_launch * 1e-3) / 1e12
         n_dense = nucleus_cells(w)
@@ -586,12 +587,13 @@ def run_ours(args, rank, world):
         if pairs:
             # the refined cells (dense FP64) take a few percent of the launch; the peak is that of
             # the pair arithmetic on the FP32 pipe
-            kname = ("k_cell_apply_sf<f2> + k_cell_apply_z3 (FP64-class cell products: sum factorization in "
-                     "FP32-pair arithmetic on single-leaf cells, FP64 dense on the refined cells)")
+            kname = ("k_cell_apply_sf<f2> + %s (FP64-class cell products: sum factorization in "
+                     "FP32-pair arithmetic on single-leaf cells, FP64 dense on the refined cells)"
+                     % ("k_cell_apply_z3" if cplx else "k_cell_apply<double>"))
             peak, psrc = PAIR_PEAK_DERIVED, "derived: 152 SM x 128 FP32 lanes x 2070 MHz / 12 per pair FMA x 2 flops"
         else:
-            kname = ("k_cell_apply_sf + k_cell_apply_z3 (FP64 cell products: sum factorization on "
-                     "single-leaf cells, dense with 3 real multiplications on the refined cells)")
+            kname = ("k_cell_apply_sf + %s (FP64 cell products: sum factorization on single-leaf cells, "
+                     "dense on the refined cells)" % ("k_cell_apply_z3" if cplx else "k_cell_apply<double>"))
             peak, psrc = FP64_PEAK_DERIVED, "derived: 152 SM x 2 DFMA/clk x 2 flops x 2070 MHz"
         roof_fp64 = {"kernel": kname,
                      "bound": "alu", "achieved": mix_ach, "peak": peak, "unit": "TFLOP/s",
